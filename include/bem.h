@@ -1,0 +1,198 @@
+/*
+ * bem.h -- C ABI of the GB300 library for acoustic transmission through a
+ * penetrable object with nonconforming interior and exterior surface grids
+ * (van 't Wout, "The boundary element method for acoustic transmission with
+ * nonconforming grids", arXiv 2206.00708).
+ *
+ * Plain C: pointers, sizes and status codes only.  Every call returns a
+ * bem_status; 0 is success and negative values are errors.  The message of the
+ * last error on the calling thread is available from bem_last_error().  No call
+ * aborts the process and no device code traps.
+ *
+ * Ownership: inputs are copied during the call and stay owned by the caller.
+ * Handles (contexts, grids, matrices, sparse matrices) belong to the library
+ * and are released with their *_destroy call.  Output arrays are allocated by
+ * the caller with the sizes stated at each call.
+ *
+ * Conventions (paper Sec. 2): time dependence exp(-i omega t); Green's function
+ * G(x,y) = exp(i k |x-y|) / (4 pi |x-y|); triangles are counter-clockwise seen
+ * from outside so that the normal (b-a) x (c-a) points outward; P1 degrees of
+ * freedom are the grid vertices, in the caller's vertex order.
+ *
+ * Complex numbers are two doubles (re, im), interleaved.  Dense matrices are
+ * row-major: entry (i, j) (test function i, trial function j) is element
+ * i * n_cols + j.
+ */
+#ifndef BEM_GB300_H
+#define BEM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Exported symbols keep default visibility when the library hides the rest. */
+#if defined(__GNUC__)
+#define BEM_API __attribute__((visibility("default")))
+#else
+#define BEM_API
+#endif
+
+typedef int32_t bem_status;
+
+#define BEM_OK                    0
+#define BEM_E_INVALID_ARG        -1  /* a pointer, size, enum or value is not allowed      */
+#define BEM_E_OOM                -2  /* device or host allocation failed                   */
+#define BEM_E_NOT_CONVERGED      -3  /* GMRES hit maxiter; outputs hold the last iterate   */
+#define BEM_E_NONFINITE          -4  /* a NaN or Inf was found in an input or a result     */
+#define BEM_E_TIMEOUT            -5  /* a request exceeded its time limit                  */
+#define BEM_E_ADMISSION_REFUSED  -6  /* a request can never fit the server's memory budget */
+#define BEM_E_BUSY               -7  /* poll: the request is not finished yet              */
+#define BEM_E_CUDA               -8  /* a CUDA runtime call failed                         */
+#define BEM_E_INTERNAL           -9  /* an internal consistency check failed               */
+
+typedef struct { double re, im; } bem_c128;
+
+typedef struct bem_context bem_context;
+typedef struct bem_grid    bem_grid;
+typedef struct bem_matrix  bem_matrix;
+typedef struct bem_sparse  bem_sparse;
+
+/* Operators (paper Sec. 2.1, eq. for V, K, T, D; Sec. 3.1 for M). */
+#define BEM_OP_V 0   /* single layer:            int int G phi_j theta_i                 */
+#define BEM_OP_K 1   /* double layer:            int int dG/dn(y) phi_j theta_i          */
+#define BEM_OP_T 2   /* adjoint double layer:    int int dG/dn(x) phi_j theta_i          */
+#define BEM_OP_D 3   /* hypersingular (with the paper's minus sign), Maue's weak form     */
+
+/* Arithmetic of assembly and matvec. */
+#define BEM_PREC_FP64   0   /* float64 throughout                                        */
+
+/* Sign variant of the multiple-traces system (paper eq. mtf:discrete). */
+#define BEM_MTF_DERIVED 0   /* transfer blocks as derived from Sec. 2.2: returns phi_int, psi_int */
+#define BEM_MTF_PRINTED 1   /* transfer blocks with the signs printed in eq. mtf:discrete      */
+
+/* Thread-local message of the last failing call (never NULL). */
+BEM_API const char* bem_last_error(void);
+
+/* Library version string. */
+BEM_API const char* bem_version(void);
+
+/* ---------------------------------------------------------------- context
+ * A context binds a CUDA device and a stream.  `stream` is a cudaStream_t
+ * passed as void*; NULL makes the context create and own a non-blocking stream.
+ * A context is not thread-safe: one caller thread at a time.                 */
+BEM_API bem_status bem_context_create(int device, void* stream, bem_context** out);
+BEM_API bem_status bem_context_destroy(bem_context* ctx);
+/* Block until all work queued on the context's stream has finished. */
+BEM_API bem_status bem_context_synchronize(bem_context* ctx);
+
+/* ---------------------------------------------------------------- grids
+ * Grid intake (paper Sec. 2.4 and Sec. 3: a conforming triangular surface grid).
+ *   xyz  [nv*3] float64 vertex coordinates; tri [nt*3] int32 vertex indices,
+ *   counter-clockwise seen from outside.  With on_device = 1 both pointers are
+ *   device pointers on the context's device; otherwise host pointers.
+ * Errors: BEM_E_INVALID_ARG for nv < 3, nt < 1, an index outside [0, nv), a
+ * triangle with a repeated vertex or zero area; BEM_E_NONFINITE for a NaN/Inf
+ * coordinate.                                                                 */
+BEM_API bem_status bem_grid_create(bem_context* ctx, const double* xyz, int64_t nv,
+                           const int32_t* tri, int64_t nt, int on_device, bem_grid** out);
+BEM_API bem_status bem_grid_destroy(bem_grid* g);
+BEM_API int64_t    bem_grid_num_vertices(const bem_grid* g);
+BEM_API int64_t    bem_grid_num_triangles(const bem_grid* g);
+
+/* ---------------------------------------------------------------- assembly
+ * Dense Galerkin matrix of operator `op` (BEM_OP_*) for wavenumber k on one P1
+ * space (paper Sec. 2.1 and Sec. 2.4; quadrature of Sec. 5.1: a 6-point
+ * degree-4 triangle rule per triangle for pairs without a common vertex,
+ * Sauter-Schwab transformations with n_singular Gauss points per axis for
+ * coincident, edge- and vertex-adjacent pairs).  test must equal trial (both
+ * operators of the method act within one grid).  n_singular in [1, 16].
+ * The result is a library-owned device matrix of nv x nv complex128.         */
+BEM_API bem_status bem_assemble(bem_context* ctx, int op, bem_c128 k, const bem_grid* test,
+                        const bem_grid* trial, int precision, int n_singular,
+                        bem_matrix** out);
+BEM_API bem_status bem_matrix_destroy(bem_matrix* m);
+/* Copy a matrix out, row-major complex128.  dst_bytes must be at least
+ * rows*cols*16.  on_device = 1: dst is a device pointer (copy on the stream,
+ * asynchronous); 0: dst is host memory (the call waits).                      */
+BEM_API bem_status bem_matrix_copy_out(bem_context* ctx, const bem_matrix* m, void* dst,
+                               int64_t dst_bytes, int on_device);
+BEM_API bem_status bem_matrix_shape(const bem_matrix* m, int64_t* rows, int64_t* cols);
+
+/* ---------------------------------------------------------------- sparse
+ * Mass matrix of one grid, M_ij = <phi_j, theta_i> (paper Sec. 3.1).         */
+BEM_API bem_status bem_mass(bem_context* ctx, const bem_grid* g, bem_sparse** out);
+/* Mortar matrix P_ab (paper Sec. 3.1): entry (i, j) is the L2 product of test
+ * function i on grid a with basis function j on grid b over the common surface.
+ * The common surface of two different polyhedra is read through central
+ * projection from `center` ([3] host doubles; NULL means the origin): each
+ * triangle of b is projected onto the plane of each triangle of a along rays from
+ * the centre, and on that plane basis j is the linear function of the projected
+ * triangle.  For coplanar grids this is the plain mortar matrix; for identical
+ * grids it is the mass matrix.  Both surfaces must be star-shaped about center.
+ * P_ba = P_ab^T (Sec. 5.4).                                                   */
+BEM_API bem_status bem_projection(bem_context* ctx, const bem_grid* a, const bem_grid* b,
+                          const double* center, bem_sparse** out);
+BEM_API bem_status bem_sparse_destroy(bem_sparse* s);
+/* Coordinate (COO) form.  Entries may repeat a (row, col) pair; repeated entries
+ * add up.  Query nnz first, then copy into host arrays of at least nnz items.  */
+BEM_API bem_status bem_sparse_info(const bem_sparse* s, int64_t* rows, int64_t* cols, int64_t* nnz);
+BEM_API bem_status bem_sparse_copy_out(bem_context* ctx, const bem_sparse* s, int32_t* row,
+                               int32_t* col, double* val, int64_t capacity);
+
+/* ---------------------------------------------------------------- solve
+ * Incident field: n_rhs plane waves amp_r * exp(i k_ext x . d_r) (paper
+ * eq. planewave), dirs [n_rhs*3] unit vectors, amps [n_rhs] (NULL = all 1).  */
+typedef struct {
+    int32_t         n_rhs;
+    const double*   dirs;
+    const bem_c128* amps;
+} bem_incident;
+
+typedef struct {
+    double  gmres_tol;        /* relative residual of the preconditioned system (default 1e-8)  */
+    int32_t gmres_maxiter;    /* default 2000; unrestarted (paper Sec. 5.1)                       */
+    int32_t precision;        /* BEM_PREC_*                                                       */
+    int32_t n_singular;       /* Gauss points per axis of singular pairs (default 4)             */
+    int32_t mtf_variant;      /* BEM_MTF_DERIVED (default) or BEM_MTF_PRINTED                     */
+    double  center[3];        /* projection centre for the mortar (default origin)               */
+} bem_solve_opts;
+
+typedef struct {
+    int32_t iterations;       /* GMRES iterations of the last right-hand side                    */
+    int32_t converged;        /* 1 if every right-hand side met gmres_tol                        */
+    double  residual;         /* final relative preconditioned residual (max over RHS)           */
+    double  t_assembly_ms;    /* device time of operator assembly (both grids)                   */
+    double  t_mortar_ms;      /* device time of mass + mortar matrices                           */
+    double  t_solve_ms;       /* device time of right-hand sides + GMRES                         */
+    int32_t mtf_variant;      /* sign variant used                                               */
+    int32_t reserved;
+} bem_solve_report;
+
+/* Fill opts with the defaults stated above. */
+BEM_API void bem_solve_opts_default(bem_solve_opts* opts);
+
+/* Solve the mass-preconditioned multiple-traces system (paper eq. mtf:discrete
+ * with the left preconditioner of Sec. 3.3) for plane-wave incidence from the
+ * exterior, on exterior grid `ext` (wavenumber k_ext) and interior grid `intr`
+ * (wavenumber k_int), density ratio rho_int / rho_ext.
+ * Outputs (caller-owned, host memory unless opts-independent flag on_device=1):
+ *   v_ext, w_ext [n_rhs * N_ext]: P1 coefficients of phi_ext = -gamma_D^+ p and
+ *                                 psi_ext = -gamma_N^+ p (paper Sec. 2.2);
+ *   v_int, w_int [n_rhs * N_int]: phi_int = gamma_D^- p and psi_int = gamma_N^- p
+ *                                 (negated for BEM_MTF_PRINTED).
+ * Right-hand side r occupies [r*N, (r+1)*N).  rep may be NULL.
+ * BEM_E_NOT_CONVERGED still writes the last iterate and the report.           */
+BEM_API bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const bem_grid* intr,
+                                  bem_c128 k_int, bem_c128 k_ext, double rho_int_over_rho_ext,
+                                  const bem_incident* inc, const bem_solve_opts* opts,
+                                  bem_c128* v_ext, bem_c128* w_ext,
+                                  bem_c128* v_int, bem_c128* w_int,
+                                  int on_device, bem_solve_report* rep);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEM_GB300_H */

@@ -1,0 +1,317 @@
+"""Thin Python binding of libbem.so, the GB300 library for acoustic transmission
+through a penetrable object with nonconforming grids (arXiv 2206.00708).
+
+Argument marshalling only: every numerical step runs in the CUDA library behind
+the C ABI of `include/bem.h`.  The functions keep the C names.  Host arrays are
+NumPy arrays; device arrays are CUDA torch tensors (PyTorch provides device
+memory and streams, nothing else).  A missing library raises at import time:
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libbem.so")
+
+BEM_OK = 0
+BEM_E_INVALID_ARG = -1
+BEM_E_OOM = -2
+BEM_E_NOT_CONVERGED = -3
+BEM_E_NONFINITE = -4
+BEM_E_TIMEOUT = -5
+BEM_E_ADMISSION_REFUSED = -6
+BEM_E_BUSY = -7
+BEM_E_CUDA = -8
+BEM_E_INTERNAL = -9
+
+BEM_OP_V, BEM_OP_K, BEM_OP_T, BEM_OP_D = 0, 1, 2, 3
+BEM_PREC_FP64 = 0
+BEM_MTF_DERIVED, BEM_MTF_PRINTED = 0, 1
+
+
+class BemError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"bem status {status}: {message}")
+        self.status = status
+
+
+class bem_c128(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class bem_incident(C.Structure):
+    _fields_ = [("n_rhs", C.c_int32), ("dirs", C.POINTER(C.c_double)), ("amps", C.POINTER(bem_c128))]
+
+
+class bem_solve_opts(C.Structure):
+    _fields_ = [
+        ("gmres_tol", C.c_double),
+        ("gmres_maxiter", C.c_int32),
+        ("precision", C.c_int32),
+        ("n_singular", C.c_int32),
+        ("mtf_variant", C.c_int32),
+        ("center", C.c_double * 3),
+    ]
+
+
+class bem_solve_report(C.Structure):
+    _fields_ = [
+        ("iterations", C.c_int32),
+        ("converged", C.c_int32),
+        ("residual", C.c_double),
+        ("t_assembly_ms", C.c_double),
+        ("t_mortar_ms", C.c_double),
+        ("t_solve_ms", C.c_double),
+        ("mtf_variant", C.c_int32),
+        ("reserved", C.c_int32),
+    ]
+
+
+_VP = C.c_void_p
+_PVP = C.POINTER(C.c_void_p)
+_I64 = C.c_int64
+_PI64 = C.POINTER(C.c_int64)
+
+_SIGNATURES = {
+    "bem_last_error": (C.c_char_p, []),
+    "bem_version": (C.c_char_p, []),
+    "bem_context_create": (C.c_int32, [C.c_int, _VP, _PVP]),
+    "bem_context_destroy": (C.c_int32, [_VP]),
+    "bem_context_synchronize": (C.c_int32, [_VP]),
+    "bem_grid_create": (C.c_int32, [_VP, _VP, _I64, _VP, _I64, C.c_int, _PVP]),
+    "bem_grid_destroy": (C.c_int32, [_VP]),
+    "bem_grid_num_vertices": (C.c_int64, [_VP]),
+    "bem_grid_num_triangles": (C.c_int64, [_VP]),
+    "bem_assemble": (C.c_int32, [_VP, C.c_int, bem_c128, _VP, _VP, C.c_int, C.c_int, _PVP]),
+    "bem_matrix_destroy": (C.c_int32, [_VP]),
+    "bem_matrix_copy_out": (C.c_int32, [_VP, _VP, _VP, _I64, C.c_int]),
+    "bem_matrix_shape": (C.c_int32, [_VP, _PI64, _PI64]),
+    "bem_mass": (C.c_int32, [_VP, _VP, _PVP]),
+    "bem_projection": (C.c_int32, [_VP, _VP, _VP, C.POINTER(C.c_double), _PVP]),
+    "bem_sparse_destroy": (C.c_int32, [_VP]),
+    "bem_sparse_info": (C.c_int32, [_VP, _PI64, _PI64, _PI64]),
+    "bem_sparse_copy_out": (C.c_int32, [_VP, _VP, _VP, _VP, _VP, _I64]),
+    "bem_solve_opts_default": (None, [C.POINTER(bem_solve_opts)]),
+    "bem_solve_transmission": (C.c_int32, [_VP, _VP, _VP, bem_c128, bem_c128, C.c_double,
+                                           C.POINTER(bem_incident), C.POINTER(bem_solve_opts),
+                                           _VP, _VP, _VP, _VP, C.c_int, C.POINTER(bem_solve_report)]),
+}
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with __graft_entry__.build() "
+                          "(the GB300 path has no CPU fallback)")
+    lib = C.CDLL(_LIB_PATH, mode=C.RTLD_GLOBAL)
+    for name, (res, args) in _SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def library():
+    """The loaded ctypes library (for tests that check the exported symbols)."""
+    return _lib
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def _check(status):
+    if status != BEM_OK:
+        raise BemError(status, _lib.bem_last_error().decode())
+    return status
+
+
+def _c128(z):
+    z = complex(z)
+    return bem_c128(z.real, z.imag)
+
+
+def _ptr(a):
+    """Data pointer of a NumPy array (host) or a torch tensor (device)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return C.c_void_p(a.ctypes.data), False
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return C.c_void_p(a.data_ptr()), bool(a.is_cuda)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+# ------------------------------------------------------------------ context / grids
+def bem_version():
+    return _lib.bem_version().decode()
+
+
+def bem_context_create(device=0, stream=None):
+    """stream: a torch.cuda.Stream, an integer cudaStream_t, or None (own stream)."""
+    h = C.c_void_p()
+    s = None
+    if stream is not None:
+        s = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(_lib.bem_context_create(int(device), s, C.byref(h)))
+    return h
+
+
+def bem_context_destroy(ctx):
+    _check(_lib.bem_context_destroy(ctx))
+
+
+def bem_context_synchronize(ctx):
+    _check(_lib.bem_context_synchronize(ctx))
+
+
+def bem_grid_create(ctx, xyz, tri):
+    """xyz float64 [N,3], tri int32 [T,3]: both NumPy (host) or both CUDA tensors."""
+    if isinstance(xyz, np.ndarray):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+    px, dx = _ptr(xyz)
+    pt, dt = _ptr(tri)
+    if dx != dt:
+        raise ValueError("xyz and tri must both be on the host or both on the device")
+    h = C.c_void_p()
+    _check(_lib.bem_grid_create(ctx, px, int(xyz.shape[0]), pt, int(tri.shape[0]), int(dx), C.byref(h)))
+    return h
+
+
+def bem_grid_destroy(g):
+    _check(_lib.bem_grid_destroy(g))
+
+
+def bem_grid_num_vertices(g):
+    return int(_lib.bem_grid_num_vertices(g))
+
+
+def bem_grid_num_triangles(g):
+    return int(_lib.bem_grid_num_triangles(g))
+
+
+# ------------------------------------------------------------------ operators
+def bem_assemble(ctx, op, k, test, trial=None, precision=BEM_PREC_FP64, n_singular=4):
+    h = C.c_void_p()
+    _check(_lib.bem_assemble(ctx, int(op), _c128(k), test, trial if trial is not None else test,
+                             int(precision), int(n_singular), C.byref(h)))
+    return h
+
+
+def bem_matrix_destroy(m):
+    _check(_lib.bem_matrix_destroy(m))
+
+
+def bem_matrix_shape(m):
+    r, c = C.c_int64(), C.c_int64()
+    _check(_lib.bem_matrix_shape(m, C.byref(r), C.byref(c)))
+    return r.value, c.value
+
+
+def bem_matrix_copy_out(ctx, m, out=None):
+    """Copy into `out` (complex128 NumPy array or CUDA tensor); allocates a NumPy
+    array when out is None.  Returns out."""
+    rows, cols = bem_matrix_shape(m)
+    if out is None:
+        out = np.empty((rows, cols), dtype=np.complex128)
+    p, dev = _ptr(out)
+    nbytes = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
+    _check(_lib.bem_matrix_copy_out(ctx, m, p, int(nbytes), int(dev)))
+    return out
+
+
+def bem_mass(ctx, g):
+    h = C.c_void_p()
+    _check(_lib.bem_mass(ctx, g, C.byref(h)))
+    return h
+
+
+def bem_projection(ctx, a, b, center=None):
+    h = C.c_void_p()
+    c = None
+    if center is not None:
+        c = (C.c_double * 3)(*[float(x) for x in center])
+    _check(_lib.bem_projection(ctx, a, b, c, C.byref(h)))
+    return h
+
+
+def bem_sparse_destroy(s):
+    _check(_lib.bem_sparse_destroy(s))
+
+
+def bem_sparse_info(s):
+    r, c, n = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(_lib.bem_sparse_info(s, C.byref(r), C.byref(c), C.byref(n)))
+    return r.value, c.value, n.value
+
+
+def bem_sparse_copy_out(ctx, s):
+    """COO triplets (row int32, col int32, val float64); repeated entries add up."""
+    _, _, nnz = bem_sparse_info(s)
+    row = np.empty(nnz, dtype=np.int32)
+    col = np.empty(nnz, dtype=np.int32)
+    val = np.empty(nnz, dtype=np.float64)
+    _check(_lib.bem_sparse_copy_out(ctx, s, row.ctypes.data, col.ctypes.data, val.ctypes.data, nnz))
+    return row, col, val
+
+
+# ------------------------------------------------------------------ solve
+def bem_solve_opts_default():
+    o = bem_solve_opts()
+    _lib.bem_solve_opts_default(C.byref(o))
+    return o
+
+
+def bem_solve_transmission(ctx, ext, intr, k_int, k_ext, rho_int_over_rho_ext, dirs, amps=None, opts=None,
+                           out=None, on_device=False):
+    """Solve the mass-preconditioned MTF for plane waves `dirs` [n_rhs, 3].
+
+    out: optional dict of preallocated outputs v_ext, w_ext [n_rhs, N_ext] and
+    v_int, w_int [n_rhs, N_int] (complex128 NumPy arrays, or CUDA tensors with
+    on_device=True).  Returns (outputs dict, report dict); raises BemError on
+    failure (BEM_E_NOT_CONVERGED included, with the outputs attached as .outputs).
+    """
+    dirs = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    n_rhs = dirs.shape[0]
+    inc = bem_incident()
+    inc.n_rhs = n_rhs
+    inc.dirs = dirs.ctypes.data_as(C.POINTER(C.c_double))
+    amp_arr = None
+    if amps is not None:
+        amp_arr = (bem_c128 * n_rhs)(*[_c128(a) for a in np.atleast_1d(amps)])
+        inc.amps = C.cast(amp_arr, C.POINTER(bem_c128))
+    if opts is None:
+        opts = bem_solve_opts_default()
+    elif isinstance(opts, dict):
+        o = bem_solve_opts_default()
+        for key, val in opts.items():
+            if key == "center":
+                o.center = (C.c_double * 3)(*val)
+            else:
+                setattr(o, key, val)
+        opts = o
+    Ne, Ni = bem_grid_num_vertices(ext), bem_grid_num_vertices(intr)
+    if out is None:
+        if on_device:
+            raise ValueError("device outputs must be preallocated")
+        out = {k: np.zeros((n_rhs, n), dtype=np.complex128) for k, n in
+               (("v_ext", Ne), ("w_ext", Ne), ("v_int", Ni), ("w_int", Ni))}
+    ptrs = [_ptr(out[k])[0] for k in ("v_ext", "w_ext", "v_int", "w_int")]
+    rep = bem_solve_report()
+    st = _lib.bem_solve_transmission(ctx, ext, intr, _c128(k_int), _c128(k_ext), float(rho_int_over_rho_ext),
+                                     C.byref(inc), C.byref(opts), *ptrs, int(bool(on_device)), C.byref(rep))
+    report = {f: getattr(rep, f) for f, _ in bem_solve_report._fields_}
+    if st != BEM_OK:
+        err = BemError(st, _lib.bem_last_error().decode())
+        err.outputs, err.report = out, report
+        raise err
+    return out, report

@@ -1,0 +1,153 @@
+// Internal declarations of the GB300 transmission-BEM library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/bem.h"
+
+namespace bem {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+
+#define BEM_CUDA_TRY(expr)                                                          \
+    do {                                                                            \
+        cudaError_t e_ = (expr);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            ::bem::set_error(std::string("CUDA error ") + cudaGetErrorString(e_) +  \
+                             " at " __FILE__ ":" + std::to_string(__LINE__) +       \
+                             " in " #expr);                                         \
+            return e_ == cudaErrorMemoryAllocation ? BEM_E_OOM : BEM_E_CUDA;        \
+        }                                                                           \
+    } while (0)
+
+#define BEM_CHECK_LAUNCH() BEM_CUDA_TRY(cudaGetLastError())
+
+#define BEM_TRY(expr)                      \
+    do {                                   \
+        bem_status s_ = (expr);            \
+        if (s_ != BEM_OK) return s_;       \
+    } while (0)
+
+#define BEM_REQUIRE(cond, msg)                                   \
+    do {                                                         \
+        if (!(cond)) {                                           \
+            ::bem::set_error(std::string("invalid argument: ") + (msg)); \
+            return BEM_E_INVALID_ARG;                            \
+        }                                                        \
+    } while (0)
+
+// ------------------------------------------------------------------ device buffers
+// Stream-ordered device allocation owned by RAII handles.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept { *this = std::move(o); }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        release();
+        p = o.p; bytes = o.bytes; stream = o.stream;
+        o.p = nullptr; o.bytes = 0;
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    bem_status alloc(size_t nbytes, cudaStream_t s);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ------------------------------------------------------------------ quadrature
+// 6-point degree-4 symmetric triangle rule on {s,t >= 0, s+t <= 1}, weights sum 1/2.
+struct TriRule {
+    double s[6], t[6], w[6];
+};
+const TriRule& tri_rule_degree4();
+
+// Sauter-Schwab tables: points (x1, x2, y1, y2) on T^ x T^ with T^ = {0<=x2<=x1<=1},
+// weight including the transformation Jacobian.  kind: 0 coincident, 1 edge, 2 vertex.
+struct SSTable {
+    int n = 0;                 // Gauss points per axis
+    int count[3] = {0, 0, 0};  // points per kind
+    int offset[3] = {0, 0, 0};
+    std::vector<double> host;  // [total][5]
+    DevBuf dev;
+};
+bem_status ss_table_get(int n, cudaStream_t stream, const double** dev_ptr, int count[3], int offset[3]);
+
+// ------------------------------------------------------------------ geometry record
+// Per-triangle record, 50 doubles (400 bytes), written by the geometry kernel.
+struct __align__(16) TriRec {
+    double q[6][3];    // physical quadrature points             (doubles  0..17)
+    double wl[6][3];   // w_p * J * lambda_a(p)                  (doubles 18..35)
+    double n[3];       // outward unit normal                    (doubles 36..38)
+    double J;          // |e1 x e2|                              (double  39)
+    double curl[3][3]; // surface curls of the shape functions   (doubles 40..48)
+    double pad;
+};
+constexpr int TRIREC_DOUBLES = 50;
+static_assert(sizeof(TriRec) == TRIREC_DOUBLES * 8, "TriRec layout");
+
+// Singular pair: kind 1 edge / 2 vertex, triangles t < s, Sauter-Schwab vertex order.
+struct SingPair {
+    int32_t t, s;
+    uint8_t pt[3], ps[3];
+    uint8_t kind, pad;
+};
+
+}  // namespace bem
+
+// ------------------------------------------------------------------ handles
+struct bem_context {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+};
+
+struct bem_grid {
+    bem_context* ctx = nullptr;
+    int64_t nv = 0, nt = 0;
+    std::vector<double> h_xyz;     // host copy (intake)
+    std::vector<int32_t> h_tri;
+    bem::DevBuf xyz, tri, rec;     // device: vertices, triangles, TriRec per triangle
+    // singular pairs (edge and vertex-adjacent, unordered t < s)
+    bem::DevBuf sing;
+    int64_t n_edge = 0, n_vertex = 0;
+    // mass matrix CSR structure (rows = vertices) and per-triangle slot map
+    bem::DevBuf m_rowptr, m_col, m_slot;   // m_slot [nt][3][3] CSR position
+    int64_t m_nnz = 0;
+    // angular disc per triangle seen from the origin (mortar prefilter)
+    double surface_area = 0.0;
+};
+
+struct bem_matrix {
+    int64_t rows = 0, cols = 0;
+    bem::DevBuf data;              // complex128 row-major
+};
+
+struct bem_sparse {
+    int64_t rows = 0, cols = 0, nnz = 0;
+    bem::DevBuf row, col, val;     // COO, int32 / int32 / double
+};
+
+namespace bem {
+
+// grid.cu
+bem_status grid_build_geometry(bem_grid* g);
+bem_status mass_values(const bem_grid* g, double* d_val, cudaStream_t s);      // [m_nnz]
+bem_status mass_inverse_diag(const bem_grid* g, const double* d_val, double* d_dinv, cudaStream_t s);
+
+// assemble.cu: V, K, T, D (row-major N x N complex128; any pointer may be null).
+bem_status assemble_operators_fp64(const bem_grid* g, double k_re, double k_im, int n_singular,
+                                   double2* V, double2* K, double2* T, double2* D, cudaStream_t s);
+
+// mortar.cu: COO of P_ab (rows: vertices of a, cols: vertices of b).
+bem_status mortar_coo(const bem_grid* a, const bem_grid* b, const double center[3],
+                      DevBuf& row, DevBuf& col, DevBuf& val, int64_t* nnz, cudaStream_t s);
+
+}  // namespace bem

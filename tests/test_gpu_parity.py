@@ -1,0 +1,237 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerance: relative L2 (Frobenius for matrices) <= 1e-10 in FP64 mode.  Both sides
+evaluate the same quadrature rules on the same points, so differences are rounding
+only; the bound leaves room for the different summation orders (atomics, FMA
+contraction) of the GPU."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import bem_inputs as bi
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def bem():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2206_00708_gb300 as b
+    return b
+
+
+@pytest.fixture(scope="module")
+def ctx(bem):
+    c = bem.bem_context_create(0)
+    yield c
+    bem.bem_context_destroy(c)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def gpu_ops(bem, ctx, v, t, k, n_singular=4):
+    g = bem.bem_grid_create(ctx, v, t)
+    out = {}
+    for name, op in (("V", bem.BEM_OP_V), ("K", bem.BEM_OP_K), ("T", bem.BEM_OP_T), ("D", bem.BEM_OP_D)):
+        m = bem.bem_assemble(ctx, op, k, g, n_singular=n_singular)
+        out[name] = bem.bem_matrix_copy_out(ctx, m)
+        bem.bem_matrix_destroy(m)
+    bem.bem_grid_destroy(g)
+    return out
+
+
+def _grids():
+    v1, t1 = bi.icosphere(1)  # 80 triangles: a ragged tile
+    ve, te, vi, ti = bi.transmission_pair(2, 2, seed=3, axes=[1.3, 0.8, 1.1])
+    vs, ts = bi.unit_square_grid(7)  # open surface, 98 triangles
+    return {"sphere-L1": (v1, t1, 1.0), "ellipsoid-L2-jitter": (vi, ti, 3.0 + 0.5j), "square": (vs, ts, 2.0)}
+
+
+@pytest.mark.parametrize("case", ["sphere-L1", "ellipsoid-L2-jitter", "square"])
+def test_operators_match_oracle(bem, ctx, case):
+    from oracle.helmholtz import assemble
+    v, t, k = _grids()[case]
+    got = gpu_ops(bem, ctx, v, t, k)
+    ref = assemble(v, t, k)
+    for op in "VKTD":
+        e = rel(got[op], ref[op])
+        assert e < TOL, (case, op, e)
+
+
+def test_operators_singular_order_6(bem, ctx):
+    from oracle.helmholtz import assemble
+    v, t = bi.icosphere(1)
+    got = gpu_ops(bem, ctx, v, t, 2.5, n_singular=6)
+    ref = assemble(v, t, 2.5, n_singular=6)
+    for op in "VKTD":
+        assert rel(got[op], ref[op]) < TOL, op
+
+
+def test_operators_many_tiles_sampled_rows(bem, ctx):
+    """1280 triangles (40 tiles): rows sampled across the grid."""
+    from oracle.helmholtz import assemble
+    v, t = bi.icosphere(3)
+    v = bi.ellipsoid(bi.rotate_and_jitter(v, t, seed=5), [1.2, 1.0, 0.9])
+    rows = np.random.default_rng(0).choice(len(v), 24, replace=False)
+    got = gpu_ops(bem, ctx, v, t, 6.0)
+    ref = assemble(v, t, 6.0, rows=rows)
+    for op in "VKTD":
+        assert rel(got[op][rows], ref[op]) < TOL, op
+
+
+@pytest.mark.parametrize("level,k", [(5, 10.0), (5, 15.0)])
+def test_operators_full_size_sampled_rows(bem, ctx, level, k):
+    """Full-size grids of the at-scale workload (20480 triangles), sampled rows."""
+    from oracle.helmholtz import assemble
+    v, t = bi.icosphere(level)
+    if k == 15.0:
+        v = bi.rotate_and_jitter(v, t, seed=2)
+    rows = np.random.default_rng(1).choice(len(v), 6, replace=False)
+    ref = assemble(v, t, k, rows=rows)
+    g = bem.bem_grid_create(ctx, v, t)
+    for name, op in (("V", bem.BEM_OP_V), ("K", bem.BEM_OP_K), ("D", bem.BEM_OP_D)):
+        m = bem.bem_assemble(ctx, op, k, g)
+        full = bem.bem_matrix_copy_out(ctx, m)
+        bem.bem_matrix_destroy(m)
+        assert rel(full[rows], ref[name]) < TOL, name
+        if name == "V":  # symmetry over the whole matrix, sampled
+            cols = np.random.default_rng(2).choice(len(v), 64, replace=False)
+            blk = full[np.ix_(cols, cols)]
+            assert np.abs(blk - blk.T).max() < 1e-14 * np.abs(blk).max()
+        del full
+    bem.bem_grid_destroy(g)
+
+
+def _coo_dense(bem, ctx, s, shape):
+    r, c, v = bem.bem_sparse_copy_out(ctx, s)
+    bem.bem_sparse_destroy(s)
+    return sp.coo_matrix((v, (r, c)), shape=shape).toarray()
+
+
+def test_mass_matches_oracle(bem, ctx):
+    from oracle.mass import mass_matrix
+    v, t = bi.icosphere(2)
+    v = bi.ellipsoid(v, [1.2, 0.7, 1.0])
+    g = bem.bem_grid_create(ctx, v, t)
+    M = _coo_dense(bem, ctx, bem.bem_mass(ctx, g), (len(v), len(v)))
+    bem.bem_grid_destroy(g)
+    assert np.abs(M - mass_matrix(v, t)).max() < 1e-15
+
+
+@pytest.mark.parametrize("le,li,axes", [(2, 2, None), (3, 2, None), (2, 3, [1.3, 0.8, 1.1])])
+def test_mortar_matches_oracle(bem, ctx, le, li, axes):
+    from oracle.mortar import mortar_matrix
+    ve, te, vi, ti = bi.transmission_pair(le, li, seed=4, axes=axes)
+    ge = bem.bem_grid_create(ctx, ve, te)
+    gi = bem.bem_grid_create(ctx, vi, ti)
+    P = _coo_dense(bem, ctx, bem.bem_projection(ctx, gi, ge), (len(vi), len(ve)))
+    bem.bem_grid_destroy(ge)
+    bem.bem_grid_destroy(gi)
+    ref = mortar_matrix(vi, ti, ve, te)
+    assert rel(P, ref) < 1e-12
+
+
+def test_mortar_identical_and_planar(bem, ctx):
+    from oracle.mass import mass_matrix
+    from oracle.mortar import mortar_matrix
+    v, t = bi.icosphere(2)
+    g = bem.bem_grid_create(ctx, v, t)
+    P = _coo_dense(bem, ctx, bem.bem_projection(ctx, g, g), (len(v), len(v)))
+    bem.bem_grid_destroy(g)
+    assert np.abs(P - mass_matrix(v, t)).max() < 1e-15
+    vi, ti = bi.unit_square_grid(6)
+    ve = bi.perturb_square_grid(vi, 0.02, seed=9)
+    a = bem.bem_grid_create(ctx, vi, ti)
+    b = bem.bem_grid_create(ctx, ve, ti)
+    c0 = (0.5, 0.5, 1.0)
+    P = _coo_dense(bem, ctx, bem.bem_projection(ctx, a, b, c0), (len(vi), len(ve)))
+    bem.bem_grid_destroy(a)
+    bem.bem_grid_destroy(b)
+    assert rel(P, mortar_matrix(vi, ti, ve, ti, center=c0)) < 1e-12
+
+
+def _solve_pair(bem, ctx, ve, te, vi, ti, k_int, k_ext, rho, dirs, amps=None, **opts):
+    ge = bem.bem_grid_create(ctx, ve, te)
+    gi = bem.bem_grid_create(ctx, vi, ti)
+    try:
+        return bem.bem_solve_transmission(ctx, ge, gi, k_int, k_ext, rho, dirs, amps=amps, opts=opts or None)
+    finally:
+        bem.bem_grid_destroy(ge)
+        bem.bem_grid_destroy(gi)
+
+
+def test_transmission_solve_matches_oracle_tiny_config(bem, ctx):
+    """Unit sphere, icosphere level 2 on both grids (interior rotated + jittered),
+    k_ext = 1, k_int = 2, rho ratio 1, plane wave along +z."""
+    from oracle.mtf import solve_transmission
+    ve, te, vi, ti = bi.transmission_pair(2, 2, seed=1)
+    d = np.array([[0.0, 0.0, 1.0]])
+    out, rep = _solve_pair(bem, ctx, ve, te, vi, ti, 2.0, 1.0, 1.0, d, gmres_tol=1e-12)
+    ref = solve_transmission(ve, te, vi, ti, 1.0, 2.0, 1.0, d[0], tol=1e-12)
+    for key in ("v_ext", "w_ext", "v_int", "w_int"):
+        assert rel(out[key][0], ref[key]) < TOL, key
+    assert rep["converged"] == 1
+    # iteration counts at the configured tolerance 1e-8
+    out8, rep8 = _solve_pair(bem, ctx, ve, te, vi, ti, 2.0, 1.0, 1.0, d)
+    ref8 = solve_transmission(ve, te, vi, ti, 1.0, 2.0, 1.0, d[0], tol=1e-8, blocks=ref["blocks"])
+    assert abs(rep8["iterations"] - ref8["iters"]) <= 1
+
+
+def test_transmission_solve_density_contrast_complex_k_and_multi_rhs(bem, ctx):
+    """Ellipsoid, different grid levels, density ratio 2, complex interior
+    wavenumber, three plane waves with complex amplitudes in one call: each
+    solution is amp_r times the oracle solution for a unit wave."""
+    from oracle.mtf import solve_transmission, mtf_blocks
+    ve, te, vi, ti = bi.transmission_pair(2, 1, seed=6, axes=[1.2, 0.9, 1.0])
+    dirs = bi.plane_wave_directions(3, seed=40)
+    amps = [1.0, 0.5 - 0.25j, 2.0j]
+    k_ext, k_int, rho = 2.0, 3.0 + 0.2j, 2.0
+    out, rep = _solve_pair(bem, ctx, ve, te, vi, ti, k_int, k_ext, rho, dirs, amps=amps, gmres_tol=1e-12)
+    B = mtf_blocks(ve, te, vi, ti, k_ext, k_int)
+    for r in range(3):
+        ref = solve_transmission(ve, te, vi, ti, k_ext, k_int, rho, dirs[r], tol=1e-12, blocks=B)
+        for key in ("v_ext", "w_ext", "v_int", "w_int"):
+            assert rel(out[key][r], amps[r] * ref[key]) < TOL, (r, key)
+
+
+def test_printed_variant_negates_interior(bem, ctx):
+    ve, te, vi, ti = bi.transmission_pair(1, 1, seed=2)
+    d = np.array([[0.0, 1.0, 0.0]])
+    a, ra = _solve_pair(bem, ctx, ve, te, vi, ti, 2.0, 1.0, 2.0, d, gmres_tol=1e-12)
+    b, rb = _solve_pair(bem, ctx, ve, te, vi, ti, 2.0, 1.0, 2.0, d, gmres_tol=1e-12, mtf_variant=1)
+    assert ra["iterations"] == rb["iterations"]
+    for key, s in (("v_ext", 1), ("w_ext", 1), ("v_int", -1), ("w_int", -1)):
+        assert rel(s * b[key], a[key]) < TOL
+
+
+def test_invalid_inputs_are_rejected(bem, ctx):
+    v, t = bi.icosphere(1)
+    bad = t.copy()
+    bad[3, 1] = len(v) + 5
+    with pytest.raises(bem.BemError) as e:
+        bem.bem_grid_create(ctx, v, bad)
+    assert e.value.status == bem.BEM_E_INVALID_ARG
+    vn = v.copy()
+    vn[2, 0] = np.nan
+    with pytest.raises(bem.BemError) as e:
+        bem.bem_grid_create(ctx, vn, t)
+    assert e.value.status == bem.BEM_E_NONFINITE
+    g = bem.bem_grid_create(ctx, v, t)
+    with pytest.raises(bem.BemError) as e:
+        bem.bem_solve_transmission(ctx, g, g, 1.0, 1.0, 1.0, np.array([[0.0, 0.0, 2.0]]))
+    assert e.value.status == bem.BEM_E_INVALID_ARG
+    with pytest.raises(bem.BemError) as e:
+        bem.bem_solve_transmission(ctx, g, g, 1.0, 1.0, -1.0, np.array([[0.0, 0.0, 1.0]]))
+    assert e.value.status == bem.BEM_E_INVALID_ARG
+    with pytest.raises(bem.BemError) as e:
+        bem.bem_solve_transmission(ctx, g, g, 1.0, 1.0, 1.0, np.array([[0.0, 0.0, 1.0]]),
+                                   opts={"gmres_maxiter": 2, "gmres_tol": 1e-14})
+    assert e.value.status == bem.BEM_E_NOT_CONVERGED
+    assert e.value.report["iterations"] == 2
+    bem.bem_grid_destroy(g)
