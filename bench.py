@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 transmission-BEM hot path.
+
+One step = one complete transmission solve of the at-scale sphere workload:
+grid intake of both grids, Galerkin assembly of V, K, T, D on both grids (regular
+and Sauter-Schwab quadrature), mass and mortar matrices, plane-wave data, and
+unrestarted GMRES on the mass-preconditioned multiple-traces system.
+
+Workload (plain FP64, at scale): unit sphere; exterior grid = icosphere level 5
+(10242 vertices, 20480 triangles); interior grid = icosphere level 5 rotated by a
+Haar-random rotation (seed 2) with 1% tangential jitter; k_ext = 10, k_int = 15,
+rho_int / rho_ext = 2; one unit plane wave along +z; GMRES tolerance 1e-8;
+40968 unknowns, 8 dense complex128 operator blocks (13.4 GB).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.  With torchrun (N > 1) every rank
+solves its own copy (the method has no data exchange between solves: replicas).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Transmission solves/s + p50/p99 latency vs plain FP64 GPU at <=1e-6 rel. err"
+UNIT = "solves/s"
+WORKLOAD = dict(level_ext=5, level_int=5, seed=2, k_ext=10.0, k_int=15.0, rho=2.0, tol=1e-8)
+WORKLOAD_NAME = ("plain FP64 at scale: unit sphere, icosphere L5 exterior (10242 vertices) + L5 interior "
+                 "rotated/jittered (seed 2), k_ext=10, k_int=15, rho_int/rho_ext=2, 1 plane wave +z, "
+                 "GMRES tol 1e-8, 40968 unknowns, 8 dense c128 blocks")
+L2_FLUSH_BYTES = 256 << 20
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x 2 flops x max SM clock
+# algorithmic FP64 flops per point pair of the regular-pair assembly kernel
+FLOP_PER_POINT_PAIR = 93
+
+
+def workload_inputs(w=WORKLOAD):
+    import bem_inputs as bi
+    return bi.transmission_pair(w["level_ext"], w["level_int"], w["seed"])
+
+
+def regular_point_pairs(t):
+    """Unordered triangle pairs without a common vertex, times 36 point pairs."""
+    t = np.asarray(t)
+    nt = len(t)
+    nv = int(t.max()) + 1
+    # singular unordered pairs (t < s sharing >= 1 vertex) via vertex -> triangle lists
+    vt = [[] for _ in range(nv)]
+    for i, tri in enumerate(t):
+        for v in tri:
+            vt[v].append(i)
+    sing = set()
+    for i, tri in enumerate(t):
+        for v in tri:
+            for j in vt[v]:
+                if j > i:
+                    sing.add((i, j))
+    return (nt * (nt - 1) // 2 - len(sing)) * 36
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index=0):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- CPU oracle sample
+def oracle_sample(seconds_hint=20.0, iters=None):
+    """Time the FP64 CPU oracle on a bounded sample of the workload and scale it
+    to one solve.  Returns (solves_per_s, sample_description, cores)."""
+    import bem_inputs as bi
+    from oracle.helmholtz import assemble
+    w = WORKLOAD
+    ve, te, vi, ti = workload_inputs()
+    rng = np.random.default_rng(0)
+    t_asm = 0.0
+    desc = []
+    for (v, t, k) in ((ve, te, w["k_ext"]), (vi, ti, w["k_int"])):
+        rows = rng.choice(len(v), 2, replace=False)
+        ntest = int(np.count_nonzero(np.isin(np.asarray(t), rows).any(axis=1)))
+        t0 = time.perf_counter()
+        assemble(v, t, k, rows=rows)
+        dt = time.perf_counter() - t0
+        t_asm += dt / ntest * len(t)
+        desc.append(f"{ntest} test triangles x {len(t)} of V,K,T,D (scaled x{len(t) / ntest:.0f})")
+    n = 2 * len(ve) + 2 * len(vi)
+    blk = 512
+    A = (rng.standard_normal((blk, n)) + 1j * rng.standard_normal((blk, n)))
+    z = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    t0 = time.perf_counter()
+    reps = 3
+    for _ in range(reps):
+        A @ z
+    t_mv = (time.perf_counter() - t0) / reps * (n / blk)
+    it = iters if iters else 300
+    desc.append(f"dense strong-form matvec on a {blk}x{n} block (scaled x{n / blk:.0f}) x {it} GMRES iterations")
+    total = t_asm + it * t_mv
+    return 1.0 / total, "; ".join(desc) + "; mortar, mass and preconditioner setup not counted", 1
+
+
+def run_oracle_child(iters):
+    """Run the oracle sample in a child with one BLAS/OpenMP thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0,%r); import bench; v,s,c=bench.oracle_sample(iters=%d); "
+            "print(json.dumps({'value':v,'sample':s,'cores':c}))" % (ROOT, iters))
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if p.returncode != 0:
+        return None
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    vals = []
+    sample = None
+    t0 = time.perf_counter()
+    for _ in range(args.warmup + args.steps):
+        r = run_oracle_child(300)
+        if r is None:
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle sample failed to run"}))
+            return
+        vals.append(r["value"])
+        sample = r
+    vals = vals[args.warmup:]
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": sample["cores"], "kind": "oracle",
+                         "sample": sample["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - t0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    import torch.distributed as dist
+    import paper_2206_00708_gb300 as bem
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = WORKLOAD
+    ve, te, vi, ti = workload_inputs()
+    dev = torch.device("cuda", local)
+    xe = torch.from_numpy(np.ascontiguousarray(ve)).to(dev)
+    tre = torch.from_numpy(np.ascontiguousarray(te, dtype=np.int32)).to(dev)
+    xi = torch.from_numpy(np.ascontiguousarray(vi)).to(dev)
+    tri_ = torch.from_numpy(np.ascontiguousarray(ti, dtype=np.int32)).to(dev)
+    Ne, Ni = len(ve), len(vi)
+    out = {k: torch.zeros((1, n), dtype=torch.complex128, device=dev)
+           for k, n in (("v_ext", Ne), ("w_ext", Ne), ("v_int", Ni), ("w_int", Ni))}
+    dirs = np.array([[0.0, 0.0, 1.0]])
+    stream = torch.cuda.current_stream(dev)
+    ctx = bem.bem_context_create(local, stream=stream)
+    opts = {"gmres_tol": w["tol"]}
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        ge = bem.bem_grid_create(ctx, xe, tre)
+        gi = bem.bem_grid_create(ctx, xi, tri_)
+        _, rep = bem.bem_solve_transmission(ctx, ge, gi, w["k_int"], w["k_ext"], w["rho"], dirs, opts=opts,
+                                            out=out, on_device=True)
+        bem.bem_grid_destroy(ge)
+        bem.bem_grid_destroy(gi)
+        return rep
+
+    for _ in range(args.warmup):
+        rep = step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    times = []
+    reports = []
+    bem.bem_profile_reset()
+    launches0 = bem.bem_launch_count()
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush outside the timed events
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            bem.bem_profile_enable(True)
+            e0.record(stream)
+            reports.append(step())
+            e1.record(stream)
+            e1.synchronize()
+            bem.bem_profile_enable(False)
+            times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    launches = bem.bem_launch_count() - launches0
+    barrier()
+    total_ms = sum(times)
+    t_max = total_ms
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * args.steps / (t_max / 1e3)
+    prof = bem.bem_profile_table()
+
+    # dominant kernel: roofline
+    top = prof[0] if prof else ("", 0.0, 0)
+    roof = None
+    asm = [p for p in prof if p[0].startswith("k_regular")]
+    if asm:
+        name, ms, n = asm[0]
+        units = (regular_point_pairs(te) + regular_point_pairs(ti)) / 2  # per launch (two grids per solve)
+        achieved = FLOP_PER_POINT_PAIR * units / (ms / n / 1e3) / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_kind": "derived FP64 FMA peak: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
+                "flop_per_point_pair": FLOP_PER_POINT_PAIR, "point_pairs_per_launch": units,
+                "avg_launch_ms": ms / n}
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the public API with pinned host buffers
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hxe, hte, hxi, hti = pin(ve), pin(np.asarray(te, dtype=np.int32)), pin(vi), pin(np.asarray(ti, dtype=np.int32))
+        hout = {k: torch.zeros((1, n), dtype=torch.complex128).pin_memory()
+                for k, n in (("v_ext", Ne), ("w_ext", Ne), ("v_int", Ni), ("w_int", Ni))}
+        e2e_times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ge = bem.bem_grid_create(ctx, hxe, hte)
+            gi = bem.bem_grid_create(ctx, hxi, hti)
+            bem.bem_solve_transmission(ctx, ge, gi, w["k_int"], w["k_ext"], w["rho"], dirs, opts=opts, out=hout)
+            bem.bem_grid_destroy(ge)
+            bem.bem_grid_destroy(gi)
+            e2e_times.append(time.perf_counter() - t0)
+        h2d = sum(int(a.numel() * a.element_size()) for a in (hxe, hte, hxi, hti))
+        d2h = sum(int(a.numel() * a.element_size()) for a in hout.values())
+        e2e = {"value": world * args.steps / sum(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = run_oracle_child(int(reports[-1]["iterations"]))
+        if r is not None:
+            cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
+
+    if rank == 0:
+        srt = sorted(times)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "256 MB write between steps; operators (13.4 GB) exceed L2",
+                       "precision": "fp64"},
+            "latency_ms": {"p50": float(np.percentile(srt, 50)), "p99": float(np.percentile(srt, 99))},
+            "clocks": clocks.summary(),
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "solve": {"iterations": reports[-1]["iterations"], "residual": reports[-1]["residual"],
+                      "t_assembly_ms": reports[-1]["t_assembly_ms"], "t_mortar_ms": reports[-1]["t_mortar_ms"],
+                      "t_solve_ms": reports[-1]["t_solve_ms"]},
+            "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in prof[:8]],
+        }
+        print(json.dumps(line), flush=True)
+    bem.bem_context_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

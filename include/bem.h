@@ -78,6 +78,22 @@ BEM_API const char* bem_last_error(void);
 /* Library version string. */
 BEM_API const char* bem_version(void);
 
+/* Number of CUDA kernels the library has launched since it was loaded (all
+ * contexts and threads; a monotone counter for profiling and accounting). */
+BEM_API uint64_t bem_launch_count(void);
+
+/* Per-kernel device timing.  While enabled, each launch of the library is
+ * bracketed by CUDA events on its own stream; totals accumulate per kernel
+ * name.  bem_profile_count() returns the number of kernel names seen and
+ * bem_profile_get(i, ...) the i-th name (NUL-terminated, truncated to name_len),
+ * its summed device time in ms and its number of launches.  Collecting waits
+ * for the recorded events.  Not meant to be toggled while a solve is running. */
+BEM_API void       bem_profile_enable(int on);
+BEM_API void       bem_profile_reset(void);
+BEM_API int        bem_profile_count(void);
+BEM_API bem_status bem_profile_get(int index, char* name, int name_len, double* total_ms,
+                                   int64_t* launches);
+
 /* ---------------------------------------------------------------- context
  * A context binds a CUDA device and a stream.  `stream` is a cudaStream_t
  * passed as void*; NULL makes the context create and own a non-blocking stream.

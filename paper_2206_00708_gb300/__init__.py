@@ -79,6 +79,11 @@ _PI64 = C.POINTER(C.c_int64)
 _SIGNATURES = {
     "bem_last_error": (C.c_char_p, []),
     "bem_version": (C.c_char_p, []),
+    "bem_launch_count": (C.c_uint64, []),
+    "bem_profile_enable": (None, [C.c_int]),
+    "bem_profile_reset": (None, []),
+    "bem_profile_count": (C.c_int, []),
+    "bem_profile_get": (C.c_int32, [C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double), _PI64]),
     "bem_context_create": (C.c_int32, [C.c_int, _VP, _PVP]),
     "bem_context_destroy": (C.c_int32, [_VP]),
     "bem_context_synchronize": (C.c_int32, [_VP]),
@@ -153,6 +158,36 @@ def _ptr(a):
 # ------------------------------------------------------------------ context / grids
 def bem_version():
     return _lib.bem_version().decode()
+
+
+def bem_launch_count():
+    return int(_lib.bem_launch_count())
+
+
+def bem_profile_enable(on=True):
+    _lib.bem_profile_enable(int(bool(on)))
+
+
+def bem_profile_reset():
+    _lib.bem_profile_reset()
+
+
+def bem_profile_count():
+    return int(_lib.bem_profile_count())
+
+
+def bem_profile_get(index):
+    """(kernel name, total device ms, launches) of the index-th profiled kernel."""
+    buf = C.create_string_buffer(256)
+    ms, n = C.c_double(), C.c_int64()
+    _check(_lib.bem_profile_get(int(index), buf, 256, C.byref(ms), C.byref(n)))
+    return buf.value.decode(), ms.value, n.value
+
+
+def bem_profile_table():
+    """All profiled kernels as a list of (name, total ms, launches), longest first."""
+    rows = [bem_profile_get(i) for i in range(bem_profile_count())]
+    return sorted(rows, key=lambda r: -r[1])
 
 
 def bem_context_create(device=0, stream=None):

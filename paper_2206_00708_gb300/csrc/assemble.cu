@@ -327,9 +327,9 @@ bem_status assemble_operators_fp64(const bem_grid* g, double k_re, double k_im, 
     }
     dim3 grid((unsigned)ntile, (unsigned)ntile);
     if (ck)
-        k_regular<true><<<grid, NTHREADS, 0, s>>>(g->rec.as<TriRec>(), g->tri.as<int32_t>(), nt, P, V, K, T, D);
+        BEM_LAUNCH(k_regular<true>, grid, NTHREADS, 0, s, g->rec.as<TriRec>(), g->tri.as<int32_t>(), nt, P, V, K, T, D);
     else
-        k_regular<false><<<grid, NTHREADS, 0, s>>>(g->rec.as<TriRec>(), g->tri.as<int32_t>(), nt, P, V, K, T, D);
+        BEM_LAUNCH(k_regular<false>, grid, NTHREADS, 0, s, g->rec.as<TriRec>(), g->tri.as<int32_t>(), nt, P, V, K, T, D);
     BEM_CHECK_LAUNCH();
     const double* ss;
     int cnt[3], off[3];
@@ -339,10 +339,10 @@ bem_status assemble_operators_fp64(const bem_grid* g, double k_re, double k_im, 
     const unsigned blocks = (unsigned)((warps * 32 + 127) / 128);
     int3 c3 = make_int3(cnt[0], cnt[1], cnt[2]), o3 = make_int3(off[0], off[1], off[2]);
     if (ck)
-        k_singular<true><<<blocks, 128, 0, s>>>(g->xyz.as<double>(), g->tri.as<int32_t>(), g->rec.as<TriRec>(),
+        BEM_LAUNCH(k_singular<true>, blocks, 128, 0, s, g->xyz.as<double>(), g->tri.as<int32_t>(), g->rec.as<TriRec>(),
                                                 g->sing.as<SingPair>(), nt, npairs, ss, c3, o3, P, V, K, T, D);
     else
-        k_singular<false><<<blocks, 128, 0, s>>>(g->xyz.as<double>(), g->tri.as<int32_t>(), g->rec.as<TriRec>(),
+        BEM_LAUNCH(k_singular<false>, blocks, 128, 0, s, g->xyz.as<double>(), g->tri.as<int32_t>(), g->rec.as<TriRec>(),
                                                  g->sing.as<SingPair>(), nt, npairs, ss, c3, o3, P, V, K, T, D);
     BEM_CHECK_LAUNCH();
     return BEM_OK;

@@ -26,6 +26,23 @@ void set_error(const std::string& msg);
 
 #define BEM_CHECK_LAUNCH() BEM_CUDA_TRY(cudaGetLastError())
 
+// Number of kernels this library has launched since it was loaded.
+void count_launch();
+
+// Optional per-kernel event timing (profile.cu); -1 when profiling is off.
+int prof_begin(const char* name, cudaStream_t s);
+void prof_end(int slot, cudaStream_t s);
+
+// Launch a kernel, time it when profiling is on, count it and check the launch.
+#define BEM_LAUNCH(kern, grid, block, smem, stream, ...)                \
+    do {                                                                \
+        const int prof_slot_ = ::bem::prof_begin(#kern, (stream));      \
+        kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);       \
+        ::bem::prof_end(prof_slot_, (stream));                          \
+        ::bem::count_launch();                                          \
+        BEM_CHECK_LAUNCH();                                             \
+    } while (0)
+
 #define BEM_TRY(expr)                      \
     do {                                   \
         bem_status s_ = (expr);            \

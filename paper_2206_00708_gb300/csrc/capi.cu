@@ -3,6 +3,7 @@
 // on the context's stream.
 #include "bem_internal.cuh"
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -12,9 +13,12 @@ namespace bem {
 
 namespace {
 thread_local std::string g_last_error = "no error";
+std::atomic<uint64_t> g_launches{0};
 }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 bem_status DevBuf::alloc(size_t nbytes, cudaStream_t s) {
     release();
@@ -61,6 +65,8 @@ extern "C" {
 const char* bem_last_error(void) { return g_last_error.c_str(); }
 
 const char* bem_version(void) { return "bem-gb300 0.1 (sm_103a)"; }
+
+uint64_t bem_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 bem_status bem_context_create(int device, void* stream, bem_context** out) {
     BEM_REQUIRE(out != nullptr, "out is null");

@@ -162,7 +162,7 @@ bem_status grid_build_geometry(bem_grid* g) {
     BEM_CUDA_TRY(cudaMemcpyAsync(g->m_slot.p, slot.data(), slot.size() * 4, cudaMemcpyHostToDevice, s));
     // ---- geometry records (device) -------------------------------------------------
     BEM_TRY(g->rec.alloc(nt * sizeof(TriRec), s));
-    k_geometry<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(g->xyz.as<double>(), g->tri.as<int32_t>(), nt,
+    BEM_LAUNCH(k_geometry, (unsigned)((nt + 127) / 128), 128, 0, s, g->xyz.as<double>(), g->tri.as<int32_t>(), nt,
                                                           tri_rule_degree4(), g->rec.as<TriRec>());
     BEM_CHECK_LAUNCH();
     // the host vectors above must outlive the asynchronous copies
@@ -172,14 +172,14 @@ bem_status grid_build_geometry(bem_grid* g) {
 
 bem_status mass_values(const bem_grid* g, double* d_val, cudaStream_t s) {
     BEM_CUDA_TRY(cudaMemsetAsync(d_val, 0, g->m_nnz * sizeof(double), s));
-    k_mass_values<<<(unsigned)((g->nt + 127) / 128), 128, 0, s>>>(g->rec.as<TriRec>(), g->m_slot.as<int32_t>(),
+    BEM_LAUNCH(k_mass_values, (unsigned)((g->nt + 127) / 128), 128, 0, s, g->rec.as<TriRec>(), g->m_slot.as<int32_t>(),
                                                                  g->nt, d_val);
     BEM_CHECK_LAUNCH();
     return BEM_OK;
 }
 
 bem_status mass_inverse_diag(const bem_grid* g, const double* d_val, double* d_dinv, cudaStream_t s) {
-    k_diag_inverse<<<(unsigned)((g->nv + 127) / 128), 128, 0, s>>>(g->m_rowptr.as<int32_t>(), g->m_col.as<int32_t>(),
+    BEM_LAUNCH(k_diag_inverse, (unsigned)((g->nv + 127) / 128), 128, 0, s, g->m_rowptr.as<int32_t>(), g->m_col.as<int32_t>(),
                                                                   d_val, g->nv, d_dinv);
     BEM_CHECK_LAUNCH();
     return BEM_OK;

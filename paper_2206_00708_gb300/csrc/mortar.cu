@@ -200,17 +200,17 @@ bem_status mortar_coo(const bem_grid* a, const bem_grid* b, const double center[
     BEM_TRY(da.alloc(a->nt * sizeof(Disc), s));
     BEM_TRY(db.alloc(b->nt * sizeof(Disc), s));
     BEM_TRY(counter.alloc(sizeof(unsigned long long), s));
-    k_discs<<<(unsigned)((a->nt + 127) / 128), 128, 0, s>>>(a->xyz.as<double>(), a->tri.as<int32_t>(), a->nt, c0,
+    BEM_LAUNCH(k_discs, (unsigned)((a->nt + 127) / 128), 128, 0, s, a->xyz.as<double>(), a->tri.as<int32_t>(), a->nt, c0,
                                                           da.as<Disc>());
     BEM_CHECK_LAUNCH();
-    k_discs<<<(unsigned)((b->nt + 127) / 128), 128, 0, s>>>(b->xyz.as<double>(), b->tri.as<int32_t>(), b->nt, c0,
+    BEM_LAUNCH(k_discs, (unsigned)((b->nt + 127) / 128), 128, 0, s, b->xyz.as<double>(), b->tri.as<int32_t>(), b->nt, c0,
                                                           db.as<Disc>());
     BEM_CHECK_LAUNCH();
     // pass 1: count
     BEM_CUDA_TRY(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), s));
     unsigned gx = (unsigned)std::min<int64_t>((b->nt + 255) / 256, 64);
     dim3 grid(gx, (unsigned)std::min<int64_t>(a->nt, 65535));
-    k_candidates<<<grid, 256, 0, s>>>(da.as<Disc>(), a->nt, db.as<Disc>(), b->nt,
+    BEM_LAUNCH(k_candidates, grid, 256, 0, s, da.as<Disc>(), a->nt, db.as<Disc>(), b->nt,
                                       counter.as<unsigned long long>(), nullptr, 0);
     BEM_CHECK_LAUNCH();
     unsigned long long ncand = 0;
@@ -223,14 +223,14 @@ bem_status mortar_coo(const bem_grid* a, const bem_grid* b, const double center[
     // pass 2: fill
     BEM_TRY(cand.alloc(ncand * sizeof(int2), s));
     BEM_CUDA_TRY(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), s));
-    k_candidates<<<grid, 256, 0, s>>>(da.as<Disc>(), a->nt, db.as<Disc>(), b->nt,
+    BEM_LAUNCH(k_candidates, grid, 256, 0, s, da.as<Disc>(), a->nt, db.as<Disc>(), b->nt,
                                       counter.as<unsigned long long>(), cand.as<int2>(), (int64_t)ncand);
     BEM_CHECK_LAUNCH();
     const int64_t n9 = 9 * (int64_t)ncand;
     BEM_TRY(row.alloc(n9 * 4, s));
     BEM_TRY(col.alloc(n9 * 4, s));
     BEM_TRY(val.alloc(n9 * 8, s));
-    k_clip<<<(unsigned)((ncand + 127) / 128), 128, 0, s>>>(a->xyz.as<double>(), a->tri.as<int32_t>(),
+    BEM_LAUNCH(k_clip, (unsigned)((ncand + 127) / 128), 128, 0, s, a->xyz.as<double>(), a->tri.as<int32_t>(),
                                                          b->xyz.as<double>(), b->tri.as<int32_t>(), cand.as<int2>(),
                                                          (int64_t)ncand, c0, row.as<int32_t>(), col.as<int32_t>(),
                                                          val.as<double>());

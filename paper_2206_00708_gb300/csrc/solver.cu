@@ -362,10 +362,10 @@ struct MtfOperator {
 };
 
 bem_status mtf_apply(const MtfOperator& op, const double2* x, double2* y, cudaStream_t s, bool weak_only = false) {
-    k_gemv_mtf<<<blocks_for(op.n * 32, 256), 256, 0, s>>>(op.B, op.n, x, op.z);
+    BEM_LAUNCH(k_gemv_mtf, blocks_for(op.n * 32, 256), 256, 0, s, op.B, op.n, x, op.z);
     BEM_CHECK_LAUNCH();
     if (op.pnnz > 0) {
-        k_transfer<<<blocks_for(op.pnnz, 256), 256, 0, s>>>(op.prow, op.pcol, op.pval, op.pnnz, op.Ne, op.Ni,
+        BEM_LAUNCH(k_transfer, blocks_for(op.pnnz, 256), 256, 0, s, op.prow, op.pcol, op.pval, op.pnnz, op.Ne, op.Ni,
                                                            op.coef, x, op.z);
         BEM_CHECK_LAUNCH();
     }
@@ -376,13 +376,13 @@ bem_status mtf_apply(const MtfOperator& op, const double2* x, double2* y, cudaSt
 bem_status mass_solve(const MtfOperator& op, const double2* z, double2* y, cudaStream_t s) {
     const double theta = 0.5 * (CHEB_BETA + CHEB_ALPHA), delta = 0.5 * (CHEB_BETA - CHEB_ALPHA);
     const double sigma = theta / delta;
-    k_cheb_init<<<blocks_for(op.n, 256), 256, 0, s>>>(op.M, z, y, op.r, op.dA, 1.0 / theta);
+    BEM_LAUNCH(k_cheb_init, blocks_for(op.n, 256), 256, 0, s, op.M, z, y, op.r, op.dA, 1.0 / theta);
     BEM_CHECK_LAUNCH();
     double rho = 1.0 / sigma;
     double2 *dk = op.dA, *dn = op.dB;
     for (int k = 0; k < CHEB_STEPS; ++k) {
         const double rho_n = 1.0 / (2.0 * sigma - rho);
-        k_cheb_step<<<blocks_for(op.n, 256), 256, 0, s>>>(op.M, dk, dn, y, op.r, rho_n * rho, 2.0 * rho_n / delta);
+        BEM_LAUNCH(k_cheb_step, blocks_for(op.n, 256), 256, 0, s, op.M, dk, dn, y, op.r, rho_n * rho, 2.0 * rho_n / delta);
         BEM_CHECK_LAUNCH();
         rho = rho_n;
         std::swap(dk, dn);
@@ -509,21 +509,21 @@ bem_status solve_transmission_fp64(bem_context* ctx, const bem_grid* ge, const b
         double2 amp = inc->amps ? make_double2(inc->amps[rr].re, inc->amps[rr].im) : make_double2(1.0, 0.0);
         BEM_CUDA_TRY(cudaMemsetAsync(fvec.p, 0, Ne * 16, s));
         BEM_CUDA_TRY(cudaMemsetAsync(gvec.p, 0, Ne * 16, s));
-        k_plane_wave<<<blocks_for(ge->nt, 128), 128, 0, s>>>(ge->rec.as<TriRec>(), ge->tri.as<int32_t>(), ge->nt,
+        BEM_LAUNCH(k_plane_wave, blocks_for(ge->nt, 128), 128, 0, s, ge->rec.as<TriRec>(), ge->tri.as<int32_t>(), ge->nt,
                                                             k_ext.re, k_ext.im, d, amp, fvec.as<double2>(),
                                                             gvec.as<double2>());
         BEM_CHECK_LAUNCH();
-        k_rhs_pack<<<eb, 256, 0, s>>>(fvec.as<double2>(), gvec.as<double2>(), Ne, n, bvec.as<double2>());
+        BEM_LAUNCH(k_rhs_pack, eb, 256, 0, s, fvec.as<double2>(), gvec.as<double2>(), Ne, n, bvec.as<double2>());
         BEM_CHECK_LAUNCH();
         // S b -> w
         BEM_TRY(mass_solve(op, bvec.as<double2>(), w.as<double2>(), s));
         // beta = ||S b||; V_0 = S b / beta; g = [beta, 0, ...]
         BEM_CUDA_TRY(cudaMemsetAsync(H.p, 0, (size_t)ldh * (maxit + 1) * 16, s));
         BEM_CUDA_TRY(cudaMemsetAsync(g.p, 0, (maxit + 2) * 16, s));
-        k_dots_partial<<<dim3(RED_BLOCKS, 1), 256, 0, s>>>(w.as<double2>(), n, ldv, w.as<double2>(),
+        BEM_LAUNCH(k_dots_partial, dim3(RED_BLOCKS, 1), 256, 0, s, w.as<double2>(), n, ldv, w.as<double2>(),
                                                            partial.as<double2>());
-        k_dots_final<<<1, 32, 0, s>>>(partial.as<double2>(), 1, nrm.as<double2>(), 0);
-        k_normalize<<<eb, 256, 0, s>>>(w.as<double2>(), n, nrm.as<double2>(), Vp, g.as<double2>());
+        BEM_LAUNCH(k_dots_final, 1, 32, 0, s, partial.as<double2>(), 1, nrm.as<double2>(), 0);
+        BEM_LAUNCH(k_normalize, eb, 256, 0, s, w.as<double2>(), n, nrm.as<double2>(), Vp, g.as<double2>());
         BEM_CHECK_LAUNCH();
         BEM_CUDA_TRY(cudaMemcpyAsync(h_res, nrm.p, 8, cudaMemcpyDeviceToHost, s));
         BEM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -537,25 +537,25 @@ bem_status solve_transmission_fp64(bem_context* ctx, const bem_grid* ge, const b
                 double2* Hj = H.as<double2>() + (int64_t)j * ldh;
                 // CGS2
                 for (int pass = 0; pass < 2; ++pass) {
-                    k_dots_partial<<<dim3(RED_BLOCKS, j + 1), 256, 0, s>>>(Vp, n, ldv, w.as<double2>(),
+                    BEM_LAUNCH(k_dots_partial, dim3(RED_BLOCKS, j + 1), 256, 0, s, Vp, n, ldv, w.as<double2>(),
                                                                           partial.as<double2>());
-                    k_dots_final<<<j + 1, 32, 0, s>>>(partial.as<double2>(), j + 1,
+                    BEM_LAUNCH(k_dots_final, j + 1, 32, 0, s, partial.as<double2>(), j + 1,
                                                       pass == 0 ? Hj : hbuf.as<double2>(), 0);
-                    k_combine<<<eb, 256, 0, s>>>(Vp, n, ldv, j + 1, pass == 0 ? Hj : hbuf.as<double2>(),
+                    BEM_LAUNCH(k_combine, eb, 256, 0, s, Vp, n, ldv, j + 1, pass == 0 ? Hj : hbuf.as<double2>(),
                                                  w.as<double2>(), 0);
                     BEM_CHECK_LAUNCH();
                 }
                 // H[:, j] += second-pass coefficients
-                k_add<<<1, 256, 0, s>>>(Hj, hbuf.as<double2>(), j + 1);
+                BEM_LAUNCH(k_add, 1, 256, 0, s, Hj, hbuf.as<double2>(), j + 1);
                 BEM_CHECK_LAUNCH();
                 // norm and next basis vector
-                k_dots_partial<<<dim3(RED_BLOCKS, 1), 256, 0, s>>>(w.as<double2>(), n, ldv, w.as<double2>(),
+                BEM_LAUNCH(k_dots_partial, dim3(RED_BLOCKS, 1), 256, 0, s, w.as<double2>(), n, ldv, w.as<double2>(),
                                                                    partial.as<double2>());
-                k_dots_final<<<1, 32, 0, s>>>(partial.as<double2>(), 1, nrm.as<double2>(), 0);
-                k_normalize<<<eb, 256, 0, s>>>(w.as<double2>(), n, nrm.as<double2>(), Vp + (int64_t)(j + 1) * ldv,
+                BEM_LAUNCH(k_dots_final, 1, 32, 0, s, partial.as<double2>(), 1, nrm.as<double2>(), 0);
+                BEM_LAUNCH(k_normalize, eb, 256, 0, s, w.as<double2>(), n, nrm.as<double2>(), Vp + (int64_t)(j + 1) * ldv,
                                                Hj + j + 1);
                 BEM_CHECK_LAUNCH();
-                k_givens<<<1, 32, 0, s>>>(H.as<double2>(), ldh, j, cs.as<double>(), sn.as<double2>(),
+                BEM_LAUNCH(k_givens, 1, 32, 0, s, H.as<double2>(), ldh, j, cs.as<double>(), sn.as<double2>(),
                                           g.as<double2>(), resd.as<double>());
                 BEM_CHECK_LAUNCH();
                 BEM_CUDA_TRY(cudaMemcpyAsync(h_res, resd.p, 8, cudaMemcpyDeviceToHost, s));
@@ -567,9 +567,9 @@ bem_status solve_transmission_fp64(bem_context* ctx, const bem_grid* ge, const b
         }
         // x = V y
         if (iters > 0) {
-            k_backsolve<<<1, 256, 0, s>>>(H.as<double2>(), ldh, iters, g.as<double2>(), y.as<double2>(),
+            BEM_LAUNCH(k_backsolve, 1, 256, 0, s, H.as<double2>(), ldh, iters, g.as<double2>(), y.as<double2>(),
                                           work.as<double2>());
-            k_combine<<<eb, 256, 0, s>>>(Vp, n, ldv, iters, y.as<double2>(), xsol.as<double2>(), 1);
+            BEM_LAUNCH(k_combine, eb, 256, 0, s, Vp, n, ldv, iters, y.as<double2>(), xsol.as<double2>(), 1);
             BEM_CHECK_LAUNCH();
         } else {
             BEM_CUDA_TRY(cudaMemsetAsync(xsol.p, 0, n * 16, s));

@@ -1,0 +1,54 @@
+"""Small, self-contained cases of the library's kernels for profiling
+(e.g. under Nsight Compute): one assembly, one mortar or one transmission solve
+on synthetic icosphere grids.
+
+    python -m paper_2206_00708_gb300.profile_case assemble --level 4 --k 10
+    python -m paper_2206_00708_gb300.profile_case solve --level 4 --k 10
+    python -m paper_2206_00708_gb300.profile_case mortar --level 4
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["assemble", "solve", "mortar"])
+    ap.add_argument("--level", type=int, default=4)
+    ap.add_argument("--k", type=float, default=10.0)
+    ap.add_argument("--repeat", type=int, default=1)
+    a = ap.parse_args(argv)
+    import bem_inputs as bi
+    import paper_2206_00708_gb300 as bem
+
+    ctx = bem.bem_context_create(0)
+    ve, te, vi, ti = bi.transmission_pair(a.level, a.level, seed=2)
+    ge = bem.bem_grid_create(ctx, ve, te)
+    gi = bem.bem_grid_create(ctx, vi, ti)
+    for _ in range(a.repeat):
+        if a.case == "assemble":
+            m = bem.bem_assemble(ctx, bem.BEM_OP_V, a.k, ge)
+            bem.bem_context_synchronize(ctx)
+            bem.bem_matrix_destroy(m)
+        elif a.case == "mortar":
+            s = bem.bem_projection(ctx, gi, ge)
+            bem.bem_sparse_destroy(s)
+        else:
+            out, rep = bem.bem_solve_transmission(ctx, ge, gi, 1.5 * a.k, a.k, 2.0, np.array([[0.0, 0.0, 1.0]]))
+            print("iterations", rep["iterations"])
+    bem.bem_grid_destroy(ge)
+    bem.bem_grid_destroy(gi)
+    bem.bem_context_destroy(ctx)
+    print("ok")
+
+
+if __name__ == "__main__":
+    main()

@@ -15,8 +15,8 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def bem():
-    from paper_2206_00708_gb300 import _build
-    _build.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_2206_00708_gb300 as b
     return b
 

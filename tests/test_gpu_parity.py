@@ -60,6 +60,9 @@ def test_operators_match_oracle(bem, ctx, case):
     got = gpu_ops(bem, ctx, v, t, k)
     ref = assemble(v, t, k)
     for op in "VKTD":
+        if np.linalg.norm(ref[op]) == 0.0:  # K, T vanish on a planar grid
+            assert np.abs(got[op]).max() < 1e-15 * np.abs(ref["V"]).max(), (case, op)
+            continue
         e = rel(got[op], ref[op])
         assert e < TOL, (case, op, e)
 
