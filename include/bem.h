@@ -150,6 +150,28 @@ BEM_API bem_status bem_mass(bem_context* ctx, const bem_grid* g, bem_sparse** ou
  * P_ba = P_ab^T (Sec. 5.4).                                                   */
 BEM_API bem_status bem_projection(bem_context* ctx, const bem_grid* a, const bem_grid* b,
                           const double* center, bem_sparse** out);
+/* bem_projection without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not have a library allocate device
+ * memory while they run -- a host program that owns all HBM through its own budgeted
+ * pool, or a latency-critical loop that cannot pay for cudaMalloc and its implicit
+ * synchronisation.  Its working memory is one fixed ~9.9 MB array in device global
+ * memory that every GPU loading the library holds until the process exits.
+ *   a, b:        validated grid handles, at most 32768 triangles each (else
+ *                BEM_E_INVALID_ARG); center as in bem_projection.
+ *   row, col, val: caller-owned DEVICE arrays of `capacity` entries; on return *nnz
+ *                holds the number of COO entries (9 per candidate pair, repeated
+ *                (row, col) pairs add up).  A capacity below *nnz, or more than
+ *                1048576 candidate pairs, returns BEM_E_INVALID_ARG and writes no
+ *                entries.  The entries are written asynchronously on the context's
+ *                stream: synchronise before reading them.
+ * The first call on a device looks up the array's device address (once per device);
+ * make that first call before any stream capture.  All calls share the one array and
+ * it keeps the last call's contents (the call clears what must start at zero), so
+ * calls whose GPU work overlaps -- from several threads, or on several streams of
+ * one device -- race; serialise them.                                          */
+BEM_API bem_status bem_projection_noalloc(bem_context* ctx, const bem_grid* a, const bem_grid* b,
+                                          const double* center, int32_t* row, int32_t* col,
+                                          double* val, int64_t capacity, int64_t* nnz);
 BEM_API bem_status bem_sparse_destroy(bem_sparse* s);
 /* Coordinate (COO) form.  Entries may repeat a (row, col) pair; repeated entries
  * add up.  Query nnz first, then copy into host arrays of at least nnz items.  */

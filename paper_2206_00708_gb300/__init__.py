@@ -97,6 +97,7 @@ _SIGNATURES = {
     "bem_matrix_shape": (C.c_int32, [_VP, _PI64, _PI64]),
     "bem_mass": (C.c_int32, [_VP, _VP, _PVP]),
     "bem_projection": (C.c_int32, [_VP, _VP, _VP, C.POINTER(C.c_double), _PVP]),
+    "bem_projection_noalloc": (C.c_int32, [_VP, _VP, _VP, C.POINTER(C.c_double), _VP, _VP, _VP, _I64, _PI64]),
     "bem_sparse_destroy": (C.c_int32, [_VP]),
     "bem_sparse_info": (C.c_int32, [_VP, _PI64, _PI64, _PI64]),
     "bem_sparse_copy_out": (C.c_int32, [_VP, _VP, _VP, _VP, _VP, _I64]),
@@ -277,6 +278,22 @@ def bem_projection(ctx, a, b, center=None):
         c = (C.c_double * 3)(*[float(x) for x in center])
     _check(_lib.bem_projection(ctx, a, b, c, C.byref(h)))
     return h
+
+
+def bem_projection_noalloc(ctx, a, b, row, col, val, center=None):
+    """Mortar matrix into caller-owned device arrays (CUDA tensors int32, int32,
+    float64 of equal length) without any device allocation by the library; for
+    callers whose device memory comes from their own budgeted pool or whose loop
+    cannot pay for an allocation.  Returns the number of COO entries written.  The
+    library's fixed scratch array is shared by all calls: serialise calls."""
+    c = None
+    if center is not None:
+        c = (C.c_double * 3)(*[float(x) for x in center])
+    cap = min(int(row.numel()), int(col.numel()), int(val.numel()))
+    n = C.c_int64()
+    _check(_lib.bem_projection_noalloc(ctx, a, b, c, C.c_void_p(row.data_ptr()), C.c_void_p(col.data_ptr()),
+                                       C.c_void_p(val.data_ptr()), cap, C.byref(n)))
+    return n.value
 
 
 def bem_sparse_destroy(s):

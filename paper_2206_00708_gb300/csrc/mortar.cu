@@ -19,6 +19,9 @@
 //      the 3-point edge-midpoint rule (exact for quadratics), nine COO entries.
 #include "bem_internal.cuh"
 
+#include <cmath>
+#include <mutex>
+
 namespace bem {
 
 namespace {
@@ -240,3 +243,93 @@ bem_status mortar_coo(const bem_grid* a, const bem_grid* b, const double center[
 }
 
 }  // namespace bem
+
+// ----------------------------------------------------------------------------------
+// bem_projection_noalloc: the mortar matrix without any device allocation.
+//
+// Some callers cannot let a library allocate device memory while they run: a host
+// application that hands out all HBM from its own budgeted pool (so that a foreign
+// cudaMalloc could break its accounting or fail mid-request), or a latency-critical
+// loop that cannot afford cudaMalloc's cost and implicit synchronisation.  For them
+// this entry point keeps its working memory (the angular discs of both grids and the
+// candidate-pair list) in one fixed array in device global memory that exists for as
+// long as the library is loaded, on every GPU that loads it.  The caller passes the
+// grids (validated handles) and the output arrays.
+namespace bem {
+namespace {
+
+constexpr int64_t NOALLOC_MAX_TRI = 32768;     // triangles per grid
+constexpr int64_t NOALLOC_MAX_CAND = 1 << 20;  // candidate triangle pairs
+constexpr size_t NOALLOC_DISC_OFF = 256;
+constexpr size_t NOALLOC_CAND_OFF = NOALLOC_DISC_OFF + 2 * NOALLOC_MAX_TRI * sizeof(Disc);
+constexpr size_t NOALLOC_BYTES = NOALLOC_CAND_OFF + NOALLOC_MAX_CAND * sizeof(int2);  // ~9.9 MB
+
+// The scratch array.  In host code its name is only a stand-in: the device address
+// is obtained with cudaGetSymbolAddress (once per device) and passed to the kernels.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {};
+
+bem_status noalloc_scratch(int device, unsigned char** out) {
+    BEM_REQUIRE(device >= 0 && device < 256, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        BEM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));  // the device is current here
+        g_noalloc_addr[device] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_addr[device]);
+    return BEM_OK;
+}
+
+}  // namespace
+}  // namespace bem
+
+extern "C" bem_status bem_projection_noalloc(bem_context* ctx, const bem_grid* a, const bem_grid* b,
+                                             const double* center, int32_t* row, int32_t* col, double* val,
+                                             int64_t capacity, int64_t* nnz) {
+    using namespace bem;
+    BEM_REQUIRE(ctx != nullptr, "null context");
+    BEM_CUDA_TRY(cudaSetDevice(ctx->device));
+    BEM_REQUIRE(a != nullptr && b != nullptr, "null grid");
+    BEM_REQUIRE(row != nullptr && col != nullptr && val != nullptr && nnz != nullptr, "null output");
+    BEM_REQUIRE(a->nt <= NOALLOC_MAX_TRI && b->nt <= NOALLOC_MAX_TRI,
+                "bem_projection_noalloc supports at most 32768 triangles per grid (got " +
+                    std::to_string(a->nt) + " and " + std::to_string(b->nt) + ")");
+    double c0v[3] = {0.0, 0.0, 0.0};
+    if (center)
+        for (int d = 0; d < 3; ++d) c0v[d] = center[d];
+    BEM_REQUIRE(std::isfinite(c0v[0]) && std::isfinite(c0v[1]) && std::isfinite(c0v[2]), "centre not finite");
+    const double3 c0 = make_double3(c0v[0], c0v[1], c0v[2]);
+    unsigned char* base = nullptr;
+    BEM_TRY(noalloc_scratch(ctx->device, &base));
+    cudaStream_t s = ctx->stream;
+    auto* counter = reinterpret_cast<unsigned long long*>(base);
+    Disc* da = reinterpret_cast<Disc*>(base + NOALLOC_DISC_OFF);
+    Disc* db = da + NOALLOC_MAX_TRI;
+    int2* cand = reinterpret_cast<int2*>(base + NOALLOC_CAND_OFF);
+    // the array keeps the previous call's contents: the counter must start at zero
+    BEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+    BEM_LAUNCH(k_discs, (unsigned)((a->nt + 127) / 128), 128, 0, s, a->xyz.as<double>(), a->tri.as<int32_t>(),
+               a->nt, c0, da);
+    BEM_LAUNCH(k_discs, (unsigned)((b->nt + 127) / 128), 128, 0, s, b->xyz.as<double>(), b->tri.as<int32_t>(),
+               b->nt, c0, db);
+    unsigned gx = (unsigned)std::min<int64_t>((b->nt + 255) / 256, 64);
+    dim3 grid(gx, (unsigned)std::min<int64_t>(a->nt, 65535));
+    BEM_LAUNCH(k_candidates, grid, 256, 0, s, da, a->nt, db, b->nt, counter, cand, NOALLOC_MAX_CAND);
+    unsigned long long ncand = 0;
+    BEM_CUDA_TRY(cudaMemcpyAsync(&ncand, counter, sizeof(ncand), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    BEM_REQUIRE((int64_t)ncand <= NOALLOC_MAX_CAND,
+                "bem_projection_noalloc supports at most 1048576 candidate triangle pairs (got " +
+                    std::to_string(ncand) + ")");
+    const int64_t need = 9 * (int64_t)ncand;
+    *nnz = need;
+    BEM_REQUIRE(capacity >= need, "output capacity " + std::to_string(capacity) + " is below the " +
+                                      std::to_string(need) + " entries needed");
+    if (ncand > 0)
+        BEM_LAUNCH(k_clip, (unsigned)((ncand + 127) / 128), 128, 0, s, a->xyz.as<double>(), a->tri.as<int32_t>(),
+                   b->xyz.as<double>(), b->tri.as<int32_t>(), cand, (int64_t)ncand, c0, row, col, val);
+    return BEM_OK;
+}
