@@ -67,6 +67,10 @@ typedef struct bem_sparse  bem_sparse;
 
 /* Arithmetic of assembly and matvec. */
 #define BEM_PREC_FP64   0   /* float64 throughout                                        */
+#define BEM_PREC_MIXED  1   /* regular pairs assembled in FP32 into complex64 operators;
+                               singular pairs, mass and mortar in FP64; solve: GMRES with an
+                               FP32 matvec inside FP64 iterative refinement (FP64 residual,
+                               FP64 Arnoldi).  Pattern (1) of the build's precision study.    */
 
 /* Sign variant of the multiple-traces system (paper eq. mtf:discrete). */
 #define BEM_MTF_DERIVED 0   /* transfer blocks as derived from Sec. 2.2: returns phi_int, psi_int */
@@ -124,13 +128,16 @@ BEM_API int64_t    bem_grid_num_triangles(const bem_grid* g);
  * Sauter-Schwab transformations with n_singular Gauss points per axis for
  * coincident, edge- and vertex-adjacent pairs).  test must equal trial (both
  * operators of the method act within one grid).  n_singular in [1, 16].
- * The result is a library-owned device matrix of nv x nv complex128.         */
+ * The result is a library-owned device matrix of nv x nv entries: complex128
+ * for BEM_PREC_FP64, complex64 (two floats) for BEM_PREC_MIXED.              */
 BEM_API bem_status bem_assemble(bem_context* ctx, int op, bem_c128 k, const bem_grid* test,
                         const bem_grid* trial, int precision, int n_singular,
                         bem_matrix** out);
 BEM_API bem_status bem_matrix_destroy(bem_matrix* m);
-/* Copy a matrix out, row-major complex128.  dst_bytes must be at least
- * rows*cols*16.  on_device = 1: dst is a device pointer (copy on the stream,
+/* Bytes per entry of a matrix: 16 (complex128) or 8 (complex64). */
+BEM_API int        bem_matrix_entry_bytes(const bem_matrix* m);
+/* Copy a matrix out, row-major, in its own entry type.  dst_bytes must be at least
+ * rows*cols*entry_bytes.  on_device = 1: dst is a device pointer (copy on the stream,
  * asynchronous); 0: dst is host memory (the call waits).                      */
 BEM_API bem_status bem_matrix_copy_out(bem_context* ctx, const bem_matrix* m, void* dst,
                                int64_t dst_bytes, int on_device);
@@ -195,17 +202,19 @@ typedef struct {
     int32_t n_singular;       /* Gauss points per axis of singular pairs (default 4)             */
     int32_t mtf_variant;      /* BEM_MTF_DERIVED (default) or BEM_MTF_PRINTED                     */
     double  center[3];        /* projection centre for the mortar (default origin)               */
+    double  ir_inner_tol;     /* BEM_PREC_MIXED: relative residual reduction asked of each inner
+                                 GMRES solve (default 1e-6; never below gmres_tol overall)        */
 } bem_solve_opts;
 
 typedef struct {
-    int32_t iterations;       /* GMRES iterations of the last right-hand side                    */
+    int32_t iterations;       /* GMRES iterations, summed over right-hand sides (and inner solves) */
     int32_t converged;        /* 1 if every right-hand side met gmres_tol                        */
     double  residual;         /* final relative preconditioned residual (max over RHS)           */
     double  t_assembly_ms;    /* device time of operator assembly (both grids)                   */
     double  t_mortar_ms;      /* device time of mass + mortar matrices                           */
     double  t_solve_ms;       /* device time of right-hand sides + GMRES                         */
     int32_t mtf_variant;      /* sign variant used                                               */
-    int32_t reserved;
+    int32_t outer_iterations; /* refinement steps (1 for BEM_PREC_FP64)                           */
 } bem_solve_report;
 
 /* Fill opts with the defaults stated above. */

@@ -30,6 +30,7 @@ BEM_E_INTERNAL = -9
 
 BEM_OP_V, BEM_OP_K, BEM_OP_T, BEM_OP_D = 0, 1, 2, 3
 BEM_PREC_FP64 = 0
+BEM_PREC_MIXED = 1
 BEM_MTF_DERIVED, BEM_MTF_PRINTED = 0, 1
 
 
@@ -55,6 +56,7 @@ class bem_solve_opts(C.Structure):
         ("n_singular", C.c_int32),
         ("mtf_variant", C.c_int32),
         ("center", C.c_double * 3),
+        ("ir_inner_tol", C.c_double),
     ]
 
 
@@ -67,7 +69,7 @@ class bem_solve_report(C.Structure):
         ("t_mortar_ms", C.c_double),
         ("t_solve_ms", C.c_double),
         ("mtf_variant", C.c_int32),
-        ("reserved", C.c_int32),
+        ("outer_iterations", C.c_int32),
     ]
 
 
@@ -94,6 +96,7 @@ _SIGNATURES = {
     "bem_assemble": (C.c_int32, [_VP, C.c_int, bem_c128, _VP, _VP, C.c_int, C.c_int, _PVP]),
     "bem_matrix_destroy": (C.c_int32, [_VP]),
     "bem_matrix_copy_out": (C.c_int32, [_VP, _VP, _VP, _I64, C.c_int]),
+    "bem_matrix_entry_bytes": (C.c_int, [_VP]),
     "bem_matrix_shape": (C.c_int32, [_VP, _PI64, _PI64]),
     "bem_mass": (C.c_int32, [_VP, _VP, _PVP]),
     "bem_projection": (C.c_int32, [_VP, _VP, _VP, C.POINTER(C.c_double), _PVP]),
@@ -253,12 +256,17 @@ def bem_matrix_shape(m):
     return r.value, c.value
 
 
+def bem_matrix_entry_bytes(m):
+    return int(_lib.bem_matrix_entry_bytes(m))
+
+
 def bem_matrix_copy_out(ctx, m, out=None):
     """Copy into `out` (complex128 NumPy array or CUDA tensor); allocates a NumPy
     array when out is None.  Returns out."""
     rows, cols = bem_matrix_shape(m)
     if out is None:
-        out = np.empty((rows, cols), dtype=np.complex128)
+        dt = np.complex128 if bem_matrix_entry_bytes(m) == 16 else np.complex64
+        out = np.empty((rows, cols), dtype=dt)
     p, dev = _ptr(out)
     nbytes = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
     _check(_lib.bem_matrix_copy_out(ctx, m, p, int(nbytes), int(dev)))

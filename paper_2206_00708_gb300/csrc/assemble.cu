@@ -68,6 +68,9 @@ __device__ __forceinline__ void add2(double2* M, int64_t idx, double re, double 
     atomicAdd(&M[idx].x, re);
     atomicAdd(&M[idx].y, im);
 }
+__device__ __forceinline__ void add2(float2* M, int64_t idx, double re, double im) {
+    atomicAdd(&M[idx], make_float2((float)re, (float)im));
+}
 
 template <bool CK>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -189,12 +192,12 @@ k_regular(const TriRec* __restrict__ rec, const int32_t* __restrict__ tri, int64
 
 // One warp per singular pair.  Pairs [0, nt) are coincident (tau = sigma = w);
 // then the edge- and vertex-adjacent list.
-template <bool CK>
+template <bool CK, typename Out>
 __global__ void __launch_bounds__(128)
 k_singular(const double* __restrict__ xyz, const int32_t* __restrict__ tri, const TriRec* __restrict__ rec,
            const SingPair* __restrict__ pairs, int64_t nt, int64_t npairs, const double* __restrict__ ss,
-           int3 count, int3 offset, KParams P, double2* __restrict__ V, double2* __restrict__ K,
-           double2* __restrict__ T, double2* __restrict__ D) {
+           int3 count, int3 offset, KParams P, Out* __restrict__ V, Out* __restrict__ K,
+           Out* __restrict__ T, Out* __restrict__ D) {
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (w >= nt + npairs) return;
@@ -339,12 +342,35 @@ bem_status assemble_operators_fp64(const bem_grid* g, double k_re, double k_im, 
     const unsigned blocks = (unsigned)((warps * 32 + 127) / 128);
     int3 c3 = make_int3(cnt[0], cnt[1], cnt[2]), o3 = make_int3(off[0], off[1], off[2]);
     if (ck)
-        BEM_LAUNCH(k_singular<true>, blocks, 128, 0, s, g->xyz.as<double>(), g->tri.as<int32_t>(), g->rec.as<TriRec>(),
+        BEM_LAUNCH((k_singular<true, double2>), blocks, 128, 0, s, g->xyz.as<double>(), g->tri.as<int32_t>(), g->rec.as<TriRec>(),
                                                 g->sing.as<SingPair>(), nt, npairs, ss, c3, o3, P, V, K, T, D);
     else
-        BEM_LAUNCH(k_singular<false>, blocks, 128, 0, s, g->xyz.as<double>(), g->tri.as<int32_t>(), g->rec.as<TriRec>(),
+        BEM_LAUNCH((k_singular<false, double2>), blocks, 128, 0, s, g->xyz.as<double>(), g->tri.as<int32_t>(), g->rec.as<TriRec>(),
                                                  g->sing.as<SingPair>(), nt, npairs, ss, c3, o3, P, V, K, T, D);
     BEM_CHECK_LAUNCH();
+    return BEM_OK;
+}
+
+bem_status assemble_singular_into_c64(const bem_grid* g, double k_re, double k_im, int n_singular, float2* V,
+                                      float2* K, float2* T, float2* D, cudaStream_t s) {
+    KParams P;
+    P.kr = k_re;
+    P.ki = k_im;
+    P.k2r = k_re * k_re - k_im * k_im;
+    P.k2i = 2.0 * k_re * k_im;
+    P.n = g->nv;
+    const double* ss;
+    int cnt[3], off[3];
+    BEM_TRY(ss_table_get(n_singular, s, &ss, cnt, off));
+    const int64_t npairs = g->n_edge + g->n_vertex, nt = g->nt;
+    const unsigned blocks = (unsigned)(((nt + npairs) * 32 + 127) / 128);
+    int3 c3 = make_int3(cnt[0], cnt[1], cnt[2]), o3 = make_int3(off[0], off[1], off[2]);
+    if (k_im != 0.0)
+        BEM_LAUNCH((k_singular<true, float2>), blocks, 128, 0, s, g->xyz.as<double>(), g->tri.as<int32_t>(),
+                   g->rec.as<TriRec>(), g->sing.as<SingPair>(), nt, npairs, ss, c3, o3, P, V, K, T, D);
+    else
+        BEM_LAUNCH((k_singular<false, float2>), blocks, 128, 0, s, g->xyz.as<double>(), g->tri.as<int32_t>(),
+                   g->rec.as<TriRec>(), g->sing.as<SingPair>(), nt, npairs, ss, c3, o3, P, V, K, T, D);
     return BEM_OK;
 }
 

@@ -110,6 +110,25 @@ struct __align__(16) TriRec {
 constexpr int TRIREC_DOUBLES = 50;
 static_assert(sizeof(TriRec) == TRIREC_DOUBLES * 8, "TriRec layout");
 
+// FP32 per-triangle record of the mixed-precision assembly (56 floats, 224 bytes),
+// stored in tile order.  The centroid is a double-float pair (hi + lo); quadrature
+// points are stored relative to the centroid so that FP32 keeps them accurate.
+struct __align__(16) TriRec32 {
+    float ch[3], cl[3];  // centroid, hi and lo parts             (floats  0..5)
+    float u[6][3];       // quadrature points minus the centroid  (floats  6..23)
+    float wl[6][3];      // w_p * J * lambda_a(p)                 (floats 24..41)
+    float n[3];          // outward unit normal                   (floats 42..44)
+    float curl[3][3];    // surface curls                         (floats 45..53)
+    float pad[2];
+};
+constexpr int TRIREC32_FLOATS = 56;
+static_assert(sizeof(TriRec32) == TRIREC32_FLOATS * 4, "TriRec32 layout");
+
+// Tiles of the mixed-precision assembly: at most TILE_TRI triangles and at most
+// TILE_NV distinct vertices each.
+constexpr int TILE_TRI = 32;
+constexpr int TILE_NV = 40;
+
 // Singular pair: kind 1 edge / 2 vertex, triangles t < s, Sauter-Schwab vertex order.
 struct SingPair {
     int32_t t, s;
@@ -138,13 +157,22 @@ struct bem_grid {
     // mass matrix CSR structure (rows = vertices) and per-triangle slot map
     bem::DevBuf m_rowptr, m_col, m_slot;   // m_slot [nt][3][3] CSR position
     int64_t m_nnz = 0;
-    // angular disc per triangle seen from the origin (mortar prefilter)
     double surface_area = 0.0;
+    // tiles of the mixed-precision assembly (triangles in tile order)
+    int64_t ntile = 0;
+    bem::DevBuf t_order;        // tile position -> triangle index           [nt]
+    bem::DevBuf t_verts;        // vertex ids of triangles in tile order     [nt][3]
+    bem::DevBuf t_slots;        // local vertex slots in the tile, 3 bytes   [nt]
+    bem::DevBuf tile_tstart;    // first tile position of each tile          [ntile + 1]
+    bem::DevBuf tile_vstart;    // first entry of each tile's vertex list    [ntile + 1]
+    bem::DevBuf tile_vert;      // tile vertex lists (global vertex ids)
+    bem::DevBuf rec32;          // TriRec32 in tile order                    [nt]
 };
 
 struct bem_matrix {
     int64_t rows = 0, cols = 0;
-    bem::DevBuf data;              // complex128 row-major
+    int entry_bytes = 16;          // 16: complex128, 8: complex64
+    bem::DevBuf data;              // row-major
 };
 
 struct bem_sparse {
@@ -158,6 +186,16 @@ namespace bem {
 bem_status grid_build_geometry(bem_grid* g);
 bem_status mass_values(const bem_grid* g, double* d_val, cudaStream_t s);      // [m_nnz]
 bem_status mass_inverse_diag(const bem_grid* g, const double* d_val, double* d_dinv, cudaStream_t s);
+
+// grid.cu: FP32 geometry records in tile order (mixed-precision assembly)
+bem_status grid_build_rec32(const bem_grid* g, cudaStream_t s);
+
+// assemble32.cu: regular pairs in FP32 into complex64 V, K, T, D (row-major, zeroed by the caller)
+bem_status assemble_regular_fp32(const bem_grid* g, double k_re, double k_im, float2* V, float2* K, float2* T,
+                                 float2* D, cudaStream_t s);
+// assemble.cu: singular pairs (FP64 quadrature) added into complex64 matrices
+bem_status assemble_singular_into_c64(const bem_grid* g, double k_re, double k_im, int n_singular, float2* V,
+                                      float2* K, float2* T, float2* D, cudaStream_t s);
 
 // assemble.cu: V, K, T, D (row-major N x N complex128; any pointer may be null).
 bem_status assemble_operators_fp64(const bem_grid* g, double k_re, double k_im, int n_singular,

@@ -45,7 +45,7 @@ void DevBuf::release() {
     bytes = 0;
 }
 
-bem_status solve_transmission_fp64(bem_context* ctx, const bem_grid* ge, const bem_grid* gi, bem_c128 k_int,
+bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const bem_grid* gi, bem_c128 k_int,
                                    bem_c128 k_ext, double rho_ratio, const bem_incident* inc,
                                    const bem_solve_opts* o, bem_c128* v_ext, bem_c128* w_ext, bem_c128* v_int,
                                    bem_c128* w_int, int on_device, bem_solve_report* rep);
@@ -191,7 +191,7 @@ bem_status bem_assemble(bem_context* ctx, int op, bem_c128 k, const bem_grid* te
     BEM_REQUIRE(test != nullptr && trial != nullptr, "null grid");
     BEM_REQUIRE(test == trial, "test and trial grids must be the same grid for V, K, T, D");
     BEM_REQUIRE(op >= BEM_OP_V && op <= BEM_OP_D, "unknown operator");
-    BEM_REQUIRE(precision == BEM_PREC_FP64, "unsupported precision");
+    BEM_REQUIRE(precision == BEM_PREC_FP64 || precision == BEM_PREC_MIXED, "unsupported precision");
     BEM_REQUIRE(n_singular >= 1 && n_singular <= 16, "n_singular must be in [1, 16]");
     BEM_REQUIRE(std::isfinite(k.re) && std::isfinite(k.im), "wavenumber is not finite");
     std::unique_ptr<bem_matrix> m(new (std::nothrow) bem_matrix());
@@ -201,14 +201,31 @@ bem_status bem_assemble(bem_context* ctx, int op, bem_c128 k, const bem_grid* te
     }
     const int64_t N = test->nv;
     m->rows = m->cols = N;
-    BEM_TRY(m->data.alloc((size_t)N * N * 16, ctx->stream));
-    double2* p = m->data.as<double2>();
-    BEM_TRY(assemble_operators_fp64(test, k.re, k.im, n_singular, op == BEM_OP_V ? p : nullptr,
-                                    op == BEM_OP_K ? p : nullptr, op == BEM_OP_T ? p : nullptr,
-                                    op == BEM_OP_D ? p : nullptr, ctx->stream));
+    cudaStream_t s = ctx->stream;
+    if (precision == BEM_PREC_FP64) {
+        m->entry_bytes = 16;
+        BEM_TRY(m->data.alloc((size_t)N * N * 16, s));
+        double2* p = m->data.as<double2>();
+        BEM_TRY(assemble_operators_fp64(test, k.re, k.im, n_singular, op == BEM_OP_V ? p : nullptr,
+                                        op == BEM_OP_K ? p : nullptr, op == BEM_OP_T ? p : nullptr,
+                                        op == BEM_OP_D ? p : nullptr, s));
+    } else {
+        m->entry_bytes = 8;
+        BEM_TRY(m->data.alloc((size_t)N * N * 8, s));
+        BEM_CUDA_TRY(cudaMemsetAsync(m->data.p, 0, (size_t)N * N * 8, s));
+        float2* p = m->data.as<float2>();
+        float2* V = op == BEM_OP_V ? p : nullptr;
+        float2* K = op == BEM_OP_K ? p : nullptr;
+        float2* T = op == BEM_OP_T ? p : nullptr;
+        float2* D = op == BEM_OP_D ? p : nullptr;
+        BEM_TRY(assemble_regular_fp32(test, k.re, k.im, V, K, T, D, s));
+        BEM_TRY(assemble_singular_into_c64(test, k.re, k.im, n_singular, V, K, T, D, s));
+    }
     *out = m.release();
     return BEM_OK;
 }
+
+int bem_matrix_entry_bytes(const bem_matrix* m) { return m ? m->entry_bytes : 0; }
 
 bem_status bem_matrix_destroy(bem_matrix* m) {
     delete m;
@@ -225,8 +242,8 @@ bem_status bem_matrix_shape(const bem_matrix* m, int64_t* rows, int64_t* cols) {
 bem_status bem_matrix_copy_out(bem_context* ctx, const bem_matrix* m, void* dst, int64_t dst_bytes, int on_device) {
     CTX_GUARD(ctx);
     BEM_REQUIRE(m != nullptr && dst != nullptr, "null matrix or destination");
-    const int64_t need = m->rows * m->cols * 16;
-    BEM_REQUIRE(dst_bytes >= need, "destination smaller than rows*cols*16 bytes");
+    const int64_t need = m->rows * m->cols * m->entry_bytes;
+    BEM_REQUIRE(dst_bytes >= need, "destination smaller than rows*cols*entry_bytes");
     BEM_CUDA_TRY(cudaMemcpyAsync(dst, m->data.p, need, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                  ctx->stream));
     if (!on_device) BEM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -320,6 +337,7 @@ void bem_solve_opts_default(bem_solve_opts* o) {
     o->n_singular = 4;
     o->mtf_variant = BEM_MTF_DERIVED;
     o->center[0] = o->center[1] = o->center[2] = 0.0;
+    o->ir_inner_tol = 1e-6;
 }
 
 bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const bem_grid* intr, bem_c128 k_int,
@@ -339,13 +357,14 @@ bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const b
     BEM_REQUIRE(o.gmres_tol >= 0.0 && o.gmres_maxiter >= 1, "bad GMRES options");
     BEM_REQUIRE(o.n_singular >= 1 && o.n_singular <= 16, "n_singular must be in [1, 16]");
     BEM_REQUIRE(o.mtf_variant == BEM_MTF_DERIVED || o.mtf_variant == BEM_MTF_PRINTED, "unknown MTF variant");
-    BEM_REQUIRE(o.precision == BEM_PREC_FP64, "unsupported precision");
+    BEM_REQUIRE(o.precision == BEM_PREC_FP64 || o.precision == BEM_PREC_MIXED, "unsupported precision");
+    BEM_REQUIRE(o.ir_inner_tol > 0.0 && o.ir_inner_tol < 1.0, "ir_inner_tol must be in (0, 1)");
     for (int r = 0; r < inc->n_rhs; ++r) {
         const double* d = inc->dirs + 3 * r;
         const double nd = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         BEM_REQUIRE(std::isfinite(nd) && std::fabs(nd - 1.0) < 1e-6, "incident directions must be unit vectors");
     }
-    return solve_transmission_fp64(ctx, ext, intr, k_int, k_ext, rho_int_over_rho_ext, inc, &o, v_ext, w_ext, v_int,
+    return solve_transmission_impl(ctx, ext, intr, k_int, k_ext, rho_int_over_rho_ext, inc, &o, v_ext, w_ext, v_int,
                                    w_int, on_device, rep);
 }
 

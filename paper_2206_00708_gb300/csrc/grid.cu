@@ -72,7 +72,108 @@ __global__ void k_diag_inverse(const int32_t* __restrict__ rowptr, const int32_t
         if (col[e] == i) dinv[i] = 1.0 / val[e];
 }
 
+__global__ void k_geometry32(const double* __restrict__ xyz, const int32_t* __restrict__ tri,
+                             const int32_t* __restrict__ order, const TriRec* __restrict__ rec, int64_t nt,
+                             TriRec32* __restrict__ out) {
+    int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pos >= nt) return;
+    const int64_t t = order[pos];
+    double c[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        const int32_t id = tri[3 * t + a];
+        for (int d = 0; d < 3; ++d) c[d] += xyz[3 * (int64_t)id + d];
+    }
+    const TriRec& R = rec[t];
+    TriRec32 r;
+    for (int d = 0; d < 3; ++d) {
+        c[d] /= 3.0;
+        r.ch[d] = (float)c[d];
+        r.cl[d] = (float)(c[d] - (double)r.ch[d]);
+        r.n[d] = (float)R.n[d];
+    }
+    for (int p = 0; p < 6; ++p)
+        for (int d = 0; d < 3; ++d) {
+            r.u[p][d] = (float)(R.q[p][d] - c[d]);
+            r.wl[p][d] = (float)R.wl[p][d];
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int d = 0; d < 3; ++d) r.curl[a][d] = (float)R.curl[a][d];
+    r.pad[0] = r.pad[1] = 0.f;
+    out[pos] = r;
+}
+
+// Morton code of a point in the unit cube (21 bits per axis)
+uint64_t morton3(double x, double y, double z) {
+    auto spread = [](uint64_t v) {
+        v &= 0x1fffffull;
+        v = (v | (v << 32)) & 0x1f00000000ffffull;
+        v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+        v = (v | (v << 8)) & 0x100f00f00f00f00full;
+        v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+        v = (v | (v << 2)) & 0x1249249249249249ull;
+        return v;
+    };
+    auto q = [](double u) { return (uint64_t)(std::min(std::max(u, 0.0), 1.0) * 2097151.0); };
+    return spread(q(x)) | (spread(q(y)) << 1) | (spread(q(z)) << 2);
+}
+
+struct Tiles {
+    std::vector<int32_t> tstart, vstart, vert;
+    std::vector<uint32_t> slots;  // per position
+    int64_t total_vertices = 0;
+};
+
+// Greedy tiles over a triangle order: a tile takes triangles while it has fewer than
+// TILE_TRI of them and at most TILE_NV distinct vertices.
+Tiles make_tiles(const std::vector<int32_t>& tri, const std::vector<int32_t>& order) {
+    Tiles T;
+    const int64_t nt = (int64_t)order.size();
+    T.slots.resize(nt);
+    std::vector<int32_t> cur;
+    int64_t start = 0;
+    auto close = [&](int64_t end) {
+        T.tstart.push_back((int32_t)start);
+        T.vstart.push_back((int32_t)T.vert.size());
+        std::vector<int32_t> vs(cur);
+        std::sort(vs.begin(), vs.end());
+        for (int64_t p = start; p < end; ++p) {
+            uint32_t pk = 0;
+            for (int a = 0; a < 3; ++a) {
+                const int32_t v = tri[3 * (int64_t)order[p] + a];
+                const uint32_t sl = (uint32_t)(std::lower_bound(vs.begin(), vs.end(), v) - vs.begin());
+                pk |= sl << (8 * a);
+            }
+            T.slots[p] = pk;
+        }
+        T.vert.insert(T.vert.end(), vs.begin(), vs.end());
+        T.total_vertices += (int64_t)vs.size();
+        cur.clear();
+        start = end;
+    };
+    for (int64_t p = 0; p < nt; ++p) {
+        const int32_t* tv = &tri[3 * (int64_t)order[p]];
+        int add = 0;
+        for (int a = 0; a < 3; ++a)
+            if (std::find(cur.begin(), cur.end(), tv[a]) == cur.end() &&
+                std::find(tv, tv + a, tv[a]) == tv + a)
+                ++add;
+        if (p > start && (p - start >= TILE_TRI || (int)cur.size() + add > TILE_NV)) close(p);
+        for (int a = 0; a < 3; ++a)
+            if (std::find(cur.begin(), cur.end(), tv[a]) == cur.end()) cur.push_back(tv[a]);
+    }
+    close(nt);
+    T.tstart.push_back((int32_t)nt);
+    T.vstart.push_back((int32_t)T.vert.size());
+    return T;
+}
+
 }  // namespace
+
+bem_status grid_build_rec32(const bem_grid* g, cudaStream_t s) {
+    BEM_LAUNCH(k_geometry32, (unsigned)((g->nt + 127) / 128), 128, 0, s, g->xyz.as<double>(), g->tri.as<int32_t>(),
+               g->t_order.as<int32_t>(), g->rec.as<TriRec>(), g->nt, g->rec32.as<TriRec32>());
+    return BEM_OK;
+}
 
 bem_status grid_build_geometry(bem_grid* g) {
     cudaStream_t s = g->ctx->stream;
@@ -160,11 +261,54 @@ bem_status grid_build_geometry(bem_grid* g) {
     BEM_CUDA_TRY(cudaMemcpyAsync(g->m_rowptr.p, rowptr.data(), rowptr.size() * 4, cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(cudaMemcpyAsync(g->m_col.p, col.data(), col.size() * 4, cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(cudaMemcpyAsync(g->m_slot.p, slot.data(), slot.size() * 4, cudaMemcpyHostToDevice, s));
+    // ---- tiles for the mixed-precision assembly (host) -------------------------------
+    // the better of the given order and a Morton order of the centroids (fewer tile vertices)
+    std::vector<int32_t> natural(nt), morton(nt);
+    for (int64_t t = 0; t < nt; ++t) natural[t] = morton[t] = (int32_t)t;
+    {
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int64_t v = 0; v < nv; ++v)
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], g->h_xyz[3 * v + d]);
+                hi[d] = std::max(hi[d], g->h_xyz[3 * v + d]);
+            }
+        std::vector<uint64_t> code(nt);
+        for (int64_t t = 0; t < nt; ++t) {
+            double c[3] = {0, 0, 0};
+            for (int a = 0; a < 3; ++a)
+                for (int d = 0; d < 3; ++d) c[d] += g->h_xyz[3 * (int64_t)g->h_tri[3 * t + a] + d] / 3.0;
+            double u[3];
+            for (int d = 0; d < 3; ++d) u[d] = hi[d] > lo[d] ? (c[d] - lo[d]) / (hi[d] - lo[d]) : 0.0;
+            code[t] = morton3(u[0], u[1], u[2]);
+        }
+        std::stable_sort(morton.begin(), morton.end(), [&](int32_t a, int32_t b) { return code[a] < code[b]; });
+    }
+    Tiles tn = make_tiles(g->h_tri, natural), tm = make_tiles(g->h_tri, morton);
+    const bool use_morton = tm.total_vertices < tn.total_vertices;
+    const Tiles& TL = use_morton ? tm : tn;
+    const std::vector<int32_t>& order = use_morton ? morton : natural;
+    g->ntile = (int64_t)TL.tstart.size() - 1;
+    std::vector<int32_t> tverts(3 * nt);
+    for (int64_t p = 0; p < nt; ++p)
+        for (int a = 0; a < 3; ++a) tverts[3 * p + a] = g->h_tri[3 * (int64_t)order[p] + a];
+    BEM_TRY(g->t_order.alloc(nt * 4, s));
+    BEM_TRY(g->t_verts.alloc(nt * 12, s));
+    BEM_TRY(g->t_slots.alloc(nt * 4, s));
+    BEM_TRY(g->tile_tstart.alloc(TL.tstart.size() * 4, s));
+    BEM_TRY(g->tile_vstart.alloc(TL.vstart.size() * 4, s));
+    BEM_TRY(g->tile_vert.alloc(TL.vert.size() * 4, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(g->t_order.p, order.data(), nt * 4, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(g->t_verts.p, tverts.data(), nt * 12, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(g->t_slots.p, TL.slots.data(), nt * 4, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(g->tile_tstart.p, TL.tstart.data(), TL.tstart.size() * 4, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(g->tile_vstart.p, TL.vstart.data(), TL.vstart.size() * 4, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(g->tile_vert.p, TL.vert.data(), TL.vert.size() * 4, cudaMemcpyHostToDevice, s));
     // ---- geometry records (device) -------------------------------------------------
     BEM_TRY(g->rec.alloc(nt * sizeof(TriRec), s));
     BEM_LAUNCH(k_geometry, (unsigned)((nt + 127) / 128), 128, 0, s, g->xyz.as<double>(), g->tri.as<int32_t>(), nt,
                                                           tri_rule_degree4(), g->rec.as<TriRec>());
-    BEM_CHECK_LAUNCH();
+    BEM_TRY(g->rec32.alloc(nt * sizeof(TriRec32), s));
+    BEM_TRY(grid_build_rec32(g, s));
     // the host vectors above must outlive the asynchronous copies
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
     return BEM_OK;

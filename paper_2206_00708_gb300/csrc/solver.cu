@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <functional>
 
 namespace bem {
 
@@ -347,55 +348,262 @@ __global__ void k_backsolve(const double2* __restrict__ H, int64_t ldh, int m, c
 
 unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// ---------------------------------------------------------------- mixed precision
+struct Blocks32 {
+    const float2* A1[4];
+    const float2* A2[4];
+    double c1[4], c2[4];
+    int64_t rows[4], base[4], x1[4], x2[4];
+};
+
+__global__ void k_to_c64(const double2* __restrict__ x, int64_t n, float2* __restrict__ y) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) y[e] = make_float2((float)x[e].x, (float)x[e].y);
+}
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// complex64 matrices, FP32 arithmetic: one warp per row, 16-byte loads (two complex
+// entries per lane), each 4-entry chunk summed plainly and added to the lane's
+// accumulator with a compensated (two-sum) update; the warp total is formed in FP64.
+__global__ void __launch_bounds__(256) k_gemv_mtf32(Blocks32 B, int64_t n, const float2* __restrict__ x,
+                                                    double2* __restrict__ z) {
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= n) return;
+    int b = 0;
+    while (b < 3 && gw >= B.base[b + 1]) ++b;
+    const int64_t i = gw - B.base[b];
+    const int64_t N = B.rows[b];
+    double2 out = make_double2(0, 0);
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const float2* __restrict__ a = (m == 0 ? B.A1[b] : B.A2[b]) + i * N;
+        const float2* __restrict__ xv = x + (m == 0 ? B.x1[b] : B.x2[b]);
+        float sr = 0.f, si = 0.f, er = 0.f, ei = 0.f;
+        // row start may be only 8-byte aligned: peel to a 16-byte boundary
+        int64_t j0 = ((reinterpret_cast<uintptr_t>(a) & 15) != 0) ? 1 : 0;
+        if (j0 && lane == 0 && N > 0) {
+            const float2 av = a[0], xx = xv[0];
+            sr = fmaf(av.x, xx.x, -av.y * xx.y);
+            si = fmaf(av.x, xx.y, av.y * xx.x);
+        }
+        const int64_t npair = (N - j0) / 2;
+        const float4* __restrict__ a4 = reinterpret_cast<const float4*>(a + j0);
+        for (int64_t p = lane; p < npair; p += 64) {
+            float cr = 0.f, ci = 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t pp = p + 32 * h;
+                if (pp < npair) {
+                    const float4 av = a4[pp];
+                    const int64_t j = j0 + 2 * pp;
+                    const float2 x0 = xv[j], x1 = xv[j + 1];
+                    cr = fmaf(av.x, x0.x, cr); cr = fmaf(-av.y, x0.y, cr);
+                    ci = fmaf(av.x, x0.y, ci); ci = fmaf(av.y, x0.x, ci);
+                    cr = fmaf(av.z, x1.x, cr); cr = fmaf(-av.w, x1.y, cr);
+                    ci = fmaf(av.z, x1.y, ci); ci = fmaf(av.w, x1.x, ci);
+                }
+            }
+            float t, e;
+            two_sum_f(sr, cr, t, e); sr = t; er += e;
+            two_sum_f(si, ci, t, e); si = t; ei += e;
+        }
+        if (((N - j0) & 1) && lane == 1) {  // odd tail
+            const int64_t j = N - 1;
+            const float2 av = a[j], xx = xv[j];
+            float t, e;
+            two_sum_f(sr, fmaf(av.x, xx.x, -av.y * xx.y), t, e); sr = t; er += e;
+            two_sum_f(si, fmaf(av.x, xx.y, av.y * xx.x), t, e); si = t; ei += e;
+        }
+        double2 v = make_double2((double)sr + (double)er, (double)si + (double)ei);
+        v = warp_sum2(v);
+        const double c = m == 0 ? B.c1[b] : B.c2[b];
+        out.x += c * v.x;
+        out.y += c * v.y;
+    }
+    if (lane == 0) z[gw] = out;
+}
+
+// complex64 matrices, FP64 arithmetic (outer residual of the refinement)
+__global__ void __launch_bounds__(256) k_gemv_mtf_c64_f64(Blocks32 B, int64_t n, const double2* __restrict__ x,
+                                                          double2* __restrict__ z) {
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= n) return;
+    int b = 0;
+    while (b < 3 && gw >= B.base[b + 1]) ++b;
+    const int64_t i = gw - B.base[b];
+    const int64_t N = B.rows[b];
+    const float2* __restrict__ a1 = B.A1[b] + i * N;
+    const float2* __restrict__ a2 = B.A2[b] + i * N;
+    const double2* __restrict__ x1 = x + B.x1[b];
+    const double2* __restrict__ x2 = x + B.x2[b];
+    double2 s1 = make_double2(0, 0), s2 = make_double2(0, 0);
+    for (int64_t j = lane; j < N; j += 32) {
+        const float2 p = a1[j], q = a2[j];
+        s1 = cfma(make_double2(p.x, p.y), x1[j], s1);
+        s2 = cfma(make_double2(q.x, q.y), x2[j], s2);
+    }
+    s1 = warp_sum2(s1);
+    s2 = warp_sum2(s2);
+    if (lane == 0) z[gw] = make_double2(B.c1[b] * s1.x + B.c2[b] * s2.x, B.c1[b] * s1.y + B.c2[b] * s2.y);
+}
+
+// y = a - b
+__global__ void k_sub(const double2* __restrict__ a, const double2* __restrict__ b, int64_t n,
+                      double2* __restrict__ y) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) y[e] = make_double2(a[e].x - b[e].x, a[e].y - b[e].y);
+}
+
+// x += d
+__global__ void k_acc(double2* __restrict__ x, const double2* __restrict__ d, int64_t n) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < n) {
+        x[e].x += d[e].x;
+        x[e].y += d[e].y;
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host driver
-struct MtfOperator {
-    int64_t Ne = 0, Ni = 0, n = 0;
-    Blocks B{};
+namespace {
+
+struct MassOp {
     MassPair M{};
+    double2 *r = nullptr, *dA = nullptr, *dB = nullptr;  // workspaces [n]
+};
+
+struct TransferOp {
     const int32_t *prow = nullptr, *pcol = nullptr;
     const double* pval = nullptr;
     int64_t pnnz = 0;
     double4 coef{};
-    double2 *z = nullptr, *r = nullptr, *dA = nullptr, *dB = nullptr;  // workspaces [n]
 };
 
-bem_status mtf_apply(const MtfOperator& op, const double2* x, double2* y, cudaStream_t s, bool weak_only = false) {
-    BEM_LAUNCH(k_gemv_mtf, blocks_for(op.n * 32, 256), 256, 0, s, op.B, op.n, x, op.z);
-    BEM_CHECK_LAUNCH();
-    if (op.pnnz > 0) {
-        BEM_LAUNCH(k_transfer, blocks_for(op.pnnz, 256), 256, 0, s, op.prow, op.pcol, op.pval, op.pnnz, op.Ne, op.Ni,
-                                                           op.coef, x, op.z);
-        BEM_CHECK_LAUNCH();
-    }
-    (void)weak_only;
-    return BEM_OK;
-}
-
-bem_status mass_solve(const MtfOperator& op, const double2* z, double2* y, cudaStream_t s) {
+// M^-1 (z) -> y on the four blocks, Chebyshev on the Jacobi-scaled mass matrices
+bem_status mass_solve(const MassOp& op, const double2* z, double2* y, cudaStream_t s) {
+    const int64_t n = op.M.n;
     const double theta = 0.5 * (CHEB_BETA + CHEB_ALPHA), delta = 0.5 * (CHEB_BETA - CHEB_ALPHA);
     const double sigma = theta / delta;
-    BEM_LAUNCH(k_cheb_init, blocks_for(op.n, 256), 256, 0, s, op.M, z, y, op.r, op.dA, 1.0 / theta);
-    BEM_CHECK_LAUNCH();
+    BEM_LAUNCH(k_cheb_init, blocks_for(n, 256), 256, 0, s, op.M, z, y, op.r, op.dA, 1.0 / theta);
     double rho = 1.0 / sigma;
     double2 *dk = op.dA, *dn = op.dB;
     for (int k = 0; k < CHEB_STEPS; ++k) {
         const double rho_n = 1.0 / (2.0 * sigma - rho);
-        BEM_LAUNCH(k_cheb_step, blocks_for(op.n, 256), 256, 0, s, op.M, dk, dn, y, op.r, rho_n * rho, 2.0 * rho_n / delta);
-        BEM_CHECK_LAUNCH();
+        BEM_LAUNCH(k_cheb_step, blocks_for(n, 256), 256, 0, s, op.M, dk, dn, y, op.r, rho_n * rho, 2.0 * rho_n / delta);
         rho = rho_n;
         std::swap(dk, dn);
     }
     return BEM_OK;
 }
 
-bem_status strong_apply(const MtfOperator& op, const double2* x, double2* y, cudaStream_t s) {
-    BEM_TRY(mtf_apply(op, x, y, s));
-    return mass_solve(op, op.z, y, s);
+bem_status transfer_add(const TransferOp& t, int64_t Ne, int64_t Ni, const double2* x, double2* z, cudaStream_t s) {
+    if (t.pnnz > 0)
+        BEM_LAUNCH(k_transfer, blocks_for(t.pnnz, 256), 256, 0, s, t.prow, t.pcol, t.pval, t.pnnz, Ne, Ni, t.coef, x, z);
+    return BEM_OK;
 }
 
-namespace {
+using Apply = std::function<bem_status(const double2* in, double2* out)>;
+
+struct GmresWork {
+    int maxit = 0;
+    int64_t n = 0, ldh = 0;
+    DevBuf Vb, H, cs, sn, g, resd, partial, hbuf, y, work, w, nrm;
+    double* h_res = nullptr;
+    ~GmresWork() {
+        if (h_res) cudaFreeHost(h_res);
+    }
+    bem_status init(int maxit_, int64_t n_, cudaStream_t s) {
+        maxit = maxit_;
+        n = n_;
+        ldh = maxit + 1;
+        BEM_TRY(Vb.alloc((size_t)(maxit + 1) * n * 16, s));
+        BEM_TRY(H.alloc((size_t)ldh * (maxit + 1) * 16, s));
+        BEM_TRY(cs.alloc((maxit + 1) * 8, s));
+        BEM_TRY(sn.alloc((maxit + 1) * 16, s));
+        BEM_TRY(g.alloc((maxit + 2) * 16, s));
+        BEM_TRY(resd.alloc(8, s));
+        BEM_TRY(partial.alloc((size_t)(maxit + 1) * RED_BLOCKS * 16, s));
+        BEM_TRY(hbuf.alloc((maxit + 1) * 16, s));
+        BEM_TRY(y.alloc((maxit + 1) * 16, s));
+        BEM_TRY(work.alloc((maxit + 1) * 16, s));
+        BEM_TRY(w.alloc(n * 16, s));
+        BEM_TRY(nrm.alloc(16, s));
+        BEM_CUDA_TRY(cudaMallocHost(&h_res, 16));
+        return BEM_OK;
+    }
+};
+
+// ||v||_2 read back to the host
+bem_status norm2(GmresWork& W, const double2* v, double* out, cudaStream_t s) {
+    BEM_LAUNCH(k_dots_partial, dim3(RED_BLOCKS, 1), 256, 0, s, v, W.n, W.n, v, W.partial.as<double2>());
+    BEM_LAUNCH(k_dots_final, 1, 32, 0, s, W.partial.as<double2>(), 1, W.nrm.as<double2>(), 0);
+    BEM_CUDA_TRY(cudaMemcpyAsync(W.h_res, W.nrm.p, 8, cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = std::sqrt(std::max(W.h_res[0], 0.0));
+    return BEM_OK;
+}
+
+// Unrestarted GMRES from x0 = 0 on apply(x) = rhs; stops when the residual estimate
+// is <= tol_abs.  Writes x; returns iterations and the final estimate.
+bem_status gmres_run(GmresWork& W, const Apply& apply, const double2* rhs, double beta, double tol_abs,
+                     double2* x, int* iters_out, double* res_out, cudaStream_t s) {
+    const int64_t n = W.n, ldv = n, ldh = W.ldh;
+    double2* Vp = W.Vb.as<double2>();
+    const unsigned eb = blocks_for(n, 256);
+    BEM_CUDA_TRY(cudaMemsetAsync(W.H.p, 0, (size_t)ldh * (W.maxit + 1) * 16, s));
+    BEM_CUDA_TRY(cudaMemsetAsync(W.g.p, 0, (W.maxit + 2) * 16, s));
+    int iters = 0;
+    double resid = beta;
+    if (beta > 0.0) {
+        // V_0 = rhs / beta, g_0 = beta
+        BEM_LAUNCH(k_dots_partial, dim3(RED_BLOCKS, 1), 256, 0, s, rhs, n, ldv, rhs, W.partial.as<double2>());
+        BEM_LAUNCH(k_dots_final, 1, 32, 0, s, W.partial.as<double2>(), 1, W.nrm.as<double2>(), 0);
+        BEM_LAUNCH(k_normalize, eb, 256, 0, s, rhs, n, W.nrm.as<double2>(), Vp, W.g.as<double2>());
+        for (int j = 0; j < W.maxit; ++j) {
+            double2* vj = Vp + (int64_t)j * ldv;
+            BEM_TRY(apply(vj, W.w.as<double2>()));
+            double2* Hj = W.H.as<double2>() + (int64_t)j * ldh;
+            for (int pass = 0; pass < 2; ++pass) {  // CGS2
+                double2* h = pass == 0 ? Hj : W.hbuf.as<double2>();
+                BEM_LAUNCH(k_dots_partial, dim3(RED_BLOCKS, j + 1), 256, 0, s, Vp, n, ldv, W.w.as<double2>(),
+                           W.partial.as<double2>());
+                BEM_LAUNCH(k_dots_final, j + 1, 32, 0, s, W.partial.as<double2>(), j + 1, h, 0);
+                BEM_LAUNCH(k_combine, eb, 256, 0, s, Vp, n, ldv, j + 1, h, W.w.as<double2>(), 0);
+            }
+            BEM_LAUNCH(k_add, 1, 256, 0, s, Hj, W.hbuf.as<double2>(), j + 1);
+            BEM_LAUNCH(k_dots_partial, dim3(RED_BLOCKS, 1), 256, 0, s, W.w.as<double2>(), n, ldv, W.w.as<double2>(),
+                       W.partial.as<double2>());
+            BEM_LAUNCH(k_dots_final, 1, 32, 0, s, W.partial.as<double2>(), 1, W.nrm.as<double2>(), 0);
+            BEM_LAUNCH(k_normalize, eb, 256, 0, s, W.w.as<double2>(), n, W.nrm.as<double2>(),
+                       Vp + (int64_t)(j + 1) * ldv, Hj + j + 1);
+            BEM_LAUNCH(k_givens, 1, 32, 0, s, W.H.as<double2>(), ldh, j, W.cs.as<double>(), W.sn.as<double2>(),
+                       W.g.as<double2>(), W.resd.as<double>());
+            BEM_CUDA_TRY(cudaMemcpyAsync(W.h_res, W.resd.p, 8, cudaMemcpyDeviceToHost, s));
+            BEM_CUDA_TRY(cudaStreamSynchronize(s));
+            iters = j + 1;
+            resid = W.h_res[0];
+            if (!(resid > tol_abs)) break;
+        }
+    }
+    if (iters > 0) {
+        BEM_LAUNCH(k_backsolve, 1, 256, 0, s, W.H.as<double2>(), ldh, iters, W.g.as<double2>(), W.y.as<double2>(),
+                   W.work.as<double2>());
+        BEM_LAUNCH(k_combine, eb, 256, 0, s, Vp, n, ldv, iters, W.y.as<double2>(), x, 1);
+    } else {
+        BEM_CUDA_TRY(cudaMemsetAsync(x, 0, n * 16, s));
+    }
+    *iters_out = iters;
+    *res_out = resid;
+    return BEM_OK;
+}
 
 struct EventTimer {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -415,27 +623,53 @@ struct EventTimer {
     }
 };
 
+template <class BT, class MT>
+void fill_blocks(BT& B, MT* const m1[4], MT* const m2[4], int64_t Ne, int64_t Ni) {
+    const double c1[4] = {-1.0, 1.0, -1.0, 1.0};
+    const int64_t rows[4] = {Ne, Ne, Ni, Ni};
+    const int64_t base[4] = {0, Ne, 2 * Ne, 2 * Ne + Ni};
+    const int64_t x1[4] = {0, 0, 2 * Ne, 2 * Ne};
+    const int64_t x2[4] = {Ne, Ne, 2 * Ne + Ni, 2 * Ne + Ni};
+    for (int b = 0; b < 4; ++b) {
+        B.A1[b] = m1[b]; B.A2[b] = m2[b]; B.c1[b] = c1[b]; B.c2[b] = 1.0;
+        B.rows[b] = rows[b]; B.base[b] = base[b]; B.x1[b] = x1[b]; B.x2[b] = x2[b];
+    }
+}
+
 }  // namespace
 
-bem_status solve_transmission_fp64(bem_context* ctx, const bem_grid* ge, const bem_grid* gi, bem_c128 k_int,
+bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const bem_grid* gi, bem_c128 k_int,
                                    bem_c128 k_ext, double rho_ratio, const bem_incident* inc,
                                    const bem_solve_opts* o, bem_c128* v_ext, bem_c128* w_ext, bem_c128* v_int,
                                    bem_c128* w_int, int on_device, bem_solve_report* rep) {
     cudaStream_t s = ctx->stream;
     const int64_t Ne = ge->nv, Ni = gi->nv, n = 2 * Ne + 2 * Ni;
+    const bool mixed = o->precision == BEM_PREC_MIXED;
     EventTimer t_asm, t_mor, t_sol;
     // ---- operators on both grids --------------------------------------------------
-    const size_t be = (size_t)Ne * Ne * sizeof(double2), bi = (size_t)Ni * Ni * sizeof(double2);
-    DevBuf Ve, Ke, Te, De, Vi, Ki, Ti, Di;
-    BEM_TRY(Ve.alloc(be, s)); BEM_TRY(Ke.alloc(be, s)); BEM_TRY(Te.alloc(be, s)); BEM_TRY(De.alloc(be, s));
-    BEM_TRY(Vi.alloc(bi, s)); BEM_TRY(Ki.alloc(bi, s)); BEM_TRY(Ti.alloc(bi, s)); BEM_TRY(Di.alloc(bi, s));
+    const size_t esz = mixed ? 8 : 16;
+    const size_t be = (size_t)Ne * Ne * esz, bi = (size_t)Ni * Ni * esz;
+    DevBuf M[8];  // Ve, Ke, Te, De, Vi, Ki, Ti, Di
+    for (int m = 0; m < 8; ++m) BEM_TRY(M[m].alloc(m < 4 ? be : bi, s));
     cudaEventRecord(t_asm.a, s);
-    BEM_TRY(assemble_operators_fp64(ge, k_ext.re, k_ext.im, o->n_singular, Ve.as<double2>(), Ke.as<double2>(),
-                                    Te.as<double2>(), De.as<double2>(), s));
-    BEM_TRY(assemble_operators_fp64(gi, k_int.re, k_int.im, o->n_singular, Vi.as<double2>(), Ki.as<double2>(),
-                                    Ti.as<double2>(), Di.as<double2>(), s));
+    if (mixed) {
+        for (int m = 0; m < 8; ++m) BEM_CUDA_TRY(cudaMemsetAsync(M[m].p, 0, m < 4 ? be : bi, s));
+        for (int side = 0; side < 2; ++side) {
+            const bem_grid* g = side == 0 ? ge : gi;
+            const bem_c128 k = side == 0 ? k_ext : k_int;
+            float2* P4[4];
+            for (int m = 0; m < 4; ++m) P4[m] = M[4 * side + m].as<float2>();
+            BEM_TRY(assemble_regular_fp32(g, k.re, k.im, P4[0], P4[1], P4[2], P4[3], s));
+            BEM_TRY(assemble_singular_into_c64(g, k.re, k.im, o->n_singular, P4[0], P4[1], P4[2], P4[3], s));
+        }
+    } else {
+        BEM_TRY(assemble_operators_fp64(ge, k_ext.re, k_ext.im, o->n_singular, M[0].as<double2>(), M[1].as<double2>(),
+                                        M[2].as<double2>(), M[3].as<double2>(), s));
+        BEM_TRY(assemble_operators_fp64(gi, k_int.re, k_int.im, o->n_singular, M[4].as<double2>(), M[5].as<double2>(),
+                                        M[6].as<double2>(), M[7].as<double2>(), s));
+    }
     cudaEventRecord(t_asm.b, s);
-    // ---- mass and mortar -----------------------------------------------------------
+    // ---- mass and mortar (FP64) ----------------------------------------------------
     cudaEventRecord(t_mor.a, s);
     DevBuf mve, mvi, dve, dvi, prow, pcol, pval;
     BEM_TRY(mve.alloc(ge->m_nnz * 8, s));
@@ -449,158 +683,134 @@ bem_status solve_transmission_fp64(bem_context* ctx, const bem_grid* ge, const b
     int64_t pnnz = 0;
     BEM_TRY(mortar_coo(gi, ge, o->center, prow, pcol, pval, &pnnz, s));
     cudaEventRecord(t_mor.b, s);
-    // ---- operator description ------------------------------------------------------
-    MtfOperator op;
-    op.Ne = Ne; op.Ni = Ni; op.n = n;
-    const double sgn = o->mtf_variant == BEM_MTF_PRINTED ? -1.0 : 1.0;
-    const double ri_re = rho_ratio, re_ri = 1.0 / rho_ratio;
-    Blocks& B = op.B;
-    const double2* mats1[4] = {Ke.as<double2>(), De.as<double2>(), Ki.as<double2>(), Di.as<double2>()};
-    const double2* mats2[4] = {Ve.as<double2>(), Te.as<double2>(), Vi.as<double2>(), Ti.as<double2>()};
-    const double c1[4] = {-1.0, 1.0, -1.0, 1.0};
-    const int64_t rows[4] = {Ne, Ne, Ni, Ni};
-    const int64_t base[4] = {0, Ne, 2 * Ne, 2 * Ne + Ni};
-    const int64_t x1[4] = {0, 0, 2 * Ne, 2 * Ne};
-    const int64_t x2[4] = {Ne, Ne, 2 * Ne + Ni, 2 * Ne + Ni};
-    for (int b = 0; b < 4; ++b) {
-        B.A1[b] = mats1[b]; B.A2[b] = mats2[b]; B.c1[b] = c1[b]; B.c2[b] = 1.0;
-        B.rows[b] = rows[b]; B.base[b] = base[b]; B.x1[b] = x1[b]; B.x2[b] = x2[b];
-    }
-    op.M.rp[0] = ge->m_rowptr.as<int32_t>(); op.M.ci[0] = ge->m_col.as<int32_t>();
-    op.M.v[0] = mve.as<double>(); op.M.dinv[0] = dve.as<double>();
-    op.M.rp[1] = gi->m_rowptr.as<int32_t>(); op.M.ci[1] = gi->m_col.as<int32_t>();
-    op.M.v[1] = mvi.as<double>(); op.M.dinv[1] = dvi.as<double>();
-    op.M.Ne = Ne; op.M.Ni = Ni; op.M.n = n;
-    op.prow = prow.as<int32_t>(); op.pcol = pcol.as<int32_t>(); op.pval = pval.as<double>(); op.pnnz = pnnz;
-    op.coef = make_double4(-0.5 * sgn, -0.5 * sgn * re_ri, 0.5 * sgn, 0.5 * sgn * ri_re);
-    DevBuf wz, wr, wa, wb;
+    // ---- operator application ------------------------------------------------------
+    DevBuf wz, wr, wa, wb, x32;
     BEM_TRY(wz.alloc(n * 16, s)); BEM_TRY(wr.alloc(n * 16, s)); BEM_TRY(wa.alloc(n * 16, s)); BEM_TRY(wb.alloc(n * 16, s));
-    op.z = wz.as<double2>(); op.r = wr.as<double2>(); op.dA = wa.as<double2>(); op.dB = wb.as<double2>();
-    // ---- GMRES workspace -----------------------------------------------------------
+    MassOp mop;
+    mop.M.rp[0] = ge->m_rowptr.as<int32_t>(); mop.M.ci[0] = ge->m_col.as<int32_t>();
+    mop.M.v[0] = mve.as<double>(); mop.M.dinv[0] = dve.as<double>();
+    mop.M.rp[1] = gi->m_rowptr.as<int32_t>(); mop.M.ci[1] = gi->m_col.as<int32_t>();
+    mop.M.v[1] = mvi.as<double>(); mop.M.dinv[1] = dvi.as<double>();
+    mop.M.Ne = Ne; mop.M.Ni = Ni; mop.M.n = n;
+    mop.r = wr.as<double2>(); mop.dA = wa.as<double2>(); mop.dB = wb.as<double2>();
+    TransferOp top;
+    const double sgn = o->mtf_variant == BEM_MTF_PRINTED ? -1.0 : 1.0;
+    top.prow = prow.as<int32_t>(); top.pcol = pcol.as<int32_t>(); top.pval = pval.as<double>(); top.pnnz = pnnz;
+    top.coef = make_double4(-0.5 * sgn, -0.5 * sgn / rho_ratio, 0.5 * sgn, 0.5 * sgn * rho_ratio);
+    double2* z = wz.as<double2>();
+    Blocks B64{};
+    Blocks32 B32{};
+    if (mixed) {
+        BEM_TRY(x32.alloc(n * 8, s));
+        const float2* m1[4] = {M[1].as<float2>(), M[3].as<float2>(), M[5].as<float2>(), M[7].as<float2>()};
+        const float2* m2[4] = {M[0].as<float2>(), M[2].as<float2>(), M[4].as<float2>(), M[6].as<float2>()};
+        fill_blocks(B32, m1, m2, Ne, Ni);
+    } else {
+        const double2* m1[4] = {M[1].as<double2>(), M[3].as<double2>(), M[5].as<double2>(), M[7].as<double2>()};
+        const double2* m2[4] = {M[0].as<double2>(), M[2].as<double2>(), M[4].as<double2>(), M[6].as<double2>()};
+        fill_blocks(B64, m1, m2, Ne, Ni);
+    }
+    // S A x in the working precision (FP64, or FP32 arithmetic on complex64 storage)
+    Apply apply_work = [&](const double2* xin, double2* yout) -> bem_status {
+        if (mixed) {
+            BEM_LAUNCH(k_to_c64, blocks_for(n, 256), 256, 0, s, xin, n, x32.as<float2>());
+            BEM_LAUNCH(k_gemv_mtf32, blocks_for(n * 32, 256), 256, 0, s, B32, n, x32.as<float2>(), z);
+        } else {
+            BEM_LAUNCH(k_gemv_mtf, blocks_for(n * 32, 256), 256, 0, s, B64, n, xin, z);
+        }
+        BEM_TRY(transfer_add(top, Ne, Ni, xin, z, s));
+        return mass_solve(mop, z, yout, s);
+    };
+    // S A x with FP64 arithmetic on the stored matrices (outer residual of the refinement)
+    Apply apply_fp64 = [&](const double2* xin, double2* yout) -> bem_status {
+        if (mixed) BEM_LAUNCH(k_gemv_mtf_c64_f64, blocks_for(n * 32, 256), 256, 0, s, B32, n, xin, z);
+        else BEM_LAUNCH(k_gemv_mtf, blocks_for(n * 32, 256), 256, 0, s, B64, n, xin, z);
+        BEM_TRY(transfer_add(top, Ne, Ni, xin, z, s));
+        return mass_solve(mop, z, yout, s);
+    };
+    // ---- GMRES ------------------------------------------------------------------------
     const int maxit = (int)std::min<int64_t>(o->gmres_maxiter, n);
-    const int64_t ldv = n;
-    const int64_t ldh = maxit + 1;
-    DevBuf Vb, H, cs, sn, g, resd, partial, hbuf, y, work, fvec, gvec, bvec, w, xsol, nrm;
-    BEM_TRY(Vb.alloc((size_t)(maxit + 1) * ldv * 16, s));
-    BEM_TRY(H.alloc((size_t)ldh * (maxit + 1) * 16, s));
-    BEM_TRY(cs.alloc((maxit + 1) * 8, s));
-    BEM_TRY(sn.alloc((maxit + 1) * 16, s));
-    BEM_TRY(g.alloc((maxit + 2) * 16, s));
-    BEM_TRY(resd.alloc(8, s));
-    BEM_TRY(partial.alloc((size_t)(maxit + 1) * RED_BLOCKS * 16, s));
-    BEM_TRY(hbuf.alloc((maxit + 1) * 16, s));
-    BEM_TRY(y.alloc((maxit + 1) * 16, s));
-    BEM_TRY(work.alloc((maxit + 1) * 16, s));
+    GmresWork W;
+    BEM_TRY(W.init(maxit, n, s));
+    DevBuf fvec, gvec, bvec, sb, xsol, dvec, rvec, tmp;
     BEM_TRY(fvec.alloc(Ne * 16, s)); BEM_TRY(gvec.alloc(Ne * 16, s)); BEM_TRY(bvec.alloc(n * 16, s));
-    BEM_TRY(w.alloc(n * 16, s)); BEM_TRY(xsol.alloc(n * 16, s)); BEM_TRY(nrm.alloc(16, s));
-    double* h_res = nullptr;
-    BEM_CUDA_TRY(cudaMallocHost(&h_res, 16));
-    struct HostFree { double* p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{h_res};
-    double2* Vp = Vb.as<double2>();
+    BEM_TRY(sb.alloc(n * 16, s)); BEM_TRY(xsol.alloc(n * 16, s)); BEM_TRY(dvec.alloc(n * 16, s));
+    BEM_TRY(rvec.alloc(n * 16, s)); BEM_TRY(tmp.alloc(n * 16, s));
     bem_status result = BEM_OK;
-    int last_iters = 0;
+    int total_inner = 0, outer_used = 0;
     double worst_res = 0.0;
     bool all_conv = true;
-    cudaEventRecord(t_sol.a, s);
     const unsigned eb = blocks_for(n, 256);
+    cudaEventRecord(t_sol.a, s);
     for (int rr = 0; rr < inc->n_rhs; ++rr) {
-        // right-hand side
         double3 d = make_double3(inc->dirs[3 * rr], inc->dirs[3 * rr + 1], inc->dirs[3 * rr + 2]);
         double2 amp = inc->amps ? make_double2(inc->amps[rr].re, inc->amps[rr].im) : make_double2(1.0, 0.0);
         BEM_CUDA_TRY(cudaMemsetAsync(fvec.p, 0, Ne * 16, s));
         BEM_CUDA_TRY(cudaMemsetAsync(gvec.p, 0, Ne * 16, s));
-        BEM_LAUNCH(k_plane_wave, blocks_for(ge->nt, 128), 128, 0, s, ge->rec.as<TriRec>(), ge->tri.as<int32_t>(), ge->nt,
-                                                            k_ext.re, k_ext.im, d, amp, fvec.as<double2>(),
-                                                            gvec.as<double2>());
-        BEM_CHECK_LAUNCH();
+        BEM_LAUNCH(k_plane_wave, blocks_for(ge->nt, 128), 128, 0, s, ge->rec.as<TriRec>(), ge->tri.as<int32_t>(),
+                   ge->nt, k_ext.re, k_ext.im, d, amp, fvec.as<double2>(), gvec.as<double2>());
         BEM_LAUNCH(k_rhs_pack, eb, 256, 0, s, fvec.as<double2>(), gvec.as<double2>(), Ne, n, bvec.as<double2>());
-        BEM_CHECK_LAUNCH();
-        // S b -> w
-        BEM_TRY(mass_solve(op, bvec.as<double2>(), w.as<double2>(), s));
-        // beta = ||S b||; V_0 = S b / beta; g = [beta, 0, ...]
-        BEM_CUDA_TRY(cudaMemsetAsync(H.p, 0, (size_t)ldh * (maxit + 1) * 16, s));
-        BEM_CUDA_TRY(cudaMemsetAsync(g.p, 0, (maxit + 2) * 16, s));
-        BEM_LAUNCH(k_dots_partial, dim3(RED_BLOCKS, 1), 256, 0, s, w.as<double2>(), n, ldv, w.as<double2>(),
-                                                           partial.as<double2>());
-        BEM_LAUNCH(k_dots_final, 1, 32, 0, s, partial.as<double2>(), 1, nrm.as<double2>(), 0);
-        BEM_LAUNCH(k_normalize, eb, 256, 0, s, w.as<double2>(), n, nrm.as<double2>(), Vp, g.as<double2>());
-        BEM_CHECK_LAUNCH();
-        BEM_CUDA_TRY(cudaMemcpyAsync(h_res, nrm.p, 8, cudaMemcpyDeviceToHost, s));
-        BEM_CUDA_TRY(cudaStreamSynchronize(s));
-        const double beta = std::sqrt(std::max(h_res[0], 0.0));
+        BEM_TRY(mass_solve(mop, bvec.as<double2>(), sb.as<double2>(), s));
+        double beta = 0.0;
+        BEM_TRY(norm2(W, sb.as<double2>(), &beta, s));
+        const double tol_abs = o->gmres_tol * beta;
         int iters = 0;
-        double resid = beta;
-        if (beta > 0.0) {
-            for (int j = 0; j < maxit; ++j) {
-                double2* vj = Vp + (int64_t)j * ldv;
-                BEM_TRY(strong_apply(op, vj, w.as<double2>(), s));
-                double2* Hj = H.as<double2>() + (int64_t)j * ldh;
-                // CGS2
-                for (int pass = 0; pass < 2; ++pass) {
-                    BEM_LAUNCH(k_dots_partial, dim3(RED_BLOCKS, j + 1), 256, 0, s, Vp, n, ldv, w.as<double2>(),
-                                                                          partial.as<double2>());
-                    BEM_LAUNCH(k_dots_final, j + 1, 32, 0, s, partial.as<double2>(), j + 1,
-                                                      pass == 0 ? Hj : hbuf.as<double2>(), 0);
-                    BEM_LAUNCH(k_combine, eb, 256, 0, s, Vp, n, ldv, j + 1, pass == 0 ? Hj : hbuf.as<double2>(),
-                                                 w.as<double2>(), 0);
-                    BEM_CHECK_LAUNCH();
-                }
-                // H[:, j] += second-pass coefficients
-                BEM_LAUNCH(k_add, 1, 256, 0, s, Hj, hbuf.as<double2>(), j + 1);
-                BEM_CHECK_LAUNCH();
-                // norm and next basis vector
-                BEM_LAUNCH(k_dots_partial, dim3(RED_BLOCKS, 1), 256, 0, s, w.as<double2>(), n, ldv, w.as<double2>(),
-                                                                   partial.as<double2>());
-                BEM_LAUNCH(k_dots_final, 1, 32, 0, s, partial.as<double2>(), 1, nrm.as<double2>(), 0);
-                BEM_LAUNCH(k_normalize, eb, 256, 0, s, w.as<double2>(), n, nrm.as<double2>(), Vp + (int64_t)(j + 1) * ldv,
-                                               Hj + j + 1);
-                BEM_CHECK_LAUNCH();
-                BEM_LAUNCH(k_givens, 1, 32, 0, s, H.as<double2>(), ldh, j, cs.as<double>(), sn.as<double2>(),
-                                          g.as<double2>(), resd.as<double>());
-                BEM_CHECK_LAUNCH();
-                BEM_CUDA_TRY(cudaMemcpyAsync(h_res, resd.p, 8, cudaMemcpyDeviceToHost, s));
-                BEM_CUDA_TRY(cudaStreamSynchronize(s));
-                iters = j + 1;
-                resid = h_res[0];
-                if (!(resid > o->gmres_tol * beta)) break;
-            }
-        }
-        // x = V y
-        if (iters > 0) {
-            BEM_LAUNCH(k_backsolve, 1, 256, 0, s, H.as<double2>(), ldh, iters, g.as<double2>(), y.as<double2>(),
-                                          work.as<double2>());
-            BEM_LAUNCH(k_combine, eb, 256, 0, s, Vp, n, ldv, iters, y.as<double2>(), xsol.as<double2>(), 1);
-            BEM_CHECK_LAUNCH();
+        double rel = 0.0;
+        if (!mixed) {
+            double est = 0.0;
+            BEM_TRY(gmres_run(W, apply_work, sb.as<double2>(), beta, tol_abs, xsol.as<double2>(), &iters, &est, s));
+            rel = beta > 0.0 ? est / beta : 0.0;
+            total_inner += iters;
+            outer_used = 1;
         } else {
+            // iterative refinement: FP64 residual of the stored system, FP32-matvec GMRES corrections
             BEM_CUDA_TRY(cudaMemsetAsync(xsol.p, 0, n * 16, s));
+            BEM_CUDA_TRY(cudaMemcpyAsync(rvec.p, sb.p, n * 16, cudaMemcpyDeviceToDevice, s));
+            double rn = beta;
+            int outer = 0;
+            const int max_outer = 12;
+            while (beta > 0.0 && rn > tol_abs && outer < max_outer && total_inner < o->gmres_maxiter) {
+                const double inner_tol = std::max(tol_abs, o->ir_inner_tol * rn);
+                int it = 0;
+                double est = 0.0;
+                BEM_TRY(gmres_run(W, apply_work, rvec.as<double2>(), rn, inner_tol, dvec.as<double2>(), &it, &est, s));
+                iters += it;
+                total_inner += it;
+                BEM_LAUNCH(k_acc, eb, 256, 0, s, xsol.as<double2>(), dvec.as<double2>(), n);
+                BEM_TRY(apply_fp64(xsol.as<double2>(), tmp.as<double2>()));
+                BEM_LAUNCH(k_sub, eb, 256, 0, s, sb.as<double2>(), tmp.as<double2>(), n, rvec.as<double2>());
+                BEM_TRY(norm2(W, rvec.as<double2>(), &rn, s));
+                ++outer;
+                if (it == 0) break;
+            }
+            outer_used = std::max(outer_used, outer);
+            rel = beta > 0.0 ? rn / beta : 0.0;
         }
-        const double rel = beta > 0.0 ? resid / beta : 0.0;
         const bool conv = beta == 0.0 || rel <= o->gmres_tol;
         all_conv = all_conv && conv;
         worst_res = std::max(worst_res, rel);
-        last_iters = iters;
         if (!conv) result = BEM_E_NOT_CONVERGED;
-        // outputs
         const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         const double2* X = xsol.as<double2>();
         BEM_CUDA_TRY(cudaMemcpyAsync(v_ext + rr * Ne, X, Ne * 16, kind, s));
         BEM_CUDA_TRY(cudaMemcpyAsync(w_ext + rr * Ne, X + Ne, Ne * 16, kind, s));
         BEM_CUDA_TRY(cudaMemcpyAsync(v_int + rr * Ni, X + 2 * Ne, Ni * 16, kind, s));
         BEM_CUDA_TRY(cudaMemcpyAsync(w_int + rr * Ni, X + 2 * Ne + Ni, Ni * 16, kind, s));
+        (void)iters;
     }
     cudaEventRecord(t_sol.b, s);
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
     if (result == BEM_E_NOT_CONVERGED)
         set_error("GMRES did not reach the tolerance within gmres_maxiter iterations; outputs hold the last iterate");
     if (rep) {
-        rep->iterations = last_iters;
+        rep->iterations = total_inner;
         rep->converged = all_conv ? 1 : 0;
         rep->residual = worst_res;
         rep->t_assembly_ms = t_asm.ms();
         rep->t_mortar_ms = t_mor.ms();
         rep->t_solve_ms = t_sol.ms();
         rep->mtf_variant = o->mtf_variant;
-        rep->reserved = 0;
+        rep->outer_iterations = outer_used;
     }
     return result;
 }

@@ -1,0 +1,124 @@
+"""Mixed-precision mode (BEM_PREC_MIXED): FP32 regular-pair assembly into complex64
+operators, FP64 singular pairs / mass / mortar, FP32-matvec GMRES inside FP64
+iterative refinement.
+
+Stated tolerances: operator blocks within relative Frobenius 1e-6 of the FP64
+oracle (the FP32 storage rounding is 6e-8); traces within relative L2 1e-6 of the
+FP64 oracle, or of the FP64 GPU path where the oracle is too slow (that path matches
+the oracle to 1e-10 in test_gpu_parity.py)."""
+import numpy as np
+import pytest
+
+import bem_inputs as bi
+
+pytestmark = pytest.mark.gpu
+
+OP_TOL = 1e-6
+TRACE_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2206_00708_gb300 as bem
+    ctx = bem.bem_context_create(0)
+    yield bem, ctx
+    bem.bem_context_destroy(ctx)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def mixed_ops(bem, ctx, v, t, k):
+    g = bem.bem_grid_create(ctx, v, t)
+    out = {}
+    for name, op in (("V", bem.BEM_OP_V), ("K", bem.BEM_OP_K), ("T", bem.BEM_OP_T), ("D", bem.BEM_OP_D)):
+        m = bem.bem_assemble(ctx, op, k, g, precision=bem.BEM_PREC_MIXED)
+        assert bem.bem_matrix_entry_bytes(m) == 8
+        out[name] = bem.bem_matrix_copy_out(ctx, m).astype(np.complex128)
+        bem.bem_matrix_destroy(m)
+    bem.bem_grid_destroy(g)
+    return out
+
+
+@pytest.mark.parametrize("case", ["sphere-L1", "ellipsoid-L2-complex-k", "sphere-L3-k8"])
+def test_mixed_operators_match_oracle(env, case):
+    from oracle.helmholtz import assemble
+    bem, ctx = env
+    if case == "sphere-L1":
+        v, t = bi.icosphere(1)
+        k = 1.0
+    elif case == "ellipsoid-L2-complex-k":
+        _, _, v, t = bi.transmission_pair(2, 2, seed=3, axes=[1.3, 0.8, 1.1])
+        k = 3.0 + 0.5j
+    else:
+        v, t = bi.icosphere(3)
+        k = 8.0
+    rows = None if len(v) < 200 else np.random.default_rng(0).choice(len(v), 24, replace=False)
+    got = mixed_ops(bem, ctx, v, t, k)
+    ref = assemble(v, t, k, rows=rows)
+    for op in "VKTD":
+        g = got[op] if rows is None else got[op][rows]
+        e = rel(g, ref[op])
+        print(case, op, e)
+        assert e < OP_TOL, (case, op, e)
+
+
+@pytest.mark.parametrize("k", [10.0, 15.0])
+def test_mixed_operators_full_size_sampled_rows(env, k):
+    from oracle.helmholtz import assemble
+    bem, ctx = env
+    v, t = bi.icosphere(5)
+    if k == 15.0:
+        v = bi.rotate_and_jitter(v, t, seed=2)
+    rows = np.random.default_rng(1).choice(len(v), 4, replace=False)
+    ref = assemble(v, t, k, rows=rows)
+    g = bem.bem_grid_create(ctx, v, t)
+    for name, op in (("V", bem.BEM_OP_V), ("K", bem.BEM_OP_K), ("D", bem.BEM_OP_D)):
+        m = bem.bem_assemble(ctx, op, k, g, precision=bem.BEM_PREC_MIXED)
+        full = bem.bem_matrix_copy_out(ctx, m)
+        bem.bem_matrix_destroy(m)
+        e = rel(full[rows].astype(np.complex128), ref[name])
+        print("L5", k, name, e)
+        assert e < OP_TOL, (name, e)
+        del full
+    bem.bem_grid_destroy(g)
+
+
+def _solve(bem, ctx, ve, te, vi, ti, k_int, k_ext, rho, dirs, **opts):
+    ge = bem.bem_grid_create(ctx, ve, te)
+    gi = bem.bem_grid_create(ctx, vi, ti)
+    try:
+        return bem.bem_solve_transmission(ctx, ge, gi, k_int, k_ext, rho, dirs, opts=opts)
+    finally:
+        bem.bem_grid_destroy(ge)
+        bem.bem_grid_destroy(gi)
+
+
+def test_mixed_solve_matches_fp64_oracle_small(env):
+    from oracle.mtf import solve_transmission
+    bem, ctx = env
+    ve, te, vi, ti = bi.transmission_pair(2, 2, seed=1)
+    d = np.array([[0.0, 0.0, 1.0]])
+    out, rep = _solve(bem, ctx, ve, te, vi, ti, 2.0, 1.0, 1.0, d, gmres_tol=1e-10, precision=bem.BEM_PREC_MIXED)
+    ref = solve_transmission(ve, te, vi, ti, 1.0, 2.0, 1.0, d[0], tol=1e-12)
+    for key in ("v_ext", "w_ext", "v_int", "w_int"):
+        e = rel(out[key][0], ref[key])
+        print(key, e, rep)
+        assert e < TRACE_TOL, (key, e)
+    assert rep["converged"] == 1 and rep["outer_iterations"] >= 1
+
+
+def test_mixed_solve_matches_fp64_gpu_at_level4(env):
+    """Level-4 grids, k 10 / 15, density ratio 2 (the at-scale wavenumbers)."""
+    bem, ctx = env
+    ve, te, vi, ti = bi.transmission_pair(4, 4, seed=2)
+    d = np.array([[0.0, 0.0, 1.0]])
+    ref, r64 = _solve(bem, ctx, ve, te, vi, ti, 15.0, 10.0, 2.0, d, gmres_tol=1e-10)
+    out, rmx = _solve(bem, ctx, ve, te, vi, ti, 15.0, 10.0, 2.0, d, gmres_tol=1e-10, precision=bem.BEM_PREC_MIXED)
+    errs = {key: rel(out[key][0], ref[key][0]) for key in ("v_ext", "w_ext", "v_int", "w_int")}
+    print(errs, r64, rmx)
+    assert max(errs.values()) < TRACE_TOL, errs
