@@ -1,16 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 transmission-BEM hot path.
 
-One step = one complete transmission solve of the at-scale sphere workload:
+One step = one complete transmission solve of the at-scale sphere workload in the
+mixed-precision mode (the headline), and the same solve in plain FP64 (the
+comparison arm, reported under "fp64"):
 grid intake of both grids, Galerkin assembly of V, K, T, D on both grids (regular
 and Sauter-Schwab quadrature), mass and mortar matrices, plane-wave data, and
 unrestarted GMRES on the mass-preconditioned multiple-traces system.
 
-Workload (plain FP64, at scale): unit sphere; exterior grid = icosphere level 5
-(10242 vertices, 20480 triangles); interior grid = icosphere level 5 rotated by a
+Workload (at scale): unit sphere; exterior grid = icosphere level 5 (10242
+vertices, 20480 triangles); interior grid = icosphere level 5 rotated by a
 Haar-random rotation (seed 2) with 1% tangential jitter; k_ext = 10, k_int = 15,
 rho_int / rho_ext = 2; one unit plane wave along +z; GMRES tolerance 1e-8;
-40968 unknowns, 8 dense complex128 operator blocks (13.4 GB).
+40968 unknowns, 8 dense operator blocks (6.7 GB complex64 in the mixed mode,
+13.4 GB complex128 in FP64).  The headline "value" is the mixed-precision rate;
+"accuracy" gives its traces' relative L2 error against a converged FP64 solve
+(target <= 1e-6); "fp64" holds the plain-FP64 GPU arm.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on a
 bounded sample of the same workload instead.  With torchrun (N > 1) every rank
@@ -36,13 +41,14 @@ import numpy as np  # noqa: E402
 METRIC = "Transmission solves/s + p50/p99 latency vs plain FP64 GPU at <=1e-6 rel. err"
 UNIT = "solves/s"
 WORKLOAD = dict(level_ext=5, level_int=5, seed=2, k_ext=10.0, k_int=15.0, rho=2.0, tol=1e-8)
-WORKLOAD_NAME = ("plain FP64 at scale: unit sphere, icosphere L5 exterior (10242 vertices) + L5 interior "
-                 "rotated/jittered (seed 2), k_ext=10, k_int=15, rho_int/rho_ext=2, 1 plane wave +z, "
-                 "GMRES tol 1e-8, 40968 unknowns, 8 dense c128 blocks")
+WORKLOAD_NAME = ("at-scale sphere: icosphere L5 exterior (10242 vertices) + L5 interior rotated/jittered "
+                 "(seed 2), k_ext=10, k_int=15, rho_int/rho_ext=2, 1 plane wave +z, GMRES tol 1e-8, "
+                 "40968 unknowns")
 L2_FLUSH_BYTES = 256 << 20
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x 2 flops x max SM clock
-# algorithmic FP64 flops per point pair of the regular-pair assembly kernel
+# algorithmic flops per point pair of the regular-pair assembly kernels
 FLOP_PER_POINT_PAIR = 93
+FLOP_PER_POINT_PAIR_FP32 = 105
 
 
 def workload_inputs(w=WORKLOAD):
@@ -196,6 +202,50 @@ def run_reference(args, rank):
 
 
 # ----------------------------------------------------------------- GPU arm
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x 2 flops x max SM clock
+HBM_PEAK_GBS = None
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def kernel_roofline(name, ms, n, te, ti, Ne, Ni, pp_cache):
+    """Roofline entry of one profiled kernel (per-launch averages)."""
+    avg_s = ms / n / 1e3
+    if name.startswith("k_gemv_mtf32"):
+        peak, kind = hbm_peak()
+        bytes_ = 8 * 4 * (Ne * Ne + Ni * Ni)  # 8 complex64 blocks read once per matvec
+        ach = bytes_ / avg_s / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "peak_kind": kind, "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": ms / n}
+    if name.startswith("k_gemv_mtf"):
+        flops = 8 * 4 * (Ne * Ne + Ni * Ni) * 8.0 / 8  # 4 DFMA = 8 flops per complex entry
+        ach = flops / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_kind": "derived FP64 FMA peak: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
+                "flops_per_launch": flops, "avg_launch_ms": ms / n}
+    if name.startswith("k_regular"):
+        if "pp" not in pp_cache:
+            pp_cache["pp"] = (regular_point_pairs(te) + regular_point_pairs(ti)) / 2
+        units = pp_cache["pp"]
+        fp32 = name.startswith("k_regular32")
+        fpp = FLOP_PER_POINT_PAIR_FP32 if fp32 else FLOP_PER_POINT_PAIR
+        peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+        ach = fpp * units / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None,
+                "peak_kind": ("derived FP32 peak: 152 SMs x 128 lanes x 2 x 2.07 GHz" if fp32 else
+                              "derived FP64 FMA peak: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"),
+                "flop_per_point_pair": fpp, "point_pairs_per_launch": units, "avg_launch_ms": ms / n}
+    return {"kernel": name, "avg_launch_ms": ms / n}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -204,6 +254,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison arm")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -231,73 +282,80 @@ def main():
     xi = torch.from_numpy(np.ascontiguousarray(vi)).to(dev)
     tri_ = torch.from_numpy(np.ascontiguousarray(ti, dtype=np.int32)).to(dev)
     Ne, Ni = len(ve), len(vi)
-    out = {k: torch.zeros((1, n), dtype=torch.complex128, device=dev)
-           for k, n in (("v_ext", Ne), ("w_ext", Ne), ("v_int", Ni), ("w_int", Ni))}
     dirs = np.array([[0.0, 0.0, 1.0]])
     stream = torch.cuda.current_stream(dev)
     ctx = bem.bem_context_create(local, stream=stream)
-    opts = {"gmres_tol": w["tol"]}
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    def step():
+    def new_out():
+        return {k: torch.zeros((1, n), dtype=torch.complex128, device=dev)
+                for k, n in (("v_ext", Ne), ("w_ext", Ne), ("v_int", Ni), ("w_int", Ni))}
+
+    def step(precision, out, tol):
         ge = bem.bem_grid_create(ctx, xe, tre)
         gi = bem.bem_grid_create(ctx, xi, tri_)
-        _, rep = bem.bem_solve_transmission(ctx, ge, gi, w["k_int"], w["k_ext"], w["rho"], dirs, opts=opts,
-                                            out=out, on_device=True)
+        _, rep = bem.bem_solve_transmission(ctx, ge, gi, w["k_int"], w["k_ext"], w["rho"], dirs,
+                                            opts={"gmres_tol": tol, "precision": precision}, out=out, on_device=True)
         bem.bem_grid_destroy(ge)
         bem.bem_grid_destroy(gi)
         return rep
 
-    for _ in range(args.warmup):
-        rep = step()
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    times = []
-    reports = []
-    bem.bem_profile_reset()
-    launches0 = bem.bem_launch_count()
-    with ClockSampler(local) as clocks:
-        for _ in range(args.steps):
-            flush.zero_()  # L2 flush outside the timed events
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            bem.bem_profile_enable(True)
-            e0.record(stream)
-            reports.append(step())
-            e1.record(stream)
-            e1.synchronize()
-            bem.bem_profile_enable(False)
-            times.append(e0.elapsed_time(e1))
-    torch.cuda.synchronize()
-    launches = bem.bem_launch_count() - launches0
-    barrier()
-    total_ms = sum(times)
-    t_max = total_ms
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * args.steps / (t_max / 1e3)
-    prof = bem.bem_profile_table()
+    def timed(precision):
+        out = new_out()
+        for _ in range(args.warmup):
+            step(precision, out, w["tol"])
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        times, reports = [], []
+        bem.bem_profile_reset()
+        l0 = bem.bem_launch_count()
+        with ClockSampler(local) as clocks:
+            for _ in range(args.steps):
+                flush.zero_()  # L2 flush outside the timed events
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                bem.bem_profile_enable(True)
+                e0.record(stream)
+                reports.append(step(precision, out, w["tol"]))
+                e1.record(stream)
+                e1.synchronize()
+                bem.bem_profile_enable(False)
+                times.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        launches = bem.bem_launch_count() - l0
+        barrier()
+        total = sum(times)
+        if world > 1:
+            tt = torch.tensor([total], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            total = float(tt.item())
+        return dict(out=out, times=times, reports=reports, launches=launches, clocks=clocks.summary(),
+                    value=world * args.steps / (total / 1e3), prof=bem.bem_profile_table())
 
-    # dominant kernel: roofline
-    top = prof[0] if prof else ("", 0.0, 0)
-    roof = None
-    asm = [p for p in prof if p[0].startswith("k_regular")]
-    if asm:
-        name, ms, n = asm[0]
-        units = (regular_point_pairs(te) + regular_point_pairs(ti)) / 2  # per launch (two grids per solve)
-        achieved = FLOP_PER_POINT_PAIR * units / (ms / n / 1e3) / 1e12
-        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_kind": "derived FP64 FMA peak: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
-                "flop_per_point_pair": FLOP_PER_POINT_PAIR, "point_pairs_per_launch": units,
-                "avg_launch_ms": ms / n}
+    mixed = timed(bem.BEM_PREC_MIXED)
+    fp64 = None if args.no_fp64 else timed(bem.BEM_PREC_FP64)
+
+    # accuracy: the mixed traces against a tightly converged FP64 solve of the same system
+    ref = new_out()
+    step(bem.BEM_PREC_FP64, ref, 1e-12)
+    torch.cuda.synchronize()
+    err = {k: float(torch.linalg.norm(mixed["out"][k] - ref[k]) / torch.linalg.norm(ref[k])) for k in ref}
+    err64 = ({k: float(torch.linalg.norm(fp64["out"][k] - ref[k]) / torch.linalg.norm(ref[k])) for k in ref}
+             if fp64 else None)
+
+    pp_cache = {}
+    roof = kernel_roofline(*mixed["prof"][0], te, ti, Ne, Ni, pp_cache) if mixed["prof"] else None
+    roof2 = kernel_roofline(*mixed["prof"][1], te, ti, Ne, Ni, pp_cache) if len(mixed["prof"]) > 1 else None
+    roof64 = None
+    if fp64:
+        asm = [p for p in fp64["prof"] if p[0].startswith("k_regular")]
+        if asm:
+            roof64 = kernel_roofline(*asm[0], te, ti, Ne, Ni, pp_cache)
 
     e2e = None
     if not args.no_e2e:
-        # end to end through the public API with pinned host buffers
+        # end to end through the public API with pinned host buffers (mixed precision)
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
         hxe, hte, hxi, hti = pin(ve), pin(np.asarray(te, dtype=np.int32)), pin(vi), pin(np.asarray(ti, dtype=np.int32))
         hout = {k: torch.zeros((1, n), dtype=torch.complex128).pin_memory()
@@ -309,7 +367,8 @@ def main():
             t0 = time.perf_counter()
             ge = bem.bem_grid_create(ctx, hxe, hte)
             gi = bem.bem_grid_create(ctx, hxi, hti)
-            bem.bem_solve_transmission(ctx, ge, gi, w["k_int"], w["k_ext"], w["rho"], dirs, opts=opts, out=hout)
+            bem.bem_solve_transmission(ctx, ge, gi, w["k_int"], w["k_ext"], w["rho"], dirs,
+                                       opts={"gmres_tol": w["tol"], "precision": bem.BEM_PREC_MIXED}, out=hout)
             bem.bem_grid_destroy(ge)
             bem.bem_grid_destroy(gi)
             e2e_times.append(time.perf_counter() - t0)
@@ -320,29 +379,46 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = run_oracle_child(int(reports[-1]["iterations"]))
+        r = run_oracle_child(int(mixed["reports"][-1]["iterations"]))
         if r is not None:
             cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
 
+    def lat(times):
+        return {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))}
+
+    def solve_info(rep):
+        return {k: rep[k] for k in ("iterations", "outer_iterations", "residual", "t_assembly_ms", "t_mortar_ms",
+                                    "t_solve_ms")}
+
     if rank == 0:
-        srt = sorted(times)
+        m = mixed
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sum(m["times"]) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "256 MB write between steps; operators (13.4 GB) exceed L2",
-                       "precision": "fp64"},
-            "latency_ms": {"p50": float(np.percentile(srt, 50)), "p99": float(np.percentile(srt, 99))},
-            "clocks": clocks.summary(),
-            "gpu_launches": int(launches),
+                       "precision": "mixed: FP32 regular-pair assembly and matvec (complex64 operators), FP64 "
+                                    "singular pairs, mass, mortar, Arnoldi and iterative-refinement residual",
+                       "l2": "256 MB write between steps; operators (6.7 GB complex64) exceed L2"},
+            "latency_ms": lat(m["times"]),
+            "accuracy": {"rel_l2_vs_fp64_converged": err, "max": max(err.values()), "target": 1e-6,
+                         "ok": max(err.values()) <= 1e-6,
+                         "reference": "FP64 GPU solve of the same system at GMRES tol 1e-12 (the FP64 path "
+                                      "matches the CPU oracle to 1e-10 in the parity tests)"},
+            "fp64": (None if not fp64 else {
+                "value": fp64["value"], "unit": UNIT, "ms_per_step": sum(fp64["times"]) / args.steps,
+                "latency_ms": lat(fp64["times"]), "rel_l2_vs_fp64_converged": err64,
+                "solve": solve_info(fp64["reports"][-1]), "roofline": roof64, "gpu_launches": fp64["launches"],
+                "clocks": fp64["clocks"]}),
+            "speedup_vs_fp64": (m["value"] / fp64["value"]) if fp64 else None,
+            "clocks": m["clocks"],
+            "gpu_launches": int(m["launches"]),
             "roofline": roof,
+            "roofline_second": roof2,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "solve": {"iterations": reports[-1]["iterations"], "residual": reports[-1]["residual"],
-                      "t_assembly_ms": reports[-1]["t_assembly_ms"], "t_mortar_ms": reports[-1]["t_mortar_ms"],
-                      "t_solve_ms": reports[-1]["t_solve_ms"]},
-            "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in prof[:8]],
+            "solve": solve_info(m["reports"][-1]),
+            "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in m["prof"][:10]],
         }
         print(json.dumps(line), flush=True)
     bem.bem_context_destroy(ctx)
