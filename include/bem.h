@@ -86,6 +86,12 @@ BEM_API const char* bem_version(void);
  * contexts and threads; a monotone counter for profiling and accounting). */
 BEM_API uint64_t bem_launch_count(void);
 
+/* Accuracy self-tests of device arithmetic written for this library (no
+ * counterpart in the paper).  which = 0: largest absolute difference between the
+ * FP32 assembly kernel's sin/cos (Cody-Waite reduction + Taylor series) and CUDA's
+ * sincosf on 2^20 evenly spaced arguments in [-64, 64]. */
+BEM_API bem_status bem_selftest(bem_context* ctx, int which, double* result);
+
 /* Per-kernel device timing.  While enabled, each launch of the library is
  * bracketed by CUDA events on its own stream; totals accumulate per kernel
  * name.  bem_profile_count() returns the number of kernel names seen and

@@ -82,6 +82,7 @@ _SIGNATURES = {
     "bem_last_error": (C.c_char_p, []),
     "bem_version": (C.c_char_p, []),
     "bem_launch_count": (C.c_uint64, []),
+    "bem_selftest": (C.c_int32, [_VP, C.c_int, C.POINTER(C.c_double)]),
     "bem_profile_enable": (None, [C.c_int]),
     "bem_profile_reset": (None, []),
     "bem_profile_count": (C.c_int, []),
@@ -166,6 +167,12 @@ def bem_version():
 
 def bem_launch_count():
     return int(_lib.bem_launch_count())
+
+
+def bem_selftest(ctx, which=0):
+    r = C.c_double()
+    _check(_lib.bem_selftest(ctx, int(which), C.byref(r)))
+    return r.value
 
 
 def bem_profile_enable(on=True):

@@ -19,6 +19,8 @@
 // The tile buffers are flushed to the global matrices with vector float2 atomics.
 #include "bem_internal.cuh"
 
+#include <algorithm>
+
 namespace bem {
 
 namespace {
@@ -46,6 +48,33 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
 __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
     p = a * b;
     e = fmaf(a, b, -p);
+}
+
+// sin and cos of a moderate FP32 argument (|x| < 2^15): Cody-Waite reduction by
+// pi/2 with a three-part constant (the first part has 8 significant bits, so n * P1 is
+// exact), then the Taylor series of sin and cos on |r| <= pi/4 (truncation below
+// 2e-9), evaluated by Horner's rule in r^2; the quadrant selects signs and swaps.
+__device__ __forceinline__ void sincos_moderate(float x, float* s, float* c) {
+    const float n = rintf(x * 0.636619772367581343f);  // 2 / pi
+    float r = fmaf(-n, 1.5703125f, x);                  // pi/2 = P1 + P2 + P3
+    r = fmaf(-n, 4.838267923332751e-4f, r);
+    r = fmaf(-n, 2.5632829192545614e-12f, r);
+    const float r2 = r * r;
+    // sin r = r (1 - r^2/3! + r^4/5! - r^6/7! + r^8/9!)
+    float ps = fmaf(r2, 2.75573192239858907e-6f, -1.98412698412698413e-4f);
+    ps = fmaf(r2, ps, 8.33333333333333333e-3f);
+    ps = fmaf(r2, ps, -1.66666666666666667e-1f);
+    const float sr = fmaf(r * r2, ps, r);
+    // cos r = 1 - r^2/2! + r^4/4! - r^6/6! + r^8/8! - r^10/10!
+    float pc = fmaf(r2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);
+    pc = fmaf(r2, pc, -1.38888888888888889e-3f);
+    pc = fmaf(r2, pc, 4.16666666666666667e-2f);
+    pc = fmaf(r2, pc, -0.5f);
+    const float cr = fmaf(r2, pc, 1.0f);
+    const int q = ((int)n) & 3;
+    const float ss = (q & 1) ? cr : sr, cc = (q & 1) ? sr : cr;
+    *s = (q & 2) ? -ss : ss;
+    *c = ((q + 1) & 2) ? -cc : cc;
 }
 
 struct TrialTile32 {
@@ -188,9 +217,9 @@ k_regular32(const TriRec32* __restrict__ rec, const int32_t* __restrict__ tverts
                     const float r2 = R2f + num;
                     const float rinv = rsqrtf(r2);
                     const float r = r2 * rinv;
-                    const float delta = num / (r + Rh);
+                    const float delta = __fdividef(num, r + Rh);
                     float sd, cd;
-                    sincosf(P.k_h * delta, &sd, &cd);
+                    sincos_moderate(P.k_h * delta, &sd, &cd);
                     float g = rinv * INV_4PI_F;
                     if (CK) g *= __expf(-P.k_i * delta);
                     // G = g exp(i k R) exp(i k delta)
@@ -280,7 +309,32 @@ k_regular32(const TriRec32* __restrict__ rec, const int32_t* __restrict__ tverts
     }
 }
 
+__global__ void k_sincos_check(int n, float xmax, float* __restrict__ err) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float x = -xmax + 2.0f * xmax * ((float)i + 0.5f) / (float)n;
+    float s0, c0, s1, c1;
+    sincosf(x, &s0, &c0);
+    sincos_moderate(x, &s1, &c1);
+    err[i] = fmaxf(fabsf(s1 - s0), fabsf(c1 - c0));
+}
+
 }  // namespace
+
+// Largest absolute difference between sincos_moderate and CUDA's sincosf on n
+// evenly spaced arguments in [-xmax, xmax].
+bem_status selftest_sincos(int n, float xmax, double* max_err, cudaStream_t s) {
+    DevBuf e;
+    BEM_TRY(e.alloc((size_t)n * 4, s));
+    BEM_LAUNCH(k_sincos_check, (unsigned)((n + 255) / 256), 256, 0, s, n, xmax, e.as<float>());
+    std::vector<float> h(n);
+    BEM_CUDA_TRY(cudaMemcpyAsync(h.data(), e.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    double m = 0.0;
+    for (float v : h) m = std::max(m, (double)v);
+    *max_err = m;
+    return BEM_OK;
+}
 
 bem_status assemble_regular_fp32(const bem_grid* g, double k_re, double k_im, float2* V, float2* K, float2* T,
                                  float2* D, cudaStream_t s) {

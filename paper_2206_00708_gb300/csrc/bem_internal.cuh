@@ -193,6 +193,8 @@ bem_status grid_build_rec32(const bem_grid* g, cudaStream_t s);
 // assemble32.cu: regular pairs in FP32 into complex64 V, K, T, D (row-major, zeroed by the caller)
 bem_status assemble_regular_fp32(const bem_grid* g, double k_re, double k_im, float2* V, float2* K, float2* T,
                                  float2* D, cudaStream_t s);
+// assemble32.cu: accuracy self-test of the FP32 kernel's sincos against CUDA's sincosf
+bem_status selftest_sincos(int n, float xmax, double* max_err, cudaStream_t s);
 // assemble.cu: singular pairs (FP64 quadrature) added into complex64 matrices
 bem_status assemble_singular_into_c64(const bem_grid* g, double k_re, double k_im, int n_singular, float2* V,
                                       float2* K, float2* T, float2* D, cudaStream_t s);

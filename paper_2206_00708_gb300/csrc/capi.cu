@@ -68,6 +68,13 @@ const char* bem_version(void) { return "bem-gb300 0.1 (sm_103a)"; }
 
 uint64_t bem_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+bem_status bem_selftest(bem_context* ctx, int which, double* result) {
+    CTX_GUARD(ctx);
+    BEM_REQUIRE(result != nullptr, "null result");
+    BEM_REQUIRE(which == 0, "unknown self-test");
+    return selftest_sincos(1 << 20, 64.0f, result, ctx->stream);
+}
+
 bem_status bem_context_create(int device, void* stream, bem_context** out) {
     BEM_REQUIRE(out != nullptr, "out is null");
     *out = nullptr;

@@ -30,7 +30,8 @@ namespace bem {
 
 namespace {
 
-constexpr int CHEB_STEPS = 34;
+constexpr int CHEB_STEPS = 34;        // error <= 2 * 3^-34 ~ 1e-16: FP64 applications
+constexpr int CHEB_STEPS_INNER = 17;  // error <= 2 * 3^-17 ~ 1.6e-8: inner solves of the refinement
 constexpr double CHEB_ALPHA = 0.5, CHEB_BETA = 2.0;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -488,14 +489,14 @@ struct TransferOp {
 };
 
 // M^-1 (z) -> y on the four blocks, Chebyshev on the Jacobi-scaled mass matrices
-bem_status mass_solve(const MassOp& op, const double2* z, double2* y, cudaStream_t s) {
+bem_status mass_solve(const MassOp& op, const double2* z, double2* y, cudaStream_t s, int steps = CHEB_STEPS) {
     const int64_t n = op.M.n;
     const double theta = 0.5 * (CHEB_BETA + CHEB_ALPHA), delta = 0.5 * (CHEB_BETA - CHEB_ALPHA);
     const double sigma = theta / delta;
     BEM_LAUNCH(k_cheb_init, blocks_for(n, 256), 256, 0, s, op.M, z, y, op.r, op.dA, 1.0 / theta);
     double rho = 1.0 / sigma;
     double2 *dk = op.dA, *dn = op.dB;
-    for (int k = 0; k < CHEB_STEPS; ++k) {
+    for (int k = 0; k < steps; ++k) {
         const double rho_n = 1.0 / (2.0 * sigma - rho);
         BEM_LAUNCH(k_cheb_step, blocks_for(n, 256), 256, 0, s, op.M, dk, dn, y, op.r, rho_n * rho, 2.0 * rho_n / delta);
         rho = rho_n;
@@ -719,7 +720,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
             BEM_LAUNCH(k_gemv_mtf, blocks_for(n * 32, 256), 256, 0, s, B64, n, xin, z);
         }
         BEM_TRY(transfer_add(top, Ne, Ni, xin, z, s));
-        return mass_solve(mop, z, yout, s);
+        return mass_solve(mop, z, yout, s, mixed ? CHEB_STEPS_INNER : CHEB_STEPS);
     };
     // S A x with FP64 arithmetic on the stored matrices (outer residual of the refinement)
     Apply apply_fp64 = [&](const double2* xin, double2* yout) -> bem_status {

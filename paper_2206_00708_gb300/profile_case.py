@@ -25,6 +25,7 @@ def main(argv=None):
     ap.add_argument("--level", type=int, default=4)
     ap.add_argument("--k", type=float, default=10.0)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--mixed", action="store_true", help="BEM_PREC_MIXED instead of FP64")
     a = ap.parse_args(argv)
     import bem_inputs as bi
     import paper_2206_00708_gb300 as bem
@@ -35,14 +36,16 @@ def main(argv=None):
     gi = bem.bem_grid_create(ctx, vi, ti)
     for _ in range(a.repeat):
         if a.case == "assemble":
-            m = bem.bem_assemble(ctx, bem.BEM_OP_V, a.k, ge)
+            m = bem.bem_assemble(ctx, bem.BEM_OP_V, a.k, ge,
+                                 precision=bem.BEM_PREC_MIXED if a.mixed else bem.BEM_PREC_FP64)
             bem.bem_context_synchronize(ctx)
             bem.bem_matrix_destroy(m)
         elif a.case == "mortar":
             s = bem.bem_projection(ctx, gi, ge)
             bem.bem_sparse_destroy(s)
         else:
-            out, rep = bem.bem_solve_transmission(ctx, ge, gi, 1.5 * a.k, a.k, 2.0, np.array([[0.0, 0.0, 1.0]]))
+            out, rep = bem.bem_solve_transmission(ctx, ge, gi, 1.5 * a.k, a.k, 2.0, np.array([[0.0, 0.0, 1.0]]),
+                                                  opts={"precision": 1 if a.mixed else 0})
             print("iterations", rep["iterations"])
     bem.bem_grid_destroy(ge)
     bem.bem_grid_destroy(gi)

@@ -32,6 +32,15 @@ def rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+def test_fp32_kernel_sincos_matches_cuda_sincosf(env):
+    """The FP32 assembly kernel's own sin/cos agrees with CUDA's sincosf to a few
+    FP32 units in the last place over [-64, 64]."""
+    bem, ctx = env
+    err = bem.bem_selftest(ctx, 0)
+    print("sincos max abs diff", err)
+    assert err < 4.8e-7  # 4 ulp of 1.0
+
+
 def mixed_ops(bem, ctx, v, t, k):
     g = bem.bem_grid_create(ctx, v, t)
     out = {}
