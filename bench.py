@@ -214,6 +214,51 @@ def hbm_peak():
         return 6800.0, "fallback 6.8 TB/s"
 
 
+def serving_stream(n, seed=50):
+    """First n requests of the seeded serving stream (ellipsoids, levels 2-4, random
+    wavenumbers, density ratios and 1-16 plane waves), grids built ahead of time."""
+    import bem_inputs as bi
+    reqs = bi.serving_requests(n, seed, rate=1.0)
+    out = []
+    for r in reqs:
+        ve, te, vi, ti = bi.transmission_pair(r["level_ext"], r["level_int"], r["seed"], axes=r["axes"])
+        out.append(dict(ve=ve, te=te, vi=vi, ti=ti, k_ext=r["k_ext"], k_int=r["k_int"], rho=r["rho_ratio"],
+                        dirs=r["dirs"], arrival=r["arrival"]))
+    return out
+
+
+def run_serving(bem, reqs, precision, rate=None, max_inflight=4):
+    """Submit the requests (all at once when rate is None, else at Poisson arrival
+    times scaled to `rate` per second); returns latencies (ms) and solves/s."""
+    srv = bem.bem_serve_create(max_inflight=max_inflight, precision=precision)
+    try:
+        t0 = time.perf_counter()
+        tickets = []
+        base = reqs[0]["arrival"]
+        for r in reqs:
+            if rate is not None:
+                due = t0 + (r["arrival"] - base) / rate
+                wait = due - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+            tickets.append(bem.bem_serve_submit(srv, r["ve"], r["te"], r["vi"], r["ti"], r["k_ext"], r["k_int"],
+                                                r["rho"], r["dirs"], precision=precision))
+        infos = []
+        for t in tickets:
+            bem.bem_serve_wait(srv, t, 0.0)
+            infos.append(bem.bem_serve_poll(srv, t))
+        wall = time.perf_counter() - t0
+        stats = bem.bem_serve_get_stats(srv)
+    finally:
+        bem.bem_serve_destroy(srv)
+    lat = np.array([i["total_ms"] for i in infos])
+    ok = sum(1 for i in infos if i["status"] == 0)
+    return {"requests": len(reqs), "ok": ok, "solves_per_s": len(reqs) / wall,
+            "rhs_per_s": sum(len(r["dirs"]) for r in reqs) / wall,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "wall_s": wall, "hbm_high_water_bytes": stats["hbm_high_water_bytes"]}
+
+
 def kernel_roofline(name, ms, n, te, ti, Ne, Ni, pp_cache):
     """Roofline entry of one profiled kernel (per-launch averages)."""
     avg_s = ms / n / 1e3
@@ -255,6 +300,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison arm")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the seeded serving stream to replay (0: skip serving)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -377,6 +424,18 @@ def main():
         e2e = {"value": world * args.steps / sum(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    serving = None
+    if args.serve_requests > 0:
+        reqs = serving_stream(args.serve_requests)
+        sat = {p: run_serving(bem, reqs, p) for p in (bem.BEM_PREC_FP64, bem.BEM_PREC_MIXED)}
+        rate = 0.7 * sat[bem.BEM_PREC_FP64]["solves_per_s"]
+        rep = {p: run_serving(bem, reqs, p, rate=rate) for p in (bem.BEM_PREC_FP64, bem.BEM_PREC_MIXED)}
+        serving = {"workload": f"first {len(reqs)} requests of the seeded serving stream (seed 50): ellipsoids "
+                               "with semi-axes U[0.5,1.5], icosphere levels 2-4 per grid, k_ext U[1,8], "
+                               "k_int/k_ext U[1.2,2], rho log-U[0.1,10], 1-16 plane waves; 4 requests in flight",
+                   "saturated": {"fp64": sat[bem.BEM_PREC_FP64], "mixed": sat[bem.BEM_PREC_MIXED]},
+                   "poisson": {"rate_per_s": rate, "fp64": rep[bem.BEM_PREC_FP64], "mixed": rep[bem.BEM_PREC_MIXED]}}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = run_oracle_child(int(mixed["reports"][-1]["iterations"]))
@@ -417,6 +476,7 @@ def main():
             "roofline_second": roof2,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "serving": serving,
             "solve": solve_info(m["reports"][-1]),
             "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in m["prof"][:10]],
         }

@@ -51,6 +51,7 @@ typedef int32_t bem_status;
 #define BEM_E_BUSY               -7  /* poll: the request is not finished yet              */
 #define BEM_E_CUDA               -8  /* a CUDA runtime call failed                         */
 #define BEM_E_INTERNAL           -9  /* an internal consistency check failed               */
+#define BEM_E_CANCELLED         -10  /* the request was cancelled                          */
 
 typedef struct { double re, im; } bem_c128;
 
@@ -243,6 +244,83 @@ BEM_API bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext,
                                   bem_c128* v_ext, bem_c128* w_ext,
                                   bem_c128* v_int, bem_c128* w_int,
                                   int on_device, bem_solve_report* rep);
+
+/* ---------------------------------------------------------------- serving
+ * A request server for streams of transmission solves (continuous batching):
+ * submitted requests wait in a FIFO queue; up to max_inflight of them run at once,
+ * each on its own CUDA stream, so the GPU work of different requests overlaps.  A
+ * request is admitted when a slot is free and its device working set (operators,
+ * Krylov basis, workspaces; an upper estimate) fits in what is left of the HBM
+ * budget; requests that could never fit are refused at submission.  The head of
+ * the queue is never overtaken, so no request starves.  The server is thread-safe.
+ * dry_run = 1 runs the scheduler without any GPU work (each request "runs" for
+ * dry_run_us_per_unknown microseconds per unknown and returns zeros): this is the
+ * host-side mode used to test admission, ordering, timeouts and cancellation.   */
+typedef struct bem_server bem_server;
+
+typedef struct {
+    int32_t device;                 /* CUDA device (ignored in dry-run mode)                 */
+    int32_t max_inflight;           /* concurrent requests, one stream each (default 4)      */
+    int64_t hbm_budget_bytes;       /* 0: 80% of the free device memory at creation          */
+    int32_t precision;              /* default precision of requests (BEM_PREC_MIXED)        */
+    int32_t gmres_maxiter;          /* default 2000                                          */
+    double  gmres_tol;              /* default 1e-8                                          */
+    int32_t dry_run;                /* 1: no GPU work (scheduler tests)                      */
+    int32_t reserved;
+    double  dry_run_us_per_unknown; /* dry-run service time per unknown (default 1 us)       */
+} bem_server_opts;
+
+typedef struct {
+    const double*  xyz_ext; int64_t nv_ext; const int32_t* tri_ext; int64_t nt_ext;  /* host */
+    const double*  xyz_int; int64_t nv_int; const int32_t* tri_int; int64_t nt_int;  /* host */
+    bem_c128 k_ext, k_int;
+    double   rho_int_over_rho_ext;
+    int32_t  n_rhs;
+    int32_t  precision;             /* BEM_PREC_*, or -1 for the server default              */
+    const double*   dirs;           /* [n_rhs*3] unit vectors (host)                         */
+    const bem_c128* amps;           /* [n_rhs] or NULL                                       */
+    double   timeout_ms;            /* 0: none; counted from submission                      */
+} bem_request;
+
+typedef struct {
+    int32_t status;                 /* outcome: BEM_OK, BEM_E_NOT_CONVERGED, BEM_E_TIMEOUT,
+                                       BEM_E_CANCELLED, BEM_E_CUDA, ...                      */
+    int32_t iterations;
+    double  residual;
+    double  queue_ms, run_ms, total_ms;  /* submit->start, start->finish, submit->finish     */
+    int64_t nv_ext, nv_int;
+    int32_t n_rhs, precision;
+    int64_t bytes_reserved;         /* admission estimate charged to the budget              */
+} bem_result;
+
+typedef struct {
+    int64_t submitted, completed, refused, cancelled, timed_out, failed;
+    int64_t queued, running;
+    int64_t hbm_budget_bytes, hbm_reserved_bytes, hbm_high_water_bytes;
+} bem_serve_stats;
+
+BEM_API void       bem_serve_opts_default(bem_server_opts* opts);
+BEM_API bem_status bem_serve_create(const bem_server_opts* opts, bem_server** out);
+/* Cancels queued requests, stops running ones at their next iteration, joins the
+ * workers and frees everything (unpolled results included). */
+BEM_API bem_status bem_serve_destroy(bem_server* srv);
+/* Copies the request (all host arrays) and queues it.  Returns
+ * BEM_E_ADMISSION_REFUSED (no ticket) if its working set exceeds the whole budget,
+ * BEM_E_INVALID_ARG for malformed input. */
+BEM_API bem_status bem_serve_submit(bem_server* srv, const bem_request* req, uint64_t* ticket);
+/* BEM_E_BUSY while the request is queued or running.  Once it has finished: fills
+ * *info (may be NULL), copies the traces into the non-NULL host arrays
+ * ([n_rhs*nv_ext] for v_ext, w_ext; [n_rhs*nv_int] for v_int, w_int), releases the
+ * request and returns BEM_OK; info->status holds the request's own outcome.
+ * Unknown or already released tickets return BEM_E_INVALID_ARG. */
+BEM_API bem_status bem_serve_poll(bem_server* srv, uint64_t ticket, bem_result* info,
+                                  bem_c128* v_ext, bem_c128* w_ext, bem_c128* v_int, bem_c128* w_int);
+/* Blocks until the request has finished or timeout_ms elapses (BEM_E_BUSY). */
+BEM_API bem_status bem_serve_wait(bem_server* srv, uint64_t ticket, double timeout_ms);
+/* Queued: removed at once; running: stops at its next GMRES iteration.  Either way
+ * its outcome becomes BEM_E_CANCELLED (unless it had already finished). */
+BEM_API bem_status bem_serve_cancel(bem_server* srv, uint64_t ticket);
+BEM_API bem_status bem_serve_get_stats(bem_server* srv, bem_serve_stats* st);
 
 #ifdef __cplusplus
 }

@@ -27,6 +27,7 @@ BEM_E_ADMISSION_REFUSED = -6
 BEM_E_BUSY = -7
 BEM_E_CUDA = -8
 BEM_E_INTERNAL = -9
+BEM_E_CANCELLED = -10
 
 BEM_OP_V, BEM_OP_K, BEM_OP_T, BEM_OP_D = 0, 1, 2, 3
 BEM_PREC_FP64 = 0
@@ -73,6 +74,49 @@ class bem_solve_report(C.Structure):
     ]
 
 
+class bem_server_opts(C.Structure):
+    _fields_ = [
+        ("device", C.c_int32),
+        ("max_inflight", C.c_int32),
+        ("hbm_budget_bytes", C.c_int64),
+        ("precision", C.c_int32),
+        ("gmres_maxiter", C.c_int32),
+        ("gmres_tol", C.c_double),
+        ("dry_run", C.c_int32),
+        ("reserved", C.c_int32),
+        ("dry_run_us_per_unknown", C.c_double),
+    ]
+
+
+class bem_request(C.Structure):
+    _fields_ = [
+        ("xyz_ext", C.c_void_p), ("nv_ext", C.c_int64), ("tri_ext", C.c_void_p), ("nt_ext", C.c_int64),
+        ("xyz_int", C.c_void_p), ("nv_int", C.c_int64), ("tri_int", C.c_void_p), ("nt_int", C.c_int64),
+        ("k_ext", bem_c128), ("k_int", bem_c128),
+        ("rho_int_over_rho_ext", C.c_double),
+        ("n_rhs", C.c_int32),
+        ("precision", C.c_int32),
+        ("dirs", C.c_void_p),
+        ("amps", C.c_void_p),
+        ("timeout_ms", C.c_double),
+    ]
+
+
+class bem_result(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32), ("iterations", C.c_int32), ("residual", C.c_double),
+        ("queue_ms", C.c_double), ("run_ms", C.c_double), ("total_ms", C.c_double),
+        ("nv_ext", C.c_int64), ("nv_int", C.c_int64), ("n_rhs", C.c_int32), ("precision", C.c_int32),
+        ("bytes_reserved", C.c_int64),
+    ]
+
+
+class bem_serve_stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("submitted", "completed", "refused", "cancelled", "timed_out", "failed",
+                                         "queued", "running", "hbm_budget_bytes", "hbm_reserved_bytes",
+                                         "hbm_high_water_bytes")]
+
+
 _VP = C.c_void_p
 _PVP = C.POINTER(C.c_void_p)
 _I64 = C.c_int64
@@ -106,6 +150,14 @@ _SIGNATURES = {
     "bem_sparse_info": (C.c_int32, [_VP, _PI64, _PI64, _PI64]),
     "bem_sparse_copy_out": (C.c_int32, [_VP, _VP, _VP, _VP, _VP, _I64]),
     "bem_solve_opts_default": (None, [C.POINTER(bem_solve_opts)]),
+    "bem_serve_opts_default": (None, [C.POINTER(bem_server_opts)]),
+    "bem_serve_create": (C.c_int32, [C.POINTER(bem_server_opts), _PVP]),
+    "bem_serve_destroy": (C.c_int32, [_VP]),
+    "bem_serve_submit": (C.c_int32, [_VP, C.POINTER(bem_request), C.POINTER(C.c_uint64)]),
+    "bem_serve_poll": (C.c_int32, [_VP, C.c_uint64, C.POINTER(bem_result), _VP, _VP, _VP, _VP]),
+    "bem_serve_wait": (C.c_int32, [_VP, C.c_uint64, C.c_double]),
+    "bem_serve_cancel": (C.c_int32, [_VP, C.c_uint64]),
+    "bem_serve_get_stats": (C.c_int32, [_VP, C.POINTER(bem_serve_stats)]),
     "bem_solve_transmission": (C.c_int32, [_VP, _VP, _VP, bem_c128, bem_c128, C.c_double,
                                            C.POINTER(bem_incident), C.POINTER(bem_solve_opts),
                                            _VP, _VP, _VP, _VP, C.c_int, C.POINTER(bem_solve_report)]),
@@ -382,3 +434,95 @@ def bem_solve_transmission(ctx, ext, intr, k_int, k_ext, rho_int_over_rho_ext, d
         err.outputs, err.report = out, report
         raise err
     return out, report
+
+
+# ------------------------------------------------------------------ serving
+def bem_serve_opts_default():
+    o = bem_server_opts()
+    _lib.bem_serve_opts_default(C.byref(o))
+    return o
+
+
+def bem_serve_create(**kw):
+    """Create a request server; keyword arguments override bem_server_opts fields."""
+    o = bem_serve_opts_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    h = C.c_void_p()
+    _check(_lib.bem_serve_create(C.byref(o), C.byref(h)))
+    return h
+
+
+def bem_serve_destroy(srv):
+    _check(_lib.bem_serve_destroy(srv))
+
+
+def bem_serve_submit(srv, xyz_ext, tri_ext, xyz_int, tri_int, k_ext, k_int, rho_int_over_rho_ext, dirs,
+                     amps=None, precision=-1, timeout_ms=0.0):
+    """Queue one request (host arrays are copied); returns the ticket."""
+    xe = np.ascontiguousarray(xyz_ext, dtype=np.float64)
+    te = np.ascontiguousarray(tri_ext, dtype=np.int32)
+    xi = np.ascontiguousarray(xyz_int, dtype=np.float64)
+    ti = np.ascontiguousarray(tri_int, dtype=np.int32)
+    d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    q = bem_request()
+    q.xyz_ext, q.nv_ext, q.tri_ext, q.nt_ext = xe.ctypes.data, len(xe), te.ctypes.data, len(te)
+    q.xyz_int, q.nv_int, q.tri_int, q.nt_int = xi.ctypes.data, len(xi), ti.ctypes.data, len(ti)
+    q.k_ext, q.k_int = _c128(k_ext), _c128(k_int)
+    q.rho_int_over_rho_ext = float(rho_int_over_rho_ext)
+    q.n_rhs = d.shape[0]
+    q.precision = int(precision)
+    q.dirs = d.ctypes.data
+    amp_arr = None
+    if amps is not None:
+        amp_arr = (bem_c128 * d.shape[0])(*[_c128(a) for a in np.atleast_1d(amps)])
+        q.amps = C.cast(amp_arr, C.c_void_p)
+    q.timeout_ms = float(timeout_ms)
+    t = C.c_uint64()
+    _check(_lib.bem_serve_submit(srv, C.byref(q), C.byref(t)))
+    return t.value
+
+
+def bem_serve_poll(srv, ticket):
+    """None while the request is queued or running; otherwise its info dict (the
+    request is released without copying traces; see bem_serve_take)."""
+    info = bem_result()
+    st = _lib.bem_serve_poll(srv, C.c_uint64(ticket), C.byref(info), None, None, None, None)
+    if st == BEM_E_BUSY:
+        return None
+    _check(st)
+    return {f: getattr(info, f) for f, _ in bem_result._fields_}
+
+
+def bem_serve_take(srv, ticket, n_rhs, nv_ext, nv_int):
+    """Like bem_serve_poll, copying the traces into new arrays of the given sizes."""
+    info = bem_result()
+    out = {"v_ext": np.zeros((n_rhs, nv_ext), dtype=np.complex128),
+           "w_ext": np.zeros((n_rhs, nv_ext), dtype=np.complex128),
+           "v_int": np.zeros((n_rhs, nv_int), dtype=np.complex128),
+           "w_int": np.zeros((n_rhs, nv_int), dtype=np.complex128)}
+    st = _lib.bem_serve_poll(srv, C.c_uint64(ticket), C.byref(info), out["v_ext"].ctypes.data,
+                             out["w_ext"].ctypes.data, out["v_int"].ctypes.data, out["w_int"].ctypes.data)
+    if st == BEM_E_BUSY:
+        return None
+    _check(st)
+    return out, {f: getattr(info, f) for f, _ in bem_result._fields_}
+
+
+def bem_serve_wait(srv, ticket, timeout_ms=0.0):
+    """True once the request has finished, False on timeout."""
+    st = _lib.bem_serve_wait(srv, C.c_uint64(ticket), float(timeout_ms))
+    if st == BEM_E_BUSY:
+        return False
+    _check(st)
+    return True
+
+
+def bem_serve_cancel(srv, ticket):
+    _check(_lib.bem_serve_cancel(srv, C.c_uint64(ticket)))
+
+
+def bem_serve_get_stats(srv):
+    st = bem_serve_stats()
+    _check(_lib.bem_serve_get_stats(srv, C.byref(st)))
+    return {f: getattr(st, f) for f, _ in bem_serve_stats._fields_}

@@ -350,12 +350,9 @@ bem_status assemble_regular_fp32(const bem_grid* g, double k_re, double k_im, fl
         return BEM_E_INVALID_ARG;
     }
     const size_t smem = 16 * TILE_NV * TILE_NV * sizeof(float) + TILE_TRI * sizeof(TriRec32) + sizeof(TrialTile32);
-    static bool attr_set = false;
-    if (!attr_set) {
-        BEM_CUDA_TRY(cudaFuncSetAttribute(k_regular32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        BEM_CUDA_TRY(cudaFuncSetAttribute(k_regular32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
+    // the attribute is per device and per function; setting it on every call is cheap and thread-safe
+    BEM_CUDA_TRY(cudaFuncSetAttribute(k_regular32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BEM_CUDA_TRY(cudaFuncSetAttribute(k_regular32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)g->ntile, (unsigned)g->ntile);
     const bool ck = k_im != 0.0;
     if (ck)

@@ -2,6 +2,9 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -9,6 +12,10 @@
 #include "../../include/bem.h"
 
 namespace bem {
+
+inline double now_seconds() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 // ------------------------------------------------------------------ errors
 void set_error(const std::string& msg);
@@ -143,6 +150,9 @@ struct bem_context {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // stop request checked by the solver between GMRES iterations (serving)
+    const std::atomic<int>* cancel = nullptr;
+    double deadline = 0.0;  // steady-clock seconds; 0 = none
 };
 
 struct bem_grid {

@@ -1,0 +1,380 @@
+// Request server for streams of transmission solves (the serving pattern of the
+// build: continuous batching with admission by HBM budget).  Host-side C++: worker
+// threads, each with its own context and CUDA stream, take requests from a FIFO
+// queue when a slot is free and the request's device working set fits in what is
+// left of the budget; the GPU work of different requests overlaps on the streams.
+#include "bem_internal.cuh"
+
+#include <condition_variable>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+
+namespace bem {
+
+bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const bem_grid* gi, bem_c128 k_int,
+                                   bem_c128 k_ext, double rho_ratio, const bem_incident* inc,
+                                   const bem_solve_opts* o, bem_c128* v_ext, bem_c128* w_ext, bem_c128* v_int,
+                                   bem_c128* w_int, int on_device, bem_solve_report* rep);
+
+namespace {
+
+enum class RState { Queued, Running, Done };
+
+struct Request {
+    uint64_t ticket = 0;
+    std::vector<double> xe, xi, dirs;
+    std::vector<int32_t> te, ti;
+    std::vector<bem_c128> amps;
+    bem_c128 k_ext{}, k_int{};
+    double rho = 1.0;
+    int32_t n_rhs = 1, precision = BEM_PREC_MIXED;
+    double t_submit = 0, t_start = 0, t_end = 0, deadline = 0;
+    int64_t bytes = 0;
+    std::atomic<int> cancel{0};
+    RState state = RState::Queued;
+    bem_result result{};
+    std::vector<bem_c128> v_ext, w_ext, v_int, w_int;
+};
+
+}  // namespace
+}  // namespace bem
+
+struct bem_server {
+    bem_server_opts opts{};
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::shared_ptr<bem::Request>> queue;
+    std::unordered_map<uint64_t, std::shared_ptr<bem::Request>> all;
+    std::vector<std::thread> workers;
+    std::vector<bem_context*> contexts;
+    bool stopping = false;
+    uint64_t next_ticket = 1;
+    int64_t reserved = 0, high_water = 0;
+    bem_serve_stats stats{};
+};
+
+namespace bem {
+namespace {
+
+// Upper estimate of a request's device working set.
+int64_t working_set_bytes(int64_t ne, int64_t ni, int precision, int maxiter) {
+    const int64_t n = 2 * ne + 2 * ni;
+    const int64_t esz = precision == BEM_PREC_MIXED ? 8 : 16;
+    const int64_t ops = 4 * (ne * ne + ni * ni) * esz;
+    const int64_t m = std::min<int64_t>(maxiter, n) + 1;
+    const int64_t krylov = m * n * 16 + m * m * 16 + m * 64 * 16;
+    const int64_t vectors = 16 * n * 16;
+    const int64_t grids = 600 * (ne + ni) * 2;
+    const int64_t mortar = 2 * 9 * 40 * (ne + ni) * 16;
+    return ops + krylov + vectors + grids + mortar + (int64_t)(16 << 20);
+}
+
+void finish_locked(bem_server* srv, const std::shared_ptr<Request>& r, int32_t status) {
+    r->t_end = now_seconds();
+    r->state = RState::Done;
+    r->result.status = status;
+    r->result.queue_ms = 1e3 * ((r->t_start > 0 ? r->t_start : r->t_end) - r->t_submit);
+    r->result.run_ms = r->t_start > 0 ? 1e3 * (r->t_end - r->t_start) : 0.0;
+    r->result.total_ms = 1e3 * (r->t_end - r->t_submit);
+    switch (status) {
+        case BEM_OK: srv->stats.completed++; break;
+        case BEM_E_CANCELLED: srv->stats.cancelled++; break;
+        case BEM_E_TIMEOUT: srv->stats.timed_out++; break;
+        default: srv->stats.failed++; break;
+    }
+}
+
+int32_t run_request(bem_server* srv, bem_context* ctx, Request& r) {
+    const int64_t ne = (int64_t)r.xe.size() / 3, ni = (int64_t)r.xi.size() / 3;
+    const size_t oe = (size_t)r.n_rhs * ne, oi = (size_t)r.n_rhs * ni;
+    r.v_ext.assign(oe, bem_c128{0, 0});
+    r.w_ext.assign(oe, bem_c128{0, 0});
+    r.v_int.assign(oi, bem_c128{0, 0});
+    r.w_int.assign(oi, bem_c128{0, 0});
+    if (srv->opts.dry_run) {
+        // simulated service time, with the same stop checks as a real solve
+        const double us = srv->opts.dry_run_us_per_unknown * (double)(2 * ne + 2 * ni) * r.n_rhs;
+        const double t_end = now_seconds() + us * 1e-6;
+        while (now_seconds() < t_end) {
+            if (r.cancel.load()) return BEM_E_CANCELLED;
+            if (r.deadline > 0 && now_seconds() > r.deadline) return BEM_E_TIMEOUT;
+            std::this_thread::sleep_for(std::chrono::microseconds(200));
+        }
+        r.result.iterations = 0;
+        r.result.residual = 0.0;
+        return BEM_OK;
+    }
+    ctx->cancel = &r.cancel;
+    ctx->deadline = r.deadline;
+    bem_grid *ge = nullptr, *gi = nullptr;
+    bem_status st = bem_grid_create(ctx, r.xe.data(), ne, r.te.data(), (int64_t)r.te.size() / 3, 0, &ge);
+    if (st == BEM_OK) st = bem_grid_create(ctx, r.xi.data(), ni, r.ti.data(), (int64_t)r.ti.size() / 3, 0, &gi);
+    if (st == BEM_OK) {
+        bem_incident inc{r.n_rhs, r.dirs.data(), r.amps.empty() ? nullptr : r.amps.data()};
+        bem_solve_opts o;
+        bem_solve_opts_default(&o);
+        o.precision = r.precision;
+        o.gmres_tol = srv->opts.gmres_tol;
+        o.gmres_maxiter = srv->opts.gmres_maxiter;
+        bem_solve_report rep{};
+        st = solve_transmission_impl(ctx, ge, gi, r.k_int, r.k_ext, r.rho, &inc, &o, r.v_ext.data(), r.w_ext.data(),
+                                     r.v_int.data(), r.w_int.data(), 0, &rep);
+        r.result.iterations = rep.iterations;
+        r.result.residual = rep.residual;
+    }
+    if (ge) bem_grid_destroy(ge);
+    if (gi) bem_grid_destroy(gi);
+    cudaStreamSynchronize(ctx->stream);
+    ctx->cancel = nullptr;
+    ctx->deadline = 0.0;
+    return st;
+}
+
+void worker_main(bem_server* srv, int idx) {
+    bem_context* ctx = srv->opts.dry_run ? nullptr : srv->contexts[idx];
+    if (ctx) cudaSetDevice(ctx->device);
+    for (;;) {
+        std::shared_ptr<Request> r;
+        {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            srv->cv_work.wait(lk, [&] {
+                if (srv->stopping) return true;
+                if (srv->queue.empty()) return false;
+                const auto& h = srv->queue.front();
+                return h->cancel.load() || srv->reserved + h->bytes <= srv->opts.hbm_budget_bytes;
+            });
+            if (srv->stopping) return;
+            r = srv->queue.front();
+            srv->queue.pop_front();
+            srv->stats.queued = (int64_t)srv->queue.size();
+            if (r->cancel.load()) {
+                finish_locked(srv, r, BEM_E_CANCELLED);
+                srv->cv_done.notify_all();
+                srv->cv_work.notify_all();
+                continue;
+            }
+            r->state = RState::Running;
+            r->t_start = now_seconds();
+            srv->reserved += r->bytes;
+            srv->high_water = std::max(srv->high_water, srv->reserved);
+            srv->stats.running++;
+        }
+        int32_t st;
+        if (r->deadline > 0 && now_seconds() > r->deadline) st = BEM_E_TIMEOUT;
+        else if (r->cancel.load()) st = BEM_E_CANCELLED;
+        else st = run_request(srv, ctx, *r);
+        {
+            std::lock_guard<std::mutex> lk(srv->mu);
+            srv->reserved -= r->bytes;
+            srv->stats.running--;
+            finish_locked(srv, r, st);
+        }
+        srv->cv_done.notify_all();
+        srv->cv_work.notify_all();
+    }
+}
+
+}  // namespace
+}  // namespace bem
+
+using namespace bem;
+
+extern "C" {
+
+void bem_serve_opts_default(bem_server_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->device = 0;
+    o->max_inflight = 4;
+    o->hbm_budget_bytes = 0;
+    o->precision = BEM_PREC_MIXED;
+    o->gmres_maxiter = 2000;
+    o->gmres_tol = 1e-8;
+    o->dry_run = 0;
+    o->dry_run_us_per_unknown = 1.0;
+}
+
+bem_status bem_serve_create(const bem_server_opts* opts, bem_server** out) {
+    BEM_REQUIRE(out != nullptr, "out is null");
+    *out = nullptr;
+    bem_server_opts o;
+    if (opts) o = *opts;
+    else bem_serve_opts_default(&o);
+    BEM_REQUIRE(o.max_inflight >= 1 && o.max_inflight <= 64, "max_inflight must be in [1, 64]");
+    BEM_REQUIRE(o.precision == BEM_PREC_FP64 || o.precision == BEM_PREC_MIXED, "unknown precision");
+    BEM_REQUIRE(o.gmres_maxiter >= 1 && o.gmres_tol >= 0.0, "bad GMRES options");
+    std::unique_ptr<bem_server> srv(new (std::nothrow) bem_server());
+    if (!srv) {
+        set_error("host allocation failed");
+        return BEM_E_OOM;
+    }
+    if (!o.dry_run) {
+        BEM_CUDA_TRY(cudaSetDevice(o.device));
+        size_t free_b = 0, total_b = 0;
+        BEM_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        if (o.hbm_budget_bytes <= 0) o.hbm_budget_bytes = (int64_t)(0.8 * (double)free_b);
+        // keep freed stream-ordered allocations in the pool between requests
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, o.device) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        for (int i = 0; i < o.max_inflight; ++i) {
+            bem_context* c = nullptr;
+            bem_status st = bem_context_create(o.device, nullptr, &c);
+            if (st != BEM_OK) {
+                for (bem_context* x : srv->contexts) bem_context_destroy(x);
+                return st;
+            }
+            srv->contexts.push_back(c);
+        }
+    } else {
+        BEM_REQUIRE(o.hbm_budget_bytes > 0, "dry-run servers need an explicit hbm_budget_bytes");
+        BEM_REQUIRE(o.dry_run_us_per_unknown >= 0.0, "dry_run_us_per_unknown must be >= 0");
+    }
+    srv->opts = o;
+    srv->stats.hbm_budget_bytes = o.hbm_budget_bytes;
+    bem_server* p = srv.release();
+    for (int i = 0; i < o.max_inflight; ++i) p->workers.emplace_back(worker_main, p, i);
+    *out = p;
+    return BEM_OK;
+}
+
+bem_status bem_serve_destroy(bem_server* srv) {
+    if (!srv) return BEM_OK;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stopping = true;
+        for (auto& kv : srv->all) kv.second->cancel.store(1);
+    }
+    srv->cv_work.notify_all();
+    for (auto& t : srv->workers) t.join();
+    for (bem_context* c : srv->contexts) bem_context_destroy(c);
+    delete srv;
+    return BEM_OK;
+}
+
+bem_status bem_serve_submit(bem_server* srv, const bem_request* q, uint64_t* ticket) {
+    BEM_REQUIRE(srv != nullptr && q != nullptr && ticket != nullptr, "null argument");
+    BEM_REQUIRE(q->xyz_ext && q->tri_ext && q->xyz_int && q->tri_int && q->dirs, "null request array");
+    BEM_REQUIRE(q->nv_ext >= 3 && q->nt_ext >= 1 && q->nv_int >= 3 && q->nt_int >= 1, "empty grid");
+    BEM_REQUIRE(q->n_rhs >= 1, "n_rhs must be >= 1");
+    BEM_REQUIRE(std::isfinite(q->rho_int_over_rho_ext) && q->rho_int_over_rho_ext > 0.0, "density ratio must be > 0");
+    BEM_REQUIRE(q->precision == -1 || q->precision == BEM_PREC_FP64 || q->precision == BEM_PREC_MIXED,
+                "unknown precision");
+    BEM_REQUIRE(q->timeout_ms >= 0.0, "timeout must be >= 0");
+    auto r = std::make_shared<Request>();
+    r->xe.assign(q->xyz_ext, q->xyz_ext + 3 * q->nv_ext);
+    r->te.assign(q->tri_ext, q->tri_ext + 3 * q->nt_ext);
+    r->xi.assign(q->xyz_int, q->xyz_int + 3 * q->nv_int);
+    r->ti.assign(q->tri_int, q->tri_int + 3 * q->nt_int);
+    r->dirs.assign(q->dirs, q->dirs + 3 * q->n_rhs);
+    if (q->amps) r->amps.assign(q->amps, q->amps + q->n_rhs);
+    r->k_ext = q->k_ext;
+    r->k_int = q->k_int;
+    r->rho = q->rho_int_over_rho_ext;
+    r->n_rhs = q->n_rhs;
+    r->precision = q->precision < 0 ? srv->opts.precision : q->precision;
+    r->bytes = working_set_bytes(q->nv_ext, q->nv_int, r->precision, srv->opts.gmres_maxiter);
+    r->result.nv_ext = q->nv_ext;
+    r->result.nv_int = q->nv_int;
+    r->result.n_rhs = q->n_rhs;
+    r->result.precision = r->precision;
+    r->result.bytes_reserved = r->bytes;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    BEM_REQUIRE(!srv->stopping, "server is shutting down");
+    if (r->bytes > srv->opts.hbm_budget_bytes) {
+        srv->stats.refused++;
+        set_error("request needs about " + std::to_string(r->bytes) + " device bytes, more than the budget of " +
+                  std::to_string(srv->opts.hbm_budget_bytes));
+        return BEM_E_ADMISSION_REFUSED;
+    }
+    r->t_submit = now_seconds();
+    r->deadline = q->timeout_ms > 0 ? r->t_submit + 1e-3 * q->timeout_ms : 0.0;
+    r->ticket = srv->next_ticket++;
+    srv->all[r->ticket] = r;
+    srv->queue.push_back(r);
+    srv->stats.submitted++;
+    srv->stats.queued = (int64_t)srv->queue.size();
+    *ticket = r->ticket;
+    srv->cv_work.notify_one();
+    return BEM_OK;
+}
+
+bem_status bem_serve_poll(bem_server* srv, uint64_t ticket, bem_result* info, bem_c128* v_ext, bem_c128* w_ext,
+                          bem_c128* v_int, bem_c128* w_int) {
+    BEM_REQUIRE(srv != nullptr, "null server");
+    std::shared_ptr<Request> r;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        auto it = srv->all.find(ticket);
+        BEM_REQUIRE(it != srv->all.end(), "unknown or released ticket");
+        r = it->second;
+        if (r->state != RState::Done) return BEM_E_BUSY;
+        srv->all.erase(it);
+    }
+    if (info) *info = r->result;
+    auto copy = [](bem_c128* dst, const std::vector<bem_c128>& src) {
+        if (dst && !src.empty()) std::memcpy(dst, src.data(), src.size() * sizeof(bem_c128));
+    };
+    copy(v_ext, r->v_ext);
+    copy(w_ext, r->w_ext);
+    copy(v_int, r->v_int);
+    copy(w_int, r->w_int);
+    return BEM_OK;
+}
+
+bem_status bem_serve_wait(bem_server* srv, uint64_t ticket, double timeout_ms) {
+    BEM_REQUIRE(srv != nullptr, "null server");
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->all.find(ticket);
+    BEM_REQUIRE(it != srv->all.end(), "unknown or released ticket");
+    std::shared_ptr<Request> r = it->second;
+    const auto pred = [&] { return r->state == RState::Done; };
+    if (timeout_ms <= 0) srv->cv_done.wait(lk, pred);
+    else if (!srv->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), pred))
+        return BEM_E_BUSY;
+    return BEM_OK;
+}
+
+bem_status bem_serve_cancel(bem_server* srv, uint64_t ticket) {
+    BEM_REQUIRE(srv != nullptr, "null server");
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        auto it = srv->all.find(ticket);
+        BEM_REQUIRE(it != srv->all.end(), "unknown or released ticket");
+        std::shared_ptr<Request> r = it->second;
+        if (r->state == RState::Done) return BEM_OK;
+        r->cancel.store(1);
+        if (r->state == RState::Queued) {
+            for (auto q = srv->queue.begin(); q != srv->queue.end(); ++q)
+                if (*q == r) {
+                    srv->queue.erase(q);
+                    break;
+                }
+            srv->stats.queued = (int64_t)srv->queue.size();
+            finish_locked(srv, r, BEM_E_CANCELLED);
+        }
+    }
+    srv->cv_done.notify_all();
+    srv->cv_work.notify_all();
+    return BEM_OK;
+}
+
+bem_status bem_serve_get_stats(bem_server* srv, bem_serve_stats* st) {
+    BEM_REQUIRE(srv != nullptr && st != nullptr, "null argument");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    *st = srv->stats;
+    st->hbm_reserved_bytes = srv->reserved;
+    st->hbm_high_water_bytes = srv->high_water;
+    st->queued = (int64_t)srv->queue.size();
+    return BEM_OK;
+}
+
+}  // extern "C"

@@ -554,8 +554,11 @@ bem_status norm2(GmresWork& W, const double2* v, double* out, cudaStream_t s) {
 
 // Unrestarted GMRES from x0 = 0 on apply(x) = rhs; stops when the residual estimate
 // is <= tol_abs.  Writes x; returns iterations and the final estimate.
+// stop check between iterations (serving: cancellation and deadlines)
+using StopCheck = std::function<bem_status()>;
+
 bem_status gmres_run(GmresWork& W, const Apply& apply, const double2* rhs, double beta, double tol_abs,
-                     double2* x, int* iters_out, double* res_out, cudaStream_t s) {
+                     double2* x, int* iters_out, double* res_out, cudaStream_t s, const StopCheck& stop) {
     const int64_t n = W.n, ldv = n, ldh = W.ldh;
     double2* Vp = W.Vb.as<double2>();
     const unsigned eb = blocks_for(n, 256);
@@ -592,6 +595,7 @@ bem_status gmres_run(GmresWork& W, const Apply& apply, const double2* rhs, doubl
             iters = j + 1;
             resid = W.h_res[0];
             if (!(resid > tol_abs)) break;
+            if (stop) BEM_TRY(stop());
         }
     }
     if (iters > 0) {
@@ -646,6 +650,18 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     cudaStream_t s = ctx->stream;
     const int64_t Ne = ge->nv, Ni = gi->nv, n = 2 * Ne + 2 * Ni;
     const bool mixed = o->precision == BEM_PREC_MIXED;
+    const StopCheck stop = [ctx]() -> bem_status {
+        if (ctx->cancel && ctx->cancel->load(std::memory_order_relaxed)) {
+            set_error("request cancelled");
+            return BEM_E_CANCELLED;
+        }
+        if (ctx->deadline > 0.0 && now_seconds() > ctx->deadline) {
+            set_error("request exceeded its time limit");
+            return BEM_E_TIMEOUT;
+        }
+        return BEM_OK;
+    };
+    BEM_TRY(stop());
     EventTimer t_asm, t_mor, t_sol;
     // ---- operators on both grids --------------------------------------------------
     const size_t esz = mixed ? 8 : 16;
@@ -759,7 +775,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
         double rel = 0.0;
         if (!mixed) {
             double est = 0.0;
-            BEM_TRY(gmres_run(W, apply_work, sb.as<double2>(), beta, tol_abs, xsol.as<double2>(), &iters, &est, s));
+            BEM_TRY(gmres_run(W, apply_work, sb.as<double2>(), beta, tol_abs, xsol.as<double2>(), &iters, &est, s, stop));
             rel = beta > 0.0 ? est / beta : 0.0;
             total_inner += iters;
             outer_used = 1;
@@ -774,7 +790,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                 const double inner_tol = std::max(tol_abs, o->ir_inner_tol * rn);
                 int it = 0;
                 double est = 0.0;
-                BEM_TRY(gmres_run(W, apply_work, rvec.as<double2>(), rn, inner_tol, dvec.as<double2>(), &it, &est, s));
+                BEM_TRY(gmres_run(W, apply_work, rvec.as<double2>(), rn, inner_tol, dvec.as<double2>(), &it, &est, s, stop));
                 iters += it;
                 total_inner += it;
                 BEM_LAUNCH(k_acc, eb, 256, 0, s, xsol.as<double2>(), dvec.as<double2>(), n);
