@@ -24,6 +24,7 @@ solves its own copy (the method has no data exchange between solves: replicas).
 from __future__ import annotations
 
 import argparse
+import re
 import json
 import os
 import statistics
@@ -259,17 +260,54 @@ def run_serving(bem, reqs, precision, rate=None, max_inflight=4):
             "wall_s": wall, "hbm_high_water_bytes": stats["hbm_high_water_bytes"]}
 
 
+BATCH_WORKLOAD = dict(level=4, seed=4, k_ext=5.0, k_int=7.5, rho=1.0, n_dirs=64, n_single=8)
+
+
+def run_batching(bem, ctx, precision):
+    """Many plane waves at one frequency: one call with all directions (solved in
+    lockstep batches of 8) against the same directions one call each."""
+    import torch
+    import bem_inputs as bi
+    b = BATCH_WORKLOAD
+    ve, te, vi, ti = bi.transmission_pair(b["level"], b["level"], b["seed"])
+    dirs = bi.plane_wave_directions(b["n_dirs"], seed=b["seed"] + 100)
+    opts = {"precision": precision}
+    ge = bem.bem_grid_create(ctx, ve, te)
+    gi = bem.bem_grid_create(ctx, vi, ti)
+    bem.bem_solve_transmission(ctx, ge, gi, b["k_int"], b["k_ext"], b["rho"], dirs[:8], opts=opts)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, rep = bem.bem_solve_transmission(ctx, ge, gi, b["k_int"], b["k_ext"], b["rho"], dirs, opts=opts)
+    t_batch = time.perf_counter() - t0
+    single_solve_ms, single_wall = [], 0.0
+    for r in range(b["n_single"]):
+        t0 = time.perf_counter()
+        _, r1 = bem.bem_solve_transmission(ctx, ge, gi, b["k_int"], b["k_ext"], b["rho"], dirs[r:r + 1], opts=opts)
+        single_wall += time.perf_counter() - t0
+        single_solve_ms.append(r1["t_solve_ms"])
+    bem.bem_grid_destroy(ge)
+    bem.bem_grid_destroy(gi)
+    return {"rhs_per_s_one_call": b["n_dirs"] / t_batch,
+            "rhs_per_s_one_call_each": b["n_single"] / single_wall,
+            "solve_ms_per_rhs_batched": rep["t_solve_ms"] / b["n_dirs"],
+            "solve_ms_per_rhs_single": float(np.mean(single_solve_ms)),
+            "iterations_per_rhs_batched": rep["iterations"] / b["n_dirs"],
+            "assembly_ms": rep["t_assembly_ms"]}
+
+
 def kernel_roofline(name, ms, n, te, ti, Ne, Ni, pp_cache):
     """Roofline entry of one profiled kernel (per-launch averages)."""
     avg_s = ms / n / 1e3
-    if name.startswith("k_gemv_mtf32"):
+    m = re.search(r"<(\d+)>", name)
+    cols = int(m.group(1)) if m else 1  # right-hand sides per launch
+    if name.startswith("k_gemm32"):
         peak, kind = hbm_peak()
-        bytes_ = 8 * 4 * (Ne * Ne + Ni * Ni)  # 8 complex64 blocks read once per matvec
+        bytes_ = 8 * 4 * (Ne * Ne + Ni * Ni)  # 8 complex64 blocks read once per operator product
         ach = bytes_ / avg_s / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": None, "peak_kind": kind, "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": ms / n}
-    if name.startswith("k_gemv_mtf"):
-        flops = 8 * 4 * (Ne * Ne + Ni * Ni) * 8.0 / 8  # 4 DFMA = 8 flops per complex entry
+    if name.startswith("k_gemm64"):
+        flops = 8 * 4 * (Ne * Ne + Ni * Ni) * cols  # 4 DFMA = 8 flops per complex entry and column
         ach = flops / avg_s / 1e12
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
@@ -300,6 +338,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison arm")
+    ap.add_argument("--no-batching", dest="batching", action="store_false",
+                    help="skip the many-directions section")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the seeded serving stream to replay (0: skip serving)")
     args = ap.parse_args()
@@ -436,6 +476,15 @@ def main():
                    "saturated": {"fp64": sat[bem.BEM_PREC_FP64], "mixed": sat[bem.BEM_PREC_MIXED]},
                    "poisson": {"rate_per_s": rate, "fp64": rep[bem.BEM_PREC_FP64], "mixed": rep[bem.BEM_PREC_MIXED]}}
 
+    batching = None
+    if args.batching:
+        bw = BATCH_WORKLOAD
+        batching = {"workload": f"unit sphere, icosphere L{bw['level']} on both grids (seed {bw['seed']}), "
+                                f"k_ext={bw['k_ext']}, k_int={bw['k_int']}, rho={bw['rho']}, {bw['n_dirs']} plane "
+                                f"waves in one call vs {bw['n_single']} of them one call each",
+                    "mixed": run_batching(bem, ctx, bem.BEM_PREC_MIXED),
+                    "fp64": run_batching(bem, ctx, bem.BEM_PREC_FP64)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = run_oracle_child(int(mixed["reports"][-1]["iterations"]))
@@ -477,6 +526,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "serving": serving,
+            "batching": batching,
             "solve": solve_info(m["reports"][-1]),
             "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in m["prof"][:10]],
         }

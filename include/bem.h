@@ -210,7 +210,9 @@ typedef struct {
     int32_t mtf_variant;      /* BEM_MTF_DERIVED (default) or BEM_MTF_PRINTED                     */
     double  center[3];        /* projection centre for the mortar (default origin)               */
     double  ir_inner_tol;     /* BEM_PREC_MIXED: relative residual reduction asked of each inner
-                                 GMRES solve (default 1e-6; never below gmres_tol overall)        */
+                                 GMRES solve (default 1e-8: the first inner solve runs to the
+                                 target tolerance, the FP64 residual then needs one short
+                                 correction); never below gmres_tol * ||S b|| overall              */
 } bem_solve_opts;
 
 typedef struct {

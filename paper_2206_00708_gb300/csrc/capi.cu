@@ -344,7 +344,7 @@ void bem_solve_opts_default(bem_solve_opts* o) {
     o->n_singular = 4;
     o->mtf_variant = BEM_MTF_DERIVED;
     o->center[0] = o->center[1] = o->center[2] = 0.0;
-    o->ir_inner_tol = 1e-6;
+    o->ir_inner_tol = 1e-8;
 }
 
 bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const bem_grid* intr, bem_c128 k_int,

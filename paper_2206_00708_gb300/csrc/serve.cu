@@ -63,13 +63,16 @@ namespace bem {
 namespace {
 
 // Upper estimate of a request's device working set.
-int64_t working_set_bytes(int64_t ne, int64_t ni, int precision, int maxiter) {
+int64_t working_set_bytes(int64_t ne, int64_t ni, int precision, int maxiter, int n_rhs) {
     const int64_t n = 2 * ne + 2 * ni;
     const int64_t esz = precision == BEM_PREC_MIXED ? 8 : 16;
     const int64_t ops = 4 * (ne * ne + ni * ni) * esz;
     const int64_t m = std::min<int64_t>(maxiter, n) + 1;
-    const int64_t krylov = m * n * 16 + m * m * 16 + m * 64 * 16;
-    const int64_t vectors = 16 * n * 16;
+    // the solver advances up to 8 right-hand sides together, each with its own
+    // Krylov basis and Hessenberg matrix
+    const int64_t R = std::max(1, std::min(n_rhs, 8));
+    const int64_t krylov = R * (m * n * 16 + m * m * 16 + m * 64 * 16);
+    const int64_t vectors = 16 * R * n * 16;
     const int64_t grids = 600 * (ne + ni) * 2;
     const int64_t mortar = 2 * 9 * 40 * (ne + ni) * 16;
     return ops + krylov + vectors + grids + mortar + (int64_t)(16 << 20);
@@ -281,7 +284,7 @@ bem_status bem_serve_submit(bem_server* srv, const bem_request* q, uint64_t* tic
     r->rho = q->rho_int_over_rho_ext;
     r->n_rhs = q->n_rhs;
     r->precision = q->precision < 0 ? srv->opts.precision : q->precision;
-    r->bytes = working_set_bytes(q->nv_ext, q->nv_int, r->precision, srv->opts.gmres_maxiter);
+    r->bytes = working_set_bytes(q->nv_ext, q->nv_int, r->precision, srv->opts.gmres_maxiter, q->n_rhs);
     r->result.nv_ext = q->nv_ext;
     r->result.nv_int = q->nv_int;
     r->result.n_rhs = q->n_rhs;

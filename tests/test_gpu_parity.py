@@ -238,3 +238,29 @@ def test_invalid_inputs_are_rejected(bem, ctx):
     assert e.value.status == bem.BEM_E_NOT_CONVERGED
     assert e.value.report["iterations"] == 2
     bem.bem_grid_destroy(g)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_right_hand_sides_equal_one_at_a_time(bem, ctx, precision):
+    """Eleven plane waves in one call run as a batch of 8 and a batch of 3 (padded
+    to a kernel width of 4); every column must equal the solve of that wave alone.
+    In FP64 the per-column arithmetic is the same in both, so columns agree to
+    rounding and the summed iteration count equals the sum of the single solves.
+    The FP32 assembly accumulates with shared-memory atomics whose order varies
+    from call to call, so two mixed-precision calls see operators that differ at
+    FP32 rounding level: there the bound is the mixed-precision tolerance 1e-6."""
+    ve, te, vi, ti = bi.transmission_pair(2, 1, seed=9, axes=[1.1, 1.0, 0.9])
+    dirs = bi.plane_wave_directions(11, seed=41)
+    amps = [1.0 + 0.1j * r for r in range(11)]
+    k_ext, k_int, rho = 2.5, 4.0, 1.5
+    out, rep = _solve_pair(bem, ctx, ve, te, vi, ti, k_int, k_ext, rho, dirs, amps=amps, precision=precision)
+    total = 0
+    for r in range(11):
+        one, r1 = _solve_pair(bem, ctx, ve, te, vi, ti, k_int, k_ext, rho, dirs[r:r + 1], amps=amps[r:r + 1],
+                              precision=precision)
+        total += r1["iterations"]
+        for key in ("v_ext", "w_ext", "v_int", "w_int"):
+            assert rel(out[key][r], one[key][0]) < (1e-13 if precision == 0 else 1e-6), (r, key)
+    if precision == 0:
+        assert rep["iterations"] == total
+    assert rep["converged"] == 1
