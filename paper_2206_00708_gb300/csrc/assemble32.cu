@@ -12,10 +12,15 @@
 //    delta = (2 D.w + |w|^2) / (r + R) with D = c_tau - c_sigma and w the difference
 //    of the centroid offsets, so exp(i k r) = exp(i k R) exp(i k delta) keeps an
 //    absolute phase error ~1e-7 even where k r is large;
-//  * the 3x3 blocks of a CTA's triangle pairs are summed in shared memory with
-//    compensated atomics: each thread recovers the exact rounding error of its own
-//    atomic add (the returned old value makes a two-sum possible) and adds it to a
-//    second buffer, so the in-tile sums are double-float accurate.
+//  * the 3x3 blocks of a CTA's triangle pairs are summed in shared memory in fixed
+//    point, with native integer atomics (FP32 atomic adds on shared memory are
+//    compare-and-swap loops): each CTA first bounds every value it will produce
+//    (smallest and largest point distance of its regular pairs, largest weight sums,
+//    areas and curls, |k|), picks a power-of-two scale 2^e that maps the bound to
+//    2^40, and adds round(v 2^e) as a 21-bit low word (uint32) and a high word
+//    (int32).  A vertex lies in at most 32 triangles of a tile, so at most 1024
+//    values meet in one entry and neither word can overflow; the in-tile sums are
+//    exact (and independent of the order of the atomics) to 2^-40 of the bound.
 // The tile buffers are flushed to the global matrices with vector float2 atomics.
 #include "bem_internal.cuh"
 
@@ -87,12 +92,34 @@ struct TrialTile32 {
     uint32_t slot[TILE_TRI];
 };
 
-// compensated shared-memory accumulation: S += c exactly up to the rounding of E
-__device__ __forceinline__ void comp_add(float* S, float* E, int idx, float c) {
-    const float old = atomicAdd(&S[idx], c);
-    float s, e;
-    two_sum(old, c, s, e);  // s is the value the atomic stored; e its exact rounding error
-    if (e != 0.0f) atomicAdd(&E[idx], e);
+// fixed-point shared-memory accumulation (see the header): value v at scale 2^e
+constexpr int FX_LO_BITS = 21;
+constexpr float FX_LIMIT = 4398046511104.0f;  // 2^42: twice the bound that sets the scale
+
+__device__ __forceinline__ void fx_add(int32_t* H, uint32_t* L, int idx, float v, float scale, int* overflow) {
+    const float c = v * scale;
+    if (!(fabsf(c) < FX_LIMIT)) {  // the bound was violated (or v is not finite)
+        *overflow = 1;
+        return;
+    }
+    const long long q = __float2ll_rn(c);
+    if (q == 0) return;
+    atomicAdd(&L[idx], (uint32_t)(q & ((1ll << FX_LO_BITS) - 1)));
+    atomicAdd(&H[idx], (int32_t)(q >> FX_LO_BITS));
+}
+
+// largest |v| of a positive float kept as its bit pattern (monotone for x >= 0)
+__device__ __forceinline__ void smax(float* a, float v) { atomicMax(reinterpret_cast<int*>(a), __float_as_int(v)); }
+__device__ __forceinline__ void smin(float* a, float v) { atomicMin(reinterpret_cast<int*>(a), __float_as_int(v)); }
+
+// true for a regular (non-touching) pair of the tile pair (it, is)
+__device__ __forceinline__ bool regular_pair(int it, int is, int tl, int sl, const int32_t (*testv)[3],
+                                             const TrialTile32* trial) {
+    if (it == is && tl >= sl) return false;
+    const int32_t ta = testv[tl][0], tb = testv[tl][1], tc = testv[tl][2];
+    const int32_t sa = trial->v[0][sl], sb = trial->v[1][sl], sc = trial->v[2][sl];
+    return !((ta == sa) | (ta == sb) | (ta == sc) | (tb == sa) | (tb == sb) | (tb == sc) | (tc == sa) |
+             (tc == sb) | (tc == sc));
 }
 
 template <bool CK>
@@ -100,23 +127,30 @@ __global__ void __launch_bounds__(NT32, 1)
 k_regular32(const TriRec32* __restrict__ rec, const int32_t* __restrict__ tverts, const uint32_t* __restrict__ tslots,
             const int32_t* __restrict__ tstart, const int32_t* __restrict__ vstart,
             const int32_t* __restrict__ tvert, KP32 P, float2* __restrict__ Vm, float2* __restrict__ Km,
-            float2* __restrict__ Tm, float2* __restrict__ Dm) {
+            float2* __restrict__ Tm, float2* __restrict__ Dm, int* __restrict__ err) {
     const int it = blockIdx.y, is = blockIdx.x;
     if (it > is) return;
     extern __shared__ float smem[];
-    // accumulation slabs: [op V,K,T,D][re,im][S,E][TILE_NV * TILE_NV]
+    // accumulation slabs: [op V,K,T,D][re,im][high int32 | low uint32][TILE_NV * TILE_NV]
     constexpr int SLAB = TILE_NV * TILE_NV;
-    float* acc = smem;
+    int32_t* acc = reinterpret_cast<int32_t*>(smem);
     TriRec32* test = reinterpret_cast<TriRec32*>(smem + 16 * SLAB);
     TrialTile32* trial = reinterpret_cast<TrialTile32*>(test + TILE_TRI);
     __shared__ int32_t testv[TILE_TRI][3];
     __shared__ uint32_t testslot[TILE_TRI];
     __shared__ int32_t vI[TILE_NV], vJ[TILE_NV];
+    __shared__ float rho_t[TILE_TRI], rho_s[TILE_TRI];
+    // bound factors: [0] min r, [1] max r, [2..3] max weight sum, [4..5] max area, [6..7] max |curl|
+    __shared__ float bnd[8];
+    __shared__ float s_scale, s_inv_scale;
+    __shared__ int s_overflow;
 
     const int t0 = tstart[it], nI = tstart[it + 1] - t0;
     const int s0 = tstart[is], nJ = tstart[is + 1] - s0;
     const int nvI = vstart[it + 1] - vstart[it], nvJ = vstart[is + 1] - vstart[is];
-    for (int e = threadIdx.x; e < 16 * SLAB; e += NT32) acc[e] = 0.0f;
+    for (int e = threadIdx.x; e < 16 * SLAB; e += NT32) acc[e] = 0;
+    if (threadIdx.x < 8) bnd[threadIdx.x] = threadIdx.x == 0 ? 3.0e38f : 0.0f;
+    if (threadIdx.x == 0) s_overflow = 0;
     {
         const float* src = reinterpret_cast<const float*>(rec + t0);
         float* dst = reinterpret_cast<float*>(test);
@@ -143,17 +177,91 @@ k_regular32(const TriRec32* __restrict__ rec, const int32_t* __restrict__ tverts
     }
     __syncthreads();
 
+    // ---- bound of every value this CTA produces, and the fixed-point scale
+    if (threadIdx.x < 2 * TILE_TRI) {  // per-triangle radius, weight sums, area, curls
+        const bool tside = threadIdx.x < TILE_TRI;
+        const int t = tside ? threadIdx.x : threadIdx.x - TILE_TRI;
+        if (t < (tside ? nI : nJ)) {
+            float rho = 0.f, area = 0.f, wmax = 0.f, cmax = 0.f;
+            for (int p = 0; p < 6; ++p) {
+                float u2 = 0.f;
+                for (int d = 0; d < 3; ++d) {
+                    const float u = tside ? test[t].u[p][d] : trial->u[p][d][t];
+                    u2 = fmaf(u, u, u2);
+                }
+                rho = fmaxf(rho, sqrtf(u2));
+            }
+            for (int a = 0; a < 3; ++a) {
+                float w = 0.f, c2 = 0.f;
+                for (int p = 0; p < 6; ++p) w += fabsf(tside ? test[t].wl[p][a] : trial->wl[p][a][t]);
+                for (int d = 0; d < 3; ++d) {
+                    const float c = tside ? test[t].curl[a][d] : trial->curl[a][d][t];
+                    c2 = fmaf(c, c, c2);
+                }
+                area += w;
+                wmax = fmaxf(wmax, w);
+                cmax = fmaxf(cmax, sqrtf(c2));
+            }
+            rho *= 1.0001f;
+            (tside ? rho_t : rho_s)[t] = rho;
+            smax(&bnd[tside ? 2 : 3], wmax);
+            smax(&bnd[tside ? 4 : 5], area);
+            smax(&bnd[tside ? 6 : 7], cmax);
+        }
+    }
+    __syncthreads();
+    for (int pidx = threadIdx.x; pidx < TILE_TRI * TILE_TRI; pidx += NT32) {  // point distances
+        const int tl = pidx / TILE_TRI, sl = pidx % TILE_TRI;
+        if (tl >= nI || sl >= nJ || !regular_pair(it, is, tl, sl, testv, trial)) continue;
+        const TriRec32& tr = test[tl];
+        float D[3], R2 = 0.f;
+        for (int d = 0; d < 3; ++d) {
+            D[d] = (tr.ch[d] - trial->ch[d][sl]) + (tr.cl[d] - trial->cl[d][sl]);
+            R2 = fmaf(D[d], D[d], R2);
+        }
+        const float R = sqrtf(R2), ro = rho_t[tl] + rho_s[sl];
+        float rmin = R - ro;
+        if (rmin < 0.5f * R) {  // near pair: the smallest of its 36 point distances
+            float m2 = 3.0e38f;
+            for (int p = 0; p < 6; ++p)
+                for (int q = 0; q < 6; ++q) {
+                    float r2 = 0.f;
+                    for (int d = 0; d < 3; ++d) {
+                        const float x = D[d] + tr.u[p][d] - trial->u[q][d][sl];
+                        r2 = fmaf(x, x, r2);
+                    }
+                    m2 = fminf(m2, r2);
+                }
+            rmin = 0.999f * sqrtf(m2);
+        }
+        smin(&bnd[0], fmaxf(rmin, 1e-30f));
+        smax(&bnd[1], R + ro);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const float rmin = bnd[0], rmax = bnd[1];
+        const float kabs = sqrtf(P.k_h * P.k_h + P.k_i * P.k_i);
+        const float amp = CK ? expf(fmaxf(0.0f, -P.k_i) * rmax) : 1.0f;
+        const float g = INV_4PI_F / rmin;
+        const float ww = bnd[2] * bnd[3];
+        const float bV = ww * g;
+        const float bK = ww * g * (1.0f + kabs * rmin) / rmin;
+        const float bD = (bnd[6] * bnd[7] * bnd[4] * bnd[5] + kabs * kabs * ww) * g;
+        float B = 2.0f * amp * fmaxf(bV, fmaxf(bK, bD));  // factor 2: FP32 rounding of the values
+        B = fminf(fmaxf(B, 1e-30f), 1e30f);                // also maps NaN (no regular pair) to 1e-30
+        int e = 40 - ilogbf(B) - 1;                        // B < 2^(ilogb B + 1), so |v| 2^e < 2^40
+        e = max(-120, min(120, e));
+        s_scale = ldexpf(1.0f, e);
+        s_inv_scale = ldexpf(1.0f, -e);
+    }
+    __syncthreads();
+    const float scale = s_scale;
+
     const float tp_h = 6.28318548202514648f, tp_l = -1.7484555314695172e-7f;  // 2 pi as hi + lo
     const float inv_tp = 0.159154943091895336f;
     for (int pidx = threadIdx.x; pidx < TILE_TRI * TILE_TRI; pidx += NT32) {
         const int tl = pidx / TILE_TRI, sl = pidx % TILE_TRI;
-        if (tl >= nI || sl >= nJ) continue;
-        if (it == is && tl >= sl) continue;
-        const int32_t ta = testv[tl][0], tb = testv[tl][1], tc = testv[tl][2];
-        const int32_t sa = trial->v[0][sl], sb = trial->v[1][sl], sc = trial->v[2][sl];
-        if ((ta == sa) | (ta == sb) | (ta == sc) | (tb == sa) | (tb == sb) | (tb == sc) | (tc == sa) |
-            (tc == sb) | (tc == sc))
-            continue;  // singular pair
+        if (tl >= nI || sl >= nJ || !regular_pair(it, is, tl, sl, testv, trial)) continue;
         const TriRec32& tr = test[tl];
         // ---- per-pair reference in double-float: D = c_tau - c_sigma, R, exp(i k R)
         float Dh[3], R2h = 0.f, R2l = 0.f;
@@ -280,26 +388,44 @@ k_regular32(const TriRec32* __restrict__ rec, const int32_t* __restrict__ tverts
                                      tr.curl[a][2] * trial->curl[b][2][sl];
                     const float dr = cc * I0r - nn2 * (P.k2r * Vr[a][b] - P.k2i * Vi[a][b]);
                     const float di = cc * I0i - nn2 * (P.k2r * Vi[a][b] + P.k2i * Vr[a][b]);
-                    const float vals[8] = {Vr[a][b], Vi[a][b], Kr[a][b], Ki[a][b], Tr[a][b], Ti[a][b], dr, di};
-#pragma unroll
-                    for (int o = 0; o < 8; ++o) {
-                        float* S = acc + (2 * o) * SLAB;
-                        comp_add(S, S + SLAB, idx, vals[o]);
-                    }
+                    // slab of value o: high words at acc + 2 o SLAB, low words SLAB further
+                    auto put = [&](int o, float v) {
+                        int32_t* H = acc + (2 * o) * SLAB;
+                        fx_add(H, reinterpret_cast<uint32_t*>(H + SLAB), idx, v, scale, &s_overflow);
+                    };
+                    put(0, Vr[a][b]);
+                    put(1, Vi[a][b]);
+                    put(2, Kr[a][b]);
+                    put(3, Ki[a][b]);
+                    put(4, Tr[a][b]);
+                    put(5, Ti[a][b]);
+                    put(6, dr);
+                    put(7, di);
                 }
             }
         }
     }
     __syncthreads();
-    // flush: S + E of every touched (i, j) to the global matrices, both orientations
+    if (s_overflow) {  // cannot happen for finite inputs if the bound holds; reported, tile not written
+        if (threadIdx.x == 0) atomicOr(err, 1);
+        return;
+    }
+    // flush: high * 2^21 + low, unscaled, of every touched (i, j) to the global matrices, both orientations
+    const float inv_scale = s_inv_scale;
     const int64_t N = P.n;
     for (int e = threadIdx.x; e < nvI * nvJ; e += NT32) {
         const int li = e / nvJ, lj = e % nvJ;
         const int idx = li * TILE_NV + lj;
         float v[8];
+        bool any = false;
 #pragma unroll
-        for (int o = 0; o < 8; ++o) v[o] = acc[(2 * o) * SLAB + idx] + acc[(2 * o + 1) * SLAB + idx];
-        if (v[0] == 0.f && v[1] == 0.f && v[2] == 0.f && v[3] == 0.f && v[4] == 0.f && v[5] == 0.f) continue;
+        for (int o = 0; o < 8; ++o) {
+            const long long q = ((long long)acc[(2 * o) * SLAB + idx] << FX_LO_BITS) +
+                                (long long)reinterpret_cast<const uint32_t*>(acc)[(2 * o + 1) * SLAB + idx];
+            any = any || q != 0;
+            v[o] = __ll2float_rn(q) * inv_scale;
+        }
+        if (!any) continue;
         const int64_t i = vI[li], j = vJ[lj];
         const int64_t ij = i * N + j, ji = j * N + i;
         if (Vm) { atomicAdd(&Vm[ij], make_float2(v[0], v[1])); atomicAdd(&Vm[ji], make_float2(v[0], v[1])); }
@@ -355,14 +481,25 @@ bem_status assemble_regular_fp32(const bem_grid* g, double k_re, double k_im, fl
     BEM_CUDA_TRY(cudaFuncSetAttribute(k_regular32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)g->ntile, (unsigned)g->ntile);
     const bool ck = k_im != 0.0;
+    DevBuf flag;
+    BEM_TRY(flag.alloc(sizeof(int), s));
+    BEM_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
     if (ck)
         BEM_LAUNCH(k_regular32<true>, grid, NT32, smem, s, g->rec32.as<TriRec32>(), g->t_verts.as<int32_t>(),
                    g->t_slots.as<uint32_t>(), g->tile_tstart.as<int32_t>(), g->tile_vstart.as<int32_t>(),
-                   g->tile_vert.as<int32_t>(), P, V, K, T, D);
+                   g->tile_vert.as<int32_t>(), P, V, K, T, D, flag.as<int>());
     else
         BEM_LAUNCH(k_regular32<false>, grid, NT32, smem, s, g->rec32.as<TriRec32>(), g->t_verts.as<int32_t>(),
                    g->t_slots.as<uint32_t>(), g->tile_tstart.as<int32_t>(), g->tile_vstart.as<int32_t>(),
-                   g->tile_vert.as<int32_t>(), P, V, K, T, D);
+                   g->tile_vert.as<int32_t>(), P, V, K, T, D, flag.as<int>());
+    int h_flag = 0;
+    BEM_CUDA_TRY(cudaMemcpyAsync(&h_flag, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h_flag) {
+        set_error("FP32 assembly: a value exceeded the fixed-point range of its tile (non-finite input or "
+                  "a degenerate grid)");
+        return BEM_E_NONFINITE;
+    }
     return BEM_OK;
 }
 
