@@ -30,7 +30,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <functional>
+#include <vector>
 
 namespace bem {
 
@@ -336,27 +338,132 @@ __global__ void k_to_c64(const double2* __restrict__ x, int64_t n, float2* __res
     if (e < n) y[e] = make_float2((float)x[e].x, (float)x[e].y);
 }
 
-// mortar part: entries (r, c, p) of P_ie; z1[c] += a p v_i[r], z2[c] += b p w_i[r],
-// z3[r] += c p v_e[c], z4[r] += d p w_e[c]; blockIdx.y = right-hand side
-__global__ void k_transfer(const int32_t* __restrict__ row, const int32_t* __restrict__ col,
-                           const double* __restrict__ val, int64_t nnz, int64_t Ne, int64_t Ni, int64_t n,
-                           double4 coef, const double2* __restrict__ xb, double2* __restrict__ zb) {
+// ---------------------------------------------------------------- mortar transfer
+// P_ie (rows: interior vertices, columns: exterior vertices) and P_ei = P_ie^T in
+// CSR form, built once per solve from the COO list of the clipping kernel: zero
+// entries are dropped and the duplicates of one (row, column) -- one per clipped
+// triangle pair -- are summed in a fixed order (sorted by value), so that the
+// product does not depend on the order in which the clipping kernel wrote them.
+__global__ void k_csr_count(const int32_t* __restrict__ key, const double* __restrict__ val, int64_t nnz,
+                            int32_t* __restrict__ cnt) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= nnz) return;
-    const double p = val[e];
-    if (p == 0.0) return;
-    const double2* x = xb + blockIdx.y * n;
-    double2* z = zb + blockIdx.y * n;
-    const int64_t r = row[e], c = col[e];
-    const double2 vi = x[2 * Ne + r], wi = x[2 * Ne + Ni + r], ve = x[c], we = x[Ne + c];
-    atomicAdd(&z[c].x, coef.x * p * vi.x);
-    atomicAdd(&z[c].y, coef.x * p * vi.y);
-    atomicAdd(&z[Ne + c].x, coef.y * p * wi.x);
-    atomicAdd(&z[Ne + c].y, coef.y * p * wi.y);
-    atomicAdd(&z[2 * Ne + r].x, coef.z * p * ve.x);
-    atomicAdd(&z[2 * Ne + r].y, coef.z * p * ve.y);
-    atomicAdd(&z[2 * Ne + Ni + r].x, coef.w * p * we.x);
-    atomicAdd(&z[2 * Ne + Ni + r].y, coef.w * p * we.y);
+    if (e < nnz && val[e] != 0.0) atomicAdd(&cnt[key[e]], 1);
+}
+
+// exclusive prefix sum of cnt[0, n) into out[0, n]; out[n] = total (one block of 1024 threads)
+__global__ void __launch_bounds__(1024) k_scan(const int32_t* __restrict__ cnt, int64_t n, int32_t* __restrict__ out) {
+    __shared__ int32_t part[1024];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const int32_t v = i < n ? cnt[i] : 0;
+        part[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan in shared memory
+            const int32_t t = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+            __syncthreads();
+            part[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < n) out[i] = carry + part[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += part[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+__global__ void k_csr_scatter(const int32_t* __restrict__ key, const int32_t* __restrict__ other,
+                              const double* __restrict__ val, int64_t nnz, const int32_t* __restrict__ start,
+                              int32_t* __restrict__ fill, int32_t* __restrict__ oc, double* __restrict__ ov) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nnz || val[e] == 0.0) return;
+    const int32_t k = key[e];
+    const int32_t p = start[k] + atomicAdd(&fill[k], 1);
+    oc[p] = other[e];
+    ov[p] = val[e];
+}
+
+// per row: sort by (column, value), sum equal columns in that order, compact in place
+__global__ void k_csr_merge(const int32_t* __restrict__ start, int64_t rows, int32_t* __restrict__ oc,
+                            double* __restrict__ ov, int32_t* __restrict__ mcnt) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= rows) return;
+    const int32_t b = start[k], e = start[k + 1];
+    for (int32_t i = b + 1; i < e; ++i) {
+        const int32_t c = oc[i];
+        const double v = ov[i];
+        int32_t j = i - 1;
+        while (j >= b && (oc[j] > c || (oc[j] == c && ov[j] > v))) {
+            oc[j + 1] = oc[j];
+            ov[j + 1] = ov[j];
+            --j;
+        }
+        oc[j + 1] = c;
+        ov[j + 1] = v;
+    }
+    int32_t w = b;
+    for (int32_t i = b; i < e;) {
+        const int32_t c = oc[i];
+        double sum = 0.0;
+        while (i < e && oc[i] == c) sum += ov[i++];
+        oc[w] = c;
+        ov[w] = sum;
+        ++w;
+    }
+    mcnt[k] = w - b;
+}
+
+__global__ void k_csr_compact(const int32_t* __restrict__ start, const int32_t* __restrict__ rp, int64_t rows,
+                              const int32_t* __restrict__ oc, const double* __restrict__ ov, int32_t* __restrict__ ci,
+                              double* __restrict__ v) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= rows) return;
+    const int32_t src = start[k], dst = rp[k], len = rp[k + 1] - rp[k];
+    for (int32_t i = 0; i < len; ++i) {
+        ci[dst + i] = oc[src + i];
+        v[dst + i] = ov[src + i];
+    }
+}
+
+struct TransferCsr {
+    const int32_t *prp, *pci;  // P_ie: rows = interior vertices
+    const double* pv;
+    const int32_t *trp, *tci;  // P_ei = P_ie^T: rows = exterior vertices
+    const double* tv;
+    int64_t Ne, Ni, n;
+    double ca, cb, cc, cd;  // z1 += ca P_ei v_i, z2 += cb P_ei w_i, z3 += cc P_ie v_e, z4 += cd P_ie w_e
+};
+
+// one thread per row of z (blockIdx.y = right-hand side); no atomics
+__global__ void k_transfer(TransferCsr T, const double2* __restrict__ xb, double2* __restrict__ zb) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= T.n) return;
+    const double2* x = xb + blockIdx.y * T.n;
+    double2* z = zb + blockIdx.y * T.n;
+    const bool ext = g < 2 * T.Ne;
+    const int32_t* rp = ext ? T.trp : T.prp;
+    const int32_t* ci = ext ? T.tci : T.pci;
+    const double* v = ext ? T.tv : T.pv;
+    int64_t row, src;
+    double c;
+    if (g < T.Ne) { row = g; src = 2 * T.Ne; c = T.ca; }
+    else if (g < 2 * T.Ne) { row = g - T.Ne; src = 2 * T.Ne + T.Ni; c = T.cb; }
+    else if (g < 2 * T.Ne + T.Ni) { row = g - 2 * T.Ne; src = 0; c = T.cc; }
+    else { row = g - 2 * T.Ne - T.Ni; src = T.Ne; c = T.cd; }
+    double sr = 0.0, si = 0.0;
+    for (int32_t e = rp[row]; e < rp[row + 1]; ++e) {
+        const double p = v[e];
+        const double2 xx = x[src + ci[e]];
+        sr = fma(p, xx.x, sr);
+        si = fma(p, xx.y, si);
+    }
+    double2 zz = z[g];
+    zz.x = fma(c, sr, zz.x);
+    zz.y = fma(c, si, zz.y);
+    z[g] = zz;
 }
 
 // ---------------------------------------------------------------- mass inverse
@@ -429,38 +536,59 @@ __global__ void k_cheb_step(MassPair M, const double2* __restrict__ dk, double2*
 // ---------------------------------------------------------------- GMRES kernels
 // Krylov basis: vector i of right-hand side r at V + (i * R + r) * n.
 // Hessenberg of r: column-major, H + r * ldh * ldh, column j at + j * ldh.
-constexpr int RED_BLOCKS = 64;
+// Inner products conj(V_{i,r}) . w_r for i < m: the rows are cut into `nblk`
+// contiguous chunks; warp (chunk, i) of grid (nblk, ceil(m / 8), R) sums its chunk
+// with eight independent accumulators per lane (eight loads in flight), reduces
+// within the warp and writes partial[((r * m) + i) * nblk + chunk].
+constexpr int DOT_ROWS = 256;         // target rows per chunk
+constexpr int DOT_MAX_BLOCKS = 1216;  // 8 per SM
 
-// partial[((r * m) + i) * RED_BLOCKS + bx] = chunk of conj(V_{i,r}) w_r
-__global__ void k_dots_partial(const double2* __restrict__ Vb, int64_t n, int R, int m,
-                               const double2* __restrict__ w, double2* __restrict__ partial) {
-    const int i = blockIdx.y, r = blockIdx.z;
-    const double2* __restrict__ v = Vb + ((int64_t)i * R + r) * n;
+int dot_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(DOT_MAX_BLOCKS, (n + DOT_ROWS - 1) / DOT_ROWS)); }
+
+__global__ void __launch_bounds__(256) k_dots_partial(const double2* __restrict__ Vb, int64_t n, int R, int m,
+                                                      const double2* __restrict__ w, int nblk,
+                                                      double2* __restrict__ partial) {
+    const int r = blockIdx.z, b = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (i >= m) return;
+    const int64_t chunk = (n + nblk - 1) / nblk;
+    const int64_t e0 = b * chunk, e1 = min(n, e0 + chunk);
     const double2* __restrict__ wr = w + (int64_t)r * n;
-    double2 s = make_double2(0, 0);
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const double2 a = v[e], b = wr[e];
-        s.x += a.x * b.x + a.y * b.y;
-        s.y += a.x * b.y - a.y * b.x;
+    const double2* __restrict__ v = Vb + ((int64_t)i * R + r) * n;
+    double2 s[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s[u] = make_double2(0, 0);
+    int64_t e = e0 + lane;
+    for (; e + 224 < e1; e += 256) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const double2 a = v[e + 32 * u], c = wr[e + 32 * u];
+            s[u].x = fma(a.x, c.x, fma(a.y, c.y, s[u].x));
+            s[u].y = fma(a.x, c.y, fma(-a.y, c.x, s[u].y));
+        }
     }
-    __shared__ double2 sh[8];
-    s = warp_sum2(s);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double2 t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : make_double2(0, 0);
-        t = warp_sum2(t);
-        if (threadIdx.x == 0) partial[((int64_t)r * m + i) * RED_BLOCKS + blockIdx.x] = t;
+    for (; e < e1; e += 32) {
+        const double2 a = v[e], c = wr[e];
+        s[0].x = fma(a.x, c.x, fma(a.y, c.y, s[0].x));
+        s[0].y = fma(a.x, c.y, fma(-a.y, c.x, s[0].y));
     }
+#pragma unroll
+    for (int u = 1; u < 8; ++u) {
+        s[0].x += s[u].x;
+        s[0].y += s[u].y;
+    }
+    const double2 t = warp_sum2(s[0]);
+    if (lane == 0) partial[((int64_t)r * m + i) * nblk + b] = t;
 }
 
 // out[r * ostride + i] = sum_b partial[r][i][b]  (+= when accumulate)
-__global__ void k_dots_final(const double2* __restrict__ partial, int m, double2* __restrict__ out,
+__global__ void k_dots_final(const double2* __restrict__ partial, int m, int nblk, double2* __restrict__ out,
                              int64_t ostride, int accumulate) {
     const int i = blockIdx.x, r = blockIdx.y;
     double2 s = make_double2(0, 0);
-    for (int b = threadIdx.x; b < RED_BLOCKS; b += 32) {
-        const double2 p = partial[((int64_t)r * m + i) * RED_BLOCKS + b];
+    for (int b = threadIdx.x; b < nblk; b += 32) {
+        const double2 p = partial[((int64_t)r * m + i) * nblk + b];
         s.x += p.x;
         s.y += p.y;
     }
@@ -472,20 +600,34 @@ __global__ void k_dots_final(const double2* __restrict__ partial, int m, double2
     }
 }
 
-// w_r -= sum_{i<m} h_r[i] V_{i,r}   or (overwrite) x_r = sum_{i<m_r} y_r[i] V_{i,r}
+// w_r -= sum_{i<m} h_r[i] V_{i,r}   or (overwrite) x_r = sum_{i<m_r} y_r[i] V_{i,r};
+// eight independent accumulators keep eight basis loads in flight per thread
 __global__ void k_combine(const double2* __restrict__ Vb, int64_t n, int R, int m, const int* __restrict__ mr,
                           const double2* __restrict__ h, int64_t hstride, double2* __restrict__ w, int overwrite) {
     const int r = blockIdx.y;
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n) return;
     const int mm = mr ? mr[r] : m;
-    double2 s = make_double2(0, 0);
-    for (int i = 0; i < mm; ++i) s = cfma(h[r * hstride + i], Vb[((int64_t)i * R + r) * n + e], s);
+    const double2* __restrict__ hr = h + r * hstride;
+    double2 s[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s[u] = make_double2(0, 0);
+    int i = 0;
+    for (; i + 8 <= mm; i += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s[u] = cfma(hr[i + u], Vb[((int64_t)(i + u) * R + r) * n + e], s[u]);
+    }
+    for (; i < mm; ++i) s[0] = cfma(hr[i], Vb[((int64_t)i * R + r) * n + e], s[0]);
+#pragma unroll
+    for (int u = 1; u < 8; ++u) {
+        s[0].x += s[u].x;
+        s[0].y += s[u].y;
+    }
     double2* wr = w + (int64_t)r * n;
-    if (overwrite) wr[e] = s;
+    if (overwrite) wr[e] = s[0];
     else {
-        const double2 t = wr[e];
-        wr[e] = make_double2(t.x - s.x, t.y - s.y);
+        const double2 q = wr[e];
+        wr[e] = make_double2(q.x - s[0].x, q.y - s[0].y);
     }
 }
 
@@ -510,84 +652,6 @@ __global__ void k_normalize(const double2* __restrict__ w, int64_t n, const doub
     v[r * vstride + e] = make_double2(w[(int64_t)r * n + e].x * inv, w[(int64_t)r * n + e].y * inv);
 }
 
-// Givens update of column j of every Hessenberg (one thread per right-hand side)
-__global__ void k_givens(double2* __restrict__ Hb, int64_t ldh, int j, double* __restrict__ csb,
-                         double2* __restrict__ snb, double2* __restrict__ gb, int64_t gstride,
-                         double* __restrict__ res, int R) {
-    const int r = threadIdx.x;
-    if (r >= R) return;
-    double2* h = Hb + (int64_t)r * ldh * ldh + (int64_t)j * ldh;
-    double* cs = csb + r * gstride;
-    double2* sn = snb + r * gstride;
-    double2* g = gb + r * gstride;
-    for (int i = 0; i < j; ++i) {
-        const double2 a = h[i], b = h[i + 1];
-        const double2 t = make_double2(cs[i] * a.x + (sn[i].x * b.x - sn[i].y * b.y),
-                                       cs[i] * a.y + (sn[i].x * b.y + sn[i].y * b.x));
-        // h[i+1] = -conj(sn) a + cs b
-        const double2 u = make_double2(-(sn[i].x * a.x + sn[i].y * a.y) + cs[i] * b.x,
-                                       -(sn[i].x * a.y - sn[i].y * a.x) + cs[i] * b.y);
-        h[i] = t;
-        h[i + 1] = u;
-    }
-    const double2 a = h[j], b = h[j + 1];
-    const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
-    double c;
-    double2 s, rr;
-    if (aa == 0.0) {
-        c = 0.0;
-        s = make_double2(1.0, 0.0);
-        rr = b;
-    } else {
-        const double t = hypot(aa, bb);
-        c = aa / t;
-        const double2 ph = make_double2(a.x / aa, a.y / aa);
-        s = make_double2((ph.x * b.x + ph.y * b.y) / t, (ph.y * b.x - ph.x * b.y) / t);  // ph conj(b) / t
-        rr = make_double2(ph.x * t, ph.y * t);
-    }
-    cs[j] = c;
-    sn[j] = s;
-    h[j] = rr;
-    h[j + 1] = make_double2(0.0, 0.0);
-    const double2 gj = g[j];
-    g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));  // -conj(s) g_j
-    g[j] = make_double2(c * gj.x, c * gj.y);
-    res[r] = hypot(g[j + 1].x, g[j + 1].y);
-}
-
-// y_r = H_r(0:m_r,0:m_r)^-1 g_r(0:m_r), column-oriented back substitution, one block per r
-__global__ void k_backsolve(const double2* __restrict__ Hb, int64_t ldh, const int* __restrict__ mr,
-                            const double2* __restrict__ gb, int64_t gstride, double2* __restrict__ yb,
-                            double2* __restrict__ workb) {
-    const int r = blockIdx.x;
-    const int m = mr[r];
-    const double2* H = Hb + (int64_t)r * ldh * ldh;
-    const double2* g = gb + r * gstride;
-    double2* y = yb + r * gstride;
-    double2* work = workb + r * gstride;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) work[i] = g[i];
-    __syncthreads();
-    __shared__ double2 yc;
-    for (int c = m - 1; c >= 0; --c) {
-        if (threadIdx.x == 0) {
-            const double2 d = H[(int64_t)c * ldh + c];
-            const double den = d.x * d.x + d.y * d.y;
-            const double2 wc = work[c];
-            yc = den > 0.0 ? make_double2((wc.x * d.x + wc.y * d.y) / den, (wc.y * d.x - wc.x * d.y) / den)
-                           : make_double2(0.0, 0.0);
-            y[c] = yc;
-        }
-        __syncthreads();
-        const double2 yy = yc;
-        for (int i = threadIdx.x; i < c; i += blockDim.x) {
-            const double2 hic = H[(int64_t)c * ldh + i];
-            work[i].x -= hic.x * yy.x - hic.y * yy.y;
-            work[i].y -= hic.x * yy.y + hic.y * yy.x;
-        }
-        __syncthreads();
-    }
-}
-
 // y = a - b;  x += d (whole blocks)
 __global__ void k_sub(const double2* __restrict__ a, const double2* __restrict__ b, int64_t n,
                       double2* __restrict__ y) {
@@ -609,13 +673,6 @@ struct MassOp {
     double2 *r = nullptr, *dA = nullptr, *dB = nullptr;  // workspaces [R * n]
 };
 
-struct TransferOp {
-    const int32_t *prow = nullptr, *pcol = nullptr;
-    const double* pval = nullptr;
-    int64_t pnnz = 0;
-    double4 coef{};
-};
-
 // M^-1 on the four blocks of R columns, Chebyshev on the Jacobi-scaled mass matrices
 bem_status mass_solve(const MassOp& op, const double2* z, double2* y, int R, cudaStream_t s, int steps) {
     const int64_t n = op.M.n;
@@ -634,11 +691,40 @@ bem_status mass_solve(const MassOp& op, const double2* z, double2* y, int R, cud
     return BEM_OK;
 }
 
-bem_status transfer_add(const TransferOp& t, int64_t Ne, int64_t Ni, int64_t n, int R, const double2* x,
-                        double2* z, cudaStream_t s) {
-    if (t.pnnz > 0)
-        BEM_LAUNCH(k_transfer, dim3(blocks_for(t.pnnz, 256), R), 256, 0, s, t.prow, t.pcol, t.pval, t.pnnz, Ne, Ni,
-                   n, t.coef, x, z);
+struct CsrBuf {
+    DevBuf rp, ci, v;
+};
+
+// CSR of the COO list (key, other, val) with `rows` rows keyed by `key`
+bem_status build_csr(const int32_t* key, const int32_t* other, const double* val, int64_t nnz, int64_t rows,
+                     CsrBuf& out, cudaStream_t s) {
+    DevBuf cnt, start, fill, oc, ov;
+    const size_t cap = (size_t)std::max<int64_t>(nnz, 1);
+    BEM_TRY(cnt.alloc(rows * 4, s));
+    BEM_TRY(start.alloc((rows + 1) * 4, s));
+    BEM_TRY(fill.alloc(rows * 4, s));
+    BEM_TRY(oc.alloc(cap * 4, s));
+    BEM_TRY(ov.alloc(cap * 8, s));
+    BEM_TRY(out.rp.alloc((rows + 1) * 4, s));
+    BEM_TRY(out.ci.alloc(cap * 4, s));
+    BEM_TRY(out.v.alloc(cap * 8, s));
+    BEM_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, rows * 4, s));
+    BEM_CUDA_TRY(cudaMemsetAsync(fill.p, 0, rows * 4, s));
+    if (nnz > 0) BEM_LAUNCH(k_csr_count, blocks_for(nnz, 256), 256, 0, s, key, val, nnz, cnt.as<int32_t>());
+    BEM_LAUNCH(k_scan, 1, 1024, 0, s, cnt.as<int32_t>(), rows, start.as<int32_t>());
+    if (nnz > 0)
+        BEM_LAUNCH(k_csr_scatter, blocks_for(nnz, 256), 256, 0, s, key, other, val, nnz, start.as<int32_t>(),
+                   fill.as<int32_t>(), oc.as<int32_t>(), ov.as<double>());
+    BEM_LAUNCH(k_csr_merge, blocks_for(rows, 128), 128, 0, s, start.as<int32_t>(), rows, oc.as<int32_t>(),
+               ov.as<double>(), cnt.as<int32_t>());
+    BEM_LAUNCH(k_scan, 1, 1024, 0, s, cnt.as<int32_t>(), rows, out.rp.as<int32_t>());
+    BEM_LAUNCH(k_csr_compact, blocks_for(rows, 128), 128, 0, s, start.as<int32_t>(), out.rp.as<int32_t>(), rows,
+               oc.as<int32_t>(), ov.as<double>(), out.ci.as<int32_t>(), out.v.as<double>());
+    return BEM_OK;
+}
+
+bem_status transfer_add(const TransferCsr& t, int R, const double2* x, double2* z, cudaStream_t s) {
+    BEM_LAUNCH(k_transfer, dim3(blocks_for(t.n, 256), R), 256, 0, s, t, x, z);
     return BEM_OK;
 }
 
@@ -649,19 +735,45 @@ int gemm_width(int R) { return R <= 1 ? 1 : R <= 2 ? 2 : R <= 4 ? 4 : 8; }
 using Apply = std::function<bem_status(const double2* in, double2* out, int R)>;
 using StopCheck = std::function<bem_status()>;
 
+// iterations a host check of the residual trails the launches by (the GPU keeps
+// this many iterations queued; at most this many are computed past convergence)
+constexpr int GMRES_LAG = 2;
+constexpr int GMRES_SLOTS = GMRES_LAG + 2;
+
+using cplx = std::complex<double>;
+
+// Arnoldi state on the device (basis, Hessenberg columns, reductions) and the small
+// least-squares problem on the host: each new Hessenberg column is copied to pinned
+// memory and the Givens QR, the residual estimate and the final back substitution
+// are done there (O(j) sequential FP64 work per iteration, microseconds on a CPU core,
+// but a long dependent chain for one GPU thread).
 struct GmresWork {
-    int maxit = 0, R = 0, RW = 0;
+    int maxit = 0, R = 0, RW = 0, nblk = 0;
     int64_t n = 0, ldh = 0, gstride = 0;
-    DevBuf Vb, H, cs, sn, g, resd, partial, hbuf, y, work, w, nrm, mr;
-    double* h_res = nullptr;  // pinned, [R]
+    DevBuf Vb, H, partial, hbuf, y, w, nrm, mr;
+    double2* h_nrm = nullptr;  // pinned, [R]
+    double2* h_col = nullptr;  // pinned, [GMRES_SLOTS][R][maxit + 2]: copied Hessenberg columns
+    double2* h_y = nullptr;    // pinned, [R][gstride]: least-squares solutions
+    int* h_mr = nullptr;       // pinned, [R]
+    cudaEvent_t ev[GMRES_SLOTS] = {};
+    cudaStream_t stream = nullptr;
     ~GmresWork() {
-        if (h_res) cudaFreeHost(h_res);
+        // an early return (cancel, deadline, error) may leave copies into pinned memory queued
+        if (stream) cudaStreamSynchronize(stream);
+        if (h_nrm) cudaFreeHost(h_nrm);
+        if (h_col) cudaFreeHost(h_col);
+        if (h_y) cudaFreeHost(h_y);
+        if (h_mr) cudaFreeHost(h_mr);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
     }
     bem_status init(int maxit_, int64_t n_, int R_, cudaStream_t s) {
         maxit = maxit_;
         n = n_;
         R = R_;
+        stream = s;
         RW = gemm_width(R_);
+        nblk = dot_blocks(n_);
         ldh = maxit + 1;
         gstride = maxit + 2;
         // (maxit + 1) basis blocks of R columns, plus RW - R spare columns read by the
@@ -670,37 +782,100 @@ struct GmresWork {
         BEM_TRY(Vb.alloc(vb, s));
         BEM_CUDA_TRY(cudaMemsetAsync(Vb.p, 0, vb, s));
         BEM_TRY(H.alloc((size_t)R * ldh * ldh * 16, s));
-        BEM_TRY(cs.alloc((size_t)R * gstride * 8, s));
-        BEM_TRY(sn.alloc((size_t)R * gstride * 16, s));
-        BEM_TRY(g.alloc((size_t)R * gstride * 16, s));
-        BEM_TRY(resd.alloc(R * 8, s));
-        BEM_TRY(partial.alloc((size_t)R * (maxit + 1) * RED_BLOCKS * 16, s));
+        BEM_TRY(partial.alloc((size_t)R * (maxit + 1) * nblk * 16, s));
         BEM_TRY(hbuf.alloc((size_t)R * gstride * 16, s));
         BEM_TRY(y.alloc((size_t)R * gstride * 16, s));
-        BEM_TRY(work.alloc((size_t)R * gstride * 16, s));
         BEM_TRY(w.alloc((size_t)R * n * 16, s));
         BEM_TRY(nrm.alloc(R * 16, s));
         BEM_TRY(mr.alloc(R * 4, s));
-        BEM_CUDA_TRY(cudaMallocHost(&h_res, R * 16 + 16));
+        BEM_CUDA_TRY(cudaMallocHost(&h_nrm, (size_t)R * 16));
+        BEM_CUDA_TRY(cudaMallocHost(&h_col, (size_t)GMRES_SLOTS * R * gstride * 16));
+        BEM_CUDA_TRY(cudaMallocHost(&h_y, (size_t)R * gstride * 16));
+        BEM_CUDA_TRY(cudaMallocHost(&h_mr, (size_t)R * 4));
+        for (cudaEvent_t& e : ev) BEM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        return BEM_OK;
+    }
+    // squared norms of the R columns of v (stored back to back) into nrm[r].x
+    bem_status sq_norms(const double2* v, cudaStream_t s) {
+        // with basis width 1 and m = 1, "basis vector 0" of column r is v + r * n
+        BEM_LAUNCH(k_dots_partial, dim3(nblk, 1, R), 256, 0, s, v, n, 1, 1, v, nblk, partial.as<double2>());
+        BEM_LAUNCH(k_dots_final, dim3(1, R), 32, 0, s, partial.as<double2>(), 1, nblk, nrm.as<double2>(), 1, 0);
         return BEM_OK;
     }
 };
 
 // 2-norms of R columns stored back to back -> host
 bem_status norms(GmresWork& W, const double2* v, int R, double* out, cudaStream_t s) {
-    // with "basis" width 1 and index 0, column r is v + r * n
-    BEM_LAUNCH(k_dots_partial, dim3(RED_BLOCKS, 1, R), 256, 0, s, v, W.n, 1, 1, v, W.partial.as<double2>());
-    BEM_LAUNCH(k_dots_final, dim3(1, R), 32, 0, s, W.partial.as<double2>(), 1, W.nrm.as<double2>(), 1, 0);
-    BEM_CUDA_TRY(cudaMemcpyAsync(W.h_res, W.nrm.p, R * 16, cudaMemcpyDeviceToHost, s));
+    BEM_TRY(W.sq_norms(v, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(W.h_nrm, W.nrm.p, R * 16, cudaMemcpyDeviceToHost, s));
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
-    const double2* h = reinterpret_cast<const double2*>(W.h_res);
-    for (int r = 0; r < R; ++r) out[r] = std::sqrt(std::max(h[r].x, 0.0));
+    for (int r = 0; r < R; ++r) out[r] = std::sqrt(std::max(W.h_nrm[r].x, 0.0));
     return BEM_OK;
 }
 
+// Givens QR of one right-hand side's Hessenberg matrix, one column at a time
+struct HostQR {
+    std::vector<std::vector<cplx>> Rc;  // Rc[j][0..j]: column j of the triangular factor
+    std::vector<double> cs;
+    std::vector<cplx> sn, g;
+    void reset(double beta) {
+        Rc.clear();
+        cs.clear();
+        sn.clear();
+        g.assign(1, cplx(beta, 0.0));
+    }
+    // column j (entries 0..j+1); returns |g_{j+1}|, the residual estimate
+    double add_column(const double2* col, int j) {
+        std::vector<cplx> h(j + 2);
+        for (int i = 0; i < j + 2; ++i) h[i] = cplx(col[i].x, col[i].y);
+        for (int i = 0; i < j; ++i) {  // h[i] = c h[i] + s h[i+1];  h[i+1] = -conj(s) h[i] + c h[i+1]
+            const cplx a = h[i], b = h[i + 1];
+            h[i] = cs[i] * a + sn[i] * b;
+            h[i + 1] = -std::conj(sn[i]) * a + cs[i] * b;
+        }
+        const cplx a = h[j], b = h[j + 1];
+        const double aa = std::abs(a), bb = std::abs(b);
+        double c;
+        cplx sv, rr;
+        if (aa == 0.0) {
+            c = 0.0;
+            sv = cplx(1.0, 0.0);
+            rr = b;
+        } else {
+            const double t = std::hypot(aa, bb);
+            const cplx ph = a / aa;
+            c = aa / t;
+            sv = ph * std::conj(b) / t;
+            rr = ph * t;
+        }
+        cs.push_back(c);
+        sn.push_back(sv);
+        h[j] = rr;
+        h.resize(j + 1);
+        Rc.push_back(std::move(h));
+        const cplx gj = g[j];
+        g.push_back(-std::conj(sv) * gj);
+        g[j] = c * gj;
+        return std::abs(g[j + 1]);
+    }
+    // y = R(0:m,0:m)^-1 g(0:m)
+    void solve(int m, double2* y) const {
+        std::vector<cplx> w(g.begin(), g.begin() + m);
+        for (int c = m - 1; c >= 0; --c) {
+            const cplx d = Rc[c][c];
+            const cplx yc = std::norm(d) > 0.0 ? w[c] / d : cplx(0.0, 0.0);
+            y[c] = make_double2(yc.real(), yc.imag());
+            for (int i = 0; i < c; ++i) w[i] -= Rc[c][i] * yc;
+        }
+    }
+};
+
 // Unrestarted GMRES from x0 = 0 on apply(x) = rhs for R columns in lockstep; column
-// r stops counting once its residual estimate is <= tol_abs[r].  Writes x (R
-// columns); returns per-column iterations and final estimates.
+// r stops counting once its residual estimate is <= tol_abs[r].  The Hessenberg
+// column of iteration j is copied to pinned memory and processed GMRES_LAG
+// iterations later, so the host never waits for the GPU to drain; iterations
+// launched past convergence do not touch the columns the solution uses.  Writes x
+// (R columns); returns per-column iterations and final estimates.
 bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs, const double* beta,
                      const double* tol_abs, double2* x, int* iters_out, double* res_out, cudaStream_t s,
                      const StopCheck& stop) {
@@ -708,61 +883,73 @@ bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs
     double2* Vp = W.Vb.as<double2>();
     const dim3 eb(blocks_for(n, 256), R);
     BEM_CUDA_TRY(cudaMemsetAsync(W.H.p, 0, (size_t)R * ldh * ldh * 16, s));
-    BEM_CUDA_TRY(cudaMemsetAsync(W.g.p, 0, (size_t)R * gs * 16, s));
+    std::vector<HostQR> qr(R);
     std::vector<int> it(R, 0);
     std::vector<char> done(R, 0);
     int ndone = 0;
     for (int r = 0; r < R; ++r) {
+        qr[r].reset(beta[r]);
         res_out[r] = beta[r];
         if (!(beta[r] > tol_abs[r])) {
             done[r] = 1;
             ++ndone;
         }
     }
+    int launched = 0, checked = 0;
+    auto check_one = [&]() -> bem_status {  // iteration `checked`, whose copy is enqueued
+        const int slot = checked % GMRES_SLOTS;
+        BEM_CUDA_TRY(cudaEventSynchronize(W.ev[slot]));
+        for (int r = 0; r < R; ++r) {
+            if (done[r]) continue;
+            const double est = qr[r].add_column(W.h_col + ((size_t)slot * R + r) * gs, checked);
+            it[r] = checked + 1;
+            res_out[r] = est;
+            if (!(est > tol_abs[r])) {
+                done[r] = 1;
+                ++ndone;
+            }
+        }
+        ++checked;
+        return BEM_OK;
+    };
     if (ndone < R) {
-        // V_0 = rhs / beta, g_0 = beta (per column)
-        BEM_LAUNCH(k_dots_partial, dim3(RED_BLOCKS, 1, R), 256, 0, s, rhs, n, 1, 1, rhs, W.partial.as<double2>());
-        BEM_LAUNCH(k_dots_final, dim3(1, R), 32, 0, s, W.partial.as<double2>(), 1, W.nrm.as<double2>(), 1, 0);
-        BEM_LAUNCH(k_normalize, eb, 256, 0, s, rhs, n, W.nrm.as<double2>(), Vp, n, W.g.as<double2>(), gs);
+        BEM_TRY(W.sq_norms(rhs, s));  // V_0 = rhs / beta
+        BEM_LAUNCH(k_normalize, eb, 256, 0, s, rhs, n, W.nrm.as<double2>(), Vp, n, nullptr, 0);
         for (int j = 0; j < W.maxit && ndone < R; ++j) {
             double2* vj = Vp + (int64_t)j * R * n;
             BEM_TRY(apply(vj, W.w.as<double2>(), R));
             double2* Hj = W.H.as<double2>() + (int64_t)j * ldh;  // + r * ldh * ldh per column
+            const unsigned gy = (unsigned)((j + 1 + 7) / 8);
             for (int pass = 0; pass < 2; ++pass) {  // CGS2
                 double2* h = pass == 0 ? Hj : W.hbuf.as<double2>();
                 const int64_t hst = pass == 0 ? ldh * ldh : gs;
-                BEM_LAUNCH(k_dots_partial, dim3(RED_BLOCKS, j + 1, R), 256, 0, s, Vp, n, R, j + 1,
-                           W.w.as<double2>(), W.partial.as<double2>());
-                BEM_LAUNCH(k_dots_final, dim3(j + 1, R), 32, 0, s, W.partial.as<double2>(), j + 1, h, hst, 0);
+                BEM_LAUNCH(k_dots_partial, dim3(W.nblk, gy, R), 256, 0, s, Vp, n, R, j + 1, W.w.as<double2>(),
+                           W.nblk, W.partial.as<double2>());
+                BEM_LAUNCH(k_dots_final, dim3(j + 1, R), 32, 0, s, W.partial.as<double2>(), j + 1, W.nblk, h, hst, 0);
                 BEM_LAUNCH(k_combine, eb, 256, 0, s, Vp, n, R, j + 1, nullptr, h, hst, W.w.as<double2>(), 0);
             }
             BEM_LAUNCH(k_add_cols, dim3(1, R), 256, 0, s, Hj, ldh * ldh, W.hbuf.as<double2>(), gs, j + 1);
-            BEM_LAUNCH(k_dots_partial, dim3(RED_BLOCKS, 1, R), 256, 0, s, W.w.as<double2>(), n, 1, 1,
-                       W.w.as<double2>(), W.partial.as<double2>());
-            BEM_LAUNCH(k_dots_final, dim3(1, R), 32, 0, s, W.partial.as<double2>(), 1, W.nrm.as<double2>(), 1, 0);
+            BEM_TRY(W.sq_norms(W.w.as<double2>(), s));
             BEM_LAUNCH(k_normalize, eb, 256, 0, s, W.w.as<double2>(), n, W.nrm.as<double2>(),
                        Vp + (int64_t)(j + 1) * R * n, n, Hj + j + 1, ldh * ldh);
-            BEM_LAUNCH(k_givens, 1, 32, 0, s, W.H.as<double2>(), ldh, j, W.cs.as<double>(), W.sn.as<double2>(),
-                       W.g.as<double2>(), gs, W.resd.as<double>(), R);
-            BEM_CUDA_TRY(cudaMemcpyAsync(W.h_res, W.resd.p, R * 8, cudaMemcpyDeviceToHost, s));
-            BEM_CUDA_TRY(cudaStreamSynchronize(s));
-            for (int r = 0; r < R; ++r) {
-                if (done[r]) continue;
-                it[r] = j + 1;
-                res_out[r] = W.h_res[r];
-                if (!(W.h_res[r] > tol_abs[r])) {
-                    done[r] = 1;
-                    ++ndone;
-                }
-            }
+            const int slot = j % GMRES_SLOTS;
+            BEM_CUDA_TRY(cudaMemcpy2DAsync(W.h_col + (size_t)slot * R * gs, gs * 16, Hj, ldh * ldh * 16,
+                                           (size_t)(j + 2) * 16, R, cudaMemcpyDeviceToHost, s));
+            BEM_CUDA_TRY(cudaEventRecord(W.ev[slot], s));
+            launched = j + 1;
+            while (checked < launched - GMRES_LAG && ndone < R) BEM_TRY(check_one());
             if (stop) BEM_TRY(stop());
         }
+        while (checked < launched && ndone < R) BEM_TRY(check_one());
     }
-    BEM_CUDA_TRY(cudaMemcpyAsync(W.mr.p, it.data(), R * 4, cudaMemcpyHostToDevice, s));
-    BEM_LAUNCH(k_backsolve, R, 256, 0, s, W.H.as<double2>(), ldh, W.mr.as<int>(), W.g.as<double2>(), gs,
-               W.y.as<double2>(), W.work.as<double2>());
+    for (int r = 0; r < R; ++r) {
+        W.h_mr[r] = it[r];
+        qr[r].solve(it[r], W.h_y + (size_t)r * gs);
+    }
+    BEM_CUDA_TRY(cudaMemcpyAsync(W.mr.p, W.h_mr, R * 4, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(W.y.p, W.h_y, (size_t)R * gs * 16, cudaMemcpyHostToDevice, s));
     BEM_LAUNCH(k_combine, eb, 256, 0, s, Vp, n, R, 0, W.mr.as<int>(), W.y.as<double2>(), gs, x, 1);
-    BEM_CUDA_TRY(cudaStreamSynchronize(s));  // `it` must outlive the copy
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));  // pinned h_y / h_mr are reused by the next run
     for (int r = 0; r < R; ++r) iters_out[r] = it[r];
     return BEM_OK;
 }
@@ -856,6 +1043,9 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     BEM_TRY(mass_inverse_diag(gi, mvi.as<double>(), dvi.as<double>(), s));
     int64_t pnnz = 0;
     BEM_TRY(mortar_coo(gi, ge, o->center, prow, pcol, pval, &pnnz, s));
+    CsrBuf csr_p, csr_t;  // P_ie and P_ei
+    BEM_TRY(build_csr(prow.as<int32_t>(), pcol.as<int32_t>(), pval.as<double>(), pnnz, Ni, csr_p, s));
+    BEM_TRY(build_csr(pcol.as<int32_t>(), prow.as<int32_t>(), pval.as<double>(), pnnz, Ne, csr_t, s));
     cudaEventRecord(t_mor.b, s);
     // ---- workspaces for batches of RB right-hand sides ---------------------------------
     const int RB = std::min<int>(RMAX, inc->n_rhs);
@@ -873,10 +1063,15 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     mop.M.v[1] = mvi.as<double>(); mop.M.dinv[1] = dvi.as<double>();
     mop.M.Ne = Ne; mop.M.Ni = Ni; mop.M.n = n;
     mop.r = wr.as<double2>(); mop.dA = wa.as<double2>(); mop.dB = wb.as<double2>();
-    TransferOp top;
+    TransferCsr top;
     const double sgn = o->mtf_variant == BEM_MTF_PRINTED ? -1.0 : 1.0;
-    top.prow = prow.as<int32_t>(); top.pcol = pcol.as<int32_t>(); top.pval = pval.as<double>(); top.pnnz = pnnz;
-    top.coef = make_double4(-0.5 * sgn, -0.5 * sgn / rho_ratio, 0.5 * sgn, 0.5 * sgn * rho_ratio);
+    top.prp = csr_p.rp.as<int32_t>(); top.pci = csr_p.ci.as<int32_t>(); top.pv = csr_p.v.as<double>();
+    top.trp = csr_t.rp.as<int32_t>(); top.tci = csr_t.ci.as<int32_t>(); top.tv = csr_t.v.as<double>();
+    top.Ne = Ne; top.Ni = Ni; top.n = n;
+    top.ca = -0.5 * sgn;
+    top.cb = -0.5 * sgn / rho_ratio;
+    top.cc = 0.5 * sgn;
+    top.cd = 0.5 * sgn * rho_ratio;
     double2* z = wz.as<double2>();
     Blocks<double2> B64{};
     Blocks<float2> B32{};
@@ -921,12 +1116,12 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     // S A x in the working precision, and with FP64 arithmetic on the stored matrices
     Apply apply_work = [&](const double2* xin, double2* yout, int R) -> bem_status {
         BEM_TRY(gemm_work(xin, R));
-        BEM_TRY(transfer_add(top, Ne, Ni, n, R, xin, z, s));
+        BEM_TRY(transfer_add(top, R, xin, z, s));
         return mass_solve(mop, z, yout, R, s, mixed ? CHEB_STEPS_INNER : CHEB_STEPS);
     };
     Apply apply_fp64 = [&](const double2* xin, double2* yout, int R) -> bem_status {
         BEM_TRY(gemm_fp64(xin, R));
-        BEM_TRY(transfer_add(top, Ne, Ni, n, R, xin, z, s));
+        BEM_TRY(transfer_add(top, R, xin, z, s));
         return mass_solve(mop, z, yout, R, s, CHEB_STEPS);
     };
     // ---- GMRES ------------------------------------------------------------------------

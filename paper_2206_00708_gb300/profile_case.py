@@ -4,6 +4,7 @@ on synthetic icosphere grids.
 
     python -m paper_2206_00708_gb300.profile_case assemble --level 4 --k 10
     python -m paper_2206_00708_gb300.profile_case solve --level 4 --k 10
+    python -m paper_2206_00708_gb300.profile_case solve --level 5 --level-int 4 --mixed
     python -m paper_2206_00708_gb300.profile_case mortar --level 4
 """
 from __future__ import annotations
@@ -23,6 +24,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["assemble", "solve", "mortar"])
     ap.add_argument("--level", type=int, default=4)
+    ap.add_argument("--level-int", type=int, default=None, help="interior grid level (default: --level)")
     ap.add_argument("--k", type=float, default=10.0)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--mixed", action="store_true", help="BEM_PREC_MIXED instead of FP64")
@@ -31,7 +33,8 @@ def main(argv=None):
     import paper_2206_00708_gb300 as bem
 
     ctx = bem.bem_context_create(0)
-    ve, te, vi, ti = bi.transmission_pair(a.level, a.level, seed=2)
+    li = a.level if a.level_int is None else a.level_int
+    ve, te, vi, ti = bi.transmission_pair(a.level, li, seed=2)
     ge = bem.bem_grid_create(ctx, ve, te)
     gi = bem.bem_grid_create(ctx, vi, ti)
     for _ in range(a.repeat):
