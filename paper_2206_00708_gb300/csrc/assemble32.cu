@@ -17,10 +17,10 @@
 //    compare-and-swap loops): each CTA first bounds every value it will produce
 //    (smallest and largest point distance of its regular pairs, largest weight sums,
 //    areas and curls, |k|), picks a power-of-two scale 2^e that maps the bound to
-//    2^40, and adds round(v 2^e) as a 21-bit low word (uint32) and a high word
-//    (int32).  A vertex lies in at most 32 triangles of a tile, so at most 1024
-//    values meet in one entry and neither word can overflow; the in-tile sums are
-//    exact (and independent of the order of the atomics) to 2^-40 of the bound.
+//    2^40, and adds round(v 2^e) split into a high word (units of 2^21) and a low
+//    word, both int32.  A vertex lies in at most 32 triangles of a tile, so at most
+//    1024 values meet in one entry and neither word can overflow; the in-tile sums
+//    are exact (and independent of the order of the atomics) to 2^-40 of the bound.
 // The tile buffers are flushed to the global matrices with vector float2 atomics.
 #include "bem_internal.cuh"
 
@@ -92,20 +92,30 @@ struct TrialTile32 {
     uint32_t slot[TILE_TRI];
 };
 
-// fixed-point shared-memory accumulation (see the header): value v at scale 2^e
-constexpr int FX_LO_BITS = 21;
-constexpr float FX_LIMIT = 4398046511104.0f;  // 2^42: twice the bound that sets the scale
+// fixed-point shared-memory accumulation (see the header): value v at scale 2^e.
+// c = v 2^e (|c| < 2^41) is split with FP32 operations only (a conversion to a
+// 64-bit integer would run on the FP64 pipe, 1/64 of the FP32 rate on this part):
+// h = rint(c 2^-21) and l = c - h 2^21 are exact, |h|, |l| <= 2^20, and adding
+// 1.5 * 2^23 to a float of magnitude below 2^22 leaves rint(x) in its low mantissa
+// bits.  Both words are signed; at most 1024 values meet in one entry, so neither
+// 32-bit sum can overflow.
+constexpr float FX_LIMIT = 2199023255552.0f;  // 2^41: twice the bound that sets the scale
+constexpr float FX_MAGIC = 12582912.0f;       // 1.5 * 2^23
+constexpr int FX_MAGIC_BITS = 0x4B400000;     // its bit pattern
 
-__device__ __forceinline__ void fx_add(int32_t* H, uint32_t* L, int idx, float v, float scale, int* overflow) {
+__device__ __forceinline__ void fx_add(int32_t* H, int32_t* L, int idx, float v, float scale, int* overflow) {
     const float c = v * scale;
     if (!(fabsf(c) < FX_LIMIT)) {  // the bound was violated (or v is not finite)
         *overflow = 1;
         return;
     }
-    const long long q = __float2ll_rn(c);
-    if (q == 0) return;
-    atomicAdd(&L[idx], (uint32_t)(q & ((1ll << FX_LO_BITS) - 1)));
-    atomicAdd(&H[idx], (int32_t)(q >> FX_LO_BITS));
+    const float th = fmaf(c, 4.76837158203125e-7f, FX_MAGIC);  // c 2^-21 + magic
+    const float h = th - FX_MAGIC;                              // rint(c 2^-21)
+    const float l = fmaf(-h, 2097152.0f, c);                    // c - h 2^21, exact
+    const int32_t hi = __float_as_int(th) - FX_MAGIC_BITS;
+    const int32_t lo = __float_as_int(l + FX_MAGIC) - FX_MAGIC_BITS;
+    if (lo != 0) atomicAdd(&L[idx], lo);
+    if (hi != 0) atomicAdd(&H[idx], hi);
 }
 
 // largest |v| of a positive float kept as its bit pattern (monotone for x >= 0)
@@ -131,7 +141,7 @@ k_regular32(const TriRec32* __restrict__ rec, const int32_t* __restrict__ tverts
     const int it = blockIdx.y, is = blockIdx.x;
     if (it > is) return;
     extern __shared__ float smem[];
-    // accumulation slabs: [op V,K,T,D][re,im][high int32 | low uint32][TILE_NV * TILE_NV]
+    // accumulation slabs: [op V,K,T,D][re,im][high | low int32][TILE_NV * TILE_NV]
     constexpr int SLAB = TILE_NV * TILE_NV;
     int32_t* acc = reinterpret_cast<int32_t*>(smem);
     TriRec32* test = reinterpret_cast<TriRec32*>(smem + 16 * SLAB);
@@ -391,7 +401,7 @@ k_regular32(const TriRec32* __restrict__ rec, const int32_t* __restrict__ tverts
                     // slab of value o: high words at acc + 2 o SLAB, low words SLAB further
                     auto put = [&](int o, float v) {
                         int32_t* H = acc + (2 * o) * SLAB;
-                        fx_add(H, reinterpret_cast<uint32_t*>(H + SLAB), idx, v, scale, &s_overflow);
+                        fx_add(H, H + SLAB, idx, v, scale, &s_overflow);
                     };
                     put(0, Vr[a][b]);
                     put(1, Vi[a][b]);
@@ -420,10 +430,10 @@ k_regular32(const TriRec32* __restrict__ rec, const int32_t* __restrict__ tverts
         bool any = false;
 #pragma unroll
         for (int o = 0; o < 8; ++o) {
-            const long long q = ((long long)acc[(2 * o) * SLAB + idx] << FX_LO_BITS) +
-                                (long long)reinterpret_cast<const uint32_t*>(acc)[(2 * o + 1) * SLAB + idx];
-            any = any || q != 0;
-            v[o] = __ll2float_rn(q) * inv_scale;
+            // high * 2^21 + low, rounded to FP32 (one extra rounding at most) and unscaled
+            const int32_t hs = acc[(2 * o) * SLAB + idx], ls = acc[(2 * o + 1) * SLAB + idx];
+            any = any || (hs | ls) != 0;
+            v[o] = fmaf((float)hs, 2097152.0f, (float)ls) * inv_scale;
         }
         if (!any) continue;
         const int64_t i = vI[li], j = vJ[lj];

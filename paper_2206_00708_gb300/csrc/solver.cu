@@ -678,13 +678,14 @@ bem_status mass_solve(const MassOp& op, const double2* z, double2* y, int R, cud
     const int64_t n = op.M.n;
     const double theta = 0.5 * (CHEB_BETA + CHEB_ALPHA), delta = 0.5 * (CHEB_BETA - CHEB_ALPHA);
     const double sigma = theta / delta;
-    const dim3 grid(blocks_for(n, 256), R);
-    BEM_LAUNCH(k_cheb_init, grid, 256, 0, s, op.M, z, y, op.r, op.dA, 1.0 / theta);
+    // small blocks: a step is FP64 work of a few rows per thread, spread over every SM
+    const dim3 grid(blocks_for(n, 64), R);
+    BEM_LAUNCH(k_cheb_init, grid, 64, 0, s, op.M, z, y, op.r, op.dA, 1.0 / theta);
     double rho = 1.0 / sigma;
     double2 *dk = op.dA, *dn = op.dB;
     for (int k = 0; k < steps; ++k) {
         const double rho_n = 1.0 / (2.0 * sigma - rho);
-        BEM_LAUNCH(k_cheb_step, grid, 256, 0, s, op.M, dk, dn, y, op.r, rho_n * rho, 2.0 * rho_n / delta);
+        BEM_LAUNCH(k_cheb_step, grid, 64, 0, s, op.M, dk, dn, y, op.r, rho_n * rho, 2.0 * rho_n / delta);
         rho = rho_n;
         std::swap(dk, dn);
     }
@@ -724,7 +725,7 @@ bem_status build_csr(const int32_t* key, const int32_t* other, const double* val
 }
 
 bem_status transfer_add(const TransferCsr& t, int R, const double2* x, double2* z, cudaStream_t s) {
-    BEM_LAUNCH(k_transfer, dim3(blocks_for(t.n, 256), R), 256, 0, s, t, x, z);
+    BEM_LAUNCH(k_transfer, dim3(blocks_for(t.n, 64), R), 64, 0, s, t, x, z);
     return BEM_OK;
 }
 
@@ -882,6 +883,7 @@ bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs
     const int64_t n = W.n, ldh = W.ldh, gs = W.gstride;
     double2* Vp = W.Vb.as<double2>();
     const dim3 eb(blocks_for(n, 256), R);
+    const dim3 eb64(blocks_for(n, 64), R);  // FP64-heavy row kernels: spread over every SM
     BEM_CUDA_TRY(cudaMemsetAsync(W.H.p, 0, (size_t)R * ldh * ldh * 16, s));
     std::vector<HostQR> qr(R);
     std::vector<int> it(R, 0);
@@ -926,7 +928,7 @@ bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs
                 BEM_LAUNCH(k_dots_partial, dim3(W.nblk, gy, R), 256, 0, s, Vp, n, R, j + 1, W.w.as<double2>(),
                            W.nblk, W.partial.as<double2>());
                 BEM_LAUNCH(k_dots_final, dim3(j + 1, R), 32, 0, s, W.partial.as<double2>(), j + 1, W.nblk, h, hst, 0);
-                BEM_LAUNCH(k_combine, eb, 256, 0, s, Vp, n, R, j + 1, nullptr, h, hst, W.w.as<double2>(), 0);
+                BEM_LAUNCH(k_combine, eb64, 64, 0, s, Vp, n, R, j + 1, nullptr, h, hst, W.w.as<double2>(), 0);
             }
             BEM_LAUNCH(k_add_cols, dim3(1, R), 256, 0, s, Hj, ldh * ldh, W.hbuf.as<double2>(), gs, j + 1);
             BEM_TRY(W.sq_norms(W.w.as<double2>(), s));
@@ -948,7 +950,7 @@ bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs
     }
     BEM_CUDA_TRY(cudaMemcpyAsync(W.mr.p, W.h_mr, R * 4, cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(cudaMemcpyAsync(W.y.p, W.h_y, (size_t)R * gs * 16, cudaMemcpyHostToDevice, s));
-    BEM_LAUNCH(k_combine, eb, 256, 0, s, Vp, n, R, 0, W.mr.as<int>(), W.y.as<double2>(), gs, x, 1);
+    BEM_LAUNCH(k_combine, eb64, 64, 0, s, Vp, n, R, 0, W.mr.as<int>(), W.y.as<double2>(), gs, x, 1);
     BEM_CUDA_TRY(cudaStreamSynchronize(s));  // pinned h_y / h_mr are reused by the next run
     for (int r = 0; r < R; ++r) iters_out[r] = it[r];
     return BEM_OK;
