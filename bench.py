@@ -261,24 +261,41 @@ def run_serving(bem, reqs, precision, rate=None, max_inflight=4):
 
 
 BATCH_WORKLOAD = dict(level=4, seed=4, k_ext=5.0, k_int=7.5, rho=1.0, n_dirs=64, n_single=8)
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates of GB300
 
 
-def run_batching(bem, ctx, precision):
+def tf32_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            v = float(json.load(fh)["bf16_tflops"])
+        return v * TF32_PER_BF16, "measured bf16 burst (MEASURED_PEAKS.json) x nominal TF32/BF16 ratio 1.1/2.25"
+    except (OSError, KeyError, ValueError):
+        return 1900.0 * TF32_PER_BF16, "fallback 1.9 PFLOP/s bf16 x nominal TF32/BF16 ratio"
+
+
+def run_batching(bem, ctx, precision, tensor_cores=1, batch_columns=0):
     """Many plane waves at one frequency: one call with all directions (solved in
-    lockstep batches of 8) against the same directions one call each."""
+    lockstep batches) against the same directions one call each; the batched call
+    is profiled per kernel."""
     import torch
     import bem_inputs as bi
     b = BATCH_WORKLOAD
     ve, te, vi, ti = bi.transmission_pair(b["level"], b["level"], b["seed"])
     dirs = bi.plane_wave_directions(b["n_dirs"], seed=b["seed"] + 100)
-    opts = {"precision": precision}
+    opts = {"precision": precision, "tensor_cores": tensor_cores, "batch_columns": batch_columns}
     ge = bem.bem_grid_create(ctx, ve, te)
     gi = bem.bem_grid_create(ctx, vi, ti)
-    bem.bem_solve_transmission(ctx, ge, gi, b["k_int"], b["k_ext"], b["rho"], dirs[:8], opts=opts)  # warm-up
+    bem.bem_solve_transmission(ctx, ge, gi, b["k_int"], b["k_ext"], b["rho"], dirs[:16], opts=opts)  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     _, rep = bem.bem_solve_transmission(ctx, ge, gi, b["k_int"], b["k_ext"], b["rho"], dirs, opts=opts)
     t_batch = time.perf_counter() - t0
+    bem.bem_profile_reset()
+    bem.bem_profile_enable(True)
+    bem.bem_solve_transmission(ctx, ge, gi, b["k_int"], b["k_ext"], b["rho"], dirs, opts=opts)
+    bem.bem_context_synchronize(ctx)
+    bem.bem_profile_enable(False)
+    prof = bem.bem_profile_table()
     single_solve_ms, single_wall = [], 0.0
     for r in range(b["n_single"]):
         t0 = time.perf_counter()
@@ -287,12 +304,27 @@ def run_batching(bem, ctx, precision):
         single_solve_ms.append(r1["t_solve_ms"])
     bem.bem_grid_destroy(ge)
     bem.bem_grid_destroy(gi)
-    return {"rhs_per_s_one_call": b["n_dirs"] / t_batch,
-            "rhs_per_s_one_call_each": b["n_single"] / single_wall,
-            "solve_ms_per_rhs_batched": rep["t_solve_ms"] / b["n_dirs"],
-            "solve_ms_per_rhs_single": float(np.mean(single_solve_ms)),
-            "iterations_per_rhs_batched": rep["iterations"] / b["n_dirs"],
-            "assembly_ms": rep["t_assembly_ms"]}
+    out = {"rhs_per_s_one_call": b["n_dirs"] / t_batch,
+           "rhs_per_s_one_call_each": b["n_single"] / single_wall,
+           "solve_ms_per_rhs_batched": rep["t_solve_ms"] / b["n_dirs"],
+           "solve_ms_per_rhs_single": float(np.mean(single_solve_ms)),
+           "iterations_per_rhs_batched": rep["iterations"] / b["n_dirs"],
+           "assembly_ms": rep["t_assembly_ms"],
+           "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in prof[:8]]}
+    tc = [p for p in prof if p[0] == "k_gemm_tc"]
+    if tc:
+        name, ms, nl = tc[0]
+        N = len(ve)  # both grids have the same level here
+        rp = (b["n_dirs"] + 7) // 8 * 8 if batch_columns == 0 else (batch_columns + 7) // 8 * 8
+        flops = 96.0 * rp * (N * N + len(vi) * len(vi))  # 3 split terms x 2 flops x K 4N x N_b x 2 RP, 4 block rows
+        peak, kind = tf32_peak()
+        ach = flops / (ms / nl / 1e3) / 1e12
+        out["tensor_roofline"] = {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak,
+                                  "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "peak_kind": kind,
+                                  "flops_per_launch": flops, "avg_launch_ms": ms / nl,
+                                  "bytes_per_launch": 8 * 4 * (N * N + len(vi) * len(vi)),
+                                  "hbm_frac": 8 * 4 * (N * N + len(vi) * len(vi)) / (ms / nl / 1e3) / 1e9 / hbm_peak()[0]}
+    return out
 
 
 def kernel_roofline(name, ms, n, te, ti, Ne, Ni, pp_cache):
@@ -481,8 +513,11 @@ def main():
         bw = BATCH_WORKLOAD
         batching = {"workload": f"unit sphere, icosphere L{bw['level']} on both grids (seed {bw['seed']}), "
                                 f"k_ext={bw['k_ext']}, k_int={bw['k_int']}, rho={bw['rho']}, {bw['n_dirs']} plane "
-                                f"waves in one call vs {bw['n_single']} of them one call each",
-                    "mixed": run_batching(bem, ctx, bem.BEM_PREC_MIXED),
+                                f"waves in one call vs {bw['n_single']} of them one call each; mixed precision "
+                                "with tensor-core products (one batch of 64) and with CUDA-core products "
+                                "(batches of 8), FP64 (batches of 8)",
+                    "mixed_tensor_cores": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 1, 0),
+                    "mixed_cuda_cores_8": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 0, 8),
                     "fp64": run_batching(bem, ctx, bem.BEM_PREC_FP64)}
 
     cpu = None

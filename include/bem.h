@@ -90,7 +90,10 @@ BEM_API uint64_t bem_launch_count(void);
 /* Accuracy self-tests of device arithmetic written for this library (no
  * counterpart in the paper).  which = 0: largest absolute difference between the
  * FP32 assembly kernel's sin/cos (Cody-Waite reduction + Taylor series) and CUDA's
- * sincosf on 2^20 evenly spaced arguments in [-64, 64]. */
+ * sincosf on 2^20 evenly spaced arguments in [-64, 64].  which = 1: relative L2
+ * difference between the tensor-core multi-column MTF product (TF32 three-term
+ * split) and the FP32 CUDA-core product on seeded random complex64 blocks
+ * (N_ext = 300, N_int = 170, 24 columns).  which = 2: the same with 8 columns. */
 BEM_API bem_status bem_selftest(bem_context* ctx, int which, double* result);
 
 /* Per-kernel device timing.  While enabled, each launch of the library is
@@ -213,6 +216,12 @@ typedef struct {
                                  GMRES solve (default 1e-8: the first inner solve runs to the
                                  target tolerance, the FP64 residual then needs one short
                                  correction); never below gmres_tol * ||S b|| overall              */
+    int32_t batch_columns;    /* right-hand sides solved together (one Krylov process each, the
+                                 operator read once per iteration for all): 0 = default (64 with
+                                 BEM_PREC_MIXED and tensor cores, else 8); 1..128                   */
+    int32_t tensor_cores;     /* BEM_PREC_MIXED batches of more than 8 right-hand sides: 1 (default)
+                                 = products on the tcgen05 tensor cores (TF32, three-term split,
+                                 FP32 accumulation), 0 = FP32 CUDA cores in groups of 8 columns    */
 } bem_solve_opts;
 
 typedef struct {

@@ -58,6 +58,8 @@ class bem_solve_opts(C.Structure):
         ("mtf_variant", C.c_int32),
         ("center", C.c_double * 3),
         ("ir_inner_tol", C.c_double),
+        ("batch_columns", C.c_int32),
+        ("tensor_cores", C.c_int32),
     ]
 
 

@@ -214,6 +214,15 @@ bem_status assemble_operators_fp64(const bem_grid* g, double k_re, double k_im, 
                                    double2* V, double2* K, double2* T, double2* D, cudaStream_t s);
 
 // mortar.cu: COO of P_ab (rows: vertices of a, cols: vertices of b).
+// tensor-core multi-column MTF product (gemm_tc.cu)
+int tc_padded_columns(int R);
+size_t tc_workspace_bytes(const int64_t N[4], int RP);
+bem_status mtf_product_tc(const float2* const a1[4], const float2* const a2[4], const double c1[4],
+                          const double c2[4], const int64_t N[4], const int64_t base[4], const int64_t x1[4],
+                          const int64_t x2[4], int64_t n, int R, const double2* x, double2* z, void* work,
+                          size_t work_bytes, int* err, cudaStream_t s);
+bem_status selftest_tc(int R, double* rel_err, cudaStream_t s);
+
 bem_status mortar_coo(const bem_grid* a, const bem_grid* b, const double center[3],
                       DevBuf& row, DevBuf& col, DevBuf& val, int64_t* nnz, cudaStream_t s);
 

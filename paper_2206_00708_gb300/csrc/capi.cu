@@ -71,8 +71,9 @@ uint64_t bem_launch_count(void) { return g_launches.load(std::memory_order_relax
 bem_status bem_selftest(bem_context* ctx, int which, double* result) {
     CTX_GUARD(ctx);
     BEM_REQUIRE(result != nullptr, "null result");
-    BEM_REQUIRE(which == 0, "unknown self-test");
-    return selftest_sincos(1 << 20, 64.0f, result, ctx->stream);
+    BEM_REQUIRE(which >= 0 && which <= 2, "unknown self-test");
+    if (which == 0) return selftest_sincos(1 << 20, 64.0f, result, ctx->stream);
+    return selftest_tc(which == 1 ? 24 : 8, result, ctx->stream);
 }
 
 bem_status bem_context_create(int device, void* stream, bem_context** out) {
@@ -345,6 +346,8 @@ void bem_solve_opts_default(bem_solve_opts* o) {
     o->mtf_variant = BEM_MTF_DERIVED;
     o->center[0] = o->center[1] = o->center[2] = 0.0;
     o->ir_inner_tol = 1e-8;
+    o->batch_columns = 0;
+    o->tensor_cores = 1;
 }
 
 bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const bem_grid* intr, bem_c128 k_int,
@@ -366,6 +369,8 @@ bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const b
     BEM_REQUIRE(o.mtf_variant == BEM_MTF_DERIVED || o.mtf_variant == BEM_MTF_PRINTED, "unknown MTF variant");
     BEM_REQUIRE(o.precision == BEM_PREC_FP64 || o.precision == BEM_PREC_MIXED, "unsupported precision");
     BEM_REQUIRE(o.ir_inner_tol > 0.0 && o.ir_inner_tol < 1.0, "ir_inner_tol must be in (0, 1)");
+    BEM_REQUIRE(o.batch_columns >= 0 && o.batch_columns <= 128, "batch_columns must be in [0, 128]");
+    BEM_REQUIRE(o.tensor_cores == 0 || o.tensor_cores == 1, "tensor_cores must be 0 or 1");
     for (int r = 0; r < inc->n_rhs; ++r) {
         const double* d = inc->dirs + 3 * r;
         const double nd = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);

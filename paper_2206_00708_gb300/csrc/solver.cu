@@ -41,7 +41,6 @@ namespace {
 constexpr int CHEB_STEPS = 34;        // error <= 2 * 3^-34 ~ 1e-16: FP64 applications
 constexpr int CHEB_STEPS_INNER = 17;  // error <= 2 * 3^-17 ~ 1.6e-8: inner solves of the refinement
 constexpr double CHEB_ALPHA = 0.5, CHEB_BETA = 2.0;
-constexpr int RMAX = 8;               // right-hand sides per batch
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -71,34 +70,15 @@ unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 // f_j = <u_inc, theta_j>, g_j = <du_inc/dn, theta_j> on the exterior grid,
 // u_inc = amp exp(i k x.d), du_inc/dn = i k (d.n) u_inc (paper eq. planewave);
 // blockIdx.y = right-hand side.
-struct Waves {
-    double3 d[RMAX];
-    double2 amp[RMAX];
-};
-
-__device__ __forceinline__ double3 sel_dir(const Waves& W, int r) {
-    double3 d = W.d[0];
-#pragma unroll
-    for (int k = 1; k < RMAX; ++k)
-        if (r == k) d = W.d[k];
-    return d;
-}
-__device__ __forceinline__ double2 sel_amp(const Waves& W, int r) {
-    double2 a = W.amp[0];
-#pragma unroll
-    for (int k = 1; k < RMAX; ++k)
-        if (r == k) a = W.amp[k];
-    return a;
-}
-
+// dirs [R][3], amps [R] (device); blockIdx.y = right-hand side
 __global__ void k_plane_wave(const TriRec* __restrict__ rec, const int32_t* __restrict__ tri, int64_t nt,
-                             double kr, double ki, Waves W, int64_t Ne, double2* __restrict__ f,
-                             double2* __restrict__ g) {
+                             double kr, double ki, const double* __restrict__ dirs, const double2* __restrict__ amps,
+                             int64_t Ne, double2* __restrict__ f, double2* __restrict__ g) {
     const int r = blockIdx.y;
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nt) return;
-    const double3 d = sel_dir(W, r);
-    const double2 amp = sel_amp(W, r);
+    const double3 d = make_double3(dirs[3 * r], dirs[3 * r + 1], dirs[3 * r + 2]);
+    const double2 amp = amps[r];
     const TriRec& R = rec[t];
     const double dn = d.x * R.n[0] + d.y * R.n[1] + d.z * R.n[2];
     double2 fa[3] = {}, ga[3] = {};
@@ -756,6 +736,7 @@ struct GmresWork {
     double2* h_col = nullptr;  // pinned, [GMRES_SLOTS][R][maxit + 2]: copied Hessenberg columns
     double2* h_y = nullptr;    // pinned, [R][gstride]: least-squares solutions
     int* h_mr = nullptr;       // pinned, [R]
+    double* h_wave = nullptr;  // pinned, [5 R]: plane-wave amplitudes (R complex) then directions (3 R)
     cudaEvent_t ev[GMRES_SLOTS] = {};
     cudaStream_t stream = nullptr;
     ~GmresWork() {
@@ -765,20 +746,21 @@ struct GmresWork {
         if (h_col) cudaFreeHost(h_col);
         if (h_y) cudaFreeHost(h_y);
         if (h_mr) cudaFreeHost(h_mr);
+        if (h_wave) cudaFreeHost(h_wave);
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
     }
-    bem_status init(int maxit_, int64_t n_, int R_, cudaStream_t s) {
+    bem_status init(int maxit_, int64_t n_, int R_, int spare, cudaStream_t s) {
         maxit = maxit_;
         n = n_;
         R = R_;
         stream = s;
-        RW = gemm_width(R_);
+        RW = R_ + spare;
         nblk = dot_blocks(n_);
         ldh = maxit + 1;
         gstride = maxit + 2;
         // (maxit + 1) basis blocks of R columns, plus RW - R spare columns read by the
-        // padded operator kernels past the last block
+        // width-padded operator kernels past the last block
         const size_t vb = ((size_t)(maxit + 1) * R + (RW - R)) * n * 16;
         BEM_TRY(Vb.alloc(vb, s));
         BEM_CUDA_TRY(cudaMemsetAsync(Vb.p, 0, vb, s));
@@ -793,6 +775,7 @@ struct GmresWork {
         BEM_CUDA_TRY(cudaMallocHost(&h_col, (size_t)GMRES_SLOTS * R * gstride * 16));
         BEM_CUDA_TRY(cudaMallocHost(&h_y, (size_t)R * gstride * 16));
         BEM_CUDA_TRY(cudaMallocHost(&h_mr, (size_t)R * 4));
+        BEM_CUDA_TRY(cudaMallocHost(&h_wave, (size_t)5 * R * 8));
         for (cudaEvent_t& e : ev) BEM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         return BEM_OK;
     }
@@ -987,7 +970,88 @@ void fill_blocks(BT& B, MT* const m1[4], MT* const m2[4], int64_t Ne, int64_t Ni
     }
 }
 
+// seeded uniform values in [lo, hi) (a 64-bit mixing hash of the index)
+__global__ void k_fill_uniform(float* __restrict__ a, int64_t count, uint64_t seed, float lo, float hi) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    uint64_t h = (uint64_t)i * 0x9E3779B97F4A7C15ull + seed;
+    h ^= h >> 30;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 27;
+    h *= 0x94D049BB133111EBull;
+    h ^= h >> 31;
+    a[i] = lo + (hi - lo) * (float)((h >> 40) * (1.0 / 16777216.0));
+}
+
+__global__ void k_widen(const float2* __restrict__ x, int64_t count, double2* __restrict__ y) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count) y[i] = make_double2(x[i].x, x[i].y);
+}
+
 }  // namespace
+
+// The tensor-core product against the FP32 CUDA-core product on seeded random
+// blocks whose entries have positive real parts (little cancellation, so the
+// relative difference measures the products' rounding and not the data).
+bem_status selftest_tc(int R, double* rel_err, cudaStream_t s) {
+    const int64_t Ne = 300, Ni = 170, n = 2 * Ne + 2 * Ni;
+    const int RW = R + 7;
+    DevBuf A[8], xf, x, x32, z1, z2, work, err;
+    for (int m = 0; m < 8; ++m) {
+        const int64_t N = m < 4 ? Ne : Ni;
+        BEM_TRY(A[m].alloc((size_t)N * N * 8, s));
+        float* f = A[m].as<float>();
+        BEM_LAUNCH(k_fill_uniform, blocks_for(2 * N * N, 256), 256, 0, s, f, 2 * N * N, 1000ull + m, 0.5f, 1.0f);
+        // imaginary parts in [-0.25, 0.25): refill the odd floats by a strided view
+        DevBuf im;
+        BEM_TRY(im.alloc((size_t)N * N * 4, s));
+        BEM_LAUNCH(k_fill_uniform, blocks_for(N * N, 256), 256, 0, s, im.as<float>(), N * N, 2000ull + m, -0.25f, 0.25f);
+        BEM_CUDA_TRY(cudaMemcpy2DAsync(f + 1, 8, im.p, 4, 4, N * N, cudaMemcpyDeviceToDevice, s));
+    }
+    BEM_TRY(xf.alloc((size_t)RW * n * 8, s));
+    BEM_LAUNCH(k_fill_uniform, blocks_for(2 * RW * n, 256), 256, 0, s, xf.as<float>(), 2 * RW * n, 3000ull, 0.5f, 1.0f);
+    BEM_TRY(x.alloc((size_t)RW * n * 16, s));
+    BEM_LAUNCH(k_widen, blocks_for(RW * n, 256), 256, 0, s, xf.as<float2>(), RW * n, x.as<double2>());
+    BEM_TRY(z1.alloc((size_t)RW * n * 16, s));
+    BEM_TRY(z2.alloc((size_t)RW * n * 16, s));
+    Blocks<float2> B{};
+    const float2* m1[4] = {A[1].as<float2>(), A[3].as<float2>(), A[5].as<float2>(), A[7].as<float2>()};
+    const float2* m2[4] = {A[0].as<float2>(), A[2].as<float2>(), A[4].as<float2>(), A[6].as<float2>()};
+    fill_blocks(B, m1, m2, Ne, Ni);
+    BEM_TRY(work.alloc(tc_workspace_bytes(B.rows, tc_padded_columns(R)), s));
+    BEM_TRY(err.alloc(sizeof(int), s));
+    BEM_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    BEM_TRY(mtf_product_tc(B.A1, B.A2, B.c1, B.c2, B.rows, B.base, B.x1, B.x2, n, R, x.as<double2>(),
+                           z1.as<double2>(), work.p, work.bytes, err.as<int>(), s));
+    const unsigned rows_blocks = blocks_for(n * 32, 256);
+    for (int c0 = 0; c0 < R; c0 += 8) {
+        const int Wd = gemm_width(std::min(8, R - c0));
+        const float2* xc = xf.as<float2>() + c0 * n;
+        double2* zc = z2.as<double2>() + c0 * n;
+        if (Wd == 1) BEM_LAUNCH(k_gemm32<1>, rows_blocks, 256, 0, s, B, n, xc, zc);
+        else if (Wd == 2) BEM_LAUNCH(k_gemm32<2>, rows_blocks, 256, 0, s, B, n, xc, zc);
+        else if (Wd == 4) BEM_LAUNCH(k_gemm32<4>, rows_blocks, 256, 0, s, B, n, xc, zc);
+        else BEM_LAUNCH(k_gemm32<8>, rows_blocks, 256, 0, s, B, n, xc, zc);
+    }
+    std::vector<double2> h1((size_t)R * n), h2((size_t)R * n);
+    int h_err = 0;
+    BEM_CUDA_TRY(cudaMemcpyAsync(h1.data(), z1.p, h1.size() * 16, cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(h2.data(), z2.p, h2.size() * 16, cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h_err) {
+        set_error("tensor-core product: an mbarrier wait timed out");
+        return BEM_E_INTERNAL;
+    }
+    double num = 0.0, den = 0.0;
+    for (size_t i = 0; i < h1.size(); ++i) {
+        const double dx = h1[i].x - h2[i].x, dy = h1[i].y - h2[i].y;
+        num += dx * dx + dy * dy;
+        den += h2[i].x * h2[i].x + h2[i].y * h2[i].y;
+    }
+    *rel_err = den > 0.0 ? std::sqrt(num / den) : 0.0;
+    return BEM_OK;
+}
 
 bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const bem_grid* gi, bem_c128 k_int,
                                    bem_c128 k_ext, double rho_ratio, const bem_incident* inc,
@@ -1050,10 +1114,15 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     BEM_TRY(build_csr(pcol.as<int32_t>(), prow.as<int32_t>(), pval.as<double>(), pnnz, Ne, csr_t, s));
     cudaEventRecord(t_mor.b, s);
     // ---- workspaces for batches of RB right-hand sides ---------------------------------
-    const int RB = std::min<int>(RMAX, inc->n_rhs);
-    const int RW = gemm_width(RB);  // column count of everything the operator kernels touch
+    const bool use_tc = mixed && o->tensor_cores != 0;
+    const int rmax = o->batch_columns > 0 ? o->batch_columns : (use_tc ? 64 : 8);
+    const int RB = std::min<int>(rmax, inc->n_rhs);
+    // CUDA-core products take the columns in groups of w <= 8 at width gemm_width(w),
+    // reading and writing up to 7 spare (in-bounds) columns past the batch
+    const int RW = RB + 7;
+    const bool tc_batches = use_tc && RB > 8;
     const size_t colb = (size_t)n * 16;
-    DevBuf wz, wr, wa, wb, x32;
+    DevBuf wz, wr, wa, wb, x32, tcw, tcerr;
     BEM_TRY(wz.alloc(RW * colb, s));
     BEM_TRY(wr.alloc(RB * colb, s));
     BEM_TRY(wa.alloc(RB * colb, s));
@@ -1083,36 +1152,54 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
         const float2* m1[4] = {M[1].as<float2>(), M[3].as<float2>(), M[5].as<float2>(), M[7].as<float2>()};
         const float2* m2[4] = {M[0].as<float2>(), M[2].as<float2>(), M[4].as<float2>(), M[6].as<float2>()};
         fill_blocks(B32, m1, m2, Ne, Ni);
+        if (tc_batches) {
+            BEM_TRY(tcw.alloc(tc_workspace_bytes(B32.rows, tc_padded_columns(RB)), s));
+            BEM_TRY(tcerr.alloc(sizeof(int), s));
+            BEM_CUDA_TRY(cudaMemsetAsync(tcerr.p, 0, sizeof(int), s));
+        }
     } else {
         const double2* m1[4] = {M[1].as<double2>(), M[3].as<double2>(), M[5].as<double2>(), M[7].as<double2>()};
         const double2* m2[4] = {M[0].as<double2>(), M[2].as<double2>(), M[4].as<double2>(), M[6].as<double2>()};
         fill_blocks(B64, m1, m2, Ne, Ni);
     }
     const unsigned rows_blocks = blocks_for(n * 32, 256);
-    // dense blocks for R columns in the working arithmetic (x must hold gemm_width(R) columns)
+    // dense blocks for R columns in the working arithmetic (x must hold R + 7 columns)
     auto gemm_work = [&](const double2* xin, int R) -> bem_status {
-        const int Wd = gemm_width(R);
-        if (mixed) {
+        if (mixed && tc_batches && R > 8)
+            return mtf_product_tc(B32.A1, B32.A2, B32.c1, B32.c2, B32.rows, B32.base, B32.x1, B32.x2, n, R, xin, z,
+                                  tcw.p, tcw.bytes, tcerr.as<int>(), s);
+        if (mixed)
             BEM_LAUNCH(k_to_c64, blocks_for((int64_t)R * n, 256), 256, 0, s, xin, (int64_t)R * n, x32.as<float2>());
-            if (Wd == 1) BEM_LAUNCH(k_gemm32<1>, rows_blocks, 256, 0, s, B32, n, x32.as<float2>(), z);
-            else if (Wd == 2) BEM_LAUNCH(k_gemm32<2>, rows_blocks, 256, 0, s, B32, n, x32.as<float2>(), z);
-            else if (Wd == 4) BEM_LAUNCH(k_gemm32<4>, rows_blocks, 256, 0, s, B32, n, x32.as<float2>(), z);
-            else BEM_LAUNCH(k_gemm32<8>, rows_blocks, 256, 0, s, B32, n, x32.as<float2>(), z);
-        } else {
-            if (Wd == 1) BEM_LAUNCH(k_gemm64<1>, rows_blocks, 256, 0, s, B64, n, xin, z);
-            else if (Wd == 2) BEM_LAUNCH(k_gemm64<2>, rows_blocks, 256, 0, s, B64, n, xin, z);
-            else if (Wd == 4) BEM_LAUNCH(k_gemm64<4>, rows_blocks, 256, 0, s, B64, n, xin, z);
-            else BEM_LAUNCH(k_gemm64<8>, rows_blocks, 256, 0, s, B64, n, xin, z);
+        for (int c0 = 0; c0 < R; c0 += 8) {
+            const int Wd = gemm_width(std::min(8, R - c0));
+            double2* zc = z + (int64_t)c0 * n;
+            if (mixed) {
+                const float2* xc = x32.as<float2>() + (int64_t)c0 * n;
+                if (Wd == 1) BEM_LAUNCH(k_gemm32<1>, rows_blocks, 256, 0, s, B32, n, xc, zc);
+                else if (Wd == 2) BEM_LAUNCH(k_gemm32<2>, rows_blocks, 256, 0, s, B32, n, xc, zc);
+                else if (Wd == 4) BEM_LAUNCH(k_gemm32<4>, rows_blocks, 256, 0, s, B32, n, xc, zc);
+                else BEM_LAUNCH(k_gemm32<8>, rows_blocks, 256, 0, s, B32, n, xc, zc);
+            } else {
+                const double2* xc = xin + (int64_t)c0 * n;
+                if (Wd == 1) BEM_LAUNCH(k_gemm64<1>, rows_blocks, 256, 0, s, B64, n, xc, zc);
+                else if (Wd == 2) BEM_LAUNCH(k_gemm64<2>, rows_blocks, 256, 0, s, B64, n, xc, zc);
+                else if (Wd == 4) BEM_LAUNCH(k_gemm64<4>, rows_blocks, 256, 0, s, B64, n, xc, zc);
+                else BEM_LAUNCH(k_gemm64<8>, rows_blocks, 256, 0, s, B64, n, xc, zc);
+            }
         }
         return BEM_OK;
     };
     auto gemm_fp64 = [&](const double2* xin, int R) -> bem_status {
         if (!mixed) return gemm_work(xin, R);
-        const int Wd = gemm_width(R);
-        if (Wd == 1) BEM_LAUNCH(k_gemm_c64_f64<1>, rows_blocks, 256, 0, s, B32, n, xin, z);
-        else if (Wd == 2) BEM_LAUNCH(k_gemm_c64_f64<2>, rows_blocks, 256, 0, s, B32, n, xin, z);
-        else if (Wd == 4) BEM_LAUNCH(k_gemm_c64_f64<4>, rows_blocks, 256, 0, s, B32, n, xin, z);
-        else BEM_LAUNCH(k_gemm_c64_f64<8>, rows_blocks, 256, 0, s, B32, n, xin, z);
+        for (int c0 = 0; c0 < R; c0 += 8) {
+            const int Wd = gemm_width(std::min(8, R - c0));
+            const double2* xc = xin + (int64_t)c0 * n;
+            double2* zc = z + (int64_t)c0 * n;
+            if (Wd == 1) BEM_LAUNCH(k_gemm_c64_f64<1>, rows_blocks, 256, 0, s, B32, n, xc, zc);
+            else if (Wd == 2) BEM_LAUNCH(k_gemm_c64_f64<2>, rows_blocks, 256, 0, s, B32, n, xc, zc);
+            else if (Wd == 4) BEM_LAUNCH(k_gemm_c64_f64<4>, rows_blocks, 256, 0, s, B32, n, xc, zc);
+            else BEM_LAUNCH(k_gemm_c64_f64<8>, rows_blocks, 256, 0, s, B32, n, xc, zc);
+        }
         return BEM_OK;
     };
     // S A x in the working precision, and with FP64 arithmetic on the stored matrices
@@ -1129,8 +1216,9 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     // ---- GMRES ------------------------------------------------------------------------
     const int maxit = (int)std::min<int64_t>(o->gmres_maxiter, n);
     GmresWork W;
-    BEM_TRY(W.init(maxit, n, RB, s));
-    DevBuf fvec, gvec, bvec, sb, xsol, dvec, rvec, tmp;
+    BEM_TRY(W.init(maxit, n, RB, RW - RB, s));
+    DevBuf fvec, gvec, bvec, sb, xsol, dvec, rvec, tmp, wave;
+    BEM_TRY(wave.alloc((size_t)5 * RB * 8, s));
     BEM_TRY(fvec.alloc((size_t)RB * Ne * 16, s));
     BEM_TRY(gvec.alloc((size_t)RB * Ne * 16, s));
     BEM_TRY(bvec.alloc(RB * colb, s));
@@ -1147,16 +1235,18 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     cudaEventRecord(t_sol.a, s);
     for (int r0 = 0; r0 < inc->n_rhs; r0 += RB) {
         const int R = std::min(RB, inc->n_rhs - r0);
-        Waves wv{};
+        // amplitudes first (2 R doubles: 16-byte aligned complex values), then directions
         for (int r = 0; r < R; ++r) {
-            const double* d = inc->dirs + 3 * (r0 + r);
-            wv.d[r] = make_double3(d[0], d[1], d[2]);
-            wv.amp[r] = inc->amps ? make_double2(inc->amps[r0 + r].re, inc->amps[r0 + r].im) : make_double2(1.0, 0.0);
+            W.h_wave[2 * r] = inc->amps ? inc->amps[r0 + r].re : 1.0;
+            W.h_wave[2 * r + 1] = inc->amps ? inc->amps[r0 + r].im : 0.0;
+            for (int d = 0; d < 3; ++d) W.h_wave[2 * RB + 3 * r + d] = inc->dirs[3 * (r0 + r) + d];
         }
+        BEM_CUDA_TRY(cudaMemcpyAsync(wave.p, W.h_wave, (size_t)5 * RB * 8, cudaMemcpyHostToDevice, s));
         BEM_CUDA_TRY(cudaMemsetAsync(fvec.p, 0, (size_t)R * Ne * 16, s));
         BEM_CUDA_TRY(cudaMemsetAsync(gvec.p, 0, (size_t)R * Ne * 16, s));
         BEM_LAUNCH(k_plane_wave, dim3(blocks_for(ge->nt, 128), R), 128, 0, s, ge->rec.as<TriRec>(),
-                   ge->tri.as<int32_t>(), ge->nt, k_ext.re, k_ext.im, wv, Ne, fvec.as<double2>(), gvec.as<double2>());
+                   ge->tri.as<int32_t>(), ge->nt, k_ext.re, k_ext.im, wave.as<double>() + 2 * RB,
+                   wave.as<double2>(), Ne, fvec.as<double2>(), gvec.as<double2>());
         BEM_LAUNCH(k_rhs_pack, dim3(blocks_for(n, 256), R), 256, 0, s, fvec.as<double2>(), gvec.as<double2>(), Ne, n,
                    bvec.as<double2>());
         BEM_TRY(mass_solve(mop, bvec.as<double2>(), sb.as<double2>(), R, s, CHEB_STEPS));
@@ -1231,6 +1321,14 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     }
     cudaEventRecord(t_sol.b, s);
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (tc_batches) {
+        int h_err = 0;
+        BEM_CUDA_TRY(cudaMemcpy(&h_err, tcerr.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (h_err) {
+            set_error("tensor-core product: an mbarrier wait timed out");
+            return BEM_E_INTERNAL;
+        }
+    }
     if (result == BEM_E_NOT_CONVERGED)
         set_error("GMRES did not reach the tolerance within gmres_maxiter iterations; outputs hold the last iterate");
     if (rep) {

@@ -5,6 +5,7 @@ on synthetic icosphere grids.
     python -m paper_2206_00708_gb300.profile_case assemble --level 4 --k 10
     python -m paper_2206_00708_gb300.profile_case solve --level 4 --k 10
     python -m paper_2206_00708_gb300.profile_case solve --level 5 --level-int 4 --mixed
+    python -m paper_2206_00708_gb300.profile_case solve --level 4 --mixed --rhs 64
     python -m paper_2206_00708_gb300.profile_case mortar --level 4
 """
 from __future__ import annotations
@@ -28,6 +29,7 @@ def main(argv=None):
     ap.add_argument("--k", type=float, default=10.0)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--mixed", action="store_true", help="BEM_PREC_MIXED instead of FP64")
+    ap.add_argument("--rhs", type=int, default=1, help="plane waves in the solve (batched)")
     a = ap.parse_args(argv)
     import bem_inputs as bi
     import paper_2206_00708_gb300 as bem
@@ -47,7 +49,8 @@ def main(argv=None):
             s = bem.bem_projection(ctx, gi, ge)
             bem.bem_sparse_destroy(s)
         else:
-            out, rep = bem.bem_solve_transmission(ctx, ge, gi, 1.5 * a.k, a.k, 2.0, np.array([[0.0, 0.0, 1.0]]),
+            dirs = np.array([[0.0, 0.0, 1.0]]) if a.rhs == 1 else bi.plane_wave_directions(a.rhs, seed=40)
+            out, rep = bem.bem_solve_transmission(ctx, ge, gi, 1.5 * a.k, a.k, 2.0, dirs,
                                                   opts={"precision": 1 if a.mixed else 0})
             print("iterations", rep["iterations"])
     bem.bem_grid_destroy(ge)

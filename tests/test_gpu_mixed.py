@@ -131,3 +131,39 @@ def test_mixed_solve_matches_fp64_gpu_at_level4(env):
     errs = {key: rel(out[key][0], ref[key][0]) for key in ("v_ext", "w_ext", "v_int", "w_int")}
     print(errs, r64, rmx)
     assert max(errs.values()) < TRACE_TOL, errs
+
+
+def test_tensor_core_product_matches_cuda_core_product(env):
+    """The tcgen05 product (TF32, three-term split, FP32 accumulation in 8 TMEM
+    accumulators summed in FP64) against the compensated FP32 CUDA-core product on
+    seeded random blocks, 24 columns (three groups of 8 on the CUDA cores) and 8
+    columns.  The split drops terms below 2^-22 of each product; the tensor cores'
+    FP32 accumulation is biased (one accumulator over K = 1200 gave 1.04e-5 here),
+    eight shorter chains keep it near 1e-6."""
+    bem, ctx = env
+    for which in (1, 2):
+        err = bem.bem_selftest(ctx, which)
+        print("tensor-core vs CUDA-core product, rel. L2", which, err)
+        assert err < 1e-5
+
+
+def test_tensor_core_batches_equal_cuda_core_batches(env):
+    """Twenty plane waves in one mixed-precision call, products on the tensor cores
+    (one batch of 20) or on the CUDA cores (groups of 8): both refine to the same
+    complex64 system, so the traces agree within the mode's tolerance."""
+    bem, ctx = env
+    ve, te, vi, ti = bi.transmission_pair(2, 2, seed=12)
+    dirs = bi.plane_wave_directions(20, seed=44)
+    ge = bem.bem_grid_create(ctx, ve, te)
+    gi = bem.bem_grid_create(ctx, vi, ti)
+    try:
+        a, ra = bem.bem_solve_transmission(ctx, ge, gi, 4.5, 3.0, 1.3, dirs,
+                                           opts={"precision": bem.BEM_PREC_MIXED, "tensor_cores": 1})
+        b, rb = bem.bem_solve_transmission(ctx, ge, gi, 4.5, 3.0, 1.3, dirs,
+                                           opts={"precision": bem.BEM_PREC_MIXED, "tensor_cores": 0})
+    finally:
+        bem.bem_grid_destroy(ge)
+        bem.bem_grid_destroy(gi)
+    assert ra["converged"] == 1 and rb["converged"] == 1
+    for key in ("v_ext", "w_ext", "v_int", "w_int"):
+        assert rel(a[key], b[key]) < TRACE_TOL, key
