@@ -327,6 +327,48 @@ def run_batching(bem, ctx, precision, tensor_cores=1, batch_columns=0):
     return out
 
 
+UNEVEN_WORKLOAD = dict(count=32, seed=42)
+
+
+def run_uneven(bem, ctx):
+    """Uneven instances: ellipsoids with semi-axes U[0.5, 1.5], exterior and interior
+    icosphere levels drawn from {2, 3, 4}, k_ext U[2, 8], k_int = 1.5 k_ext, density
+    ratio 1, one random plane wave each; all in one bem_solve_many call against the
+    same instances solved one call each (mixed precision)."""
+    import torch
+    import bem_inputs as bi
+    u = UNEVEN_WORKLOAD
+    rng = np.random.default_rng(u["seed"])
+    probs, grids = [], []
+    for i in range(u["count"]):
+        axes = rng.uniform(0.5, 1.5, 3)
+        le, li = int(rng.integers(2, 5)), int(rng.integers(2, 5))
+        ve, te, vi, ti = bi.transmission_pair(le, li, seed=u["seed"] * 1000 + i, axes=axes)
+        ge, gi = bem.bem_grid_create(ctx, ve, te), bem.bem_grid_create(ctx, vi, ti)
+        grids += [ge, gi]
+        k = float(rng.uniform(2.0, 8.0))
+        d = bi.plane_wave_directions(1, seed=u["seed"] * 1000 + 500 + i)[0]
+        probs.append(dict(ext=ge, intr=gi, k_ext=k, k_int=1.5 * k, rho=1.0, dir=d, levels=(le, li)))
+    bem.bem_solve_many(ctx, probs[:4])  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, reps = bem.bem_solve_many(ctx, probs)
+    t_many = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    its_single = 0
+    for p in probs:
+        _, r1 = bem.bem_solve_transmission(ctx, p["ext"], p["intr"], p["k_int"], p["k_ext"], p["rho"],
+                                           np.array([p["dir"]]), opts={"precision": bem.BEM_PREC_MIXED})
+        its_single += r1["iterations"]
+    t_single = time.perf_counter() - t0
+    for g in grids:
+        bem.bem_grid_destroy(g)
+    return {"instances": u["count"], "levels": [p["levels"] for p in probs],
+            "instances_per_s_one_call": u["count"] / t_many, "instances_per_s_one_call_each": u["count"] / t_single,
+            "speedup": t_single / t_many, "iterations_one_call": int(sum(r["iterations"] for r in reps)),
+            "iterations_one_call_each": int(its_single), "all_converged": all(r["converged"] for r in reps)}
+
+
 def kernel_roofline(name, ms, n, te, ti, Ne, Ni, pp_cache):
     """Roofline entry of one profiled kernel (per-launch averages)."""
     avg_s = ms / n / 1e3
@@ -518,7 +560,8 @@ def main():
                                 "(batches of 8), FP64 (batches of 8)",
                     "mixed_tensor_cores": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 1, 0),
                     "mixed_cuda_cores_8": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 0, 8),
-                    "fp64": run_batching(bem, ctx, bem.BEM_PREC_FP64)}
+                    "fp64": run_batching(bem, ctx, bem.BEM_PREC_FP64),
+                    "uneven_instances": run_uneven(bem, ctx)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

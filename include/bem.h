@@ -256,6 +256,32 @@ BEM_API bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext,
                                   bem_c128* v_int, bem_c128* w_int,
                                   int on_device, bem_solve_report* rep);
 
+/* Many independent transmission problems of uneven sizes in one call (the batching
+ * pattern for uneven instances; no counterpart in the paper, which solves one
+ * problem at a time).  Each instance has its own grids, wavenumbers, density ratio
+ * and one plane wave; the mixed-precision solve of eq. mtf:discrete runs for all of
+ * them together: the regular-pair assembly of all grids is one persistent launch,
+ * and every step of the lockstep GMRES / iterative refinement is one launch for all
+ * instances, each with its own Krylov process and stopping test, so each result is
+ * the one the instance gets alone (up to FP32 rounding of its assembly).
+ * opts: as for bem_solve_transmission; precision must be BEM_PREC_MIXED
+ * (batch_columns and tensor_cores do not apply).  Outputs per instance as in
+ * bem_solve_transmission (host memory unless on_device = 1); reports [count] may be
+ * NULL.  Grids may be shared between instances.                                   */
+typedef struct {
+    const bem_grid* ext;           /* exterior grid                                        */
+    const bem_grid* intr;          /* interior grid                                        */
+    bem_c128 k_ext, k_int;         /* wavenumbers                                          */
+    double rho_int_over_rho_ext;   /* density ratio (> 0)                                  */
+    double dir[3];                 /* unit propagation direction of the plane wave         */
+    bem_c128 amp;                  /* its amplitude                                        */
+    bem_c128 *v_ext, *w_ext;       /* outputs [N_ext]                                      */
+    bem_c128 *v_int, *w_int;       /* outputs [N_int]                                      */
+} bem_instance;
+
+BEM_API bem_status bem_solve_many(bem_context* ctx, int32_t count, const bem_instance* instances,
+                                  const bem_solve_opts* opts, int on_device, bem_solve_report* reports);
+
 /* ---------------------------------------------------------------- serving
  * A request server for streams of transmission solves (continuous batching):
  * submitted requests wait in a FIFO queue; up to max_inflight of them run at once,

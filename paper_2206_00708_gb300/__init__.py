@@ -63,6 +63,22 @@ class bem_solve_opts(C.Structure):
     ]
 
 
+class bem_instance(C.Structure):
+    _fields_ = [
+        ("ext", C.c_void_p),
+        ("intr", C.c_void_p),
+        ("k_ext", bem_c128),
+        ("k_int", bem_c128),
+        ("rho_int_over_rho_ext", C.c_double),
+        ("dir", C.c_double * 3),
+        ("amp", bem_c128),
+        ("v_ext", C.c_void_p),
+        ("w_ext", C.c_void_p),
+        ("v_int", C.c_void_p),
+        ("w_int", C.c_void_p),
+    ]
+
+
 class bem_solve_report(C.Structure):
     _fields_ = [
         ("iterations", C.c_int32),
@@ -160,6 +176,7 @@ _SIGNATURES = {
     "bem_serve_wait": (C.c_int32, [_VP, C.c_uint64, C.c_double]),
     "bem_serve_cancel": (C.c_int32, [_VP, C.c_uint64]),
     "bem_serve_get_stats": (C.c_int32, [_VP, C.POINTER(bem_serve_stats)]),
+    "bem_solve_many": (C.c_int32, [_VP, C.c_int32, _VP, _VP, C.c_int, _VP]),
     "bem_solve_transmission": (C.c_int32, [_VP, _VP, _VP, bem_c128, bem_c128, C.c_double,
                                            C.POINTER(bem_incident), C.POINTER(bem_solve_opts),
                                            _VP, _VP, _VP, _VP, C.c_int, C.POINTER(bem_solve_report)]),
@@ -436,6 +453,56 @@ def bem_solve_transmission(ctx, ext, intr, k_int, k_ext, rho_int_over_rho_ext, d
         err.outputs, err.report = out, report
         raise err
     return out, report
+
+
+def _opts(opts):
+    if opts is None:
+        return bem_solve_opts_default()
+    if isinstance(opts, dict):
+        o = bem_solve_opts_default()
+        for key, val in opts.items():
+            if key == "center":
+                o.center = (C.c_double * 3)(*val)
+            else:
+                setattr(o, key, val)
+        return o
+    return opts
+
+
+def bem_solve_many(ctx, problems, opts=None):
+    """Solve many independent transmission problems together (mixed precision).
+
+    problems: list of dicts with keys ext, intr (grid handles), k_ext, k_int, rho
+    (rho_int / rho_ext), dir (3 floats, unit) and optional amp (default 1).
+    Returns (list of output dicts v_ext, w_ext, v_int, w_int, list of report dicts);
+    raises BemError on failure (with .outputs and .reports attached).
+    """
+    if opts is None or isinstance(opts, dict):
+        opts = {"precision": BEM_PREC_MIXED, **(opts or {})}
+    o = _opts(opts)
+    n = len(problems)
+    arr = (bem_instance * n)()
+    outs = []
+    for i, p in enumerate(problems):
+        Ne, Ni = bem_grid_num_vertices(p["ext"]), bem_grid_num_vertices(p["intr"])
+        out = {k: np.zeros(m, dtype=np.complex128) for k, m in
+               (("v_ext", Ne), ("w_ext", Ne), ("v_int", Ni), ("w_int", Ni))}
+        outs.append(out)
+        q = arr[i]
+        q.ext, q.intr = p["ext"], p["intr"]
+        q.k_ext, q.k_int = _c128(p["k_ext"]), _c128(p["k_int"])
+        q.rho_int_over_rho_ext = float(p["rho"])
+        q.dir = (C.c_double * 3)(*[float(v) for v in p["dir"]])
+        q.amp = _c128(p.get("amp", 1.0))
+        q.v_ext, q.w_ext, q.v_int, q.w_int = [out[k].ctypes.data for k in ("v_ext", "w_ext", "v_int", "w_int")]
+    reps = (bem_solve_report * n)()
+    st = _lib.bem_solve_many(ctx, n, C.cast(arr, C.c_void_p), C.byref(o), 0, C.cast(reps, C.c_void_p))
+    reports = [{f: getattr(r, f) for f, _ in bem_solve_report._fields_} for r in reps]
+    if st != BEM_OK:
+        err = BemError(st, _lib.bem_last_error().decode())
+        err.outputs, err.reports = outs, reports
+        raise err
+    return outs, reports
 
 
 # ------------------------------------------------------------------ serving

@@ -25,6 +25,7 @@
 #include "bem_internal.cuh"
 
 #include <algorithm>
+#include <vector>
 
 namespace bem {
 
@@ -132,14 +133,35 @@ __device__ __forceinline__ bool regular_pair(int it, int is, int tl, int sl, con
              (tc == sb) | (tc == sc));
 }
 
+// everything one regular-pair tile pair needs from its grid
+struct Grid32 {
+    const TriRec32* rec;
+    const int32_t* tverts;
+    const uint32_t* tslots;
+    const int32_t* tstart;
+    const int32_t* vstart;
+    const int32_t* tvert;
+    KP32 P;
+    float2 *Vm, *Km, *Tm, *Dm;
+    int* err;
+    int ck;  // complex wavenumber
+};
+
+// One CTA's work: the regular pairs of test tile it and trial tile is (it <= is).
 template <bool CK>
-__global__ void __launch_bounds__(NT32, 1)
-k_regular32(const TriRec32* __restrict__ rec, const int32_t* __restrict__ tverts, const uint32_t* __restrict__ tslots,
-            const int32_t* __restrict__ tstart, const int32_t* __restrict__ vstart,
-            const int32_t* __restrict__ tvert, KP32 P, float2* __restrict__ Vm, float2* __restrict__ Km,
-            float2* __restrict__ Tm, float2* __restrict__ Dm, int* __restrict__ err) {
-    const int it = blockIdx.y, is = blockIdx.x;
-    if (it > is) return;
+__device__ __forceinline__ void regular32_tile(const Grid32& G, const int it, const int is) {
+    const TriRec32* __restrict__ rec = G.rec;
+    const int32_t* __restrict__ tverts = G.tverts;
+    const uint32_t* __restrict__ tslots = G.tslots;
+    const int32_t* __restrict__ tstart = G.tstart;
+    const int32_t* __restrict__ vstart = G.vstart;
+    const int32_t* __restrict__ tvert = G.tvert;
+    const KP32 P = G.P;
+    float2* __restrict__ Vm = G.Vm;
+    float2* __restrict__ Km = G.Km;
+    float2* __restrict__ Tm = G.Tm;
+    float2* __restrict__ Dm = G.Dm;
+    int* __restrict__ err = G.err;
     extern __shared__ float smem[];
     // accumulation slabs: [op V,K,T,D][re,im][high | low int32][TILE_NV * TILE_NV]
     constexpr int SLAB = TILE_NV * TILE_NV;
@@ -445,6 +467,32 @@ k_regular32(const TriRec32* __restrict__ rec, const int32_t* __restrict__ tverts
     }
 }
 
+template <bool CK>
+__global__ void __launch_bounds__(NT32, 1) k_regular32(Grid32 G) {
+    const int it = blockIdx.y, is = blockIdx.x;
+    if (it > is) return;
+    regular32_tile<CK>(G, it, is);
+}
+
+// Persistent form for many grids of uneven sizes in one launch: one CTA per SM
+// takes (grid, it, is) items from a shared counter until the list is exhausted.
+__global__ void __launch_bounds__(NT32, 1) k_regular32_many(const Grid32* __restrict__ grids,
+                                                            const int4* __restrict__ items, int nitems,
+                                                            int* __restrict__ counter) {
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int w = s_item;
+        __syncthreads();  // every thread has read s_item before it is overwritten
+        if (w >= nitems) break;
+        const int4 item = items[w];
+        if (grids[item.x].ck) regular32_tile<true>(grids[item.x], item.y, item.z);
+        else regular32_tile<false>(grids[item.x], item.y, item.z);
+        __syncthreads();  // the tile's shared memory is reused by the next item
+    }
+}
+
 __global__ void k_sincos_check(int n, float xmax, float* __restrict__ err) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -472,36 +520,37 @@ bem_status selftest_sincos(int n, float xmax, double* max_err, cudaStream_t s) {
     return BEM_OK;
 }
 
-bem_status assemble_regular_fp32(const bem_grid* g, double k_re, double k_im, float2* V, float2* K, float2* T,
-                                 float2* D, cudaStream_t s) {
-    KP32 P;
-    P.k_h = (float)k_re;
-    P.k_l = (float)(k_re - (double)P.k_h);
-    P.k_i = (float)k_im;
-    P.k2r = (float)(k_re * k_re - k_im * k_im);
-    P.k2i = (float)(2.0 * k_re * k_im);
-    P.n = g->nv;
-    if (g->ntile > 65535) {
-        set_error("grid too large for the tile grid of the mixed-precision assembly");
-        return BEM_E_INVALID_ARG;
-    }
-    const size_t smem = 16 * TILE_NV * TILE_NV * sizeof(float) + TILE_TRI * sizeof(TriRec32) + sizeof(TrialTile32);
-    // the attribute is per device and per function; setting it on every call is cheap and thread-safe
-    BEM_CUDA_TRY(cudaFuncSetAttribute(k_regular32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    BEM_CUDA_TRY(cudaFuncSetAttribute(k_regular32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid((unsigned)g->ntile, (unsigned)g->ntile);
-    const bool ck = k_im != 0.0;
-    DevBuf flag;
-    BEM_TRY(flag.alloc(sizeof(int), s));
-    BEM_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
-    if (ck)
-        BEM_LAUNCH(k_regular32<true>, grid, NT32, smem, s, g->rec32.as<TriRec32>(), g->t_verts.as<int32_t>(),
-                   g->t_slots.as<uint32_t>(), g->tile_tstart.as<int32_t>(), g->tile_vstart.as<int32_t>(),
-                   g->tile_vert.as<int32_t>(), P, V, K, T, D, flag.as<int>());
-    else
-        BEM_LAUNCH(k_regular32<false>, grid, NT32, smem, s, g->rec32.as<TriRec32>(), g->t_verts.as<int32_t>(),
-                   g->t_slots.as<uint32_t>(), g->tile_tstart.as<int32_t>(), g->tile_vstart.as<int32_t>(),
-                   g->tile_vert.as<int32_t>(), P, V, K, T, D, flag.as<int>());
+namespace {
+
+size_t regular32_smem() {
+    return 16 * TILE_NV * TILE_NV * sizeof(float) + TILE_TRI * sizeof(TriRec32) + sizeof(TrialTile32);
+}
+
+Grid32 grid32_args(const bem_grid* g, double k_re, double k_im, float2* V, float2* K, float2* T, float2* D,
+                   int* flag) {
+    Grid32 G{};
+    G.rec = g->rec32.as<TriRec32>();
+    G.tverts = g->t_verts.as<int32_t>();
+    G.tslots = g->t_slots.as<uint32_t>();
+    G.tstart = g->tile_tstart.as<int32_t>();
+    G.vstart = g->tile_vstart.as<int32_t>();
+    G.tvert = g->tile_vert.as<int32_t>();
+    G.P.k_h = (float)k_re;
+    G.P.k_l = (float)(k_re - (double)G.P.k_h);
+    G.P.k_i = (float)k_im;
+    G.P.k2r = (float)(k_re * k_re - k_im * k_im);
+    G.P.k2i = (float)(2.0 * k_re * k_im);
+    G.P.n = g->nv;
+    G.Vm = V;
+    G.Km = K;
+    G.Tm = T;
+    G.Dm = D;
+    G.err = flag;
+    G.ck = k_im != 0.0;
+    return G;
+}
+
+bem_status check_flag(const DevBuf& flag, cudaStream_t s) {
     int h_flag = 0;
     BEM_CUDA_TRY(cudaMemcpyAsync(&h_flag, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -511,6 +560,59 @@ bem_status assemble_regular_fp32(const bem_grid* g, double k_re, double k_im, fl
         return BEM_E_NONFINITE;
     }
     return BEM_OK;
+}
+
+}  // namespace
+
+bem_status assemble_regular_fp32(const bem_grid* g, double k_re, double k_im, float2* V, float2* K, float2* T,
+                                 float2* D, cudaStream_t s) {
+    if (g->ntile > 65535) {
+        set_error("grid too large for the tile grid of the mixed-precision assembly");
+        return BEM_E_INVALID_ARG;
+    }
+    const size_t smem = regular32_smem();
+    // the attribute is per device and per function; setting it on every call is cheap and thread-safe
+    BEM_CUDA_TRY(cudaFuncSetAttribute(k_regular32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BEM_CUDA_TRY(cudaFuncSetAttribute(k_regular32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)g->ntile, (unsigned)g->ntile);
+    DevBuf flag;
+    BEM_TRY(flag.alloc(sizeof(int), s));
+    BEM_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+    const Grid32 G = grid32_args(g, k_re, k_im, V, K, T, D, flag.as<int>());
+    if (G.ck) BEM_LAUNCH(k_regular32<true>, grid, NT32, smem, s, G);
+    else BEM_LAUNCH(k_regular32<false>, grid, NT32, smem, s, G);
+    return check_flag(flag, s);
+}
+
+bem_status assemble_regular_fp32_many(int count, const bem_grid* const* g, const double* k_re, const double* k_im,
+                                      float2* const* V, float2* const* K, float2* const* T, float2* const* D,
+                                      cudaStream_t s) {
+    if (count <= 0) return BEM_OK;
+    DevBuf flag, dgrids, ditems, counter;
+    BEM_TRY(flag.alloc(sizeof(int), s));
+    BEM_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+    std::vector<Grid32> grids(count);
+    std::vector<int4> items;
+    for (int i = 0; i < count; ++i) {
+        grids[i] = grid32_args(g[i], k_re[i], k_im[i], V[i], K[i], T[i], D[i], flag.as<int>());
+        for (int it = 0; it < (int)g[i]->ntile; ++it)
+            for (int is = it; is < (int)g[i]->ntile; ++is) items.push_back(make_int4(i, it, is, 0));
+    }
+    BEM_TRY(dgrids.alloc(grids.size() * sizeof(Grid32), s));
+    BEM_TRY(ditems.alloc(items.size() * sizeof(int4), s));
+    BEM_TRY(counter.alloc(sizeof(int), s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(dgrids.p, grids.data(), grids.size() * sizeof(Grid32), cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(ditems.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemsetAsync(counter.p, 0, sizeof(int), s));
+    const size_t smem = regular32_smem();
+    BEM_CUDA_TRY(cudaFuncSetAttribute(k_regular32_many, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0;
+    BEM_CUDA_TRY(cudaGetDevice(&dev));
+    BEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int ctas = std::max(1, std::min<int>(sms, (int)items.size()));
+    BEM_LAUNCH(k_regular32_many, ctas, NT32, smem, s, dgrids.as<Grid32>(), ditems.as<int4>(), (int)items.size(),
+               counter.as<int>());
+    return check_flag(flag, s);  // also keeps the host vectors alive until the copies are done
 }
 
 }  // namespace bem

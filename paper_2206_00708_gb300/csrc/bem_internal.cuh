@@ -214,6 +214,11 @@ bem_status assemble_operators_fp64(const bem_grid* g, double k_re, double k_im, 
                                    double2* V, double2* K, double2* T, double2* D, cudaStream_t s);
 
 // mortar.cu: COO of P_ab (rows: vertices of a, cols: vertices of b).
+// FP32 regular pairs of many grids in one persistent launch (assemble32.cu)
+bem_status assemble_regular_fp32_many(int count, const bem_grid* const* g, const double* k_re, const double* k_im,
+                                      float2* const* V, float2* const* K, float2* const* T, float2* const* D,
+                                      cudaStream_t s);
+
 // tensor-core multi-column MTF product (gemm_tc.cu)
 int tc_padded_columns(int R);
 size_t tc_workspace_bytes(const int64_t N[4], int RP);

@@ -49,6 +49,8 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                                    bem_c128 k_ext, double rho_ratio, const bem_incident* inc,
                                    const bem_solve_opts* o, bem_c128* v_ext, bem_c128* w_ext, bem_c128* v_int,
                                    bem_c128* w_int, int on_device, bem_solve_report* rep);
+bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst, const bem_solve_opts* o,
+                           int on_device, bem_solve_report* reps);
 
 }  // namespace bem
 
@@ -378,6 +380,35 @@ bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const b
     }
     return solve_transmission_impl(ctx, ext, intr, k_int, k_ext, rho_int_over_rho_ext, inc, &o, v_ext, w_ext, v_int,
                                    w_int, on_device, rep);
+}
+
+bem_status bem_solve_many(bem_context* ctx, int32_t count, const bem_instance* instances, const bem_solve_opts* opts,
+                          int on_device, bem_solve_report* reports) {
+    CTX_GUARD(ctx);
+    BEM_REQUIRE(count >= 1 && instances != nullptr, "need count >= 1 instances");
+    bem_solve_opts o;
+    if (opts) o = *opts;
+    else {
+        bem_solve_opts_default(&o);
+        o.precision = BEM_PREC_MIXED;
+    }
+    BEM_REQUIRE(o.precision == BEM_PREC_MIXED, "bem_solve_many runs the mixed-precision mode");
+    BEM_REQUIRE(o.gmres_tol >= 0.0 && o.gmres_maxiter >= 1, "bad GMRES options");
+    BEM_REQUIRE(o.n_singular >= 1 && o.n_singular <= 16, "n_singular must be in [1, 16]");
+    BEM_REQUIRE(o.mtf_variant == BEM_MTF_DERIVED || o.mtf_variant == BEM_MTF_PRINTED, "unknown MTF variant");
+    BEM_REQUIRE(o.ir_inner_tol > 0.0 && o.ir_inner_tol < 1.0, "ir_inner_tol must be in (0, 1)");
+    for (int i = 0; i < count; ++i) {
+        const bem_instance& q = instances[i];
+        BEM_REQUIRE(q.ext != nullptr && q.intr != nullptr, "null grid");
+        BEM_REQUIRE(q.v_ext && q.w_ext && q.v_int && q.w_int, "null output array");
+        BEM_REQUIRE(std::isfinite(q.rho_int_over_rho_ext) && q.rho_int_over_rho_ext > 0.0, "density ratio must be > 0");
+        BEM_REQUIRE(std::isfinite(q.k_int.re) && std::isfinite(q.k_int.im) && std::isfinite(q.k_ext.re) &&
+                        std::isfinite(q.k_ext.im) && std::isfinite(q.amp.re) && std::isfinite(q.amp.im),
+                    "wavenumber or amplitude is not finite");
+        const double nd = std::sqrt(q.dir[0] * q.dir[0] + q.dir[1] * q.dir[1] + q.dir[2] * q.dir[2]);
+        BEM_REQUIRE(std::isfinite(nd) && std::fabs(nd - 1.0) < 1e-6, "incident directions must be unit vectors");
+    }
+    return solve_many_impl(ctx, count, instances, &o, on_device, reports);
 }
 
 }  // extern "C"

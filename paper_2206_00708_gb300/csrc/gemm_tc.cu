@@ -21,9 +21,12 @@
 // threads stage A (split into Ah, Al) and copy Bh, Bl into shared memory in the
 // canonical no-swizzle K-major layout (core matrices of 8 rows x 16 bytes); one
 // thread issues 4 x 3 MMAs (M = 128, N = 2R, K = 8) into one of 2-8 TMEM accumulators
-// (chosen by stage, summed in FP64 at the end) and commits them to the stage's mbarrier; two stages alternate so that the loads of
-// stage s + 1 overlap the MMAs of stage s.  The epilogue reads the accumulator with
-// tcgen05.ld (warps 0-3: real parts, warps 4-7: imaginary parts).
+// (chosen by stage, summed in FP64 at the end) and commits them to the stage's
+// mbarrier; two shared-memory stages alternate and the global loads of stage s + 1
+// are in flight while stage s is staged and issued.  With fewer row tiles than SMs
+// the K range is split between two CTAs whose results are added into a zeroed z
+// (two addends: their order cannot change the sum).  The epilogue reads the
+// accumulators with tcgen05.ld (warps 0-3: real parts, warps 4-7: imaginary parts).
 #include "bem_internal.cuh"
 
 #include <algorithm>
@@ -180,7 +183,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs P, double* __r
     const float* __restrict__ a1 = br.a1;
     const float* __restrict__ a2 = br.a2;
     const int64_t N = br.N;
-    const int S = br.stages;
+    // K split: blockIdx.y of gridDim.y takes stages [s_begin, s_end)
+    const int s_begin = (int)((int64_t)br.stages * blockIdx.y / gridDim.y);
+    const int s_end = (int)((int64_t)br.stages * (blockIdx.y + 1) / gridDim.y);
+    const int S = s_end - s_begin;
     const int nb = 2 * P.RP;                 // MMA N and B rows
     const int b_stage = nb * TC_KS * 4;      // bytes of one B stage (hi or lo)
     const int stage_bytes = 2 * TC_A_STAGE + 2 * b_stage;
@@ -215,46 +221,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs P, double* __r
     const int64_t grow = (int64_t)tile * TC_M + arow;  // row within the block row
     const bool row_ok = grow < N;
 
-    for (int s = 0; s < S; ++s) {
-        const int buf = s & 1;
+    // A of the next stage is loaded into registers while the current stage is staged
+    // and its MMAs are issued
+    float2 pa[8];
+    auto load_a = [&](int sg) {
+        const int64_t k0 = (int64_t)sg * TC_KS + ahalf * 16;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t k = k0 + 2 * q;
+            float2 v = make_float2(0.f, 0.f);
+            if (row_ok) {
+                if (k < 2 * N) v = *reinterpret_cast<const float2*>(a1 + grow * 2 * N + k);
+                else if (k < 4 * N) v = *reinterpret_cast<const float2*>(a2 + grow * 2 * N + (k - 2 * N));
+            }
+            pa[q] = v;
+        }
+    };
+    if (S > 0) load_a(s_begin);
+    for (int ls = 0; ls < S; ++ls) {
+        const int sg = s_begin + ls;  // global stage
+        const int buf = ls & 1;
         unsigned char* st = tsm + buf * stage_bytes;
-        if (s >= 2) {  // MMAs of stage s - 2 read this buffer
-            if (!mbar_wait(smem_u32(&mbar[buf]), (uint32_t)(((s - 2) >> 1) & 1))) s_fail = 1;
+        if (ls >= 2) {  // MMAs of stage ls - 2 read this buffer
+            if (!mbar_wait(smem_u32(&mbar[buf]), (uint32_t)(((ls - 2) >> 1) & 1))) s_fail = 1;
         }
         // A: 16 floats per thread, split into TF32 hi / lo
-        {
-            float av[16];
-            const int64_t k0 = (int64_t)s * TC_KS + ahalf * 16;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int64_t k = k0 + 2 * q;
-                float2 v = make_float2(0.f, 0.f);
-                if (row_ok) {
-                    if (k < 2 * N) v = *reinterpret_cast<const float2*>(a1 + grow * 2 * N + k);
-                    else if (k < 4 * N) v = *reinterpret_cast<const float2*>(a2 + grow * 2 * N + (k - 2 * N));
-                }
-                av[2 * q] = v.x;
-                av[2 * q + 1] = v.y;
-            }
-#pragma unroll
-            for (int g4 = 0; g4 < 4; ++g4) {
-                const int kk = ahalf * 16 + 4 * g4;
-                float4 h, l;
-                h.x = tf32_rn(av[4 * g4 + 0]); l.x = av[4 * g4 + 0] - h.x;
-                h.y = tf32_rn(av[4 * g4 + 1]); l.y = av[4 * g4 + 1] - h.y;
-                h.z = tf32_rn(av[4 * g4 + 2]); l.z = av[4 * g4 + 2] - h.z;
-                h.w = tf32_rn(av[4 * g4 + 3]); l.w = av[4 * g4 + 3] - h.w;
-                const uint32_t off = tile_off(arow, kk, TC_M);
-                *reinterpret_cast<float4*>(st + off) = h;
-                *reinterpret_cast<float4*>(st + TC_A_STAGE + off) = l;
-            }
+        for (int g4 = 0; g4 < 4; ++g4) {
+            const int kk = ahalf * 16 + 4 * g4;
+            const float a0 = pa[2 * g4].x, a1v = pa[2 * g4].y, a2v = pa[2 * g4 + 1].x, a3 = pa[2 * g4 + 1].y;
+            float4 h, l;
+            h.x = tf32_rn(a0); l.x = a0 - h.x;
+            h.y = tf32_rn(a1v); l.y = a1v - h.y;
+            h.z = tf32_rn(a2v); l.z = a2v - h.z;
+            h.w = tf32_rn(a3); l.w = a3 - h.w;
+            const uint32_t off = tile_off(arow, kk, TC_M);
+            *reinterpret_cast<float4*>(st + off) = h;
+            *reinterpret_cast<float4*>(st + TC_A_STAGE + off) = l;
         }
+        if (ls + 1 < S) load_a(sg + 1);
         // B: contiguous copies of the prepared stage tiles
         {
             const float4* __restrict__ sh = reinterpret_cast<const float4*>(
-                reinterpret_cast<const char*>(br.bh) + (int64_t)s * b_stage);
+                reinterpret_cast<const char*>(br.bh) + (int64_t)sg * b_stage);
             const float4* __restrict__ sl = reinterpret_cast<const float4*>(
-                reinterpret_cast<const char*>(br.bl) + (int64_t)s * b_stage);
+                reinterpret_cast<const char*>(br.bl) + (int64_t)sg * b_stage);
             float4* dh = reinterpret_cast<float4*>(st + 2 * TC_A_STAGE);
             float4* dl = reinterpret_cast<float4*>(st + 2 * TC_A_STAGE + b_stage);
             for (int i = threadIdx.x; i < b_stage / 16; i += TC_THREADS) {
@@ -272,8 +283,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs P, double* __r
             for (int k8 = 0; k8 < 4; ++k8) {
                 const uint64_t dah = smem_desc(ah + k8 * TC_A_SUB), dal = smem_desc(al + k8 * TC_A_SUB);
                 const uint64_t dbh = smem_desc(bh + k8 * nb * 32), dbl = smem_desc(bl + k8 * nb * 32);
-                const uint32_t d = tmem + (uint32_t)((s % nacc) * nb);
-                mma_tf32(d, dah, dbh, idesc, (s >= nacc || k8 > 0) ? 1 : 0);
+                const uint32_t d = tmem + (uint32_t)((ls % nacc) * nb);
+                mma_tf32(d, dah, dbh, idesc, (ls >= nacc || k8 > 0) ? 1 : 0);
                 mma_tf32(d, dah, dbl, idesc, 1);
                 mma_tf32(d, dal, dbh, idesc, 1);
             }
@@ -281,7 +292,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs P, double* __r
         }
     }
     // the last commit covers every MMA issued before it
-    if (!mbar_wait(smem_u32(&mbar[(S - 1) & 1]), (uint32_t)(((S - 1) >> 1) & 1))) s_fail = 1;
+    if (S > 0 && !mbar_wait(smem_u32(&mbar[(S - 1) & 1]), (uint32_t)(((S - 1) >> 1) & 1))) s_fail = 1;
     tc_fence_after();
     __syncthreads();
     if (!s_fail) {
@@ -290,7 +301,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs P, double* __r
         const int64_t row = (int64_t)tile * TC_M + 32 * q + lane;
         for (int c0 = 0; c0 < P.RP; c0 += 8) {
             double sum[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int acc = 0; acc < nacc && acc < S; ++acc) {
+            for (int acc = 0; acc < nacc && acc < S; ++acc) {  // accumulators this CTA wrote
                 uint32_t v[8];
                 const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * nb + h * P.RP + c0);
                 asm volatile(
@@ -306,7 +317,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs P, double* __r
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int r = c0 + j;
-                    if (r < P.R) z[2 * ((int64_t)r * P.n + br.base + row) + h] = sum[j];
+                    if (r >= P.R) continue;
+                    double* zz = z + 2 * ((int64_t)r * P.n + br.base + row) + h;
+                    if (gridDim.y == 1) *zz = sum[j];
+                    else atomicAdd(zz, sum[j]);  // two K halves into a zeroed z: order-free
                 }
             }
         }
@@ -386,7 +400,13 @@ bem_status mtf_product_tc(const float2* const a1[4], const float2* const a2[4], 
     // all 512 columns) never waits for another CTA
     const int smem = std::max(2 * (2 * TC_A_STAGE + 2 * b_stage), 116 * 1024);
     BEM_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    BEM_LAUNCH(k_gemm_tc, tiles, TC_THREADS, smem, s, ta, reinterpret_cast<double*>(z), err);
+    // fewer row tiles than SMs: split K in two halves (their two sums commute exactly)
+    int sms = 0, dev = 0;
+    BEM_CUDA_TRY(cudaGetDevice(&dev));
+    BEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int ksplit = tiles < sms ? 2 : 1;
+    if (ksplit > 1) BEM_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)R * n * sizeof(double2), s));
+    BEM_LAUNCH(k_gemm_tc, dim3(tiles, ksplit), TC_THREADS, smem, s, ta, reinterpret_cast<double*>(z), err);
     return BEM_OK;
 }
 

@@ -580,34 +580,45 @@ __global__ void k_dots_final(const double2* __restrict__ partial, int m, int nbl
     }
 }
 
-// w_r -= sum_{i<m} h_r[i] V_{i,r}   or (overwrite) x_r = sum_{i<m_r} y_r[i] V_{i,r};
-// eight independent accumulators keep eight basis loads in flight per thread
-__global__ void k_combine(const double2* __restrict__ Vb, int64_t n, int R, int m, const int* __restrict__ mr,
-                          const double2* __restrict__ h, int64_t hstride, double2* __restrict__ w, int overwrite) {
+// w_r -= sum_{i<m} h_r[i] V_{i,r}   or (overwrite) x_r = sum_{i<m_r} y_r[i] V_{i,r}.
+// A block takes 32 rows; its 8 warps take the basis vectors i = warp (mod 8), four
+// loads in flight per thread, and the 8 partial sums of a row are added in a fixed
+// order: many more threads than rows for the latency-bound late iterations.
+__global__ void __launch_bounds__(256) k_combine(const double2* __restrict__ Vb, int64_t n, int R, int m,
+                                                 const int* __restrict__ mr, const double2* __restrict__ h,
+                                                 int64_t hstride, double2* __restrict__ w, int overwrite) {
     const int r = blockIdx.y;
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= n) return;
+    const int lr = threadIdx.x & 31, sl = threadIdx.x >> 5;
+    const int64_t e = blockIdx.x * 32ll + lr;
     const int mm = mr ? mr[r] : m;
     const double2* __restrict__ hr = h + r * hstride;
-    double2 s[8];
+    double2 s[4];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) s[u] = make_double2(0, 0);
-    int i = 0;
-    for (; i + 8 <= mm; i += 8) {
+    for (int u = 0; u < 4; ++u) s[u] = make_double2(0, 0);
+    if (e < n) {
+        int i = sl;
+        for (; i + 24 < mm; i += 32) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) s[u] = cfma(hr[i + u], Vb[((int64_t)(i + u) * R + r) * n + e], s[u]);
+            for (int u = 0; u < 4; ++u) s[u] = cfma(hr[i + 8 * u], Vb[((int64_t)(i + 8 * u) * R + r) * n + e], s[u]);
+        }
+        for (; i < mm; i += 8) s[0] = cfma(hr[i], Vb[((int64_t)i * R + r) * n + e], s[0]);
     }
-    for (; i < mm; ++i) s[0] = cfma(hr[i], Vb[((int64_t)i * R + r) * n + e], s[0]);
+    __shared__ double2 part[8][32];
+    part[sl][lr] = make_double2((s[0].x + s[1].x) + (s[2].x + s[3].x), (s[0].y + s[1].y) + (s[2].y + s[3].y));
+    __syncthreads();
+    if (sl == 0 && e < n) {
+        double2 t = part[0][lr];
 #pragma unroll
-    for (int u = 1; u < 8; ++u) {
-        s[0].x += s[u].x;
-        s[0].y += s[u].y;
-    }
-    double2* wr = w + (int64_t)r * n;
-    if (overwrite) wr[e] = s[0];
-    else {
-        const double2 q = wr[e];
-        wr[e] = make_double2(q.x - s[0].x, q.y - s[0].y);
+        for (int k = 1; k < 8; ++k) {
+            t.x += part[k][lr].x;
+            t.y += part[k][lr].y;
+        }
+        double2* wr = w + (int64_t)r * n;
+        if (overwrite) wr[e] = t;
+        else {
+            const double2 q = wr[e];
+            wr[e] = make_double2(q.x - t.x, q.y - t.y);
+        }
     }
 }
 
@@ -866,7 +877,7 @@ bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs
     const int64_t n = W.n, ldh = W.ldh, gs = W.gstride;
     double2* Vp = W.Vb.as<double2>();
     const dim3 eb(blocks_for(n, 256), R);
-    const dim3 eb64(blocks_for(n, 64), R);  // FP64-heavy row kernels: spread over every SM
+    const dim3 ecb(blocks_for(n, 32), R);  // k_combine: 32 rows per block
     BEM_CUDA_TRY(cudaMemsetAsync(W.H.p, 0, (size_t)R * ldh * ldh * 16, s));
     std::vector<HostQR> qr(R);
     std::vector<int> it(R, 0);
@@ -911,7 +922,7 @@ bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs
                 BEM_LAUNCH(k_dots_partial, dim3(W.nblk, gy, R), 256, 0, s, Vp, n, R, j + 1, W.w.as<double2>(),
                            W.nblk, W.partial.as<double2>());
                 BEM_LAUNCH(k_dots_final, dim3(j + 1, R), 32, 0, s, W.partial.as<double2>(), j + 1, W.nblk, h, hst, 0);
-                BEM_LAUNCH(k_combine, eb64, 64, 0, s, Vp, n, R, j + 1, nullptr, h, hst, W.w.as<double2>(), 0);
+                BEM_LAUNCH(k_combine, ecb, 256, 0, s, Vp, n, R, j + 1, nullptr, h, hst, W.w.as<double2>(), 0);
             }
             BEM_LAUNCH(k_add_cols, dim3(1, R), 256, 0, s, Hj, ldh * ldh, W.hbuf.as<double2>(), gs, j + 1);
             BEM_TRY(W.sq_norms(W.w.as<double2>(), s));
@@ -933,7 +944,7 @@ bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs
     }
     BEM_CUDA_TRY(cudaMemcpyAsync(W.mr.p, W.h_mr, R * 4, cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(cudaMemcpyAsync(W.y.p, W.h_y, (size_t)R * gs * 16, cudaMemcpyHostToDevice, s));
-    BEM_LAUNCH(k_combine, eb64, 64, 0, s, Vp, n, R, 0, W.mr.as<int>(), W.y.as<double2>(), gs, x, 1);
+    BEM_LAUNCH(k_combine, ecb, 256, 0, s, Vp, n, R, 0, W.mr.as<int>(), W.y.as<double2>(), gs, x, 1);
     BEM_CUDA_TRY(cudaStreamSynchronize(s));  // pinned h_y / h_mr are reused by the next run
     for (int r = 0; r < R; ++r) iters_out[r] = it[r];
     return BEM_OK;
@@ -1341,6 +1352,687 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
         rep->mtf_variant = o->mtf_variant;
         rep->outer_iterations = outer_used;
     }
+    return result;
+}
+
+// ================================================================ many instances
+// Independent transmission problems of uneven sizes (different grids, wavenumbers,
+// density ratios), one plane wave each, solved together: their vectors are
+// concatenated, every row-indexed kernel looks up the instance of its row, and each
+// step of the lockstep GMRES / refinement is one launch for all instances, each with
+// its own Krylov process and stopping test.  The regular-pair assembly of all their
+// grids is one persistent launch.  Mixed-precision mode.
+
+namespace {
+
+struct InstDesc {
+    int64_t off, n;    // the instance's vector occupies [off, off + n) of the concatenation
+    Blocks<float2> B;  // complex64 operator blocks (vector offsets relative to off)
+    MassPair M;        // mass matrices of its two grids
+    TransferCsr T;     // mortar transfer
+};
+
+// complex64 blocks, FP32 arithmetic, one warp per global row (compensated as k_gemm32)
+__global__ void __launch_bounds__(256) k_gemm32_many(const InstDesc* __restrict__ D, const int32_t* __restrict__ row_inst,
+                                                     int64_t total, const float2* __restrict__ xall,
+                                                     double2* __restrict__ z) {
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= total) return;
+    const InstDesc& d = D[row_inst[gw]];
+    const int64_t li = gw - d.off;
+    int b = 0;
+    while (b < 3 && li >= d.B.base[b + 1]) ++b;
+    const int64_t N = d.B.rows[b], i = li - d.B.base[b];
+    const float2* __restrict__ x = xall + d.off;
+    double2 out = make_double2(0, 0);
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const float2* __restrict__ a = (m == 0 ? d.B.A1[b] : d.B.A2[b]) + i * N;
+        const int64_t xo = m == 0 ? d.B.x1[b] : d.B.x2[b];
+        float sr = 0.f, si = 0.f, er = 0.f, ei = 0.f;
+        const int64_t j0 = ((reinterpret_cast<uintptr_t>(a) & 15) != 0) ? 1 : 0;
+        if (j0 && lane == 0 && N > 0) {
+            const float2 av = a[0], xx = x[xo];
+            sr = fmaf(av.x, xx.x, -av.y * xx.y);
+            si = fmaf(av.x, xx.y, av.y * xx.x);
+        }
+        const int64_t npair = (N - j0) / 2;
+        const float4* __restrict__ a4 = reinterpret_cast<const float4*>(a + j0);
+        for (int64_t p = lane; p < npair; p += 64) {
+            float cr = 0.f, ci = 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t pp = p + 32 * h;
+                if (pp < npair) {
+                    const float4 av = a4[pp];
+                    const int64_t j = j0 + 2 * pp;
+                    const float2 x0 = x[xo + j], x1 = x[xo + j + 1];
+                    cr = fmaf(av.x, x0.x, cr); cr = fmaf(-av.y, x0.y, cr);
+                    ci = fmaf(av.x, x0.y, ci); ci = fmaf(av.y, x0.x, ci);
+                    cr = fmaf(av.z, x1.x, cr); cr = fmaf(-av.w, x1.y, cr);
+                    ci = fmaf(av.z, x1.y, ci); ci = fmaf(av.w, x1.x, ci);
+                }
+            }
+            float t, e;
+            two_sum_f(sr, cr, t, e); sr = t; er += e;
+            two_sum_f(si, ci, t, e); si = t; ei += e;
+        }
+        if (((N - j0) & 1) && lane == 1) {
+            const float2 av = a[N - 1], xx = x[xo + N - 1];
+            float t, e;
+            two_sum_f(sr, fmaf(av.x, xx.x, -av.y * xx.y), t, e); sr = t; er += e;
+            two_sum_f(si, fmaf(av.x, xx.y, av.y * xx.x), t, e); si = t; ei += e;
+        }
+        const double2 v = warp_sum2(make_double2((double)sr + (double)er, (double)si + (double)ei));
+        const double c = m == 0 ? d.B.c1[b] : d.B.c2[b];
+        out.x += c * v.x;
+        out.y += c * v.y;
+    }
+    if (lane == 0) z[gw] = out;
+}
+
+// complex64 blocks, FP64 arithmetic (outer residual of the refinement)
+__global__ void __launch_bounds__(256) k_gemm_c64_f64_many(const InstDesc* __restrict__ D,
+                                                           const int32_t* __restrict__ row_inst, int64_t total,
+                                                           const double2* __restrict__ xall, double2* __restrict__ z) {
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= total) return;
+    const InstDesc& d = D[row_inst[gw]];
+    const int64_t li = gw - d.off;
+    int b = 0;
+    while (b < 3 && li >= d.B.base[b + 1]) ++b;
+    const int64_t N = d.B.rows[b], i = li - d.B.base[b];
+    const double2* __restrict__ x = xall + d.off;
+    const float2* __restrict__ a1 = d.B.A1[b] + i * N;
+    const float2* __restrict__ a2 = d.B.A2[b] + i * N;
+    const int64_t x1 = d.B.x1[b], x2 = d.B.x2[b];
+    double2 s1 = make_double2(0, 0), s2 = make_double2(0, 0);
+    for (int64_t j = lane; j < N; j += 32) {
+        const float2 p = a1[j], q = a2[j];
+        s1 = cfma(make_double2(p.x, p.y), x[x1 + j], s1);
+        s2 = cfma(make_double2(q.x, q.y), x[x2 + j], s2);
+    }
+    const double2 u = warp_sum2(s1), v = warp_sum2(s2);
+    const double c1 = d.B.c1[b], c2 = d.B.c2[b];
+    if (lane == 0) z[gw] = make_double2(c1 * u.x + c2 * v.x, c1 * u.y + c2 * v.y);
+}
+
+__global__ void k_transfer_many(const InstDesc* __restrict__ D, const int32_t* __restrict__ row_inst, int64_t total,
+                                const double2* __restrict__ xall, double2* __restrict__ zall) {
+    const int64_t gw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gw >= total) return;
+    const InstDesc& d = D[row_inst[gw]];
+    const TransferCsr& T = d.T;
+    const int64_t g = gw - d.off;
+    const double2* x = xall + d.off;
+    const bool ext = g < 2 * T.Ne;
+    const int32_t* rp = ext ? T.trp : T.prp;
+    const int32_t* ci = ext ? T.tci : T.pci;
+    const double* v = ext ? T.tv : T.pv;
+    int64_t row, src;
+    double c;
+    if (g < T.Ne) { row = g; src = 2 * T.Ne; c = T.ca; }
+    else if (g < 2 * T.Ne) { row = g - T.Ne; src = 2 * T.Ne + T.Ni; c = T.cb; }
+    else if (g < 2 * T.Ne + T.Ni) { row = g - 2 * T.Ne; src = 0; c = T.cc; }
+    else { row = g - 2 * T.Ne - T.Ni; src = T.Ne; c = T.cd; }
+    double sr = 0.0, si = 0.0;
+    for (int32_t e = rp[row]; e < rp[row + 1]; ++e) {
+        const double p = v[e];
+        const double2 xx = x[src + ci[e]];
+        sr = fma(p, xx.x, sr);
+        si = fma(p, xx.y, si);
+    }
+    double2 zz = zall[gw];
+    zz.x = fma(c, sr, zz.x);
+    zz.y = fma(c, si, zz.y);
+    zall[gw] = zz;
+}
+
+__global__ void k_cheb_init_many(const InstDesc* __restrict__ D, const int32_t* __restrict__ row_inst,
+                                 int64_t total, const double2* __restrict__ z, double2* __restrict__ y,
+                                 double2* __restrict__ r, double2* __restrict__ d0, double inv_theta) {
+    const int64_t gw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gw >= total) return;
+    const InstDesc& d = D[row_inst[gw]];
+    const MassRow m = mass_row(d.M, gw - d.off);
+    const double2 zz = z[gw];
+    const double sc = m.dinv[m.i] * inv_theta;
+    y[gw] = make_double2(0, 0);
+    r[gw] = zz;
+    d0[gw] = make_double2(sc * zz.x, sc * zz.y);
+}
+
+__global__ void k_cheb_step_many(const InstDesc* __restrict__ D, const int32_t* __restrict__ row_inst,
+                                 int64_t total, const double2* __restrict__ dk, double2* __restrict__ dn,
+                                 double2* __restrict__ y, double2* __restrict__ r, double c1, double c2) {
+    const int64_t gw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gw >= total) return;
+    const InstDesc& d = D[row_inst[gw]];
+    const MassRow m = mass_row(d.M, gw - d.off);
+    const double2* dki = dk + d.off + m.base;
+    double2 md = make_double2(0, 0);
+    for (int32_t e = m.rp[m.i]; e < m.rp[m.i + 1]; ++e) {
+        const double v = m.v[e];
+        const double2 dd = dki[m.ci[e]];
+        md.x += v * dd.x;
+        md.y += v * dd.y;
+    }
+    const double2 d0 = dk[gw];
+    double2 yy = y[gw], rr = r[gw];
+    yy.x += d0.x;
+    yy.y += d0.y;
+    rr.x -= md.x;
+    rr.y -= md.y;
+    y[gw] = yy;
+    r[gw] = rr;
+    const double sc = c2 * m.dinv[m.i];
+    dn[gw] = make_double2(c1 * d0.x + sc * rr.x, c1 * d0.y + sc * rr.y);
+}
+
+// inner products over chunks that never straddle two instances: chunk c covers
+// rows [cs[c], ce[c]) of instance ci[c]; partial[i * nchunks + c]
+__global__ void __launch_bounds__(256) k_dots_partial_many(const double2* __restrict__ Vb, int64_t total, int m,
+                                                           const double2* __restrict__ w,
+                                                           const int64_t* __restrict__ cs,
+                                                           const int64_t* __restrict__ ce, int nchunks,
+                                                           double2* __restrict__ partial) {
+    const int c = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (i >= m) return;
+    const double2* __restrict__ v = Vb + (int64_t)i * total;
+    const int64_t e1 = ce[c];
+    double2 s[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s[u] = make_double2(0, 0);
+    int64_t e = cs[c] + lane;
+    for (; e + 96 < e1; e += 128) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double2 a = v[e + 32 * u], b = w[e + 32 * u];
+            s[u].x = fma(a.x, b.x, fma(a.y, b.y, s[u].x));
+            s[u].y = fma(a.x, b.y, fma(-a.y, b.x, s[u].y));
+        }
+    }
+    for (; e < e1; e += 32) {
+        const double2 a = v[e], b = w[e];
+        s[0].x = fma(a.x, b.x, fma(a.y, b.y, s[0].x));
+        s[0].y = fma(a.x, b.y, fma(-a.y, b.x, s[0].y));
+    }
+    const double2 t = warp_sum2(make_double2((s[0].x + s[1].x) + (s[2].x + s[3].x),
+                                             (s[0].y + s[1].y) + (s[2].y + s[3].y)));
+    if (lane == 0) partial[(int64_t)i * nchunks + c] = t;
+}
+
+// out[r * ostride + i] = sum of the chunks of instance r (grid (m, instances))
+__global__ void k_dots_final_many(const double2* __restrict__ partial, int nchunks, const int* __restrict__ cb,
+                                  double2* __restrict__ out, int64_t ostride) {
+    const int i = blockIdx.x, r = blockIdx.y;
+    double2 s = make_double2(0, 0);
+    for (int c = cb[r] + threadIdx.x; c < cb[r + 1]; c += 32) {
+        const double2 p = partial[(int64_t)i * nchunks + c];
+        s.x += p.x;
+        s.y += p.y;
+    }
+    s = warp_sum2(s);
+    if (threadIdx.x == 0) out[r * ostride + i] = s;
+}
+
+__global__ void __launch_bounds__(256) k_combine_many(const double2* __restrict__ Vb, int64_t total, int m,
+                                                      const int* __restrict__ mr, const int32_t* __restrict__ row_inst,
+                                                      const double2* __restrict__ h, int64_t hstride,
+                                                      double2* __restrict__ w, int overwrite) {
+    const int lr = threadIdx.x & 31, sl = threadIdx.x >> 5;
+    const int64_t e = blockIdx.x * 32ll + lr;
+    double2 s[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s[u] = make_double2(0, 0);
+    if (e < total) {
+        const int r = row_inst[e];
+        const int mm = mr ? mr[r] : m;
+        const double2* __restrict__ hr = h + r * hstride;
+        int i = sl;
+        for (; i + 24 < mm; i += 32) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s[u] = cfma(hr[i + 8 * u], Vb[(int64_t)(i + 8 * u) * total + e], s[u]);
+        }
+        for (; i < mm; i += 8) s[0] = cfma(hr[i], Vb[(int64_t)i * total + e], s[0]);
+    }
+    __shared__ double2 part[8][32];
+    part[sl][lr] = make_double2((s[0].x + s[1].x) + (s[2].x + s[3].x), (s[0].y + s[1].y) + (s[2].y + s[3].y));
+    __syncthreads();
+    if (sl == 0 && e < total) {
+        double2 t = part[0][lr];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) {
+            t.x += part[k][lr].x;
+            t.y += part[k][lr].y;
+        }
+        if (overwrite) w[e] = t;
+        else w[e] = make_double2(w[e].x - t.x, w[e].y - t.y);
+    }
+}
+
+// v = w / |w| per instance; the first row of each instance writes |w| to dst[r * dstride]
+__global__ void k_normalize_many(const InstDesc* __restrict__ D, const int32_t* __restrict__ row_inst,
+                                 const double2* __restrict__ w, int64_t total, const double2* __restrict__ nrm2,
+                                 double2* __restrict__ v, double2* __restrict__ dst, int64_t dstride) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int r = row_inst[e];
+    const double nr = sqrt(fmax(nrm2[r].x, 0.0));
+    if (dst && e == D[r].off) dst[r * dstride] = make_double2(nr, 0.0);
+    const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+    v[e] = make_double2(w[e].x * inv, w[e].y * inv);
+}
+
+// b = [-f, -g, 0, 0] of instance r from its plane-wave data f, g (N_ext each)
+__global__ void k_rhs_pack_one(const double2* __restrict__ f, const double2* __restrict__ g, int64_t Ne, int64_t n,
+                               double2* __restrict__ b) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double2 v = make_double2(0.0, 0.0);
+    if (e < Ne) v = make_double2(-f[e].x, -f[e].y);
+    else if (e < 2 * Ne) v = make_double2(-g[e - Ne].x, -g[e - Ne].y);
+    b[e] = v;
+}
+
+// device layout of many instances and the workspaces of their lockstep solve
+struct ManyLayout {
+    int count = 0, nchunks = 0;
+    int64_t total = 0;
+    std::vector<int64_t> off, len;
+    DevBuf desc, row_inst, cs, ce, cb;
+};
+
+struct ManyGmres {
+    int maxit = 0, count = 0;
+    int64_t total = 0, ldh = 0, gstride = 0;
+    DevBuf Vb, H, partial, hbuf, y, w, nrm, mr;
+    double2* h_nrm = nullptr;
+    double2* h_col = nullptr;
+    double2* h_y = nullptr;
+    int* h_mr = nullptr;
+    cudaEvent_t ev[GMRES_SLOTS] = {};
+    cudaStream_t stream = nullptr;
+    ~ManyGmres() {
+        if (stream) cudaStreamSynchronize(stream);
+        if (h_nrm) cudaFreeHost(h_nrm);
+        if (h_col) cudaFreeHost(h_col);
+        if (h_y) cudaFreeHost(h_y);
+        if (h_mr) cudaFreeHost(h_mr);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    bem_status init(int maxit_, const ManyLayout& L, cudaStream_t s) {
+        maxit = maxit_;
+        count = L.count;
+        total = L.total;
+        stream = s;
+        ldh = maxit + 1;
+        gstride = maxit + 2;
+        BEM_TRY(Vb.alloc((size_t)(maxit + 1) * total * 16, s));
+        BEM_TRY(H.alloc((size_t)count * ldh * ldh * 16, s));
+        BEM_TRY(partial.alloc((size_t)(maxit + 1) * L.nchunks * 16, s));
+        BEM_TRY(hbuf.alloc((size_t)count * gstride * 16, s));
+        BEM_TRY(y.alloc((size_t)count * gstride * 16, s));
+        BEM_TRY(w.alloc((size_t)total * 16, s));
+        BEM_TRY(nrm.alloc((size_t)count * 16, s));
+        BEM_TRY(mr.alloc((size_t)count * 4, s));
+        BEM_CUDA_TRY(cudaMallocHost(&h_nrm, (size_t)count * 16));
+        BEM_CUDA_TRY(cudaMallocHost(&h_col, (size_t)GMRES_SLOTS * count * gstride * 16));
+        BEM_CUDA_TRY(cudaMallocHost(&h_y, (size_t)count * gstride * 16));
+        BEM_CUDA_TRY(cudaMallocHost(&h_mr, (size_t)count * 4));
+        for (cudaEvent_t& e : ev) BEM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        return BEM_OK;
+    }
+};
+
+bem_status many_sq_norms(const ManyLayout& L, ManyGmres& W, const double2* v, cudaStream_t s) {
+    BEM_LAUNCH(k_dots_partial_many, dim3(L.nchunks, 1), 256, 0, s, v, L.total, 1, v, L.cs.as<int64_t>(),
+               L.ce.as<int64_t>(), L.nchunks, W.partial.as<double2>());
+    BEM_LAUNCH(k_dots_final_many, dim3(1, L.count), 32, 0, s, W.partial.as<double2>(), L.nchunks, L.cb.as<int>(),
+               W.nrm.as<double2>(), 1);
+    return BEM_OK;
+}
+
+bem_status many_norms(const ManyLayout& L, ManyGmres& W, const double2* v, double* out, cudaStream_t s) {
+    BEM_TRY(many_sq_norms(L, W, v, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(W.h_nrm, W.nrm.p, (size_t)L.count * 16, cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int r = 0; r < L.count; ++r) out[r] = std::sqrt(std::max(W.h_nrm[r].x, 0.0));
+    return BEM_OK;
+}
+
+using ApplyMany = std::function<bem_status(const double2* in, double2* out)>;
+
+// the lockstep GMRES of gmres_run, one Krylov process per instance
+bem_status gmres_run_many(const ManyLayout& L, ManyGmres& W, const ApplyMany& apply, const double2* rhs,
+                          const double* beta, const double* tol_abs, double2* x, int* iters_out, double* res_out,
+                          cudaStream_t s) {
+    const int C = L.count;
+    const int64_t T = L.total, ldh = W.ldh, gs = W.gstride;
+    double2* Vp = W.Vb.as<double2>();
+    const unsigned eb = blocks_for(T, 256), ecb = blocks_for(T, 32);
+    BEM_CUDA_TRY(cudaMemsetAsync(W.H.p, 0, (size_t)C * ldh * ldh * 16, s));
+    std::vector<HostQR> qr(C);
+    std::vector<int> it(C, 0);
+    std::vector<char> done(C, 0);
+    int ndone = 0;
+    for (int r = 0; r < C; ++r) {
+        qr[r].reset(beta[r]);
+        res_out[r] = beta[r];
+        if (!(beta[r] > tol_abs[r])) {
+            done[r] = 1;
+            ++ndone;
+        }
+    }
+    int launched = 0, checked = 0;
+    auto check_one = [&]() -> bem_status {
+        const int slot = checked % GMRES_SLOTS;
+        BEM_CUDA_TRY(cudaEventSynchronize(W.ev[slot]));
+        for (int r = 0; r < C; ++r) {
+            if (done[r]) continue;
+            const double est = qr[r].add_column(W.h_col + ((size_t)slot * C + r) * gs, checked);
+            it[r] = checked + 1;
+            res_out[r] = est;
+            if (!(est > tol_abs[r])) {
+                done[r] = 1;
+                ++ndone;
+            }
+        }
+        ++checked;
+        return BEM_OK;
+    };
+    const InstDesc* D = L.desc.as<InstDesc>();
+    const int32_t* RI = L.row_inst.as<int32_t>();
+    if (ndone < C) {
+        BEM_TRY(many_sq_norms(L, W, rhs, s));
+        BEM_LAUNCH(k_normalize_many, eb, 256, 0, s, D, RI, rhs, T, W.nrm.as<double2>(), Vp, nullptr, 0);
+        for (int j = 0; j < W.maxit && ndone < C; ++j) {
+            const double2* vj = Vp + (int64_t)j * T;
+            BEM_TRY(apply(vj, W.w.as<double2>()));
+            double2* Hj = W.H.as<double2>() + (int64_t)j * ldh;
+            const unsigned gy = (unsigned)((j + 1 + 7) / 8);
+            for (int pass = 0; pass < 2; ++pass) {
+                double2* h = pass == 0 ? Hj : W.hbuf.as<double2>();
+                const int64_t hst = pass == 0 ? ldh * ldh : gs;
+                BEM_LAUNCH(k_dots_partial_many, dim3(L.nchunks, gy), 256, 0, s, Vp, T, j + 1, W.w.as<double2>(),
+                           L.cs.as<int64_t>(), L.ce.as<int64_t>(), L.nchunks, W.partial.as<double2>());
+                BEM_LAUNCH(k_dots_final_many, dim3(j + 1, C), 32, 0, s, W.partial.as<double2>(), L.nchunks,
+                           L.cb.as<int>(), h, hst);
+                BEM_LAUNCH(k_combine_many, ecb, 256, 0, s, Vp, T, j + 1, nullptr, RI, h, hst, W.w.as<double2>(), 0);
+            }
+            BEM_LAUNCH(k_add_cols, dim3(1, C), 256, 0, s, Hj, ldh * ldh, W.hbuf.as<double2>(), gs, j + 1);
+            BEM_TRY(many_sq_norms(L, W, W.w.as<double2>(), s));
+            BEM_LAUNCH(k_normalize_many, eb, 256, 0, s, D, RI, W.w.as<double2>(), T, W.nrm.as<double2>(),
+                       Vp + (int64_t)(j + 1) * T, Hj + j + 1, ldh * ldh);
+            const int slot = j % GMRES_SLOTS;
+            BEM_CUDA_TRY(cudaMemcpy2DAsync(W.h_col + (size_t)slot * C * gs, gs * 16, Hj, ldh * ldh * 16,
+                                           (size_t)(j + 2) * 16, C, cudaMemcpyDeviceToHost, s));
+            BEM_CUDA_TRY(cudaEventRecord(W.ev[slot], s));
+            launched = j + 1;
+            while (checked < launched - GMRES_LAG && ndone < C) BEM_TRY(check_one());
+        }
+        while (checked < launched && ndone < C) BEM_TRY(check_one());
+    }
+    for (int r = 0; r < C; ++r) {
+        W.h_mr[r] = it[r];
+        qr[r].solve(it[r], W.h_y + (size_t)r * gs);
+    }
+    BEM_CUDA_TRY(cudaMemcpyAsync(W.mr.p, W.h_mr, (size_t)C * 4, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(W.y.p, W.h_y, (size_t)C * gs * 16, cudaMemcpyHostToDevice, s));
+    BEM_LAUNCH(k_combine_many, ecb, 256, 0, s, Vp, T, 0, W.mr.as<int>(), RI, W.y.as<double2>(), gs, x, 1);
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int r = 0; r < C; ++r) iters_out[r] = it[r];
+    return BEM_OK;
+}
+
+// operators, masses and mortar of one instance (owned buffers)
+struct InstanceData {
+    DevBuf M[8], mve, mvi, dve, dvi, prow, pcol, pval;
+    CsrBuf csr_p, csr_t;
+};
+
+}  // namespace
+
+bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst, const bem_solve_opts* o,
+                           int on_device, bem_solve_report* reps) {
+    cudaStream_t s = ctx->stream;
+    std::vector<InstanceData> data(count);
+    EventTimer t_asm, t_mor, t_sol;
+    // ---- operators: one persistent launch for the regular pairs of all grids, then the
+    // singular pairs grid by grid
+    cudaEventRecord(t_asm.a, s);
+    std::vector<const bem_grid*> grids;
+    std::vector<double> kre, kim;
+    std::vector<float2*> PV, PK, PT, PD;
+    for (int i = 0; i < count; ++i) {
+        const int64_t Ne = inst[i].ext->nv, Ni = inst[i].intr->nv;
+        for (int m = 0; m < 8; ++m) {
+            const size_t bytes = (size_t)(m < 4 ? Ne * Ne : Ni * Ni) * 8;
+            BEM_TRY(data[i].M[m].alloc(bytes, s));
+            BEM_CUDA_TRY(cudaMemsetAsync(data[i].M[m].p, 0, bytes, s));
+        }
+        for (int side = 0; side < 2; ++side) {
+            grids.push_back(side == 0 ? inst[i].ext : inst[i].intr);
+            const bem_c128 k = side == 0 ? inst[i].k_ext : inst[i].k_int;
+            kre.push_back(k.re);
+            kim.push_back(k.im);
+            PV.push_back(data[i].M[4 * side + 0].as<float2>());
+            PK.push_back(data[i].M[4 * side + 1].as<float2>());
+            PT.push_back(data[i].M[4 * side + 2].as<float2>());
+            PD.push_back(data[i].M[4 * side + 3].as<float2>());
+        }
+    }
+    BEM_TRY(assemble_regular_fp32_many((int)grids.size(), grids.data(), kre.data(), kim.data(), PV.data(), PK.data(),
+                                       PT.data(), PD.data(), s));
+    for (size_t g = 0; g < grids.size(); ++g)
+        BEM_TRY(assemble_singular_into_c64(grids[g], kre[g], kim[g], o->n_singular, PV[g], PK[g], PT[g], PD[g], s));
+    cudaEventRecord(t_asm.b, s);
+    // ---- masses and mortar, instance by instance
+    cudaEventRecord(t_mor.a, s);
+    for (int i = 0; i < count; ++i) {
+        const bem_grid *ge = inst[i].ext, *gi = inst[i].intr;
+        InstanceData& d = data[i];
+        BEM_TRY(d.mve.alloc(ge->m_nnz * 8, s));
+        BEM_TRY(d.mvi.alloc(gi->m_nnz * 8, s));
+        BEM_TRY(d.dve.alloc(ge->nv * 8, s));
+        BEM_TRY(d.dvi.alloc(gi->nv * 8, s));
+        BEM_TRY(mass_values(ge, d.mve.as<double>(), s));
+        BEM_TRY(mass_values(gi, d.mvi.as<double>(), s));
+        BEM_TRY(mass_inverse_diag(ge, d.mve.as<double>(), d.dve.as<double>(), s));
+        BEM_TRY(mass_inverse_diag(gi, d.mvi.as<double>(), d.dvi.as<double>(), s));
+        int64_t pnnz = 0;
+        BEM_TRY(mortar_coo(gi, ge, o->center, d.prow, d.pcol, d.pval, &pnnz, s));
+        BEM_TRY(build_csr(d.prow.as<int32_t>(), d.pcol.as<int32_t>(), d.pval.as<double>(), pnnz, gi->nv, d.csr_p, s));
+        BEM_TRY(build_csr(d.pcol.as<int32_t>(), d.prow.as<int32_t>(), d.pval.as<double>(), pnnz, ge->nv, d.csr_t, s));
+    }
+    cudaEventRecord(t_mor.b, s);
+    // ---- concatenated layout and instance descriptors
+    ManyLayout L;
+    L.count = count;
+    std::vector<InstDesc> desc(count);
+    std::vector<int32_t> rinst;
+    std::vector<int64_t> cs, ce;
+    std::vector<int> cb(count + 1, 0);
+    const double sgn = o->mtf_variant == BEM_MTF_PRINTED ? -1.0 : 1.0;
+    for (int i = 0; i < count; ++i) {
+        const int64_t Ne = inst[i].ext->nv, Ni = inst[i].intr->nv, n = 2 * Ne + 2 * Ni;
+        const double rho = inst[i].rho_int_over_rho_ext;
+        InstanceData& d = data[i];
+        InstDesc& D = desc[i];
+        D.off = L.total;
+        D.n = n;
+        const float2* m1[4] = {d.M[1].as<float2>(), d.M[3].as<float2>(), d.M[5].as<float2>(), d.M[7].as<float2>()};
+        const float2* m2[4] = {d.M[0].as<float2>(), d.M[2].as<float2>(), d.M[4].as<float2>(), d.M[6].as<float2>()};
+        fill_blocks(D.B, m1, m2, Ne, Ni);
+        D.M.rp[0] = inst[i].ext->m_rowptr.as<int32_t>(); D.M.ci[0] = inst[i].ext->m_col.as<int32_t>();
+        D.M.v[0] = d.mve.as<double>(); D.M.dinv[0] = d.dve.as<double>();
+        D.M.rp[1] = inst[i].intr->m_rowptr.as<int32_t>(); D.M.ci[1] = inst[i].intr->m_col.as<int32_t>();
+        D.M.v[1] = d.mvi.as<double>(); D.M.dinv[1] = d.dvi.as<double>();
+        D.M.Ne = Ne; D.M.Ni = Ni; D.M.n = n;
+        D.T.prp = d.csr_p.rp.as<int32_t>(); D.T.pci = d.csr_p.ci.as<int32_t>(); D.T.pv = d.csr_p.v.as<double>();
+        D.T.trp = d.csr_t.rp.as<int32_t>(); D.T.tci = d.csr_t.ci.as<int32_t>(); D.T.tv = d.csr_t.v.as<double>();
+        D.T.Ne = Ne; D.T.Ni = Ni; D.T.n = n;
+        D.T.ca = -0.5 * sgn;
+        D.T.cb = -0.5 * sgn / rho;
+        D.T.cc = 0.5 * sgn;
+        D.T.cd = 0.5 * sgn * rho;
+        L.off.push_back(L.total);
+        L.len.push_back(n);
+        rinst.insert(rinst.end(), (size_t)n, i);
+        cb[i] = (int)cs.size();
+        for (int64_t c0 = 0; c0 < n; c0 += DOT_ROWS) {
+            cs.push_back(L.total + c0);
+            ce.push_back(L.total + std::min<int64_t>(n, c0 + DOT_ROWS));
+        }
+        L.total += n;
+    }
+    cb[count] = (int)cs.size();
+    L.nchunks = (int)cs.size();
+    const int64_t T = L.total;
+    BEM_TRY(L.desc.alloc(desc.size() * sizeof(InstDesc), s));
+    BEM_TRY(L.row_inst.alloc(rinst.size() * 4, s));
+    BEM_TRY(L.cs.alloc(cs.size() * 8, s));
+    BEM_TRY(L.ce.alloc(ce.size() * 8, s));
+    BEM_TRY(L.cb.alloc(cb.size() * 4, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(L.desc.p, desc.data(), desc.size() * sizeof(InstDesc), cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(L.row_inst.p, rinst.data(), rinst.size() * 4, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(L.cs.p, cs.data(), cs.size() * 8, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(L.ce.p, ce.data(), ce.size() * 8, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(L.cb.p, cb.data(), cb.size() * 4, cudaMemcpyHostToDevice, s));
+    const InstDesc* Dd = L.desc.as<InstDesc>();
+    const int32_t* RI = L.row_inst.as<int32_t>();
+    // ---- workspaces
+    DevBuf z, wr, wa, wb, x32, bvec, sb, xsol, dvec, rvec, tmp, fg;
+    for (DevBuf* b : {&z, &wr, &wa, &wb, &bvec, &sb, &xsol, &dvec, &rvec, &tmp}) BEM_TRY(b->alloc((size_t)T * 16, s));
+    BEM_TRY(x32.alloc((size_t)T * 8, s));
+    const unsigned rows_blocks = blocks_for(T * 32, 256);
+    const double theta = 0.5 * (CHEB_BETA + CHEB_ALPHA), delta = 0.5 * (CHEB_BETA - CHEB_ALPHA);
+    const double sigma = theta / delta;
+    auto mass_many = [&](const double2* zin, double2* yout, int steps) -> bem_status {
+        const unsigned g64 = blocks_for(T, 64);
+        BEM_LAUNCH(k_cheb_init_many, g64, 64, 0, s, Dd, RI, T, zin, yout, wr.as<double2>(), wa.as<double2>(),
+                   1.0 / theta);
+        double rho = 1.0 / sigma;
+        double2 *dk = wa.as<double2>(), *dn = wb.as<double2>();
+        for (int k = 0; k < steps; ++k) {
+            const double rho_n = 1.0 / (2.0 * sigma - rho);
+            BEM_LAUNCH(k_cheb_step_many, g64, 64, 0, s, Dd, RI, T, dk, dn, yout, wr.as<double2>(), rho_n * rho,
+                       2.0 * rho_n / delta);
+            rho = rho_n;
+            std::swap(dk, dn);
+        }
+        return BEM_OK;
+    };
+    ApplyMany apply_work = [&](const double2* xin, double2* yout) -> bem_status {
+        BEM_LAUNCH(k_to_c64, blocks_for(T, 256), 256, 0, s, xin, T, x32.as<float2>());
+        BEM_LAUNCH(k_gemm32_many, rows_blocks, 256, 0, s, Dd, RI, T, x32.as<float2>(), z.as<double2>());
+        BEM_LAUNCH(k_transfer_many, blocks_for(T, 64), 64, 0, s, Dd, RI, T, xin, z.as<double2>());
+        return mass_many(z.as<double2>(), yout, CHEB_STEPS_INNER);
+    };
+    ApplyMany apply_fp64 = [&](const double2* xin, double2* yout) -> bem_status {
+        BEM_LAUNCH(k_gemm_c64_f64_many, rows_blocks, 256, 0, s, Dd, RI, T, xin, z.as<double2>());
+        BEM_LAUNCH(k_transfer_many, blocks_for(T, 64), 64, 0, s, Dd, RI, T, xin, z.as<double2>());
+        return mass_many(z.as<double2>(), yout, CHEB_STEPS);
+    };
+    // ---- right-hand sides
+    cudaEventRecord(t_sol.a, s);
+    int64_t maxNe = 0;
+    for (int i = 0; i < count; ++i) maxNe = std::max<int64_t>(maxNe, inst[i].ext->nv);
+    BEM_TRY(fg.alloc((size_t)2 * maxNe * 16, s));
+    DevBuf wave;
+    BEM_TRY(wave.alloc((size_t)5 * count * 8, s));
+    std::vector<double> hw(5 * (size_t)count);
+    for (int i = 0; i < count; ++i) {
+        hw[2 * i] = inst[i].amp.re;
+        hw[2 * i + 1] = inst[i].amp.im;
+        for (int dd = 0; dd < 3; ++dd) hw[2 * count + 3 * i + dd] = inst[i].dir[dd];
+    }
+    BEM_CUDA_TRY(cudaMemcpyAsync(wave.p, hw.data(), hw.size() * 8, cudaMemcpyHostToDevice, s));
+    for (int i = 0; i < count; ++i) {
+        const bem_grid* ge = inst[i].ext;
+        const int64_t Ne = ge->nv;
+        BEM_CUDA_TRY(cudaMemsetAsync(fg.p, 0, (size_t)2 * Ne * 16, s));
+        double2* f = fg.as<double2>();
+        double2* g = f + Ne;
+        BEM_LAUNCH(k_plane_wave, dim3(blocks_for(ge->nt, 128), 1), 128, 0, s, ge->rec.as<TriRec>(),
+                   ge->tri.as<int32_t>(), ge->nt, inst[i].k_ext.re, inst[i].k_ext.im,
+                   wave.as<double>() + 2 * count + 3 * i, wave.as<double2>() + i, Ne, f, g);
+        BEM_LAUNCH(k_rhs_pack_one, blocks_for(L.len[i], 256), 256, 0, s, f, g, Ne, L.len[i],
+                   bvec.as<double2>() + L.off[i]);
+    }
+    BEM_TRY(mass_many(bvec.as<double2>(), sb.as<double2>(), CHEB_STEPS));
+    const int maxit = (int)std::min<int64_t>(o->gmres_maxiter, T);
+    ManyGmres W;
+    BEM_TRY(W.init(maxit, L, s));
+    std::vector<double> beta(count), tol_abs(count), rn(count), est(count), inner_tol(count);
+    std::vector<int> its(count), total(count, 0);
+    BEM_TRY(many_norms(L, W, sb.as<double2>(), beta.data(), s));
+    for (int r = 0; r < count; ++r) tol_abs[r] = o->gmres_tol * beta[r];
+    // ---- iterative refinement, all instances in lockstep
+    BEM_CUDA_TRY(cudaMemsetAsync(xsol.p, 0, (size_t)T * 16, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(rvec.p, sb.p, (size_t)T * 16, cudaMemcpyDeviceToDevice, s));
+    rn = beta;
+    auto pending = [&](int r) { return beta[r] > 0.0 && rn[r] > tol_abs[r] && total[r] < o->gmres_maxiter; };
+    int outer = 0;
+    for (; outer < 12; ++outer) {
+        bool any = false;
+        for (int r = 0; r < count; ++r) {
+            inner_tol[r] = pending(r) ? std::max(tol_abs[r], o->ir_inner_tol * rn[r]) : rn[r];
+            any = any || pending(r);
+        }
+        if (!any) break;
+        BEM_TRY(gmres_run_many(L, W, apply_work, rvec.as<double2>(), rn.data(), inner_tol.data(), dvec.as<double2>(),
+                               its.data(), est.data(), s));
+        int moved = 0;
+        for (int r = 0; r < count; ++r) {
+            total[r] += its[r];
+            moved += its[r];
+        }
+        BEM_LAUNCH(k_acc, blocks_for(T, 256), 256, 0, s, xsol.as<double2>(), dvec.as<double2>(), T);
+        BEM_TRY(apply_fp64(xsol.as<double2>(), tmp.as<double2>()));
+        BEM_LAUNCH(k_sub, blocks_for(T, 256), 256, 0, s, sb.as<double2>(), tmp.as<double2>(), T, rvec.as<double2>());
+        BEM_TRY(many_norms(L, W, rvec.as<double2>(), rn.data(), s));
+        if (moved == 0) {
+            ++outer;
+            break;
+        }
+    }
+    // ---- outputs
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int i = 0; i < count; ++i) {
+        const int64_t Ne = inst[i].ext->nv, Ni = inst[i].intr->nv;
+        const double2* X = xsol.as<double2>() + L.off[i];
+        BEM_CUDA_TRY(cudaMemcpyAsync(inst[i].v_ext, X, Ne * 16, kind, s));
+        BEM_CUDA_TRY(cudaMemcpyAsync(inst[i].w_ext, X + Ne, Ne * 16, kind, s));
+        BEM_CUDA_TRY(cudaMemcpyAsync(inst[i].v_int, X + 2 * Ne, Ni * 16, kind, s));
+        BEM_CUDA_TRY(cudaMemcpyAsync(inst[i].w_int, X + 2 * Ne + Ni, Ni * 16, kind, s));
+    }
+    cudaEventRecord(t_sol.b, s);
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    bem_status result = BEM_OK;
+    const float ms_asm = t_asm.ms(), ms_mor = t_mor.ms(), ms_sol = t_sol.ms();
+    for (int r = 0; r < count; ++r) {
+        const double rel = beta[r] > 0.0 ? rn[r] / beta[r] : 0.0;
+        const bool conv = beta[r] == 0.0 || rel <= o->gmres_tol;
+        if (!conv) result = BEM_E_NOT_CONVERGED;
+        if (reps) {
+            reps[r].iterations = total[r];
+            reps[r].converged = conv ? 1 : 0;
+            reps[r].residual = rel;
+            reps[r].t_assembly_ms = ms_asm;
+            reps[r].t_mortar_ms = ms_mor;
+            reps[r].t_solve_ms = ms_sol;
+            reps[r].mtf_variant = o->mtf_variant;
+            reps[r].outer_iterations = outer;
+        }
+    }
+    if (result == BEM_E_NOT_CONVERGED)
+        set_error("GMRES did not reach the tolerance within gmres_maxiter iterations for some instance");
     return result;
 }
 
