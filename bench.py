@@ -374,7 +374,7 @@ def kernel_roofline(name, ms, n, te, ti, Ne, Ni, pp_cache):
     avg_s = ms / n / 1e3
     m = re.search(r"<(\d+)>", name)
     cols = int(m.group(1)) if m else 1  # right-hand sides per launch
-    if name.startswith("k_gemm32"):
+    if name.startswith("k_gemm32") or name.startswith("k_gemv_dd"):
         peak, kind = hbm_peak()
         bytes_ = 8 * 4 * (Ne * Ne + Ni * Ni)  # 8 complex64 blocks read once per operator product
         ach = bytes_ / avg_s / 1e9

@@ -52,7 +52,7 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
     e = b - (s - a);
 }
 __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-    p = a * b;
+    p = __fmul_rn(a, b);  // never contracted into a following sum
     e = fmaf(a, b, -p);
 }
 

@@ -167,6 +167,7 @@ struct bem_grid {
     // mass matrix CSR structure (rows = vertices) and per-triangle slot map
     bem::DevBuf m_rowptr, m_col, m_slot;   // m_slot [nt][3][3] CSR position
     int64_t m_nnz = 0;
+    int32_t m_maxrow = 0;                  // largest number of entries in a mass row
     double surface_area = 0.0;
     // tiles of the mixed-precision assembly (triangles in tile order)
     int64_t ntile = 0;

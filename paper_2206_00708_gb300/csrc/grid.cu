@@ -255,6 +255,8 @@ bem_status grid_build_geometry(bem_grid* g) {
                 slot[9 * t + 3 * a + b] = (int32_t)(it - col.begin());
             }
     g->m_nnz = (int64_t)col.size();
+    g->m_maxrow = 0;
+    for (int64_t v = 0; v < nv; ++v) g->m_maxrow = std::max(g->m_maxrow, rowptr[v + 1] - rowptr[v]);
     BEM_TRY(g->m_rowptr.alloc(rowptr.size() * 4, s));
     BEM_TRY(g->m_col.alloc(col.size() * 4, s));
     BEM_TRY(g->m_slot.alloc(slot.size() * 4, s));

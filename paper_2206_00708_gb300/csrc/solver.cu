@@ -39,7 +39,8 @@ namespace bem {
 namespace {
 
 constexpr int CHEB_STEPS = 34;        // error <= 2 * 3^-34 ~ 1e-16: FP64 applications
-constexpr int CHEB_STEPS_INNER = 17;  // error <= 2 * 3^-17 ~ 1.6e-8: inner solves of the refinement
+constexpr int CHEB_STEPS_INNER = 17;  // error <= 2 * 3^-17 ~ 1.6e-8: inner solves with FP32 products
+constexpr int CHEB_STEPS_DD = 24;     // error <= 2 * 3^-24 ~ 7e-12: inner solves with double-float products
 constexpr double CHEB_ALPHA = 0.5, CHEB_BETA = 2.0;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -318,6 +319,92 @@ __global__ void k_to_c64(const double2* __restrict__ x, int64_t n, float2* __res
     if (e < n) y[e] = make_float2((float)x[e].x, (float)x[e].y);
 }
 
+// x split into FP32 high and low parts, (Re hi, Im hi, Re lo, Im lo): x = hi + lo to
+// about 2^-48 relative
+__global__ void k_split_x(const double2* __restrict__ x, int64_t n, float4* __restrict__ xs) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double2 v = x[e];
+    const float hr = (float)v.x, hi = (float)v.y;
+    xs[e] = make_float4(hr, hi, (float)(v.x - (double)hr), (float)(v.y - (double)hi));
+}
+
+// s + p into the double-float pair (s, e): the rounding error of the FP32 sum and the
+// given exact remainder pe are carried in e
+__device__ __forceinline__ void dd_add(float& s, float& e, float p, float pe) {
+    float t, q;
+    two_sum_f(s, p, t, q);
+    s = t;
+    e += q + pe;
+}
+
+// (sr, si) += a x for a complex64 entry a = (ar, ai) and x = hi + lo (float4 as in
+// k_split_x): the products with the high part are split exactly (two-product by
+// FMA) and summed with two-sums; the products with the low part go to the error
+// words directly (their own rounding is below 2^-48 of a x)
+// (__fmul_rn keeps the compiler from contracting a product into the following sum,
+// which would break the two-sum)
+__device__ __forceinline__ void dd_cmac(float ar, float ai, float4 x, float& sr, float& er, float& si, float& ei) {
+    float p = __fmul_rn(ar, x.x);
+    dd_add(sr, er, p, fmaf(ar, x.x, -p));
+    p = __fmul_rn(-ai, x.y);
+    dd_add(sr, er, p, fmaf(-ai, x.y, -p));
+    er = fmaf(ar, x.z, er);
+    er = fmaf(-ai, x.w, er);
+    p = __fmul_rn(ar, x.y);
+    dd_add(si, ei, p, fmaf(ar, x.y, -p));
+    p = __fmul_rn(ai, x.x);
+    dd_add(si, ei, p, fmaf(ai, x.x, -p));
+    ei = fmaf(ar, x.w, ei);
+    ei = fmaf(ai, x.z, ei);
+}
+
+// complex64 blocks, one column, double-float arithmetic on the FP32 pipe: the stored
+// (FP32) operator applied to an FP64 vector to ~1e-12 relative, reading the same
+// 8 bytes per entry as k_gemm32<1>.  Used for the single-column inner products of the
+// refinement, which then converge on the stored system instead of stagnating at the
+// FP32 rounding of the product.
+__global__ void __launch_bounds__(256) k_gemv_dd(Blocks<float2> B, int64_t n, const float4* __restrict__ xs,
+                                                 double2* __restrict__ z) {
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= n) return;
+    int b = 0;
+    while (b < 3 && gw >= B.base[b + 1]) ++b;
+    const int64_t N = B.rows[b];
+    const int64_t i = gw - B.base[b];
+    double2 out = make_double2(0, 0);
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const float2* __restrict__ a = (m == 0 ? B.A1[b] : B.A2[b]) + i * N;
+        const float4* __restrict__ x = xs + (m == 0 ? B.x1[b] : B.x2[b]);
+        float sr = 0.f, er = 0.f, si = 0.f, ei = 0.f;
+        const int64_t j0 = ((reinterpret_cast<uintptr_t>(a) & 15) != 0) ? 1 : 0;
+        if (j0 && lane == 0 && N > 0) {
+            const float2 av = a[0];
+            dd_cmac(av.x, av.y, x[0], sr, er, si, ei);
+        }
+        const int64_t npair = (N - j0) / 2;
+        const float4* __restrict__ a4 = reinterpret_cast<const float4*>(a + j0);
+        for (int64_t p = lane; p < npair; p += 32) {
+            const float4 av = a4[p];
+            const int64_t j = j0 + 2 * p;
+            const float4 x0 = x[j], x1 = x[j + 1];
+            dd_cmac(av.x, av.y, x0, sr, er, si, ei);
+            dd_cmac(av.z, av.w, x1, sr, er, si, ei);
+        }
+        if (((N - j0) & 1) && lane == 1) {
+            const float2 av = a[N - 1];
+            dd_cmac(av.x, av.y, x[N - 1], sr, er, si, ei);
+        }
+        const double2 v = warp_sum2(make_double2((double)sr + (double)er, (double)si + (double)ei));
+        const double c = m == 0 ? B.c1[b] : B.c2[b];
+        out.x += c * v.x;
+        out.y += c * v.y;
+    }
+    if (lane == 0) z[gw] = out;
+}
+
 // ---------------------------------------------------------------- mortar transfer
 // P_ie (rows: interior vertices, columns: exterior vertices) and P_ei = P_ie^T in
 // CSR form, built once per solve from the COO list of the clipping kernel: zero
@@ -447,30 +534,61 @@ __global__ void k_transfer(TransferCsr T, const double2* __restrict__ xb, double
 }
 
 // ---------------------------------------------------------------- mass inverse
+// Mass matrices of the two grids in ELL form (column-major [W][N]: entry k of row i
+// at k * N + i; rows shorter than W padded with (i, 0)), so that all column indices
+// and values of a row are loaded at once, independent of each other.
 struct MassPair {
-    const int32_t *rp[2], *ci[2];
+    const int32_t* ci[2];
     const double *v[2], *dinv[2];
+    int W[2];
     int64_t Ne, Ni, n;
 };
 
 struct MassRow {
-    const int32_t *rp, *ci;
+    const int32_t* ci;
     const double *v, *dinv;
-    int64_t i, base;
+    int W;
+    int64_t N, i, base;
 };
 
 __device__ __forceinline__ MassRow mass_row(const MassPair& M, int64_t g) {
     MassRow m;
     const bool ext = g < 2 * M.Ne;
-    m.rp = ext ? M.rp[0] : M.rp[1];
     m.ci = ext ? M.ci[0] : M.ci[1];
     m.v = ext ? M.v[0] : M.v[1];
     m.dinv = ext ? M.dinv[0] : M.dinv[1];
+    m.W = ext ? M.W[0] : M.W[1];
+    m.N = ext ? M.Ne : M.Ni;
     if (g < M.Ne) { m.i = g; m.base = 0; }
     else if (g < 2 * M.Ne) { m.i = g - M.Ne; m.base = M.Ne; }
     else if (g < 2 * M.Ne + M.Ni) { m.i = g - 2 * M.Ne; m.base = 2 * M.Ne; }
     else { m.i = g - 2 * M.Ne - M.Ni; m.base = 2 * M.Ne + M.Ni; }
     return m;
+}
+
+// (M d)_i over the ELL row of m, d the vector block of that grid
+__device__ __forceinline__ double2 mass_apply_row(const MassRow& m, const double2* __restrict__ d) {
+    double2 md = make_double2(0, 0);
+    for (int k = 0; k < m.W; ++k) {
+        const double v = m.v[(int64_t)k * m.N + m.i];
+        const double2 dd = d[m.ci[(int64_t)k * m.N + m.i]];
+        md.x += v * dd.x;
+        md.y += v * dd.y;
+    }
+    return md;
+}
+
+// ELL copy of one grid's mass CSR (one thread per row)
+__global__ void k_mass_ell(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                           const double* __restrict__ val, int64_t N, int W, int32_t* __restrict__ ci,
+                           double* __restrict__ v) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int32_t b = rp[i], len = rp[i + 1] - b;
+    for (int k = 0; k < W; ++k) {
+        ci[(int64_t)k * N + i] = k < len ? col[b + k] : (int32_t)i;
+        v[(int64_t)k * N + i] = k < len ? val[b + k] : 0.0;
+    }
 }
 
 // y = 0, r = z, d = D^-1 r / theta  (blockIdx.y = right-hand side)
@@ -494,13 +612,7 @@ __global__ void k_cheb_step(MassPair M, const double2* __restrict__ dk, double2*
     if (g >= M.n) return;
     const int64_t off = blockIdx.y * M.n;
     const MassRow m = mass_row(M, g);
-    double2 md = make_double2(0, 0);
-    for (int32_t e = m.rp[m.i]; e < m.rp[m.i + 1]; ++e) {
-        const double v = m.v[e];
-        const double2 dd = dk[off + m.base + m.ci[e]];
-        md.x += v * dd.x;
-        md.y += v * dd.y;
-    }
+    const double2 md = mass_apply_row(m, dk + off + m.base);
     const double2 d0 = dk[off + g];
     double2 yy = y[off + g], rr = r[off + g];
     yy.x += d0.x;
@@ -659,6 +771,20 @@ __global__ void k_acc(double2* __restrict__ x, const double2* __restrict__ d, in
 }
 
 // ------------------------------------------------------------------ host side
+// ELL form of one grid's mass matrix (values of this solve)
+struct MassEll {
+    DevBuf ci, v;
+    int W = 0;
+    bem_status build(const bem_grid* g, const double* val, cudaStream_t s) {
+        W = std::max(1, (int)g->m_maxrow);
+        BEM_TRY(ci.alloc((size_t)W * g->nv * 4, s));
+        BEM_TRY(v.alloc((size_t)W * g->nv * 8, s));
+        BEM_LAUNCH(k_mass_ell, blocks_for(g->nv, 128), 128, 0, s, g->m_rowptr.as<int32_t>(), g->m_col.as<int32_t>(),
+                   val, g->nv, W, ci.as<int32_t>(), v.as<double>());
+        return BEM_OK;
+    }
+};
+
 struct MassOp {
     MassPair M{};
     double2 *r = nullptr, *dA = nullptr, *dB = nullptr;  // workspaces [R * n]
@@ -1132,17 +1258,23 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     // reading and writing up to 7 spare (in-bounds) columns past the batch
     const int RW = RB + 7;
     const bool tc_batches = use_tc && RB > 8;
+    // single-column inner products of the refinement in double-float arithmetic
+    const bool dd_single = mixed && RB == 1;
     const size_t colb = (size_t)n * 16;
-    DevBuf wz, wr, wa, wb, x32, tcw, tcerr;
+    DevBuf wz, wr, wa, wb, x32, tcw, tcerr, xsplit;
+    if (dd_single) BEM_TRY(xsplit.alloc((size_t)n * 16, s));
     BEM_TRY(wz.alloc(RW * colb, s));
     BEM_TRY(wr.alloc(RB * colb, s));
     BEM_TRY(wa.alloc(RB * colb, s));
     BEM_TRY(wb.alloc(RB * colb, s));
     MassOp mop;
-    mop.M.rp[0] = ge->m_rowptr.as<int32_t>(); mop.M.ci[0] = ge->m_col.as<int32_t>();
-    mop.M.v[0] = mve.as<double>(); mop.M.dinv[0] = dve.as<double>();
-    mop.M.rp[1] = gi->m_rowptr.as<int32_t>(); mop.M.ci[1] = gi->m_col.as<int32_t>();
-    mop.M.v[1] = mvi.as<double>(); mop.M.dinv[1] = dvi.as<double>();
+    MassEll ell_e, ell_i;
+    BEM_TRY(ell_e.build(ge, mve.as<double>(), s));
+    BEM_TRY(ell_i.build(gi, mvi.as<double>(), s));
+    mop.M.ci[0] = ell_e.ci.as<int32_t>(); mop.M.v[0] = ell_e.v.as<double>(); mop.M.W[0] = ell_e.W;
+    mop.M.dinv[0] = dve.as<double>();
+    mop.M.ci[1] = ell_i.ci.as<int32_t>(); mop.M.v[1] = ell_i.v.as<double>(); mop.M.W[1] = ell_i.W;
+    mop.M.dinv[1] = dvi.as<double>();
     mop.M.Ne = Ne; mop.M.Ni = Ni; mop.M.n = n;
     mop.r = wr.as<double2>(); mop.dA = wa.as<double2>(); mop.dB = wb.as<double2>();
     TransferCsr top;
@@ -1179,6 +1311,11 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
         if (mixed && tc_batches && R > 8)
             return mtf_product_tc(B32.A1, B32.A2, B32.c1, B32.c2, B32.rows, B32.base, B32.x1, B32.x2, n, R, xin, z,
                                   tcw.p, tcw.bytes, tcerr.as<int>(), s);
+        if (mixed && R == 1 && dd_single) {
+            BEM_LAUNCH(k_split_x, blocks_for(n, 256), 256, 0, s, xin, n, xsplit.as<float4>());
+            BEM_LAUNCH(k_gemv_dd, rows_blocks, 256, 0, s, B32, n, xsplit.as<float4>(), z);
+            return BEM_OK;
+        }
         if (mixed)
             BEM_LAUNCH(k_to_c64, blocks_for((int64_t)R * n, 256), 256, 0, s, xin, (int64_t)R * n, x32.as<float2>());
         for (int c0 = 0; c0 < R; c0 += 8) {
@@ -1217,7 +1354,8 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     Apply apply_work = [&](const double2* xin, double2* yout, int R) -> bem_status {
         BEM_TRY(gemm_work(xin, R));
         BEM_TRY(transfer_add(top, R, xin, z, s));
-        return mass_solve(mop, z, yout, R, s, mixed ? CHEB_STEPS_INNER : CHEB_STEPS);
+        return mass_solve(mop, z, yout, R, s,
+                          !mixed ? CHEB_STEPS : (R == 1 && dd_single) ? CHEB_STEPS_DD : CHEB_STEPS_INNER);
     };
     Apply apply_fp64 = [&](const double2* xin, double2* yout, int R) -> bem_status {
         BEM_TRY(gemm_fp64(xin, R));
@@ -1511,14 +1649,7 @@ __global__ void k_cheb_step_many(const InstDesc* __restrict__ D, const int32_t* 
     if (gw >= total) return;
     const InstDesc& d = D[row_inst[gw]];
     const MassRow m = mass_row(d.M, gw - d.off);
-    const double2* dki = dk + d.off + m.base;
-    double2 md = make_double2(0, 0);
-    for (int32_t e = m.rp[m.i]; e < m.rp[m.i + 1]; ++e) {
-        const double v = m.v[e];
-        const double2 dd = dki[m.ci[e]];
-        md.x += v * dd.x;
-        md.y += v * dd.y;
-    }
+    const double2 md = mass_apply_row(m, dk + d.off + m.base);
     const double2 d0 = dk[gw];
     double2 yy = y[gw], rr = r[gw];
     yy.x += d0.x;
@@ -1794,6 +1925,7 @@ bem_status gmres_run_many(const ManyLayout& L, ManyGmres& W, const ApplyMany& ap
 struct InstanceData {
     DevBuf M[8], mve, mvi, dve, dvi, prow, pcol, pval;
     CsrBuf csr_p, csr_t;
+    MassEll ell_e, ell_i;
 };
 
 }  // namespace
@@ -1869,10 +2001,12 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
         const float2* m1[4] = {d.M[1].as<float2>(), d.M[3].as<float2>(), d.M[5].as<float2>(), d.M[7].as<float2>()};
         const float2* m2[4] = {d.M[0].as<float2>(), d.M[2].as<float2>(), d.M[4].as<float2>(), d.M[6].as<float2>()};
         fill_blocks(D.B, m1, m2, Ne, Ni);
-        D.M.rp[0] = inst[i].ext->m_rowptr.as<int32_t>(); D.M.ci[0] = inst[i].ext->m_col.as<int32_t>();
-        D.M.v[0] = d.mve.as<double>(); D.M.dinv[0] = d.dve.as<double>();
-        D.M.rp[1] = inst[i].intr->m_rowptr.as<int32_t>(); D.M.ci[1] = inst[i].intr->m_col.as<int32_t>();
-        D.M.v[1] = d.mvi.as<double>(); D.M.dinv[1] = d.dvi.as<double>();
+        BEM_TRY(d.ell_e.build(inst[i].ext, d.mve.as<double>(), s));
+        BEM_TRY(d.ell_i.build(inst[i].intr, d.mvi.as<double>(), s));
+        D.M.ci[0] = d.ell_e.ci.as<int32_t>(); D.M.v[0] = d.ell_e.v.as<double>(); D.M.W[0] = d.ell_e.W;
+        D.M.dinv[0] = d.dve.as<double>();
+        D.M.ci[1] = d.ell_i.ci.as<int32_t>(); D.M.v[1] = d.ell_i.v.as<double>(); D.M.W[1] = d.ell_i.W;
+        D.M.dinv[1] = d.dvi.as<double>();
         D.M.Ne = Ne; D.M.Ni = Ni; D.M.n = n;
         D.T.prp = d.csr_p.rp.as<int32_t>(); D.T.pci = d.csr_p.ci.as<int32_t>(); D.T.pv = d.csr_p.v.as<double>();
         D.T.trp = d.csr_t.rp.as<int32_t>(); D.T.tci = d.csr_t.ci.as<int32_t>(); D.T.tv = d.csr_t.v.as<double>();
