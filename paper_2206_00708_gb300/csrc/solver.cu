@@ -41,6 +41,7 @@ namespace {
 constexpr int CHEB_STEPS = 34;        // error <= 2 * 3^-34 ~ 1e-16: FP64 applications
 constexpr int CHEB_STEPS_INNER = 17;  // error <= 2 * 3^-17 ~ 1.6e-8: inner solves with FP32 products
 constexpr int CHEB_STEPS_DD = 24;     // error <= 2 * 3^-24 ~ 7e-12: inner solves with double-float products
+constexpr double DD_SWITCH = 1e-2;    // inner relative residual below which single-column products run in FP32
 constexpr double CHEB_ALPHA = 0.5, CHEB_BETA = 2.0;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -999,7 +1000,7 @@ struct HostQR {
 // (R columns); returns per-column iterations and final estimates.
 bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs, const double* beta,
                      const double* tol_abs, double2* x, int* iters_out, double* res_out, cudaStream_t s,
-                     const StopCheck& stop) {
+                     const StopCheck& stop, double* progress = nullptr) {
     const int64_t n = W.n, ldh = W.ldh, gs = W.gstride;
     double2* Vp = W.Vb.as<double2>();
     const dim3 eb(blocks_for(n, 256), R);
@@ -1017,6 +1018,7 @@ bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs
             ++ndone;
         }
     }
+    if (progress) *progress = 1.0;
     int launched = 0, checked = 0;
     auto check_one = [&]() -> bem_status {  // iteration `checked`, whose copy is enqueued
         const int slot = checked % GMRES_SLOTS;
@@ -1030,6 +1032,12 @@ bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs
                 done[r] = 1;
                 ++ndone;
             }
+        }
+        if (progress) {  // largest relative estimate over the columns still iterating
+            double worst = 0.0;
+            for (int r = 0; r < R; ++r)
+                if (!done[r] && beta[r] > 0.0) worst = std::max(worst, res_out[r] / beta[r]);
+            *progress = worst;
         }
         ++checked;
         return BEM_OK;
@@ -1258,8 +1266,16 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     // reading and writing up to 7 spare (in-bounds) columns past the batch
     const int RW = RB + 7;
     const bool tc_batches = use_tc && RB > 8;
-    // single-column inner products of the refinement in double-float arithmetic
+    // Single-column inner solves of the refinement: the products run in double-float
+    // arithmetic while the inner residual is above DD_SWITCH of its right-hand side and
+    // in FP32 after it.  GMRES tolerates product errors that grow as the residual falls
+    // (the residual gap is a sum of each product's error times its coefficient in the
+    // solution, and those coefficients shrink with the residual), so a 1e-7 FP32
+    // product after the switch leaves the inner solve accurate to ~1e-9 and the
+    // refinement converges in one pass, without paying double-float on every product.
     const bool dd_single = mixed && RB == 1;
+    double inner_progress = 1.0;
+    auto dd_now = [&]() { return dd_single && inner_progress > DD_SWITCH; };
     const size_t colb = (size_t)n * 16;
     DevBuf wz, wr, wa, wb, x32, tcw, tcerr, xsplit;
     if (dd_single) BEM_TRY(xsplit.alloc((size_t)n * 16, s));
@@ -1311,7 +1327,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
         if (mixed && tc_batches && R > 8)
             return mtf_product_tc(B32.A1, B32.A2, B32.c1, B32.c2, B32.rows, B32.base, B32.x1, B32.x2, n, R, xin, z,
                                   tcw.p, tcw.bytes, tcerr.as<int>(), s);
-        if (mixed && R == 1 && dd_single) {
+        if (mixed && R == 1 && dd_now()) {
             BEM_LAUNCH(k_split_x, blocks_for(n, 256), 256, 0, s, xin, n, xsplit.as<float4>());
             BEM_LAUNCH(k_gemv_dd, rows_blocks, 256, 0, s, B32, n, xsplit.as<float4>(), z);
             return BEM_OK;
@@ -1355,7 +1371,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
         BEM_TRY(gemm_work(xin, R));
         BEM_TRY(transfer_add(top, R, xin, z, s));
         return mass_solve(mop, z, yout, R, s,
-                          !mixed ? CHEB_STEPS : (R == 1 && dd_single) ? CHEB_STEPS_DD : CHEB_STEPS_INNER);
+                          !mixed ? CHEB_STEPS : (R == 1 && dd_now()) ? CHEB_STEPS_DD : CHEB_STEPS_INNER);
     };
     Apply apply_fp64 = [&](const double2* xin, double2* yout, int R) -> bem_status {
         BEM_TRY(gemm_fp64(xin, R));
@@ -1432,7 +1448,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                 for (int r = 0; r < R; ++r)
                     inner_tol[r] = pending(r) ? std::max(tol_abs[r], o->ir_inner_tol * rn[r]) : rn[r];
                 BEM_TRY(gmres_run(W, R, apply_work, rvec.as<double2>(), rn.data(), inner_tol.data(),
-                                  dvec.as<double2>(), its.data(), est.data(), s, stop));
+                                  dvec.as<double2>(), its.data(), est.data(), s, stop, &inner_progress));
                 int moved = 0;
                 for (int r = 0; r < R; ++r) {
                     total[r] += its[r];
