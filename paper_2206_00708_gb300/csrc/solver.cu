@@ -41,7 +41,7 @@ namespace {
 constexpr int CHEB_STEPS = 34;        // error <= 2 * 3^-34 ~ 1e-16: FP64 applications
 constexpr int CHEB_STEPS_INNER = 17;  // error <= 2 * 3^-17 ~ 1.6e-8: inner solves with FP32 products
 constexpr int CHEB_STEPS_DD = 24;     // error <= 2 * 3^-24 ~ 7e-12: inner solves with double-float products
-constexpr double DD_SWITCH = 1e-2;    // inner relative residual below which single-column products run in FP32
+constexpr double DD_SWITCH = 1e-3;    // inner relative residual below which single-column products run in FP32
 constexpr double CHEB_ALPHA = 0.5, CHEB_BETA = 2.0;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
