@@ -22,8 +22,9 @@
 // canonical no-swizzle K-major layout (core matrices of 8 rows x 16 bytes); one
 // thread issues 4 x 3 MMAs (M = 128, N = 2R, K = 8) into one of 2-8 TMEM accumulators
 // (chosen by stage, summed in FP64 at the end) and commits them to the stage's
-// mbarrier; two shared-memory stages alternate and the global loads of stage s + 1
-// are in flight while stage s is staged and issued.  With fewer row tiles than SMs
+// mbarrier; two shared-memory stages alternate and the global loads of A for stages
+// s + 1 and s + 2 are in flight (two register buffers) while stage s is staged and
+// issued.  With fewer row tiles than SMs
 // the K range is split between two CTAs whose results are added into a zeroed z
 // (two addends: their order cannot change the sum).  The epilogue reads the
 // accumulators with tcgen05.ld (warps 0-3: real parts, warps 4-7: imaginary parts).
@@ -221,10 +222,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs P, double* __r
     const int64_t grow = (int64_t)tile * TC_M + arow;  // row within the block row
     const bool row_ok = grow < N;
 
-    // A of the next stage is loaded into registers while the current stage is staged
-    // and its MMAs are issued
-    float2 pa[8];
-    auto load_a = [&](int sg) {
+    // A is loaded into registers two stages ahead (two register buffers, used
+    // alternately), so two stages of global loads are in flight while a stage is
+    // staged and its MMAs are issued
+    auto load_a = [&](float2 (&pa)[8], int sg) {
         const int64_t k0 = (int64_t)sg * TC_KS + ahalf * 16;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -237,8 +238,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs P, double* __r
             pa[q] = v;
         }
     };
-    if (S > 0) load_a(s_begin);
-    for (int ls = 0; ls < S; ++ls) {
+    float2 pa0[8], pa1[8];
+    if (S > 0) load_a(pa0, s_begin);
+    if (S > 1) load_a(pa1, s_begin + 1);
+    auto stage = [&](float2 (&pa)[8], int ls) {
         const int sg = s_begin + ls;  // global stage
         const int buf = ls & 1;
         unsigned char* st = tsm + buf * stage_bytes;
@@ -259,7 +262,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs P, double* __r
             *reinterpret_cast<float4*>(st + off) = h;
             *reinterpret_cast<float4*>(st + TC_A_STAGE + off) = l;
         }
-        if (ls + 1 < S) load_a(sg + 1);
+        if (ls + 2 < S) load_a(pa, sg + 2);
         // B: contiguous copies of the prepared stage tiles
         {
             const float4* __restrict__ sh = reinterpret_cast<const float4*>(
@@ -290,6 +293,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs P, double* __r
             }
             mma_commit(smem_u32(&mbar[buf]));
         }
+    };
+    for (int ls = 0; ls < S; ls += 2) {
+        stage(pa0, ls);
+        if (ls + 1 < S) stage(pa1, ls + 1);
     }
     // the last commit covers every MMA issued before it
     if (S > 0 && !mbar_wait(smem_u32(&mbar[(S - 1) & 1]), (uint32_t)(((S - 1) >> 1) & 1))) s_fail = 1;
