@@ -470,8 +470,22 @@ def main():
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
+        # one step with every launch timed by the library's event profiler: the kernel
+        # table, and the two longest kernels for the rooflines
+        bem.bem_profile_select(None)
+        bem.bem_profile_reset()
+        bem.bem_profile_enable(True)
+        flush.zero_()
+        step(precision, out, w["tol"])
+        torch.cuda.synchronize()
+        bem.bem_profile_enable(False)
+        table = bem.bem_profile_table()
+        top = [p[0] for p in table[:2]]
+        # timed steps: only those two kernels are bracketed by events (on the library's
+        # stream), so the rooflines are measured over the timed region itself
         times, reports = [], []
         bem.bem_profile_reset()
+        bem.bem_profile_select(top)
         l0 = bem.bem_launch_count()
         with ClockSampler(local) as clocks:
             for _ in range(args.steps):
@@ -487,6 +501,8 @@ def main():
                 times.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
         launches = bem.bem_launch_count() - l0
+        timed_prof = bem.bem_profile_table()
+        bem.bem_profile_select(None)
         barrier()
         total = sum(times)
         if world > 1:
@@ -494,7 +510,7 @@ def main():
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             total = float(tt.item())
         return dict(out=out, times=times, reports=reports, launches=launches, clocks=clocks.summary(),
-                    value=world * args.steps / (total / 1e3), prof=bem.bem_profile_table())
+                    value=world * args.steps / (total / 1e3), prof=timed_prof, table=table)
 
     mixed = timed(bem.BEM_PREC_MIXED)
     fp64 = None if args.no_fp64 else timed(bem.BEM_PREC_FP64)
@@ -611,7 +627,7 @@ def main():
             "serving": serving,
             "batching": batching,
             "solve": solve_info(m["reports"][-1]),
-            "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in m["prof"][:10]],
+            "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in m["table"][:10]],
         }
         print(json.dumps(line), flush=True)
     bem.bem_context_destroy(ctx)

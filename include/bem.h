@@ -103,6 +103,10 @@ BEM_API bem_status bem_selftest(bem_context* ctx, int which, double* result);
  * its summed device time in ms and its number of launches.  Collecting waits
  * for the recorded events.  Not meant to be toggled while a solve is running. */
 BEM_API void       bem_profile_enable(int on);
+/* Restrict the timing to kernels whose names start with one of the comma-separated
+ * prefixes (NULL or "": every kernel), so that a few kernels can be timed inside a
+ * measured region without bracketing every launch. */
+BEM_API void       bem_profile_select(const char* prefixes);
 BEM_API void       bem_profile_reset(void);
 BEM_API int        bem_profile_count(void);
 BEM_API bem_status bem_profile_get(int index, char* name, int name_len, double* total_ms,

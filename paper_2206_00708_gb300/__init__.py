@@ -146,6 +146,7 @@ _SIGNATURES = {
     "bem_launch_count": (C.c_uint64, []),
     "bem_selftest": (C.c_int32, [_VP, C.c_int, C.POINTER(C.c_double)]),
     "bem_profile_enable": (None, [C.c_int]),
+    "bem_profile_select": (None, [C.c_char_p]),
     "bem_profile_reset": (None, []),
     "bem_profile_count": (C.c_int, []),
     "bem_profile_get": (C.c_int32, [C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double), _PI64]),
@@ -248,6 +249,11 @@ def bem_selftest(ctx, which=0):
 
 def bem_profile_enable(on=True):
     _lib.bem_profile_enable(int(bool(on)))
+
+
+def bem_profile_select(prefixes=None):
+    """Time only kernels whose names start with one of `prefixes` (list of str); None: all."""
+    _lib.bem_profile_select(",".join(prefixes).encode() if prefixes else None)
 
 
 def bem_profile_reset():

@@ -5,6 +5,7 @@
 
 #include <atomic>
 #include <cstdio>
+#include <cstring>
 #include <iterator>
 #include <map>
 #include <mutex>
@@ -23,6 +24,14 @@ std::mutex g_mu;
 std::vector<Live> g_live;
 std::vector<cudaEvent_t> g_pool;
 std::map<std::string, std::pair<double, int64_t>> g_acc;
+std::vector<std::string> g_select;  // name prefixes to time (empty: every kernel)
+
+bool selected_locked(const char* name) {
+    if (g_select.empty()) return true;
+    for (const auto& p : g_select)
+        if (std::strncmp(name, p.c_str(), p.size()) == 0) return true;
+    return false;
+}
 
 cudaEvent_t take_event() {
     cudaEvent_t e = nullptr;
@@ -55,6 +64,7 @@ void drain_locked() {
 int prof_begin(const char* name, cudaStream_t s) {
     if (!g_on.load(std::memory_order_relaxed)) return -1;
     std::lock_guard<std::mutex> lk(g_mu);
+    if (!selected_locked(name)) return -1;
     if (g_live.size() >= 65536) drain_locked();  // bound the number of pending events
     Live L{name, take_event(), take_event()};
     cudaEventRecord(L.a, s);
@@ -78,6 +88,21 @@ void bem_profile_enable(int on) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!on) drain_locked();
     g_on.store(on != 0);
+}
+
+void bem_profile_select(const char* prefixes) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_select.clear();
+    if (!prefixes) return;
+    std::string all(prefixes);
+    size_t pos = 0;
+    while (pos <= all.size()) {
+        const size_t c = all.find(',', pos);
+        const std::string item = all.substr(pos, c == std::string::npos ? std::string::npos : c - pos);
+        if (!item.empty()) g_select.push_back(item);
+        if (c == std::string::npos) break;
+        pos = c + 1;
+    }
 }
 
 void bem_profile_reset(void) {
