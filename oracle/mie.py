@@ -68,3 +68,24 @@ def mie_potentials(v_ext, v_int, d, k_e, k_i, rho_int_over_rho_ext, R=1.0):
     gDp, gNp, _, _ = mie_traces(v_ext, d, k_e, k_i, rho_int_over_rho_ext, R)
     _, _, gDm, gNm = mie_traces(v_int, d, k_e, k_i, rho_int_over_rho_ext, R)
     return -gDp, -gNp, gDm, gNm
+
+
+def mie_field(x, d, k_e, k_i, rho_int_over_rho_ext, R=1.0, n_max=None):
+    """Total field at points x [M, 3] off the sphere |x| = R: inside sum c_n j_n(k_i r) P_n,
+    outside sum (j_n(k_e r) + a_n h_n(k_e r)) P_n, each term times i^n (2n + 1); returns
+    (total, incident) so that the scattered field outside is total - incident."""
+    a, c = mie_coefficients(k_e, k_i, rho_int_over_rho_ext, R, n_max)
+    x = np.asarray(x, dtype=np.float64)
+    r = np.linalg.norm(x, axis=1)
+    rs = np.where(r > 0, r, 1.0)  # at the centre only n = 0 contributes (j_n(0) = 0 for n > 0)
+    ct = np.clip((x @ np.asarray(d, dtype=np.float64)) / rs, -1.0, 1.0)
+    inside = r < R
+    tot = np.zeros(len(x), dtype=np.complex128)
+    for n in range(len(a)):
+        Pn = eval_legendre(n, ct)
+        f = (1j ** n) * (2 * n + 1)
+        term_in = c[n] * spherical_jn(n, k_i * r)
+        term_out = spherical_jn(n, k_e * r) + a[n] * _h(n, k_e * np.where(inside, R, r))
+        tot += f * np.where(inside, term_in, term_out) * Pn
+    inc = np.exp(1j * k_e * (x @ np.asarray(d, dtype=np.float64)))
+    return tot, inc
