@@ -1,0 +1,64 @@
+"""Pins of the exterior PMCHWT oracle (oracle/pmchwt.py): convergence to the Mie
+series at O(h^2), agreement with the multiple-traces solution up to the
+discretisation error (the two formulations discretise the same problem), the
+transmission conditions satisfied by its interior potentials, and Table 1's
+structure (8 dense operators, 2 unknown potentials)."""
+import numpy as np
+
+import bem_inputs as bi
+from oracle.mie import mie_potentials
+from oracle.mtf import solve_transmission
+from oracle.pmchwt import pmchwt_matrix, solve_pmchwt
+
+
+def _merr(x, y, M):
+    d = x - y
+    return np.sqrt(np.real(np.conj(d) @ M @ d) / np.real(np.conj(y) @ M @ y))
+
+
+def test_pmchwt_converges_to_mie():
+    d = [0.0, 0.0, 1.0]
+    k_e, k_i, rr = 1.0, 2.0, 1.5
+    errs = []
+    for L in (1, 2):
+        ve, te, vi, ti = bi.transmission_pair(L, L, seed=1)
+        r = solve_pmchwt(ve, te, vi, ti, k_e, k_i, rr, d, tol=1e-10)
+        ref = mie_potentials(ve, vi, d, k_e, k_i, rr)
+        B = r["blocks"]
+        errs.append([_merr(r[key], ref[i], B[M]) for i, (key, M) in enumerate(
+            [("v_ext", "Me"), ("w_ext", "Me"), ("v_int", "Mi"), ("w_int", "Mi")])])
+    errs = np.array(errs)
+    assert np.all(errs[0] / errs[1] > 3.0), errs  # O(h^2)
+    assert errs[1].max() < 0.05, errs
+
+
+def test_pmchwt_agrees_with_mtf_to_discretisation_error():
+    d = np.array([0.0, 0.6, 0.8])
+    diffs = []
+    for L in (1, 2):
+        ve, te, vi, ti = bi.transmission_pair(L, L, seed=3, axes=[1.2, 0.9, 1.0])
+        p = solve_pmchwt(ve, te, vi, ti, 1.5, 2.5, 0.5, d, tol=1e-11)
+        m = solve_transmission(ve, te, vi, ti, 1.5, 2.5, 0.5, d, tol=1e-11, blocks=p["blocks"])
+        diffs.append(max(np.linalg.norm(p[k] - m[k]) / np.linalg.norm(m[k]) for k in ("v_ext", "w_ext")))
+    assert diffs[1] < diffs[0] and diffs[1] < 2e-2, diffs
+
+
+def test_pmchwt_interior_potentials_satisfy_the_transmission_conditions():
+    ve, te, vi, ti = bi.transmission_pair(2, 1, seed=5)
+    rho = 3.0
+    p = solve_pmchwt(ve, te, vi, ti, 1.0, 1.7, rho, [1.0, 0.0, 0.0], tol=1e-11)
+    B = p["blocks"]
+    assert np.allclose(B["Mi"] @ p["v_int"], -B["Pie"] @ p["v_ext"], rtol=0, atol=1e-12)
+    assert np.allclose(B["Mi"] @ p["w_int"], -rho * (B["Pie"] @ p["w_ext"]), rtol=0, atol=1e-12)
+
+
+def test_pmchwt_identical_grids_reduce_to_the_conforming_operator():
+    """With the interior grid equal to the exterior one, P_ie = M and the hat
+    transformation is the identity: the matrix is the conforming PMCHWT."""
+    from oracle.mtf import mtf_blocks
+    v, t = bi.icosphere(1)
+    B = mtf_blocks(v, t, v, t, 1.0, 2.0)
+    A = pmchwt_matrix(B, 2.0)
+    Ae, Ai = B["ext"], B["int"]
+    ref = np.block([[-Ae["K"] - Ai["K"], Ae["V"] + 2.0 * Ai["V"]], [Ae["D"] + Ai["D"] / 2.0, Ae["T"] + Ai["T"]]])
+    assert np.abs(A - ref).max() < 1e-12 * np.abs(ref).max()
