@@ -327,6 +327,32 @@ def run_batching(bem, ctx, precision, tensor_cores=1, batch_columns=0):
     return out
 
 
+def run_field(bem, ctx, w, ve, te, vi, ti, out):
+    """Fields of the headline solve (mixed-precision traces) on a 100 x 100 grid of
+    the plane z = 0 over [-2, 2]^2 (the paper evaluates its fields on a 100 x 100 plane
+    grid): the interior field with the interior grid and the scattered field with the
+    exterior grid, each at every point.  Their accuracy against the Mie series is
+    checked in the tests; here only the throughput."""
+    import torch
+    g1 = np.linspace(-2.0, 2.0, 100)
+    X, Y = np.meshgrid(g1, g1, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], axis=1)
+    ge, gi = bem.bem_grid_create(ctx, ve, te), bem.bem_grid_create(ctx, vi, ti)
+    host = {k: out[k][0].cpu().numpy() for k in out}
+    bem.bem_field(ctx, gi, w["k_int"], pts[:64], phi=host["v_int"], psi=host["w_int"])  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bem.bem_field(ctx, gi, w["k_int"], pts, phi=host["v_int"], psi=host["w_int"])
+    bem.bem_field(ctx, ge, w["k_ext"], pts, phi=host["v_ext"], psi=host["w_ext"])
+    t = time.perf_counter() - t0
+    bem.bem_grid_destroy(ge)
+    bem.bem_grid_destroy(gi)
+    evals = len(pts) * 6 * (len(te) + len(ti))  # (point, quadrature point) pairs of both calls
+    return {"points": len(pts), "plane": "z = 0, [-2, 2]^2, 100 x 100", "seconds": t,
+            "evaluations_per_s": evals / t,
+            "note": "interior and scattered fields of the at-scale traces, FP64 kernel, host buffers"}
+
+
 UNEVEN_WORKLOAD = dict(count=32, seed=42)
 
 
@@ -414,6 +440,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison arm")
     ap.add_argument("--no-accuracy", dest="accuracy", action="store_false",
                     help="skip the converged FP64 reference solve (profiling runs)")
+    ap.add_argument("--no-field", dest="field", action="store_false", help="skip the field-evaluation section")
     ap.add_argument("--no-batching", dest="batching", action="store_false",
                     help="skip the many-directions section")
     ap.add_argument("--serve-requests", type=int, default=24,
@@ -570,6 +597,10 @@ def main():
                    "saturated": {"fp64": sat[bem.BEM_PREC_FP64], "mixed": sat[bem.BEM_PREC_MIXED]},
                    "poisson": {"rate_per_s": rate, "fp64": rep[bem.BEM_PREC_FP64], "mixed": rep[bem.BEM_PREC_MIXED]}}
 
+    field = None
+    if args.field and rank == 0:
+        field = run_field(bem, ctx, w, ve, te, vi, ti, mixed["out"])
+
     batching = None
     if args.batching:
         bw = BATCH_WORKLOAD
@@ -626,6 +657,7 @@ def main():
             "e2e": e2e,
             "serving": serving,
             "batching": batching,
+            "field": field,
             "solve": solve_info(m["reports"][-1]),
             "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in m["table"][:10]],
         }

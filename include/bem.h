@@ -260,6 +260,22 @@ BEM_API bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext,
                                   bem_c128* v_int, bem_c128* w_int,
                                   int on_device, bem_solve_report* rep);
 
+/* Field of P1 densities at points off the surface (paper Sec. 2.1, eq.
+ * representation):
+ *     u(x) = [V psi](x) - [K phi](x)
+ *          = int G(x,y) psi(y) dy - int dG/dn(y)(x,y) phi(y) dy,   G = exp(ik|x-y|) / (4 pi |x-y|),
+ * integrated with the 6-point degree-4 rule of the regular Galerkin pairs on each
+ * triangle of g (points within about one triangle size of the surface get only that
+ * rule's accuracy).  With the interior grid, k_int and (v_int, w_int) of
+ * bem_solve_transmission this is the interior field; with the exterior grid, k_ext and
+ * (v_ext, w_ext) it is the scattered field (add the incident wave for the total field).
+ * phi, psi: [N] vertex values (either may be NULL: its term is left out, not both);
+ * points: [npts][3]; u: [npts].  All host memory, or all device memory with
+ * on_device = 1.  FP64; the result does not depend on scheduling.              */
+BEM_API bem_status bem_field(bem_context* ctx, const bem_grid* g, bem_c128 k, const bem_c128* phi,
+                             const bem_c128* psi, const double* points, int64_t npts, bem_c128* u,
+                             int on_device);
+
 /* Many independent transmission problems of uneven sizes in one call (the batching
  * pattern for uneven instances; no counterpart in the paper, which solves one
  * problem at a time).  Each instance has its own grids, wavenumbers, density ratio

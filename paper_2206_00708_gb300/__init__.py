@@ -178,6 +178,7 @@ _SIGNATURES = {
     "bem_serve_cancel": (C.c_int32, [_VP, C.c_uint64]),
     "bem_serve_get_stats": (C.c_int32, [_VP, C.POINTER(bem_serve_stats)]),
     "bem_solve_many": (C.c_int32, [_VP, C.c_int32, _VP, _VP, C.c_int, _VP]),
+    "bem_field": (C.c_int32, [_VP, _VP, bem_c128, _VP, _VP, _VP, _I64, _VP, C.c_int]),
     "bem_solve_transmission": (C.c_int32, [_VP, _VP, _VP, bem_c128, bem_c128, C.c_double,
                                            C.POINTER(bem_incident), C.POINTER(bem_solve_opts),
                                            _VP, _VP, _VP, _VP, C.c_int, C.POINTER(bem_solve_report)]),
@@ -459,6 +460,17 @@ def bem_solve_transmission(ctx, ext, intr, k_int, k_ext, rho_int_over_rho_ext, d
         err.outputs, err.report = out, report
         raise err
     return out, report
+
+
+def bem_field(ctx, grid, k, points, phi=None, psi=None):
+    """u [M] = V[psi] - K[phi] at points [M, 3] (host NumPy arrays); phi, psi: [N] or None."""
+    pts = np.ascontiguousarray(np.atleast_2d(points), dtype=np.float64)
+    u = np.zeros(len(pts), dtype=np.complex128)
+    ph = None if phi is None else np.ascontiguousarray(phi, dtype=np.complex128)
+    ps = None if psi is None else np.ascontiguousarray(psi, dtype=np.complex128)
+    _check(_lib.bem_field(ctx, grid, _c128(k), None if ph is None else ph.ctypes.data,
+                          None if ps is None else ps.ctypes.data, pts.ctypes.data, len(pts), u.ctypes.data, 0))
+    return u
 
 
 def _opts(opts):

@@ -51,6 +51,8 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                                    bem_c128* w_int, int on_device, bem_solve_report* rep);
 bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst, const bem_solve_opts* o,
                            int on_device, bem_solve_report* reps);
+bem_status field_impl(bem_context* ctx, const bem_grid* g, bem_c128 k, const bem_c128* phi, const bem_c128* psi,
+                      const double* points, int64_t npts, bem_c128* u, int on_device);
 
 }  // namespace bem
 
@@ -380,6 +382,19 @@ bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const b
     }
     return solve_transmission_impl(ctx, ext, intr, k_int, k_ext, rho_int_over_rho_ext, inc, &o, v_ext, w_ext, v_int,
                                    w_int, on_device, rep);
+}
+
+bem_status bem_field(bem_context* ctx, const bem_grid* g, bem_c128 k, const bem_c128* phi, const bem_c128* psi,
+                     const double* points, int64_t npts, bem_c128* u, int on_device) {
+    CTX_GUARD(ctx);
+    BEM_REQUIRE(g != nullptr, "null grid");
+    BEM_REQUIRE(phi != nullptr || psi != nullptr, "need phi or psi");
+    BEM_REQUIRE(npts >= 0 && (npts == 0 || (points != nullptr && u != nullptr)), "bad points or output");
+    BEM_REQUIRE(std::isfinite(k.re) && std::isfinite(k.im), "wavenumber is not finite");
+    if (npts == 0) return BEM_OK;
+    if (!on_device)
+        for (int64_t i = 0; i < 3 * npts; ++i) BEM_REQUIRE(std::isfinite(points[i]), "point is not finite");
+    return field_impl(ctx, g, k, phi, psi, points, npts, u, on_device);
 }
 
 bem_status bem_solve_many(bem_context* ctx, int32_t count, const bem_instance* instances, const bem_solve_opts* opts,

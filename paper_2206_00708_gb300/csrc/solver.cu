@@ -250,17 +250,19 @@ __global__ void __launch_bounds__(256) k_gemm32(Blocks<float2> B, int64_t n, con
         }
         const int64_t npair = (N - j0) / 2;
         const float4* __restrict__ a4 = reinterpret_cast<const float4*>(a + j0);
-        for (int64_t p = lane; p < npair; p += 64) {
-            // two 16-byte loads in flight per lane; four products summed plainly per
-            // right-hand side before the compensated update
+        // H 16-byte loads in flight per lane (streamed past L1: the operator is read
+        // once); 4 H products summed plainly per right-hand side before the
+        // compensated update
+        constexpr int H = R == 1 ? 4 : 2;
+        for (int64_t p = lane; p < npair; p += 32 * H) {
             float cr[R], ci[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) cr[r] = ci[r] = 0.f;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < H; ++h) {
                 const int64_t pp = p + 32 * h;
                 if (pp < npair) {
-                    const float4 av = a4[pp];
+                    const float4 av = __ldcs(a4 + pp);
                     const int64_t j = j0 + 2 * pp;
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
@@ -387,12 +389,18 @@ __global__ void __launch_bounds__(256) k_gemv_dd(Blocks<float2> B, int64_t n, co
         }
         const int64_t npair = (N - j0) / 2;
         const float4* __restrict__ a4 = reinterpret_cast<const float4*>(a + j0);
-        for (int64_t p = lane; p < npair; p += 32) {
-            const float4 av = a4[p];
-            const int64_t j = j0 + 2 * p;
-            const float4 x0 = x[j], x1 = x[j + 1];
-            dd_cmac(av.x, av.y, x0, sr, er, si, ei);
-            dd_cmac(av.z, av.w, x1, sr, er, si, ei);
+        for (int64_t p = lane; p < npair; p += 64) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t pp = p + 32 * h;
+                if (pp < npair) {
+                    const float4 av = __ldcs(a4 + pp);
+                    const int64_t j = j0 + 2 * pp;
+                    const float4 x0 = x[j], x1 = x[j + 1];
+                    dd_cmac(av.x, av.y, x0, sr, er, si, ei);
+                    dd_cmac(av.z, av.w, x1, sr, er, si, ei);
+                }
+            }
         }
         if (((N - j0) & 1) && lane == 1) {
             const float2 av = a[N - 1];
