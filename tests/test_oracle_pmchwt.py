@@ -62,3 +62,72 @@ def test_pmchwt_identical_grids_reduce_to_the_conforming_operator():
     Ae, Ai = B["ext"], B["int"]
     ref = np.block([[-Ae["K"] - Ai["K"], Ae["V"] + 2.0 * Ai["V"]], [Ae["D"] + Ai["D"] / 2.0, Ae["T"] + Ai["T"]]])
     assert np.abs(A - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_single_trace_exterior_pmchwt_is_the_pmchwt_matrix():
+    from oracle.mtf import mtf_blocks
+    from oracle.pmchwt import single_trace_matrix
+    ve, te, vi, ti = bi.transmission_pair(1, 1, seed=4)
+    B = mtf_blocks(ve, te, vi, ti, 1.0, 2.0)
+    A = single_trace_matrix(B, 0.7, "pmchwt_ext")
+    assert np.abs(A - pmchwt_matrix(B, 0.7)).max() < 1e-13 * np.abs(A).max()
+
+
+def test_single_trace_variants_converge_to_mie():
+    """Exterior Mueller, interior PMCHWT and interior Mueller on nonconforming sphere
+    pairs: all four potentials converge to the Mie series at O(h^2)."""
+    from oracle.mtf import mtf_blocks
+    from oracle.pmchwt import solve_single_trace
+    d = [0.0, 0.0, 1.0]
+    k_e, k_i, rr = 1.0, 2.0, 1.5
+    forms = ("muller_ext", "pmchwt_int", "muller_int")
+    errs = {f: [] for f in forms}
+    for L in (1, 2):
+        ve, te, vi, ti = bi.transmission_pair(L, L, seed=1)
+        B = mtf_blocks(ve, te, vi, ti, k_e, k_i)
+        ref = mie_potentials(ve, vi, d, k_e, k_i, rr)
+        for f in forms:
+            r = solve_single_trace(ve, te, vi, ti, k_e, k_i, rr, d, f, tol=1e-10, blocks=B)
+            errs[f].append([_merr(r[key], ref[i], B[M]) for i, (key, M) in enumerate(
+                [("v_ext", "Me"), ("w_ext", "Me"), ("v_int", "Mi"), ("w_int", "Mi")])])
+    for f in forms:
+        e = np.array(errs[f])
+        assert np.all(e[0] / e[1] > 3.0), (f, e)
+        assert e[1].max() < 0.05, (f, e)
+
+
+def test_interior_and_exterior_variants_coincide_on_identical_grids():
+    """With one grid for both sides (P_ie = M) the interior system is the exterior one
+    with v_i = -v_e, w_i = -(rho_i/rho_e) w_e substituted and rows rescaled, so the two
+    variants of each formulation give the same four potentials."""
+    from oracle.mtf import mtf_blocks
+    from oracle.pmchwt import solve_single_trace
+    v, t = bi.icosphere(2)
+    rho, d = 2.5, np.array([0.6, 0.0, 0.8])
+    B = mtf_blocks(v, t, v, t, 1.3, 2.1 + 0.1j)
+    for kind in ("pmchwt", "muller"):
+        a = solve_single_trace(v, t, v, t, 1.3, 2.1 + 0.1j, rho, d, kind + "_ext", tol=1e-12, blocks=B)
+        b = solve_single_trace(v, t, v, t, 1.3, 2.1 + 0.1j, rho, d, kind + "_int", tol=1e-12, blocks=B)
+        for key in ("v_ext", "w_ext", "v_int", "w_int"):
+            assert np.linalg.norm(a[key] - b[key]) < 1e-9 * np.linalg.norm(a[key]), (kind, key)
+
+
+def test_muller_without_contrast_returns_the_incident_traces():
+    """Same medium inside and out, same grid: the exterior Mueller operator is
+    M + A - A^ = M exactly (the hat is the identity map), so its solution is the L2
+    projection of the incident traces (phi_ext = -u_inc, psi_ext = -du_inc/dn); the
+    interior variant gives the interior traces +u_inc, +du_inc/dn."""
+    from oracle.mass import mass_matrix
+    from oracle.mtf import mtf_blocks, plane_wave_data
+    from oracle.pmchwt import solve_single_trace
+    v, t = bi.icosphere(2)
+    d = np.array([0.0, 1.0, 0.0])
+    B = mtf_blocks(v, t, v, t, 2.0, 2.0)
+    f, g = plane_wave_data(v, t, 2.0, d)
+    M = mass_matrix(v, t)
+    pf, pg = np.linalg.solve(M, f), np.linalg.solve(M, g)
+    e = solve_single_trace(v, t, v, t, 2.0, 2.0, 1.0, d, "muller_ext", tol=1e-13, blocks=B)
+    i = solve_single_trace(v, t, v, t, 2.0, 2.0, 1.0, d, "muller_int", tol=1e-13, blocks=B)
+    for got, want in ((e["v_ext"], -pf), (e["w_ext"], -pg), (i["v_int"], pf), (i["w_int"], pg)):
+        assert np.linalg.norm(got - want) < 1e-10 * np.linalg.norm(want)
+    assert e["iters"] <= 2 and i["iters"] <= 2
