@@ -441,6 +441,8 @@ def main():
     ap.add_argument("--no-accuracy", dest="accuracy", action="store_false",
                     help="skip the converged FP64 reference solve (profiling runs)")
     ap.add_argument("--no-field", dest="field", action="store_false", help="skip the field-evaluation section")
+    ap.add_argument("--no-single-trace", dest="single_trace", action="store_false",
+                    help="skip the single-trace formulations section")
     ap.add_argument("--no-batching", dest="batching", action="store_false",
                     help="skip the many-directions section")
     ap.add_argument("--serve-requests", type=int, default=24,
@@ -481,11 +483,12 @@ def main():
         return {k: torch.zeros((1, n), dtype=torch.complex128, device=dev)
                 for k, n in (("v_ext", Ne), ("w_ext", Ne), ("v_int", Ni), ("w_int", Ni))}
 
-    def step(precision, out, tol):
+    def step(precision, out, tol, formulation=0):
         ge = bem.bem_grid_create(ctx, xe, tre)
         gi = bem.bem_grid_create(ctx, xi, tri_)
         _, rep = bem.bem_solve_transmission(ctx, ge, gi, w["k_int"], w["k_ext"], w["rho"], dirs,
-                                            opts={"gmres_tol": tol, "precision": precision}, out=out, on_device=True)
+                                            opts={"gmres_tol": tol, "precision": precision,
+                                                  "formulation": formulation}, out=out, on_device=True)
         bem.bem_grid_destroy(ge)
         bem.bem_grid_destroy(gi)
         return rep
@@ -601,6 +604,44 @@ def main():
     if args.field and rank == 0:
         field = run_field(bem, ctx, w, ve, te, vi, ti, mixed["out"])
 
+    single = None
+    if args.single_trace and rank == 0:
+        # the single-trace formulations on the same workload: mixed-precision solves timed
+        # like the headline, accuracy against each one's own converged FP64 solve, and the
+        # distance of their exterior traces from the multiple-traces ones (discretisation)
+        rn = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+        single = {"note": "Sec. 2.2 single-trace systems on the nonconforming pair, discretised as eq. "
+                          "pmchwt:discrete: 2 unknowns per vertex of one grid; every product applies that "
+                          "grid's operators and P M^-1 A M^-1 P of the other grid's (never formed)"}
+        for name, form in (("pmchwt_ext", bem.BEM_FORM_PMCHWT), ("muller_ext", bem.BEM_FORM_MULLER),
+                           ("pmchwt_int", bem.BEM_FORM_PMCHWT_INT), ("muller_int", bem.BEM_FORM_MULLER_INT)):
+            pout = new_out()
+            step(bem.BEM_PREC_MIXED, pout, w["tol"], form)
+            ptimes, preps = [], []
+            for _ in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                preps.append(step(bem.BEM_PREC_MIXED, pout, w["tol"], form))
+                e1.record(stream)
+                e1.synchronize()
+                ptimes.append(e0.elapsed_time(e1))
+            entry = {"value": args.steps / (sum(ptimes) / 1e3), "unit": UNIT,
+                     "ms_per_step": sum(ptimes) / args.steps, "precision": "mixed",
+                     "solve": {k: preps[-1][k] for k in ("iterations", "outer_iterations", "residual",
+                                                         "t_assembly_ms", "t_solve_ms")},
+                     "exterior_traces_vs_mtf": {k: rn(pout[k], mixed["out"][k]) for k in ("v_ext", "w_ext")}}
+            if args.accuracy:
+                pref = new_out()
+                step(bem.BEM_PREC_FP64, pref, 1e-12, form)
+                torch.cuda.synchronize()
+                perr = {k: rn(pout[k], pref[k]) for k in pref}
+                entry["rel_l2_vs_fp64_converged"] = perr
+                entry["max_err"] = max(perr.values())
+            single[name] = entry
+
     batching = None
     if args.batching:
         bw = BATCH_WORKLOAD
@@ -658,6 +699,7 @@ def main():
             "serving": serving,
             "batching": batching,
             "field": field,
+            "single_trace": single,
             "solve": solve_info(m["reports"][-1]),
             "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in m["table"][:10]],
         }

@@ -77,6 +77,15 @@ typedef struct bem_sparse  bem_sparse;
 #define BEM_MTF_DERIVED 0   /* transfer blocks as derived from Sec. 2.2: returns phi_int, psi_int */
 #define BEM_MTF_PRINTED 1   /* transfer blocks with the signs printed in eq. mtf:discrete      */
 
+/* Boundary integral formulation of bem_solve_transmission (bem_solve_opts.formulation) */
+#define BEM_FORM_MTF        0  /* multiple-traces system of eq. mtf:discrete: 4 unknowns      */
+#define BEM_FORM_PMCHWT     1  /* exterior PMCHWT (eq. pmchwt:ext, discretised by eq.
+                                  pmchwt:discrete): 2 unknowns on the exterior grid          */
+#define BEM_FORM_MULLER     2  /* exterior Mueller (eq. muller:ext)                          */
+#define BEM_FORM_PMCHWT_INT 3  /* interior PMCHWT (eq. pmchwt:int): 2 unknowns on the
+                                  interior grid                                              */
+#define BEM_FORM_MULLER_INT 4  /* interior Mueller (eq. muller:int)                          */
+
 /* Thread-local message of the last failing call (never NULL). */
 BEM_API const char* bem_last_error(void);
 
@@ -226,6 +235,9 @@ typedef struct {
     int32_t tensor_cores;     /* BEM_PREC_MIXED batches of more than 8 right-hand sides: 1 (default)
                                  = products on the tcgen05 tensor cores (TF32, three-term split,
                                  FP32 accumulation), 0 = FP32 CUDA cores in groups of 8 columns    */
+    int32_t formulation;      /* BEM_FORM_* (default BEM_FORM_MTF); the single-trace systems are
+                                 available in bem_solve_transmission only (bem_solve_many and the
+                                 server solve the multiple-traces system)                         */
 } bem_solve_opts;
 
 typedef struct {
@@ -252,7 +264,23 @@ BEM_API void bem_solve_opts_default(bem_solve_opts* opts);
  *   v_int, w_int [n_rhs * N_int]: phi_int = gamma_D^- p and psi_int = gamma_N^- p
  *                                 (negated for BEM_MTF_PRINTED).
  * Right-hand side r occupies [r*N, (r+1)*N).  rep may be NULL.
- * BEM_E_NOT_CONVERGED still writes the last iterate and the report.           */
+ * BEM_E_NOT_CONVERGED still writes the last iterate and the report.
+ *
+ * Single-trace formulations (paper Sec. 2.2, discretised as eq. pmchwt:discrete;
+ * r = rho_i/rho_e, A_g = [[-K_g, V_g], [D_g, T_g]] on grid g):
+ *   BEM_FORM_PMCHWT      (A_e + hat_e(A_i^r)) [v_e; w_e] = [-f; -g]
+ *   BEM_FORM_MULLER      (M_e + A_e - hat_e(A_i^r)) [v_e; w_e] = [-f; -g]
+ *   BEM_FORM_PMCHWT_INT  (A_i + hat_i(A_e^r)) [v_i; w_i] = [P_ie M_e^-1 f; r P_ie M_e^-1 g]
+ *   BEM_FORM_MULLER_INT  (M_i + hat_i(A_e^r) - A_i) [v_i; w_i] = (the same)
+ * with A_i^r = [[-K_i, r V_i], [D_i / r, T_i]], A_e^r = [[-K_e, V_e / r], [r D_e, T_e]],
+ * hat_e(X) = P_ei M_i^-1 X M_i^-1 P_ie and hat_i(X) = P_ie M_e^-1 X M_e^-1 P_ei (the
+ * Mueller identity is the mass matrix: the paper's exact projection of the identity),
+ * left-preconditioned by the mass inverse of the unknowns' grid.  The hatted operators
+ * are never formed: every product applies P, M^-1, the other grid's operators, M^-1
+ * and P in turn.  The other grid's potentials follow from the transmission conditions
+ * tested on it: v_i = -M_i^-1 P_ie v_e, w_i = -r M_i^-1 P_ie w_e (exterior variants),
+ * v_e = -M_e^-1 P_ei v_i, w_e = -(1/r) M_e^-1 P_ei w_i (interior variants), so the
+ * four outputs keep the meaning stated above.  mtf_variant is ignored.          */
 BEM_API bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const bem_grid* intr,
                                   bem_c128 k_int, bem_c128 k_ext, double rho_int_over_rho_ext,
                                   const bem_incident* inc, const bem_solve_opts* opts,

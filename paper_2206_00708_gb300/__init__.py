@@ -33,6 +33,7 @@ BEM_OP_V, BEM_OP_K, BEM_OP_T, BEM_OP_D = 0, 1, 2, 3
 BEM_PREC_FP64 = 0
 BEM_PREC_MIXED = 1
 BEM_MTF_DERIVED, BEM_MTF_PRINTED = 0, 1
+BEM_FORM_MTF, BEM_FORM_PMCHWT, BEM_FORM_MULLER, BEM_FORM_PMCHWT_INT, BEM_FORM_MULLER_INT = 0, 1, 2, 3, 4
 
 
 class BemError(RuntimeError):
@@ -60,6 +61,7 @@ class bem_solve_opts(C.Structure):
         ("ir_inner_tol", C.c_double),
         ("batch_columns", C.c_int32),
         ("tensor_cores", C.c_int32),
+        ("formulation", C.c_int32),
     ]
 
 

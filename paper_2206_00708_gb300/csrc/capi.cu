@@ -352,6 +352,7 @@ void bem_solve_opts_default(bem_solve_opts* o) {
     o->ir_inner_tol = 1e-8;
     o->batch_columns = 0;
     o->tensor_cores = 1;
+    o->formulation = BEM_FORM_MTF;
 }
 
 bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const bem_grid* intr, bem_c128 k_int,
@@ -375,6 +376,7 @@ bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const b
     BEM_REQUIRE(o.ir_inner_tol > 0.0 && o.ir_inner_tol < 1.0, "ir_inner_tol must be in (0, 1)");
     BEM_REQUIRE(o.batch_columns >= 0 && o.batch_columns <= 128, "batch_columns must be in [0, 128]");
     BEM_REQUIRE(o.tensor_cores == 0 || o.tensor_cores == 1, "tensor_cores must be 0 or 1");
+    BEM_REQUIRE(o.formulation >= BEM_FORM_MTF && o.formulation <= BEM_FORM_MULLER_INT, "unknown formulation");
     for (int r = 0; r < inc->n_rhs; ++r) {
         const double* d = inc->dirs + 3 * r;
         const double nd = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -408,6 +410,7 @@ bem_status bem_solve_many(bem_context* ctx, int32_t count, const bem_instance* i
         o.precision = BEM_PREC_MIXED;
     }
     BEM_REQUIRE(o.precision == BEM_PREC_MIXED, "bem_solve_many runs the mixed-precision mode");
+    BEM_REQUIRE(o.formulation == BEM_FORM_MTF, "bem_solve_many solves the multiple-traces system only");
     BEM_REQUIRE(o.gmres_tol >= 0.0 && o.gmres_maxiter >= 1, "bad GMRES options");
     BEM_REQUIRE(o.n_singular >= 1 && o.n_singular <= 16, "n_singular must be in [1, 16]");
     BEM_REQUIRE(o.mtf_variant == BEM_MTF_DERIVED || o.mtf_variant == BEM_MTF_PRINTED, "unknown MTF variant");

@@ -542,6 +542,33 @@ __global__ void k_transfer(TransferCsr T, const double2* __restrict__ xb, double
     z[g] = zz;
 }
 
+// One mortar matrix (CSR, `rows` rows, columns on a grid of `cols` vertices) applied to
+// both potentials of a column: z[b rows + i] = c_b (P x_b)_i for b = 0, 1, with x_b at
+// x + b cols (x of stride nx, z of stride nz, blockIdx.y = right-hand side); `add`
+// accumulates into z instead.  One thread per row of z, no atomics.
+__global__ void k_csr_pair(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ v, int64_t rows, int64_t cols, const double2* __restrict__ xb,
+                           int64_t nx, double2* __restrict__ zb, int64_t nz, double c0, double c1, int add) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= 2 * rows) return;
+    const int b = g >= rows ? 1 : 0;
+    const int64_t i = g - b * rows;
+    const double2* x = xb + blockIdx.y * nx + b * cols;
+    double sr = 0.0, si = 0.0;
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+        const double p = v[e];
+        const double2 xx = x[ci[e]];
+        sr = fma(p, xx.x, sr);
+        si = fma(p, xx.y, si);
+    }
+    const double c = b ? c1 : c0;
+    double2* zp = zb + blockIdx.y * nz + g;
+    double2 zz = add ? *zp : make_double2(0.0, 0.0);
+    zz.x = fma(c, sr, zz.x);
+    zz.y = fma(c, si, zz.y);
+    *zp = zz;
+}
+
 // ---------------------------------------------------------------- mass inverse
 // Mass matrices of the two grids in ELL form (column-major [W][N]: entry k of row i
 // at k * N + i; rows shorter than W padded with (i, 0)), so that all column indices
@@ -1110,6 +1137,31 @@ struct EventTimer {
     }
 };
 
+// Single-trace systems (Sec. 2.2): the Calderon operator of the unknowns' grid A,
+// [[-K_A, V_A], [D_A, T_A]] times sA, on (v_A, w_A) ("own"), and the density-scaled
+// Calderon operator of the other grid B, [[-K_B, cv V_B], [cd D_B, T_B]] times sB, on
+// the two vectors mapped to B ("hat"); the unused block rows 2, 3 are empty (no rows,
+// based at the end of the vector).  m1 = (K_e, D_e, K_i, D_i), m2 = (V_e, T_e, V_i, T_i);
+// oA, oB = 0 for the exterior grid's operators, 2 for the interior grid's.
+template <class BT, class MT>
+void fill_blocks_single(BT& Bo, BT& Bh, MT* const m1[4], MT* const m2[4], int oA, int oB, int64_t NA, int64_t NB,
+                        double sA, double sB, double cv, double cd) {
+    for (int b = 0; b < 4; ++b) {
+        const int u = b < 2 ? b : 1;
+        Bo.A1[b] = m1[oA + u]; Bo.A2[b] = m2[oA + u];
+        Bo.c1[b] = u == 0 ? -sA : sA; Bo.c2[b] = sA;
+        Bo.rows[b] = b < 2 ? NA : 0;
+        Bo.base[b] = b < 2 ? b * NA : 2 * NA;
+        Bo.x1[b] = 0; Bo.x2[b] = b < 2 ? NA : 0;
+        Bh.A1[b] = m1[oB + u]; Bh.A2[b] = m2[oB + u];
+        Bh.c1[b] = u == 0 ? -sB : cd * sB;
+        Bh.c2[b] = u == 0 ? cv * sB : sB;
+        Bh.rows[b] = b < 2 ? NB : 0;
+        Bh.base[b] = b < 2 ? b * NB : 2 * NB;
+        Bh.x1[b] = 0; Bh.x2[b] = b < 2 ? NB : 0;
+    }
+}
+
 template <class BT, class MT>
 void fill_blocks(BT& B, MT* const m1[4], MT* const m2[4], int64_t Ne, int64_t Ni) {
     const double c1[4] = {-1.0, 1.0, -1.0, 1.0};
@@ -1211,7 +1263,18 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                                    const bem_solve_opts* o, bem_c128* v_ext, bem_c128* w_ext, bem_c128* v_int,
                                    bem_c128* w_int, int on_device, bem_solve_report* rep) {
     cudaStream_t s = ctx->stream;
-    const int64_t Ne = ge->nv, Ni = gi->nv, n = 2 * Ne + 2 * Ni;
+    // unknowns per right-hand side: (v_e, w_e, v_i, w_i) for the multiple-traces system;
+    // for a single-trace system the two potentials of one grid A (the exterior grid for
+    // the exterior variants, the interior grid for the interior ones), whose products
+    // also apply the other grid B's operators to vectors of nB = 2 N_B entries (the two
+    // potentials mapped by M_B^-1 P_BA)
+    const int form = o->formulation;
+    const bool st = form != BEM_FORM_MTF;
+    const bool st_int = form == BEM_FORM_PMCHWT_INT || form == BEM_FORM_MULLER_INT;
+    const bool muller = form == BEM_FORM_MULLER || form == BEM_FORM_MULLER_INT;
+    const int64_t Ne = ge->nv, Ni = gi->nv;
+    const int64_t NA = st_int ? Ni : Ne, NB = st_int ? Ne : Ni, nB = 2 * NB;
+    const int64_t n = st ? 2 * NA : 2 * Ne + 2 * Ni;
     const bool mixed = o->precision == BEM_PREC_MIXED;
     const StopCheck stop = [ctx]() -> bem_status {
         if (ctx->cancel && ctx->cancel->load(std::memory_order_relaxed)) {
@@ -1286,7 +1349,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     auto dd_now = [&]() { return dd_single && inner_progress > DD_SWITCH; };
     const size_t colb = (size_t)n * 16;
     DevBuf wz, wr, wa, wb, x32, tcw, tcerr, xsplit;
-    if (dd_single) BEM_TRY(xsplit.alloc((size_t)n * 16, s));
+    if (dd_single) BEM_TRY(xsplit.alloc((size_t)(st ? std::max(n, nB) : n) * 16, s));
     BEM_TRY(wz.alloc(RW * colb, s));
     BEM_TRY(wr.alloc(RB * colb, s));
     BEM_TRY(wa.alloc(RB * colb, s));
@@ -1299,8 +1362,37 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     mop.M.dinv[0] = dve.as<double>();
     mop.M.ci[1] = ell_i.ci.as<int32_t>(); mop.M.v[1] = ell_i.v.as<double>(); mop.M.W[1] = ell_i.W;
     mop.M.dinv[1] = dvi.as<double>();
-    mop.M.Ne = Ne; mop.M.Ni = Ni; mop.M.n = n;
+    // a MassPair with no rows on one grid is the mass inverse of the other grid alone
+    // (vectors of its two potentials): single-trace systems use M_A^-1 (mop) and M_B^-1 (mopB)
+    mop.M.Ne = st_int ? 0 : Ne; mop.M.Ni = st && !st_int ? 0 : Ni; mop.M.n = n;
     mop.r = wr.as<double2>(); mop.dA = wa.as<double2>(); mop.dB = wb.as<double2>();
+    // single-trace: the grid-B vectors of a product (tb1: M_B^-1 P_BA x, then M_B^-1 of the
+    // grid-B product; tb2, tb3: input and output of the grid-B product, which reads and
+    // writes up to 7 spare columns)
+    MassOp mopB;
+    DevBuf wrb, wab, wbb, tb1, tb2, tb3, x32b;
+    if (st) {
+        const size_t colB = (size_t)nB * 16;
+        BEM_TRY(wrb.alloc(RB * colB, s));
+        BEM_TRY(wab.alloc(RB * colB, s));
+        BEM_TRY(wbb.alloc(RB * colB, s));
+        BEM_TRY(tb1.alloc(RB * colB, s));
+        BEM_TRY(tb2.alloc(RW * colB, s));
+        BEM_TRY(tb3.alloc(RW * colB, s));
+        BEM_CUDA_TRY(cudaMemsetAsync(tb2.p, 0, tb2.bytes, s));
+        mopB.M = mop.M;
+        mopB.M.Ne = st_int ? Ne : 0; mopB.M.Ni = st_int ? 0 : Ni; mopB.M.n = nB;
+        mopB.r = wrb.as<double2>(); mopB.dA = wab.as<double2>(); mopB.dB = wbb.as<double2>();
+    }
+    // P_BA (rows on grid B) and P_AB = P_BA^T: P_ie and P_ei for the exterior variants
+    const CsrBuf& csr_ba = st_int ? csr_t : csr_p;
+    const CsrBuf& csr_ab = st_int ? csr_p : csr_t;
+    // density scaling of grid B's Calderon operator, r = rho_i / rho_e: (cv V, cd D) =
+    // (r V_i, D_i / r) mapped to the exterior grid, (V_e / r, r D_e) to the interior grid;
+    // Mueller: exterior A_e - hat, interior hat - A_i (identity added after M_A^-1)
+    const double cv = st_int ? 1.0 / rho_ratio : rho_ratio, cd = st_int ? rho_ratio : 1.0 / rho_ratio;
+    const double sA = form == BEM_FORM_MULLER_INT ? -1.0 : 1.0, sB = form == BEM_FORM_MULLER ? -1.0 : 1.0;
+    const int oA = st_int ? 2 : 0, oB = st_int ? 0 : 2;
     TransferCsr top;
     const double sgn = o->mtf_variant == BEM_MTF_PRINTED ? -1.0 : 1.0;
     top.prp = csr_p.rp.as<int32_t>(); top.pci = csr_p.ci.as<int32_t>(); top.pv = csr_p.v.as<double>();
@@ -1311,78 +1403,116 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     top.cc = 0.5 * sgn;
     top.cd = 0.5 * sgn * rho_ratio;
     double2* z = wz.as<double2>();
-    Blocks<double2> B64{};
-    Blocks<float2> B32{};
+    // dense blocks: the four block rows of the multiple-traces system, or for the PMCHWT
+    // the two exterior block rows (B*) and the two scaled interior ones (Bi*)
+    Blocks<double2> B64{}, Bh64{};
+    Blocks<float2> B32{}, Bh32{};
     if (mixed) {
         BEM_TRY(x32.alloc((size_t)RW * n * 8, s));
         BEM_CUDA_TRY(cudaMemsetAsync(x32.p, 0, x32.bytes, s));
         const float2* m1[4] = {M[1].as<float2>(), M[3].as<float2>(), M[5].as<float2>(), M[7].as<float2>()};
         const float2* m2[4] = {M[0].as<float2>(), M[2].as<float2>(), M[4].as<float2>(), M[6].as<float2>()};
-        fill_blocks(B32, m1, m2, Ne, Ni);
+        if (st) {
+            fill_blocks_single(B32, Bh32, m1, m2, oA, oB, NA, NB, sA, sB, cv, cd);
+            BEM_TRY(x32b.alloc((size_t)RW * nB * 8, s));
+            BEM_CUDA_TRY(cudaMemsetAsync(x32b.p, 0, x32b.bytes, s));
+        } else {
+            fill_blocks(B32, m1, m2, Ne, Ni);
+        }
         if (tc_batches) {
-            BEM_TRY(tcw.alloc(tc_workspace_bytes(B32.rows, tc_padded_columns(RB)), s));
+            const int RP = tc_padded_columns(RB);
+            BEM_TRY(tcw.alloc(std::max(tc_workspace_bytes(B32.rows, RP), st ? tc_workspace_bytes(Bh32.rows, RP) : 0),
+                              s));
             BEM_TRY(tcerr.alloc(sizeof(int), s));
             BEM_CUDA_TRY(cudaMemsetAsync(tcerr.p, 0, sizeof(int), s));
         }
     } else {
         const double2* m1[4] = {M[1].as<double2>(), M[3].as<double2>(), M[5].as<double2>(), M[7].as<double2>()};
         const double2* m2[4] = {M[0].as<double2>(), M[2].as<double2>(), M[4].as<double2>(), M[6].as<double2>()};
-        fill_blocks(B64, m1, m2, Ne, Ni);
+        if (st) fill_blocks_single(B64, Bh64, m1, m2, oA, oB, NA, NB, sA, sB, cv, cd);
+        else fill_blocks(B64, m1, m2, Ne, Ni);
     }
-    const unsigned rows_blocks = blocks_for(n * 32, 256);
-    // dense blocks for R columns in the working arithmetic (x must hold R + 7 columns)
-    auto gemm_work = [&](const double2* xin, int R) -> bem_status {
+    // zo = dense blocks (b32 or b64) of nn rows applied to R columns xin, in the working
+    // arithmetic (xin and zo must hold R + 7 columns of nn; xw is the complex64 copy of xin)
+    auto gemm_work_on = [&](const Blocks<float2>& b32, const Blocks<double2>& b64, int64_t nn, float2* xw,
+                            const double2* xin, double2* zo, int R) -> bem_status {
+        const unsigned rows_blocks = blocks_for(nn * 32, 256);
         if (mixed && tc_batches && R > 8)
-            return mtf_product_tc(B32.A1, B32.A2, B32.c1, B32.c2, B32.rows, B32.base, B32.x1, B32.x2, n, R, xin, z,
+            return mtf_product_tc(b32.A1, b32.A2, b32.c1, b32.c2, b32.rows, b32.base, b32.x1, b32.x2, nn, R, xin, zo,
                                   tcw.p, tcw.bytes, tcerr.as<int>(), s);
         if (mixed && R == 1 && dd_now()) {
-            BEM_LAUNCH(k_split_x, blocks_for(n, 256), 256, 0, s, xin, n, xsplit.as<float4>());
-            BEM_LAUNCH(k_gemv_dd, rows_blocks, 256, 0, s, B32, n, xsplit.as<float4>(), z);
+            BEM_LAUNCH(k_split_x, blocks_for(nn, 256), 256, 0, s, xin, nn, xsplit.as<float4>());
+            BEM_LAUNCH(k_gemv_dd, rows_blocks, 256, 0, s, b32, nn, xsplit.as<float4>(), zo);
             return BEM_OK;
         }
         if (mixed)
-            BEM_LAUNCH(k_to_c64, blocks_for((int64_t)R * n, 256), 256, 0, s, xin, (int64_t)R * n, x32.as<float2>());
+            BEM_LAUNCH(k_to_c64, blocks_for((int64_t)R * nn, 256), 256, 0, s, xin, (int64_t)R * nn, xw);
         for (int c0 = 0; c0 < R; c0 += 8) {
             const int Wd = gemm_width(std::min(8, R - c0));
-            double2* zc = z + (int64_t)c0 * n;
+            double2* zc = zo + (int64_t)c0 * nn;
             if (mixed) {
-                const float2* xc = x32.as<float2>() + (int64_t)c0 * n;
-                if (Wd == 1) BEM_LAUNCH(k_gemm32<1>, rows_blocks, 256, 0, s, B32, n, xc, zc);
-                else if (Wd == 2) BEM_LAUNCH(k_gemm32<2>, rows_blocks, 256, 0, s, B32, n, xc, zc);
-                else if (Wd == 4) BEM_LAUNCH(k_gemm32<4>, rows_blocks, 256, 0, s, B32, n, xc, zc);
-                else BEM_LAUNCH(k_gemm32<8>, rows_blocks, 256, 0, s, B32, n, xc, zc);
+                const float2* xc = xw + (int64_t)c0 * nn;
+                if (Wd == 1) BEM_LAUNCH(k_gemm32<1>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
+                else if (Wd == 2) BEM_LAUNCH(k_gemm32<2>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
+                else if (Wd == 4) BEM_LAUNCH(k_gemm32<4>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
+                else BEM_LAUNCH(k_gemm32<8>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
             } else {
-                const double2* xc = xin + (int64_t)c0 * n;
-                if (Wd == 1) BEM_LAUNCH(k_gemm64<1>, rows_blocks, 256, 0, s, B64, n, xc, zc);
-                else if (Wd == 2) BEM_LAUNCH(k_gemm64<2>, rows_blocks, 256, 0, s, B64, n, xc, zc);
-                else if (Wd == 4) BEM_LAUNCH(k_gemm64<4>, rows_blocks, 256, 0, s, B64, n, xc, zc);
-                else BEM_LAUNCH(k_gemm64<8>, rows_blocks, 256, 0, s, B64, n, xc, zc);
+                const double2* xc = xin + (int64_t)c0 * nn;
+                if (Wd == 1) BEM_LAUNCH(k_gemm64<1>, rows_blocks, 256, 0, s, b64, nn, xc, zc);
+                else if (Wd == 2) BEM_LAUNCH(k_gemm64<2>, rows_blocks, 256, 0, s, b64, nn, xc, zc);
+                else if (Wd == 4) BEM_LAUNCH(k_gemm64<4>, rows_blocks, 256, 0, s, b64, nn, xc, zc);
+                else BEM_LAUNCH(k_gemm64<8>, rows_blocks, 256, 0, s, b64, nn, xc, zc);
             }
         }
         return BEM_OK;
     };
-    auto gemm_fp64 = [&](const double2* xin, int R) -> bem_status {
-        if (!mixed) return gemm_work(xin, R);
+    // the same with FP64 arithmetic on the stored matrices
+    auto gemm_fp64_on = [&](const Blocks<float2>& b32, const Blocks<double2>& b64, int64_t nn, float2* xw,
+                            const double2* xin, double2* zo, int R) -> bem_status {
+        if (!mixed) return gemm_work_on(b32, b64, nn, xw, xin, zo, R);
+        const unsigned rows_blocks = blocks_for(nn * 32, 256);
         for (int c0 = 0; c0 < R; c0 += 8) {
             const int Wd = gemm_width(std::min(8, R - c0));
-            const double2* xc = xin + (int64_t)c0 * n;
-            double2* zc = z + (int64_t)c0 * n;
-            if (Wd == 1) BEM_LAUNCH(k_gemm_c64_f64<1>, rows_blocks, 256, 0, s, B32, n, xc, zc);
-            else if (Wd == 2) BEM_LAUNCH(k_gemm_c64_f64<2>, rows_blocks, 256, 0, s, B32, n, xc, zc);
-            else if (Wd == 4) BEM_LAUNCH(k_gemm_c64_f64<4>, rows_blocks, 256, 0, s, B32, n, xc, zc);
-            else BEM_LAUNCH(k_gemm_c64_f64<8>, rows_blocks, 256, 0, s, B32, n, xc, zc);
+            const double2* xc = xin + (int64_t)c0 * nn;
+            double2* zc = zo + (int64_t)c0 * nn;
+            if (Wd == 1) BEM_LAUNCH(k_gemm_c64_f64<1>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
+            else if (Wd == 2) BEM_LAUNCH(k_gemm_c64_f64<2>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
+            else if (Wd == 4) BEM_LAUNCH(k_gemm_c64_f64<4>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
+            else BEM_LAUNCH(k_gemm_c64_f64<8>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
         }
+        return BEM_OK;
+    };
+    // single-trace product z = sA A_A x + sB P_AB M_B^-1 A_B^rho M_B^-1 P_BA x (the hat
+    // transformation applied factor by factor), then y = M_A^-1 z, plus x for Mueller
+    auto apply_single = [&](bool fp64, const double2* xin, double2* yout, int R, int steps) -> bem_status {
+        auto prod = [&](const Blocks<float2>& b32, const Blocks<double2>& b64, int64_t nn, float2* xw,
+                        const double2* xi, double2* zo) -> bem_status {
+            return fp64 ? gemm_fp64_on(b32, b64, nn, xw, xi, zo, R) : gemm_work_on(b32, b64, nn, xw, xi, zo, R);
+        };
+        BEM_TRY(prod(B32, B64, n, x32.as<float2>(), xin, z));
+        BEM_LAUNCH(k_csr_pair, dim3(blocks_for(nB, 64), R), 64, 0, s, csr_ba.rp.as<int32_t>(),
+                   csr_ba.ci.as<int32_t>(), csr_ba.v.as<double>(), NB, NA, xin, n, tb1.as<double2>(), nB, 1.0, 1.0, 0);
+        BEM_TRY(mass_solve(mopB, tb1.as<double2>(), tb2.as<double2>(), R, s, steps));
+        BEM_TRY(prod(Bh32, Bh64, nB, x32b.as<float2>(), tb2.as<double2>(), tb3.as<double2>()));
+        BEM_TRY(mass_solve(mopB, tb3.as<double2>(), tb1.as<double2>(), R, s, steps));
+        BEM_LAUNCH(k_csr_pair, dim3(blocks_for(n, 64), R), 64, 0, s, csr_ab.rp.as<int32_t>(), csr_ab.ci.as<int32_t>(),
+                   csr_ab.v.as<double>(), NA, NB, tb1.as<double2>(), nB, z, n, 1.0, 1.0, 1);
+        BEM_TRY(mass_solve(mop, z, yout, R, s, steps));
+        if (muller)
+            BEM_LAUNCH(k_acc, blocks_for((int64_t)R * n, 256), 256, 0, s, yout, xin, (int64_t)R * n);
         return BEM_OK;
     };
     // S A x in the working precision, and with FP64 arithmetic on the stored matrices
     Apply apply_work = [&](const double2* xin, double2* yout, int R) -> bem_status {
-        BEM_TRY(gemm_work(xin, R));
+        const int steps = !mixed ? CHEB_STEPS : (R == 1 && dd_now()) ? CHEB_STEPS_DD : CHEB_STEPS_INNER;
+        if (st) return apply_single(false, xin, yout, R, steps);
+        BEM_TRY(gemm_work_on(B32, B64, n, x32.as<float2>(), xin, z, R));
         BEM_TRY(transfer_add(top, R, xin, z, s));
-        return mass_solve(mop, z, yout, R, s,
-                          !mixed ? CHEB_STEPS : (R == 1 && dd_now()) ? CHEB_STEPS_DD : CHEB_STEPS_INNER);
+        return mass_solve(mop, z, yout, R, s, steps);
     };
     Apply apply_fp64 = [&](const double2* xin, double2* yout, int R) -> bem_status {
-        BEM_TRY(gemm_fp64(xin, R));
+        if (st) return apply_single(true, xin, yout, R, CHEB_STEPS);
+        BEM_TRY(gemm_fp64_on(B32, B64, n, x32.as<float2>(), xin, z, R));
         BEM_TRY(transfer_add(top, R, xin, z, s));
         return mass_solve(mop, z, yout, R, s, CHEB_STEPS);
     };
@@ -1420,8 +1550,18 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
         BEM_LAUNCH(k_plane_wave, dim3(blocks_for(ge->nt, 128), R), 128, 0, s, ge->rec.as<TriRec>(),
                    ge->tri.as<int32_t>(), ge->nt, k_ext.re, k_ext.im, wave.as<double>() + 2 * RB,
                    wave.as<double2>(), Ne, fvec.as<double2>(), gvec.as<double2>());
-        BEM_LAUNCH(k_rhs_pack, dim3(blocks_for(n, 256), R), 256, 0, s, fvec.as<double2>(), gvec.as<double2>(), Ne, n,
-                   bvec.as<double2>());
+        if (st_int) {
+            // interior variants: [P_ie M_e^-1 f; (rho_i / rho_e) P_ie M_e^-1 g]
+            BEM_LAUNCH(k_rhs_pack, dim3(blocks_for(nB, 256), R), 256, 0, s, fvec.as<double2>(), gvec.as<double2>(),
+                       Ne, nB, tb1.as<double2>());
+            BEM_TRY(mass_solve(mopB, tb1.as<double2>(), tb2.as<double2>(), R, s, CHEB_STEPS));
+            BEM_LAUNCH(k_csr_pair, dim3(blocks_for(n, 64), R), 64, 0, s, csr_ab.rp.as<int32_t>(),
+                       csr_ab.ci.as<int32_t>(), csr_ab.v.as<double>(), NA, NB, tb2.as<double2>(), nB,
+                       bvec.as<double2>(), n, -1.0, -rho_ratio, 0);
+        } else {
+            BEM_LAUNCH(k_rhs_pack, dim3(blocks_for(n, 256), R), 256, 0, s, fvec.as<double2>(), gvec.as<double2>(),
+                       Ne, n, bvec.as<double2>());
+        }
         BEM_TRY(mass_solve(mop, bvec.as<double2>(), sb.as<double2>(), R, s, CHEB_STEPS));
         std::vector<double> beta(R), tol_abs(R), rn(R), est(R), inner_tol(R);
         std::vector<int> its(R), total(R, 0);
@@ -1482,13 +1622,25 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
             if (!conv) result = BEM_E_NOT_CONVERGED;
         }
         const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (st) {
+            // the other grid's potentials from the transmission conditions tested on it:
+            // v_i = -M_i^-1 P_ie v_e, w_i = -(rho_i / rho_e) M_i^-1 P_ie w_e (exterior
+            // variants); v_e = -M_e^-1 P_ei v_i, w_e = -(rho_e / rho_i) M_e^-1 P_ei w_i
+            BEM_LAUNCH(k_csr_pair, dim3(blocks_for(nB, 64), R), 64, 0, s, csr_ba.rp.as<int32_t>(),
+                       csr_ba.ci.as<int32_t>(), csr_ba.v.as<double>(), NB, NA, xsol.as<double2>(), n,
+                       tb1.as<double2>(), nB, -1.0, st_int ? -1.0 / rho_ratio : -rho_ratio, 0);
+            BEM_TRY(mass_solve(mopB, tb1.as<double2>(), tb2.as<double2>(), R, s, CHEB_STEPS));
+        }
         for (int r = 0; r < R; ++r) {
             const double2* X = xsol.as<double2>() + (int64_t)r * n;
+            const double2* XB = st ? tb2.as<double2>() + (int64_t)r * nB : nullptr;
+            const double2* XE = !st ? X : st_int ? XB : X;
+            const double2* XI = !st ? X + 2 * Ne : st_int ? X : XB;
             const int64_t rr = r0 + r;
-            BEM_CUDA_TRY(cudaMemcpyAsync(v_ext + rr * Ne, X, Ne * 16, kind, s));
-            BEM_CUDA_TRY(cudaMemcpyAsync(w_ext + rr * Ne, X + Ne, Ne * 16, kind, s));
-            BEM_CUDA_TRY(cudaMemcpyAsync(v_int + rr * Ni, X + 2 * Ne, Ni * 16, kind, s));
-            BEM_CUDA_TRY(cudaMemcpyAsync(w_int + rr * Ni, X + 2 * Ne + Ni, Ni * 16, kind, s));
+            BEM_CUDA_TRY(cudaMemcpyAsync(v_ext + rr * Ne, XE, Ne * 16, kind, s));
+            BEM_CUDA_TRY(cudaMemcpyAsync(w_ext + rr * Ne, XE + Ne, Ne * 16, kind, s));
+            BEM_CUDA_TRY(cudaMemcpyAsync(v_int + rr * Ni, XI, Ni * 16, kind, s));
+            BEM_CUDA_TRY(cudaMemcpyAsync(w_int + rr * Ni, XI + Ni, Ni * 16, kind, s));
         }
         BEM_CUDA_TRY(cudaStreamSynchronize(s));
     }
