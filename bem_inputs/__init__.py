@@ -26,6 +26,7 @@ __all__ = [
     "plane_wave_directions",
     "unit_square_grid",
     "perturb_square_grid",
+    "cube_grid",
     "serving_requests",
 ]
 
@@ -180,6 +181,60 @@ def unit_square_grid(n: int):
             else:
                 tri += [[a, b, d], [b, c, d]]
     return v, np.array(tri, dtype=np.int32)
+
+
+def cube_grid(n: int, jitter: float = 0.0, seed: int = 0):
+    """Surface of the unit cube [0,1]^3 (the geometry of the accuracy and efficiency
+    benchmarks of Sec. 5.3-5.5) with each face a structured n x n grid of squares cut
+    into two triangles (diagonals alternating), faces sharing their edge nodes, so the
+    surface grid is conforming with 6 n^2 + 2 nodes.  jitter > 0 moves the nodes
+    inside each face (not those on cube edges) by a seeded uniform offset of at most
+    jitter * (1/n) along each in-face axis, so two grids of one size still differ.
+    Triangles are counter-clockwise seen from outside."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h = 1.0 / n
+    index = {}
+    verts = []
+
+    def node(p):
+        key = tuple(int(c) for c in p)
+        if key not in index:
+            index[key] = len(verts)
+            verts.append(key)
+        return index[key]
+
+    tris = []
+    for axis in range(3):
+        u, w = [a for a in range(3) if a != axis]
+        for side in (0, n):
+            ids = np.empty((n + 1, n + 1), dtype=np.int64)
+            for i in range(n + 1):
+                for j in range(n + 1):
+                    p = [0, 0, 0]
+                    p[axis], p[u], p[w] = side, i, j
+                    ids[i, j] = node(p)
+            for i in range(n):
+                for j in range(n):
+                    a, b, c, d = ids[i, j], ids[i + 1, j], ids[i + 1, j + 1], ids[i, j + 1]
+                    if (i + j) % 2 == 0:
+                        tris += [[a, b, c], [a, c, d]]
+                    else:
+                        tris += [[a, b, d], [b, c, d]]
+    lat = np.array(verts, dtype=np.float64)
+    v = lat * h
+    if jitter > 0.0:
+        on_edge = ((lat == 0) | (lat == n)).sum(axis=1) >= 2
+        off = rng.uniform(-jitter * h, jitter * h, size=v.shape)
+        face_axis = np.argmax((lat == 0) | (lat == n), axis=1)
+        off[np.arange(len(v)), face_axis] = 0.0
+        off[on_edge] = 0.0
+        v = v + off
+    f = np.array(tris, dtype=np.int64)
+    a, b, c = v[f[:, 0]], v[f[:, 1]], v[f[:, 2]]
+    nrm = np.cross(b - a, c - a)
+    flip = np.einsum("ij,ij->i", nrm, (a + b + c) / 3.0 - 0.5) < 0
+    f[flip, 1], f[flip, 2] = f[flip, 2].copy(), f[flip, 1].copy()
+    return v, f.astype(np.int32)
 
 
 def perturb_square_grid(v, sigma: float, seed: int):
