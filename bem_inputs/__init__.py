@@ -27,6 +27,7 @@ __all__ = [
     "unit_square_grid",
     "perturb_square_grid",
     "cube_grid",
+    "screen_grid",
     "serving_requests",
 ]
 
@@ -235,6 +236,41 @@ def cube_grid(n: int, jitter: float = 0.0, seed: int = 0):
     flip = np.einsum("ij,ij->i", nrm, (a + b + c) / 3.0 - 0.5) < 0
     f[flip, 1], f[flip, 2] = f[flip, 2].copy(), f[flip, 1].copy()
     return v, f.astype(np.int32)
+
+
+# Corners of the rectangular screen of the operator-preconditioning benchmark (Sec. 5.7):
+# edge lengths about 2.06 (first direction) and 2.
+SCREEN_CORNERS = ((-0.25, -1.0, -1.0), (0.25, 1.0, -1.0), (0.25, 1.0, 1.0), (-0.25, -1.0, 1.0))
+
+
+def screen_grid(nu: int, nv: int, jitter: float = 0.0, seed: int = 0):
+    """Open rectangular screen with corners SCREEN_CORNERS (c0, c1, c2, c3), a structured
+    nu x nv grid of cells along c1 - c0 and c3 - c0 cut into two triangles each
+    (diagonals alternating), (nu + 1)(nv + 1) nodes.  jitter > 0 moves the nodes that are
+    not on the boundary by a seeded uniform in-plane offset of at most jitter cell widths
+    along each direction.  Every triangle is oriented like (c1 - c0) x (c3 - c0)."""
+    c0, c1, _, c3 = (np.asarray(c, dtype=np.float64) for c in SCREEN_CORNERS)
+    eu, ev = c1 - c0, c3 - c0
+    s = np.linspace(0.0, 1.0, nu + 1)
+    t = np.linspace(0.0, 1.0, nv + 1)
+    S, T = np.meshgrid(s, t, indexing="ij")
+    S, T = S.ravel().copy(), T.ravel().copy()
+    if jitter > 0.0:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        inner = (S > 0) & (S < 1) & (T > 0) & (T < 1)
+        S[inner] += rng.uniform(-jitter / nu, jitter / nu, inner.sum())
+        T[inner] += rng.uniform(-jitter / nv, jitter / nv, inner.sum())
+    v = c0[None, :] + S[:, None] * eu[None, :] + T[:, None] * ev[None, :]
+    idx = lambda i, j: i * (nv + 1) + j
+    tri = []
+    for i in range(nu):
+        for j in range(nv):
+            a, b, c, d = idx(i, j), idx(i + 1, j), idx(i + 1, j + 1), idx(i, j + 1)
+            if (i + j) % 2 == 0:
+                tri += [[a, b, c], [a, c, d]]
+            else:
+                tri += [[a, b, d], [b, c, d]]
+    return v, np.array(tri, dtype=np.int32)
 
 
 def perturb_square_grid(v, sigma: float, seed: int):
