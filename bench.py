@@ -47,9 +47,40 @@ WORKLOAD_NAME = ("at-scale sphere: icosphere L5 exterior (10242 vertices) + L5 i
                  "40968 unknowns")
 L2_FLUSH_BYTES = 256 << 20
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x 2 flops x max SM clock
-# algorithmic flops per point pair of the regular-pair assembly kernels
+# algorithmic flops per point pair of the regular-pair assembly kernels, counted from their source
+# (FMA = 2, sin/cos = 2, rsqrt = 1 each)
 FLOP_PER_POINT_PAIR = 93
 FLOP_PER_POINT_PAIR_FP32 = 105
+
+
+# Unit-cube efficiency benchmarks (Sec. 5.5): the physics of the paper's table of physical
+# parameters (wavenumber 2 pi f / c of each medium; density ratio rho_int / rho_ext) and
+# nonconforming grids with the node counts of its mesh table (N_ext, N_int), here structured
+# cube grids with n nodes per cube edge, n chosen so that 6 n^2 + 2 is nearest to N; GMRES
+# tolerance 1e-5 as in Sec. 5.1; plane wave along +x (eq. planewave).
+CUBE_BENCHMARKS = (
+    dict(name="standard", f=1.0, c_ext=0.3, c_int=1.1, rho_ext=1.0, rho_int=2.0, N_ext=2836, N_int=272),
+    dict(name="high frequency", f=3.0, c_ext=0.3, c_int=1.1, rho_ext=1.0, rho_int=2.0, N_ext=25302, N_int=2072),
+    dict(name="high contrast", f=1.0, c_ext=0.1, c_int=1.1, rho_ext=0.11, rho_int=2.0, N_ext=25302, N_int=272),
+)
+CUBE_TOL = 1e-5
+CUBE_CENTER = (0.5, 0.5, 0.5)
+
+
+def cube_edge_nodes(N):
+    """n with 6 n^2 + 2 nearest to N (nodes of a structured cube grid)."""
+    n = max(1, int(round(((N - 2) / 6.0) ** 0.5)))
+    return min((m for m in (n - 1, n, n + 1) if m >= 1), key=lambda m: abs(6 * m * m + 2 - N))
+
+
+def cube_case(b):
+    """(grids, k_ext, k_int, rho) of one cube benchmark."""
+    import bem_inputs as bi
+    ve, te = bi.cube_grid(cube_edge_nodes(b["N_ext"]), jitter=0.3, seed=61)
+    vi, ti = bi.cube_grid(cube_edge_nodes(b["N_int"]), jitter=0.3, seed=62)
+    k_ext = 2.0 * np.pi * b["f"] / b["c_ext"]
+    k_int = 2.0 * np.pi * b["f"] / b["c_int"]
+    return (ve, te, vi, ti), k_ext, k_int, b["rho_int"] / b["rho_ext"]
 
 
 def workload_inputs(w=WORKLOAD):
@@ -356,6 +387,127 @@ def run_field(bem, ctx, w, ve, te, vi, ti, out):
 UNEVEN_WORKLOAD = dict(count=32, seed=42)
 
 
+def run_cube(bem, ctx, formulations=("mtf", "pmchwt_ext", "hc_ext_neu")):
+    """The unit-cube efficiency benchmarks (CUBE_BENCHMARKS) with nonconforming grids, and the
+    standard one also with conforming grids (the interior grid as fine as the exterior one):
+    one mixed-precision solve per formulation, host buffers, times from the solve report
+    (device events) and the wall clock."""
+    import torch
+    forms = {"mtf": bem.BEM_FORM_MTF, "pmchwt_ext": bem.BEM_FORM_PMCHWT, "muller_ext": bem.BEM_FORM_MULLER,
+             "pmchwt_int": bem.BEM_FORM_PMCHWT_INT, "muller_int": bem.BEM_FORM_MULLER_INT,
+             "hc_ext_neu": bem.BEM_FORM_HC_EXT_NEU, "hc_ext_dir": bem.BEM_FORM_HC_EXT_DIR,
+             "hc_int_neu": bem.BEM_FORM_HC_INT_NEU, "hc_int_dir": bem.BEM_FORM_HC_INT_DIR}
+    cases = [(b["name"], b) for b in CUBE_BENCHMARKS]
+    cases.insert(1, ("standard (conforming)", dict(CUBE_BENCHMARKS[0], N_int=CUBE_BENCHMARKS[0]["N_ext"])))
+    out = {"workload": "unit cube [0,1]^3, structured face grids with in-face jitter 0.3 (seeds 61/62), "
+                       "plane wave +x, GMRES tol 1e-5, mixed precision, one solve each",
+           "cases": []}
+    for name, b in cases:
+        (ve, te, vi, ti), k_ext, k_int, rho = cube_case(b)
+        entry = {"benchmark": name, "k_ext": k_ext, "k_int": k_int, "rho_int_over_rho_ext": rho,
+                 "N_ext": len(ve), "N_int": len(vi), "paper_N": [b["N_ext"], b["N_int"]]}
+        for fname in formulations:
+            opts = {"precision": bem.BEM_PREC_MIXED, "gmres_tol": CUBE_TOL, "gmres_maxiter": 6000,
+                    "formulation": forms[fname], "center": CUBE_CENTER}
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ge, gi = bem.bem_grid_create(ctx, ve, te), bem.bem_grid_create(ctx, vi, ti)
+            try:
+                _, rep = bem.bem_solve_transmission(ctx, ge, gi, k_int, k_ext, rho, np.array([[1.0, 0.0, 0.0]]),
+                                                    opts=opts)
+            except bem.BemError as e:
+                rep = e.report
+            finally:
+                bem.bem_grid_destroy(ge)
+                bem.bem_grid_destroy(gi)
+            wall = time.perf_counter() - t0
+            entry[fname] = {"seconds": wall, "iterations": rep["iterations"], "converged": bool(rep["converged"]),
+                            "residual": rep["residual"], "t_assembly_ms": rep["t_assembly_ms"],
+                            "t_mortar_ms": rep["t_mortar_ms"], "t_solve_ms": rep["t_solve_ms"],
+                            "ms_per_iteration": rep["t_solve_ms"] / max(1, rep["iterations"]),
+                            "mortar_share_of_assembly": rep["t_mortar_ms"] / max(1e-9, rep["t_assembly_ms"])}
+        out["cases"].append(entry)
+    return out
+
+
+# The screen benchmark of Sec. 5.7: the rectangle of bem_inputs.SCREEN_CORNERS, f = 15, c = 1
+# (k = 94.2), plane wave along +x; a fine grid with the paper's 87,712 nodes (here a
+# structured 300 x 291 grid, 87,892 nodes) and a coarse one with its 9934 (100 x 97, 9898).
+SCREEN_WORKLOAD = dict(fine=(300, 291), coarse=(100, 97), f=15.0, c=1.0, tol=1e-5)
+
+
+def run_screen(bem, ctx):
+    """Mass-matrix, conforming and nonconforming opposite-order preconditioning of the
+    Neumann screen at the paper's size, mixed precision, one solve each (host buffers):
+    iterations and times from the report, and each opposite-order solution's distance
+    from the mass-preconditioned one."""
+    import torch
+    import bem_inputs as bi
+    w = SCREEN_WORKLOAD
+    v, t = bi.screen_grid(*w["fine"], jitter=0.2, seed=71)
+    vc, tc = bi.screen_grid(*w["coarse"], jitter=0.2, seed=72)
+    k = 2.0 * np.pi * w["f"] / w["c"]
+    gf, gc = bem.bem_grid_create(ctx, v, t), bem.bem_grid_create(ctx, vc, tc)
+    out = {"workload": f"rectangular screen (corners as in the paper), fine {len(v)} nodes, coarse {len(vc)} nodes, "
+                       f"k = {k:.1f}, plane wave +x, mixed precision, GMRES tol {w['tol']}", "runs": {}}
+    phis = {}
+    for name, coarse, pre in (("mass", None, bem.BEM_SCREEN_MASS), ("oo_conforming", gf, bem.BEM_SCREEN_OO),
+                              ("oo_nonconforming", gc, bem.BEM_SCREEN_OO)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            phi, rep = bem.bem_solve_screen(ctx, gf, k, np.array([[1.0, 0.0, 0.0]]), coarse=coarse, precond=pre,
+                                            opts={"precision": bem.BEM_PREC_MIXED, "gmres_tol": w["tol"]})
+        except bem.BemError as e:
+            phi, rep = e.outputs, e.report
+        wall = time.perf_counter() - t0
+        phis[name] = phi[0]
+        out["runs"][name] = {"seconds": wall, "iterations": rep["iterations"], "converged": bool(rep["converged"]),
+                             "t_assembly_ms": rep["t_assembly_ms"], "t_mortar_ms": rep["t_mortar_ms"],
+                             "t_solve_ms": rep["t_solve_ms"],
+                             "ms_per_iteration": rep["t_solve_ms"] / max(1, rep["iterations"])}
+    ref = phis["mass"]
+    for name in ("oo_conforming", "oo_nonconforming"):
+        out["runs"][name]["rel_l2_vs_mass_preconditioned"] = float(np.linalg.norm(phis[name] - ref) /
+                                                                   np.linalg.norm(ref))
+    bem.bem_grid_destroy(gf)
+    bem.bem_grid_destroy(gc)
+    return out
+
+
+def run_graphs(bem, ctx, reps=5):
+    """CUDA-graph replay of the iteration's fixed launch sequences on and off: one
+    mixed-precision solve (k_ext 10, k_int 15, rho 2, one wave) per grid level, wall
+    time per solve with host buffers (median of reps), and the library's launch count."""
+    import torch
+    import bem_inputs as bi
+    out = {"workload": "icosphere pair L/L (seed 2), k_ext=10, k_int=15, rho=2, one plane wave +z, mixed, "
+                       "tol 1e-8; median of %d solves per setting" % reps, "levels": []}
+    for L in (2, 3, 4):
+        ve, te, vi, ti = bi.transmission_pair(L, L, seed=2)
+        ge, gi = bem.bem_grid_create(ctx, ve, te), bem.bem_grid_create(ctx, vi, ti)
+        entry = {"level": L, "unknowns": 2 * (len(ve) + len(vi))}
+        for g in (0, 1):
+            opts = {"precision": bem.BEM_PREC_MIXED, "cuda_graphs": g}
+            bem.bem_solve_transmission(ctx, ge, gi, 15.0, 10.0, 2.0, np.array([[0.0, 0.0, 1.0]]), opts=opts)
+            ts, launches = [], 0
+            for _ in range(reps):
+                torch.cuda.synchronize()
+                l0 = bem.bem_launch_count()
+                t0 = time.perf_counter()
+                _, rep = bem.bem_solve_transmission(ctx, ge, gi, 15.0, 10.0, 2.0, np.array([[0.0, 0.0, 1.0]]),
+                                                    opts=opts)
+                ts.append(time.perf_counter() - t0)
+                launches = bem.bem_launch_count() - l0
+            entry["graphs" if g else "no_graphs"] = {"ms": 1e3 * statistics.median(ts), "iterations": rep["iterations"],
+                                                     "kernels": launches}
+        entry["speedup"] = entry["no_graphs"]["ms"] / entry["graphs"]["ms"]
+        bem.bem_grid_destroy(ge)
+        bem.bem_grid_destroy(gi)
+        out["levels"].append(entry)
+    return out
+
+
 def run_uneven(bem, ctx):
     """Uneven instances: ellipsoids with semi-axes U[0.5, 1.5], exterior and interior
     icosphere levels drawn from {2, 3, 4}, k_ext U[2, 8], k_int = 1.5 k_ext, density
@@ -441,8 +593,14 @@ def main():
     ap.add_argument("--no-accuracy", dest="accuracy", action="store_false",
                     help="skip the converged FP64 reference solve (profiling runs)")
     ap.add_argument("--no-field", dest="field", action="store_false", help="skip the field-evaluation section")
-    ap.add_argument("--no-single-trace", dest="single_trace", action="store_false",
-                    help="skip the single-trace formulations section")
+    ap.add_argument("--no-cube", dest="cube", action="store_false", help="skip the unit-cube benchmarks")
+    ap.add_argument("--no-screen", dest="screen", action="store_false", help="skip the screen benchmark")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the built-in launch shapes (no bem_autotune before the measured steps)")
+    ap.add_argument("--no-graphs", dest="graphs", action="store_false",
+                    help="skip the CUDA-graph on/off comparison")
+    ap.add_argument("--no-formulations", dest="single_trace", action="store_false",
+                    help="skip the section timing the other formulations (single-trace, high-contrast)")
     ap.add_argument("--no-batching", dest="batching", action="store_false",
                     help="skip the many-directions section")
     ap.add_argument("--serve-requests", type=int, default=24,
@@ -542,6 +700,49 @@ def main():
         return dict(out=out, times=times, reports=reports, launches=launches, clocks=clocks.summary(),
                     value=world * args.steps / (total / 1e3), prof=timed_prof, table=table)
 
+    # launch shapes for this workload's sizes, timed once before any measured step
+    tuning = None
+    if args.autotune:
+        ge, gi = bem.bem_grid_create(ctx, xe, tre), bem.bem_grid_create(ctx, xi, tri_)
+        t0 = time.perf_counter()
+        bem.bem_autotune(ctx, ge, gi, 1)
+        n_unk = 2 * (Ne + Ni)
+        tuning = {"seconds": time.perf_counter() - t0,
+                  "chosen": {f"{k}/{w}": dict(zip(("block", "variant", "ms"), bem.bem_tune_get(k, w, n_unk)))
+                             for k, w in (("gemm32", 1), ("gemm32", 2), ("gemm32", 4), ("gemm32", 8),
+                                          ("gemv_dd", 1), ("cheb", 1), ("cheb", 8))}}
+        bem.bem_grid_destroy(ge)
+        bem.bem_grid_destroy(gi)
+        # in-solve check: one solve with the tuned shapes and one with the built-in ones,
+        # the products timed by the library's profiler; the faster set is kept (the
+        # tuner times its candidates alone, and a solve interleaves them with other work)
+        import tempfile
+
+        def product_ms():
+            bem.bem_profile_select(["k_gemm32<1>", "k_gemv_dd"])
+            bem.bem_profile_reset()
+            bem.bem_profile_enable(True)
+            step(bem.BEM_PREC_MIXED, new_out(), w["tol"])
+            torch.cuda.synchronize()
+            bem.bem_profile_enable(False)
+            rows = {name: (ms, n) for name, ms, n in bem.bem_profile_table()}
+            bem.bem_profile_select(None)
+            return {name: ms / max(n, 1) for name, (ms, n) in rows.items()}, sum(ms for ms, _ in rows.values())
+
+        step(bem.BEM_PREC_MIXED, new_out(), w["tol"])  # warm
+        with tempfile.TemporaryDirectory() as td:
+            path = os.path.join(td, "tune.json")
+            bem.bem_tune_save(path)
+            per_tuned, tot_tuned = product_ms()
+            bem.bem_tune_clear()
+            per_builtin, tot_builtin = product_ms()
+            keep = tot_tuned < tot_builtin
+            if keep:
+                bem.bem_tune_load(path)
+        tuning["in_solve"] = {"tuned_ms_per_launch": per_tuned, "built_in_ms_per_launch": per_builtin,
+                              "tuned_total_ms": tot_tuned, "built_in_total_ms": tot_builtin,
+                              "kept": "tuned" if keep else "built-in"}
+
     mixed = timed(bem.BEM_PREC_MIXED)
     fp64 = None if args.no_fp64 else timed(bem.BEM_PREC_FP64)
 
@@ -606,15 +807,17 @@ def main():
 
     single = None
     if args.single_trace and rank == 0:
-        # the single-trace formulations on the same workload: mixed-precision solves timed
-        # like the headline, accuracy against each one's own converged FP64 solve, and the
-        # distance of their exterior traces from the multiple-traces ones (discretisation)
+        # the other formulations on the same workload: mixed-precision solves timed like the
+        # headline, accuracy against each one's own converged FP64 solve, and the distance
+        # of their exterior traces from the multiple-traces ones (discretisation)
         rn = lambda a, b: float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
-        single = {"note": "Sec. 2.2 single-trace systems on the nonconforming pair, discretised as eq. "
-                          "pmchwt:discrete: 2 unknowns per vertex of one grid; every product applies that "
-                          "grid's operators and P M^-1 A M^-1 P of the other grid's (never formed)"}
+        single = {"note": "Sec. 2.2 single-trace and Sec. 2.3 high-contrast systems on the nonconforming pair, "
+                          "discretised as eq. pmchwt:discrete: 2 unknowns per vertex of one grid; every product "
+                          "applies that grid's operators and P M^-1 A M^-1 P of the other grid's (never formed)"}
         for name, form in (("pmchwt_ext", bem.BEM_FORM_PMCHWT), ("muller_ext", bem.BEM_FORM_MULLER),
-                           ("pmchwt_int", bem.BEM_FORM_PMCHWT_INT), ("muller_int", bem.BEM_FORM_MULLER_INT)):
+                           ("pmchwt_int", bem.BEM_FORM_PMCHWT_INT), ("muller_int", bem.BEM_FORM_MULLER_INT),
+                           ("hc_ext_neu", bem.BEM_FORM_HC_EXT_NEU), ("hc_ext_dir", bem.BEM_FORM_HC_EXT_DIR),
+                           ("hc_int_neu", bem.BEM_FORM_HC_INT_NEU), ("hc_int_dir", bem.BEM_FORM_HC_INT_DIR)):
             pout = new_out()
             step(bem.BEM_PREC_MIXED, pout, w["tol"], form)
             ptimes, preps = [], []
@@ -641,6 +844,18 @@ def main():
                 entry["rel_l2_vs_fp64_converged"] = perr
                 entry["max_err"] = max(perr.values())
             single[name] = entry
+
+    screen = None
+    if args.screen and rank == 0:
+        screen = run_screen(bem, ctx)
+
+    graphs = None
+    if args.graphs and rank == 0:
+        graphs = run_graphs(bem, ctx)
+
+    cube = None
+    if args.cube and rank == 0:
+        cube = run_cube(bem, ctx)
 
     batching = None
     if args.batching:
@@ -699,7 +914,11 @@ def main():
             "serving": serving,
             "batching": batching,
             "field": field,
-            "single_trace": single,
+            "formulations": single,
+            "cube": cube,
+            "cuda_graphs": graphs,
+            "screen": screen,
+            "autotune": tuning,
             "solve": solve_info(m["reports"][-1]),
             "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in m["table"][:10]],
         }

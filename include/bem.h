@@ -85,6 +85,10 @@ typedef struct bem_sparse  bem_sparse;
 #define BEM_FORM_PMCHWT_INT 3  /* interior PMCHWT (eq. pmchwt:int): 2 unknowns on the
                                   interior grid                                              */
 #define BEM_FORM_MULLER_INT 4  /* interior Mueller (eq. muller:int)                          */
+#define BEM_FORM_HC_EXT_NEU 5  /* exterior high-contrast Neumann (eq. highcontrast:ext:neu)    */
+#define BEM_FORM_HC_EXT_DIR 6  /* exterior high-contrast Dirichlet (eq. highcontrast:ext:dir)  */
+#define BEM_FORM_HC_INT_NEU 7  /* interior high-contrast Neumann (eq. highcontrast:int:neu)    */
+#define BEM_FORM_HC_INT_DIR 8  /* interior high-contrast Dirichlet (eq. highcontrast:int:dir)  */
 
 /* Thread-local message of the last failing call (never NULL). */
 BEM_API const char* bem_last_error(void);
@@ -120,6 +124,33 @@ BEM_API void       bem_profile_reset(void);
 BEM_API int        bem_profile_count(void);
 BEM_API bem_status bem_profile_get(int index, char* name, int name_len, double* total_ms,
                                    int64_t* launches);
+
+/* ---------------------------------------------------------------- autotuner
+ * Launch shapes of the iteration's kernels (no counterpart in the paper, which runs
+ * on CPUs).  bem_autotune times the candidates on complex64 operators of the two
+ * grids' sizes (seeded random values) and on the grids' mass matrices, and keeps the
+ * fastest in a process-wide table keyed by (kernel, width, ceil(log2(rows))):
+ *   "gemm32"  FP32 dense product, width 1, 2, 4, 8 columns: block 128/256/512
+ *             threads, variant = 16-byte loads in flight per lane (2 or 4);
+ *   "gemv_dd" double-float single-column product: block 128/256/512, variant 0;
+ *   "cheb"    Chebyshev mass-inverse steps, width 1 and 8 columns: block 64/128/256;
+ *   "gemm_tc" tensor-core product of min(n_rhs, 64) columns (only if n_rhs > 8),
+ *             width = columns padded to 8: variant = K splits (1 or 2).
+ * Solves of any later call look their shapes up there (built-in defaults where no
+ * entry matches); results do not depend on the shapes beyond rounding.  Takes a
+ * few seconds at 10^4 vertices per grid and needs the same device memory as the
+ * operators of a mixed-precision solve.  bem_tune_get returns block = 0 when no
+ * entry matches (ms: the measured time, may be NULL).  bem_tune_save writes the
+ * table as JSON (format "bem-tune-1"); bem_tune_load merges such a file into it
+ * (entries with the same key are replaced; malformed files: BEM_E_INVALID_ARG,
+ * nothing merged).  The table functions need no GPU. */
+BEM_API bem_status bem_autotune(bem_context* ctx, const bem_grid* ext, const bem_grid* intr, int32_t n_rhs);
+BEM_API bem_status bem_tune_get(const char* kernel, int32_t width, int64_t rows, int32_t* block,
+                                int32_t* variant, double* ms);
+BEM_API int32_t    bem_tune_count(void);
+BEM_API void       bem_tune_clear(void);
+BEM_API bem_status bem_tune_save(const char* path);
+BEM_API bem_status bem_tune_load(const char* path);
 
 /* ---------------------------------------------------------------- context
  * A context binds a CUDA device and a stream.  `stream` is a cudaStream_t
@@ -238,6 +269,10 @@ typedef struct {
     int32_t formulation;      /* BEM_FORM_* (default BEM_FORM_MTF); the single-trace systems are
                                  available in bem_solve_transmission only (bem_solve_many and the
                                  server solve the multiple-traces system)                         */
+    int32_t cuda_graphs;      /* 1 (default): the fixed launch sequences of each iteration (the
+                                 Chebyshev mass inverses) are captured once per solve and replayed
+                                 as CUDA graphs; 0: every kernel is launched on its own. Results
+                                 are identical either way.                                        */
 } bem_solve_opts;
 
 typedef struct {
@@ -280,13 +315,55 @@ BEM_API void bem_solve_opts_default(bem_solve_opts* opts);
  * and P in turn.  The other grid's potentials follow from the transmission conditions
  * tested on it: v_i = -M_i^-1 P_ie v_e, w_i = -r M_i^-1 P_ie w_e (exterior variants),
  * v_e = -M_e^-1 P_ei v_i, w_e = -(1/r) M_e^-1 P_ei w_i (interior variants), so the
- * four outputs keep the meaning stated above.  mtf_variant is ignored.          */
+ * four outputs keep the meaning stated above.  mtf_variant is ignored.
+ *
+ * High-contrast formulations (paper Sec. 2.3), discretised the same way (a mass
+ * inverse between two operators and on a data vector an operator acts on; X^ the
+ * other grid's operator mapped as above):
+ *   BEM_FORM_HC_EXT_NEU  unknowns a = gamma_N^+ p and mu (u_s = V mu), exterior grid:
+ *     [M_e/2 - T^_i, -(1/r) D^_i M_e^-1 V_e; M_e, M_e/2 - T_e] = [(1/r) D^_i M_e^-1 f; g]
+ *   BEM_FORM_HC_EXT_DIR  unknowns nu (u_s = -K nu) and b = gamma_D^+ p:
+ *     [M_e/2 + K_e, M_e; -r V^_i M_e^-1 D_e, M_e/2 + K^_i] = [f; r V^_i M_e^-1 g]
+ *   BEM_FORM_HC_INT_NEU  unknowns a = gamma_N^- p and mu (u_int = V mu), interior grid:
+ *     [M_i/2 + T^_e, r D^_e M_i^-1 V_i; -M_i, M_i/2 + T_i]
+ *       = [r P_ie M_e^-1 (D_e M_e^-1 f + g/2 + T_e M_e^-1 g); 0]
+ *   BEM_FORM_HC_INT_DIR  unknowns nu (u_int = -K nu) and b = gamma_D^- p:
+ *     [M_i/2 - K_i, -M_i; (1/r) V^_e M_i^-1 D_i, M_i/2 - K^_e]
+ *       = [0; P_ie M_e^-1 (V_e M_e^-1 g + f/2 - K_e M_e^-1 f)]
+ * left-preconditioned by the mass inverse of the unknowns' grid.  The unknowns' grid
+ * traces follow from the representation (e.g. v_e = -M_e^-1 (f + V_e mu)), the other
+ * grid's from the transmission conditions; the four outputs keep their meaning.  Their
+ * products run on the CUDA cores (tensor_cores is ignored).                   */
 BEM_API bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const bem_grid* intr,
                                   bem_c128 k_int, bem_c128 k_ext, double rho_int_over_rho_ext,
                                   const bem_incident* inc, const bem_solve_opts* opts,
                                   bem_c128* v_ext, bem_c128* w_ext,
                                   bem_c128* v_int, bem_c128* w_int,
                                   int on_device, bem_solve_report* rep);
+
+/* Neumann screen (paper Sec. 4.2, eq. neumannscreen; the benchmark of Sec. 5.7): a
+ * sound-hard open surface `screen` (a grid with a boundary: nodes on edges of one
+ * triangle), u_s = K phi with phi the jump of the total field across the screen, and
+ *     D phi = gamma_N u_inc   on the screen,
+ * discretised with the P1 functions of the screen's interior nodes (phi = 0 on its
+ * boundary), data g_i = <i k (d . n) exp(i k x . d), theta_i> (n: the triangles' normal),
+ * and solved by unrestarted GMRES on the left-preconditioned system
+ *   BEM_SCREEN_MASS  M^-1 D phi = M^-1 g,
+ *   BEM_SCREEN_OO    M^-1 V^_c M^-1 D phi = M^-1 V^_c M^-1 g  (opposite-order),
+ *                    V^_c = P_cs^T M_c^-1 V_c M_c^-1 P_cs: the single layer on the grid
+ *                    `coarse` (coplanar, all its nodes) through the mortar matrix,
+ * M the screen's mass matrix on its interior nodes.  With a coarse grid V^_c has rank
+ * at most its node count, so the OO iterate solves the preconditioned system, not
+ * D phi = g itself; coarse = screen gives the conforming preconditioner (same solution
+ * as BEM_SCREEN_MASS).  phi: [n_rhs * N_screen] (host, or device with on_device = 1),
+ * zero at boundary nodes.  opts: gmres_tol, gmres_maxiter, precision (FP64 or mixed:
+ * FP32 assembly, complex64 storage, FP64 refinement), n_singular, batch_columns (1..8,
+ * default 8), cuda_graphs; the others are ignored.  rep as for bem_solve_transmission. */
+#define BEM_SCREEN_MASS 0
+#define BEM_SCREEN_OO   1
+BEM_API bem_status bem_solve_screen(bem_context* ctx, const bem_grid* screen, const bem_grid* coarse,
+                                    bem_c128 k, const bem_incident* inc, const bem_solve_opts* opts,
+                                    int32_t precond, bem_c128* phi, int on_device, bem_solve_report* rep);
 
 /* Field of P1 densities at points off the surface (paper Sec. 2.1, eq.
  * representation):

@@ -34,6 +34,7 @@ BEM_PREC_FP64 = 0
 BEM_PREC_MIXED = 1
 BEM_MTF_DERIVED, BEM_MTF_PRINTED = 0, 1
 BEM_FORM_MTF, BEM_FORM_PMCHWT, BEM_FORM_MULLER, BEM_FORM_PMCHWT_INT, BEM_FORM_MULLER_INT = 0, 1, 2, 3, 4
+BEM_FORM_HC_EXT_NEU, BEM_FORM_HC_EXT_DIR, BEM_FORM_HC_INT_NEU, BEM_FORM_HC_INT_DIR = 5, 6, 7, 8
 
 
 class BemError(RuntimeError):
@@ -62,6 +63,7 @@ class bem_solve_opts(C.Structure):
         ("batch_columns", C.c_int32),
         ("tensor_cores", C.c_int32),
         ("formulation", C.c_int32),
+        ("cuda_graphs", C.c_int32),
     ]
 
 
@@ -150,6 +152,14 @@ _SIGNATURES = {
     "bem_profile_enable": (None, [C.c_int]),
     "bem_profile_select": (None, [C.c_char_p]),
     "bem_profile_reset": (None, []),
+    "bem_autotune": (C.c_int32, [_VP, _VP, _VP, C.c_int32]),
+    "bem_solve_screen": (C.c_int32, [_VP, _VP, _VP, bem_c128, _VP, _VP, C.c_int32, _VP, C.c_int, _VP]),
+    "bem_tune_get": (C.c_int32, [C.c_char_p, C.c_int32, _I64, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_double)]),
+    "bem_tune_count": (C.c_int32, []),
+    "bem_tune_clear": (None, []),
+    "bem_tune_save": (C.c_int32, [C.c_char_p]),
+    "bem_tune_load": (C.c_int32, [C.c_char_p]),
     "bem_profile_count": (C.c_int, []),
     "bem_profile_get": (C.c_int32, [C.c_int, C.c_char_p, C.c_int, C.POINTER(C.c_double), _PI64]),
     "bem_context_create": (C.c_int32, [C.c_int, _VP, _PVP]),
@@ -261,6 +271,69 @@ def bem_profile_select(prefixes=None):
 
 def bem_profile_reset():
     _lib.bem_profile_reset()
+
+
+BEM_SCREEN_MASS, BEM_SCREEN_OO = 0, 1
+
+
+def bem_solve_screen(ctx, screen, k, dirs, coarse=None, precond=BEM_SCREEN_MASS, amps=None, opts=None, out=None,
+                     on_device=False):
+    """Neumann screen D phi = gamma_N u_inc (mass or opposite-order preconditioning).
+
+    Returns (phi [n_rhs, N] complex128 (zero on the screen's boundary), report dict);
+    raises BemError on failure (BEM_E_NOT_CONVERGED with .outputs and .report)."""
+    dirs = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    n_rhs = dirs.shape[0]
+    inc = bem_incident()
+    inc.n_rhs = n_rhs
+    inc.dirs = dirs.ctypes.data_as(C.POINTER(C.c_double))
+    amp_arr = None
+    if amps is not None:
+        amp_arr = (bem_c128 * n_rhs)(*[_c128(a) for a in np.atleast_1d(amps)])
+        inc.amps = C.cast(amp_arr, C.POINTER(bem_c128))
+    o = _opts(opts)
+    N = bem_grid_num_vertices(screen)
+    if out is None:
+        if on_device:
+            raise ValueError("device outputs must be preallocated")
+        out = np.zeros((n_rhs, N), dtype=np.complex128)
+    rep = bem_solve_report()
+    st = _lib.bem_solve_screen(ctx, screen, coarse, _c128(k), C.byref(inc), C.byref(o), int(precond), _ptr(out)[0],
+                               int(bool(on_device)), C.byref(rep))
+    report = {f: getattr(rep, f) for f, _ in bem_solve_report._fields_}
+    if st != BEM_OK:
+        err = BemError(st, _lib.bem_last_error().decode())
+        err.outputs, err.report = out, report
+        raise err
+    return out, report
+
+
+def bem_autotune(ctx, ext, intr, n_rhs=1):
+    """Time the candidate launch shapes for these grids' sizes and keep the fastest."""
+    _check(_lib.bem_autotune(ctx, ext, intr, int(n_rhs)))
+
+
+def bem_tune_get(kernel, width, rows):
+    """(block, variant, ms) chosen for (kernel, width, rows); block 0: no entry."""
+    b, v, ms = C.c_int32(), C.c_int32(), C.c_double()
+    _check(_lib.bem_tune_get(kernel.encode(), int(width), int(rows), C.byref(b), C.byref(v), C.byref(ms)))
+    return b.value, v.value, ms.value
+
+
+def bem_tune_count():
+    return int(_lib.bem_tune_count())
+
+
+def bem_tune_clear():
+    _lib.bem_tune_clear()
+
+
+def bem_tune_save(path):
+    _check(_lib.bem_tune_save(os.fsencode(path)))
+
+
+def bem_tune_load(path):
+    _check(_lib.bem_tune_load(os.fsencode(path)))
 
 
 def bem_profile_count():

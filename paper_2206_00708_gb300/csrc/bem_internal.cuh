@@ -17,6 +17,28 @@ inline double now_seconds() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// ------------------------------------------------------------------ autotuner table
+// Launch shapes chosen by bem_autotune (tune.cu): per kernel family, width (columns per
+// launch) and size class ceil(log2(rows)), a block size and a variant.
+enum { TUNE_GEMM32 = 0, TUNE_GEMV_DD = 1, TUNE_GEMM_TC = 2, TUNE_CHEB = 3, TUNE_KERNELS = 4 };
+struct TuneChoice {
+    int block;    // threads per block (0: the kernel's own)
+    int variant;  // gemm32: 16-byte loads in flight per lane (2 or 4); gemm_tc: K splits (1 or 2)
+    double ms;    // time measured for it
+};
+int size_class(int64_t n);
+TuneChoice tune_get(int kernel, int width, int64_t n, TuneChoice dflt);
+void tune_put(int kernel, int width, int64_t n, TuneChoice c);
+inline bool tune_choice_valid(int kernel, const TuneChoice& c) {
+    switch (kernel) {
+        case TUNE_GEMM32: return (c.block == 128 || c.block == 256 || c.block == 512) && (c.variant == 2 || c.variant == 4);
+        case TUNE_GEMV_DD: return (c.block == 128 || c.block == 256 || c.block == 512) && c.variant == 0;
+        case TUNE_GEMM_TC: return c.block == 0 && (c.variant == 1 || c.variant == 2);
+        case TUNE_CHEB: return (c.block == 64 || c.block == 128 || c.block == 256) && c.variant == 0;
+        default: return false;
+    }
+}
+
 // ------------------------------------------------------------------ errors
 void set_error(const std::string& msg);
 
@@ -33,20 +55,41 @@ void set_error(const std::string& msg);
 
 #define BEM_CHECK_LAUNCH() BEM_CUDA_TRY(cudaGetLastError())
 
-// Number of kernels this library has launched since it was loaded.
-void count_launch();
+// Number of kernels this library has launched since it was loaded (a CUDA graph launch
+// counts its kernel nodes).
+void count_launch(uint64_t n = 1);
+
+// Nonzero while this thread records launches into a CUDA graph (stream capture): they
+// are then neither timed nor counted (the graph's launches are counted instead).
+extern thread_local int g_capturing;
 
 // Optional per-kernel event timing (profile.cu); -1 when profiling is off.
 int prof_begin(const char* name, cudaStream_t s);
 void prof_end(int slot, cudaStream_t s);
+// True while profiling times every kernel (no selection): fixed launch sequences are
+// then launched kernel by kernel instead of as CUDA graphs, so that each is timed.
+bool prof_times_every_kernel();
 
 // Launch a kernel, time it when profiling is on, count it and check the launch.
 #define BEM_LAUNCH(kern, grid, block, smem, stream, ...)                \
     do {                                                                \
-        const int prof_slot_ = ::bem::prof_begin(#kern, (stream));      \
+        const int prof_slot_ =                                          \
+            ::bem::g_capturing ? -1 : ::bem::prof_begin(#kern, (stream)); \
         kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);       \
         ::bem::prof_end(prof_slot_, (stream));                          \
-        ::bem::count_launch();                                          \
+        if (!::bem::g_capturing) ::bem::count_launch();                 \
+        BEM_CHECK_LAUNCH();                                             \
+    } while (0)
+
+// The same for a kernel given as a function pointer (a template instance chosen at run
+// time), timed by the profiler under `name`.
+#define BEM_LAUNCH_PTR(name, kptr, grid, block, smem, stream, ...)       \
+    do {                                                                \
+        const int prof_slot_ =                                          \
+            ::bem::g_capturing ? -1 : ::bem::prof_begin((name), (stream)); \
+        (kptr)<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);     \
+        ::bem::prof_end(prof_slot_, (stream));                          \
+        if (!::bem::g_capturing) ::bem::count_launch();                 \
         BEM_CHECK_LAUNCH();                                             \
     } while (0)
 

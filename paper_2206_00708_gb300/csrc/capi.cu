@@ -18,7 +18,8 @@ std::atomic<uint64_t> g_launches{0};
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+thread_local int g_capturing = 0;
 
 bem_status DevBuf::alloc(size_t nbytes, cudaStream_t s) {
     release();
@@ -51,6 +52,10 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                                    bem_c128* w_int, int on_device, bem_solve_report* rep);
 bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst, const bem_solve_opts* o,
                            int on_device, bem_solve_report* reps);
+bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_grid* gc, bem_c128 k,
+                             const bem_incident* inc, const bem_solve_opts* o, int precond, bem_c128* phi,
+                             int on_device, bem_solve_report* rep);
+bem_status autotune_impl(bem_context* ctx, const bem_grid* ge, const bem_grid* gi, int n_rhs, int reps);
 bem_status field_impl(bem_context* ctx, const bem_grid* g, bem_c128 k, const bem_c128* phi, const bem_c128* psi,
                       const double* points, int64_t npts, bem_c128* u, int on_device);
 
@@ -353,6 +358,7 @@ void bem_solve_opts_default(bem_solve_opts* o) {
     o->batch_columns = 0;
     o->tensor_cores = 1;
     o->formulation = BEM_FORM_MTF;
+    o->cuda_graphs = 1;
 }
 
 bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const bem_grid* intr, bem_c128 k_int,
@@ -376,7 +382,8 @@ bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const b
     BEM_REQUIRE(o.ir_inner_tol > 0.0 && o.ir_inner_tol < 1.0, "ir_inner_tol must be in (0, 1)");
     BEM_REQUIRE(o.batch_columns >= 0 && o.batch_columns <= 128, "batch_columns must be in [0, 128]");
     BEM_REQUIRE(o.tensor_cores == 0 || o.tensor_cores == 1, "tensor_cores must be 0 or 1");
-    BEM_REQUIRE(o.formulation >= BEM_FORM_MTF && o.formulation <= BEM_FORM_MULLER_INT, "unknown formulation");
+    BEM_REQUIRE(o.formulation >= BEM_FORM_MTF && o.formulation <= BEM_FORM_HC_INT_DIR, "unknown formulation");
+    BEM_REQUIRE(o.cuda_graphs == 0 || o.cuda_graphs == 1, "cuda_graphs must be 0 or 1");
     for (int r = 0; r < inc->n_rhs; ++r) {
         const double* d = inc->dirs + 3 * r;
         const double nd = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -384,6 +391,40 @@ bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const b
     }
     return solve_transmission_impl(ctx, ext, intr, k_int, k_ext, rho_int_over_rho_ext, inc, &o, v_ext, w_ext, v_int,
                                    w_int, on_device, rep);
+}
+
+bem_status bem_solve_screen(bem_context* ctx, const bem_grid* screen, const bem_grid* coarse, bem_c128 k,
+                            const bem_incident* inc, const bem_solve_opts* opts, int32_t precond, bem_c128* phi,
+                            int on_device, bem_solve_report* rep) {
+    CTX_GUARD(ctx);
+    BEM_REQUIRE(screen != nullptr, "null screen grid");
+    BEM_REQUIRE(precond == BEM_SCREEN_MASS || precond == BEM_SCREEN_OO, "unknown screen preconditioner");
+    BEM_REQUIRE(precond == BEM_SCREEN_MASS || coarse != nullptr, "the opposite-order preconditioner needs a grid");
+    BEM_REQUIRE(inc != nullptr && inc->n_rhs >= 1 && inc->dirs != nullptr, "incident field needs n_rhs >= 1 and dirs");
+    BEM_REQUIRE(phi != nullptr, "null output array");
+    BEM_REQUIRE(std::isfinite(k.re) && std::isfinite(k.im), "wavenumber is not finite");
+    bem_solve_opts o;
+    if (opts) o = *opts;
+    else bem_solve_opts_default(&o);
+    BEM_REQUIRE(o.gmres_tol >= 0.0 && o.gmres_maxiter >= 1, "bad GMRES options");
+    BEM_REQUIRE(o.n_singular >= 1 && o.n_singular <= 16, "n_singular must be in [1, 16]");
+    BEM_REQUIRE(o.precision == BEM_PREC_FP64 || o.precision == BEM_PREC_MIXED, "unsupported precision");
+    BEM_REQUIRE(o.ir_inner_tol > 0.0 && o.ir_inner_tol < 1.0, "ir_inner_tol must be in (0, 1)");
+    BEM_REQUIRE(o.batch_columns >= 0 && o.batch_columns <= 128, "batch_columns must be in [0, 128]");
+    BEM_REQUIRE(o.cuda_graphs == 0 || o.cuda_graphs == 1, "cuda_graphs must be 0 or 1");
+    for (int r = 0; r < inc->n_rhs; ++r) {
+        const double* d = inc->dirs + 3 * r;
+        const double nd = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        BEM_REQUIRE(std::isfinite(nd) && std::fabs(nd - 1.0) < 1e-6, "incident directions must be unit vectors");
+    }
+    return solve_screen_impl(ctx, screen, coarse, k, inc, &o, precond, phi, on_device, rep);
+}
+
+bem_status bem_autotune(bem_context* ctx, const bem_grid* ext, const bem_grid* intr, int32_t n_rhs) {
+    CTX_GUARD(ctx);
+    BEM_REQUIRE(ext != nullptr && intr != nullptr, "null grid");
+    BEM_REQUIRE(n_rhs >= 1 && n_rhs <= 4096, "n_rhs must be in [1, 4096]");
+    return autotune_impl(ctx, ext, intr, n_rhs, 5);
 }
 
 bem_status bem_field(bem_context* ctx, const bem_grid* g, bem_c128 k, const bem_c128* phi, const bem_c128* psi,
@@ -411,6 +452,7 @@ bem_status bem_solve_many(bem_context* ctx, int32_t count, const bem_instance* i
     }
     BEM_REQUIRE(o.precision == BEM_PREC_MIXED, "bem_solve_many runs the mixed-precision mode");
     BEM_REQUIRE(o.formulation == BEM_FORM_MTF, "bem_solve_many solves the multiple-traces system only");
+    BEM_REQUIRE(o.cuda_graphs == 0 || o.cuda_graphs == 1, "cuda_graphs must be 0 or 1");
     BEM_REQUIRE(o.gmres_tol >= 0.0 && o.gmres_maxiter >= 1, "bad GMRES options");
     BEM_REQUIRE(o.n_singular >= 1 && o.n_singular <= 16, "n_singular must be in [1, 16]");
     BEM_REQUIRE(o.mtf_variant == BEM_MTF_DERIVED || o.mtf_variant == BEM_MTF_PRINTED, "unknown MTF variant");

@@ -24,7 +24,7 @@
 // (chosen by stage, summed in FP64 at the end) and commits them to the stage's
 // mbarrier; two shared-memory stages alternate and the global loads of A for stages
 // s + 1 and s + 2 are in flight (two register buffers) while stage s is staged and
-// issued.  With fewer row tiles than SMs
+// issued.  With fewer row tiles than SMs (or as the autotuner chose for the shape)
 // the K range is split between two CTAs whose results are added into a zeroed z
 // (two addends: their order cannot change the sum).  The epilogue reads the
 // accumulators with tcgen05.ld (warps 0-3: real parts, warps 4-7: imaginary parts).
@@ -407,11 +407,12 @@ bem_status mtf_product_tc(const float2* const a1[4], const float2* const a2[4], 
     // all 512 columns) never waits for another CTA
     const int smem = std::max(2 * (2 * TC_A_STAGE + 2 * b_stage), 116 * 1024);
     BEM_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    // fewer row tiles than SMs: split K in two halves (their two sums commute exactly)
+    // fewer row tiles than SMs: split K in two halves (their two sums commute exactly),
+    // unless the autotuner measured otherwise for this shape
     int sms = 0, dev = 0;
     BEM_CUDA_TRY(cudaGetDevice(&dev));
     BEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int ksplit = tiles < sms ? 2 : 1;
+    const int ksplit = tune_get(TUNE_GEMM_TC, RP, n, TuneChoice{0, tiles < sms ? 2 : 1, 0.0}).variant;
     if (ksplit > 1) BEM_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)R * n * sizeof(double2), s));
     BEM_LAUNCH(k_gemm_tc, dim3(tiles, ksplit), TC_THREADS, smem, s, ta, reinterpret_cast<double*>(z), err);
     return BEM_OK;

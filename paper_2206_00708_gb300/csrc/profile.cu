@@ -72,6 +72,12 @@ int prof_begin(const char* name, cudaStream_t s) {
     return (int)g_live.size() - 1;
 }
 
+bool prof_times_every_kernel() {
+    if (!g_on.load(std::memory_order_relaxed)) return false;
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_select.empty();
+}
+
 void prof_end(int slot, cudaStream_t s) {
     if (slot < 0) return;
     std::lock_guard<std::mutex> lk(g_mu);

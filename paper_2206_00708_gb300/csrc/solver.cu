@@ -215,8 +215,8 @@ __global__ void __launch_bounds__(256) k_gemm_c64_f64(Blocks<float2> B, int64_t 
 // entries per lane) shared by the R right-hand sides; products are summed plainly in
 // groups of four and added to the lane's accumulator with a compensated (two-sum)
 // update; warp totals are formed in FP64.
-template <int R>
-__global__ void __launch_bounds__(256) k_gemm32(Blocks<float2> B, int64_t n, const float2* __restrict__ x,
+template <int R, int H>
+__global__ void __launch_bounds__(512) k_gemm32(Blocks<float2> B, int64_t n, const float2* __restrict__ x,
                                                 double2* __restrict__ z) {
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(256) k_gemm32(Blocks<float2> B, int64_t n, con
     for (int r = 0; r < R; ++r) out[r] = make_double2(0, 0);
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
+        if (m == 1 && B.A2[b] == nullptr) break;  // a block row of one matrix
         const float2* __restrict__ a = (m == 0 ? B.A1[b] : B.A2[b]) + i * N;
         const int64_t xo = m == 0 ? B.x1[b] : B.x2[b];
         float sr[R], si[R], er[R], ei[R];
@@ -253,7 +254,6 @@ __global__ void __launch_bounds__(256) k_gemm32(Blocks<float2> B, int64_t n, con
         // H 16-byte loads in flight per lane (streamed past L1: the operator is read
         // once); 4 H products summed plainly per right-hand side before the
         // compensated update
-        constexpr int H = R == 1 ? 4 : 2;
         for (int64_t p = lane; p < npair; p += 32 * H) {
             float cr[R], ci[R];
 #pragma unroll
@@ -367,7 +367,7 @@ __device__ __forceinline__ void dd_cmac(float ar, float ai, float4 x, float& sr,
 // 8 bytes per entry as k_gemm32<1>.  Used for the single-column inner products of the
 // refinement, which then converge on the stored system instead of stagnating at the
 // FP32 rounding of the product.
-__global__ void __launch_bounds__(256) k_gemv_dd(Blocks<float2> B, int64_t n, const float4* __restrict__ xs,
+__global__ void __launch_bounds__(512) k_gemv_dd(Blocks<float2> B, int64_t n, const float4* __restrict__ xs,
                                                  double2* __restrict__ z) {
     const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -379,6 +379,7 @@ __global__ void __launch_bounds__(256) k_gemv_dd(Blocks<float2> B, int64_t n, co
     double2 out = make_double2(0, 0);
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
+        if (m == 1 && B.A2[b] == nullptr) break;  // a block row of one matrix
         const float2* __restrict__ a = (m == 0 ? B.A1[b] : B.A2[b]) + i * N;
         const float4* __restrict__ x = xs + (m == 0 ? B.x1[b] : B.x2[b]);
         float sr = 0.f, er = 0.f, si = 0.f, ei = 0.f;
@@ -412,6 +413,43 @@ __global__ void __launch_bounds__(256) k_gemv_dd(Blocks<float2> B, int64_t n, co
         out.y += c * v.y;
     }
     if (lane == 0) z[gw] = out;
+}
+
+// k_gemm32 for W = 1, 2, 4 or 8 columns with the tuned block size and loads in flight
+// (defaults: 256 threads; 4 loads for one column, 2 for more)
+using Gemm32Fn = void (*)(Blocks<float2>, int64_t, const float2*, double2*);
+
+Gemm32Fn gemm32_fn(int W, int H) {
+    switch (W * 10 + H) {
+        case 12: return k_gemm32<1, 2>;
+        case 14: return k_gemm32<1, 4>;
+        case 22: return k_gemm32<2, 2>;
+        case 24: return k_gemm32<2, 4>;
+        case 42: return k_gemm32<4, 2>;
+        case 44: return k_gemm32<4, 4>;
+        case 82: return k_gemm32<8, 2>;
+        default: return k_gemm32<8, 4>;
+    }
+}
+
+const char* gemm32_name(int W) {
+    return W == 1 ? "k_gemm32<1>" : W == 2 ? "k_gemm32<2>" : W == 4 ? "k_gemm32<4>" : "k_gemm32<8>";
+}
+
+TuneChoice gemm32_default(int W) { return TuneChoice{256, W == 1 ? 4 : 2, 0.0}; }
+
+bem_status launch_gemm32(int W, const Blocks<float2>& B, int64_t n, const float2* x, double2* z, cudaStream_t s,
+                         const TuneChoice* force = nullptr) {
+    const TuneChoice c = force ? *force : tune_get(TUNE_GEMM32, W, n, gemm32_default(W));
+    BEM_LAUNCH_PTR(gemm32_name(W), gemm32_fn(W, c.variant), blocks_for(n * 32, c.block), c.block, 0, s, B, n, x, z);
+    return BEM_OK;
+}
+
+bem_status launch_gemv_dd(const Blocks<float2>& B, int64_t n, const float4* xs, double2* z, cudaStream_t s,
+                          const TuneChoice* force = nullptr) {
+    const TuneChoice c = force ? *force : tune_get(TUNE_GEMV_DD, 1, n, TuneChoice{256, 0, 0.0});
+    BEM_LAUNCH(k_gemv_dd, blocks_for(n * 32, c.block), c.block, 0, s, B, n, xs, z);
+    return BEM_OK;
 }
 
 // ---------------------------------------------------------------- mortar transfer
@@ -462,34 +500,67 @@ __global__ void k_csr_scatter(const int32_t* __restrict__ key, const int32_t* __
     ov[p] = val[e];
 }
 
-// per row: sort by (column, value), sum equal columns in that order, compact in place
-__global__ void k_csr_merge(const int32_t* __restrict__ start, int64_t rows, int32_t* __restrict__ oc,
-                            double* __restrict__ ov, int32_t* __restrict__ mcnt) {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// Entries of one row sorted in shared memory (12 bytes each: 48 KB); longer rows are
+// sorted in place in global memory by the same network.
+constexpr int CSR_MERGE_SMEM = 4096;
+
+__device__ __forceinline__ bool csr_less(int32_t ca, double va, int32_t cb, double vb) {
+    return ca < cb || (ca == cb && va < vb);
+}
+
+// One block per row: sort the row's entries by (column, value), then sum equal columns
+// in that order and compact in place (the order, hence the sums, do not depend on the
+// order in which the entries were produced).  Bitonic network with every comparator
+// ascending (the first step of each stage pairs i with its mirror i ^ (size - 1)), so
+// the row length need not be a power of two: slots past its end act as +infinity and
+// are never touched.
+__global__ void __launch_bounds__(256) k_csr_merge(const int32_t* __restrict__ start, int64_t rows,
+                                                   int32_t* __restrict__ oc, double* __restrict__ ov,
+                                                   int32_t* __restrict__ mcnt) {
+    __shared__ int32_t s_c[CSR_MERGE_SMEM];
+    __shared__ double s_v[CSR_MERGE_SMEM];
+    const int64_t k = blockIdx.x;
     if (k >= rows) return;
-    const int32_t b = start[k], e = start[k + 1];
-    for (int32_t i = b + 1; i < e; ++i) {
-        const int32_t c = oc[i];
-        const double v = ov[i];
-        int32_t j = i - 1;
-        while (j >= b && (oc[j] > c || (oc[j] == c && ov[j] > v))) {
-            oc[j + 1] = oc[j];
-            ov[j + 1] = ov[j];
-            --j;
+    const int32_t b = start[k], len = start[k + 1] - b;
+    const bool in_smem = len <= CSR_MERGE_SMEM;
+    int32_t* C = in_smem ? s_c : oc + b;
+    double* V = in_smem ? s_v : ov + b;
+    if (in_smem)
+        for (int32_t i = threadIdx.x; i < len; i += blockDim.x) {
+            s_c[i] = oc[b + i];
+            s_v[i] = ov[b + i];
         }
-        oc[j + 1] = c;
-        ov[j + 1] = v;
+    __syncthreads();
+    int32_t p2 = 1;
+    while (p2 < len) p2 <<= 1;
+    for (int32_t size = 2; size <= p2; size <<= 1) {
+        for (int32_t j = size >> 1; j > 0; j >>= 1) {
+            for (int32_t i = threadIdx.x; i < p2; i += blockDim.x) {
+                const int32_t partner = j == (size >> 1) ? (i ^ (size - 1)) : (i ^ j);
+                if (partner > i && partner < len && csr_less(C[partner], V[partner], C[i], V[i])) {
+                    const int32_t tc = C[i];
+                    const double tv = V[i];
+                    C[i] = C[partner];
+                    V[i] = V[partner];
+                    C[partner] = tc;
+                    V[partner] = tv;
+                }
+            }
+            __syncthreads();
+        }
     }
-    int32_t w = b;
-    for (int32_t i = b; i < e;) {
-        const int32_t c = oc[i];
-        double sum = 0.0;
-        while (i < e && oc[i] == c) sum += ov[i++];
-        oc[w] = c;
-        ov[w] = sum;
-        ++w;
+    if (threadIdx.x == 0) {  // the write position never passes the read position
+        int32_t w = 0;
+        for (int32_t i = 0; i < len;) {
+            const int32_t c = C[i];
+            double sum = 0.0;
+            while (i < len && C[i] == c) sum += V[i++];
+            oc[b + w] = c;
+            ov[b + w] = sum;
+            ++w;
+        }
+        mcnt[k] = w;
     }
-    mcnt[k] = w - b;
 }
 
 __global__ void k_csr_compact(const int32_t* __restrict__ start, const int32_t* __restrict__ rp, int64_t rows,
@@ -543,17 +614,18 @@ __global__ void k_transfer(TransferCsr T, const double2* __restrict__ xb, double
 }
 
 // One mortar matrix (CSR, `rows` rows, columns on a grid of `cols` vertices) applied to
-// both potentials of a column: z[b rows + i] = c_b (P x_b)_i for b = 0, 1, with x_b at
-// x + b cols (x of stride nx, z of stride nz, blockIdx.y = right-hand side); `add`
-// accumulates into z instead.  One thread per row of z, no atomics.
+// two vectors of a column: z[b rows + i] = c_b (P x_b)_i for b = 0, 1, with x_b at
+// x0 or x1 (both of column stride nx; z of stride nz, blockIdx.y = right-hand side);
+// `add` accumulates into z instead.  One thread per row of z, no atomics.
 __global__ void k_csr_pair(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                           const double* __restrict__ v, int64_t rows, int64_t cols, const double2* __restrict__ xb,
-                           int64_t nx, double2* __restrict__ zb, int64_t nz, double c0, double c1, int add) {
+                           const double* __restrict__ v, int64_t rows, const double2* __restrict__ x0,
+                           const double2* __restrict__ x1, int64_t nx, double2* __restrict__ zb, int64_t nz,
+                           double c0, double c1, int add) {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= 2 * rows) return;
     const int b = g >= rows ? 1 : 0;
     const int64_t i = g - b * rows;
-    const double2* x = xb + blockIdx.y * nx + b * cols;
+    const double2* x = (b ? x1 : x0) + blockIdx.y * nx;
     double sr = 0.0, si = 0.0;
     for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
         const double p = v[e];
@@ -567,6 +639,76 @@ __global__ void k_csr_pair(const int32_t* __restrict__ rp, const int32_t* __rest
     zz.x = fma(c, sr, zz.x);
     zz.y = fma(c, si, zz.y);
     *zp = zz;
+}
+
+// y = C s over pairs of vectors of one grid (R columns of stride `stride`, two halves of
+// N entries): for half b, y_b = sum_k C[6 b + k] s_k with s = (x_0, x_1, u_0, u_1, w_0, w_1)
+// the halves of x, u and w.  Real coefficients; y must not be one of the inputs.
+struct PairCoef {
+    double c[12];
+};
+
+__global__ void k_pair_lin(double2* __restrict__ y, const double2* x, const double2* u, const double2* w, int64_t N,
+                           int64_t stride, PairCoef C) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= 2 * N) return;
+    const int b = g >= N ? 1 : 0;
+    const int64_t i = g - b * N, off = blockIdx.y * stride;
+    const double2 s[6] = {x[off + i], x[off + N + i], u[off + i], u[off + N + i], w[off + i], w[off + N + i]};
+    double2 r = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double c = C.c[6 * b + k];
+        r.x = fma(c, s[k].x, r.x);
+        r.y = fma(c, s[k].y, r.y);
+    }
+    y[off + g] = r;
+}
+
+// ---------------------------------------------------------------- open screens
+// A CSR matrix on one vector per column: z = c P x (x of stride nx, z of stride nz,
+// blockIdx.y = right-hand side), one thread per row
+__global__ void k_csr_apply(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ v, int64_t rows, const double2* __restrict__ x, int64_t nx,
+                            double2* __restrict__ z, int64_t nz, double c) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    const double2* xc = x + blockIdx.y * nx;
+    double sr = 0.0, si = 0.0;
+    for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+        const double p = v[e];
+        const double2 xx = xc[ci[e]];
+        sr = fma(p, xx.x, sr);
+        si = fma(p, xx.y, si);
+    }
+    z[blockIdx.y * nz + i] = make_double2(c * sr, c * si);
+}
+
+// y[i] = 0 at the screen's boundary nodes (keep[i] == 0), R columns of stride n
+__global__ void k_mask_rows(double2* __restrict__ y, const uint8_t* __restrict__ keep, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n && !keep[i]) y[blockIdx.y * n + i] = make_double2(0.0, 0.0);
+}
+
+// The ELL mass matrix of the functions that vanish on the boundary, padded to the full
+// node set: boundary rows become identity rows, couplings to boundary columns are
+// dropped; the Jacobi diagonal of a boundary row is 1.
+__global__ void k_mask_mass_ell(int32_t* __restrict__ ci, double* __restrict__ v, double* __restrict__ dinv, int W,
+                                int64_t N, const uint8_t* __restrict__ keep) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    if (!keep[i]) {
+        for (int k = 0; k < W; ++k) {
+            ci[(int64_t)k * N + i] = (int32_t)i;
+            v[(int64_t)k * N + i] = k == 0 ? 1.0 : 0.0;
+        }
+        dinv[i] = 1.0;
+        return;
+    }
+    for (int k = 0; k < W; ++k) {
+        const int32_t c = ci[(int64_t)k * N + i];
+        if (!keep[c]) v[(int64_t)k * N + i] = 0.0;
+    }
 }
 
 // ---------------------------------------------------------------- mass inverse
@@ -821,24 +963,98 @@ struct MassEll {
     }
 };
 
+// Fixed launch sequences of an iteration (the same kernels with the same arguments and
+// buffers every time it runs) replayed as CUDA graphs: the sequence is captured on its
+// first run under a key that fixes all of its arguments, and each later run with that
+// key is one graph launch.  Used for the Chebyshev mass inverses (18 to 35 short
+// kernels per application).  Profiling that times every kernel, a disabled cache, or a
+// stream that cannot be captured runs the sequence kernel by kernel instead (same
+// kernels, same results).
+struct GraphKey {
+    const void *a, *b, *c;
+    int64_t i, j;
+    bool operator==(const GraphKey& o) const { return a == o.a && b == o.b && c == o.c && i == o.i && j == o.j; }
+};
+
+struct GraphCache {
+    struct Entry {
+        GraphKey key;
+        cudaGraphExec_t exec;
+        uint64_t kernels;
+    };
+    std::vector<Entry> entries;
+    bool enabled = true;
+    explicit GraphCache(bool on) : enabled(on) {}
+    GraphCache(const GraphCache&) = delete;
+    GraphCache& operator=(const GraphCache&) = delete;
+    ~GraphCache() {
+        for (Entry& e : entries) cudaGraphExecDestroy(e.exec);
+    }
+    template <class F>
+    bem_status run(const GraphKey& key, cudaStream_t s, F&& body) {
+        if (!enabled || s == nullptr || prof_times_every_kernel()) return body();
+        for (const Entry& e : entries)
+            if (e.key == key) {
+                BEM_CUDA_TRY(cudaGraphLaunch(e.exec, s));
+                count_launch(e.kernels);
+                return BEM_OK;
+            }
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            enabled = false;
+            return body();
+        }
+        g_capturing = 1;
+        const bem_status st = body();
+        g_capturing = 0;
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(s, &g);
+        cudaGraphExec_t ex = nullptr;
+        size_t nodes = 0;
+        const bool ok = st == BEM_OK && ce == cudaSuccess && g != nullptr &&
+                        cudaGraphGetNodes(g, nullptr, &nodes) == cudaSuccess &&
+                        cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        if (!ok) {
+            cudaGetLastError();
+            if (st != BEM_OK) return st;
+            enabled = false;  // capture refused on this stream: launch kernel by kernel
+            return body();
+        }
+        entries.push_back({key, ex, (uint64_t)nodes});
+        BEM_CUDA_TRY(cudaGraphLaunch(ex, s));
+        count_launch(nodes);
+        return BEM_OK;
+    }
+};
+
 struct MassOp {
     MassPair M{};
     double2 *r = nullptr, *dA = nullptr, *dB = nullptr;  // workspaces [R * n]
+    GraphCache* graphs = nullptr;                        // replay the step sequence as a graph
 };
 
 // M^-1 on the four blocks of R columns, Chebyshev on the Jacobi-scaled mass matrices
 bem_status mass_solve(const MassOp& op, const double2* z, double2* y, int R, cudaStream_t s, int steps) {
+    if (op.graphs && !g_capturing) {
+        MassOp eager = op;
+        eager.graphs = nullptr;
+        return op.graphs->run(GraphKey{op.r, z, y, R, steps}, s,
+                              [&]() { return mass_solve(eager, z, y, R, s, steps); });
+    }
     const int64_t n = op.M.n;
     const double theta = 0.5 * (CHEB_BETA + CHEB_ALPHA), delta = 0.5 * (CHEB_BETA - CHEB_ALPHA);
     const double sigma = theta / delta;
-    // small blocks: a step is FP64 work of a few rows per thread, spread over every SM
-    const dim3 grid(blocks_for(n, 64), R);
-    BEM_LAUNCH(k_cheb_init, grid, 64, 0, s, op.M, z, y, op.r, op.dA, 1.0 / theta);
+    // small blocks by default: a step is FP64 work of a few rows per thread, spread over
+    // every SM
+    const int nb = tune_get(TUNE_CHEB, R, n, TuneChoice{64, 0, 0.0}).block;
+    const dim3 grid(blocks_for(n, nb), R);
+    BEM_LAUNCH(k_cheb_init, grid, nb, 0, s, op.M, z, y, op.r, op.dA, 1.0 / theta);
     double rho = 1.0 / sigma;
     double2 *dk = op.dA, *dn = op.dB;
     for (int k = 0; k < steps; ++k) {
         const double rho_n = 1.0 / (2.0 * sigma - rho);
-        BEM_LAUNCH(k_cheb_step, grid, 64, 0, s, op.M, dk, dn, y, op.r, rho_n * rho, 2.0 * rho_n / delta);
+        BEM_LAUNCH(k_cheb_step, grid, nb, 0, s, op.M, dk, dn, y, op.r, rho_n * rho, 2.0 * rho_n / delta);
         rho = rho_n;
         std::swap(dk, dn);
     }
@@ -869,8 +1085,9 @@ bem_status build_csr(const int32_t* key, const int32_t* other, const double* val
     if (nnz > 0)
         BEM_LAUNCH(k_csr_scatter, blocks_for(nnz, 256), 256, 0, s, key, other, val, nnz, start.as<int32_t>(),
                    fill.as<int32_t>(), oc.as<int32_t>(), ov.as<double>());
-    BEM_LAUNCH(k_csr_merge, blocks_for(rows, 128), 128, 0, s, start.as<int32_t>(), rows, oc.as<int32_t>(),
-               ov.as<double>(), cnt.as<int32_t>());
+    if (rows > 0)
+        BEM_LAUNCH(k_csr_merge, (unsigned)rows, 256, 0, s, start.as<int32_t>(), rows, oc.as<int32_t>(), ov.as<double>(),
+               cnt.as<int32_t>());
     BEM_LAUNCH(k_scan, 1, 1024, 0, s, cnt.as<int32_t>(), rows, out.rp.as<int32_t>());
     BEM_LAUNCH(k_csr_compact, blocks_for(rows, 128), 128, 0, s, start.as<int32_t>(), out.rp.as<int32_t>(), rows,
                oc.as<int32_t>(), ov.as<double>(), out.ci.as<int32_t>(), out.v.as<double>());
@@ -1162,6 +1379,68 @@ void fill_blocks_single(BT& Bo, BT& Bh, MT* const m1[4], MT* const m2[4], int oA
     }
 }
 
+// High-contrast systems (Sec. 2.3): every dense product is one of these.  A block row
+// with A2 == nullptr holds one matrix; rows past the used ones are empty (no columns).
+//   own: the unknowns' grid A, two rows of one matrix each applied to one half of x:
+//        Neumann variants (T_A mu; V_A mu), Dirichlet variants (K_A nu; D_A nu);
+//   hat: the other grid B, one row c1 X1 t_0 + c2 X2 t_1 on a pair t of grid-B vectors:
+//        Neumann (T_B, D_B), Dirichlet (V_B, K_B); the second row is empty.
+// m1 = (K_e, D_e, K_i, D_i), m2 = (V_e, T_e, V_i, T_i); oA, oB index the grids in them.
+template <class BT, class MT>
+void fill_blocks_hc(BT& Bo, BT& Bh, MT* const m1[4], MT* const m2[4], int oA, int oB, int64_t NA, int64_t NB,
+                    bool neumann, double c1, double c2) {
+    MT* const KA = m1[oA];
+    MT* const DA = m1[oA + 1];
+    MT* const VA = m2[oA];
+    MT* const TA = m2[oA + 1];
+    MT* const KB = m1[oB];
+    MT* const DB = m1[oB + 1];
+    MT* const VB = m2[oB];
+    MT* const TB = m2[oB + 1];
+    for (int b = 0; b < 4; ++b) {
+        Bo.A1[b] = b == 0 ? (neumann ? TA : KA) : (neumann ? VA : DA);
+        Bo.A2[b] = nullptr;
+        Bo.c1[b] = 1.0; Bo.c2[b] = 0.0;
+        Bo.rows[b] = b < 2 ? NA : 0;
+        Bo.base[b] = b < 2 ? b * NA : 2 * NA;
+        Bo.x1[b] = neumann ? NA : 0; Bo.x2[b] = 0;
+        Bh.A1[b] = neumann ? TB : VB;
+        Bh.A2[b] = b == 0 ? (neumann ? DB : KB) : nullptr;
+        Bh.c1[b] = c1; Bh.c2[b] = c2;
+        Bh.rows[b] = b == 0 ? NB : 0;
+        Bh.base[b] = b == 0 ? 0 : (b == 1 ? NB : 2 * NB);
+        Bh.x1[b] = 0; Bh.x2[b] = NB;
+    }
+}
+
+// One row c1 X1 x_{o1} + c2 X2 x_{o2} (X2 may be null) over pairs of one grid's vectors,
+// the second row empty: the products of the high-contrast data and outputs.
+template <class BT, class MT>
+void fill_blocks_row(BT& B, MT* X1, int64_t o1, double c1, MT* X2, int64_t o2, double c2, int64_t N) {
+    for (int b = 0; b < 4; ++b) {
+        B.A1[b] = X1;
+        B.A2[b] = b == 0 ? X2 : nullptr;
+        B.c1[b] = c1; B.c2[b] = c2;
+        B.rows[b] = b == 0 ? N : 0;
+        B.base[b] = b == 0 ? 0 : (b == 1 ? N : 2 * N);
+        B.x1[b] = o1; B.x2[b] = X2 ? o2 : 0;
+    }
+}
+
+// For the FP64 kernels, which read both matrices of a row in one loop: a row of one
+// matrix reads its matrix twice, the second time with coefficient 0.
+template <class BT>
+BT both_matrices(const BT& B) {
+    BT D = B;
+    for (int b = 0; b < 4; ++b)
+        if (D.A2[b] == nullptr) {
+            D.A2[b] = D.A1[b];
+            D.c2[b] = 0.0;
+            D.x2[b] = D.x1[b];
+        }
+    return D;
+}
+
 template <class BT, class MT>
 void fill_blocks(BT& B, MT* const m1[4], MT* const m2[4], int64_t Ne, int64_t Ni) {
     const double c1[4] = {-1.0, 1.0, -1.0, 1.0};
@@ -1228,15 +1507,9 @@ bem_status selftest_tc(int R, double* rel_err, cudaStream_t s) {
     BEM_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     BEM_TRY(mtf_product_tc(B.A1, B.A2, B.c1, B.c2, B.rows, B.base, B.x1, B.x2, n, R, x.as<double2>(),
                            z1.as<double2>(), work.p, work.bytes, err.as<int>(), s));
-    const unsigned rows_blocks = blocks_for(n * 32, 256);
     for (int c0 = 0; c0 < R; c0 += 8) {
         const int Wd = gemm_width(std::min(8, R - c0));
-        const float2* xc = xf.as<float2>() + c0 * n;
-        double2* zc = z2.as<double2>() + c0 * n;
-        if (Wd == 1) BEM_LAUNCH(k_gemm32<1>, rows_blocks, 256, 0, s, B, n, xc, zc);
-        else if (Wd == 2) BEM_LAUNCH(k_gemm32<2>, rows_blocks, 256, 0, s, B, n, xc, zc);
-        else if (Wd == 4) BEM_LAUNCH(k_gemm32<4>, rows_blocks, 256, 0, s, B, n, xc, zc);
-        else BEM_LAUNCH(k_gemm32<8>, rows_blocks, 256, 0, s, B, n, xc, zc);
+        BEM_TRY(launch_gemm32(Wd, B, n, xf.as<float2>() + c0 * n, z2.as<double2>() + c0 * n, s));
     }
     std::vector<double2> h1((size_t)R * n), h2((size_t)R * n);
     int h_err = 0;
@@ -1258,6 +1531,171 @@ bem_status selftest_tc(int R, double* rel_err, cudaStream_t s) {
     return BEM_OK;
 }
 
+// Autotuner: times the candidate launch shapes of the iteration's kernels on operators
+// of the given grids' sizes (seeded random complex64 blocks; the timing of these
+// bandwidth- and latency-bound kernels does not depend on the values) and the grids'
+// own mass matrices, and records the fastest per (kernel, width, size class):
+//   k_gemm32 for 1, 2, 4, 8 columns: 128, 256 or 512 threads x 2 or 4 loads in flight;
+//   k_gemv_dd: 128, 256 or 512 threads;
+//   Chebyshev mass steps for 1 and 8 columns: 64, 128 or 256 threads;
+//   tensor-core product of n_rhs > 8 columns (batches of up to 64): 1 or 2 K splits.
+// The GPU is first kept busy for a while (clocks up), each candidate runs once untimed,
+// then the candidates are timed round-robin `reps` times, four launches back to back
+// between CUDA events (so that a drift of the clocks affects all alike), and the median
+// counts; the kernel's built-in shape is kept unless another is faster by more than 2 %.
+bem_status autotune_impl(bem_context* ctx, const bem_grid* ge, const bem_grid* gi, int n_rhs, int reps) {
+    cudaStream_t s = ctx->stream;
+    const int64_t Ne = ge->nv, Ni = gi->nv, n = 2 * Ne + 2 * Ni;
+    const int RW = 8 + 7;
+    DevBuf A[8], xf, x, z, xs;
+    for (int m = 0; m < 8; ++m) {
+        const int64_t N = m < 4 ? Ne : Ni;
+        BEM_TRY(A[m].alloc((size_t)N * N * 8, s));
+        BEM_LAUNCH(k_fill_uniform, blocks_for(2 * N * N, 256), 256, 0, s, A[m].as<float>(), 2 * N * N, 5000ull + m,
+                   -1.0f, 1.0f);
+    }
+    Blocks<float2> B{};
+    const float2* m1[4] = {A[1].as<float2>(), A[3].as<float2>(), A[5].as<float2>(), A[7].as<float2>()};
+    const float2* m2[4] = {A[0].as<float2>(), A[2].as<float2>(), A[4].as<float2>(), A[6].as<float2>()};
+    fill_blocks(B, m1, m2, Ne, Ni);
+    const int RT = std::max(RW, 64 + 7);
+    BEM_TRY(xf.alloc((size_t)RT * n * 8, s));
+    BEM_LAUNCH(k_fill_uniform, blocks_for(2 * RT * n, 256), 256, 0, s, xf.as<float>(), 2 * RT * n, 6000ull, -1.0f, 1.0f);
+    BEM_TRY(x.alloc((size_t)RT * n * 16, s));
+    BEM_LAUNCH(k_widen, blocks_for(RT * n, 256), 256, 0, s, xf.as<float2>(), RT * n, x.as<double2>());
+    BEM_TRY(z.alloc((size_t)RT * n * 16, s));
+    BEM_TRY(xs.alloc((size_t)n * 16, s));
+    BEM_LAUNCH(k_split_x, blocks_for(n, 256), 256, 0, s, x.as<double2>(), n, xs.as<float4>());
+    EventTimer ev;
+    // times of the candidates (index 0: the built-in shape), round-robin; returns the
+    // index chosen and its median time
+    auto pick = [&](int count, const std::function<bem_status(int)>& run, double* best_ms) -> int {
+        std::vector<std::vector<float>> t(count);
+        for (int c = 0; c < count; ++c)
+            if (run(c) != BEM_OK) return -1;
+        // each sample: 4 launches back to back (the steady state of an iteration, not a
+        // launch after an idle GPU), per launch
+        for (int r = 0; r < reps; ++r)
+            for (int c = 0; c < count; ++c) {
+                if (cudaEventRecord(ev.a, s) != cudaSuccess) return -1;
+                for (int k = 0; k < 4; ++k)
+                    if (run(c) != BEM_OK) return -1;
+                if (cudaEventRecord(ev.b, s) != cudaSuccess) return -1;
+                t[c].push_back(ev.ms() / 4.0f);
+            }
+        std::vector<double> med(count);
+        for (int c = 0; c < count; ++c) {
+            std::sort(t[c].begin(), t[c].end());
+            med[c] = t[c][reps / 2];
+        }
+        int best = 0;
+        for (int c = 1; c < count; ++c)
+            if (med[c] < med[best]) best = c;
+        if (med[best] > 0.98 * med[0]) best = 0;
+        *best_ms = med[best];
+        return best;
+    };
+    auto tune_failed = []() {
+        set_error("autotune: a candidate launch failed");
+        return BEM_E_CUDA;
+    };
+    // keep the GPU busy for ~0.3 s before measuring
+    {
+        const TuneChoice d = gemm32_default(1);
+        const auto t0 = now_seconds();
+        while (now_seconds() - t0 < 0.3) {
+            for (int k = 0; k < 8; ++k) BEM_TRY(launch_gemm32(1, B, n, xf.as<float2>(), z.as<double2>(), s, &d));
+            BEM_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+    }
+    // dense products
+    for (int W : {1, 2, 4, 8}) {
+        std::vector<TuneChoice> cand{gemm32_default(W)};
+        for (int block : {128, 256, 512})
+            for (int H : {2, 4})
+                if (!(block == cand[0].block && H == cand[0].variant)) cand.push_back(TuneChoice{block, H, 0.0});
+        double ms = 0.0;
+        const int b = pick((int)cand.size(), [&](int c) {
+            return launch_gemm32(W, B, n, xf.as<float2>(), z.as<double2>(), s, &cand[c]);
+        }, &ms);
+        if (b < 0) return tune_failed();
+        tune_put(TUNE_GEMM32, W, n, TuneChoice{cand[b].block, cand[b].variant, ms});
+    }
+    {
+        const std::vector<TuneChoice> cand{{256, 0, 0.0}, {128, 0, 0.0}, {512, 0, 0.0}};
+        double ms = 0.0;
+        const int b = pick(3, [&](int c) { return launch_gemv_dd(B, n, xs.as<float4>(), z.as<double2>(), s, &cand[c]); },
+                           &ms);
+        if (b < 0) return tune_failed();
+        tune_put(TUNE_GEMV_DD, 1, n, TuneChoice{cand[b].block, 0, ms});
+    }
+    // Chebyshev mass steps on the grids' own mass matrices (MTF layout: both grids)
+    {
+        DevBuf mve, mvi, dve, dvi, wr, wa, wb, y;
+        BEM_TRY(mve.alloc(ge->m_nnz * 8, s));
+        BEM_TRY(mvi.alloc(gi->m_nnz * 8, s));
+        BEM_TRY(dve.alloc(Ne * 8, s));
+        BEM_TRY(dvi.alloc(Ni * 8, s));
+        BEM_TRY(mass_values(ge, mve.as<double>(), s));
+        BEM_TRY(mass_values(gi, mvi.as<double>(), s));
+        BEM_TRY(mass_inverse_diag(ge, mve.as<double>(), dve.as<double>(), s));
+        BEM_TRY(mass_inverse_diag(gi, mvi.as<double>(), dvi.as<double>(), s));
+        MassEll ell_e, ell_i;
+        BEM_TRY(ell_e.build(ge, mve.as<double>(), s));
+        BEM_TRY(ell_i.build(gi, mvi.as<double>(), s));
+        for (DevBuf* b : {&wr, &wa, &wb, &y}) BEM_TRY(b->alloc((size_t)8 * n * 16, s));
+        MassOp op;
+        op.M.ci[0] = ell_e.ci.as<int32_t>(); op.M.v[0] = ell_e.v.as<double>(); op.M.W[0] = ell_e.W;
+        op.M.dinv[0] = dve.as<double>();
+        op.M.ci[1] = ell_i.ci.as<int32_t>(); op.M.v[1] = ell_i.v.as<double>(); op.M.W[1] = ell_i.W;
+        op.M.dinv[1] = dvi.as<double>();
+        op.M.Ne = Ne; op.M.Ni = Ni; op.M.n = n;
+        op.r = wr.as<double2>(); op.dA = wa.as<double2>(); op.dB = wb.as<double2>();
+        for (int R : {1, 8}) {
+            const int blocks[3] = {64, 128, 256};
+            double ms = 0.0;
+            const int b = pick(3, [&](int c) {
+                tune_put(TUNE_CHEB, R, n, TuneChoice{blocks[c], 0, 0.0});
+                return mass_solve(op, x.as<double2>(), y.as<double2>(), R, s, CHEB_STEPS);
+            }, &ms);
+            if (b < 0) return tune_failed();
+            tune_put(TUNE_CHEB, R, n, TuneChoice{blocks[b], 0, ms});
+        }
+    }
+    // tensor-core product
+    if (n_rhs > 8) {
+        const int R = std::min(n_rhs, 64);
+        const int RP = tc_padded_columns(R);
+        DevBuf work, err;
+        BEM_TRY(work.alloc(tc_workspace_bytes(B.rows, RP), s));
+        BEM_TRY(err.alloc(sizeof(int), s));
+        BEM_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+        int sms = 0, dev = 0;
+        BEM_CUDA_TRY(cudaGetDevice(&dev));
+        BEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int64_t tiles = 0;
+        for (int b = 0; b < 4; ++b) tiles += (B.rows[b] + 127) / 128;
+        const int dflt = tiles < sms ? 2 : 1;
+        const int ks[2] = {dflt, 3 - dflt};
+        double ms = 0.0;
+        const int b = pick(2, [&](int c) {
+            tune_put(TUNE_GEMM_TC, RP, n, TuneChoice{0, ks[c], 0.0});
+            return mtf_product_tc(B.A1, B.A2, B.c1, B.c2, B.rows, B.base, B.x1, B.x2, n, R, x.as<double2>(),
+                                  z.as<double2>(), work.p, work.bytes, err.as<int>(), s);
+        }, &ms);
+        if (b < 0) return tune_failed();
+        tune_put(TUNE_GEMM_TC, RP, n, TuneChoice{0, ks[b], ms});
+        int h_err = 0;
+        BEM_CUDA_TRY(cudaMemcpy(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (h_err) {
+            set_error("tensor-core product: an mbarrier wait timed out");
+            return BEM_E_INTERNAL;
+        }
+    }
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    return BEM_OK;
+}
+
 bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const bem_grid* gi, bem_c128 k_int,
                                    bem_c128 k_ext, double rho_ratio, const bem_incident* inc,
                                    const bem_solve_opts* o, bem_c128* v_ext, bem_c128* w_ext, bem_c128* v_int,
@@ -1270,7 +1708,10 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     // potentials mapped by M_B^-1 P_BA)
     const int form = o->formulation;
     const bool st = form != BEM_FORM_MTF;
-    const bool st_int = form == BEM_FORM_PMCHWT_INT || form == BEM_FORM_MULLER_INT;
+    const bool hc = form >= BEM_FORM_HC_EXT_NEU;  // high-contrast systems (Sec. 2.3)
+    const bool hc_neu = form == BEM_FORM_HC_EXT_NEU || form == BEM_FORM_HC_INT_NEU;
+    const bool st_int = form == BEM_FORM_PMCHWT_INT || form == BEM_FORM_MULLER_INT || form == BEM_FORM_HC_INT_NEU ||
+                        form == BEM_FORM_HC_INT_DIR;
     const bool muller = form == BEM_FORM_MULLER || form == BEM_FORM_MULLER_INT;
     const int64_t Ne = ge->nv, Ni = gi->nv;
     const int64_t NA = st_int ? Ni : Ne, NB = st_int ? Ne : Ni, nB = 2 * NB;
@@ -1289,6 +1730,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     };
     BEM_TRY(stop());
     EventTimer t_asm, t_mor, t_sol;
+    GraphCache graphs(o->cuda_graphs != 0);
     // ---- operators on both grids --------------------------------------------------
     const size_t esz = mixed ? 8 : 16;
     const size_t be = (size_t)Ne * Ne * esz, bi = (size_t)Ni * Ni * esz;
@@ -1336,7 +1778,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     // CUDA-core products take the columns in groups of w <= 8 at width gemm_width(w),
     // reading and writing up to 7 spare (in-bounds) columns past the batch
     const int RW = RB + 7;
-    const bool tc_batches = use_tc && RB > 8;
+    const bool tc_batches = use_tc && RB > 8 && !hc;  // high-contrast products: CUDA cores
     // Single-column inner solves of the refinement: the products run in double-float
     // arithmetic while the inner residual is above DD_SWITCH of its right-hand side and
     // in FP32 after it.  GMRES tolerates product errors that grow as the residual falls
@@ -1366,6 +1808,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     // (vectors of its two potentials): single-trace systems use M_A^-1 (mop) and M_B^-1 (mopB)
     mop.M.Ne = st_int ? 0 : Ne; mop.M.Ni = st && !st_int ? 0 : Ni; mop.M.n = n;
     mop.r = wr.as<double2>(); mop.dA = wa.as<double2>(); mop.dB = wb.as<double2>();
+    mop.graphs = &graphs;
     // single-trace: the grid-B vectors of a product (tb1: M_B^-1 P_BA x, then M_B^-1 of the
     // grid-B product; tb2, tb3: input and output of the grid-B product, which reads and
     // writes up to 7 spare columns)
@@ -1383,6 +1826,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
         mopB.M = mop.M;
         mopB.M.Ne = st_int ? Ne : 0; mopB.M.Ni = st_int ? 0 : Ni; mopB.M.n = nB;
         mopB.r = wrb.as<double2>(); mopB.dA = wab.as<double2>(); mopB.dB = wbb.as<double2>();
+        mopB.graphs = &graphs;
     }
     // P_BA (rows on grid B) and P_AB = P_BA^T: P_ie and P_ei for the exterior variants
     const CsrBuf& csr_ba = st_int ? csr_t : csr_p;
@@ -1393,6 +1837,13 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     const double cv = st_int ? 1.0 / rho_ratio : rho_ratio, cd = st_int ? rho_ratio : 1.0 / rho_ratio;
     const double sA = form == BEM_FORM_MULLER_INT ? -1.0 : 1.0, sB = form == BEM_FORM_MULLER ? -1.0 : 1.0;
     const int oA = st_int ? 2 : 0, oB = st_int ? 0 : 2;
+    // high-contrast: coefficients of the grid-B row (X1 t_0, X2 t_1), r = rho_i / rho_e:
+    // exterior Neumann -T_i, -D_i / r; interior Neumann T_e, r D_e; exterior Dirichlet
+    // -r V_i, K_i; interior Dirichlet V_e / r, -K_e
+    const double hc_c1 = form == BEM_FORM_HC_EXT_NEU ? -1.0 : form == BEM_FORM_HC_INT_NEU ? 1.0
+                       : form == BEM_FORM_HC_EXT_DIR ? -rho_ratio : 1.0 / rho_ratio;
+    const double hc_c2 = form == BEM_FORM_HC_EXT_NEU ? -1.0 / rho_ratio : form == BEM_FORM_HC_INT_NEU ? rho_ratio
+                       : form == BEM_FORM_HC_EXT_DIR ? 1.0 : -1.0;
     TransferCsr top;
     const double sgn = o->mtf_variant == BEM_MTF_PRINTED ? -1.0 : 1.0;
     top.prp = csr_p.rp.as<int32_t>(); top.pci = csr_p.ci.as<int32_t>(); top.pv = csr_p.v.as<double>();
@@ -1405,14 +1856,42 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     double2* z = wz.as<double2>();
     // dense blocks: the four block rows of the multiple-traces system, or for the PMCHWT
     // the two exterior block rows (B*) and the two scaled interior ones (Bi*)
-    Blocks<double2> B64{}, Bh64{};
-    Blocks<float2> B32{}, Bh32{};
+    Blocks<double2> B64{}, Bh64{}, Br64{}, Bo64{};
+    Blocks<float2> B32{}, Bh32{}, Br32{}, Bo32{};
+    // high-contrast data (Br, a row on grid B) and outputs (Bo, a row on grid A), with the
+    // matrices m1 = (K_e, D_e, K_i, D_i), m2 = (V_e, T_e, V_i, T_i) of the working storage
+    auto fill_hc_extra = [&](auto& Br, auto& Bo, auto* const* m1, auto* const* m2) {
+        const double r = rho_ratio;
+        switch (form) {
+            case BEM_FORM_HC_EXT_NEU:  // (1/r) D_i t_0;  -V_e x_1
+                fill_blocks_row(Br, m1[3], 0, 1.0 / r, decltype(m1[0])(nullptr), 0, 0.0, NB);
+                fill_blocks_row(Bo, m2[0], NA, -1.0, decltype(m1[0])(nullptr), 0, 0.0, NA);
+                break;
+            case BEM_FORM_HC_EXT_DIR:  // r V_i t_0;  -D_e x_0
+                fill_blocks_row(Br, m2[2], 0, r, decltype(m1[0])(nullptr), 0, 0.0, NB);
+                fill_blocks_row(Bo, m1[1], 0, -1.0, decltype(m1[0])(nullptr), 0, 0.0, NA);
+                break;
+            case BEM_FORM_HC_INT_NEU:  // D_e t_0 + T_e t_1;  V_i x_1
+                fill_blocks_row(Br, m1[1], 0, 1.0, m2[1], NB, 1.0, NB);
+                fill_blocks_row(Bo, m2[2], NA, 1.0, decltype(m1[0])(nullptr), 0, 0.0, NA);
+                break;
+            default:  // interior Dirichlet: V_e t_1 - K_e t_0;  D_i x_0
+                fill_blocks_row(Br, m2[0], NB, 1.0, m1[0], 0, -1.0, NB);
+                fill_blocks_row(Bo, m1[3], 0, 1.0, decltype(m1[0])(nullptr), 0, 0.0, NA);
+                break;
+        }
+    };
     if (mixed) {
         BEM_TRY(x32.alloc((size_t)RW * n * 8, s));
         BEM_CUDA_TRY(cudaMemsetAsync(x32.p, 0, x32.bytes, s));
         const float2* m1[4] = {M[1].as<float2>(), M[3].as<float2>(), M[5].as<float2>(), M[7].as<float2>()};
         const float2* m2[4] = {M[0].as<float2>(), M[2].as<float2>(), M[4].as<float2>(), M[6].as<float2>()};
-        if (st) {
+        if (hc) {
+            fill_blocks_hc(B32, Bh32, m1, m2, oA, oB, NA, NB, hc_neu, hc_c1, hc_c2);
+            fill_hc_extra(Br32, Bo32, m1, m2);
+            BEM_TRY(x32b.alloc((size_t)RW * nB * 8, s));
+            BEM_CUDA_TRY(cudaMemsetAsync(x32b.p, 0, x32b.bytes, s));
+        } else if (st) {
             fill_blocks_single(B32, Bh32, m1, m2, oA, oB, NA, NB, sA, sB, cv, cd);
             BEM_TRY(x32b.alloc((size_t)RW * nB * 8, s));
             BEM_CUDA_TRY(cudaMemsetAsync(x32b.p, 0, x32b.bytes, s));
@@ -1429,7 +1908,11 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     } else {
         const double2* m1[4] = {M[1].as<double2>(), M[3].as<double2>(), M[5].as<double2>(), M[7].as<double2>()};
         const double2* m2[4] = {M[0].as<double2>(), M[2].as<double2>(), M[4].as<double2>(), M[6].as<double2>()};
-        if (st) fill_blocks_single(B64, Bh64, m1, m2, oA, oB, NA, NB, sA, sB, cv, cd);
+        if (hc) {
+            fill_blocks_hc(B64, Bh64, m1, m2, oA, oB, NA, NB, hc_neu, hc_c1, hc_c2);
+            fill_hc_extra(Br64, Bo64, m1, m2);
+        }
+        else if (st) fill_blocks_single(B64, Bh64, m1, m2, oA, oB, NA, NB, sA, sB, cv, cd);
         else fill_blocks(B64, m1, m2, Ne, Ni);
     }
     // zo = dense blocks (b32 or b64) of nn rows applied to R columns xin, in the working
@@ -1442,26 +1925,23 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                                   tcw.p, tcw.bytes, tcerr.as<int>(), s);
         if (mixed && R == 1 && dd_now()) {
             BEM_LAUNCH(k_split_x, blocks_for(nn, 256), 256, 0, s, xin, nn, xsplit.as<float4>());
-            BEM_LAUNCH(k_gemv_dd, rows_blocks, 256, 0, s, b32, nn, xsplit.as<float4>(), zo);
+            BEM_TRY(launch_gemv_dd(b32, nn, xsplit.as<float4>(), zo, s));
             return BEM_OK;
         }
         if (mixed)
             BEM_LAUNCH(k_to_c64, blocks_for((int64_t)R * nn, 256), 256, 0, s, xin, (int64_t)R * nn, xw);
+        const Blocks<double2> d64 = both_matrices(b64);
         for (int c0 = 0; c0 < R; c0 += 8) {
             const int Wd = gemm_width(std::min(8, R - c0));
             double2* zc = zo + (int64_t)c0 * nn;
             if (mixed) {
-                const float2* xc = xw + (int64_t)c0 * nn;
-                if (Wd == 1) BEM_LAUNCH(k_gemm32<1>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
-                else if (Wd == 2) BEM_LAUNCH(k_gemm32<2>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
-                else if (Wd == 4) BEM_LAUNCH(k_gemm32<4>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
-                else BEM_LAUNCH(k_gemm32<8>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
+                BEM_TRY(launch_gemm32(Wd, b32, nn, xw + (int64_t)c0 * nn, zc, s));
             } else {
                 const double2* xc = xin + (int64_t)c0 * nn;
-                if (Wd == 1) BEM_LAUNCH(k_gemm64<1>, rows_blocks, 256, 0, s, b64, nn, xc, zc);
-                else if (Wd == 2) BEM_LAUNCH(k_gemm64<2>, rows_blocks, 256, 0, s, b64, nn, xc, zc);
-                else if (Wd == 4) BEM_LAUNCH(k_gemm64<4>, rows_blocks, 256, 0, s, b64, nn, xc, zc);
-                else BEM_LAUNCH(k_gemm64<8>, rows_blocks, 256, 0, s, b64, nn, xc, zc);
+                if (Wd == 1) BEM_LAUNCH(k_gemm64<1>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
+                else if (Wd == 2) BEM_LAUNCH(k_gemm64<2>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
+                else if (Wd == 4) BEM_LAUNCH(k_gemm64<4>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
+                else BEM_LAUNCH(k_gemm64<8>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
             }
         }
         return BEM_OK;
@@ -1471,14 +1951,15 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                             const double2* xin, double2* zo, int R) -> bem_status {
         if (!mixed) return gemm_work_on(b32, b64, nn, xw, xin, zo, R);
         const unsigned rows_blocks = blocks_for(nn * 32, 256);
+        const Blocks<float2> d32 = both_matrices(b32);
         for (int c0 = 0; c0 < R; c0 += 8) {
             const int Wd = gemm_width(std::min(8, R - c0));
             const double2* xc = xin + (int64_t)c0 * nn;
             double2* zc = zo + (int64_t)c0 * nn;
-            if (Wd == 1) BEM_LAUNCH(k_gemm_c64_f64<1>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
-            else if (Wd == 2) BEM_LAUNCH(k_gemm_c64_f64<2>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
-            else if (Wd == 4) BEM_LAUNCH(k_gemm_c64_f64<4>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
-            else BEM_LAUNCH(k_gemm_c64_f64<8>, rows_blocks, 256, 0, s, b32, nn, xc, zc);
+            if (Wd == 1) BEM_LAUNCH(k_gemm_c64_f64<1>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
+            else if (Wd == 2) BEM_LAUNCH(k_gemm_c64_f64<2>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
+            else if (Wd == 4) BEM_LAUNCH(k_gemm_c64_f64<4>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
+            else BEM_LAUNCH(k_gemm_c64_f64<8>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
         }
         return BEM_OK;
     };
@@ -1491,26 +1972,86 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
         };
         BEM_TRY(prod(B32, B64, n, x32.as<float2>(), xin, z));
         BEM_LAUNCH(k_csr_pair, dim3(blocks_for(nB, 64), R), 64, 0, s, csr_ba.rp.as<int32_t>(),
-                   csr_ba.ci.as<int32_t>(), csr_ba.v.as<double>(), NB, NA, xin, n, tb1.as<double2>(), nB, 1.0, 1.0, 0);
+                   csr_ba.ci.as<int32_t>(), csr_ba.v.as<double>(), NB, xin, xin + NA, n, tb1.as<double2>(), nB, 1.0,
+                   1.0, 0);
         BEM_TRY(mass_solve(mopB, tb1.as<double2>(), tb2.as<double2>(), R, s, steps));
         BEM_TRY(prod(Bh32, Bh64, nB, x32b.as<float2>(), tb2.as<double2>(), tb3.as<double2>()));
         BEM_TRY(mass_solve(mopB, tb3.as<double2>(), tb1.as<double2>(), R, s, steps));
         BEM_LAUNCH(k_csr_pair, dim3(blocks_for(n, 64), R), 64, 0, s, csr_ab.rp.as<int32_t>(), csr_ab.ci.as<int32_t>(),
-                   csr_ab.v.as<double>(), NA, NB, tb1.as<double2>(), nB, z, n, 1.0, 1.0, 1);
+                   csr_ab.v.as<double>(), NA, tb1.as<double2>(), tb1.as<double2>() + NB, nB, z, n, 1.0, 1.0, 1);
         BEM_TRY(mass_solve(mop, z, yout, R, s, steps));
         if (muller)
             BEM_LAUNCH(k_acc, blocks_for((int64_t)R * n, 256), 256, 0, s, yout, xin, (int64_t)R * n);
         return BEM_OK;
     };
+    // high-contrast product (Sec. 2.3; the strong form of the system, left-multiplied by
+    // M_A^-1), for x = (x_0, x_1) on grid A:
+    //   z = own rows (T_A x_1; V_A x_1) or (K_A x_0; D_A x_0);  w = M_A^-1 z
+    //   t = M_B^-1 P_BA (x_0; w_1) [Neumann] or (w_1; x_1) [Dirichlet]
+    //   h = M_B^-1 (c1 X1 t_0 + c2 X2 t_1);  u = M_A^-1 P_AB h into half 0 [Neumann] or 1
+    //   y = the formulation's combination of x, u and w (hc_y)
+    DevBuf hw, hz2, hu, hfp, hmf;
+    if (hc) {
+        BEM_TRY(hw.alloc(RB * colb, s));
+        BEM_TRY(hz2.alloc(RB * colb, s));
+        BEM_TRY(hu.alloc(RB * colb, s));
+        BEM_TRY(hfp.alloc((size_t)RB * 2 * Ne * 16, s));  // -(f; g), exterior grid
+        BEM_TRY(hmf.alloc((size_t)RB * 2 * Ne * 16, s));  // M_e^-1 of it (exterior variants)
+    }
+    PairCoef hc_y{};
+    {
+        // sources (x_0, x_1, u_0, u_1, w_0, w_1) of y_0 (first six) and y_1
+        const double en[12] = {0.5, 0, 1, 0, 0, 0, 1, 0.5, 0, 0, -1, 0};   // exterior Neumann
+        const double in[12] = {0.5, 0, 1, 0, 0, 0, -1, 0.5, 0, 0, 1, 0};   // interior Neumann
+        const double ed[12] = {0.5, 1, 0, 0, 1, 0, 0, 0.5, 0, 1, 0, 0};    // exterior Dirichlet
+        const double id[12] = {0.5, -1, 0, 0, -1, 0, 0, 0.5, 0, 1, 0, 0};  // interior Dirichlet
+        const double* c = form == BEM_FORM_HC_EXT_NEU ? en : form == BEM_FORM_HC_INT_NEU ? in
+                        : form == BEM_FORM_HC_EXT_DIR ? ed : id;
+        for (int k = 0; k < 12; ++k) hc_y.c[k] = c[k];
+    }
+    auto pair_lin = [&](double2* y, const double2* x, const double2* u, const double2* w, int64_t N, int R,
+                        const PairCoef& C) -> bem_status {
+        BEM_LAUNCH(k_pair_lin, dim3(blocks_for(2 * N, 256), R), 256, 0, s, y, x, u, w, N, 2 * N, C);
+        return BEM_OK;
+    };
+    auto csr_pair = [&](const CsrBuf& P, int64_t rows, const double2* x0, const double2* x1, int64_t nx, double2* zo,
+                        int64_t nz, double c0, double c1, int R) -> bem_status {
+        BEM_LAUNCH(k_csr_pair, dim3(blocks_for(2 * rows, 64), R), 64, 0, s, P.rp.as<int32_t>(), P.ci.as<int32_t>(),
+                   P.v.as<double>(), rows, x0, x1, nx, zo, nz, c0, c1, 0);
+        return BEM_OK;
+    };
+    auto apply_hc = [&](bool fp64, const double2* xin, double2* yout, int R, int steps) -> bem_status {
+        auto prod = [&](const Blocks<float2>& b32, const Blocks<double2>& b64, int64_t nn, float2* xw,
+                        const double2* xi, double2* zo) -> bem_status {
+            return fp64 ? gemm_fp64_on(b32, b64, nn, xw, xi, zo, R) : gemm_work_on(b32, b64, nn, xw, xi, zo, R);
+        };
+        double2* w = hw.as<double2>();
+        BEM_TRY(prod(B32, B64, n, x32.as<float2>(), xin, z));
+        BEM_TRY(mass_solve(mop, z, w, R, s, steps));
+        if (hc_neu) BEM_TRY(csr_pair(csr_ba, NB, xin, w + NA, n, tb1.as<double2>(), nB, 1.0, 1.0, R));
+        else BEM_TRY(csr_pair(csr_ba, NB, w + NA, xin + NA, n, tb1.as<double2>(), nB, 1.0, 1.0, R));
+        BEM_TRY(mass_solve(mopB, tb1.as<double2>(), tb2.as<double2>(), R, s, steps));
+        BEM_TRY(prod(Bh32, Bh64, nB, x32b.as<float2>(), tb2.as<double2>(), tb3.as<double2>()));
+        BEM_TRY(mass_solve(mopB, tb3.as<double2>(), tb1.as<double2>(), R, s, steps));
+        // tb1 = (M_B^-1 h; 0): P_AB of its first half into half 0 (Neumann) or 1 (Dirichlet)
+        const double2* t0 = tb1.as<double2>();
+        const double2* t1 = tb1.as<double2>() + NB;
+        if (hc_neu) BEM_TRY(csr_pair(csr_ab, NA, t0, t1, nB, hz2.as<double2>(), n, 1.0, 0.0, R));
+        else BEM_TRY(csr_pair(csr_ab, NA, t1, t0, nB, hz2.as<double2>(), n, 0.0, 1.0, R));
+        BEM_TRY(mass_solve(mop, hz2.as<double2>(), hu.as<double2>(), R, s, steps));
+        return pair_lin(yout, xin, hu.as<double2>(), w, NA, R, hc_y);
+    };
     // S A x in the working precision, and with FP64 arithmetic on the stored matrices
     Apply apply_work = [&](const double2* xin, double2* yout, int R) -> bem_status {
         const int steps = !mixed ? CHEB_STEPS : (R == 1 && dd_now()) ? CHEB_STEPS_DD : CHEB_STEPS_INNER;
+        if (hc) return apply_hc(false, xin, yout, R, steps);
         if (st) return apply_single(false, xin, yout, R, steps);
         BEM_TRY(gemm_work_on(B32, B64, n, x32.as<float2>(), xin, z, R));
         BEM_TRY(transfer_add(top, R, xin, z, s));
         return mass_solve(mop, z, yout, R, s, steps);
     };
     Apply apply_fp64 = [&](const double2* xin, double2* yout, int R) -> bem_status {
+        if (hc) return apply_hc(true, xin, yout, R, CHEB_STEPS);
         if (st) return apply_single(true, xin, yout, R, CHEB_STEPS);
         BEM_TRY(gemm_fp64_on(B32, B64, n, x32.as<float2>(), xin, z, R));
         BEM_TRY(transfer_add(top, R, xin, z, s));
@@ -1550,14 +2091,49 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
         BEM_LAUNCH(k_plane_wave, dim3(blocks_for(ge->nt, 128), R), 128, 0, s, ge->rec.as<TriRec>(),
                    ge->tri.as<int32_t>(), ge->nt, k_ext.re, k_ext.im, wave.as<double>() + 2 * RB,
                    wave.as<double2>(), Ne, fvec.as<double2>(), gvec.as<double2>());
-        if (st_int) {
+        if (hc) {
+            // high-contrast data (weak form), from F = -(f; g):
+            //   exterior Neumann ((1/r) D^_i M_e^-1 f; g), Dirichlet (f; r V^_i M_e^-1 g);
+            //   interior Neumann (r P_ie M_e^-1 (D_e M_e^-1 f + g/2 + T_e M_e^-1 g); 0),
+            //   Dirichlet (0; P_ie M_e^-1 (V_e M_e^-1 g + f/2 - K_e M_e^-1 f))
+            const MassOp& E = st_int ? mopB : mop;  // the exterior grid's pair
+            double2* F = hfp.as<double2>();
+            double2* mF = st_int ? tb2.as<double2>() : hmf.as<double2>();
+            BEM_LAUNCH(k_rhs_pack, dim3(blocks_for(2 * Ne, 256), R), 256, 0, s, fvec.as<double2>(),
+                       gvec.as<double2>(), Ne, 2 * Ne, F);
+            BEM_TRY(mass_solve(E, F, mF, R, s, CHEB_STEPS));
+            if (!st_int) {
+                const double2* src = hc_neu ? mF : mF + Ne;
+                BEM_TRY(csr_pair(csr_p, Ni, src, src, 2 * Ne, tb1.as<double2>(), nB, 1.0, 0.0, R));
+                BEM_TRY(mass_solve(mopB, tb1.as<double2>(), tb2.as<double2>(), R, s, CHEB_STEPS));
+                BEM_TRY(gemm_fp64_on(Br32, Br64, nB, x32b.as<float2>(), tb2.as<double2>(), tb3.as<double2>(), R));
+                BEM_TRY(mass_solve(mopB, tb3.as<double2>(), tb1.as<double2>(), R, s, CHEB_STEPS));
+                BEM_TRY(csr_pair(csr_t, Ne, tb1.as<double2>(), tb1.as<double2>(), nB, hz2.as<double2>(), n, 1.0, 0.0,
+                                 R));
+                PairCoef C{};  // sources (x = hat part, u = F): negated, F = -(f; g)
+                if (hc_neu) { C.c[0] = -1.0; C.c[6 + 3] = -1.0; }
+                else { C.c[2] = -1.0; C.c[6 + 0] = -1.0; }
+                BEM_TRY(pair_lin(bvec.as<double2>(), hz2.as<double2>(), F, F, Ne, R, C));
+            } else {
+                BEM_TRY(gemm_fp64_on(Br32, Br64, nB, x32b.as<float2>(), mF, tb3.as<double2>(), R));
+                PairCoef C{};  // (x = product, u = F): x_0 + F_1 / 2 (Neumann) or x_0 + F_0 / 2
+                C.c[0] = 1.0;
+                C.c[hc_neu ? 3 : 2] = 0.5;
+                BEM_TRY(pair_lin(tb1.as<double2>(), tb3.as<double2>(), F, F, Ne, R, C));
+                BEM_TRY(mass_solve(mopB, tb1.as<double2>(), tb2.as<double2>(), R, s, CHEB_STEPS));
+                const double2* t0 = tb2.as<double2>();
+                const double2* t1 = tb2.as<double2>() + Ne;
+                if (hc_neu) BEM_TRY(csr_pair(csr_p, Ni, t0, t1, nB, bvec.as<double2>(), n, -rho_ratio, 0.0, R));
+                else BEM_TRY(csr_pair(csr_p, Ni, t1, t0, nB, bvec.as<double2>(), n, 0.0, -1.0, R));
+            }
+        } else if (st_int) {
             // interior variants: [P_ie M_e^-1 f; (rho_i / rho_e) P_ie M_e^-1 g]
             BEM_LAUNCH(k_rhs_pack, dim3(blocks_for(nB, 256), R), 256, 0, s, fvec.as<double2>(), gvec.as<double2>(),
                        Ne, nB, tb1.as<double2>());
             BEM_TRY(mass_solve(mopB, tb1.as<double2>(), tb2.as<double2>(), R, s, CHEB_STEPS));
             BEM_LAUNCH(k_csr_pair, dim3(blocks_for(n, 64), R), 64, 0, s, csr_ab.rp.as<int32_t>(),
-                       csr_ab.ci.as<int32_t>(), csr_ab.v.as<double>(), NA, NB, tb2.as<double2>(), nB,
-                       bvec.as<double2>(), n, -1.0, -rho_ratio, 0);
+                       csr_ab.ci.as<int32_t>(), csr_ab.v.as<double>(), NA, tb2.as<double2>(), tb2.as<double2>() + NB,
+                       nB, bvec.as<double2>(), n, -1.0, -rho_ratio, 0);
         } else {
             BEM_LAUNCH(k_rhs_pack, dim3(blocks_for(n, 256), R), 256, 0, s, fvec.as<double2>(), gvec.as<double2>(),
                        Ne, n, bvec.as<double2>());
@@ -1622,17 +2198,42 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
             if (!conv) result = BEM_E_NOT_CONVERGED;
         }
         const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        const double2* trace_src = xsol.as<double2>();
+        if (hc) {
+            // the unknowns' grid traces from the representation formula:
+            //   exterior Neumann (M_e^-1 (f + V_e mu) negated; -a), Dirichlet (-b; -M_e^-1 (g + D_e nu)),
+            //   interior Neumann (M_i^-1 V_i mu; a), Dirichlet (b; M_i^-1 D_i nu)
+            BEM_TRY(gemm_fp64_on(Bo32, Bo64, n, x32.as<float2>(), xsol.as<double2>(), z, R));
+            const double2* zin = z;
+            if (!st_int) {
+                PairCoef C{};  // z_0 + F_0 (Neumann) or z_0 + F_1, F = -(f; g)
+                C.c[0] = 1.0;
+                C.c[hc_neu ? 2 : 3] = 1.0;
+                BEM_TRY(pair_lin(hz2.as<double2>(), z, hfp.as<double2>(), hfp.as<double2>(), NA, R, C));
+                zin = hz2.as<double2>();
+            }
+            BEM_TRY(mass_solve(mop, zin, hu.as<double2>(), R, s, CHEB_STEPS));
+            PairCoef C{};  // sources (x = unknowns, u = M_A^-1 part)
+            switch (form) {
+                case BEM_FORM_HC_EXT_NEU: C.c[2] = 1.0; C.c[6 + 0] = -1.0; break;
+                case BEM_FORM_HC_EXT_DIR: C.c[1] = -1.0; C.c[6 + 2] = 1.0; break;
+                case BEM_FORM_HC_INT_NEU: C.c[2] = 1.0; C.c[6 + 0] = 1.0; break;
+                default: C.c[1] = 1.0; C.c[6 + 2] = 1.0; break;
+            }
+            BEM_TRY(pair_lin(hw.as<double2>(), xsol.as<double2>(), hu.as<double2>(), hu.as<double2>(), NA, R, C));
+            trace_src = hw.as<double2>();
+        }
         if (st) {
             // the other grid's potentials from the transmission conditions tested on it:
             // v_i = -M_i^-1 P_ie v_e, w_i = -(rho_i / rho_e) M_i^-1 P_ie w_e (exterior
             // variants); v_e = -M_e^-1 P_ei v_i, w_e = -(rho_e / rho_i) M_e^-1 P_ei w_i
             BEM_LAUNCH(k_csr_pair, dim3(blocks_for(nB, 64), R), 64, 0, s, csr_ba.rp.as<int32_t>(),
-                       csr_ba.ci.as<int32_t>(), csr_ba.v.as<double>(), NB, NA, xsol.as<double2>(), n,
+                       csr_ba.ci.as<int32_t>(), csr_ba.v.as<double>(), NB, trace_src, trace_src + NA, n,
                        tb1.as<double2>(), nB, -1.0, st_int ? -1.0 / rho_ratio : -rho_ratio, 0);
             BEM_TRY(mass_solve(mopB, tb1.as<double2>(), tb2.as<double2>(), R, s, CHEB_STEPS));
         }
         for (int r = 0; r < R; ++r) {
-            const double2* X = xsol.as<double2>() + (int64_t)r * n;
+            const double2* X = trace_src + (int64_t)r * n;
             const double2* XB = st ? tb2.as<double2>() + (int64_t)r * nB : nullptr;
             const double2* XE = !st ? X : st_int ? XB : X;
             const double2* XI = !st ? X + 2 * Ne : st_int ? X : XB;
@@ -2223,7 +2824,12 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     const unsigned rows_blocks = blocks_for(T * 32, 256);
     const double theta = 0.5 * (CHEB_BETA + CHEB_ALPHA), delta = 0.5 * (CHEB_BETA - CHEB_ALPHA);
     const double sigma = theta / delta;
+    GraphCache graphs(o->cuda_graphs != 0);
+    std::function<bem_status(const double2*, double2*, int)> mass_many_eager;
     auto mass_many = [&](const double2* zin, double2* yout, int steps) -> bem_status {
+        return graphs.run(GraphKey{wr.p, zin, yout, 0, steps}, s, [&]() { return mass_many_eager(zin, yout, steps); });
+    };
+    mass_many_eager = [&](const double2* zin, double2* yout, int steps) -> bem_status {
         const unsigned g64 = blocks_for(T, 64);
         BEM_LAUNCH(k_cheb_init_many, g64, 64, 0, s, Dd, RI, T, zin, yout, wr.as<double2>(), wa.as<double2>(),
                    1.0 / theta);
@@ -2343,6 +2949,344 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     }
     if (result == BEM_E_NOT_CONVERGED)
         set_error("GMRES did not reach the tolerance within gmres_maxiter iterations for some instance");
+    return result;
+}
+
+// ================================================================ Neumann screen
+// Sec. 4.2 (eq. neumannscreen) and the screen of Sec. 5.7: D phi = gamma_N u_inc on an
+// open screen, phi in the P1 functions of the screen's interior nodes (padded to all
+// nodes with zeros at the boundary).  precond = BEM_SCREEN_MASS: M^-1 D; BEM_SCREEN_OO:
+// M^-1 V^_c M^-1 D with V^_c = P_cf^T M_c^-1 V_c M_c^-1 P_cf the single layer of the
+// coarse grid c through the mortar (paper: Z_e^-1 Z_i V_i Z_i^-1 Z_e D_e), left-applied
+// to both sides.  M is the fine grid's mass matrix restricted to the interior nodes.
+bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_grid* gc, bem_c128 k,
+                             const bem_incident* inc, const bem_solve_opts* o, int precond, bem_c128* phi,
+                             int on_device, bem_solve_report* rep) {
+    cudaStream_t s = ctx->stream;
+    const bool oo = precond == BEM_SCREEN_OO;
+    const bool mixed = o->precision == BEM_PREC_MIXED;
+    const int64_t N = gf->nv, Nc = oo ? gc->nv : 0;
+    const StopCheck stop = [ctx]() -> bem_status {
+        if (ctx->cancel && ctx->cancel->load(std::memory_order_relaxed)) {
+            set_error("request cancelled");
+            return BEM_E_CANCELLED;
+        }
+        if (ctx->deadline > 0.0 && now_seconds() > ctx->deadline) {
+            set_error("request exceeded its time limit");
+            return BEM_E_TIMEOUT;
+        }
+        return BEM_OK;
+    };
+    EventTimer t_asm, t_mor, t_sol;
+    GraphCache graphs(o->cuda_graphs != 0);
+    // ---- boundary nodes (edges of one triangle) on the host
+    std::vector<uint8_t> keep(N, 1);
+    {
+        std::vector<std::pair<int32_t, int32_t>> edges;
+        edges.reserve(3 * gf->nt);
+        for (int64_t t = 0; t < gf->nt; ++t)
+            for (int a = 0; a < 3; ++a) {
+                int32_t p = gf->h_tri[3 * t + a], q = gf->h_tri[3 * t + (a + 1) % 3];
+                edges.emplace_back(std::min(p, q), std::max(p, q));
+            }
+        std::sort(edges.begin(), edges.end());
+        for (size_t i = 0; i < edges.size();) {
+            size_t j = i;
+            while (j < edges.size() && edges[j] == edges[i]) ++j;
+            if (j - i == 1) keep[edges[i].first] = keep[edges[i].second] = 0;
+            i = j;
+        }
+    }
+    DevBuf dkeep;
+    BEM_TRY(dkeep.alloc((size_t)N, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(dkeep.p, keep.data(), (size_t)N, cudaMemcpyHostToDevice, s));
+    const uint8_t* K8 = dkeep.as<uint8_t>();
+    // ---- operators: D on the screen, V on the coarse grid
+    const size_t esz = mixed ? 8 : 16;
+    DevBuf Dm, Vc;
+    BEM_TRY(Dm.alloc((size_t)N * N * esz, s));
+    if (oo) BEM_TRY(Vc.alloc((size_t)Nc * Nc * esz, s));
+    cudaEventRecord(t_asm.a, s);
+    if (mixed) {
+        // the conforming preconditioner's V comes out of the same assembly pass as D
+        float2* Vsame = oo && gc == gf ? Vc.as<float2>() : nullptr;
+        BEM_CUDA_TRY(cudaMemsetAsync(Dm.p, 0, Dm.bytes, s));
+        if (Vsame) BEM_CUDA_TRY(cudaMemsetAsync(Vc.p, 0, Vc.bytes, s));
+        BEM_TRY(assemble_regular_fp32(gf, k.re, k.im, Vsame, nullptr, nullptr, Dm.as<float2>(), s));
+        BEM_TRY(assemble_singular_into_c64(gf, k.re, k.im, o->n_singular, Vsame, nullptr, nullptr, Dm.as<float2>(),
+                                           s));
+        if (oo && gc != gf) {
+            BEM_CUDA_TRY(cudaMemsetAsync(Vc.p, 0, Vc.bytes, s));
+            BEM_TRY(assemble_regular_fp32(gc, k.re, k.im, Vc.as<float2>(), nullptr, nullptr, nullptr, s));
+            BEM_TRY(assemble_singular_into_c64(gc, k.re, k.im, o->n_singular, Vc.as<float2>(), nullptr, nullptr,
+                                               nullptr, s));
+        }
+    } else {
+        BEM_TRY(assemble_operators_fp64(gf, k.re, k.im, o->n_singular, oo && gc == gf ? Vc.as<double2>() : nullptr,
+                                        nullptr, nullptr, Dm.as<double2>(), s));
+        if (oo && gc != gf)
+            BEM_TRY(assemble_operators_fp64(gc, k.re, k.im, o->n_singular, Vc.as<double2>(), nullptr, nullptr, nullptr,
+                                            s));
+    }
+    cudaEventRecord(t_asm.b, s);
+    // ---- mass matrices (the screen's restricted to its interior nodes) and mortar
+    cudaEventRecord(t_mor.a, s);
+    DevBuf mvf, dvf, mvc, dvc, prow, pcol, pval;
+    BEM_TRY(mvf.alloc(gf->m_nnz * 8, s));
+    BEM_TRY(dvf.alloc(N * 8, s));
+    BEM_TRY(mass_values(gf, mvf.as<double>(), s));
+    BEM_TRY(mass_inverse_diag(gf, mvf.as<double>(), dvf.as<double>(), s));
+    MassEll ell_f, ell_c;
+    BEM_TRY(ell_f.build(gf, mvf.as<double>(), s));
+    BEM_LAUNCH(k_mask_mass_ell, blocks_for(N, 128), 128, 0, s, ell_f.ci.as<int32_t>(), ell_f.v.as<double>(),
+               dvf.as<double>(), ell_f.W, N, K8);
+    CsrBuf csr_cf, csr_fc;  // P_cf (rows: coarse nodes) and P_fc
+    if (oo) {
+        BEM_TRY(mvc.alloc(gc->m_nnz * 8, s));
+        BEM_TRY(dvc.alloc(Nc * 8, s));
+        BEM_TRY(mass_values(gc, mvc.as<double>(), s));
+        BEM_TRY(mass_inverse_diag(gc, mvc.as<double>(), dvc.as<double>(), s));
+        BEM_TRY(ell_c.build(gc, mvc.as<double>(), s));
+        // central projection from a point off the screen's plane (identity on coplanar grids)
+        double cen[3] = {0.0, 0.0, 0.0}, nrm[3] = {0.0, 0.0, 0.0};
+        for (int64_t i = 0; i < N; ++i)
+            for (int d = 0; d < 3; ++d) cen[d] += gf->h_xyz[3 * i + d] / (double)N;
+        {
+            const int32_t* t = gf->h_tri.data();
+            const double* x = gf->h_xyz.data();
+            double e1[3], e2[3];
+            for (int d = 0; d < 3; ++d) {
+                e1[d] = x[3 * t[1] + d] - x[3 * t[0] + d];
+                e2[d] = x[3 * t[2] + d] - x[3 * t[0] + d];
+            }
+            nrm[0] = e1[1] * e2[2] - e1[2] * e2[1];
+            nrm[1] = e1[2] * e2[0] - e1[0] * e2[2];
+            nrm[2] = e1[0] * e2[1] - e1[1] * e2[0];
+            const double l = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+            for (int d = 0; d < 3; ++d) cen[d] += nrm[d] / l;
+        }
+        int64_t pnnz = 0;
+        BEM_TRY(mortar_coo(gc, gf, cen, prow, pcol, pval, &pnnz, s));
+        BEM_TRY(build_csr(prow.as<int32_t>(), pcol.as<int32_t>(), pval.as<double>(), pnnz, Nc, csr_cf, s));
+        BEM_TRY(build_csr(pcol.as<int32_t>(), prow.as<int32_t>(), pval.as<double>(), pnnz, N, csr_fc, s));
+    }
+    cudaEventRecord(t_mor.b, s);
+    // ---- workspaces
+    const int RB = std::min<int>(o->batch_columns > 0 ? std::min(o->batch_columns, 8) : 8, inc->n_rhs);
+    const int RW = RB + 7;
+    const size_t colf = (size_t)N * 16, colc = (size_t)std::max<int64_t>(Nc, 1) * 16;
+    DevBuf z, w, u, wr, wa, wb, x32, xsplit, c1, c2, c3, x32c, wrc, wac, wbc;
+    BEM_TRY(z.alloc(RW * colf, s));
+    for (DevBuf* b : {&w, &u, &wr, &wa, &wb}) BEM_TRY(b->alloc(RB * colf, s));
+    if (mixed) {
+        BEM_TRY(x32.alloc((size_t)RW * N * 8, s));
+        BEM_CUDA_TRY(cudaMemsetAsync(x32.p, 0, x32.bytes, s));
+    }
+    const bool dd_single = mixed && RB == 1;
+    double inner_progress = 1.0;
+    auto dd_now = [&]() { return dd_single && inner_progress > DD_SWITCH; };
+    if (dd_single) BEM_TRY(xsplit.alloc((size_t)std::max(N, Nc) * 16, s));
+    MassOp mf;
+    mf.M.ci[0] = ell_f.ci.as<int32_t>(); mf.M.v[0] = ell_f.v.as<double>(); mf.M.W[0] = ell_f.W;
+    mf.M.dinv[0] = dvf.as<double>();
+    mf.M.ci[1] = mf.M.ci[0]; mf.M.v[1] = mf.M.v[0]; mf.M.W[1] = mf.M.W[0]; mf.M.dinv[1] = mf.M.dinv[0];
+    mf.M.Ne = N; mf.M.Ni = 0; mf.M.n = N;  // one vector of the screen per column
+    mf.r = wr.as<double2>(); mf.dA = wa.as<double2>(); mf.dB = wb.as<double2>();
+    mf.graphs = &graphs;
+    MassOp mc;
+    if (oo) {
+        for (DevBuf* b : {&c1, &wrc, &wac, &wbc}) BEM_TRY(b->alloc(RB * colc, s));
+        for (DevBuf* b : {&c2, &c3}) BEM_TRY(b->alloc(RW * colc, s));
+        BEM_CUDA_TRY(cudaMemsetAsync(c2.p, 0, c2.bytes, s));
+        if (mixed) {
+            BEM_TRY(x32c.alloc((size_t)RW * Nc * 8, s));
+            BEM_CUDA_TRY(cudaMemsetAsync(x32c.p, 0, x32c.bytes, s));
+        }
+        mc.M.ci[0] = ell_c.ci.as<int32_t>(); mc.M.v[0] = ell_c.v.as<double>(); mc.M.W[0] = ell_c.W;
+        mc.M.dinv[0] = dvc.as<double>();
+        mc.M.ci[1] = mc.M.ci[0]; mc.M.v[1] = mc.M.v[0]; mc.M.W[1] = mc.M.W[0]; mc.M.dinv[1] = mc.M.dinv[0];
+        mc.M.Ne = Nc; mc.M.Ni = 0; mc.M.n = Nc;
+        mc.r = wrc.as<double2>(); mc.dA = wac.as<double2>(); mc.dB = wbc.as<double2>();
+        mc.graphs = &graphs;
+    }
+    Blocks<float2> BD32{}, BV32{};
+    Blocks<double2> BD64{}, BV64{};
+    if (mixed) {
+        fill_blocks_row(BD32, Dm.as<float2>(), 0, 1.0, (float2*)nullptr, 0, 0.0, N);
+        if (oo) fill_blocks_row(BV32, Vc.as<float2>(), 0, 1.0, (float2*)nullptr, 0, 0.0, Nc);
+    } else {
+        fill_blocks_row(BD64, Dm.as<double2>(), 0, 1.0, (double2*)nullptr, 0, 0.0, N);
+        if (oo) fill_blocks_row(BV64, Vc.as<double2>(), 0, 1.0, (double2*)nullptr, 0, 0.0, Nc);
+    }
+    // zo = one-matrix product on nn rows in the working arithmetic or in FP64 arithmetic
+    auto product = [&](bool fp64, const Blocks<float2>& b32, const Blocks<double2>& b64, int64_t nn, float2* xw,
+                       const double2* xin, double2* zo, int R) -> bem_status {
+        const unsigned rows_blocks = blocks_for(nn * 32, 256);
+        if (!mixed) {
+            const Blocks<double2> d64 = both_matrices(b64);
+            for (int c0 = 0; c0 < R; c0 += 8) {
+                const int Wd = gemm_width(std::min(8, R - c0));
+                const double2* xc = xin + (int64_t)c0 * nn;
+                double2* zc = zo + (int64_t)c0 * nn;
+                if (Wd == 1) BEM_LAUNCH(k_gemm64<1>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
+                else if (Wd == 2) BEM_LAUNCH(k_gemm64<2>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
+                else if (Wd == 4) BEM_LAUNCH(k_gemm64<4>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
+                else BEM_LAUNCH(k_gemm64<8>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
+            }
+            return BEM_OK;
+        }
+        if (fp64) {
+            const Blocks<float2> d32 = both_matrices(b32);
+            for (int c0 = 0; c0 < R; c0 += 8) {
+                const int Wd = gemm_width(std::min(8, R - c0));
+                const double2* xc = xin + (int64_t)c0 * nn;
+                double2* zc = zo + (int64_t)c0 * nn;
+                if (Wd == 1) BEM_LAUNCH(k_gemm_c64_f64<1>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
+                else if (Wd == 2) BEM_LAUNCH(k_gemm_c64_f64<2>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
+                else if (Wd == 4) BEM_LAUNCH(k_gemm_c64_f64<4>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
+                else BEM_LAUNCH(k_gemm_c64_f64<8>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
+            }
+            return BEM_OK;
+        }
+        if (R == 1 && dd_now()) {
+            BEM_LAUNCH(k_split_x, blocks_for(nn, 256), 256, 0, s, xin, nn, xsplit.as<float4>());
+            return launch_gemv_dd(b32, nn, xsplit.as<float4>(), zo, s);
+        }
+        BEM_LAUNCH(k_to_c64, blocks_for((int64_t)R * nn, 256), 256, 0, s, xin, (int64_t)R * nn, xw);
+        for (int c0 = 0; c0 < R; c0 += 8) {
+            const int Wd = gemm_width(std::min(8, R - c0));
+            BEM_TRY(launch_gemm32(Wd, b32, nn, xw + (int64_t)c0 * nn, zo + (int64_t)c0 * nn, s));
+        }
+        return BEM_OK;
+    };
+    // y = M^-1 V^_c M^-1 v (OO) or M^-1 v, for v on the screen (boundary entries ignored)
+    auto precondition = [&](bool fp64, const double2* v, double2* y, int R, int steps) -> bem_status {
+        BEM_LAUNCH(k_mask_rows, dim3(blocks_for(N, 256), R), 256, 0, s, const_cast<double2*>(v), K8, N);
+        if (!oo) return mass_solve(mf, v, y, R, s, steps);
+        BEM_TRY(mass_solve(mf, v, u.as<double2>(), R, s, steps));
+        BEM_LAUNCH(k_csr_apply, dim3(blocks_for(Nc, 128), R), 128, 0, s, csr_cf.rp.as<int32_t>(),
+                   csr_cf.ci.as<int32_t>(), csr_cf.v.as<double>(), Nc, u.as<double2>(), N, c1.as<double2>(), Nc, 1.0);
+        BEM_TRY(mass_solve(mc, c1.as<double2>(), c2.as<double2>(), R, s, steps));
+        BEM_TRY(product(fp64, BV32, BV64, Nc, x32c.as<float2>(), c2.as<double2>(), c3.as<double2>(), R));
+        BEM_TRY(mass_solve(mc, c3.as<double2>(), c1.as<double2>(), R, s, steps));
+        BEM_LAUNCH(k_csr_apply, dim3(blocks_for(N, 128), R), 128, 0, s, csr_fc.rp.as<int32_t>(),
+                   csr_fc.ci.as<int32_t>(), csr_fc.v.as<double>(), N, c1.as<double2>(), Nc, u.as<double2>(), N, 1.0);
+        BEM_LAUNCH(k_mask_rows, dim3(blocks_for(N, 256), R), 256, 0, s, u.as<double2>(), K8, N);
+        return mass_solve(mf, u.as<double2>(), y, R, s, steps);
+    };
+    auto apply_on = [&](bool fp64, const double2* xin, double2* yout, int R, int steps) -> bem_status {
+        BEM_TRY(product(fp64, BD32, BD64, N, x32.as<float2>(), xin, z.as<double2>(), R));
+        return precondition(fp64, z.as<double2>(), yout, R, steps);
+    };
+    Apply apply_work = [&](const double2* xin, double2* yout, int R) -> bem_status {
+        const int steps = !mixed ? CHEB_STEPS : (R == 1 && dd_now()) ? CHEB_STEPS_DD : CHEB_STEPS_INNER;
+        return apply_on(false, xin, yout, R, steps);
+    };
+    Apply apply_fp64 = [&](const double2* xin, double2* yout, int R) -> bem_status {
+        return apply_on(true, xin, yout, R, CHEB_STEPS);
+    };
+    // ---- right-hand sides and GMRES (with refinement in the mixed mode)
+    const int maxit = (int)std::min<int64_t>(o->gmres_maxiter, N);
+    GmresWork W;
+    BEM_TRY(W.init(maxit, N, RB, RW - RB, s));
+    DevBuf fvec, gvec, sb, xsol, dvec, rvec, tmp, wave;
+    BEM_TRY(wave.alloc((size_t)5 * RB * 8, s));
+    BEM_TRY(fvec.alloc(RB * colf, s));
+    BEM_TRY(gvec.alloc(RB * colf, s));
+    BEM_TRY(sb.alloc(RB * colf, s));
+    BEM_TRY(xsol.alloc(RW * colf, s));
+    BEM_CUDA_TRY(cudaMemsetAsync(xsol.p, 0, RW * colf, s));
+    for (DevBuf* b : {&dvec, &rvec, &tmp}) BEM_TRY(b->alloc(RB * colf, s));
+    bem_status result = BEM_OK;
+    int total_inner = 0, outer_used = 0;
+    double worst_res = 0.0;
+    bool all_conv = true;
+    cudaEventRecord(t_sol.a, s);
+    for (int r0 = 0; r0 < inc->n_rhs; r0 += RB) {
+        const int R = std::min(RB, inc->n_rhs - r0);
+        for (int r = 0; r < R; ++r) {
+            W.h_wave[2 * r] = inc->amps ? inc->amps[r0 + r].re : 1.0;
+            W.h_wave[2 * r + 1] = inc->amps ? inc->amps[r0 + r].im : 0.0;
+            for (int d = 0; d < 3; ++d) W.h_wave[2 * RB + 3 * r + d] = inc->dirs[3 * (r0 + r) + d];
+        }
+        BEM_CUDA_TRY(cudaMemcpyAsync(wave.p, W.h_wave, (size_t)5 * RB * 8, cudaMemcpyHostToDevice, s));
+        BEM_CUDA_TRY(cudaMemsetAsync(fvec.p, 0, (size_t)R * colf, s));
+        BEM_CUDA_TRY(cudaMemsetAsync(gvec.p, 0, (size_t)R * colf, s));
+        BEM_LAUNCH(k_plane_wave, dim3(blocks_for(gf->nt, 128), R), 128, 0, s, gf->rec.as<TriRec>(),
+                   gf->tri.as<int32_t>(), gf->nt, k.re, k.im, wave.as<double>() + 2 * RB, wave.as<double2>(), N,
+                   fvec.as<double2>(), gvec.as<double2>());
+        // g_i = <gamma_N u_inc, theta_i>: the preconditioned right-hand side
+        BEM_TRY(precondition(true, gvec.as<double2>(), sb.as<double2>(), R, CHEB_STEPS));
+        std::vector<double> beta(R), tol_abs(R), rn(R), est(R), inner_tol(R);
+        std::vector<int> its(R), total(R, 0);
+        BEM_TRY(norms(W, sb.as<double2>(), R, beta.data(), s));
+        for (int r = 0; r < R; ++r) tol_abs[r] = o->gmres_tol * beta[r];
+        if (!mixed) {
+            BEM_TRY(gmres_run(W, R, apply_work, sb.as<double2>(), beta.data(), tol_abs.data(), xsol.as<double2>(),
+                              its.data(), est.data(), s, stop));
+            for (int r = 0; r < R; ++r) {
+                rn[r] = est[r];
+                total[r] = its[r];
+            }
+            outer_used = 1;
+        } else {
+            BEM_CUDA_TRY(cudaMemsetAsync(xsol.p, 0, (size_t)R * colf, s));
+            BEM_CUDA_TRY(cudaMemcpyAsync(rvec.p, sb.p, (size_t)R * colf, cudaMemcpyDeviceToDevice, s));
+            rn = beta;
+            int outer = 0;
+            auto pending = [&](int r) { return beta[r] > 0.0 && rn[r] > tol_abs[r] && total[r] < o->gmres_maxiter; };
+            auto any_pending = [&] {
+                for (int r = 0; r < R; ++r)
+                    if (pending(r)) return true;
+                return false;
+            };
+            while (any_pending() && outer < 12) {
+                for (int r = 0; r < R; ++r)
+                    inner_tol[r] = pending(r) ? std::max(tol_abs[r], o->ir_inner_tol * rn[r]) : rn[r];
+                BEM_TRY(gmres_run(W, R, apply_work, rvec.as<double2>(), rn.data(), inner_tol.data(), dvec.as<double2>(),
+                                  its.data(), est.data(), s, stop, &inner_progress));
+                int moved = 0;
+                for (int r = 0; r < R; ++r) {
+                    total[r] += its[r];
+                    moved += its[r];
+                }
+                BEM_LAUNCH(k_acc, blocks_for((int64_t)R * N, 256), 256, 0, s, xsol.as<double2>(), dvec.as<double2>(),
+                           (int64_t)R * N);
+                BEM_TRY(apply_fp64(xsol.as<double2>(), tmp.as<double2>(), R));
+                BEM_LAUNCH(k_sub, blocks_for((int64_t)R * N, 256), 256, 0, s, sb.as<double2>(), tmp.as<double2>(),
+                           (int64_t)R * N, rvec.as<double2>());
+                BEM_TRY(norms(W, rvec.as<double2>(), R, rn.data(), s));
+                ++outer;
+                if (moved == 0) break;
+            }
+            outer_used = std::max(outer_used, outer);
+        }
+        for (int r = 0; r < R; ++r) {
+            const double rel = beta[r] > 0.0 ? rn[r] / beta[r] : 0.0;
+            const bool conv = beta[r] == 0.0 || rel <= o->gmres_tol;
+            all_conv = all_conv && conv;
+            worst_res = std::max(worst_res, rel);
+            total_inner += total[r];
+            if (!conv) result = BEM_E_NOT_CONVERGED;
+        }
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        BEM_CUDA_TRY(cudaMemcpyAsync(phi + (int64_t)r0 * N, xsol.p, (size_t)R * colf, kind, s));
+        BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    cudaEventRecord(t_sol.b, s);
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (result == BEM_E_NOT_CONVERGED)
+        set_error("GMRES did not reach the tolerance within gmres_maxiter iterations; outputs hold the last iterate");
+    if (rep) {
+        rep->iterations = total_inner;
+        rep->converged = all_conv ? 1 : 0;
+        rep->residual = worst_res;
+        rep->t_assembly_ms = t_asm.ms();
+        rep->t_mortar_ms = t_mor.ms();
+        rep->t_solve_ms = t_sol.ms();
+        rep->mtf_variant = 0;
+        rep->outer_iterations = outer_used;
+    }
     return result;
 }
 

@@ -59,3 +59,19 @@ def test_table3_node_counts_set_the_system_size():
     ve, te, vi, ti = bi.transmission_pair(1, 0, seed=7)
     B = mtf_blocks(ve, te, vi, ti, 1.0, 1.5)
     assert mtf_matrix(B, 2.0).shape[0] == 2 * (len(ve) + len(vi))
+
+
+def test_cube_benchmarks_follow_tables_2_and_3():
+    """The unit-cube benchmarks timed by bench.py use Table 2's physics (f, c, rho of
+    both media) and nonconforming cube grids whose node counts are within 10 % of
+    Table 3's N_ext and nonconforming N_int."""
+    import bench
+    t2 = {r[0]: list(map(float, r[1:6])) for r in _rows("table2")}
+    t3 = {r[0]: (int(r[1]), int(r[4])) for r in _rows("table3")}
+    for b in bench.CUBE_BENCHMARKS:
+        key = b["name"].replace(" ", "-")
+        assert [b["f"], b["c_ext"], b["c_int"], b["rho_ext"], b["rho_int"]] == t2[key], key
+        assert (b["N_ext"], b["N_int"]) == t3[key], key
+        for N in t3[key]:
+            n = bench.cube_edge_nodes(N)
+            assert abs(6 * n * n + 2 - N) <= 0.1 * N, (key, N, n)

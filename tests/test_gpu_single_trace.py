@@ -191,7 +191,7 @@ def test_single_trace_rejected_where_not_supported(env):
         assert e.value.status == bem.BEM_E_INVALID_ARG
         with pytest.raises(bem.BemError) as e:
             bem.bem_solve_transmission(ctx, ge, gi, 2.0, 1.0, 1.0, np.array([[0.0, 0.0, 1.0]]),
-                                       opts={"formulation": 7})
+                                       opts={"formulation": 99})
         assert e.value.status == bem.BEM_E_INVALID_ARG
     finally:
         bem.bem_grid_destroy(ge)
