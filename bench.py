@@ -476,18 +476,22 @@ def run_screen(bem, ctx):
 
 
 def run_graphs(bem, ctx, reps=5):
-    """CUDA-graph replay of the iteration's fixed launch sequences on and off: one
-    mixed-precision solve (k_ext 10, k_int 15, rho 2, one wave) per grid level, wall
-    time per solve with host buffers (median of reps), and the library's launch count."""
+    """Launch forms of the mass inverses (the 18-35 short kernels of each application):
+    one launch per Chebyshev step, the same replayed as CUDA graphs (the default), and one
+    cooperative launch per inverse (an exclusive context).  One mixed-precision solve
+    (k_ext 10, k_int 15, rho 2, one wave) per grid level, wall time per solve with host
+    buffers (median of reps), and the library's launch count."""
     import torch
     import bem_inputs as bi
     out = {"workload": "icosphere pair L/L (seed 2), k_ext=10, k_int=15, rho=2, one plane wave +z, mixed, "
                        "tol 1e-8; median of %d solves per setting" % reps, "levels": []}
+    modes = (("steps", 0, 0), ("steps_graphs", 0, 1), ("fused", 1, 1))
     for L in (2, 3, 4):
         ve, te, vi, ti = bi.transmission_pair(L, L, seed=2)
         ge, gi = bem.bem_grid_create(ctx, ve, te), bem.bem_grid_create(ctx, vi, ti)
         entry = {"level": L, "unknowns": 2 * (len(ve) + len(vi))}
-        for g in (0, 1):
+        for name, excl, g in modes:
+            bem.bem_context_set_exclusive(ctx, bool(excl))
             opts = {"precision": bem.BEM_PREC_MIXED, "cuda_graphs": g}
             bem.bem_solve_transmission(ctx, ge, gi, 15.0, 10.0, 2.0, np.array([[0.0, 0.0, 1.0]]), opts=opts)
             ts, launches = [], 0
@@ -499,9 +503,10 @@ def run_graphs(bem, ctx, reps=5):
                                                     opts=opts)
                 ts.append(time.perf_counter() - t0)
                 launches = bem.bem_launch_count() - l0
-            entry["graphs" if g else "no_graphs"] = {"ms": 1e3 * statistics.median(ts), "iterations": rep["iterations"],
-                                                     "kernels": launches}
-        entry["speedup"] = entry["no_graphs"]["ms"] / entry["graphs"]["ms"]
+            entry[name] = {"ms": 1e3 * statistics.median(ts), "iterations": rep["iterations"], "kernels": launches}
+        bem.bem_context_set_exclusive(ctx, False)
+        entry["speedup_graphs"] = entry["steps"]["ms"] / entry["steps_graphs"]["ms"]
+        entry["speedup_fused"] = entry["steps"]["ms"] / entry["fused"]["ms"]
         bem.bem_grid_destroy(ge)
         bem.bem_grid_destroy(gi)
         out["levels"].append(entry)
@@ -547,6 +552,13 @@ def run_uneven(bem, ctx):
             "iterations_one_call_each": int(its_single), "all_converged": all(r["converged"] for r in reps)}
 
 
+# DRAM bytes (read + write) per launch of k_gemm32<1> over its algorithmic bytes, from an
+# ncu capture of the current kernel on the L4 pair (423.0 MB against 420.1 MB per launch);
+# the traffic of a launch grows with the operator bytes, so the at-scale figure is this
+# ratio times the at-scale algorithmic bytes
+GEMM32_TRAFFIC_RATIO = 423020458 / 420086016
+
+
 def kernel_roofline(name, ms, n, te, ti, Ne, Ni, pp_cache):
     """Roofline entry of one profiled kernel (per-launch averages)."""
     avg_s = ms / n / 1e3
@@ -556,8 +568,12 @@ def kernel_roofline(name, ms, n, te, ti, Ne, Ni, pp_cache):
         peak, kind = hbm_peak()
         bytes_ = 8 * 4 * (Ne * Ne + Ni * Ni)  # 8 complex64 blocks read once per operator product
         ach = bytes_ / avg_s / 1e9
+        traffic = bytes_ * GEMM32_TRAFFIC_RATIO if name == "k_gemm32<1>" else None
         return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": None, "peak_kind": kind, "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": ms / n}
+                "traffic": traffic, "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the L4 "
+                                                     "capture, scaled to this launch by the operator bytes")
+                if traffic else None,
+                "peak_kind": kind, "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": ms / n}
     if name.startswith("k_gemm64"):
         flops = 8 * 4 * (Ne * Ne + Ni * Ni) * cols  # 4 DFMA = 8 flops per complex entry and column
         ach = flops / avg_s / 1e12

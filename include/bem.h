@@ -106,7 +106,11 @@ BEM_API uint64_t bem_launch_count(void);
  * sincosf on 2^20 evenly spaced arguments in [-64, 64].  which = 1: relative L2
  * difference between the tensor-core multi-column MTF product (TF32 three-term
  * split) and the FP32 CUDA-core product on seeded random complex64 blocks
- * (N_ext = 300, N_int = 170, 24 columns).  which = 2: the same with 8 columns. */
+ * (N_ext = 300, N_int = 170, 24 columns).  which = 2: the same with 8 columns.
+ * which = 3: the bounded wait of the grid barrier that the fused mass inverse uses:
+ * two cooperative blocks whose barrier can never complete must each give up after
+ * about a second and flag it; result = 1000 * flag + elapsed seconds (expected
+ * 1000 + ~1). */
 BEM_API bem_status bem_selftest(bem_context* ctx, int which, double* result);
 
 /* Per-kernel device timing.  While enabled, each launch of the library is
@@ -160,6 +164,14 @@ BEM_API bem_status bem_context_create(int device, void* stream, bem_context** ou
 BEM_API bem_status bem_context_destroy(bem_context* ctx);
 /* Block until all work queued on the context's stream has finished. */
 BEM_API bem_status bem_context_synchronize(bem_context* ctx);
+/* exclusive = 1: the caller guarantees that this context's solves never overlap with
+ * other solves on the device, and each mass-matrix inverse then runs as one
+ * cooperative launch whose blocks synchronise through a grid barrier (bounded waits).
+ * exclusive = 0 (default): one launch per Chebyshev step, replayed as CUDA graphs when
+ * cuda_graphs is on (on GB300 this measured faster: a barrier step costs about what a
+ * graph node does, and the graph form keeps more parallel work in flight).  The results
+ * do not depend on it. */
+BEM_API bem_status bem_context_set_exclusive(bem_context* ctx, int exclusive);
 
 /* ---------------------------------------------------------------- grids
  * Grid intake (paper Sec. 2.4 and Sec. 3: a conforming triangular surface grid).
@@ -269,6 +281,10 @@ typedef struct {
     int32_t formulation;      /* BEM_FORM_* (default BEM_FORM_MTF); the single-trace systems are
                                  available in bem_solve_transmission only (bem_solve_many and the
                                  server solve the multiple-traces system)                         */
+    double  dd_switch;        /* BEM_PREC_MIXED, one right-hand side: the inner GMRES products run
+                                 in double-float arithmetic while the inner residual is above
+                                 dd_switch of its right-hand side, in FP32 below (default 1e-3;
+                                 0: double-float throughout, 1: FP32 throughout)                  */
     int32_t cuda_graphs;      /* 1 (default): the fixed launch sequences of each iteration (the
                                  Chebyshev mass inverses) are captured once per solve and replayed
                                  as CUDA graphs; 0: every kernel is launched on its own. Results

@@ -63,6 +63,7 @@ class bem_solve_opts(C.Structure):
         ("batch_columns", C.c_int32),
         ("tensor_cores", C.c_int32),
         ("formulation", C.c_int32),
+        ("dd_switch", C.c_double),
         ("cuda_graphs", C.c_int32),
     ]
 
@@ -153,6 +154,7 @@ _SIGNATURES = {
     "bem_profile_select": (None, [C.c_char_p]),
     "bem_profile_reset": (None, []),
     "bem_autotune": (C.c_int32, [_VP, _VP, _VP, C.c_int32]),
+    "bem_context_set_exclusive": (C.c_int32, [_VP, C.c_int]),
     "bem_solve_screen": (C.c_int32, [_VP, _VP, _VP, bem_c128, _VP, _VP, C.c_int32, _VP, C.c_int, _VP]),
     "bem_tune_get": (C.c_int32, [C.c_char_p, C.c_int32, _I64, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                  C.POINTER(C.c_double)]),
@@ -362,6 +364,13 @@ def bem_context_create(device=0, stream=None):
         s = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(_lib.bem_context_create(int(device), s, C.byref(h)))
     return h
+
+
+def bem_context_set_exclusive(ctx, exclusive=True):
+    """True only if this context's solves never overlap with others on the device: the
+    mass inverses then run as one cooperative launch each (default False: step launches
+    replayed as CUDA graphs)."""
+    _check(_lib.bem_context_set_exclusive(ctx, int(bool(exclusive))))
 
 
 def bem_context_destroy(ctx):

@@ -196,6 +196,10 @@ struct bem_context {
     // stop request checked by the solver between GMRES iterations (serving)
     const std::atomic<int>* cancel = nullptr;
     double deadline = 0.0;  // steady-clock seconds; 0 = none
+    // set by the caller when its solves never overlap with others on the device: the
+    // mass inverses then run as one cooperative launch with grid barriers (off by
+    // default: measured no faster than the step launches replayed as CUDA graphs)
+    bool exclusive = false;
 };
 
 struct bem_grid {
@@ -271,6 +275,7 @@ bem_status mtf_product_tc(const float2* const a1[4], const float2* const a2[4], 
                           const int64_t x2[4], int64_t n, int R, const double2* x, double2* z, void* work,
                           size_t work_bytes, int* err, cudaStream_t s);
 bem_status selftest_tc(int R, double* rel_err, cudaStream_t s);
+bem_status selftest_barrier(double* result, cudaStream_t s);
 
 bem_status mortar_coo(const bem_grid* a, const bem_grid* b, const double center[3],
                       DevBuf& row, DevBuf& col, DevBuf& val, int64_t* nnz, cudaStream_t s);

@@ -80,8 +80,9 @@ uint64_t bem_launch_count(void) { return g_launches.load(std::memory_order_relax
 bem_status bem_selftest(bem_context* ctx, int which, double* result) {
     CTX_GUARD(ctx);
     BEM_REQUIRE(result != nullptr, "null result");
-    BEM_REQUIRE(which >= 0 && which <= 2, "unknown self-test");
+    BEM_REQUIRE(which >= 0 && which <= 3, "unknown self-test");
     if (which == 0) return selftest_sincos(1 << 20, 64.0f, result, ctx->stream);
+    if (which == 3) return selftest_barrier(result, ctx->stream);
     return selftest_tc(which == 1 ? 24 : 8, result, ctx->stream);
 }
 
@@ -358,6 +359,7 @@ void bem_solve_opts_default(bem_solve_opts* o) {
     o->batch_columns = 0;
     o->tensor_cores = 1;
     o->formulation = BEM_FORM_MTF;
+    o->dd_switch = 1e-3;
     o->cuda_graphs = 1;
 }
 
@@ -384,6 +386,7 @@ bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const b
     BEM_REQUIRE(o.tensor_cores == 0 || o.tensor_cores == 1, "tensor_cores must be 0 or 1");
     BEM_REQUIRE(o.formulation >= BEM_FORM_MTF && o.formulation <= BEM_FORM_HC_INT_DIR, "unknown formulation");
     BEM_REQUIRE(o.cuda_graphs == 0 || o.cuda_graphs == 1, "cuda_graphs must be 0 or 1");
+    BEM_REQUIRE(o.dd_switch >= 0.0 && o.dd_switch <= 1.0, "dd_switch must be in [0, 1]");
     for (int r = 0; r < inc->n_rhs; ++r) {
         const double* d = inc->dirs + 3 * r;
         const double nd = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -391,6 +394,13 @@ bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const b
     }
     return solve_transmission_impl(ctx, ext, intr, k_int, k_ext, rho_int_over_rho_ext, inc, &o, v_ext, w_ext, v_int,
                                    w_int, on_device, rep);
+}
+
+bem_status bem_context_set_exclusive(bem_context* ctx, int exclusive) {
+    CTX_GUARD(ctx);
+    BEM_REQUIRE(exclusive == 0 || exclusive == 1, "exclusive must be 0 or 1");
+    ctx->exclusive = exclusive != 0;
+    return BEM_OK;
 }
 
 bem_status bem_solve_screen(bem_context* ctx, const bem_grid* screen, const bem_grid* coarse, bem_c128 k,
@@ -412,6 +422,7 @@ bem_status bem_solve_screen(bem_context* ctx, const bem_grid* screen, const bem_
     BEM_REQUIRE(o.ir_inner_tol > 0.0 && o.ir_inner_tol < 1.0, "ir_inner_tol must be in (0, 1)");
     BEM_REQUIRE(o.batch_columns >= 0 && o.batch_columns <= 128, "batch_columns must be in [0, 128]");
     BEM_REQUIRE(o.cuda_graphs == 0 || o.cuda_graphs == 1, "cuda_graphs must be 0 or 1");
+    BEM_REQUIRE(o.dd_switch >= 0.0 && o.dd_switch <= 1.0, "dd_switch must be in [0, 1]");
     for (int r = 0; r < inc->n_rhs; ++r) {
         const double* d = inc->dirs + 3 * r;
         const double nd = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -453,6 +464,7 @@ bem_status bem_solve_many(bem_context* ctx, int32_t count, const bem_instance* i
     BEM_REQUIRE(o.precision == BEM_PREC_MIXED, "bem_solve_many runs the mixed-precision mode");
     BEM_REQUIRE(o.formulation == BEM_FORM_MTF, "bem_solve_many solves the multiple-traces system only");
     BEM_REQUIRE(o.cuda_graphs == 0 || o.cuda_graphs == 1, "cuda_graphs must be 0 or 1");
+    BEM_REQUIRE(o.dd_switch >= 0.0 && o.dd_switch <= 1.0, "dd_switch must be in [0, 1]");
     BEM_REQUIRE(o.gmres_tol >= 0.0 && o.gmres_maxiter >= 1, "bad GMRES options");
     BEM_REQUIRE(o.n_singular >= 1 && o.n_singular <= 16, "n_singular must be in [1, 16]");
     BEM_REQUIRE(o.mtf_variant == BEM_MTF_DERIVED || o.mtf_variant == BEM_MTF_PRINTED, "unknown MTF variant");

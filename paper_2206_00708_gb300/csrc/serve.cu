@@ -236,6 +236,7 @@ bem_status bem_serve_create(const bem_server_opts* opts, bem_server** out) {
                 for (bem_context* x : srv->contexts) bem_context_destroy(x);
                 return st;
             }
+            c->exclusive = false;  // the workers' solves overlap on the device (never fused)
             srv->contexts.push_back(c);
         }
     } else {

@@ -41,7 +41,6 @@ namespace {
 constexpr int CHEB_STEPS = 34;        // error <= 2 * 3^-34 ~ 1e-16: FP64 applications
 constexpr int CHEB_STEPS_INNER = 17;  // error <= 2 * 3^-17 ~ 1.6e-8: inner solves with FP32 products
 constexpr int CHEB_STEPS_DD = 24;     // error <= 2 * 3^-24 ~ 7e-12: inner solves with double-float products
-constexpr double DD_SWITCH = 1e-3;    // inner relative residual below which single-column products run in FP32
 constexpr double CHEB_ALPHA = 0.5, CHEB_BETA = 2.0;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -803,6 +802,102 @@ __global__ void k_cheb_step(MassPair M, const double2* __restrict__ dk, double2*
     dn[off + g] = make_double2(c1 * d0.x + s * rr.x, c1 * d0.y + s * rr.y);
 }
 
+// Grid-wide barrier of a cooperative launch (all blocks resident): a generation counter
+// that the last block to arrive advances.  Waits are bounded: a block that waits about
+// a second, or sees another block's failure, records it in *err and returns false, and
+// the kernel then returns (its results are not used: the host checks *err).
+struct GridBarrier {
+    unsigned int count, gen;
+};
+
+__device__ bool grid_sync(GridBarrier* b, int* err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int* vgen = &b->gen;
+        volatile int* verr = err;
+        const unsigned int g = *vgen;
+        __threadfence();
+        if (atomicAdd(&b->count, 1u) + 1u == gridDim.x) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            unsigned int spins = 0;
+            while (*vgen == g) {
+                if (*verr) {
+                    ok = 0;
+                    break;
+                }
+                if (++spins > (1u << 21)) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Barrier rounds only (the self-test of the bounded wait)
+__global__ void k_barrier_probe(GridBarrier* bar, int* err, int rounds) {
+    for (int k = 0; k < rounds; ++k)
+        if (!grid_sync(bar, err)) return;
+}
+
+// The whole Chebyshev iteration of mass_solve in one cooperative launch: the
+// arithmetic of k_cheb_init and k_cheb_step, item by item (item = row of one column),
+// with a grid barrier between steps (a step reads its neighbours' d_k).
+__global__ void __launch_bounds__(256) k_cheb_fused(MassPair M, const double2* __restrict__ z,
+                                                    double2* __restrict__ y, double2* __restrict__ r, double2* dA,
+                                                    double2* dB, int R, int steps, double inv_theta, double sigma,
+                                                    double delta, GridBarrier* bar, int* err) {
+    const int64_t n = M.n, items = (int64_t)R * n;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t first = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t e = first; e < items; e += stride) {
+        const int64_t off = (e / n) * n, g = e - off;
+        const MassRow m = mass_row(M, g);
+        const double2 zz = z[off + g];
+        const double sc = m.dinv[m.i] * inv_theta;
+        y[off + g] = make_double2(0, 0);
+        r[off + g] = zz;
+        dA[off + g] = make_double2(sc * zz.x, sc * zz.y);
+    }
+    double rho = 1.0 / sigma;
+    double2 *dk = dA, *dn = dB;
+    for (int k = 0; k < steps; ++k) {
+        if (!grid_sync(bar, err)) return;
+        const double rho_n = 1.0 / (2.0 * sigma - rho);
+        const double c1 = rho_n * rho, c2 = 2.0 * rho_n / delta;
+        for (int64_t e = first; e < items; e += stride) {
+            const int64_t off = (e / n) * n, g = e - off;
+            const MassRow m = mass_row(M, g);
+            const double2 md = mass_apply_row(m, dk + off + m.base);
+            const double2 d0 = dk[off + g];
+            double2 yy = y[off + g], rr = r[off + g];
+            yy.x += d0.x;
+            yy.y += d0.y;
+            rr.x -= md.x;
+            rr.y -= md.y;
+            y[off + g] = yy;
+            r[off + g] = rr;
+            const double sc = c2 * m.dinv[m.i];
+            dn[off + g] = make_double2(c1 * d0.x + sc * rr.x, c1 * d0.y + sc * rr.y);
+        }
+        rho = rho_n;
+        double2* t = dk;
+        dk = dn;
+        dn = t;
+    }
+}
+
 // ---------------------------------------------------------------- GMRES kernels
 // Krylov basis: vector i of right-hand side r at V + (i * R + r) * n.
 // Hessenberg of r: column-major, H + r * ldh * ldh, column j at + j * ldh.
@@ -1011,19 +1106,30 @@ struct GraphCache {
         const cudaError_t ce = cudaStreamEndCapture(s, &g);
         cudaGraphExec_t ex = nullptr;
         size_t nodes = 0;
-        const bool ok = st == BEM_OK && ce == cudaSuccess && g != nullptr &&
-                        cudaGraphGetNodes(g, nullptr, &nodes) == cudaSuccess &&
-                        cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+        bool ok = st == BEM_OK && ce == cudaSuccess && g != nullptr &&
+                  cudaGraphGetNodes(g, nullptr, &nodes) == cudaSuccess;
+        uint64_t kernels = 0;  // kernel nodes (memset nodes are not launches)
+        if (ok) {
+            std::vector<cudaGraphNode_t> list(nodes);
+            ok = cudaGraphGetNodes(g, list.data(), &nodes) == cudaSuccess;
+            for (size_t i = 0; ok && i < nodes; ++i) {
+                cudaGraphNodeType t;
+                ok = cudaGraphNodeGetType(list[i], &t) == cudaSuccess;
+                if (ok && t == cudaGraphNodeTypeKernel) ++kernels;
+            }
+        }
+        ok = ok && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
         if (g) cudaGraphDestroy(g);
         if (!ok) {
+            // capture refused (this stream, or a launch that cannot be captured): from now on
+            // launch the sequences directly; a real error shows again when they run
             cudaGetLastError();
-            if (st != BEM_OK) return st;
-            enabled = false;  // capture refused on this stream: launch kernel by kernel
+            enabled = false;
             return body();
         }
-        entries.push_back({key, ex, (uint64_t)nodes});
+        entries.push_back({key, ex, kernels});
         BEM_CUDA_TRY(cudaGraphLaunch(ex, s));
-        count_launch(nodes);
+        count_launch(kernels);
         return BEM_OK;
     }
 };
@@ -1032,6 +1138,53 @@ struct MassOp {
     MassPair M{};
     double2 *r = nullptr, *dA = nullptr, *dB = nullptr;  // workspaces [R * n]
     GraphCache* graphs = nullptr;                        // replay the step sequence as a graph
+    GridBarrier* bar = nullptr;  // set: the iteration runs as one cooperative launch
+    int* err = nullptr;          // its barrier's failure flag (checked by the solve)
+};
+
+// Blocks of k_cheb_fused that fit on the device at once (0: no cooperative launch)
+int cheb_fused_capacity() {
+    static int cap = -1;
+    if (cap < 0) {
+        int dev = 0, sms = 0, coop = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_fused, 256, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cap = 0;
+        } else {
+            cap = coop ? sms * per_sm : 0;
+        }
+    }
+    return cap;
+}
+
+// Barrier and failure flag shared by the fused mass inverses of one solve (its launches
+// run one after another on one stream)
+struct ChebSync {
+    DevBuf buf;
+    bem_status init(cudaStream_t s) {
+        BEM_TRY(buf.alloc(64, s));
+        BEM_CUDA_TRY(cudaMemsetAsync(buf.p, 0, 64, s));
+        return BEM_OK;
+    }
+    GridBarrier* bar() { return buf.as<GridBarrier>(); }
+    int* err() { return reinterpret_cast<int*>(static_cast<char*>(buf.p) + 32); }
+    void attach(MassOp& op) {
+        op.bar = bar();
+        op.err = err();
+    }
+    // a barrier wait that timed out in any of the solve's mass inverses
+    bem_status check() {
+        int h = 0;
+        BEM_CUDA_TRY(cudaMemcpy(&h, err(), sizeof(int), cudaMemcpyDeviceToHost));
+        if (h) {
+            set_error("mass inverse: a grid barrier wait timed out");
+            return BEM_E_INTERNAL;
+        }
+        return BEM_OK;
+    }
 };
 
 // M^-1 on the four blocks of R columns, Chebyshev on the Jacobi-scaled mass matrices
@@ -1045,6 +1198,29 @@ bem_status mass_solve(const MassOp& op, const double2* z, double2* y, int R, cud
     const int64_t n = op.M.n;
     const double theta = 0.5 * (CHEB_BETA + CHEB_ALPHA), delta = 0.5 * (CHEB_BETA - CHEB_ALPHA);
     const double sigma = theta / delta;
+    const int cap = op.bar ? cheb_fused_capacity() : 0;
+    if (cap > 0) {
+        // one cooperative launch for the whole iteration (steps + 1 launches otherwise):
+        // one item per thread where half the resident blocks suffice (so that a second
+        // such launch from another stream would still fit beside it)
+        const int64_t items = (int64_t)R * n;
+        const int G = (int)std::max<int64_t>(1, std::min<int64_t>(std::max(1, cap / 2), (items + 255) / 256));
+        BEM_CUDA_TRY(cudaMemsetAsync(op.bar, 0, sizeof(GridBarrier), s));
+        MassPair M = op.M;
+        const double2* zp = z;
+        double2 *yp = y, *rp = op.r, *ap = op.dA, *bp = op.dB;
+        int Rv = R, sv = steps;
+        double inv_theta = 1.0 / theta, sg = sigma, dl = delta;
+        GridBarrier* bar = op.bar;
+        int* err = op.err;
+        void* args[] = {&M, &zp, &yp, &rp, &ap, &bp, &Rv, &sv, &inv_theta, &sg, &dl, &bar, &err};
+        const int slot = g_capturing ? -1 : prof_begin("k_cheb_fused", s);
+        const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_cheb_fused, dim3(G), dim3(256), args, 0, s);
+        prof_end(slot, s);
+        BEM_CUDA_TRY(e);
+        if (!g_capturing) count_launch();
+        return BEM_OK;
+    }
     // small blocks by default: a step is FP64 work of a few rows per thread, spread over
     // every SM
     const int nb = tune_get(TUNE_CHEB, R, n, TuneChoice{64, 0, 0.0}).block;
@@ -1477,6 +1653,29 @@ __global__ void k_widen(const float2* __restrict__ x, int64_t count, double2* __
 // The tensor-core product against the FP32 CUDA-core product on seeded random
 // blocks whose entries have positive real parts (little cancellation, so the
 // relative difference measures the products' rounding and not the data).
+// The grid barrier's bounded wait: two cooperative blocks whose barrier count starts
+// past the grid size, so that it never completes; both must give up and flag it.
+// Returns the flag (1) times 1000 plus the elapsed seconds.
+bem_status selftest_barrier(double* result, cudaStream_t s) {
+    DevBuf b;
+    BEM_TRY(b.alloc(64, s));
+    BEM_CUDA_TRY(cudaMemsetAsync(b.p, 0, 64, s));
+    const unsigned int start = 7;  // > gridDim.x: the last arrival is never seen
+    BEM_CUDA_TRY(cudaMemcpyAsync(b.p, &start, sizeof(start), cudaMemcpyHostToDevice, s));
+    GridBarrier* bar = b.as<GridBarrier>();
+    int* err = reinterpret_cast<int*>(static_cast<char*>(b.p) + 32);
+    int rounds = 3;
+    void* args[] = {&bar, &err, &rounds};
+    const double t0 = now_seconds();
+    BEM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_barrier_probe, dim3(2), dim3(64), args, 0, s));
+    count_launch();
+    int h = 0;
+    BEM_CUDA_TRY(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    *result = 1000.0 * h + (now_seconds() - t0);
+    return BEM_OK;
+}
+
 bem_status selftest_tc(int R, double* rel_err, cudaStream_t s) {
     const int64_t Ne = 300, Ni = 170, n = 2 * Ne + 2 * Ni;
     const int RW = R + 7;
@@ -1780,7 +1979,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     const int RW = RB + 7;
     const bool tc_batches = use_tc && RB > 8 && !hc;  // high-contrast products: CUDA cores
     // Single-column inner solves of the refinement: the products run in double-float
-    // arithmetic while the inner residual is above DD_SWITCH of its right-hand side and
+    // arithmetic while the inner residual is above dd_switch of its right-hand side and
     // in FP32 after it.  GMRES tolerates product errors that grow as the residual falls
     // (the residual gap is a sum of each product's error times its coefficient in the
     // solution, and those coefficients shrink with the residual), so a 1e-7 FP32
@@ -1788,7 +1987,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     // refinement converges in one pass, without paying double-float on every product.
     const bool dd_single = mixed && RB == 1;
     double inner_progress = 1.0;
-    auto dd_now = [&]() { return dd_single && inner_progress > DD_SWITCH; };
+    auto dd_now = [&]() { return dd_single && inner_progress > o->dd_switch; };
     const size_t colb = (size_t)n * 16;
     DevBuf wz, wr, wa, wb, x32, tcw, tcerr, xsplit;
     if (dd_single) BEM_TRY(xsplit.alloc((size_t)(st ? std::max(n, nB) : n) * 16, s));
@@ -1809,6 +2008,9 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     mop.M.Ne = st_int ? 0 : Ne; mop.M.Ni = st && !st_int ? 0 : Ni; mop.M.n = n;
     mop.r = wr.as<double2>(); mop.dA = wa.as<double2>(); mop.dB = wb.as<double2>();
     mop.graphs = &graphs;
+    ChebSync csync;
+    BEM_TRY(csync.init(s));
+    if (ctx->exclusive) csync.attach(mop);
     // single-trace: the grid-B vectors of a product (tb1: M_B^-1 P_BA x, then M_B^-1 of the
     // grid-B product; tb2, tb3: input and output of the grid-B product, which reads and
     // writes up to 7 spare columns)
@@ -1827,6 +2029,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
         mopB.M.Ne = st_int ? Ne : 0; mopB.M.Ni = st_int ? 0 : Ni; mopB.M.n = nB;
         mopB.r = wrb.as<double2>(); mopB.dA = wab.as<double2>(); mopB.dB = wbb.as<double2>();
         mopB.graphs = &graphs;
+        if (ctx->exclusive) csync.attach(mopB);
     }
     // P_BA (rows on grid B) and P_AB = P_BA^T: P_ie and P_ei for the exterior variants
     const CsrBuf& csr_ba = st_int ? csr_t : csr_p;
@@ -2255,6 +2458,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
             return BEM_E_INTERNAL;
         }
     }
+    BEM_TRY(csync.check());
     if (result == BEM_E_NOT_CONVERGED)
         set_error("GMRES did not reach the tolerance within gmres_maxiter iterations; outputs hold the last iterate");
     if (rep) {
@@ -3084,7 +3288,7 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
     }
     const bool dd_single = mixed && RB == 1;
     double inner_progress = 1.0;
-    auto dd_now = [&]() { return dd_single && inner_progress > DD_SWITCH; };
+    auto dd_now = [&]() { return dd_single && inner_progress > o->dd_switch; };
     if (dd_single) BEM_TRY(xsplit.alloc((size_t)std::max(N, Nc) * 16, s));
     MassOp mf;
     mf.M.ci[0] = ell_f.ci.as<int32_t>(); mf.M.v[0] = ell_f.v.as<double>(); mf.M.W[0] = ell_f.W;
@@ -3093,6 +3297,9 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
     mf.M.Ne = N; mf.M.Ni = 0; mf.M.n = N;  // one vector of the screen per column
     mf.r = wr.as<double2>(); mf.dA = wa.as<double2>(); mf.dB = wb.as<double2>();
     mf.graphs = &graphs;
+    ChebSync csync;
+    BEM_TRY(csync.init(s));
+    if (ctx->exclusive) csync.attach(mf);
     MassOp mc;
     if (oo) {
         for (DevBuf* b : {&c1, &wrc, &wac, &wbc}) BEM_TRY(b->alloc(RB * colc, s));
@@ -3108,6 +3315,7 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
         mc.M.Ne = Nc; mc.M.Ni = 0; mc.M.n = Nc;
         mc.r = wrc.as<double2>(); mc.dA = wac.as<double2>(); mc.dB = wbc.as<double2>();
         mc.graphs = &graphs;
+        if (ctx->exclusive) csync.attach(mc);
     }
     Blocks<float2> BD32{}, BV32{};
     Blocks<double2> BD64{}, BV64{};
@@ -3275,6 +3483,7 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
     }
     cudaEventRecord(t_sol.b, s);
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    BEM_TRY(csync.check());
     if (result == BEM_E_NOT_CONVERGED)
         set_error("GMRES did not reach the tolerance within gmres_maxiter iterations; outputs hold the last iterate");
     if (rep) {

@@ -74,3 +74,41 @@ def test_graphs_on_and_off_agree_in_mixed_precision_and_many_instances(env):
     finally:
         for g in (ge, gi, g2e, g2i):
             bem.bem_grid_destroy(g)
+
+
+def test_grid_barrier_wait_is_bounded(env):
+    """The fused mass inverse synchronises its blocks with a grid barrier whose waits
+    give up after about a second: a barrier that can never complete (its count starts
+    past the grid size) is flagged, and the launch returns."""
+    bem, ctx = env
+    r = bem.bem_selftest(ctx, 3)
+    assert 1000.0 <= r < 1010.0, r
+
+
+def test_fused_mass_inverse_matches_the_servers_step_launches(env):
+    """Solves on an exclusive context run each mass inverse as one cooperative launch;
+    the server's contexts (whose solves overlap) launch one kernel per step.  The
+    arithmetic is the same item by item, so the traces agree to the run-to-run rounding
+    of the FP64 assembly's atomics."""
+    bem, ctx = env
+    ve, te, vi, ti = bi.transmission_pair(2, 2, seed=3, axes=[1.1, 0.9, 1.0])
+    ge, gi = bem.bem_grid_create(ctx, ve, te), bem.bem_grid_create(ctx, vi, ti)
+    d = np.array([[0.0, 0.0, 1.0]])
+    bem.bem_context_set_exclusive(ctx, True)
+    try:
+        a, ra = bem.bem_solve_transmission(ctx, ge, gi, 3.0, 2.0, 1.5, d)
+    finally:
+        bem.bem_context_set_exclusive(ctx, False)
+        bem.bem_grid_destroy(ge)
+        bem.bem_grid_destroy(gi)
+    srv = bem.bem_serve_create(max_inflight=1)
+    try:
+        t = bem.bem_serve_submit(srv, ve, te, vi, ti, 2.0, 3.0, 1.5, d, precision=bem.BEM_PREC_FP64)
+        assert bem.bem_serve_wait(srv, t, 120000.0)
+        out, info = bem.bem_serve_take(srv, t, 1, len(ve), len(vi))
+    finally:
+        bem.bem_serve_destroy(srv)
+    assert info["iterations"] == ra["iterations"]
+    for key in a:
+        e = np.linalg.norm(a[key][0] - out[key][0]) / np.linalg.norm(a[key][0])
+        assert e < 1e-12, (key, e)
