@@ -32,6 +32,7 @@
 #include <cmath>
 #include <complex>
 #include <functional>
+#include <mutex>
 #include <vector>
 
 namespace bem {
@@ -1142,22 +1143,30 @@ struct MassOp {
     int* err = nullptr;          // its barrier's failure flag (checked by the solve)
 };
 
-// Blocks of k_cheb_fused that fit on the device at once (0: no cooperative launch)
+// Blocks of k_cheb_fused that fit on the current device at once (0: no cooperative launch)
 int cheb_fused_capacity() {
-    static int cap = -1;
-    if (cap < 0) {
-        int dev = 0, sms = 0, coop = 0, per_sm = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+    static std::mutex mu;
+    static int cap[64];
+    static bool known[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 0;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!known[dev]) {
+        int sms = 0, coop = 0, per_sm = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_fused, 256, 0) != cudaSuccess) {
             cudaGetLastError();
-            cap = 0;
+            cap[dev] = 0;
         } else {
-            cap = coop ? sms * per_sm : 0;
+            cap[dev] = coop ? sms * per_sm : 0;
         }
+        known[dev] = true;
     }
-    return cap;
+    return cap[dev];
 }
 
 // Barrier and failure flag shared by the fused mass inverses of one solve (its launches
