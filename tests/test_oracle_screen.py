@@ -52,3 +52,18 @@ def test_coarse_opposite_order_preconditioner_is_rank_deficient():
     assert b["iters"] <= len(vc)  # the Krylov space lies in a space of that dimension
     # the iterate does not solve D phi = g: it differs from the mass-preconditioned one
     assert np.linalg.norm(a["phi"] - b["phi"]) > 1e-2 * np.linalg.norm(a["phi"])
+
+
+def test_screen_grid_geometry():
+    """The rectangle of the paper's screen: area 2.06 x 2, one normal for all triangles,
+    (nu + 1)(nv + 1) nodes, jitter kept in the plane and off the boundary."""
+    nu, nv = 7, 5
+    v, t = bi.screen_grid(nu, nv, jitter=0.3, seed=9)
+    assert len(v) == (nu + 1) * (nv + 1) and len(t) == 2 * nu * nv
+    a, b, c = v[t[:, 0]], v[t[:, 1]], v[t[:, 2]]
+    cr = np.cross(b - a, c - a)
+    area = 0.5 * np.linalg.norm(cr, axis=1).sum()
+    assert abs(area - 2.0 * np.sqrt(0.5 ** 2 + 2.0 ** 2)) < 1e-12
+    n = cr / np.linalg.norm(cr, axis=1)[:, None]
+    assert np.abs(n - n[0]).max() < 1e-12
+    assert np.abs((v - v[0]) @ n[0]).max() < 1e-12  # planar
