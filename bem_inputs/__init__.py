@@ -28,6 +28,7 @@ __all__ = [
     "perturb_square_grid",
     "cube_grid",
     "screen_grid",
+    "disk_grid",
     "serving_requests",
 ]
 
@@ -271,6 +272,40 @@ def screen_grid(nu: int, nv: int, jitter: float = 0.0, seed: int = 0):
             else:
                 tri += [[a, b, d], [b, c, d]]
     return v, np.array(tri, dtype=np.int32)
+
+
+def disk_grid(n: int):
+    """The unit disk in the plane z = 0 as a ring grid: the centre and n rings of radius
+    k/n with 6k nodes each (1 + 3n(n + 1) nodes, 6n^2 triangles), neighbouring rings
+    joined in order of angle; every triangle is counter-clockwise seen from +z."""
+    pts = [(0.0, 0.0)]
+    rings = [[0]]
+    for k in range(1, n + 1):
+        m = 6 * k
+        ids = []
+        for q in range(m):
+            th = 2.0 * np.pi * q / m
+            ids.append(len(pts))
+            pts.append((k / n * np.cos(th), k / n * np.sin(th)))
+        rings.append(ids)
+    tri = [(0, rings[1][q], rings[1][(q + 1) % 6]) for q in range(6)]
+    for k in range(2, n + 1):
+        inner, outer = rings[k - 1], rings[k]
+        mi, mo = len(inner), len(outer)
+        i = j = 0
+        while i < mi or j < mo:
+            if j < mo and (i >= mi or (j + 1) * mi <= (i + 1) * mo):
+                tri.append((inner[i % mi], outer[j % mo], outer[(j + 1) % mo]))
+                j += 1
+            else:
+                tri.append((inner[i % mi], outer[j % mo], inner[(i + 1) % mi]))
+                i += 1
+    v = np.array([(x, y, 0.0) for x, y in pts])
+    t = np.array(tri, dtype=np.int64)
+    a, b, c = v[t[:, 0]], v[t[:, 1]], v[t[:, 2]]
+    flip = np.cross(b - a, c - a)[:, 2] < 0
+    t[flip, 1], t[flip, 2] = t[flip, 2].copy(), t[flip, 1].copy()
+    return v, t.astype(np.int32)
 
 
 def perturb_square_grid(v, sigma: float, seed: int):

@@ -67,3 +67,24 @@ def test_screen_grid_geometry():
     n = cr / np.linalg.norm(cr, axis=1)[:, None]
     assert np.abs(n - n[0]).max() < 1e-12
     assert np.abs((v - v[0]) @ n[0]).max() < 1e-12  # planar
+
+
+def test_laplace_disk_screen_matches_the_closed_form():
+    """k = 0 on the unit disk: the double-layer density phi = (4/pi) sqrt(1 - r^2) has
+    normal derivative -1 on the disk (its Hankel transform is (4/pi)(sin x - x cos x)/x^3
+    and the Weber-Schafheitlin integrals give d_z u = -(1/2)(4/pi)(pi/2)), so D phi = 1.
+    The oracle's hypersingular system on the interior nodes with data <1, theta_i>
+    converges to it (relative M-norm error, the polygonal boundary included)."""
+    errs = []
+    for n in (3, 6):
+        v, t = bi.disk_grid(n)
+        I = np.flatnonzero(~boundary_nodes(t, len(v)))
+        D = assemble(v, t, 0.0)["D"]
+        M = mass_matrix(v, t)
+        phi = np.zeros(len(v), dtype=np.complex128)
+        phi[I] = np.linalg.solve(D[np.ix_(I, I)], (M @ np.ones(len(v)))[I])
+        r = np.linalg.norm(v[:, :2], axis=1)
+        exact = 4.0 / np.pi * np.sqrt(np.clip(1.0 - r ** 2, 0.0, None))
+        d = phi - exact
+        errs.append(np.sqrt(np.real(np.conj(d) @ M @ d) / (exact @ M @ exact)))
+    assert errs[0] > 1.8 * errs[1] and errs[1] < 0.025, errs
