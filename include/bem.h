@@ -147,7 +147,8 @@ BEM_API bem_status bem_profile_get(int index, char* name, int name_len, double* 
  * entry matches (ms: the measured time, may be NULL).  bem_tune_save writes the
  * table as JSON (format "bem-tune-1"); bem_tune_load merges such a file into it
  * (entries with the same key are replaced; malformed files: BEM_E_INVALID_ARG,
- * nothing merged).  The table functions need no GPU. */
+ * nothing merged).  The table functions need no GPU.  If the environment variable
+ * BEM_TUNE_FILE names such a file when the library is loaded, it is merged then. */
 BEM_API bem_status bem_autotune(bem_context* ctx, const bem_grid* ext, const bem_grid* intr, int32_t n_rhs);
 BEM_API bem_status bem_tune_get(const char* kernel, int32_t width, int64_t rows, int32_t* block,
                                 int32_t* variant, double* ms);

@@ -7,9 +7,11 @@
 #include "bem_internal.cuh"
 
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <sstream>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -175,8 +177,17 @@ bem_status bem_tune_load(const char* path) {
                     "tuning entry misses a field");
         const int k = kernel_id(name);
         BEM_REQUIRE(k >= 0, "unknown kernel in tuning file: " + name);
-        TuneEntry t{k, std::stoi(w), std::stoi(nl), {std::stoi(b), std::stoi(v), 0.0}};
-        if (json_field(obj, "ms", ms)) t.c.ms = std::stod(ms);
+        TuneEntry t{k, 0, 0, {0, 0, 0.0}};
+        try {  // numbers as written by bem_tune_save; anything else is a malformed file
+            t.width = std::stoi(w);
+            t.nlog2 = std::stoi(nl);
+            t.c.block = std::stoi(b);
+            t.c.variant = std::stoi(v);
+            if (json_field(obj, "ms", ms)) t.c.ms = std::stod(ms);
+        } catch (const std::exception&) {
+            set_error("tuning entry holds a malformed number");
+            return BEM_E_INVALID_ARG;
+        }
         BEM_REQUIRE(t.width >= 1 && t.width <= 256 && t.nlog2 >= 0 && t.nlog2 <= 62, "tuning entry out of range");
         BEM_REQUIRE(tune_choice_valid(k, t.c), "tuning entry names an unsupported block size or variant");
         got.push_back(t);
@@ -196,3 +207,15 @@ bem_status bem_tune_load(const char* path) {
 }
 
 }  // extern "C"
+
+namespace {
+// A tuning file named by the environment variable BEM_TUNE_FILE is merged into the table
+// when the library is loaded, so that shapes tuned once serve every later process.  A
+// missing or malformed file leaves the table empty (nothing else changes).
+struct TuneFileAtLoad {
+    TuneFileAtLoad() {
+        const char* path = std::getenv("BEM_TUNE_FILE");
+        if (path && *path) bem_tune_load(path);
+    }
+} g_tune_file_at_load;
+}  // namespace

@@ -61,6 +61,8 @@ def test_load_replaces_entries_with_the_same_key(bem, tmp_path):
     ([{"kernel": "nope", "width": 1, "n_log2": 16, "block": 256, "variant": 2}], "bem-tune-1"),
     ([{"kernel": "cheb", "width": 1, "n_log2": 16, "variant": 0}], "bem-tune-1"),
     ([{"kernel": "cheb", "width": 1, "n_log2": 16, "block": 64, "variant": 0}], "other"),
+    ([{"kernel": "cheb", "width": "one", "n_log2": 16, "block": 64, "variant": 0}], "bem-tune-1"),
+    ([{"kernel": "gemm32", "width": 1, "n_log2": 16, "block": 99999999999999999999, "variant": 2}], "bem-tune-1"),
 ])
 def test_malformed_files_are_rejected_and_merge_nothing(bem, tmp_path, entries, fmt):
     p = tmp_path / "bad.json"
@@ -71,3 +73,19 @@ def test_malformed_files_are_rejected_and_merge_nothing(bem, tmp_path, entries, 
     assert bem.bem_tune_count() == 0
     with pytest.raises(bem.BemError):
         bem.bem_tune_load(str(tmp_path / "missing.json"))
+
+
+def test_tuning_file_named_in_the_environment_is_loaded_with_the_library(tmp_path):
+    """BEM_TUNE_FILE: the table of a fresh process starts with that file's entries."""
+    import os
+    import subprocess
+    import sys
+    p = tmp_path / "env.json"
+    _write(p, [{"kernel": "gemm32", "width": 8, "n_log2": 14, "block": 512, "variant": 4, "ms": 2.5}])
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import paper_2206_00708_gb300 as b; "
+            "print(b.bem_tune_count(), b.bem_tune_get('gemm32', 8, 10000)[:2])")
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True,
+                         env=dict(os.environ, BEM_TUNE_FILE=str(p)), timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "1 (512, 4)", out.stdout
