@@ -279,17 +279,18 @@ typedef struct {
     int32_t tensor_cores;     /* BEM_PREC_MIXED batches of more than 8 right-hand sides: 1 (default)
                                  = products on the tcgen05 tensor cores (TF32, three-term split,
                                  FP32 accumulation), 0 = FP32 CUDA cores in groups of 8 columns    */
-    int32_t formulation;      /* BEM_FORM_* (default BEM_FORM_MTF); the single-trace systems are
-                                 available in bem_solve_transmission only (bem_solve_many and the
-                                 server solve the multiple-traces system)                         */
+    int32_t formulation;      /* BEM_FORM_* (default BEM_FORM_MTF); the single-trace and
+                                 high-contrast systems are available in bem_solve_transmission
+                                 only (bem_solve_many and the server solve the multiple-traces
+                                 system); high-contrast products always use the CUDA cores         */
     double  dd_switch;        /* BEM_PREC_MIXED, one right-hand side: the inner GMRES products run
                                  in double-float arithmetic while the inner residual is above
                                  dd_switch of its right-hand side, in FP32 below (default 1e-3;
                                  0: double-float throughout, 1: FP32 throughout)                  */
     int32_t cuda_graphs;      /* 1 (default): the fixed launch sequences of each iteration (the
                                  Chebyshev mass inverses) are captured once per solve and replayed
-                                 as CUDA graphs; 0: every kernel is launched on its own. Results
-                                 are identical either way.                                        */
+                                 as CUDA graphs; 0: every kernel is launched on its own.  Results
+                                 agree to the run-to-run rounding of the assembly either way.      */
 } bem_solve_opts;
 
 typedef struct {
