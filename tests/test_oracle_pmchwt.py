@@ -131,3 +131,26 @@ def test_muller_without_contrast_returns_the_incident_traces():
     for got, want in ((e["v_ext"], -pf), (e["w_ext"], -pg), (i["v_int"], pf), (i["w_int"], pg)):
         assert np.linalg.norm(got - want) < 1e-10 * np.linalg.norm(want)
     assert e["iters"] <= 2 and i["iters"] <= 2
+
+
+def test_single_trace_variants_at_high_contrast():
+    """The paper's high-contrast densities (rho_int / rho_ext = 2 / 0.11): every
+    single-trace system still converges to the Mie series (a misplaced density ratio
+    would show here first)."""
+    from oracle.mtf import mtf_blocks
+    from oracle.pmchwt import SINGLE_TRACE, solve_single_trace
+    d = [0.0, 0.0, 1.0]
+    k_e, k_i, rr = 1.0, 0.5, 2.0 / 0.11
+    errs = {f: [] for f in SINGLE_TRACE}
+    for L in (1, 2):
+        ve, te, vi, ti = bi.transmission_pair(L, L, seed=1)
+        B = mtf_blocks(ve, te, vi, ti, k_e, k_i)
+        ref = mie_potentials(ve, vi, d, k_e, k_i, rr)
+        for f in SINGLE_TRACE:
+            r = solve_single_trace(ve, te, vi, ti, k_e, k_i, rr, d, f, tol=1e-10, blocks=B)
+            errs[f].append([_merr(r[key], ref[i], B[M]) for i, (key, M) in enumerate(
+                [("v_ext", "Me"), ("w_ext", "Me"), ("v_int", "Mi"), ("w_int", "Mi")])])
+    for f in SINGLE_TRACE:
+        e = np.array(errs[f])
+        assert np.all(e[0] / e[1] > 2.0), (f, e)
+        assert e[1].max() < 0.1, (f, e)
