@@ -17,9 +17,16 @@ rho_int / rho_ext = 2; one unit plane wave along +z; GMRES tolerance 1e-8;
 "accuracy" gives its traces' relative L2 error against a converged FP64 solve
 (target <= 1e-6); "fp64" holds the plain-FP64 GPU arm.
 
-Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on a
-bounded sample of the same workload instead.  With torchrun (N > 1) every rank
-solves its own copy (the method has no data exchange between solves: replicas).
+Output (rank 0): one JSON line per section ({"section": name, ...}: autotune, mixed,
+fp64, e2e, serving, field, formulations, screen, cuda_graphs, cube, batching,
+uneven_instances, cpu_baseline), then, as the LAST line, the compact contract line
+(metric, value, latency, accuracy, fp64 arm, rooflines, cpu_baseline, e2e, clocks,
+launches; under 1.5 KB).  The headline steps are timed with CUDA events and no
+profiler events; the rooflines come from separate profiled steps of the same workload.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload
+on all host cores, extrapolated to one solve.  `--case` runs one small profiling case
+(for ncu) instead.  With torchrun (N > 1) every rank solves its own copy (the method
+has no data exchange between solves: replicas).
 """
 from __future__ import annotations
 
@@ -47,10 +54,26 @@ WORKLOAD_NAME = ("at-scale sphere: icosphere L5 exterior (10242 vertices) + L5 i
                  "40968 unknowns")
 L2_FLUSH_BYTES = 256 << 20
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk/SM x 2 flops x max SM clock
-# algorithmic flops per point pair of the regular-pair assembly kernels, counted from their source
-# (FMA = 2, sin/cos = 2, rsqrt = 1 each)
-FLOP_PER_POINT_PAIR = 93
-FLOP_PER_POINT_PAIR_FP32 = 105
+# Algorithmic flops per point pair of the regular-pair assembly, counted from the
+# oracle's formula (G, dG/dn(y), dG/dn(x) of Sec. 2.1 and the Galerkin sums of V, K, T,
+# with D formed per triangle pair from V and the integral of G), FMA = 2, add/mul = 1,
+# sqrt = rcp = 1, sincos = 2, summed over q first (the per-p outer sums amortised over
+# the 6 points q of the trial triangle):
+FLOP_COUNT_PER_POINT_PAIR = (
+    ("d = x - y", 3),
+    ("r^2 = d.d", 5),
+    ("r = sqrt(r^2), 1/r", 2),
+    ("phase k r", 1),
+    ("cos, sin of the phase", 2),
+    ("1 / (4 pi r)", 1),
+    ("G = exp(i k r) / (4 pi r)", 2),
+    ("F = G (1 - i k r) / r^2", 7),
+    ("d.n(y), d.n(x)", 10),
+    ("dG/dn(y) = F d.n(y), dG/dn(x) = -F d.n(x)", 4),
+    ("sum over q of (w L_b)(q) x {G, dG/dn(y), dG/dn(x)}, b = 0..2", 36),
+    ("sum over p of (w L_a)(p) x the three 3-vectors, per q", 18),
+)
+FLOP_PER_POINT_PAIR = sum(f for _, f in FLOP_COUNT_PER_POINT_PAIR)  # 91, FP64 and FP32 kernels alike
 
 
 # Unit-cube efficiency benchmarks (Sec. 5.5): the physics of the paper's table of physical
@@ -160,73 +183,137 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- CPU oracle sample
-def oracle_sample(seconds_hint=20.0, iters=None):
-    """Time the FP64 CPU oracle on a bounded sample of the workload and scale it
-    to one solve.  Returns (solves_per_s, sample_description, cores)."""
-    import bem_inputs as bi
+# GMRES iterations of one at-scale solve at tol 1e-8: the GPU path takes 205 in FP64 and
+# 205 inner iterations in the mixed mode, and the oracle's GMRES matches the FP64 path's
+# count within one (parity tests), so the extrapolated oracle solve uses the same count
+# in both arms.
+ORACLE_GMRES_ITERS = 205
+ORACLE_MATVEC_ROWS = 512
+_ORACLE_STATE = {}
+
+
+def _oracle_init():
+    """Pool worker set-up: the workload's grids, built once per worker process."""
+    _ORACLE_STATE["grids"] = workload_inputs()
+
+
+def _oracle_task(seed):
+    """Oracle assembly of all four operators for the test triangles of one random row of
+    each grid (the row's vertex star); returns (t_start, t_end, test triangles done)."""
     from oracle.helmholtz import assemble
     w = WORKLOAD
-    ve, te, vi, ti = workload_inputs()
-    rng = np.random.default_rng(0)
-    t_asm = 0.0
-    desc = []
+    if "grids" not in _ORACLE_STATE:
+        _oracle_init()
+    ve, te, vi, ti = _ORACLE_STATE["grids"]
+    rng = np.random.default_rng(seed)
+    t0 = time.monotonic()
+    done = 0
     for (v, t, k) in ((ve, te, w["k_ext"]), (vi, ti, w["k_int"])):
-        rows = rng.choice(len(v), 2, replace=False)
-        ntest = int(np.count_nonzero(np.isin(np.asarray(t), rows).any(axis=1)))
-        t0 = time.perf_counter()
+        rows = rng.choice(len(v), 1, replace=False)
+        done += int(np.count_nonzero(np.isin(np.asarray(t), rows).any(axis=1)))
         assemble(v, t, k, rows=rows)
-        dt = time.perf_counter() - t0
-        t_asm += dt / ntest * len(t)
-        desc.append(f"{ntest} test triangles x {len(t)} of V,K,T,D (scaled x{len(t) / ntest:.0f})")
+    return t0, time.monotonic(), done
+
+
+def oracle_sample_steps(steps, cores, seed=0):
+    """Run `steps` bounded samples of the FP64 CPU oracle on `cores` host cores and
+    extrapolate each to one at-scale solve.  Per sample: `cores` processes each assemble
+    V, K, T, D for one random row of each grid (about 6 test triangles x 20480 trial
+    triangles per grid); the wall time of that concurrent phase gives the oracle's
+    assembly rate in test triangles per second on `cores` cores, scaled to both grids'
+    40960 test triangles; then the dense strong-form matvec on a 512-row block of the
+    40968 x 40968 system (BLAS on `cores` threads), scaled by rows and by the GMRES
+    iteration count.  Mortar, mass, preconditioner and Arnoldi are not counted."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    ve, te, vi, ti = workload_inputs()
     n = 2 * len(ve) + 2 * len(vi)
-    blk = 512
+    nt_total = len(te) + len(ti)
+    rng = np.random.default_rng(seed)
+    blk = ORACLE_MATVEC_ROWS
     A = (rng.standard_normal((blk, n)) + 1j * rng.standard_normal((blk, n)))
     z = rng.standard_normal(n) + 1j * rng.standard_normal(n)
-    t0 = time.perf_counter()
-    reps = 3
-    for _ in range(reps):
-        A @ z
-    t_mv = (time.perf_counter() - t0) / reps * (n / blk)
-    it = iters if iters else 300
-    desc.append(f"dense strong-form matvec on a {blk}x{n} block (scaled x{n / blk:.0f}) x {it} GMRES iterations")
-    total = t_asm + it * t_mv
-    return 1.0 / total, "; ".join(desc) + "; mortar, mass and preconditioner setup not counted", 1
+    out = []
+    pool = None
+    if cores > 1:
+        # workers do their assembly on one thread each (they are the parallelism)
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        pool = ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"), initializer=_oracle_init)
+        list(pool.map(_oracle_task, [10_000 + i for i in range(cores)], chunksize=1))  # start + warm the workers
+    try:
+        for s in range(steps):
+            t_step = time.monotonic()
+            seeds = [1000 * (s + 1) + i for i in range(cores)]
+            res = list(pool.map(_oracle_task, seeds, chunksize=1)) if pool else [_oracle_task(seeds[0])]
+            wall = max(r[1] for r in res) - min(r[0] for r in res)
+            tris = sum(r[2] for r in res)
+            t_asm = wall / tris * nt_total
+            t0 = time.monotonic()
+            reps = 3
+            for _ in range(reps):
+                A @ z
+            t_mv = (time.monotonic() - t0) / reps * (n / blk)
+            total = t_asm + ORACLE_GMRES_ITERS * t_mv
+            out.append({"value": 1.0 / total, "step_ms": 1e3 * (time.monotonic() - t_step),
+                        "t_assembly_s": t_asm, "t_matvec_s": t_mv, "test_triangles": tris})
+    finally:
+        if pool:
+            pool.shutdown()
+    desc = (f"extrapolated: V,K,T,D of ~{out[-1]['test_triangles']} of {nt_total} test triangles "
+            f"(x{nt_total / out[-1]['test_triangles']:.0f}) + a {blk}-row block of the {n}-row dense matvec "
+            f"(x{n / blk:.0f}) x {ORACLE_GMRES_ITERS} GMRES iterations; mortar/mass/Arnoldi not counted")
+    return out, desc
 
 
-def run_oracle_child(iters):
-    """Run the oracle sample in a child with one BLAS/OpenMP thread."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import json,sys; sys.path.insert(0,%r); import bench; v,s,c=bench.oracle_sample(iters=%d); "
-            "print(json.dumps({'value':v,'sample':s,'cores':c}))" % (ROOT, iters))
-    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+def run_oracle_child(steps, cores):
+    """The oracle sample in a child process whose BLAS uses `cores` threads; returns
+    dict(steps=[...], sample=..., cores=...) or None if it failed."""
+    c = str(cores)
+    env = dict(os.environ, OMP_NUM_THREADS=c, OPENBLAS_NUM_THREADS=c, MKL_NUM_THREADS=c)
+    code = ("import json,sys; sys.path.insert(0,%r); import bench; r,d=bench.oracle_sample_steps(%d,%d); "
+            "print(json.dumps({'steps':r,'sample':d}))" % (ROOT, steps, cores))
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if p.returncode != 0:
+        sys.stderr.write(p.stderr[-2000:])
         return None
-    return json.loads(p.stdout.strip().splitlines()[-1])
+    r = json.loads(p.stdout.strip().splitlines()[-1])
+    r["cores"] = cores
+    return r
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
 # ----------------------------------------------------------------- reference arm
 def run_reference(args, rank):
+    """The FP64 CPU oracle as the reference arm: each step is one bounded sample of the
+    at-scale workload on all host cores, extrapolated to one solve (value = median over
+    the timed steps); a one-core sample is reported beside it."""
     if rank != 0:
         return
-    vals = []
-    sample = None
     t0 = time.perf_counter()
-    for _ in range(args.warmup + args.steps):
-        r = run_oracle_child(300)
-        if r is None:
-            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle sample failed to run"}))
-            return
-        vals.append(r["value"])
-        sample = r
-    vals = vals[args.warmup:]
-    value = statistics.median(vals)
+    cores = host_cores()
+    r = run_oracle_child(args.warmup + args.steps, cores)
+    one = run_oracle_child(1, 1)
+    if r is None:
+        print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle sample failed to run"}))
+        return
+    timed = r["steps"][args.warmup:]
+    value = statistics.median(s["value"] for s in timed)
+    ms_step = statistics.mean(s["step_ms"] for s in timed)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "extrapolated": True,
+        "ms_per_solve_extrapolated": 1e3 / value,
         "config": {"workload": WORKLOAD_NAME, "parallelism": "replicas"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": sample["cores"], "kind": "oracle",
-                         "sample": sample["sample"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": r["sample"],
+                         "one_core_value": (one["steps"][0]["value"] if one else None)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.perf_counter() - t0,
     }
@@ -586,7 +673,7 @@ def kernel_roofline(name, ms, n, te, ti, Ne, Ni, pp_cache):
             pp_cache["pp"] = (regular_point_pairs(te) + regular_point_pairs(ti)) / 2
         units = pp_cache["pp"]
         fp32 = name.startswith("k_regular32")
-        fpp = FLOP_PER_POINT_PAIR_FP32 if fp32 else FLOP_PER_POINT_PAIR
+        fpp = FLOP_PER_POINT_PAIR
         peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
         ach = fpp * units / avg_s / 1e12
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
@@ -595,6 +682,126 @@ def kernel_roofline(name, ms, n, te, ti, Ne, Ni, pp_cache):
                               "derived FP64 FMA peak: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"),
                 "flop_per_point_pair": fpp, "point_pairs_per_launch": units, "avg_launch_ms": ms / n}
     return {"kernel": name, "avg_launch_ms": ms / n}
+
+
+def _r(x, nd=4):
+    """x rounded to nd significant digits (keeps the contract line short)."""
+    if x is None or isinstance(x, (bool, int, str)):
+        return x
+    return float(f"{x:.{nd}g}")
+
+
+def _short_roof(r):
+    if not r:
+        return None
+    keep = ("kernel", "bound", "achieved", "peak", "unit", "frac", "traffic", "avg_launch_ms")
+    out = {k: _r(r.get(k)) for k in keep if k in r}
+    if "algorithmic_bytes_per_launch" in r:
+        out["bytes"] = _r(r["algorithmic_bytes_per_launch"])
+    if "flop_per_point_pair" in r:
+        out["flop_per_point_pair"] = r["flop_per_point_pair"]
+    return out
+
+
+CONTRACT_KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                 "scaling", "vs_baseline", "dtype", "data", "config", "latency_ms", "accuracy", "fp64",
+                 "speedup_vs_fp64", "roofline", "roofline_second", "cpu_baseline", "e2e", "clocks",
+                 "gpu_launches")
+CONTRACT_MAX_BYTES = 1536
+
+
+def contract_line(*, value, steps, warmup, world, times, clocks, launches, err=None, fp64=None, roof=None,
+                  roof2=None, cpu=None, e2e=None):
+    """The bench's last output line: the headline metric and its evidence, compact
+    (numbers to 4 significant digits, short strings) so that it stays under
+    CONTRACT_MAX_BYTES; the full sections are printed on earlier lines."""
+    line = {
+        "metric": METRIC, "value": _r(value), "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": _r(sum(times) / len(times)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_SHORT, "parallelism": "replicas" if world > 1 else "single",
+                   "precision": "mixed: FP32 assembly/matvec (c64), FP64 singular/mass/mortar/refinement",
+                   "l2": "inputs > L2 + 256 MB flush"},
+        "latency_ms": {"p50": _r(float(np.percentile(times, 50))), "p99": _r(float(np.percentile(times, 99)))},
+        "accuracy": (None if err is None else {"max": _r(max(err.values()), 3), "target": 1e-6,
+                                               "ok": max(err.values()) <= 1e-6}),
+        "fp64": (None if fp64 is None else {"value": _r(fp64["value"]),
+                                            "ms_per_step": _r(sum(fp64["times"]) / len(fp64["times"]))}),
+        "speedup_vs_fp64": _r(value / fp64["value"]) if fp64 else None,
+        "roofline": _short_roof(roof),
+        "roofline_second": _short_roof(roof2),
+        "cpu_baseline": (None if cpu is None else {"value": _r(cpu["value"]), "unit": UNIT, "cores": cpu["cores"],
+                                                   "kind": "oracle", "sample": cpu["sample_short"]}),
+        "e2e": (None if e2e is None else {"value": _r(e2e["value"]), "unit": UNIT,
+                                          "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                                          "d2h_bytes_per_step": e2e["d2h_bytes_per_step"]}),
+        "clocks": {"sm_mhz": clocks.get("sm_mhz"), "sm_max_mhz": clocks.get("sm_max_mhz"),
+                   "reasons": clocks.get("reasons", [])},
+        "gpu_launches": int(launches),
+    }
+    return line
+
+
+def emit_section(name, obj):
+    """One earlier output line per bench section."""
+    print(json.dumps({"section": name, **(obj if isinstance(obj, dict) else {"data": obj})}), flush=True)
+
+
+def emit_contract(line):
+    s = json.dumps(line, separators=(",", ":"))
+    if len(s) > CONTRACT_MAX_BYTES:  # never expected: drop the secondary evidence first
+        for k in ("roofline_second", "fp64"):
+            line[k] = None
+            s = json.dumps(line, separators=(",", ":"))
+            if len(s) <= CONTRACT_MAX_BYTES:
+                break
+    print(s, flush=True)
+
+
+WORKLOAD_SHORT = ("icosphere L5 ext (10242 v) + L5 int rotated+jittered (seed 2), k_ext 10, k_int 15, "
+                  "rho 2, 1 plane wave +z, GMRES tol 1e-8, 40968 unknowns")
+
+
+def run_case(args):
+    """Small standalone cases of the library's kernels for ncu captures (no timing, no
+    JSON): one assembly, one mortar, one transmission solve or one screen solve on the
+    synthetic icosphere grids."""
+    import bem_inputs as bi
+    import paper_2206_00708_gb300 as bem
+
+    ctx = bem.bem_context_create(0)
+    li = args.level if args.level_int is None else args.level_int
+    ve, te, vi, ti = bi.transmission_pair(args.level, li, seed=2)
+    ge = bem.bem_grid_create(ctx, ve, te)
+    gi = bem.bem_grid_create(ctx, vi, ti)
+    prec = bem.BEM_PREC_MIXED if args.mixed else bem.BEM_PREC_FP64
+    for _ in range(args.repeat):
+        if args.case == "assemble":
+            m = bem.bem_assemble(ctx, bem.BEM_OP_V, args.k, ge, precision=prec)
+            bem.bem_context_synchronize(ctx)
+            bem.bem_matrix_destroy(m)
+        elif args.case == "mortar":
+            s = bem.bem_projection(ctx, gi, ge)
+            bem.bem_sparse_destroy(s)
+        elif args.case == "screen":
+            vs, ts = bi.screen_grid(args.screen_cells, args.screen_cells, jitter=0.2, seed=71)
+            c = max(2, args.screen_cells // 3)
+            vc, tc = bi.screen_grid(c, c, jitter=0.2, seed=72)
+            gs, gc = bem.bem_grid_create(ctx, vs, ts), bem.bem_grid_create(ctx, vc, tc)
+            _, rep = bem.bem_solve_screen(ctx, gs, args.k, np.array([[1.0, 0.0, 0.0]]), coarse=gc,
+                                          precond=bem.BEM_SCREEN_OO, opts={"precision": prec})
+            bem.bem_grid_destroy(gs)
+            bem.bem_grid_destroy(gc)
+            print("iterations", rep["iterations"])
+        else:
+            dirs = np.array([[0.0, 0.0, 1.0]]) if args.rhs == 1 else bi.plane_wave_directions(args.rhs, seed=40)
+            _, rep = bem.bem_solve_transmission(ctx, ge, gi, 1.5 * args.k, args.k, 2.0, dirs,
+                                                opts={"precision": prec, "formulation": args.formulation})
+            print("iterations", rep["iterations"])
+    bem.bem_grid_destroy(ge)
+    bem.bem_grid_destroy(gi)
+    bem.bem_context_destroy(ctx)
+    print("ok")
 
 
 def main():
@@ -621,12 +828,25 @@ def main():
                     help="skip the many-directions section")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the seeded serving stream to replay (0: skip serving)")
+    ap.add_argument("--case", choices=["assemble", "solve", "mortar", "screen"], default=None,
+                    help="run one small profiling case instead of the benchmark (for ncu)")
+    ap.add_argument("--level", type=int, default=4, help="--case: exterior icosphere level")
+    ap.add_argument("--level-int", type=int, default=None, help="--case: interior level (default: --level)")
+    ap.add_argument("--k", type=float, default=10.0, help="--case: exterior wavenumber (interior 1.5 k)")
+    ap.add_argument("--repeat", type=int, default=1, help="--case: repetitions")
+    ap.add_argument("--mixed", action="store_true", help="--case: mixed precision instead of FP64")
+    ap.add_argument("--rhs", type=int, default=1, help="--case solve: plane waves (batched)")
+    ap.add_argument("--formulation", type=int, default=0, help="--case solve: BEM_FORM_* formulation")
+    ap.add_argument("--screen-cells", dest="screen_cells", type=int, default=60,
+                    help="--case screen: cells per side of the fine grid")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.case:
+        return run_case(args)
 
     import torch
     import torch.distributed as dist
@@ -667,15 +887,38 @@ def main():
         bem.bem_grid_destroy(gi)
         return rep
 
-    def timed(precision):
+    def timed(precision, roof_steps):
+        """Warm-up, then the timed steps (CUDA events around each solve on the launching
+        stream, no profiler events inside), then untimed profiled steps: one with every
+        launch bracketed (the kernel table) and `roof_steps` with only the two longest
+        kernels bracketed (their average launch durations for the rooflines)."""
         out = new_out()
         for _ in range(args.warmup):
             step(precision, out, w["tol"])
         torch.cuda.synchronize()
         barrier()
         torch.cuda.synchronize()
-        # one step with every launch timed by the library's event profiler: the kernel
-        # table, and the two longest kernels for the rooflines
+        times, reports = [], []
+        l0 = bem.bem_launch_count()
+        with ClockSampler(local) as clocks:
+            for _ in range(args.steps):
+                flush.zero_()  # L2 flush outside the timed events
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                reports.append(step(precision, out, w["tol"]))
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        launches = bem.bem_launch_count() - l0
+        barrier()
+        total = sum(times)
+        if world > 1:
+            tt = torch.tensor([total], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            total = float(tt.item())
+        # profiled steps (not part of the timed region)
         bem.bem_profile_select(None)
         bem.bem_profile_reset()
         bem.bem_profile_enable(True)
@@ -685,48 +928,29 @@ def main():
         bem.bem_profile_enable(False)
         table = bem.bem_profile_table()
         top = [p[0] for p in table[:2]]
-        # timed steps: only those two kernels are bracketed by events (on the library's
-        # stream), so the rooflines are measured over the timed region itself
-        times, reports = [], []
         bem.bem_profile_reset()
         bem.bem_profile_select(top)
-        l0 = bem.bem_launch_count()
-        with ClockSampler(local) as clocks:
-            for _ in range(args.steps):
-                flush.zero_()  # L2 flush outside the timed events
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                bem.bem_profile_enable(True)
-                e0.record(stream)
-                reports.append(step(precision, out, w["tol"]))
-                e1.record(stream)
-                e1.synchronize()
-                bem.bem_profile_enable(False)
-                times.append(e0.elapsed_time(e1))
-        torch.cuda.synchronize()
-        launches = bem.bem_launch_count() - l0
-        timed_prof = bem.bem_profile_table()
+        for _ in range(roof_steps):
+            flush.zero_()
+            bem.bem_profile_enable(True)
+            step(precision, out, w["tol"])
+            torch.cuda.synchronize()
+            bem.bem_profile_enable(False)
+        prof = bem.bem_profile_table()
         bem.bem_profile_select(None)
-        barrier()
-        total = sum(times)
-        if world > 1:
-            tt = torch.tensor([total], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            total = float(tt.item())
         return dict(out=out, times=times, reports=reports, launches=launches, clocks=clocks.summary(),
-                    value=world * args.steps / (total / 1e3), prof=timed_prof, table=table)
+                    value=world * args.steps / (total / 1e3), prof=prof, table=table)
 
     # launch shapes for this workload's sizes, timed once before any measured step
-    tuning = None
     if args.autotune:
         ge, gi = bem.bem_grid_create(ctx, xe, tre), bem.bem_grid_create(ctx, xi, tri_)
         t0 = time.perf_counter()
         bem.bem_autotune(ctx, ge, gi, 1)
         n_unk = 2 * (Ne + Ni)
         tuning = {"seconds": time.perf_counter() - t0,
-                  "chosen": {f"{k}/{w}": dict(zip(("block", "variant", "ms"), bem.bem_tune_get(k, w, n_unk)))
-                             for k, w in (("gemm32", 1), ("gemm32", 2), ("gemm32", 4), ("gemm32", 8),
-                                          ("gemv_dd", 1), ("cheb", 1), ("cheb", 8))}}
+                  "chosen": {f"{k}/{w_}": dict(zip(("block", "variant", "ms"), bem.bem_tune_get(k, w_, n_unk)))
+                             for k, w_ in (("gemm32", 1), ("gemm32", 2), ("gemm32", 4), ("gemm32", 8),
+                                           ("gemv_dd", 1), ("cheb", 1), ("cheb", 8))}}
         bem.bem_grid_destroy(ge)
         bem.bem_grid_destroy(gi)
         # in-solve check: one solve with the tuned shapes and one with the built-in ones,
@@ -758,9 +982,11 @@ def main():
         tuning["in_solve"] = {"tuned_ms_per_launch": per_tuned, "built_in_ms_per_launch": per_builtin,
                               "tuned_total_ms": tot_tuned, "built_in_total_ms": tot_builtin,
                               "kept": "tuned" if keep else "built-in"}
+        if rank == 0:
+            emit_section("autotune", tuning)
 
-    mixed = timed(bem.BEM_PREC_MIXED)
-    fp64 = None if args.no_fp64 else timed(bem.BEM_PREC_FP64)
+    mixed = timed(bem.BEM_PREC_MIXED, args.steps)
+    fp64 = None if args.no_fp64 else timed(bem.BEM_PREC_FP64, min(args.steps, 2))
 
     # accuracy: the mixed traces against a tightly converged FP64 solve of the same system
     err, err64 = None, None
@@ -775,11 +1001,31 @@ def main():
     pp_cache = {}
     roof = kernel_roofline(*mixed["prof"][0], te, ti, Ne, Ni, pp_cache) if mixed["prof"] else None
     roof2 = kernel_roofline(*mixed["prof"][1], te, ti, Ne, Ni, pp_cache) if len(mixed["prof"]) > 1 else None
-    roof64 = None
-    if fp64:
-        asm = [p for p in fp64["prof"] if p[0].startswith("k_regular")]
-        if asm:
-            roof64 = kernel_roofline(*asm[0], te, ti, Ne, Ni, pp_cache)
+    roof64 = [kernel_roofline(*p, te, ti, Ne, Ni, pp_cache) for p in fp64["prof"]] if fp64 else None
+
+    def solve_info(rep):
+        return {k: rep[k] for k in ("iterations", "outer_iterations", "residual", "t_assembly_ms", "t_mortar_ms",
+                                    "t_solve_ms")}
+
+    def lat(times):
+        return {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))}
+
+    if rank == 0:
+        emit_section("mixed", {"workload": WORKLOAD_NAME, "value": mixed["value"], "unit": UNIT,
+                               "times_ms": mixed["times"], "solve": solve_info(mixed["reports"][-1]),
+                               "gpu_launches": mixed["launches"], "clocks": mixed["clocks"],
+                               "accuracy": {"rel_l2_vs_fp64_converged": err, "target": 1e-6,
+                                            "reference": "FP64 GPU solve of the same system at GMRES tol 1e-12 "
+                                                         "(the FP64 path matches the CPU oracle to 1e-10)"},
+                               "roofline": roof, "roofline_second": roof2,
+                               "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in mixed["table"][:12]]})
+        if fp64:
+            emit_section("fp64", {"value": fp64["value"], "unit": UNIT, "times_ms": fp64["times"],
+                                  "latency_ms": lat(fp64["times"]), "rel_l2_vs_fp64_converged": err64,
+                                  "solve": solve_info(fp64["reports"][-1]), "rooflines": roof64,
+                                  "gpu_launches": fp64["launches"], "clocks": fp64["clocks"],
+                                  "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]}
+                                              for p in fp64["table"][:10]]})
 
     e2e = None
     if not args.no_e2e:
@@ -804,24 +1050,27 @@ def main():
         d2h = sum(int(a.numel() * a.element_size()) for a in hout.values())
         e2e = {"value": world * args.steps / sum(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
+        if rank == 0:
+            emit_section("e2e", dict(e2e, times_s=e2e_times,
+                                     note="bem_grid_create + bem_solve_transmission from pinned host buffers, "
+                                          "traces copied back to pinned host buffers, wall clock"))
 
-    serving = None
     if args.serve_requests > 0:
         reqs = serving_stream(args.serve_requests)
         sat = {p: run_serving(bem, reqs, p) for p in (bem.BEM_PREC_FP64, bem.BEM_PREC_MIXED)}
         rate = 0.7 * sat[bem.BEM_PREC_FP64]["solves_per_s"]
         rep = {p: run_serving(bem, reqs, p, rate=rate) for p in (bem.BEM_PREC_FP64, bem.BEM_PREC_MIXED)}
-        serving = {"workload": f"first {len(reqs)} requests of the seeded serving stream (seed 50): ellipsoids "
-                               "with semi-axes U[0.5,1.5], icosphere levels 2-4 per grid, k_ext U[1,8], "
-                               "k_int/k_ext U[1.2,2], rho log-U[0.1,10], 1-16 plane waves; 4 requests in flight",
-                   "saturated": {"fp64": sat[bem.BEM_PREC_FP64], "mixed": sat[bem.BEM_PREC_MIXED]},
-                   "poisson": {"rate_per_s": rate, "fp64": rep[bem.BEM_PREC_FP64], "mixed": rep[bem.BEM_PREC_MIXED]}}
+        if rank == 0:
+            emit_section("serving", {
+                "workload": f"first {len(reqs)} requests of the seeded serving stream (seed 50): ellipsoids "
+                            "with semi-axes U[0.5,1.5], icosphere levels 2-4 per grid, k_ext U[1,8], "
+                            "k_int/k_ext U[1.2,2], rho log-U[0.1,10], 1-16 plane waves; 4 requests in flight",
+                "saturated": {"fp64": sat[bem.BEM_PREC_FP64], "mixed": sat[bem.BEM_PREC_MIXED]},
+                "poisson": {"rate_per_s": rate, "fp64": rep[bem.BEM_PREC_FP64], "mixed": rep[bem.BEM_PREC_MIXED]}})
 
-    field = None
     if args.field and rank == 0:
-        field = run_field(bem, ctx, w, ve, te, vi, ti, mixed["out"])
+        emit_section("field", run_field(bem, ctx, w, ve, te, vi, ti, mixed["out"]))
 
-    single = None
     if args.single_trace and rank == 0:
         # the other formulations on the same workload: mixed-precision solves timed like the
         # headline, accuracy against each one's own converged FP64 solve, and the distance
@@ -860,85 +1109,45 @@ def main():
                 entry["rel_l2_vs_fp64_converged"] = perr
                 entry["max_err"] = max(perr.values())
             single[name] = entry
+        emit_section("formulations", single)
 
-    screen = None
     if args.screen and rank == 0:
-        screen = run_screen(bem, ctx)
+        emit_section("screen", run_screen(bem, ctx))
 
-    graphs = None
     if args.graphs and rank == 0:
-        graphs = run_graphs(bem, ctx)
+        emit_section("cuda_graphs", run_graphs(bem, ctx))
 
-    cube = None
     if args.cube and rank == 0:
-        cube = run_cube(bem, ctx)
+        emit_section("cube", run_cube(bem, ctx))
 
-    batching = None
-    if args.batching:
+    if args.batching and rank == 0:
         bw = BATCH_WORKLOAD
-        batching = {"workload": f"unit sphere, icosphere L{bw['level']} on both grids (seed {bw['seed']}), "
-                                f"k_ext={bw['k_ext']}, k_int={bw['k_int']}, rho={bw['rho']}, {bw['n_dirs']} plane "
-                                f"waves in one call vs {bw['n_single']} of them one call each; mixed precision "
-                                "with tensor-core products (one batch of 64) and with CUDA-core products "
-                                "(batches of 8), FP64 (batches of 8)",
-                    "mixed_tensor_cores": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 1, 0),
-                    "mixed_cuda_cores_8": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 0, 8),
-                    "fp64": run_batching(bem, ctx, bem.BEM_PREC_FP64),
-                    "uneven_instances": run_uneven(bem, ctx)}
+        emit_section("batching", {
+            "workload": f"unit sphere, icosphere L{bw['level']} on both grids (seed {bw['seed']}), "
+                        f"k_ext={bw['k_ext']}, k_int={bw['k_int']}, rho={bw['rho']}, {bw['n_dirs']} plane "
+                        f"waves in one call vs {bw['n_single']} of them one call each; mixed precision "
+                        "with tensor-core products (one batch of 64) and with CUDA-core products "
+                        "(batches of 8), FP64 (batches of 8)",
+            "mixed_tensor_cores": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 1, 0),
+            "mixed_cuda_cores_8": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 0, 8),
+            "fp64": run_batching(bem, ctx, bem.BEM_PREC_FP64)})
+        emit_section("uneven_instances", run_uneven(bem, ctx))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = run_oracle_child(int(mixed["reports"][-1]["iterations"]))
+        cores = host_cores()
+        r = run_oracle_child(1, cores)
         if r is not None:
-            cpu = {"value": r["value"], "unit": UNIT, "cores": r["cores"], "kind": "oracle", "sample": r["sample"]}
-
-    def lat(times):
-        return {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))}
-
-    def solve_info(rep):
-        return {k: rep[k] for k in ("iterations", "outer_iterations", "residual", "t_assembly_ms", "t_mortar_ms",
-                                    "t_solve_ms")}
+            cpu = {"value": r["steps"][-1]["value"], "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": r["sample"],
+                   "sample_short": (f"extrapolated from ~{r['steps'][-1]['test_triangles']} test triangles + "
+                                    f"a {ORACLE_MATVEC_ROWS}-row matvec block x {ORACLE_GMRES_ITERS} iterations")}
+            emit_section("cpu_baseline", cpu)
 
     if rank == 0:
-        m = mixed
-        line = {
-            "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": sum(m["times"]) / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "parallelism": "replicas" if world > 1 else "single",
-                       "precision": "mixed: FP32 regular-pair assembly and matvec (complex64 operators), FP64 "
-                                    "singular pairs, mass, mortar, Arnoldi and iterative-refinement residual",
-                       "l2": "256 MB write between steps; operators (6.7 GB complex64) exceed L2"},
-            "latency_ms": lat(m["times"]),
-            "accuracy": (None if err is None else {
-                "rel_l2_vs_fp64_converged": err, "max": max(err.values()), "target": 1e-6,
-                "ok": max(err.values()) <= 1e-6,
-                "reference": "FP64 GPU solve of the same system at GMRES tol 1e-12 (the FP64 path "
-                             "matches the CPU oracle to 1e-10 in the parity tests)"}),
-            "fp64": (None if not fp64 else {
-                "value": fp64["value"], "unit": UNIT, "ms_per_step": sum(fp64["times"]) / args.steps,
-                "latency_ms": lat(fp64["times"]), "rel_l2_vs_fp64_converged": err64,
-                "solve": solve_info(fp64["reports"][-1]), "roofline": roof64, "gpu_launches": fp64["launches"],
-                "clocks": fp64["clocks"]}),
-            "speedup_vs_fp64": (m["value"] / fp64["value"]) if fp64 else None,
-            "clocks": m["clocks"],
-            "gpu_launches": int(m["launches"]),
-            "roofline": roof,
-            "roofline_second": roof2,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "serving": serving,
-            "batching": batching,
-            "field": field,
-            "formulations": single,
-            "cube": cube,
-            "cuda_graphs": graphs,
-            "screen": screen,
-            "autotune": tuning,
-            "solve": solve_info(m["reports"][-1]),
-            "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in m["table"][:10]],
-        }
-        print(json.dumps(line), flush=True)
+        emit_contract(contract_line(value=mixed["value"], steps=args.steps, warmup=args.warmup, world=world,
+                                    times=mixed["times"], clocks=mixed["clocks"], launches=mixed["launches"],
+                                    err=err, fp64=fp64, roof=roof, roof2=roof2, cpu=cpu, e2e=e2e))
     bem.bem_context_destroy(ctx)
     if world > 1:
         dist.destroy_process_group()

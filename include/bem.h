@@ -238,6 +238,8 @@ BEM_API bem_status bem_projection(bem_context* ctx, const bem_grid* a, const bem
  *                1048576 candidate pairs, returns BEM_E_INVALID_ARG and writes no
  *                entries.  The entries are written asynchronously on the context's
  *                stream: synchronise before reading them.
+ * Part-way through, the call waits for the context's stream: it reads the number of
+ * candidate pairs back to the host before it launches the clipping kernel.
  * The first call on a device looks up the array's device address (once per device);
  * make that first call before any stream capture.  All calls share the one array and
  * it keeps the last call's contents (the call clears what must start at zero), so

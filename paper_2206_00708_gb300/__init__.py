@@ -363,7 +363,16 @@ def bem_context_create(device=0, stream=None):
     if stream is not None:
         s = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(_lib.bem_context_create(int(device), s, C.byref(h)))
+    _CTX_DEVICE[h.value] = int(device)
     return h
+
+
+_CTX_DEVICE = {}  # context handle -> CUDA device index it was created on
+
+
+def bem_context_device(ctx):
+    """The CUDA device index of a context created by this binding (None if unknown)."""
+    return _CTX_DEVICE.get(ctx.value if hasattr(ctx, "value") else ctx)
 
 
 def bem_context_set_exclusive(ctx, exclusive=True):
@@ -375,6 +384,7 @@ def bem_context_set_exclusive(ctx, exclusive=True):
 
 def bem_context_destroy(ctx):
     _check(_lib.bem_context_destroy(ctx))
+    _CTX_DEVICE.pop(ctx.value if hasattr(ctx, "value") else ctx, None)
 
 
 def bem_context_synchronize(ctx):
@@ -463,6 +473,17 @@ def bem_projection_noalloc(ctx, a, b, row, col, val, center=None):
     callers whose device memory comes from their own budgeted pool or whose loop
     cannot pay for an allocation.  Returns the number of COO entries written.  The
     library's fixed scratch array is shared by all calls: serialise calls."""
+    import torch
+    for name, t, dt in (("row", row, torch.int32), ("col", col, torch.int32), ("val", val, torch.float64)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must have dtype {dt} (got {t.dtype})")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        dev = bem_context_device(ctx)
+        if dev is not None and t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the context on cuda:{dev}")
     c = None
     if center is not None:
         c = (C.c_double * 3)(*[float(x) for x in center])

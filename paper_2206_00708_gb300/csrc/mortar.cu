@@ -311,13 +311,17 @@ extern "C" bem_status bem_projection_noalloc(bem_context* ctx, const bem_grid* a
     int2* cand = reinterpret_cast<int2*>(base + NOALLOC_CAND_OFF);
     // the array keeps the previous call's contents: the counter must start at zero
     BEM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+    BEM_REQUIRE(a->nt > 0 && b->nt > 0, "grid without triangles");
     BEM_LAUNCH(k_discs, (unsigned)((a->nt + 127) / 128), 128, 0, s, a->xyz.as<double>(), a->tri.as<int32_t>(),
                a->nt, c0, da);
+    BEM_CHECK_LAUNCH();
     BEM_LAUNCH(k_discs, (unsigned)((b->nt + 127) / 128), 128, 0, s, b->xyz.as<double>(), b->tri.as<int32_t>(),
                b->nt, c0, db);
+    BEM_CHECK_LAUNCH();
     unsigned gx = (unsigned)std::min<int64_t>((b->nt + 255) / 256, 64);
     dim3 grid(gx, (unsigned)std::min<int64_t>(a->nt, 65535));
     BEM_LAUNCH(k_candidates, grid, 256, 0, s, da, a->nt, db, b->nt, counter, cand, NOALLOC_MAX_CAND);
+    BEM_CHECK_LAUNCH();
     unsigned long long ncand = 0;
     BEM_CUDA_TRY(cudaMemcpyAsync(&ncand, counter, sizeof(ncand), cudaMemcpyDeviceToHost, s));
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -328,8 +332,10 @@ extern "C" bem_status bem_projection_noalloc(bem_context* ctx, const bem_grid* a
     *nnz = need;
     BEM_REQUIRE(capacity >= need, "output capacity " + std::to_string(capacity) + " is below the " +
                                       std::to_string(need) + " entries needed");
-    if (ncand > 0)
+    if (ncand > 0) {
         BEM_LAUNCH(k_clip, (unsigned)((ncand + 127) / 128), 128, 0, s, a->xyz.as<double>(), a->tri.as<int32_t>(),
                    b->xyz.as<double>(), b->tri.as<int32_t>(), cand, (int64_t)ncand, c0, row, col, val);
+        BEM_CHECK_LAUNCH();
+    }
     return BEM_OK;
 }

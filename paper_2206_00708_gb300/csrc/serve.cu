@@ -62,7 +62,9 @@ struct bem_server {
 namespace bem {
 namespace {
 
-// Upper estimate of a request's device working set.
+// Upper estimate of a request's device working set.  A served request always solves
+// the multiple-traces system (bem_request carries no formulation): its operators are the
+// four blocks of each grid, its Krylov vectors have 2 N_e + 2 N_i entries.
 int64_t working_set_bytes(int64_t ne, int64_t ni, int precision, int maxiter, int n_rhs) {
     const int64_t n = 2 * ne + 2 * ni;
     const int64_t esz = precision == BEM_PREC_MIXED ? 8 : 16;

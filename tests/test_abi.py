@@ -52,3 +52,17 @@ def test_host_side_errors_without_gpu(bem):
         bem.bem_context_create(0)
     assert ei.value.status in (bem.BEM_E_CUDA, bem.BEM_E_INVALID_ARG)
     assert isinstance(bem.library().bem_last_error(), bytes)
+
+
+def test_noalloc_wrapper_rejects_unsuitable_outputs_before_calling(bem):
+    """bem_projection_noalloc writes with device stores into the caller's arrays: the
+    binding must refuse host tensors, wrong dtypes and strided views before the call."""
+    import ctypes
+    import torch
+    fake_ctx = ctypes.c_void_p(0x1000)
+    i32 = torch.zeros(16, dtype=torch.int32)
+    f64 = torch.zeros(16, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        bem.bem_projection_noalloc(fake_ctx, None, None, i32, i32, f64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        bem.bem_projection_noalloc(fake_ctx, None, None, i32.numpy(), i32, f64)

@@ -21,3 +21,9 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["value"] > 0.0 and d["unit"] == "solves/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    # the value is an extrapolation from a bounded sample, and says so; ms_per_step is the
+    # measured time of one sampled step (it fits the run), the extrapolated solve time is
+    # given separately
+    assert d["extrapolated"] is True and "extrapolated" in d["cpu_baseline"]["sample"]
+    assert d["ms_per_solve_extrapolated"] > d["ms_per_step"]
+    assert d["cpu_baseline"]["one_core_value"] > 0.0

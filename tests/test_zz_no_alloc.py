@@ -97,3 +97,19 @@ def test_noalloc_rejects_sizes_beyond_its_limits(env):
     assert e.value.status == bem.BEM_E_INVALID_ARG and "32768" in str(e.value)
     bem.bem_grid_destroy(g6)
     bem.bem_grid_destroy(g)
+
+
+def test_noalloc_rejects_unsuitable_device_outputs(env):
+    """Wrong dtypes and strided views are refused by the binding before the call."""
+    bem, ctx, torch = env
+    v, t = bi.icosphere(1)
+    g = bem.bem_grid_create(ctx, v, t)
+    i32 = torch.zeros(4096, dtype=torch.int32, device="cuda")
+    f64 = torch.zeros(4096, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError, match="dtype"):
+        bem.bem_projection_noalloc(ctx, g, g, i32.long(), i32, f64)
+    with pytest.raises(ValueError, match="dtype"):
+        bem.bem_projection_noalloc(ctx, g, g, i32, i32, f64.float())
+    with pytest.raises(ValueError, match="contiguous"):
+        bem.bem_projection_noalloc(ctx, g, g, i32[::2], i32[::2], f64[::2])
+    bem.bem_grid_destroy(g)
