@@ -256,12 +256,31 @@ BEM_API bem_status bem_sparse_copy_out(bem_context* ctx, const bem_sparse* s, in
                                int32_t* col, double* val, int64_t capacity);
 
 /* ---------------------------------------------------------------- solve
- * Incident field: n_rhs plane waves amp_r * exp(i k_ext x . d_r) (paper
- * eq. planewave), dirs [n_rhs*3] unit vectors, amps [n_rhs] (NULL = all 1).  */
+ * Incident field (paper Sec. 2: u_inc in the exterior medium, data f_j = <u_inc, theta_j>
+ * and g_j = <du_inc/dn, theta_j> on the exterior grid, the right-hand side of
+ * eq. mtf:discrete), n_rhs of them, of one kind:
+ *   BEM_INC_PLANE_WAVE (0, the default of a zeroed struct): amp_r exp(i k_ext x . d_r)
+ *     (eq. planewave); dirs [n_rhs*3] unit vectors.
+ *   BEM_INC_POINT_SOURCE: amp_r exp(i k_ext |x - s_r|) / (4 pi |x - s_r|), the field of
+ *     a monopole at s_r in the exterior medium; sources [n_rhs*3] positions, which the
+ *     caller places in the exterior medium and off the surface (not checked).
+ *   BEM_INC_USER_TRACES: the weak-form data themselves, f and g [n_rhs*N_ext]
+ *     (right-hand side r at offset r*N_ext), on the host, or on the device when the
+ *     solve's on_device flag is set.  Any incident field, or any data of the form
+ *     (<a, theta_j>, <b, theta_j>), enters this way.
+ * amps [n_rhs] (NULL = all 1) scale plane waves and point sources.
+ * bem_solve_screen uses g only (the Neumann data of its one grid).  */
+#define BEM_INC_PLANE_WAVE   0
+#define BEM_INC_POINT_SOURCE 1
+#define BEM_INC_USER_TRACES  2
 typedef struct {
     int32_t         n_rhs;
-    const double*   dirs;
-    const bem_c128* amps;
+    const double*   dirs;     /* BEM_INC_PLANE_WAVE: [n_rhs*3] unit directions              */
+    const bem_c128* amps;     /* plane waves and point sources: [n_rhs] or NULL             */
+    int32_t         kind;     /* BEM_INC_*                                                   */
+    const double*   sources;  /* BEM_INC_POINT_SOURCE: [n_rhs*3] source positions           */
+    const bem_c128* f;        /* BEM_INC_USER_TRACES: [n_rhs*N_ext] <u_inc, theta_j>         */
+    const bem_c128* g;        /* BEM_INC_USER_TRACES: [n_rhs*N_ext] <du_inc/dn, theta_j>     */
 } bem_incident;
 
 typedef struct {

@@ -19,7 +19,9 @@ so its solution is the derived one with the interior potentials negated.  The
 derived variant is the default, so that v_int, w_int are phi_int, psi_int.
 
 Data (Sec. 2.2 and eq. planewave): f_j = <u_inc, theta_j>, g_j = <d u_inc/dn, theta_j>
-on the exterior grid with u_inc = exp(i k_ext x . d), d u_inc/dn = i k_ext (d . n) u_inc.
+on the exterior grid with u_inc = exp(i k_ext x . d), d u_inc/dn = i k_ext (d . n) u_inc;
+the same tests of a point source's field (the fundamental solution with its pole in
+the exterior medium), or data given by the caller.
 
 Mass-matrix preconditioning (Sec. 3.3): left multiplication by
 blockdiag(M_ext^-1, M_ext^-1, M_int^-1, M_int^-1).  GMRES (Sec. 5.1): no restart,
@@ -47,6 +49,30 @@ def plane_wave_data(v, tri, k, d, amp=1.0):
     d = np.asarray(d, dtype=np.float64)
     u = amp * np.exp(1j * k * (X @ d))  # [T,q]
     dn = 1j * k * (geo["n"] @ d)[:, None] * u
+    wj = w[None, :] * geo["J"][:, None]
+    fl = np.einsum("tq,tq,qa->ta", wj, u, L)
+    gl = np.einsum("tq,tq,qa->ta", wj, dn, L)
+    N = len(v)
+    f = np.zeros(N, dtype=np.complex128)
+    g = np.zeros(N, dtype=np.complex128)
+    np.add.at(f, tri, fl)
+    np.add.at(g, tri, gl)
+    return f, g
+
+
+def point_source_data(v, tri, k, src, amp=1.0):
+    """f, g [N] of the point-source field u = amp exp(i k r) / (4 pi r), r = |x - src|
+    (the fundamental solution with its pole at src), tested with P1 functions:
+    du/dn = u (i k - 1/r) ((x - src) . n) / r."""
+    tri = np.asarray(tri, dtype=np.int64)
+    geo = triangle_geometry(v, tri)
+    pts, w = triangle_rule_degree4()
+    L = shape_values(pts)
+    X = geo["a"][:, None, :] + pts[None, :, 0:1] * geo["e1"][:, None, :] + pts[None, :, 1:2] * geo["e2"][:, None, :]
+    R = X - np.asarray(src, dtype=np.float64)
+    r = np.linalg.norm(R, axis=-1)  # [T,q]
+    u = amp * np.exp(1j * k * r) / (4.0 * np.pi * r)
+    dn = u * (1j * k - 1.0 / r) * np.einsum("tqd,td->tq", R, geo["n"]) / r
     wj = w[None, :] * geo["J"][:, None]
     fl = np.einsum("tq,tq,qa->ta", wj, u, L)
     gl = np.einsum("tq,tq,qa->ta", wj, dn, L)
@@ -152,12 +178,14 @@ def gmres(matvec, b, tol, maxiter):
 
 def solve_transmission(v_ext, t_ext, v_int, t_int, k_ext, k_int, rho_int_over_rho_ext, d,
                        tol=1e-8, maxiter=2000, variant="derived", n_singular=4, blocks=None,
-                       center=(0.0, 0.0, 0.0)):
-    """Full oracle solve.  Returns dict(v_ext, w_ext, v_int, w_int, iters, hist, blocks)."""
+                       center=(0.0, 0.0, 0.0), data=None):
+    """Full oracle solve for the plane wave along d, or for the weak-form data
+    data = (f, g) on the exterior grid (any incident field) when given.
+    Returns dict(v_ext, w_ext, v_int, w_int, iters, hist, blocks)."""
     if blocks is None:
         blocks = mtf_blocks(v_ext, t_ext, v_int, t_int, k_ext, k_int, n_singular, center)
     A = mtf_matrix(blocks, rho_int_over_rho_ext, variant)
-    f, g = plane_wave_data(v_ext, t_ext, k_ext, d)
+    f, g = plane_wave_data(v_ext, t_ext, k_ext, d) if data is None else data
     Ne, Ni = len(v_ext), len(v_int)
     b = np.concatenate([-f, -g, np.zeros(2 * Ni, dtype=np.complex128)])
     SA, Sb = strong_form(A, b, blocks["Me"], blocks["Mi"])

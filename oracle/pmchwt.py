@@ -131,14 +131,15 @@ def single_trace_rhs(blocks, rho_int_over_rho_ext, formulation, f, g):
 
 
 def solve_single_trace(v_ext, t_ext, v_int, t_int, k_ext, k_int, rho_int_over_rho_ext, d, formulation,
-                       tol=1e-8, maxiter=2000, n_singular=4, blocks=None, center=(0.0, 0.0, 0.0)):
-    """Full oracle solve of one of SINGLE_TRACE.  Returns dict(v_ext, w_ext, v_int, w_int,
-    iters, hist, blocks) with the potentials in the conventions of the MTF solve."""
+                       tol=1e-8, maxiter=2000, n_singular=4, blocks=None, center=(0.0, 0.0, 0.0), data=None):
+    """Full oracle solve of one of SINGLE_TRACE for the plane wave along d, or for the
+    exterior-grid data data = (f, g) when given.  Returns dict(v_ext, w_ext, v_int,
+    w_int, iters, hist, blocks) with the potentials in the conventions of the MTF solve."""
     if blocks is None:
         blocks = mtf_blocks(v_ext, t_ext, v_int, t_int, k_ext, k_int, n_singular, center)
     r = rho_int_over_rho_ext
     A = single_trace_matrix(blocks, r, formulation)
-    f, g = plane_wave_data(v_ext, t_ext, k_ext, d)
+    f, g = plane_wave_data(v_ext, t_ext, k_ext, d) if data is None else data
     b = single_trace_rhs(blocks, r, formulation, f, g)
     Me, Mi, Pie = blocks["Me"], blocks["Mi"], blocks["Pie"]
     ext = formulation.endswith("_ext")

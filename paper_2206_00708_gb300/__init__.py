@@ -48,7 +48,59 @@ class bem_c128(C.Structure):
 
 
 class bem_incident(C.Structure):
-    _fields_ = [("n_rhs", C.c_int32), ("dirs", C.POINTER(C.c_double)), ("amps", C.POINTER(bem_c128))]
+    _fields_ = [("n_rhs", C.c_int32), ("dirs", C.POINTER(C.c_double)), ("amps", C.POINTER(bem_c128)),
+                ("kind", C.c_int32), ("sources", C.POINTER(C.c_double)), ("f", C.POINTER(bem_c128)),
+                ("g", C.POINTER(bem_c128))]
+
+
+BEM_INC_PLANE_WAVE, BEM_INC_POINT_SOURCE, BEM_INC_USER_TRACES = 0, 1, 2
+
+
+def _incident(dirs=None, amps=None, sources=None, traces=None, on_device=False):
+    """bem_incident for plane waves (dirs [n, 3]), point sources (sources [n, 3]) or the
+    caller's weak-form data (traces = (f, g), each [n, N_ext]; f may be None for a
+    screen; NumPy arrays, or CUDA tensors with on_device).  Returns (struct, n_rhs,
+    arrays kept alive for the call)."""
+    inc = bem_incident()
+    keep = []
+    given = [x is not None for x in (dirs, sources, traces)]
+    if sum(given) != 1:
+        raise ValueError("give exactly one of dirs, sources, traces")
+    if traces is not None:
+        f, g = traces
+        inc.kind = BEM_INC_USER_TRACES
+        n_rhs = None
+        for name, a in (("f", f), ("g", g)):
+            if a is None:
+                continue
+            if isinstance(a, np.ndarray):
+                if on_device:
+                    raise ValueError("traces must be CUDA tensors when on_device is set")
+                a = np.ascontiguousarray(np.atleast_2d(a), dtype=np.complex128)
+            elif not on_device:
+                raise ValueError("traces must be NumPy arrays unless on_device is set")
+            keep.append(a)
+            n_rhs = int(a.shape[0]) if a.ndim == 2 else 1
+            setattr(inc, name, C.cast(_ptr(a)[0], C.POINTER(bem_c128)))
+        if n_rhs is None:
+            raise ValueError("traces need g")
+        inc.n_rhs = n_rhs
+        return inc, n_rhs, keep
+    pos = np.ascontiguousarray(np.atleast_2d(dirs if dirs is not None else sources), dtype=np.float64)
+    keep.append(pos)
+    n_rhs = pos.shape[0]
+    inc.n_rhs = n_rhs
+    if dirs is not None:
+        inc.kind = BEM_INC_PLANE_WAVE
+        inc.dirs = pos.ctypes.data_as(C.POINTER(C.c_double))
+    else:
+        inc.kind = BEM_INC_POINT_SOURCE
+        inc.sources = pos.ctypes.data_as(C.POINTER(C.c_double))
+    if amps is not None:
+        amp_arr = (bem_c128 * n_rhs)(*[_c128(a) for a in np.atleast_1d(amps)])
+        keep.append(amp_arr)
+        inc.amps = C.cast(amp_arr, C.POINTER(bem_c128))
+    return inc, n_rhs, keep
 
 
 class bem_solve_opts(C.Structure):
@@ -278,21 +330,14 @@ def bem_profile_reset():
 BEM_SCREEN_MASS, BEM_SCREEN_OO = 0, 1
 
 
-def bem_solve_screen(ctx, screen, k, dirs, coarse=None, precond=BEM_SCREEN_MASS, amps=None, opts=None, out=None,
-                     on_device=False):
-    """Neumann screen D phi = gamma_N u_inc (mass or opposite-order preconditioning).
+def bem_solve_screen(ctx, screen, k, dirs=None, coarse=None, precond=BEM_SCREEN_MASS, amps=None, opts=None, out=None,
+                     on_device=False, sources=None, traces=None):
+    """Neumann screen D phi = gamma_N u_inc (mass or opposite-order preconditioning), for
+    plane waves (dirs), point sources (sources) or the caller's data (traces = (None, g)).
 
     Returns (phi [n_rhs, N] complex128 (zero on the screen's boundary), report dict);
     raises BemError on failure (BEM_E_NOT_CONVERGED with .outputs and .report)."""
-    dirs = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
-    n_rhs = dirs.shape[0]
-    inc = bem_incident()
-    inc.n_rhs = n_rhs
-    inc.dirs = dirs.ctypes.data_as(C.POINTER(C.c_double))
-    amp_arr = None
-    if amps is not None:
-        amp_arr = (bem_c128 * n_rhs)(*[_c128(a) for a in np.atleast_1d(amps)])
-        inc.amps = C.cast(amp_arr, C.POINTER(bem_c128))
+    inc, n_rhs, _keep = _incident(dirs, amps, sources, traces, on_device)
     o = _opts(opts)
     N = bem_grid_num_vertices(screen)
     if out is None:
@@ -521,24 +566,18 @@ def bem_solve_opts_default():
     return o
 
 
-def bem_solve_transmission(ctx, ext, intr, k_int, k_ext, rho_int_over_rho_ext, dirs, amps=None, opts=None,
-                           out=None, on_device=False):
-    """Solve the mass-preconditioned MTF for plane waves `dirs` [n_rhs, 3].
+def bem_solve_transmission(ctx, ext, intr, k_int, k_ext, rho_int_over_rho_ext, dirs=None, amps=None, opts=None,
+                           out=None, on_device=False, sources=None, traces=None):
+    """Solve the mass-preconditioned MTF (or opts["formulation"]) for plane waves
+    `dirs` [n_rhs, 3], point sources `sources` [n_rhs, 3] (with amplitudes `amps`), or
+    the caller's weak-form data `traces` = (f, g), each [n_rhs, N_ext].
 
     out: optional dict of preallocated outputs v_ext, w_ext [n_rhs, N_ext] and
     v_int, w_int [n_rhs, N_int] (complex128 NumPy arrays, or CUDA tensors with
     on_device=True).  Returns (outputs dict, report dict); raises BemError on
     failure (BEM_E_NOT_CONVERGED included, with the outputs attached as .outputs).
     """
-    dirs = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
-    n_rhs = dirs.shape[0]
-    inc = bem_incident()
-    inc.n_rhs = n_rhs
-    inc.dirs = dirs.ctypes.data_as(C.POINTER(C.c_double))
-    amp_arr = None
-    if amps is not None:
-        amp_arr = (bem_c128 * n_rhs)(*[_c128(a) for a in np.atleast_1d(amps)])
-        inc.amps = C.cast(amp_arr, C.POINTER(bem_c128))
+    inc, n_rhs, _keep = _incident(dirs, amps, sources, traces, on_device)
     if opts is None:
         opts = bem_solve_opts_default()
     elif isinstance(opts, dict):

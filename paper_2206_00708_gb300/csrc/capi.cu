@@ -69,6 +69,36 @@ using namespace bem;
         BEM_CUDA_TRY(cudaSetDevice((ctx)->device));            \
     } while (0)
 
+namespace {
+
+// Validation of an incident field (bem_incident) on the host: kind, sizes and finite,
+// unit or present inputs.
+bem_status check_incident(const bem_incident* inc) {
+    BEM_REQUIRE(inc != nullptr && inc->n_rhs >= 1, "incident field needs n_rhs >= 1");
+    BEM_REQUIRE(inc->kind == BEM_INC_PLANE_WAVE || inc->kind == BEM_INC_POINT_SOURCE ||
+                    inc->kind == BEM_INC_USER_TRACES, "unknown incident-field kind");
+    if (inc->kind == BEM_INC_USER_TRACES) {
+        BEM_REQUIRE(inc->g != nullptr, "BEM_INC_USER_TRACES needs g (and f, except for a screen)");
+        return BEM_OK;
+    }
+    const double* p = inc->kind == BEM_INC_PLANE_WAVE ? inc->dirs : inc->sources;
+    BEM_REQUIRE(p != nullptr, inc->kind == BEM_INC_PLANE_WAVE ? "plane waves need dirs" : "point sources need sources");
+    for (int r = 0; r < inc->n_rhs; ++r) {
+        const double* d = p + 3 * r;
+        BEM_REQUIRE(std::isfinite(d[0]) && std::isfinite(d[1]) && std::isfinite(d[2]),
+                    "incident directions or source positions are not finite");
+        if (inc->kind == BEM_INC_PLANE_WAVE) {
+            const double nd = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            BEM_REQUIRE(std::fabs(nd - 1.0) < 1e-6, "incident directions must be unit vectors");
+        }
+        if (inc->amps)
+            BEM_REQUIRE(std::isfinite(inc->amps[r].re) && std::isfinite(inc->amps[r].im), "amplitude not finite");
+    }
+    return BEM_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* bem_last_error(void) { return g_last_error.c_str(); }
@@ -369,7 +399,8 @@ bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const b
                                   bem_c128* w_int, int on_device, bem_solve_report* rep) {
     CTX_GUARD(ctx);
     BEM_REQUIRE(ext != nullptr && intr != nullptr, "null grid");
-    BEM_REQUIRE(inc != nullptr && inc->n_rhs >= 1 && inc->dirs != nullptr, "incident field needs n_rhs >= 1 and dirs");
+    BEM_TRY(check_incident(inc));
+    BEM_REQUIRE(inc->kind != BEM_INC_USER_TRACES || inc->f != nullptr, "BEM_INC_USER_TRACES needs f and g");
     BEM_REQUIRE(v_ext && w_ext && v_int && w_int, "null output array");
     BEM_REQUIRE(std::isfinite(rho_int_over_rho_ext) && rho_int_over_rho_ext > 0.0, "density ratio must be > 0");
     BEM_REQUIRE(std::isfinite(k_int.re) && std::isfinite(k_int.im) && std::isfinite(k_ext.re) &&
@@ -387,11 +418,6 @@ bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const b
     BEM_REQUIRE(o.formulation >= BEM_FORM_MTF && o.formulation <= BEM_FORM_HC_INT_DIR, "unknown formulation");
     BEM_REQUIRE(o.cuda_graphs == 0 || o.cuda_graphs == 1, "cuda_graphs must be 0 or 1");
     BEM_REQUIRE(o.dd_switch >= 0.0 && o.dd_switch <= 1.0, "dd_switch must be in [0, 1]");
-    for (int r = 0; r < inc->n_rhs; ++r) {
-        const double* d = inc->dirs + 3 * r;
-        const double nd = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        BEM_REQUIRE(std::isfinite(nd) && std::fabs(nd - 1.0) < 1e-6, "incident directions must be unit vectors");
-    }
     return solve_transmission_impl(ctx, ext, intr, k_int, k_ext, rho_int_over_rho_ext, inc, &o, v_ext, w_ext, v_int,
                                    w_int, on_device, rep);
 }
@@ -410,7 +436,7 @@ bem_status bem_solve_screen(bem_context* ctx, const bem_grid* screen, const bem_
     BEM_REQUIRE(screen != nullptr, "null screen grid");
     BEM_REQUIRE(precond == BEM_SCREEN_MASS || precond == BEM_SCREEN_OO, "unknown screen preconditioner");
     BEM_REQUIRE(precond == BEM_SCREEN_MASS || coarse != nullptr, "the opposite-order preconditioner needs a grid");
-    BEM_REQUIRE(inc != nullptr && inc->n_rhs >= 1 && inc->dirs != nullptr, "incident field needs n_rhs >= 1 and dirs");
+    BEM_TRY(check_incident(inc));
     BEM_REQUIRE(phi != nullptr, "null output array");
     BEM_REQUIRE(std::isfinite(k.re) && std::isfinite(k.im), "wavenumber is not finite");
     bem_solve_opts o;
@@ -423,11 +449,6 @@ bem_status bem_solve_screen(bem_context* ctx, const bem_grid* screen, const bem_
     BEM_REQUIRE(o.batch_columns >= 0 && o.batch_columns <= 128, "batch_columns must be in [0, 128]");
     BEM_REQUIRE(o.cuda_graphs == 0 || o.cuda_graphs == 1, "cuda_graphs must be 0 or 1");
     BEM_REQUIRE(o.dd_switch >= 0.0 && o.dd_switch <= 1.0, "dd_switch must be in [0, 1]");
-    for (int r = 0; r < inc->n_rhs; ++r) {
-        const double* d = inc->dirs + 3 * r;
-        const double nd = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        BEM_REQUIRE(std::isfinite(nd) && std::fabs(nd - 1.0) < 1e-6, "incident directions must be unit vectors");
-    }
     return solve_screen_impl(ctx, screen, coarse, k, inc, &o, precond, phi, on_device, rep);
 }
 

@@ -107,6 +107,46 @@ __global__ void k_plane_wave(const TriRec* __restrict__ rec, const int32_t* __re
     }
 }
 
+// The same data for point sources (the incident-field kind BEM_INC_POINT_SOURCE):
+// u_inc = amp exp(i k r) / (4 pi r) with r = |x - s|, du_inc/dn = u_inc (i k - 1/r) ((x - s).n) / r.
+// src [R][3], amps [R] (device); blockIdx.y = right-hand side
+__global__ void k_point_source(const TriRec* __restrict__ rec, const int32_t* __restrict__ tri, int64_t nt,
+                               double kr, double ki, const double* __restrict__ src,
+                               const double2* __restrict__ amps, int64_t Ne, double2* __restrict__ f,
+                               double2* __restrict__ g) {
+    const int r = blockIdx.y;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const double3 c = make_double3(src[3 * r], src[3 * r + 1], src[3 * r + 2]);
+    const double2 amp = amps[r];
+    const TriRec& R = rec[t];
+    double2 fa[3] = {}, ga[3] = {};
+    for (int p = 0; p < 6; ++p) {
+        const double dx = R.q[p][0] - c.x, dy = R.q[p][1] - c.y, dz = R.q[p][2] - c.z;
+        const double rr = sqrt(dx * dx + dy * dy + dz * dz);
+        const double ri = 1.0 / rr;
+        double sn, cs;
+        sincos(kr * rr, &sn, &cs);
+        const double mag = ((ki != 0.0) ? exp(-ki * rr) : 1.0) * ri * 0.07957747154594767;  // 1 / (4 pi r)
+        const double2 u = cmul(amp, make_double2(mag * cs, mag * sn));
+        const double dn = (dx * R.n[0] + dy * R.n[1] + dz * R.n[2]) * ri;
+        const double2 du = cmul(make_double2((-ki - ri) * dn, kr * dn), u);  // (i k - 1/r) (x - s).n / r u
+        for (int a = 0; a < 3; ++a) {
+            fa[a].x += R.wl[p][a] * u.x;
+            fa[a].y += R.wl[p][a] * u.y;
+            ga[a].x += R.wl[p][a] * du.x;
+            ga[a].y += R.wl[p][a] * du.y;
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        const int64_t v = r * Ne + tri[3 * t + a];
+        atomicAdd(&f[v].x, fa[a].x);
+        atomicAdd(&f[v].y, fa[a].y);
+        atomicAdd(&g[v].x, ga[a].x);
+        atomicAdd(&g[v].y, ga[a].y);
+    }
+}
+
 // b = [-f, -g, 0, 0] per right-hand side
 __global__ void k_rhs_pack(const double2* __restrict__ f, const double2* __restrict__ g, int64_t Ne, int64_t n,
                            double2* __restrict__ b) {
@@ -1904,6 +1944,40 @@ bem_status autotune_impl(bem_context* ctx, const bem_grid* ge, const bem_grid* g
     return BEM_OK;
 }
 
+// f, g [R][N] of right-hand sides r0 .. r0 + R - 1 of an incident field on grid g (plane
+// waves, point sources, or the caller's data copied in); wave is a device buffer of at
+// least 5 RB doubles, h_wave its pinned host staging (amplitudes, then directions or
+// source positions); inputs_on_device tells where the caller's f, g live.
+bem_status incident_data(const bem_incident* inc, int r0, int R, int RB, const bem_grid* g, bem_c128 k,
+                         double* h_wave, DevBuf& wave, double2* f, double2* gv, bool inputs_on_device,
+                         cudaStream_t s) {
+    const int64_t N = g->nv;
+    if (inc->kind == BEM_INC_USER_TRACES) {
+        const cudaMemcpyKind kind = inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (inc->f) BEM_CUDA_TRY(cudaMemcpyAsync(f, inc->f + (int64_t)r0 * N, (size_t)R * N * 16, kind, s));
+        else BEM_CUDA_TRY(cudaMemsetAsync(f, 0, (size_t)R * N * 16, s));
+        BEM_CUDA_TRY(cudaMemcpyAsync(gv, inc->g + (int64_t)r0 * N, (size_t)R * N * 16, kind, s));
+        return BEM_OK;
+    }
+    const double* pos = inc->kind == BEM_INC_POINT_SOURCE ? inc->sources : inc->dirs;
+    // amplitudes first (2 R doubles: 16-byte aligned complex values), then 3 R coordinates
+    for (int r = 0; r < R; ++r) {
+        h_wave[2 * r] = inc->amps ? inc->amps[r0 + r].re : 1.0;
+        h_wave[2 * r + 1] = inc->amps ? inc->amps[r0 + r].im : 0.0;
+        for (int d = 0; d < 3; ++d) h_wave[2 * RB + 3 * r + d] = pos[3 * (r0 + r) + d];
+    }
+    BEM_CUDA_TRY(cudaMemcpyAsync(wave.p, h_wave, (size_t)5 * RB * 8, cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemsetAsync(f, 0, (size_t)R * N * 16, s));
+    BEM_CUDA_TRY(cudaMemsetAsync(gv, 0, (size_t)R * N * 16, s));
+    if (inc->kind == BEM_INC_POINT_SOURCE)
+        BEM_LAUNCH(k_point_source, dim3(blocks_for(g->nt, 128), R), 128, 0, s, g->rec.as<TriRec>(),
+                   g->tri.as<int32_t>(), g->nt, k.re, k.im, wave.as<double>() + 2 * RB, wave.as<double2>(), N, f, gv);
+    else
+        BEM_LAUNCH(k_plane_wave, dim3(blocks_for(g->nt, 128), R), 128, 0, s, g->rec.as<TriRec>(),
+                   g->tri.as<int32_t>(), g->nt, k.re, k.im, wave.as<double>() + 2 * RB, wave.as<double2>(), N, f, gv);
+    return BEM_OK;
+}
+
 bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const bem_grid* gi, bem_c128 k_int,
                                    bem_c128 k_ext, double rho_ratio, const bem_incident* inc,
                                    const bem_solve_opts* o, bem_c128* v_ext, bem_c128* w_ext, bem_c128* v_int,
@@ -2291,18 +2365,8 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     cudaEventRecord(t_sol.a, s);
     for (int r0 = 0; r0 < inc->n_rhs; r0 += RB) {
         const int R = std::min(RB, inc->n_rhs - r0);
-        // amplitudes first (2 R doubles: 16-byte aligned complex values), then directions
-        for (int r = 0; r < R; ++r) {
-            W.h_wave[2 * r] = inc->amps ? inc->amps[r0 + r].re : 1.0;
-            W.h_wave[2 * r + 1] = inc->amps ? inc->amps[r0 + r].im : 0.0;
-            for (int d = 0; d < 3; ++d) W.h_wave[2 * RB + 3 * r + d] = inc->dirs[3 * (r0 + r) + d];
-        }
-        BEM_CUDA_TRY(cudaMemcpyAsync(wave.p, W.h_wave, (size_t)5 * RB * 8, cudaMemcpyHostToDevice, s));
-        BEM_CUDA_TRY(cudaMemsetAsync(fvec.p, 0, (size_t)R * Ne * 16, s));
-        BEM_CUDA_TRY(cudaMemsetAsync(gvec.p, 0, (size_t)R * Ne * 16, s));
-        BEM_LAUNCH(k_plane_wave, dim3(blocks_for(ge->nt, 128), R), 128, 0, s, ge->rec.as<TriRec>(),
-                   ge->tri.as<int32_t>(), ge->nt, k_ext.re, k_ext.im, wave.as<double>() + 2 * RB,
-                   wave.as<double2>(), Ne, fvec.as<double2>(), gvec.as<double2>());
+        BEM_TRY(incident_data(inc, r0, R, RB, ge, k_ext, W.h_wave, wave, fvec.as<double2>(), gvec.as<double2>(),
+                              on_device != 0, s));
         if (hc) {
             // high-contrast data (weak form), from F = -(f; g):
             //   exterior Neumann ((1/r) D^_i M_e^-1 f; g), Dirichlet (f; r V^_i M_e^-1 g);
@@ -3421,17 +3485,8 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
     cudaEventRecord(t_sol.a, s);
     for (int r0 = 0; r0 < inc->n_rhs; r0 += RB) {
         const int R = std::min(RB, inc->n_rhs - r0);
-        for (int r = 0; r < R; ++r) {
-            W.h_wave[2 * r] = inc->amps ? inc->amps[r0 + r].re : 1.0;
-            W.h_wave[2 * r + 1] = inc->amps ? inc->amps[r0 + r].im : 0.0;
-            for (int d = 0; d < 3; ++d) W.h_wave[2 * RB + 3 * r + d] = inc->dirs[3 * (r0 + r) + d];
-        }
-        BEM_CUDA_TRY(cudaMemcpyAsync(wave.p, W.h_wave, (size_t)5 * RB * 8, cudaMemcpyHostToDevice, s));
-        BEM_CUDA_TRY(cudaMemsetAsync(fvec.p, 0, (size_t)R * colf, s));
-        BEM_CUDA_TRY(cudaMemsetAsync(gvec.p, 0, (size_t)R * colf, s));
-        BEM_LAUNCH(k_plane_wave, dim3(blocks_for(gf->nt, 128), R), 128, 0, s, gf->rec.as<TriRec>(),
-                   gf->tri.as<int32_t>(), gf->nt, k.re, k.im, wave.as<double>() + 2 * RB, wave.as<double2>(), N,
-                   fvec.as<double2>(), gvec.as<double2>());
+        BEM_TRY(incident_data(inc, r0, R, RB, gf, k, W.h_wave, wave, fvec.as<double2>(), gvec.as<double2>(),
+                              on_device != 0, s));
         // g_i = <gamma_N u_inc, theta_i>: the preconditioned right-hand side
         BEM_TRY(precondition(true, gvec.as<double2>(), sb.as<double2>(), R, CHEB_STEPS));
         std::vector<double> beta(R), tol_abs(R), rn(R), est(R), inner_tol(R);

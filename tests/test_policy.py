@@ -1,7 +1,7 @@
 """Separation of the product path from the oracle (CPU only): nothing in the library
 package or the shared input generators imports the oracle, the CUDA sources do not
 reference it, and bench.py imports it only inside its CPU-baseline sample (the
-function the `cpu_baseline` and `--impl reference` legs call)."""
+pool task that the `cpu_baseline` and `--impl reference` legs run)."""
 import ast
 import os
 
@@ -41,4 +41,4 @@ def test_bench_imports_the_oracle_only_in_its_cpu_sample():
             p = parents.get(node)
             while p is not None and not isinstance(p, ast.FunctionDef):
                 p = parents.get(p)
-            assert p is not None and p.name == "oracle_sample", (mod, getattr(p, "name", None))
+            assert p is not None and p.name == "_oracle_task", (mod, getattr(p, "name", None))
