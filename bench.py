@@ -639,35 +639,33 @@ def run_uneven(bem, ctx):
             "iterations_one_call_each": int(its_single), "all_converged": all(r["converged"] for r in reps)}
 
 
-# DRAM bytes (read + write) per launch of k_gemm32<1> over its algorithmic bytes, from an
-# ncu capture of the current kernel on the L4 pair (423.0 MB against 420.1 MB per launch);
-# the traffic of a launch grows with the operator bytes, so the at-scale figure is this
-# ratio times the at-scale algorithmic bytes
-GEMM32_TRAFFIC_RATIO = 423020458 / 420086016
+def tiled_operator_bytes(N, entry_bytes):
+    """Bytes of one grid's operators in the tiled storage that one product streams:
+    V and D as the 64 x 64 tiles of their upper tile triangles, K as all tiles (T = K^T
+    is not stored)."""
+    nt = (N + 63) // 64
+    return (nt * (nt + 1) + nt * nt) * 64 * 64 * entry_bytes
+
+
+# DRAM bytes (read + write) per launch of the single-column tile product over the bytes it
+# streams, from an ncu capture of the current kernel (None until captured)
+TILE_TRAFFIC_RATIO = None
 
 
 def kernel_roofline(name, ms, n, te, ti, Ne, Ni, pp_cache):
     """Roofline entry of one profiled kernel (per-launch averages)."""
     avg_s = ms / n / 1e3
-    m = re.search(r"<(\d+)>", name)
-    cols = int(m.group(1)) if m else 1  # right-hand sides per launch
-    if name.startswith("k_gemm32") or name.startswith("k_gemv_dd"):
+    if name.startswith("k_tile<"):
+        # the product streams the tiled operators of both grids once per launch
         peak, kind = hbm_peak()
-        bytes_ = 8 * 4 * (Ne * Ne + Ni * Ni)  # 8 complex64 blocks read once per operator product
+        eb = 16 if "c128" in name else 8
+        bytes_ = tiled_operator_bytes(Ne, eb) + tiled_operator_bytes(Ni, eb)
         ach = bytes_ / avg_s / 1e9
-        traffic = bytes_ * GEMM32_TRAFFIC_RATIO if name == "k_gemm32<1>" else None
+        traffic = bytes_ * TILE_TRAFFIC_RATIO if (TILE_TRAFFIC_RATIO and name == "k_tile<c64,f32,1>") else None
         return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": traffic, "traffic_note": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the L4 "
-                                                     "capture, scaled to this launch by the operator bytes")
-                if traffic else None,
-                "peak_kind": kind, "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": ms / n}
-    if name.startswith("k_gemm64"):
-        flops = 8 * 4 * (Ne * Ne + Ni * Ni) * cols  # 4 DFMA = 8 flops per complex entry and column
-        ach = flops / avg_s / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_kind": "derived FP64 FMA peak: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
-                "flops_per_launch": flops, "avg_launch_ms": ms / n}
+                "traffic": traffic, "peak_kind": kind, "algorithmic_bytes_per_launch": bytes_,
+                "bytes_note": "V, D upper tile triangles + K, 64 x 64 tiles, both grids (T = K^T not stored)",
+                "avg_launch_ms": ms / n}
     if name.startswith("k_regular"):
         if "pp" not in pp_cache:
             pp_cache["pp"] = (regular_point_pairs(te) + regular_point_pairs(ti)) / 2
@@ -949,39 +947,9 @@ def main():
         n_unk = 2 * (Ne + Ni)
         tuning = {"seconds": time.perf_counter() - t0,
                   "chosen": {f"{k}/{w_}": dict(zip(("block", "variant", "ms"), bem.bem_tune_get(k, w_, n_unk)))
-                             for k, w_ in (("gemm32", 1), ("gemm32", 2), ("gemm32", 4), ("gemm32", 8),
-                                           ("gemv_dd", 1), ("cheb", 1), ("cheb", 8))}}
+                             for k, w_ in (("cheb", 1), ("cheb", 8))}}
         bem.bem_grid_destroy(ge)
         bem.bem_grid_destroy(gi)
-        # in-solve check: one solve with the tuned shapes and one with the built-in ones,
-        # the products timed by the library's profiler; the faster set is kept (the
-        # tuner times its candidates alone, and a solve interleaves them with other work)
-        import tempfile
-
-        def product_ms():
-            bem.bem_profile_select(["k_gemm32<1>", "k_gemv_dd"])
-            bem.bem_profile_reset()
-            bem.bem_profile_enable(True)
-            step(bem.BEM_PREC_MIXED, new_out(), w["tol"])
-            torch.cuda.synchronize()
-            bem.bem_profile_enable(False)
-            rows = {name: (ms, n) for name, ms, n in bem.bem_profile_table()}
-            bem.bem_profile_select(None)
-            return {name: ms / max(n, 1) for name, (ms, n) in rows.items()}, sum(ms for ms, _ in rows.values())
-
-        step(bem.BEM_PREC_MIXED, new_out(), w["tol"])  # warm
-        with tempfile.TemporaryDirectory() as td:
-            path = os.path.join(td, "tune.json")
-            bem.bem_tune_save(path)
-            per_tuned, tot_tuned = product_ms()
-            bem.bem_tune_clear()
-            per_builtin, tot_builtin = product_ms()
-            keep = tot_tuned < tot_builtin
-            if keep:
-                bem.bem_tune_load(path)
-        tuning["in_solve"] = {"tuned_ms_per_launch": per_tuned, "built_in_ms_per_launch": per_builtin,
-                              "tuned_total_ms": tot_tuned, "built_in_total_ms": tot_builtin,
-                              "kept": "tuned" if keep else "built-in"}
         if rank == 0:
             emit_section("autotune", tuning)
 

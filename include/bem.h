@@ -110,7 +110,12 @@ BEM_API uint64_t bem_launch_count(void);
  * which = 3: the bounded wait of the grid barrier that the fused mass inverse uses:
  * two cooperative blocks whose barrier can never complete must each give up after
  * about a second and flag it; result = 1000 * flag + elapsed seconds (expected
- * 1000 + ~1). */
+ * 1000 + ~1).  which = 4..9: relative L2 difference between the tiled operator
+ * product (symmetry-packed V, D; K applied as K and K^T) and an FP64 product with
+ * dense copies of the same seeded random operators (two grids of 300 and 170
+ * vertices): 4 FP32 on complex64, 1 column; 5 the same, 5 columns; 6 double-float on
+ * complex64, 1 column; 7 the same, 3 columns; 8 double-float on complex128, 1 column;
+ * 9 the same, 8 columns. */
 BEM_API bem_status bem_selftest(bem_context* ctx, int which, double* result);
 
 /* Per-kernel device timing.  While enabled, each launch of the library is
@@ -134,9 +139,6 @@ BEM_API bem_status bem_profile_get(int index, char* name, int name_len, double* 
  * on CPUs).  bem_autotune times the candidates on complex64 operators of the two
  * grids' sizes (seeded random values) and on the grids' mass matrices, and keeps the
  * fastest in a process-wide table keyed by (kernel, width, ceil(log2(rows))):
- *   "gemm32"  FP32 dense product, width 1, 2, 4, 8 columns: block 128/256/512
- *             threads, variant = 16-byte loads in flight per lane (2 or 4);
- *   "gemv_dd" double-float single-column product: block 128/256/512, variant 0;
  *   "cheb"    Chebyshev mass-inverse steps, width 1 and 8 columns: block 64/128/256;
  *   "gemm_tc" tensor-core product of min(n_rhs, 64) columns (only if n_rhs > 8),
  *             width = columns padded to 8: variant = K splits (1 or 2).

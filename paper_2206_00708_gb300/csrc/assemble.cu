@@ -34,6 +34,8 @@ struct KParams {
     double kr, ki;        // wavenumber
     double k2r, k2i;      // k^2
     int64_t n;            // matrix order (vertices)
+    int nt;               // 64 x 64 tiles per side (tiled layouts)
+    int lay[4];           // storage layouts of V, K, T, D (OP_DENSE, OP_FULL, OP_SYM)
 };
 
 struct TrialTile {
@@ -65,11 +67,17 @@ __device__ __forceinline__ void kernel_values(bool complex_k, const KParams& P, 
 }
 
 __device__ __forceinline__ void add2(double2* M, int64_t idx, double re, double im) {
+    if (idx < 0) return;  // a symmetric layout keeps the mirror entry, added by the caller too
     atomicAdd(&M[idx].x, re);
     atomicAdd(&M[idx].y, im);
 }
 __device__ __forceinline__ void add2(float2* M, int64_t idx, double re, double im) {
+    if (idx < 0) return;
     atomicAdd(&M[idx], make_float2((float)re, (float)im));
+}
+// storage index of entry (i, j) of operator op (0 V, 1 K, 2 T, 3 D)
+__device__ __forceinline__ int64_t at(const KParams& P, int op, int64_t i, int64_t j) {
+    return op_index(P.lay[op], P.n, P.nt, i, j);
 }
 
 template <bool CK>
@@ -167,23 +175,22 @@ k_regular(const TriRec* __restrict__ rec, const int32_t* __restrict__ tri, int64
             }
         const double nn = ntx * nsx + nty * nsy + ntz * nsz;
         const int32_t tv[3] = {ta, tb, tc}, sv[3] = {sa, sb, sc};
-        const int64_t N = P.n;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-                const int64_t ij = (int64_t)tv[a] * N + sv[b], ji = (int64_t)sv[b] * N + tv[a];
-                if (V) { add2(V, ij, Vr[a][b], Vi[a][b]); add2(V, ji, Vr[a][b], Vi[a][b]); }
-                if (K) { add2(K, ij, Kr[a][b], Ki[a][b]); add2(K, ji, Tr[a][b], Ti[a][b]); }
-                if (T) { add2(T, ij, Tr[a][b], Ti[a][b]); add2(T, ji, Kr[a][b], Ki[a][b]); }
+                const int64_t i = tv[a], j = sv[b];
+                if (V) { add2(V, at(P, 0, i, j), Vr[a][b], Vi[a][b]); add2(V, at(P, 0, j, i), Vr[a][b], Vi[a][b]); }
+                if (K) { add2(K, at(P, 1, i, j), Kr[a][b], Ki[a][b]); add2(K, at(P, 1, j, i), Tr[a][b], Ti[a][b]); }
+                if (T) { add2(T, at(P, 2, i, j), Tr[a][b], Ti[a][b]); add2(T, at(P, 2, j, i), Kr[a][b], Ki[a][b]); }
                 if (D) {
                     const double cc = tr.curl[a][0] * trial.curl[b][0][sl] + tr.curl[a][1] * trial.curl[b][1][sl] +
                                       tr.curl[a][2] * trial.curl[b][2][sl];
                     // D = cc I0 - k^2 nn V
                     const double dr = cc * I0r - nn * (P.k2r * Vr[a][b] - P.k2i * Vi[a][b]);
                     const double di = cc * I0i - nn * (P.k2r * Vi[a][b] + P.k2i * Vr[a][b]);
-                    add2(D, ij, dr, di);
-                    add2(D, ji, dr, di);
+                    add2(D, at(P, 3, i, j), dr, di);
+                    add2(D, at(P, 3, j, i), dr, di);
                 }
             }
         }
@@ -293,35 +300,40 @@ k_singular(const double* __restrict__ xyz, const int32_t* __restrict__ tri, cons
     const double nn = nt0 * ns0 + nt1 * ns1 + nt2 * ns2;
     const double dr = cc * I0r - nn * (P.k2r * vr - P.k2i * vi);
     const double di = cc * I0i - nn * (P.k2r * vi + P.k2i * vr);
-    const int64_t N = P.n;
-    const int32_t iv = tri[3 * (int64_t)t + a], jv = tri[3 * (int64_t)s + b];
-    const int64_t ij = (int64_t)iv * N + jv, ji = (int64_t)jv * N + iv;
-    if (V) add2(V, ij, vr, vi);
-    if (K) add2(K, ij, kr, ki);
-    if (T) add2(T, ij, tr, ti);
-    if (D) add2(D, ij, dr, di);
+    const int64_t iv = tri[3 * (int64_t)t + a], jv = tri[3 * (int64_t)s + b];
+    if (V) add2(V, at(P, 0, iv, jv), vr, vi);
+    if (K) add2(K, at(P, 1, iv, jv), kr, ki);
+    if (T) add2(T, at(P, 2, iv, jv), tr, ti);
+    if (D) add2(D, at(P, 3, iv, jv), dr, di);
     if (kind != 0) {
-        if (V) add2(V, ji, vr, vi);
-        if (K) add2(K, ji, tr, ti);
-        if (T) add2(T, ji, kr, ki);
-        if (D) add2(D, ji, dr, di);
+        if (V) add2(V, at(P, 0, jv, iv), vr, vi);
+        if (K) add2(K, at(P, 1, jv, iv), tr, ti);
+        if (T) add2(T, at(P, 2, jv, iv), kr, ki);
+        if (D) add2(D, at(P, 3, jv, iv), dr, di);
     }
 }
 
 }  // namespace
 
-bem_status assemble_operators_fp64(const bem_grid* g, double k_re, double k_im, int n_singular, double2* V,
-                                   double2* K, double2* T, double2* D, cudaStream_t s) {
-    const int64_t N = g->nv, nt = g->nt;
-    const size_t bytes = (size_t)N * N * sizeof(double2);
-    for (double2* M : {V, K, T, D})
-        if (M) BEM_CUDA_TRY(cudaMemsetAsync(M, 0, bytes, s));
+static KParams kparams(const bem_grid* g, double k_re, double k_im, const OpLayouts& L) {
     KParams P;
     P.kr = k_re;
     P.ki = k_im;
     P.k2r = k_re * k_re - k_im * k_im;
     P.k2i = 2.0 * k_re * k_im;
-    P.n = N;
+    P.n = g->nv;
+    P.nt = op_tiles(g->nv);
+    for (int i = 0; i < 4; ++i) P.lay[i] = L.lay[i];
+    return P;
+}
+
+bem_status assemble_operators_fp64(const bem_grid* g, double k_re, double k_im, int n_singular, double2* V,
+                                   double2* K, double2* T, double2* D, const OpLayouts& L, cudaStream_t s) {
+    const int64_t N = g->nv, nt = g->nt;
+    double2* const ops[4] = {V, K, T, D};
+    for (int o = 0; o < 4; ++o)
+        if (ops[o]) BEM_CUDA_TRY(cudaMemsetAsync(ops[o], 0, op_entries(L.lay[o], N) * sizeof(double2), s));
+    const KParams P = kparams(g, k_re, k_im, L);
     const bool ck = k_im != 0.0;
     const int64_t ntile = (nt + TB - 1) / TB;
     if (ntile > 65535) {
@@ -352,13 +364,8 @@ bem_status assemble_operators_fp64(const bem_grid* g, double k_re, double k_im, 
 }
 
 bem_status assemble_singular_into_c64(const bem_grid* g, double k_re, double k_im, int n_singular, float2* V,
-                                      float2* K, float2* T, float2* D, cudaStream_t s) {
-    KParams P;
-    P.kr = k_re;
-    P.ki = k_im;
-    P.k2r = k_re * k_re - k_im * k_im;
-    P.k2i = 2.0 * k_re * k_im;
-    P.n = g->nv;
+                                      float2* K, float2* T, float2* D, const OpLayouts& L, cudaStream_t s) {
+    const KParams P = kparams(g, k_re, k_im, L);
     const double* ss;
     int cnt[3], off[3];
     BEM_TRY(ss_table_get(n_singular, s, &ss, cnt, off));

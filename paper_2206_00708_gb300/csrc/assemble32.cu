@@ -144,7 +144,9 @@ struct Grid32 {
     KP32 P;
     float2 *Vm, *Km, *Tm, *Dm;
     int* err;
-    int ck;  // complex wavenumber
+    int ck;      // complex wavenumber
+    int nt;      // 64 x 64 tiles per side (tiled layouts)
+    int lay[4];  // storage layouts of V, K, T, D
 };
 
 // One CTA's work: the regular pairs of test tile it and trial tile is (it <= is).
@@ -459,11 +461,15 @@ __device__ __forceinline__ void regular32_tile(const Grid32& G, const int it, co
         }
         if (!any) continue;
         const int64_t i = vI[li], j = vJ[lj];
-        const int64_t ij = i * N + j, ji = j * N + i;
-        if (Vm) { atomicAdd(&Vm[ij], make_float2(v[0], v[1])); atomicAdd(&Vm[ji], make_float2(v[0], v[1])); }
-        if (Km) { atomicAdd(&Km[ij], make_float2(v[2], v[3])); atomicAdd(&Km[ji], make_float2(v[4], v[5])); }
-        if (Tm) { atomicAdd(&Tm[ij], make_float2(v[4], v[5])); atomicAdd(&Tm[ji], make_float2(v[2], v[3])); }
-        if (Dm) { atomicAdd(&Dm[ij], make_float2(v[6], v[7])); atomicAdd(&Dm[ji], make_float2(v[6], v[7])); }
+        // storage index per layout (-1: a symmetric layout keeps the mirror, added here too)
+        auto put = [&](float2* M, int op, int64_t a, int64_t b, float re, float im) {
+            const int64_t x = op_index(G.lay[op], N, G.nt, a, b);
+            if (x >= 0) atomicAdd(&M[x], make_float2(re, im));
+        };
+        if (Vm) { put(Vm, 0, i, j, v[0], v[1]); put(Vm, 0, j, i, v[0], v[1]); }
+        if (Km) { put(Km, 1, i, j, v[2], v[3]); put(Km, 1, j, i, v[4], v[5]); }
+        if (Tm) { put(Tm, 2, i, j, v[4], v[5]); put(Tm, 2, j, i, v[2], v[3]); }
+        if (Dm) { put(Dm, 3, i, j, v[6], v[7]); put(Dm, 3, j, i, v[6], v[7]); }
     }
 }
 
@@ -527,7 +533,7 @@ size_t regular32_smem() {
 }
 
 Grid32 grid32_args(const bem_grid* g, double k_re, double k_im, float2* V, float2* K, float2* T, float2* D,
-                   int* flag) {
+                   const OpLayouts& L, int* flag) {
     Grid32 G{};
     G.rec = g->rec32.as<TriRec32>();
     G.tverts = g->t_verts.as<int32_t>();
@@ -547,6 +553,8 @@ Grid32 grid32_args(const bem_grid* g, double k_re, double k_im, float2* V, float
     G.Dm = D;
     G.err = flag;
     G.ck = k_im != 0.0;
+    G.nt = op_tiles(g->nv);
+    for (int i = 0; i < 4; ++i) G.lay[i] = L.lay[i];
     return G;
 }
 
@@ -565,7 +573,7 @@ bem_status check_flag(const DevBuf& flag, cudaStream_t s) {
 }  // namespace
 
 bem_status assemble_regular_fp32(const bem_grid* g, double k_re, double k_im, float2* V, float2* K, float2* T,
-                                 float2* D, cudaStream_t s) {
+                                 float2* D, const OpLayouts& L, cudaStream_t s) {
     if (g->ntile > 65535) {
         set_error("grid too large for the tile grid of the mixed-precision assembly");
         return BEM_E_INVALID_ARG;
@@ -578,7 +586,7 @@ bem_status assemble_regular_fp32(const bem_grid* g, double k_re, double k_im, fl
     DevBuf flag;
     BEM_TRY(flag.alloc(sizeof(int), s));
     BEM_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
-    const Grid32 G = grid32_args(g, k_re, k_im, V, K, T, D, flag.as<int>());
+    const Grid32 G = grid32_args(g, k_re, k_im, V, K, T, D, L, flag.as<int>());
     if (G.ck) BEM_LAUNCH(k_regular32<true>, grid, NT32, smem, s, G);
     else BEM_LAUNCH(k_regular32<false>, grid, NT32, smem, s, G);
     return check_flag(flag, s);
@@ -586,7 +594,7 @@ bem_status assemble_regular_fp32(const bem_grid* g, double k_re, double k_im, fl
 
 bem_status assemble_regular_fp32_many(int count, const bem_grid* const* g, const double* k_re, const double* k_im,
                                       float2* const* V, float2* const* K, float2* const* T, float2* const* D,
-                                      cudaStream_t s) {
+                                      const OpLayouts& L, cudaStream_t s) {
     if (count <= 0) return BEM_OK;
     DevBuf flag, dgrids, ditems, counter;
     BEM_TRY(flag.alloc(sizeof(int), s));
@@ -594,7 +602,7 @@ bem_status assemble_regular_fp32_many(int count, const bem_grid* const* g, const
     std::vector<Grid32> grids(count);
     std::vector<int4> items;
     for (int i = 0; i < count; ++i) {
-        grids[i] = grid32_args(g[i], k_re[i], k_im[i], V[i], K[i], T[i], D[i], flag.as<int>());
+        grids[i] = grid32_args(g[i], k_re[i], k_im[i], V[i], K[i], T[i], D[i], L, flag.as<int>());
         for (int it = 0; it < (int)g[i]->ntile; ++it)
             for (int is = it; is < (int)g[i]->ntile; ++is) items.push_back(make_int4(i, it, is, 0));
     }

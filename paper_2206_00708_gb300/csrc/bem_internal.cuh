@@ -20,10 +20,10 @@ inline double now_seconds() {
 // ------------------------------------------------------------------ autotuner table
 // Launch shapes chosen by bem_autotune (tune.cu): per kernel family, width (columns per
 // launch) and size class ceil(log2(rows)), a block size and a variant.
-enum { TUNE_GEMM32 = 0, TUNE_GEMV_DD = 1, TUNE_GEMM_TC = 2, TUNE_CHEB = 3, TUNE_KERNELS = 4 };
+enum { TUNE_GEMM_TC = 0, TUNE_CHEB = 1, TUNE_KERNELS = 2 };
 struct TuneChoice {
     int block;    // threads per block (0: the kernel's own)
-    int variant;  // gemm32: 16-byte loads in flight per lane (2 or 4); gemm_tc: K splits (1 or 2)
+    int variant;  // gemm_tc: K splits (1 or 2); cheb: 0
     double ms;    // time measured for it
 };
 int size_class(int64_t n);
@@ -31,8 +31,6 @@ TuneChoice tune_get(int kernel, int width, int64_t n, TuneChoice dflt);
 void tune_put(int kernel, int width, int64_t n, TuneChoice c);
 inline bool tune_choice_valid(int kernel, const TuneChoice& c) {
     switch (kernel) {
-        case TUNE_GEMM32: return (c.block == 128 || c.block == 256 || c.block == 512) && (c.variant == 2 || c.variant == 4);
-        case TUNE_GEMV_DD: return (c.block == 128 || c.block == 256 || c.block == 512) && c.variant == 0;
         case TUNE_GEMM_TC: return c.block == 0 && (c.variant == 1 || c.variant == 2);
         case TUNE_CHEB: return (c.block == 64 || c.block == 128 || c.block == 256) && c.variant == 0;
         default: return false;
@@ -240,6 +238,93 @@ struct bem_sparse {
 
 namespace bem {
 
+// ------------------------------------------------------------------ operator storage
+// Dense operators of one grid as 64 x 64 tiles, each tile contiguous (row-major
+// inside, 64 x 64 entries) so that a whole tile is one bulk copy:
+//   OP_FULL: all nt x nt tiles, tile (I, J) at index I nt + J (K);
+//   OP_SYM:  a symmetric matrix (V, D) keeps only the tiles I <= J, in row-major order
+//            of the upper tile triangle, tile (I, J) at index I nt - I (I - 1) / 2 + (J - I);
+//            diagonal tiles hold both halves.  Entry (i, j) of a lower tile is entry
+//            (j, i) of its mirror.
+//   OP_DENSE: plain row-major N x N (bem_assemble's result).
+// T = K^T is never stored: products apply K in both orientations.  Rows and columns
+// past N in the last tile row / column are zero.
+constexpr int OPT = 64;
+enum : int { OP_DENSE = 0, OP_FULL = 1, OP_SYM = 2 };
+__host__ __device__ inline int op_tiles(int64_t N) { return (int)((N + OPT - 1) / OPT); }
+__host__ __device__ inline int64_t op_sym_tile(int64_t I, int64_t J, int64_t nt) {
+    return I * nt - I * (I - 1) / 2 + (J - I);
+}
+inline size_t op_entries(int layout, int64_t N) {
+    const size_t nt = (size_t)op_tiles(N);
+    return layout == OP_DENSE ? (size_t)N * N : layout == OP_FULL ? nt * nt * OPT * OPT : nt * (nt + 1) / 2 * OPT * OPT;
+}
+// storage index of entry (i, j), or -1 where a symmetric layout keeps its mirror instead
+__host__ __device__ inline int64_t op_index(int layout, int64_t N, int nt, int64_t i, int64_t j) {
+    if (layout == OP_DENSE) return i * N + j;
+    const int64_t I = i >> 6, J = j >> 6;
+    const int64_t in = ((i & 63) << 6) | (j & 63);
+    if (layout == OP_FULL) return ((I * nt + J) << 12) | in;
+    if (I > J) return -1;
+    return (op_sym_tile(I, J, nt) << 12) | in;
+}
+// storage layouts of (V, K, T, D) in a product-ready operator set and in bem_assemble
+struct OpLayouts {
+    int lay[4];
+};
+inline OpLayouts op_layouts_tiled() { return OpLayouts{{OP_SYM, OP_FULL, OP_FULL, OP_SYM}}; }
+inline OpLayouts op_layouts_dense() { return OpLayouts{{OP_DENSE, OP_DENSE, OP_DENSE, OP_DENSE}}; }
+
+// ------------------------------------------------------------------ tile products
+// One grid's operators in one product (tile_product.cu):
+//   y1 = cK K xa + cV V xb,   y2 = cD D xc + cT K^T xd
+// with K, V, D tiled (OP_FULL, OP_SYM, OP_SYM; complex64 or complex128 by the product's
+// storage), x and z columns of n entries, the inputs at offsets xa..xd of a column and
+// the outputs written at offsets y1, y2 (-1: not computed).  A zero coefficient (or a
+// null matrix) skips that matrix's bytes altogether.
+struct TileSet {
+    const void* K;
+    const void* V;
+    const void* D;
+    int64_t N;
+    int32_t nt, pad;
+    double c[4];            // cK, cV, cD, cT
+    float ch[4], cl[4];     // the same as double-float pairs (high, low)
+    int64_t xa, xb, xc, xd;
+    int64_t y1, y2;
+    int64_t item0;          // first work item of this set in the launch (items: tile pairs I <= J)
+    int64_t rtile0;         // first output row tile (2 nt per set)
+    int64_t part;           // element offset of this set's partial sums (per column)
+};
+enum : int { TP_F32 = 0, TP_DD = 1 };  // arithmetic: FP32 on complex64; double-float (FP64-accurate)
+struct TileProd {
+    std::vector<TileSet> sets;
+    DevBuf dsets;            // device copy of sets
+    int64_t items = 0, rtiles = 0, part_per_col = 0;
+    int64_t n = 0;           // column length of x and z
+    int storage = 8;         // bytes per matrix entry: 8 (complex64) or 16 (complex128)
+};
+// add a set (coefficients cK, cV, cD, cT; offsets) to a product under construction
+void tile_prod_add(TileProd& P, const void* K, const void* V, const void* D, int64_t N, double cK, double cV,
+                   double cD, double cT, int64_t xa, int64_t xb, int64_t xc, int64_t xd, int64_t y1, int64_t y2);
+// upload the sets (once; the product is then reused with any inputs)
+bem_status tile_prod_finish(TileProd& P, int64_t n, int storage, cudaStream_t s);
+// bytes of partial sums one product of R columns needs
+size_t tile_part_bytes(const TileProd& P, int mode, int R);
+// z (rc <= 8 columns of n) = the product applied to x: complex64 x (float2) in TP_F32,
+// double-float x (float4: re hi, im hi, re lo, im lo) in TP_DD.  part: tile_part_bytes.
+bem_status tile_product(const TileProd& P, int mode, int rc, const void* x, double2* z, void* part, int* err,
+                        cudaStream_t s);
+// dense row-major copy of a tiled operator (transpose: K^T, i.e. T, from K's tiles)
+bem_status tiles_to_dense(const void* src, int layout, bool transpose, int64_t N, int storage, void* dst,
+                          cudaStream_t s);
+// seeded random operators of an N-vertex grid in the tiled storage (tiles: V, K, D) and,
+// if dense is not null, their dense row-major copies (dense: V, K, T, D)
+bem_status random_tiled_ops(int64_t N, int storage, uint64_t seed, DevBuf tiles[3], DevBuf* dense, cudaStream_t s);
+// self-test: tile products on seeded random operators against an FP64 dense product
+// (max relative error over the outputs)
+bem_status selftest_tile(int mode, int storage, int R, double* rel_err, cudaStream_t s);
+
 // grid.cu
 bem_status grid_build_geometry(bem_grid* g);
 bem_status mass_values(const bem_grid* g, double* d_val, cudaStream_t s);      // [m_nnz]
@@ -248,24 +333,25 @@ bem_status mass_inverse_diag(const bem_grid* g, const double* d_val, double* d_d
 // grid.cu: FP32 geometry records in tile order (mixed-precision assembly)
 bem_status grid_build_rec32(const bem_grid* g, cudaStream_t s);
 
-// assemble32.cu: regular pairs in FP32 into complex64 V, K, T, D (row-major, zeroed by the caller)
+// assemble32.cu: regular pairs in FP32 into complex64 V, K, T, D (layouts L; zeroed by the caller)
 bem_status assemble_regular_fp32(const bem_grid* g, double k_re, double k_im, float2* V, float2* K, float2* T,
-                                 float2* D, cudaStream_t s);
+                                 float2* D, const OpLayouts& L, cudaStream_t s);
 // assemble32.cu: accuracy self-test of the FP32 kernel's sincos against CUDA's sincosf
 bem_status selftest_sincos(int n, float xmax, double* max_err, cudaStream_t s);
-// assemble.cu: singular pairs (FP64 quadrature) added into complex64 matrices
+// assemble.cu: singular pairs (FP64 quadrature) added into complex64 matrices (layouts L)
 bem_status assemble_singular_into_c64(const bem_grid* g, double k_re, double k_im, int n_singular, float2* V,
-                                      float2* K, float2* T, float2* D, cudaStream_t s);
+                                      float2* K, float2* T, float2* D, const OpLayouts& L, cudaStream_t s);
 
-// assemble.cu: V, K, T, D (row-major N x N complex128; any pointer may be null).
+// assemble.cu: V, K, T, D (complex128 in layouts L, zeroed here; any pointer may be null).
 bem_status assemble_operators_fp64(const bem_grid* g, double k_re, double k_im, int n_singular,
-                                   double2* V, double2* K, double2* T, double2* D, cudaStream_t s);
+                                   double2* V, double2* K, double2* T, double2* D, const OpLayouts& L,
+                                   cudaStream_t s);
 
 // mortar.cu: COO of P_ab (rows: vertices of a, cols: vertices of b).
 // FP32 regular pairs of many grids in one persistent launch (assemble32.cu)
 bem_status assemble_regular_fp32_many(int count, const bem_grid* const* g, const double* k_re, const double* k_im,
                                       float2* const* V, float2* const* K, float2* const* T, float2* const* D,
-                                      cudaStream_t s);
+                                      const OpLayouts& L, cudaStream_t s);
 
 // tensor-core multi-column MTF product (gemm_tc.cu)
 int tc_padded_columns(int R);

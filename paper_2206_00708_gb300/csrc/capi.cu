@@ -110,9 +110,16 @@ uint64_t bem_launch_count(void) { return g_launches.load(std::memory_order_relax
 bem_status bem_selftest(bem_context* ctx, int which, double* result) {
     CTX_GUARD(ctx);
     BEM_REQUIRE(result != nullptr, "null result");
-    BEM_REQUIRE(which >= 0 && which <= 3, "unknown self-test");
+    BEM_REQUIRE(which >= 0 && which <= 9, "unknown self-test");
     if (which == 0) return selftest_sincos(1 << 20, 64.0f, result, ctx->stream);
     if (which == 3) return selftest_barrier(result, ctx->stream);
+    if (which >= 4) {
+        // tile products: (arithmetic, storage bytes, columns)
+        const int cfg[6][3] = {{TP_F32, 8, 1}, {TP_F32, 8, 5}, {TP_DD, 8, 1}, {TP_DD, 8, 3}, {TP_DD, 16, 1},
+                               {TP_DD, 16, 8}};
+        const int* c = cfg[which - 4];
+        return selftest_tile(c[0], c[1], c[2], result, ctx->stream);
+    }
     return selftest_tc(which == 1 ? 24 : 8, result, ctx->stream);
 }
 
@@ -256,7 +263,7 @@ bem_status bem_assemble(bem_context* ctx, int op, bem_c128 k, const bem_grid* te
         double2* p = m->data.as<double2>();
         BEM_TRY(assemble_operators_fp64(test, k.re, k.im, n_singular, op == BEM_OP_V ? p : nullptr,
                                         op == BEM_OP_K ? p : nullptr, op == BEM_OP_T ? p : nullptr,
-                                        op == BEM_OP_D ? p : nullptr, s));
+                                        op == BEM_OP_D ? p : nullptr, op_layouts_dense(), s));
     } else {
         m->entry_bytes = 8;
         BEM_TRY(m->data.alloc((size_t)N * N * 8, s));
@@ -266,8 +273,8 @@ bem_status bem_assemble(bem_context* ctx, int op, bem_c128 k, const bem_grid* te
         float2* K = op == BEM_OP_K ? p : nullptr;
         float2* T = op == BEM_OP_T ? p : nullptr;
         float2* D = op == BEM_OP_D ? p : nullptr;
-        BEM_TRY(assemble_regular_fp32(test, k.re, k.im, V, K, T, D, s));
-        BEM_TRY(assemble_singular_into_c64(test, k.re, k.im, n_singular, V, K, T, D, s));
+        BEM_TRY(assemble_regular_fp32(test, k.re, k.im, V, K, T, D, op_layouts_dense(), s));
+        BEM_TRY(assemble_singular_into_c64(test, k.re, k.im, n_singular, V, K, T, D, op_layouts_dense(), s));
     }
     *out = m.release();
     return BEM_OK;

@@ -68,17 +68,23 @@ namespace {
 int64_t working_set_bytes(int64_t ne, int64_t ni, int precision, int maxiter, int n_rhs) {
     const int64_t n = 2 * ne + 2 * ni;
     const int64_t esz = precision == BEM_PREC_MIXED ? 8 : 16;
-    const int64_t ops = 4 * (ne * ne + ni * ni) * esz;
+    // tiled operators: V, D as upper tile triangles, K in full (64 x 64 tiles)
+    const int64_t te = op_tiles(ne), ti = op_tiles(ni);
+    const int64_t ops = (te * (te + 1) + te * te + ti * (ti + 1) + ti * ti) * OPT * OPT * esz;
     const int64_t m = std::min<int64_t>(maxiter, n) + 1;
     // the solver advances up to 64 (mixed precision, tensor-core products) or 8
     // right-hand sides together, each with its own Krylov basis and Hessenberg matrix
     const int64_t R = std::max(1, std::min(n_rhs, precision == BEM_PREC_MIXED ? 64 : 8));
     const int64_t krylov = R * (m * n * 16 + m * m * 16 + m * 64 * 16);
     const int64_t vectors = 16 * (R + 8) * n * 16;
-    const int64_t tc = precision == BEM_PREC_MIXED ? 128 * ((R + 7) / 8 * 8) * (ne + ni + 16) : 0;
+    // partial sums of the tile products (8 columns, double-float) and the input splits
+    const int64_t partial = 2 * (te * te + ti * ti) * OPT * 8 * 16 + 8 * n * 16;
+    // tensor-core batches (mixed, more than 8 waves) also keep dense copies of the blocks
+    const int64_t dense = precision == BEM_PREC_MIXED && R > 8 ? 4 * (ne * ne + ni * ni) * 8 : 0;
+    const int64_t tc = precision == BEM_PREC_MIXED ? 128 * ((R + 7) / 8 * 8) * (ne + ni + 16) + dense : 0;
     const int64_t grids = 600 * (ne + ni) * 2;
     const int64_t mortar = 2 * 9 * 40 * (ne + ni) * 16;
-    return ops + krylov + vectors + tc + grids + mortar + (int64_t)(16 << 20);
+    return ops + krylov + vectors + partial + tc + grids + mortar + (int64_t)(16 << 20);
 }
 
 void finish_locked(bem_server* srv, const std::shared_ptr<Request>& r, int32_t status) {

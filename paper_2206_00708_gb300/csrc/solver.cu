@@ -60,11 +60,6 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
     return v;
 }
 
-__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
-    s = a + b;
-    float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
 
 unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -170,193 +165,6 @@ struct Blocks {
     int64_t x1[4], x2[4];  // offsets of the vectors multiplying A1, A2
 };
 
-// the block row of global row gw and its parameters
-template <class MT>
-struct RowBlock {
-    const MT *a1, *a2;
-    double c1, c2;
-    int64_t N, i, x1, x2;
-};
-
-template <class MT>
-__device__ __forceinline__ RowBlock<MT> row_block(const Blocks<MT>& B, int64_t gw) {
-    int b = 0;
-    while (b < 3 && gw >= B.base[b + 1]) ++b;
-    RowBlock<MT> rb;
-    rb.a1 = B.A1[b];
-    rb.a2 = B.A2[b];
-    rb.c1 = B.c1[b];
-    rb.c2 = B.c2[b];
-    rb.N = B.rows[b];
-    rb.i = gw - B.base[b];
-    rb.x1 = B.x1[b];
-    rb.x2 = B.x2[b];
-    return rb;
-}
-
-// complex128 blocks, FP64 arithmetic: one warp per row, R right-hand sides
-template <int R>
-__global__ void __launch_bounds__(256) k_gemm64(Blocks<double2> B, int64_t n, const double2* __restrict__ x,
-                                                double2* __restrict__ z) {
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw >= n) return;
-    const RowBlock<double2> rb = row_block(B, gw);
-    const double2* __restrict__ a1 = rb.a1 + rb.i * rb.N;
-    const double2* __restrict__ a2 = rb.a2 + rb.i * rb.N;
-    double2 s1[R], s2[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) s1[r] = s2[r] = make_double2(0, 0);
-    for (int64_t j = lane; j < rb.N; j += 32) {
-        const double2 p = a1[j], q = a2[j];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            s1[r] = cfma(p, x[r * n + rb.x1 + j], s1[r]);
-            s2[r] = cfma(q, x[r * n + rb.x2 + j], s2[r]);
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const double2 u = warp_sum2(s1[r]), v = warp_sum2(s2[r]);
-        if (lane == 0) z[r * n + gw] = make_double2(rb.c1 * u.x + rb.c2 * v.x, rb.c1 * u.y + rb.c2 * v.y);
-    }
-}
-
-// complex64 blocks, FP64 arithmetic (outer residual of the refinement)
-template <int R>
-__global__ void __launch_bounds__(256) k_gemm_c64_f64(Blocks<float2> B, int64_t n, const double2* __restrict__ x,
-                                                      double2* __restrict__ z) {
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw >= n) return;
-    const RowBlock<float2> rb = row_block(B, gw);
-    const float2* __restrict__ a1 = rb.a1 + rb.i * rb.N;
-    const float2* __restrict__ a2 = rb.a2 + rb.i * rb.N;
-    double2 s1[R], s2[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) s1[r] = s2[r] = make_double2(0, 0);
-    for (int64_t j = lane; j < rb.N; j += 32) {
-        const float2 pf = a1[j], qf = a2[j];
-        const double2 p = make_double2(pf.x, pf.y), q = make_double2(qf.x, qf.y);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            s1[r] = cfma(p, x[r * n + rb.x1 + j], s1[r]);
-            s2[r] = cfma(q, x[r * n + rb.x2 + j], s2[r]);
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const double2 u = warp_sum2(s1[r]), v = warp_sum2(s2[r]);
-        if (lane == 0) z[r * n + gw] = make_double2(rb.c1 * u.x + rb.c2 * v.x, rb.c1 * u.y + rb.c2 * v.y);
-    }
-}
-
-// complex64 blocks, FP32 arithmetic: one warp per row, 16-byte loads (two complex
-// entries per lane) shared by the R right-hand sides; products are summed plainly in
-// groups of four and added to the lane's accumulator with a compensated (two-sum)
-// update; warp totals are formed in FP64.
-template <int R, int H>
-__global__ void __launch_bounds__(512) k_gemm32(Blocks<float2> B, int64_t n, const float2* __restrict__ x,
-                                                double2* __restrict__ z) {
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw >= n) return;
-    // block-row parameters are read where they are used (not held across the loop:
-    // the single-column kernel is bandwidth-bound and wants few registers)
-    int b = 0;
-    while (b < 3 && gw >= B.base[b + 1]) ++b;
-    const int64_t N = B.rows[b];
-    const int64_t i = gw - B.base[b];
-    double2 out[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) out[r] = make_double2(0, 0);
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-        if (m == 1 && B.A2[b] == nullptr) break;  // a block row of one matrix
-        const float2* __restrict__ a = (m == 0 ? B.A1[b] : B.A2[b]) + i * N;
-        const int64_t xo = m == 0 ? B.x1[b] : B.x2[b];
-        float sr[R], si[R], er[R], ei[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) sr[r] = si[r] = er[r] = ei[r] = 0.f;
-        // row start may be only 8-byte aligned: peel to a 16-byte boundary
-        const int64_t j0 = ((reinterpret_cast<uintptr_t>(a) & 15) != 0) ? 1 : 0;
-        if (j0 && lane == 0 && N > 0) {
-            const float2 av = a[0];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const float2 xx = x[r * n + xo];
-                sr[r] = fmaf(av.x, xx.x, -av.y * xx.y);
-                si[r] = fmaf(av.x, xx.y, av.y * xx.x);
-            }
-        }
-        const int64_t npair = (N - j0) / 2;
-        const float4* __restrict__ a4 = reinterpret_cast<const float4*>(a + j0);
-        // H 16-byte loads in flight per lane (streamed past L1: the operator is read
-        // once); 4 H products summed plainly per right-hand side before the
-        // compensated update
-        for (int64_t p = lane; p < npair; p += 32 * H) {
-            float cr[R], ci[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) cr[r] = ci[r] = 0.f;
-#pragma unroll
-            for (int h = 0; h < H; ++h) {
-                const int64_t pp = p + 32 * h;
-                if (pp < npair) {
-                    const float4 av = __ldcs(a4 + pp);
-                    const int64_t j = j0 + 2 * pp;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float2 x0 = x[r * n + xo + j], x1 = x[r * n + xo + j + 1];
-                        cr[r] = fmaf(av.x, x0.x, cr[r]);
-                        cr[r] = fmaf(-av.y, x0.y, cr[r]);
-                        ci[r] = fmaf(av.x, x0.y, ci[r]);
-                        ci[r] = fmaf(av.y, x0.x, ci[r]);
-                        cr[r] = fmaf(av.z, x1.x, cr[r]);
-                        cr[r] = fmaf(-av.w, x1.y, cr[r]);
-                        ci[r] = fmaf(av.z, x1.y, ci[r]);
-                        ci[r] = fmaf(av.w, x1.x, ci[r]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float t, e;
-                two_sum_f(sr[r], cr[r], t, e);
-                sr[r] = t;
-                er[r] += e;
-                two_sum_f(si[r], ci[r], t, e);
-                si[r] = t;
-                ei[r] += e;
-            }
-        }
-        if (((N - j0) & 1) && lane == 1) {  // odd tail
-            const float2 av = a[N - 1];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const float2 xx = x[r * n + xo + N - 1];
-                float t, e;
-                two_sum_f(sr[r], fmaf(av.x, xx.x, -av.y * xx.y), t, e);
-                sr[r] = t;
-                er[r] += e;
-                two_sum_f(si[r], fmaf(av.x, xx.y, av.y * xx.x), t, e);
-                si[r] = t;
-                ei[r] += e;
-            }
-        }
-        const double c = m == 0 ? B.c1[b] : B.c2[b];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const double2 v = warp_sum2(make_double2((double)sr[r] + (double)er[r], (double)si[r] + (double)ei[r]));
-            out[r].x += c * v.x;
-            out[r].y += c * v.y;
-        }
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) z[r * n + gw] = out[r];
-    }
-}
-
 __global__ void k_to_c64(const double2* __restrict__ x, int64_t n, float2* __restrict__ y) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e < n) y[e] = make_float2((float)x[e].x, (float)x[e].y);
@@ -370,126 +178,6 @@ __global__ void k_split_x(const double2* __restrict__ x, int64_t n, float4* __re
     const double2 v = x[e];
     const float hr = (float)v.x, hi = (float)v.y;
     xs[e] = make_float4(hr, hi, (float)(v.x - (double)hr), (float)(v.y - (double)hi));
-}
-
-// s + p into the double-float pair (s, e): the rounding error of the FP32 sum and the
-// given exact remainder pe are carried in e
-__device__ __forceinline__ void dd_add(float& s, float& e, float p, float pe) {
-    float t, q;
-    two_sum_f(s, p, t, q);
-    s = t;
-    e += q + pe;
-}
-
-// (sr, si) += a x for a complex64 entry a = (ar, ai) and x = hi + lo (float4 as in
-// k_split_x): the products with the high part are split exactly (two-product by
-// FMA) and summed with two-sums; the products with the low part go to the error
-// words directly (their own rounding is below 2^-48 of a x)
-// (__fmul_rn keeps the compiler from contracting a product into the following sum,
-// which would break the two-sum)
-__device__ __forceinline__ void dd_cmac(float ar, float ai, float4 x, float& sr, float& er, float& si, float& ei) {
-    float p = __fmul_rn(ar, x.x);
-    dd_add(sr, er, p, fmaf(ar, x.x, -p));
-    p = __fmul_rn(-ai, x.y);
-    dd_add(sr, er, p, fmaf(-ai, x.y, -p));
-    er = fmaf(ar, x.z, er);
-    er = fmaf(-ai, x.w, er);
-    p = __fmul_rn(ar, x.y);
-    dd_add(si, ei, p, fmaf(ar, x.y, -p));
-    p = __fmul_rn(ai, x.x);
-    dd_add(si, ei, p, fmaf(ai, x.x, -p));
-    ei = fmaf(ar, x.w, ei);
-    ei = fmaf(ai, x.z, ei);
-}
-
-// complex64 blocks, one column, double-float arithmetic on the FP32 pipe: the stored
-// (FP32) operator applied to an FP64 vector to ~1e-12 relative, reading the same
-// 8 bytes per entry as k_gemm32<1>.  Used for the single-column inner products of the
-// refinement, which then converge on the stored system instead of stagnating at the
-// FP32 rounding of the product.
-__global__ void __launch_bounds__(512) k_gemv_dd(Blocks<float2> B, int64_t n, const float4* __restrict__ xs,
-                                                 double2* __restrict__ z) {
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw >= n) return;
-    int b = 0;
-    while (b < 3 && gw >= B.base[b + 1]) ++b;
-    const int64_t N = B.rows[b];
-    const int64_t i = gw - B.base[b];
-    double2 out = make_double2(0, 0);
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-        if (m == 1 && B.A2[b] == nullptr) break;  // a block row of one matrix
-        const float2* __restrict__ a = (m == 0 ? B.A1[b] : B.A2[b]) + i * N;
-        const float4* __restrict__ x = xs + (m == 0 ? B.x1[b] : B.x2[b]);
-        float sr = 0.f, er = 0.f, si = 0.f, ei = 0.f;
-        const int64_t j0 = ((reinterpret_cast<uintptr_t>(a) & 15) != 0) ? 1 : 0;
-        if (j0 && lane == 0 && N > 0) {
-            const float2 av = a[0];
-            dd_cmac(av.x, av.y, x[0], sr, er, si, ei);
-        }
-        const int64_t npair = (N - j0) / 2;
-        const float4* __restrict__ a4 = reinterpret_cast<const float4*>(a + j0);
-        for (int64_t p = lane; p < npair; p += 64) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t pp = p + 32 * h;
-                if (pp < npair) {
-                    const float4 av = __ldcs(a4 + pp);
-                    const int64_t j = j0 + 2 * pp;
-                    const float4 x0 = x[j], x1 = x[j + 1];
-                    dd_cmac(av.x, av.y, x0, sr, er, si, ei);
-                    dd_cmac(av.z, av.w, x1, sr, er, si, ei);
-                }
-            }
-        }
-        if (((N - j0) & 1) && lane == 1) {
-            const float2 av = a[N - 1];
-            dd_cmac(av.x, av.y, x[N - 1], sr, er, si, ei);
-        }
-        const double2 v = warp_sum2(make_double2((double)sr + (double)er, (double)si + (double)ei));
-        const double c = m == 0 ? B.c1[b] : B.c2[b];
-        out.x += c * v.x;
-        out.y += c * v.y;
-    }
-    if (lane == 0) z[gw] = out;
-}
-
-// k_gemm32 for W = 1, 2, 4 or 8 columns with the tuned block size and loads in flight
-// (defaults: 256 threads; 4 loads for one column, 2 for more)
-using Gemm32Fn = void (*)(Blocks<float2>, int64_t, const float2*, double2*);
-
-Gemm32Fn gemm32_fn(int W, int H) {
-    switch (W * 10 + H) {
-        case 12: return k_gemm32<1, 2>;
-        case 14: return k_gemm32<1, 4>;
-        case 22: return k_gemm32<2, 2>;
-        case 24: return k_gemm32<2, 4>;
-        case 42: return k_gemm32<4, 2>;
-        case 44: return k_gemm32<4, 4>;
-        case 82: return k_gemm32<8, 2>;
-        default: return k_gemm32<8, 4>;
-    }
-}
-
-const char* gemm32_name(int W) {
-    return W == 1 ? "k_gemm32<1>" : W == 2 ? "k_gemm32<2>" : W == 4 ? "k_gemm32<4>" : "k_gemm32<8>";
-}
-
-TuneChoice gemm32_default(int W) { return TuneChoice{256, W == 1 ? 4 : 2, 0.0}; }
-
-bem_status launch_gemm32(int W, const Blocks<float2>& B, int64_t n, const float2* x, double2* z, cudaStream_t s,
-                         const TuneChoice* force = nullptr) {
-    const TuneChoice c = force ? *force : tune_get(TUNE_GEMM32, W, n, gemm32_default(W));
-    BEM_LAUNCH_PTR(gemm32_name(W), gemm32_fn(W, c.variant), blocks_for(n * 32, c.block), c.block, 0, s, B, n, x, z);
-    return BEM_OK;
-}
-
-bem_status launch_gemv_dd(const Blocks<float2>& B, int64_t n, const float4* xs, double2* z, cudaStream_t s,
-                          const TuneChoice* force = nullptr) {
-    const TuneChoice c = force ? *force : tune_get(TUNE_GEMV_DD, 1, n, TuneChoice{256, 0, 0.0});
-    BEM_LAUNCH(k_gemv_dd, blocks_for(n * 32, c.block), c.block, 0, s, B, n, xs, z);
-    return BEM_OK;
 }
 
 // ---------------------------------------------------------------- mortar transfer
@@ -1326,7 +1014,6 @@ bem_status transfer_add(const TransferCsr& t, int R, const double2* x, double2* 
 
 // compiled widths of the multi-column kernels; a batch of R columns runs at the
 // next width and the padding columns read and write spare, in-bounds slots
-int gemm_width(int R) { return R <= 1 ? 1 : R <= 2 ? 2 : R <= 4 ? 4 : 8; }
 
 using Apply = std::function<bem_status(const double2* in, double2* out, int R)>;
 using StopCheck = std::function<bem_status()>;
@@ -1604,68 +1291,6 @@ void fill_blocks_single(BT& Bo, BT& Bh, MT* const m1[4], MT* const m2[4], int oA
     }
 }
 
-// High-contrast systems (Sec. 2.3): every dense product is one of these.  A block row
-// with A2 == nullptr holds one matrix; rows past the used ones are empty (no columns).
-//   own: the unknowns' grid A, two rows of one matrix each applied to one half of x:
-//        Neumann variants (T_A mu; V_A mu), Dirichlet variants (K_A nu; D_A nu);
-//   hat: the other grid B, one row c1 X1 t_0 + c2 X2 t_1 on a pair t of grid-B vectors:
-//        Neumann (T_B, D_B), Dirichlet (V_B, K_B); the second row is empty.
-// m1 = (K_e, D_e, K_i, D_i), m2 = (V_e, T_e, V_i, T_i); oA, oB index the grids in them.
-template <class BT, class MT>
-void fill_blocks_hc(BT& Bo, BT& Bh, MT* const m1[4], MT* const m2[4], int oA, int oB, int64_t NA, int64_t NB,
-                    bool neumann, double c1, double c2) {
-    MT* const KA = m1[oA];
-    MT* const DA = m1[oA + 1];
-    MT* const VA = m2[oA];
-    MT* const TA = m2[oA + 1];
-    MT* const KB = m1[oB];
-    MT* const DB = m1[oB + 1];
-    MT* const VB = m2[oB];
-    MT* const TB = m2[oB + 1];
-    for (int b = 0; b < 4; ++b) {
-        Bo.A1[b] = b == 0 ? (neumann ? TA : KA) : (neumann ? VA : DA);
-        Bo.A2[b] = nullptr;
-        Bo.c1[b] = 1.0; Bo.c2[b] = 0.0;
-        Bo.rows[b] = b < 2 ? NA : 0;
-        Bo.base[b] = b < 2 ? b * NA : 2 * NA;
-        Bo.x1[b] = neumann ? NA : 0; Bo.x2[b] = 0;
-        Bh.A1[b] = neumann ? TB : VB;
-        Bh.A2[b] = b == 0 ? (neumann ? DB : KB) : nullptr;
-        Bh.c1[b] = c1; Bh.c2[b] = c2;
-        Bh.rows[b] = b == 0 ? NB : 0;
-        Bh.base[b] = b == 0 ? 0 : (b == 1 ? NB : 2 * NB);
-        Bh.x1[b] = 0; Bh.x2[b] = NB;
-    }
-}
-
-// One row c1 X1 x_{o1} + c2 X2 x_{o2} (X2 may be null) over pairs of one grid's vectors,
-// the second row empty: the products of the high-contrast data and outputs.
-template <class BT, class MT>
-void fill_blocks_row(BT& B, MT* X1, int64_t o1, double c1, MT* X2, int64_t o2, double c2, int64_t N) {
-    for (int b = 0; b < 4; ++b) {
-        B.A1[b] = X1;
-        B.A2[b] = b == 0 ? X2 : nullptr;
-        B.c1[b] = c1; B.c2[b] = c2;
-        B.rows[b] = b == 0 ? N : 0;
-        B.base[b] = b == 0 ? 0 : (b == 1 ? N : 2 * N);
-        B.x1[b] = o1; B.x2[b] = X2 ? o2 : 0;
-    }
-}
-
-// For the FP64 kernels, which read both matrices of a row in one loop: a row of one
-// matrix reads its matrix twice, the second time with coefficient 0.
-template <class BT>
-BT both_matrices(const BT& B) {
-    BT D = B;
-    for (int b = 0; b < 4; ++b)
-        if (D.A2[b] == nullptr) {
-            D.A2[b] = D.A1[b];
-            D.c2[b] = 0.0;
-            D.x2[b] = D.x1[b];
-        }
-    return D;
-}
-
 template <class BT, class MT>
 void fill_blocks(BT& B, MT* const m1[4], MT* const m2[4], int64_t Ne, int64_t Ni) {
     const double c1[4] = {-1.0, 1.0, -1.0, 1.0};
@@ -1699,6 +1324,73 @@ __global__ void k_widen(const float2* __restrict__ x, int64_t count, double2* __
 
 }  // namespace
 
+// One grid's operators in the tiled storage (V, D upper tile triangles, K full; T = K^T
+// is never stored), complex64 (mixed) or complex128.
+struct GridOps {
+    DevBuf V, K, D;
+    int64_t N = 0;
+    size_t esz = 16;
+    // assemble the requested operators of grid g at wavenumber k
+    bem_status assemble(const bem_grid* g, bem_c128 k, bool mixed, int n_singular, cudaStream_t s,
+                        bool want_v = true, bool want_k = true, bool want_d = true) {
+        N = g->nv;
+        esz = mixed ? 8 : 16;
+        const OpLayouts L = op_layouts_tiled();
+        if (want_v) BEM_TRY(V.alloc(op_entries(OP_SYM, N) * esz, s));
+        if (want_k) BEM_TRY(K.alloc(op_entries(OP_FULL, N) * esz, s));
+        if (want_d) BEM_TRY(D.alloc(op_entries(OP_SYM, N) * esz, s));
+        if (mixed) {
+            for (DevBuf* b : {&V, &K, &D})
+                if (b->p) BEM_CUDA_TRY(cudaMemsetAsync(b->p, 0, b->bytes, s));
+            BEM_TRY(assemble_regular_fp32(g, k.re, k.im, V.as<float2>(), K.as<float2>(), nullptr, D.as<float2>(), L,
+                                          s));
+            BEM_TRY(assemble_singular_into_c64(g, k.re, k.im, n_singular, V.as<float2>(), K.as<float2>(), nullptr,
+                                               D.as<float2>(), L, s));
+        } else {
+            BEM_TRY(assemble_operators_fp64(g, k.re, k.im, n_singular, V.as<double2>(), K.as<double2>(), nullptr,
+                                            D.as<double2>(), L, s));
+        }
+        return BEM_OK;
+    }
+    // zeroed buffers for V, K, D of an N-vertex grid (assembled by the caller)
+    bem_status alloc(int64_t n_vertices, size_t entry_bytes, cudaStream_t s) {
+        N = n_vertices;
+        esz = entry_bytes;
+        BEM_TRY(V.alloc(op_entries(OP_SYM, N) * esz, s));
+        BEM_TRY(K.alloc(op_entries(OP_FULL, N) * esz, s));
+        BEM_TRY(D.alloc(op_entries(OP_SYM, N) * esz, s));
+        for (DevBuf* b : {&V, &K, &D}) BEM_CUDA_TRY(cudaMemsetAsync(b->p, 0, b->bytes, s));
+        return BEM_OK;
+    }
+    // a set y1 = cK K xa + cV V xb, y2 = cD D xc + cT K^T xd of product P
+    void add(TileProd& P, double cK, double cV, double cD, double cT, int64_t xa, int64_t xb, int64_t xc, int64_t xd,
+             int64_t y1, int64_t y2) const {
+        tile_prod_add(P, K.p, V.p, D.p, N, cK, cV, cD, cT, xa, xb, xc, xd, y1, y2);
+    }
+    // dense row-major copies [V, K, T, D] (for the tensor-core products)
+    bem_status dense_copies(DevBuf* out, cudaStream_t s) const {
+        const int esz_i = (int)esz;
+        for (int m = 0; m < 4; ++m) BEM_TRY(out[m].alloc((size_t)N * N * esz, s));
+        BEM_TRY(tiles_to_dense(V.p, OP_SYM, false, N, esz_i, out[0].p, s));
+        BEM_TRY(tiles_to_dense(K.p, OP_FULL, false, N, esz_i, out[1].p, s));
+        BEM_TRY(tiles_to_dense(K.p, OP_FULL, true, N, esz_i, out[2].p, s));
+        BEM_TRY(tiles_to_dense(D.p, OP_SYM, false, N, esz_i, out[3].p, s));
+        return BEM_OK;
+    }
+};
+
+// the tile products' error flag (an mbarrier wait that gave up)
+bem_status check_tile_flag(const DevBuf& flag) {
+    int h = 0;
+    BEM_CUDA_TRY(cudaMemcpy(&h, flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        set_error("tile product: an mbarrier wait timed out");
+        return BEM_E_INTERNAL;
+    }
+    return BEM_OK;
+}
+
+
 // The tensor-core product against the FP32 CUDA-core product on seeded random
 // blocks whose entries have positive real parts (little cancellation, so the
 // relative difference measures the products' rounding and not the data).
@@ -1728,37 +1420,37 @@ bem_status selftest_barrier(double* result, cudaStream_t s) {
 bem_status selftest_tc(int R, double* rel_err, cudaStream_t s) {
     const int64_t Ne = 300, Ni = 170, n = 2 * Ne + 2 * Ni;
     const int RW = R + 7;
-    DevBuf A[8], xf, x, x32, z1, z2, work, err;
-    for (int m = 0; m < 8; ++m) {
-        const int64_t N = m < 4 ? Ne : Ni;
-        BEM_TRY(A[m].alloc((size_t)N * N * 8, s));
-        float* f = A[m].as<float>();
-        BEM_LAUNCH(k_fill_uniform, blocks_for(2 * N * N, 256), 256, 0, s, f, 2 * N * N, 1000ull + m, 0.5f, 1.0f);
-        // imaginary parts in [-0.25, 0.25): refill the odd floats by a strided view
-        DevBuf im;
-        BEM_TRY(im.alloc((size_t)N * N * 4, s));
-        BEM_LAUNCH(k_fill_uniform, blocks_for(N * N, 256), 256, 0, s, im.as<float>(), N * N, 2000ull + m, -0.25f, 0.25f);
-        BEM_CUDA_TRY(cudaMemcpy2DAsync(f + 1, 8, im.p, 4, 4, N * N, cudaMemcpyDeviceToDevice, s));
-    }
+    DevBuf tl[2][3], dn[2][4], xf, x, z1, z2, work, err, part, tperr;
+    BEM_TRY(random_tiled_ops(Ne, 8, 1000, tl[0], dn[0], s));
+    BEM_TRY(random_tiled_ops(Ni, 8, 2000, tl[1], dn[1], s));
     BEM_TRY(xf.alloc((size_t)RW * n * 8, s));
     BEM_LAUNCH(k_fill_uniform, blocks_for(2 * RW * n, 256), 256, 0, s, xf.as<float>(), 2 * RW * n, 3000ull, 0.5f, 1.0f);
     BEM_TRY(x.alloc((size_t)RW * n * 16, s));
     BEM_LAUNCH(k_widen, blocks_for(RW * n, 256), 256, 0, s, xf.as<float2>(), RW * n, x.as<double2>());
     BEM_TRY(z1.alloc((size_t)RW * n * 16, s));
     BEM_TRY(z2.alloc((size_t)RW * n * 16, s));
+    // the tensor-core product on the dense copies
     Blocks<float2> B{};
-    const float2* m1[4] = {A[1].as<float2>(), A[3].as<float2>(), A[5].as<float2>(), A[7].as<float2>()};
-    const float2* m2[4] = {A[0].as<float2>(), A[2].as<float2>(), A[4].as<float2>(), A[6].as<float2>()};
+    const float2* m1[4] = {dn[0][1].as<float2>(), dn[0][3].as<float2>(), dn[1][1].as<float2>(), dn[1][3].as<float2>()};
+    const float2* m2[4] = {dn[0][0].as<float2>(), dn[0][2].as<float2>(), dn[1][0].as<float2>(), dn[1][2].as<float2>()};
     fill_blocks(B, m1, m2, Ne, Ni);
     BEM_TRY(work.alloc(tc_workspace_bytes(B.rows, tc_padded_columns(R)), s));
     BEM_TRY(err.alloc(sizeof(int), s));
     BEM_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     BEM_TRY(mtf_product_tc(B.A1, B.A2, B.c1, B.c2, B.rows, B.base, B.x1, B.x2, n, R, x.as<double2>(),
                            z1.as<double2>(), work.p, work.bytes, err.as<int>(), s));
-    for (int c0 = 0; c0 < R; c0 += 8) {
-        const int Wd = gemm_width(std::min(8, R - c0));
-        BEM_TRY(launch_gemm32(Wd, B, n, xf.as<float2>() + c0 * n, z2.as<double2>() + c0 * n, s));
-    }
+    // the FP32 tile product of the same operators
+    TileProd P;
+    tile_prod_add(P, tl[0][1].p, tl[0][0].p, tl[0][2].p, Ne, -1.0, 1.0, 1.0, 1.0, 0, Ne, 0, Ne, 0, Ne);
+    tile_prod_add(P, tl[1][1].p, tl[1][0].p, tl[1][2].p, Ni, -1.0, 1.0, 1.0, 1.0, 2 * Ne, 2 * Ne + Ni, 2 * Ne,
+                  2 * Ne + Ni, 2 * Ne, 2 * Ne + Ni);
+    BEM_TRY(tile_prod_finish(P, n, 8, s));
+    BEM_TRY(part.alloc(tile_part_bytes(P, TP_F32, 8), s));
+    BEM_TRY(tperr.alloc(sizeof(int), s));
+    BEM_CUDA_TRY(cudaMemsetAsync(tperr.p, 0, sizeof(int), s));
+    for (int c0 = 0; c0 < R; c0 += 8)
+        BEM_TRY(tile_product(P, TP_F32, std::min(8, R - c0), xf.as<float2>() + c0 * n, z2.as<double2>() + c0 * n,
+                             part.p, tperr.as<int>(), s));
     std::vector<double2> h1((size_t)R * n), h2((size_t)R * n);
     int h_err = 0;
     BEM_CUDA_TRY(cudaMemcpyAsync(h1.data(), z1.p, h1.size() * 16, cudaMemcpyDeviceToHost, s));
@@ -1769,6 +1461,7 @@ bem_status selftest_tc(int R, double* rel_err, cudaStream_t s) {
         set_error("tensor-core product: an mbarrier wait timed out");
         return BEM_E_INTERNAL;
     }
+    BEM_TRY(check_tile_flag(tperr));
     double num = 0.0, den = 0.0;
     for (size_t i = 0; i < h1.size(); ++i) {
         const double dx = h1[i].x - h2[i].x, dy = h1[i].y - h2[i].y;
@@ -1779,41 +1472,47 @@ bem_status selftest_tc(int R, double* rel_err, cudaStream_t s) {
     return BEM_OK;
 }
 
-// Autotuner: times the candidate launch shapes of the iteration's kernels on operators
-// of the given grids' sizes (seeded random complex64 blocks; the timing of these
-// bandwidth- and latency-bound kernels does not depend on the values) and the grids'
-// own mass matrices, and records the fastest per (kernel, width, size class):
-//   k_gemm32 for 1, 2, 4, 8 columns: 128, 256 or 512 threads x 2 or 4 loads in flight;
-//   k_gemv_dd: 128, 256 or 512 threads;
+// Autotuner: times the candidate launch shapes of the iteration's kernels for the given
+// grids' sizes (the grids' own mass matrices; seeded random operators for the
+// tensor-core product, whose timing does not depend on the values) and records the
+// fastest per (kernel, width, size class):
 //   Chebyshev mass steps for 1 and 8 columns: 64, 128 or 256 threads;
 //   tensor-core product of n_rhs > 8 columns (batches of up to 64): 1 or 2 K splits.
-// The GPU is first kept busy for a while (clocks up), each candidate runs once untimed,
-// then the candidates are timed round-robin `reps` times, four launches back to back
-// between CUDA events (so that a drift of the clocks affects all alike), and the median
-// counts; the kernel's built-in shape is kept unless another is faster by more than 2 %.
+// (The dense single- and few-column products are persistent tile-product launches, one
+// CTA per SM, with nothing to tune.)  The GPU is first kept busy for a while (clocks
+// up), each candidate runs once untimed, then the candidates are timed round-robin
+// `reps` times, four launches back to back between CUDA events (so that a drift of the
+// clocks affects all alike), and the median counts; the kernel's built-in shape is kept
+// unless another is faster by more than 2 %.
 bem_status autotune_impl(bem_context* ctx, const bem_grid* ge, const bem_grid* gi, int n_rhs, int reps) {
     cudaStream_t s = ctx->stream;
     const int64_t Ne = ge->nv, Ni = gi->nv, n = 2 * Ne + 2 * Ni;
-    const int RW = 8 + 7;
-    DevBuf A[8], xf, x, z, xs;
-    for (int m = 0; m < 8; ++m) {
-        const int64_t N = m < 4 ? Ne : Ni;
-        BEM_TRY(A[m].alloc((size_t)N * N * 8, s));
-        BEM_LAUNCH(k_fill_uniform, blocks_for(2 * N * N, 256), 256, 0, s, A[m].as<float>(), 2 * N * N, 5000ull + m,
-                   -1.0f, 1.0f);
-    }
-    Blocks<float2> B{};
-    const float2* m1[4] = {A[1].as<float2>(), A[3].as<float2>(), A[5].as<float2>(), A[7].as<float2>()};
-    const float2* m2[4] = {A[0].as<float2>(), A[2].as<float2>(), A[4].as<float2>(), A[6].as<float2>()};
-    fill_blocks(B, m1, m2, Ne, Ni);
-    const int RT = std::max(RW, 64 + 7);
+    const int RT = 64 + 7;
+    DevBuf tl[2][3], dn[2][4], xf, x, z, part, tperr;
+    const bool tc = n_rhs > 8;
+    BEM_TRY(random_tiled_ops(Ne, 8, 5000, tl[0], tc ? dn[0] : nullptr, s));
+    BEM_TRY(random_tiled_ops(Ni, 8, 6000, tl[1], tc ? dn[1] : nullptr, s));
     BEM_TRY(xf.alloc((size_t)RT * n * 8, s));
     BEM_LAUNCH(k_fill_uniform, blocks_for(2 * RT * n, 256), 256, 0, s, xf.as<float>(), 2 * RT * n, 6000ull, -1.0f, 1.0f);
     BEM_TRY(x.alloc((size_t)RT * n * 16, s));
     BEM_LAUNCH(k_widen, blocks_for(RT * n, 256), 256, 0, s, xf.as<float2>(), RT * n, x.as<double2>());
     BEM_TRY(z.alloc((size_t)RT * n * 16, s));
-    BEM_TRY(xs.alloc((size_t)n * 16, s));
-    BEM_LAUNCH(k_split_x, blocks_for(n, 256), 256, 0, s, x.as<double2>(), n, xs.as<float4>());
+    TileProd P;  // the multiple-traces product of the random operators (warm-up)
+    tile_prod_add(P, tl[0][1].p, tl[0][0].p, tl[0][2].p, Ne, -1.0, 1.0, 1.0, 1.0, 0, Ne, 0, Ne, 0, Ne);
+    tile_prod_add(P, tl[1][1].p, tl[1][0].p, tl[1][2].p, Ni, -1.0, 1.0, 1.0, 1.0, 2 * Ne, 2 * Ne + Ni, 2 * Ne,
+                  2 * Ne + Ni, 2 * Ne, 2 * Ne + Ni);
+    BEM_TRY(tile_prod_finish(P, n, 8, s));
+    BEM_TRY(part.alloc(tile_part_bytes(P, TP_F32, 1), s));
+    BEM_TRY(tperr.alloc(sizeof(int), s));
+    BEM_CUDA_TRY(cudaMemsetAsync(tperr.p, 0, sizeof(int), s));
+    Blocks<float2> B{};
+    if (tc) {
+        const float2* m1[4] = {dn[0][1].as<float2>(), dn[0][3].as<float2>(), dn[1][1].as<float2>(),
+                               dn[1][3].as<float2>()};
+        const float2* m2[4] = {dn[0][0].as<float2>(), dn[0][2].as<float2>(), dn[1][0].as<float2>(),
+                               dn[1][2].as<float2>()};
+        fill_blocks(B, m1, m2, Ne, Ni);
+    }
     EventTimer ev;
     // times of the candidates (index 0: the built-in shape), round-robin; returns the
     // index chosen and its median time
@@ -1849,33 +1548,13 @@ bem_status autotune_impl(bem_context* ctx, const bem_grid* ge, const bem_grid* g
     };
     // keep the GPU busy for ~0.3 s before measuring
     {
-        const TuneChoice d = gemm32_default(1);
         const auto t0 = now_seconds();
         while (now_seconds() - t0 < 0.3) {
-            for (int k = 0; k < 8; ++k) BEM_TRY(launch_gemm32(1, B, n, xf.as<float2>(), z.as<double2>(), s, &d));
+            for (int k = 0; k < 8; ++k)
+                BEM_TRY(tile_product(P, TP_F32, 1, xf.p, z.as<double2>(), part.p, tperr.as<int>(), s));
             BEM_CUDA_TRY(cudaStreamSynchronize(s));
         }
-    }
-    // dense products
-    for (int W : {1, 2, 4, 8}) {
-        std::vector<TuneChoice> cand{gemm32_default(W)};
-        for (int block : {128, 256, 512})
-            for (int H : {2, 4})
-                if (!(block == cand[0].block && H == cand[0].variant)) cand.push_back(TuneChoice{block, H, 0.0});
-        double ms = 0.0;
-        const int b = pick((int)cand.size(), [&](int c) {
-            return launch_gemm32(W, B, n, xf.as<float2>(), z.as<double2>(), s, &cand[c]);
-        }, &ms);
-        if (b < 0) return tune_failed();
-        tune_put(TUNE_GEMM32, W, n, TuneChoice{cand[b].block, cand[b].variant, ms});
-    }
-    {
-        const std::vector<TuneChoice> cand{{256, 0, 0.0}, {128, 0, 0.0}, {512, 0, 0.0}};
-        double ms = 0.0;
-        const int b = pick(3, [&](int c) { return launch_gemv_dd(B, n, xs.as<float4>(), z.as<double2>(), s, &cand[c]); },
-                           &ms);
-        if (b < 0) return tune_failed();
-        tune_put(TUNE_GEMV_DD, 1, n, TuneChoice{cand[b].block, 0, ms});
+        BEM_TRY(check_tile_flag(tperr));
     }
     // Chebyshev mass steps on the grids' own mass matrices (MTF layout: both grids)
     {
@@ -1911,7 +1590,7 @@ bem_status autotune_impl(bem_context* ctx, const bem_grid* ge, const bem_grid* g
         }
     }
     // tensor-core product
-    if (n_rhs > 8) {
+    if (tc) {
         const int R = std::min(n_rhs, 64);
         const int RP = tc_padded_columns(R);
         DevBuf work, err;
@@ -2014,27 +1693,13 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     EventTimer t_asm, t_mor, t_sol;
     GraphCache graphs(o->cuda_graphs != 0);
     // ---- operators on both grids --------------------------------------------------
+    // tiled storage: V and D as their upper tile triangles, K in full, no T (= K^T)
     const size_t esz = mixed ? 8 : 16;
-    const size_t be = (size_t)Ne * Ne * esz, bi = (size_t)Ni * Ni * esz;
-    DevBuf M[8];  // Ve, Ke, Te, De, Vi, Ki, Ti, Di
-    for (int m = 0; m < 8; ++m) BEM_TRY(M[m].alloc(m < 4 ? be : bi, s));
+    const OpLayouts TL = op_layouts_tiled();
+    GridOps ops[2];  // exterior, interior
     cudaEventRecord(t_asm.a, s);
-    if (mixed) {
-        for (int m = 0; m < 8; ++m) BEM_CUDA_TRY(cudaMemsetAsync(M[m].p, 0, m < 4 ? be : bi, s));
-        for (int side = 0; side < 2; ++side) {
-            const bem_grid* g = side == 0 ? ge : gi;
-            const bem_c128 k = side == 0 ? k_ext : k_int;
-            float2* P4[4];
-            for (int m = 0; m < 4; ++m) P4[m] = M[4 * side + m].as<float2>();
-            BEM_TRY(assemble_regular_fp32(g, k.re, k.im, P4[0], P4[1], P4[2], P4[3], s));
-            BEM_TRY(assemble_singular_into_c64(g, k.re, k.im, o->n_singular, P4[0], P4[1], P4[2], P4[3], s));
-        }
-    } else {
-        BEM_TRY(assemble_operators_fp64(ge, k_ext.re, k_ext.im, o->n_singular, M[0].as<double2>(), M[1].as<double2>(),
-                                        M[2].as<double2>(), M[3].as<double2>(), s));
-        BEM_TRY(assemble_operators_fp64(gi, k_int.re, k_int.im, o->n_singular, M[4].as<double2>(), M[5].as<double2>(),
-                                        M[6].as<double2>(), M[7].as<double2>(), s));
-    }
+    BEM_TRY(ops[0].assemble(ge, k_ext, mixed, o->n_singular, s));
+    BEM_TRY(ops[1].assemble(gi, k_int, mixed, o->n_singular, s));
     cudaEventRecord(t_asm.b, s);
     // ---- mass and mortar (FP64) ----------------------------------------------------
     cudaEventRecord(t_mor.a, s);
@@ -2073,7 +1738,6 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     auto dd_now = [&]() { return dd_single && inner_progress > o->dd_switch; };
     const size_t colb = (size_t)n * 16;
     DevBuf wz, wr, wa, wb, x32, tcw, tcerr, xsplit;
-    if (dd_single) BEM_TRY(xsplit.alloc((size_t)(st ? std::max(n, nB) : n) * 16, s));
     BEM_TRY(wz.alloc(RW * colb, s));
     BEM_TRY(wr.alloc(RB * colb, s));
     BEM_TRY(wa.alloc(RB * colb, s));
@@ -2140,128 +1804,139 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     top.cc = 0.5 * sgn;
     top.cd = 0.5 * sgn * rho_ratio;
     double2* z = wz.as<double2>();
-    // dense blocks: the four block rows of the multiple-traces system, or for the PMCHWT
-    // the two exterior block rows (B*) and the two scaled interior ones (Bi*)
-    Blocks<double2> B64{}, Bh64{}, Br64{}, Bo64{};
-    Blocks<float2> B32{}, Bh32{}, Br32{}, Bo32{};
-    // high-contrast data (Br, a row on grid B) and outputs (Bo, a row on grid A), with the
-    // matrices m1 = (K_e, D_e, K_i, D_i), m2 = (V_e, T_e, V_i, T_i) of the working storage
-    auto fill_hc_extra = [&](auto& Br, auto& Bo, auto* const* m1, auto* const* m2) {
+    // ---- the dense products as tile products (tile_product.cu) ------------------------
+    //   P0: the multiple-traces blocks of both grids, or the own-grid rows of a
+    //       single-trace / high-contrast system (vectors of n);
+    //   Ph: the other grid's rows (vectors of nB); Pr, Pq: the high-contrast data and
+    //       output rows (vectors of nB and n).
+    TileProd P0, Ph, Pr, Pq;
+    const GridOps& gA = ops[st_int ? 1 : 0];
+    const GridOps& gB = ops[st_int ? 0 : 1];
+    if (hc) {
+        if (hc_neu) {  // own rows (T_A mu; V_A mu), mu = x_1; hat row c1 T_B t_0 + c2 D_B t_1
+            gA.add(P0, 0.0, 1.0, 0.0, 1.0, 0, NA, 0, NA, NA, 0);
+            gB.add(Ph, 0.0, 0.0, hc_c2, hc_c1, 0, 0, NB, 0, -1, 0);
+        } else {       // own rows (K_A nu; D_A nu), nu = x_0; hat row c1 V_B t_0 + c2 K_B t_1
+            gA.add(P0, 1.0, 0.0, 1.0, 0.0, 0, 0, 0, 0, 0, NA);
+            gB.add(Ph, hc_c2, hc_c1, 0.0, 0.0, NB, 0, 0, 0, 0, -1);
+        }
         const double r = rho_ratio;
         switch (form) {
             case BEM_FORM_HC_EXT_NEU:  // (1/r) D_i t_0;  -V_e x_1
-                fill_blocks_row(Br, m1[3], 0, 1.0 / r, decltype(m1[0])(nullptr), 0, 0.0, NB);
-                fill_blocks_row(Bo, m2[0], NA, -1.0, decltype(m1[0])(nullptr), 0, 0.0, NA);
+                gB.add(Pr, 0.0, 0.0, 1.0 / r, 0.0, 0, 0, 0, 0, -1, 0);
+                gA.add(Pq, 0.0, -1.0, 0.0, 0.0, 0, NA, 0, 0, 0, -1);
                 break;
             case BEM_FORM_HC_EXT_DIR:  // r V_i t_0;  -D_e x_0
-                fill_blocks_row(Br, m2[2], 0, r, decltype(m1[0])(nullptr), 0, 0.0, NB);
-                fill_blocks_row(Bo, m1[1], 0, -1.0, decltype(m1[0])(nullptr), 0, 0.0, NA);
+                gB.add(Pr, 0.0, r, 0.0, 0.0, 0, 0, 0, 0, 0, -1);
+                gA.add(Pq, 0.0, 0.0, -1.0, 0.0, 0, 0, 0, 0, -1, 0);
                 break;
             case BEM_FORM_HC_INT_NEU:  // D_e t_0 + T_e t_1;  V_i x_1
-                fill_blocks_row(Br, m1[1], 0, 1.0, m2[1], NB, 1.0, NB);
-                fill_blocks_row(Bo, m2[2], NA, 1.0, decltype(m1[0])(nullptr), 0, 0.0, NA);
+                gB.add(Pr, 0.0, 0.0, 1.0, 1.0, 0, 0, 0, NB, -1, 0);
+                gA.add(Pq, 0.0, 1.0, 0.0, 0.0, 0, NA, 0, 0, 0, -1);
                 break;
             default:  // interior Dirichlet: V_e t_1 - K_e t_0;  D_i x_0
-                fill_blocks_row(Br, m2[0], NB, 1.0, m1[0], 0, -1.0, NB);
-                fill_blocks_row(Bo, m1[3], 0, 1.0, decltype(m1[0])(nullptr), 0, 0.0, NA);
+                gB.add(Pr, -1.0, 1.0, 0.0, 0.0, 0, NB, 0, 0, 0, -1);
+                gA.add(Pq, 0.0, 0.0, 1.0, 0.0, 0, 0, 0, 0, -1, 0);
                 break;
         }
-    };
+        BEM_TRY(tile_prod_finish(Pr, nB, (int)esz, s));
+        BEM_TRY(tile_prod_finish(Pq, n, (int)esz, s));
+    } else if (st) {  // own: sA [[-K_A, V_A], [D_A, T_A]]; hat: sB [[-K_B, cv V_B], [cd D_B, T_B]]
+        gA.add(P0, -sA, sA, sA, sA, 0, NA, 0, NA, 0, NA);
+        gB.add(Ph, -sB, cv * sB, cd * sB, sB, 0, NB, 0, NB, 0, NB);
+    } else {  // [[-K_e, V_e], [D_e, T_e]] on (v_e, w_e) and the same on the interior grid
+        ops[0].add(P0, -1.0, 1.0, 1.0, 1.0, 0, Ne, 0, Ne, 0, Ne);
+        ops[1].add(P0, -1.0, 1.0, 1.0, 1.0, 2 * Ne, 2 * Ne + Ni, 2 * Ne, 2 * Ne + Ni, 2 * Ne, 2 * Ne + Ni);
+    }
+    BEM_TRY(tile_prod_finish(P0, n, (int)esz, s));
+    if (st) BEM_TRY(tile_prod_finish(Ph, nB, (int)esz, s));
+    // workspaces: complex64 copies of the inputs (FP32 products), double-float splits of
+    // 8 columns (FP64-accurate products), partial sums of 8 columns, error flag
+    const int64_t nmax = st ? std::max(n, nB) : n;
+    DevBuf part, tperr;
+    BEM_TRY(xsplit.alloc((size_t)8 * nmax * 16, s));
+    {
+        size_t pb = 0;
+        for (const TileProd* q : {&P0, &Ph, &Pr, &Pq})
+            if (!q->sets.empty()) pb = std::max(pb, tile_part_bytes(*q, TP_DD, std::min(RB, 8)));
+        BEM_TRY(part.alloc(pb, s));
+    }
+    BEM_TRY(tperr.alloc(sizeof(int), s));
+    BEM_CUDA_TRY(cudaMemsetAsync(tperr.p, 0, sizeof(int), s));
+    // tensor-core batches read dense row-major blocks: dense copies of the operators
+    DevBuf dense[8];  // Ve, Ke, Te, De, Vi, Ki, Ti, Di
+    Blocks<float2> B32{}, Bh32{};
     if (mixed) {
         BEM_TRY(x32.alloc((size_t)RW * n * 8, s));
         BEM_CUDA_TRY(cudaMemsetAsync(x32.p, 0, x32.bytes, s));
-        const float2* m1[4] = {M[1].as<float2>(), M[3].as<float2>(), M[5].as<float2>(), M[7].as<float2>()};
-        const float2* m2[4] = {M[0].as<float2>(), M[2].as<float2>(), M[4].as<float2>(), M[6].as<float2>()};
-        if (hc) {
-            fill_blocks_hc(B32, Bh32, m1, m2, oA, oB, NA, NB, hc_neu, hc_c1, hc_c2);
-            fill_hc_extra(Br32, Bo32, m1, m2);
+        if (st) {
             BEM_TRY(x32b.alloc((size_t)RW * nB * 8, s));
             BEM_CUDA_TRY(cudaMemsetAsync(x32b.p, 0, x32b.bytes, s));
-        } else if (st) {
-            fill_blocks_single(B32, Bh32, m1, m2, oA, oB, NA, NB, sA, sB, cv, cd);
-            BEM_TRY(x32b.alloc((size_t)RW * nB * 8, s));
-            BEM_CUDA_TRY(cudaMemsetAsync(x32b.p, 0, x32b.bytes, s));
-        } else {
-            fill_blocks(B32, m1, m2, Ne, Ni);
         }
         if (tc_batches) {
+            for (int g = 0; g < 2; ++g) BEM_TRY(ops[g].dense_copies(&dense[4 * g], s));
+            const float2* m1[4] = {dense[1].as<float2>(), dense[3].as<float2>(), dense[5].as<float2>(),
+                                   dense[7].as<float2>()};
+            const float2* m2[4] = {dense[0].as<float2>(), dense[2].as<float2>(), dense[4].as<float2>(),
+                                   dense[6].as<float2>()};
+            if (st) fill_blocks_single(B32, Bh32, m1, m2, oA, oB, NA, NB, sA, sB, cv, cd);
+            else fill_blocks(B32, m1, m2, Ne, Ni);
             const int RP = tc_padded_columns(RB);
             BEM_TRY(tcw.alloc(std::max(tc_workspace_bytes(B32.rows, RP), st ? tc_workspace_bytes(Bh32.rows, RP) : 0),
                               s));
             BEM_TRY(tcerr.alloc(sizeof(int), s));
             BEM_CUDA_TRY(cudaMemsetAsync(tcerr.p, 0, sizeof(int), s));
         }
-    } else {
-        const double2* m1[4] = {M[1].as<double2>(), M[3].as<double2>(), M[5].as<double2>(), M[7].as<double2>()};
-        const double2* m2[4] = {M[0].as<double2>(), M[2].as<double2>(), M[4].as<double2>(), M[6].as<double2>()};
-        if (hc) {
-            fill_blocks_hc(B64, Bh64, m1, m2, oA, oB, NA, NB, hc_neu, hc_c1, hc_c2);
-            fill_hc_extra(Br64, Bo64, m1, m2);
-        }
-        else if (st) fill_blocks_single(B64, Bh64, m1, m2, oA, oB, NA, NB, sA, sB, cv, cd);
-        else fill_blocks(B64, m1, m2, Ne, Ni);
     }
-    // zo = dense blocks (b32 or b64) of nn rows applied to R columns xin, in the working
-    // arithmetic (xin and zo must hold R + 7 columns of nn; xw is the complex64 copy of xin)
-    auto gemm_work_on = [&](const Blocks<float2>& b32, const Blocks<double2>& b64, int64_t nn, float2* xw,
-                            const double2* xin, double2* zo, int R) -> bem_status {
-        const unsigned rows_blocks = blocks_for(nn * 32, 256);
+    // zo = product P of nn rows applied to R columns xin in the working arithmetic: FP32
+    // on complex64 (mixed; xw receives the complex64 copy of xin), double-float for the
+    // single-column products of the mixed mode above the dd_switch, double-float on
+    // complex128 (FP64 mode), tensor cores for mixed batches of more than 8 columns (tcb:
+    // the dense view of the same blocks)
+    auto gemm_work_on = [&](const TileProd& P, const Blocks<float2>* tcb, int64_t nn, float2* xw, const double2* xin,
+                            double2* zo, int R) -> bem_status {
         if (mixed && tc_batches && R > 8)
-            return mtf_product_tc(b32.A1, b32.A2, b32.c1, b32.c2, b32.rows, b32.base, b32.x1, b32.x2, nn, R, xin, zo,
-                                  tcw.p, tcw.bytes, tcerr.as<int>(), s);
-        if (mixed && R == 1 && dd_now()) {
-            BEM_LAUNCH(k_split_x, blocks_for(nn, 256), 256, 0, s, xin, nn, xsplit.as<float4>());
-            BEM_TRY(launch_gemv_dd(b32, nn, xsplit.as<float4>(), zo, s));
-            return BEM_OK;
-        }
-        if (mixed)
+            return mtf_product_tc(tcb->A1, tcb->A2, tcb->c1, tcb->c2, tcb->rows, tcb->base, tcb->x1, tcb->x2, nn, R,
+                                  xin, zo, tcw.p, tcw.bytes, tcerr.as<int>(), s);
+        const bool dd = !mixed || (R == 1 && dd_now());
+        if (mixed && !dd)
             BEM_LAUNCH(k_to_c64, blocks_for((int64_t)R * nn, 256), 256, 0, s, xin, (int64_t)R * nn, xw);
-        const Blocks<double2> d64 = both_matrices(b64);
         for (int c0 = 0; c0 < R; c0 += 8) {
-            const int Wd = gemm_width(std::min(8, R - c0));
+            const int w = std::min(8, R - c0);
             double2* zc = zo + (int64_t)c0 * nn;
-            if (mixed) {
-                BEM_TRY(launch_gemm32(Wd, b32, nn, xw + (int64_t)c0 * nn, zc, s));
+            if (dd) {
+                BEM_LAUNCH(k_split_x, blocks_for((int64_t)w * nn, 256), 256, 0, s, xin + (int64_t)c0 * nn,
+                           (int64_t)w * nn, xsplit.as<float4>());
+                BEM_TRY(tile_product(P, TP_DD, w, xsplit.p, zc, part.p, tperr.as<int>(), s));
             } else {
-                const double2* xc = xin + (int64_t)c0 * nn;
-                if (Wd == 1) BEM_LAUNCH(k_gemm64<1>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
-                else if (Wd == 2) BEM_LAUNCH(k_gemm64<2>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
-                else if (Wd == 4) BEM_LAUNCH(k_gemm64<4>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
-                else BEM_LAUNCH(k_gemm64<8>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
+                BEM_TRY(tile_product(P, TP_F32, w, xw + (int64_t)c0 * nn, zc, part.p, tperr.as<int>(), s));
             }
         }
         return BEM_OK;
     };
-    // the same with FP64 arithmetic on the stored matrices
-    auto gemm_fp64_on = [&](const Blocks<float2>& b32, const Blocks<double2>& b64, int64_t nn, float2* xw,
-                            const double2* xin, double2* zo, int R) -> bem_status {
-        if (!mixed) return gemm_work_on(b32, b64, nn, xw, xin, zo, R);
-        const unsigned rows_blocks = blocks_for(nn * 32, 256);
-        const Blocks<float2> d32 = both_matrices(b32);
+    // the same with FP64-accurate arithmetic on the stored matrices (double-float)
+    auto gemm_fp64_on = [&](const TileProd& P, int64_t nn, const double2* xin, double2* zo, int R) -> bem_status {
         for (int c0 = 0; c0 < R; c0 += 8) {
-            const int Wd = gemm_width(std::min(8, R - c0));
-            const double2* xc = xin + (int64_t)c0 * nn;
-            double2* zc = zo + (int64_t)c0 * nn;
-            if (Wd == 1) BEM_LAUNCH(k_gemm_c64_f64<1>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
-            else if (Wd == 2) BEM_LAUNCH(k_gemm_c64_f64<2>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
-            else if (Wd == 4) BEM_LAUNCH(k_gemm_c64_f64<4>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
-            else BEM_LAUNCH(k_gemm_c64_f64<8>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
+            const int w = std::min(8, R - c0);
+            BEM_LAUNCH(k_split_x, blocks_for((int64_t)w * nn, 256), 256, 0, s, xin + (int64_t)c0 * nn, (int64_t)w * nn,
+                       xsplit.as<float4>());
+            BEM_TRY(tile_product(P, TP_DD, w, xsplit.p, zo + (int64_t)c0 * nn, part.p, tperr.as<int>(), s));
         }
         return BEM_OK;
     };
     // single-trace product z = sA A_A x + sB P_AB M_B^-1 A_B^rho M_B^-1 P_BA x (the hat
     // transformation applied factor by factor), then y = M_A^-1 z, plus x for Mueller
     auto apply_single = [&](bool fp64, const double2* xin, double2* yout, int R, int steps) -> bem_status {
-        auto prod = [&](const Blocks<float2>& b32, const Blocks<double2>& b64, int64_t nn, float2* xw,
-                        const double2* xi, double2* zo) -> bem_status {
-            return fp64 ? gemm_fp64_on(b32, b64, nn, xw, xi, zo, R) : gemm_work_on(b32, b64, nn, xw, xi, zo, R);
+        auto prod = [&](const TileProd& P, const Blocks<float2>* tcb, int64_t nn, float2* xw, const double2* xi,
+                        double2* zo) -> bem_status {
+            return fp64 ? gemm_fp64_on(P, nn, xi, zo, R) : gemm_work_on(P, tcb, nn, xw, xi, zo, R);
         };
-        BEM_TRY(prod(B32, B64, n, x32.as<float2>(), xin, z));
+        BEM_TRY(prod(P0, &B32, n, x32.as<float2>(), xin, z));
         BEM_LAUNCH(k_csr_pair, dim3(blocks_for(nB, 64), R), 64, 0, s, csr_ba.rp.as<int32_t>(),
                    csr_ba.ci.as<int32_t>(), csr_ba.v.as<double>(), NB, xin, xin + NA, n, tb1.as<double2>(), nB, 1.0,
                    1.0, 0);
         BEM_TRY(mass_solve(mopB, tb1.as<double2>(), tb2.as<double2>(), R, s, steps));
-        BEM_TRY(prod(Bh32, Bh64, nB, x32b.as<float2>(), tb2.as<double2>(), tb3.as<double2>()));
+        BEM_TRY(prod(Ph, &Bh32, nB, x32b.as<float2>(), tb2.as<double2>(), tb3.as<double2>()));
         BEM_TRY(mass_solve(mopB, tb3.as<double2>(), tb1.as<double2>(), R, s, steps));
         BEM_LAUNCH(k_csr_pair, dim3(blocks_for(n, 64), R), 64, 0, s, csr_ab.rp.as<int32_t>(), csr_ab.ci.as<int32_t>(),
                    csr_ab.v.as<double>(), NA, tb1.as<double2>(), tb1.as<double2>() + NB, nB, z, n, 1.0, 1.0, 1);
@@ -2307,17 +1982,17 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
         return BEM_OK;
     };
     auto apply_hc = [&](bool fp64, const double2* xin, double2* yout, int R, int steps) -> bem_status {
-        auto prod = [&](const Blocks<float2>& b32, const Blocks<double2>& b64, int64_t nn, float2* xw,
-                        const double2* xi, double2* zo) -> bem_status {
-            return fp64 ? gemm_fp64_on(b32, b64, nn, xw, xi, zo, R) : gemm_work_on(b32, b64, nn, xw, xi, zo, R);
+        auto prod = [&](const TileProd& P, const Blocks<float2>* tcb, int64_t nn, float2* xw, const double2* xi,
+                        double2* zo) -> bem_status {
+            return fp64 ? gemm_fp64_on(P, nn, xi, zo, R) : gemm_work_on(P, tcb, nn, xw, xi, zo, R);
         };
         double2* w = hw.as<double2>();
-        BEM_TRY(prod(B32, B64, n, x32.as<float2>(), xin, z));
+        BEM_TRY(prod(P0, &B32, n, x32.as<float2>(), xin, z));
         BEM_TRY(mass_solve(mop, z, w, R, s, steps));
         if (hc_neu) BEM_TRY(csr_pair(csr_ba, NB, xin, w + NA, n, tb1.as<double2>(), nB, 1.0, 1.0, R));
         else BEM_TRY(csr_pair(csr_ba, NB, w + NA, xin + NA, n, tb1.as<double2>(), nB, 1.0, 1.0, R));
         BEM_TRY(mass_solve(mopB, tb1.as<double2>(), tb2.as<double2>(), R, s, steps));
-        BEM_TRY(prod(Bh32, Bh64, nB, x32b.as<float2>(), tb2.as<double2>(), tb3.as<double2>()));
+        BEM_TRY(prod(Ph, &Bh32, nB, x32b.as<float2>(), tb2.as<double2>(), tb3.as<double2>()));
         BEM_TRY(mass_solve(mopB, tb3.as<double2>(), tb1.as<double2>(), R, s, steps));
         // tb1 = (M_B^-1 h; 0): P_AB of its first half into half 0 (Neumann) or 1 (Dirichlet)
         const double2* t0 = tb1.as<double2>();
@@ -2332,14 +2007,14 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
         const int steps = !mixed ? CHEB_STEPS : (R == 1 && dd_now()) ? CHEB_STEPS_DD : CHEB_STEPS_INNER;
         if (hc) return apply_hc(false, xin, yout, R, steps);
         if (st) return apply_single(false, xin, yout, R, steps);
-        BEM_TRY(gemm_work_on(B32, B64, n, x32.as<float2>(), xin, z, R));
+        BEM_TRY(gemm_work_on(P0, &B32, n, x32.as<float2>(), xin, z, R));
         BEM_TRY(transfer_add(top, R, xin, z, s));
         return mass_solve(mop, z, yout, R, s, steps);
     };
     Apply apply_fp64 = [&](const double2* xin, double2* yout, int R) -> bem_status {
         if (hc) return apply_hc(true, xin, yout, R, CHEB_STEPS);
         if (st) return apply_single(true, xin, yout, R, CHEB_STEPS);
-        BEM_TRY(gemm_fp64_on(B32, B64, n, x32.as<float2>(), xin, z, R));
+        BEM_TRY(gemm_fp64_on(P0, n, xin, z, R));
         BEM_TRY(transfer_add(top, R, xin, z, s));
         return mass_solve(mop, z, yout, R, s, CHEB_STEPS);
     };
@@ -2382,7 +2057,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                 const double2* src = hc_neu ? mF : mF + Ne;
                 BEM_TRY(csr_pair(csr_p, Ni, src, src, 2 * Ne, tb1.as<double2>(), nB, 1.0, 0.0, R));
                 BEM_TRY(mass_solve(mopB, tb1.as<double2>(), tb2.as<double2>(), R, s, CHEB_STEPS));
-                BEM_TRY(gemm_fp64_on(Br32, Br64, nB, x32b.as<float2>(), tb2.as<double2>(), tb3.as<double2>(), R));
+                BEM_TRY(gemm_fp64_on(Pr, nB, tb2.as<double2>(), tb3.as<double2>(), R));
                 BEM_TRY(mass_solve(mopB, tb3.as<double2>(), tb1.as<double2>(), R, s, CHEB_STEPS));
                 BEM_TRY(csr_pair(csr_t, Ne, tb1.as<double2>(), tb1.as<double2>(), nB, hz2.as<double2>(), n, 1.0, 0.0,
                                  R));
@@ -2391,7 +2066,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                 else { C.c[2] = -1.0; C.c[6 + 0] = -1.0; }
                 BEM_TRY(pair_lin(bvec.as<double2>(), hz2.as<double2>(), F, F, Ne, R, C));
             } else {
-                BEM_TRY(gemm_fp64_on(Br32, Br64, nB, x32b.as<float2>(), mF, tb3.as<double2>(), R));
+                BEM_TRY(gemm_fp64_on(Pr, nB, mF, tb3.as<double2>(), R));
                 PairCoef C{};  // (x = product, u = F): x_0 + F_1 / 2 (Neumann) or x_0 + F_0 / 2
                 C.c[0] = 1.0;
                 C.c[hc_neu ? 3 : 2] = 0.5;
@@ -2479,7 +2154,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
             // the unknowns' grid traces from the representation formula:
             //   exterior Neumann (M_e^-1 (f + V_e mu) negated; -a), Dirichlet (-b; -M_e^-1 (g + D_e nu)),
             //   interior Neumann (M_i^-1 V_i mu; a), Dirichlet (b; M_i^-1 D_i nu)
-            BEM_TRY(gemm_fp64_on(Bo32, Bo64, n, x32.as<float2>(), xsol.as<double2>(), z, R));
+            BEM_TRY(gemm_fp64_on(Pq, n, xsol.as<double2>(), z, R));
             const double2* zin = z;
             if (!st_int) {
                 PairCoef C{};  // z_0 + F_0 (Neumann) or z_0 + F_1, F = -(f; g)
@@ -2531,6 +2206,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
             return BEM_E_INTERNAL;
         }
     }
+    BEM_TRY(check_tile_flag(tperr));
     BEM_TRY(csync.check());
     if (result == BEM_E_NOT_CONVERGED)
         set_error("GMRES did not reach the tolerance within gmres_maxiter iterations; outputs hold the last iterate");
@@ -2559,97 +2235,9 @@ namespace {
 
 struct InstDesc {
     int64_t off, n;    // the instance's vector occupies [off, off + n) of the concatenation
-    Blocks<float2> B;  // complex64 operator blocks (vector offsets relative to off)
     MassPair M;        // mass matrices of its two grids
     TransferCsr T;     // mortar transfer
 };
-
-// complex64 blocks, FP32 arithmetic, one warp per global row (compensated as k_gemm32)
-__global__ void __launch_bounds__(256) k_gemm32_many(const InstDesc* __restrict__ D, const int32_t* __restrict__ row_inst,
-                                                     int64_t total, const float2* __restrict__ xall,
-                                                     double2* __restrict__ z) {
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw >= total) return;
-    const InstDesc& d = D[row_inst[gw]];
-    const int64_t li = gw - d.off;
-    int b = 0;
-    while (b < 3 && li >= d.B.base[b + 1]) ++b;
-    const int64_t N = d.B.rows[b], i = li - d.B.base[b];
-    const float2* __restrict__ x = xall + d.off;
-    double2 out = make_double2(0, 0);
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-        const float2* __restrict__ a = (m == 0 ? d.B.A1[b] : d.B.A2[b]) + i * N;
-        const int64_t xo = m == 0 ? d.B.x1[b] : d.B.x2[b];
-        float sr = 0.f, si = 0.f, er = 0.f, ei = 0.f;
-        const int64_t j0 = ((reinterpret_cast<uintptr_t>(a) & 15) != 0) ? 1 : 0;
-        if (j0 && lane == 0 && N > 0) {
-            const float2 av = a[0], xx = x[xo];
-            sr = fmaf(av.x, xx.x, -av.y * xx.y);
-            si = fmaf(av.x, xx.y, av.y * xx.x);
-        }
-        const int64_t npair = (N - j0) / 2;
-        const float4* __restrict__ a4 = reinterpret_cast<const float4*>(a + j0);
-        for (int64_t p = lane; p < npair; p += 64) {
-            float cr = 0.f, ci = 0.f;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t pp = p + 32 * h;
-                if (pp < npair) {
-                    const float4 av = a4[pp];
-                    const int64_t j = j0 + 2 * pp;
-                    const float2 x0 = x[xo + j], x1 = x[xo + j + 1];
-                    cr = fmaf(av.x, x0.x, cr); cr = fmaf(-av.y, x0.y, cr);
-                    ci = fmaf(av.x, x0.y, ci); ci = fmaf(av.y, x0.x, ci);
-                    cr = fmaf(av.z, x1.x, cr); cr = fmaf(-av.w, x1.y, cr);
-                    ci = fmaf(av.z, x1.y, ci); ci = fmaf(av.w, x1.x, ci);
-                }
-            }
-            float t, e;
-            two_sum_f(sr, cr, t, e); sr = t; er += e;
-            two_sum_f(si, ci, t, e); si = t; ei += e;
-        }
-        if (((N - j0) & 1) && lane == 1) {
-            const float2 av = a[N - 1], xx = x[xo + N - 1];
-            float t, e;
-            two_sum_f(sr, fmaf(av.x, xx.x, -av.y * xx.y), t, e); sr = t; er += e;
-            two_sum_f(si, fmaf(av.x, xx.y, av.y * xx.x), t, e); si = t; ei += e;
-        }
-        const double2 v = warp_sum2(make_double2((double)sr + (double)er, (double)si + (double)ei));
-        const double c = m == 0 ? d.B.c1[b] : d.B.c2[b];
-        out.x += c * v.x;
-        out.y += c * v.y;
-    }
-    if (lane == 0) z[gw] = out;
-}
-
-// complex64 blocks, FP64 arithmetic (outer residual of the refinement)
-__global__ void __launch_bounds__(256) k_gemm_c64_f64_many(const InstDesc* __restrict__ D,
-                                                           const int32_t* __restrict__ row_inst, int64_t total,
-                                                           const double2* __restrict__ xall, double2* __restrict__ z) {
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw >= total) return;
-    const InstDesc& d = D[row_inst[gw]];
-    const int64_t li = gw - d.off;
-    int b = 0;
-    while (b < 3 && li >= d.B.base[b + 1]) ++b;
-    const int64_t N = d.B.rows[b], i = li - d.B.base[b];
-    const double2* __restrict__ x = xall + d.off;
-    const float2* __restrict__ a1 = d.B.A1[b] + i * N;
-    const float2* __restrict__ a2 = d.B.A2[b] + i * N;
-    const int64_t x1 = d.B.x1[b], x2 = d.B.x2[b];
-    double2 s1 = make_double2(0, 0), s2 = make_double2(0, 0);
-    for (int64_t j = lane; j < N; j += 32) {
-        const float2 p = a1[j], q = a2[j];
-        s1 = cfma(make_double2(p.x, p.y), x[x1 + j], s1);
-        s2 = cfma(make_double2(q.x, q.y), x[x2 + j], s2);
-    }
-    const double2 u = warp_sum2(s1), v = warp_sum2(s2);
-    const double c1 = d.B.c1[b], c2 = d.B.c2[b];
-    if (lane == 0) z[gw] = make_double2(c1 * u.x + c2 * v.x, c1 * u.y + c2 * v.y);
-}
 
 __global__ void k_transfer_many(const InstDesc* __restrict__ D, const int32_t* __restrict__ row_inst, int64_t total,
                                 const double2* __restrict__ xall, double2* __restrict__ zall) {
@@ -2977,7 +2565,8 @@ bem_status gmres_run_many(const ManyLayout& L, ManyGmres& W, const ApplyMany& ap
 
 // operators, masses and mortar of one instance (owned buffers)
 struct InstanceData {
-    DevBuf M[8], mve, mvi, dve, dvi, prow, pcol, pval;
+    GridOps ops[2];  // exterior, interior
+    DevBuf mve, mvi, dve, dvi, prow, pcol, pval;
     CsrBuf csr_p, csr_t;
     MassEll ell_e, ell_i;
 };
@@ -2995,28 +2584,27 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     std::vector<const bem_grid*> grids;
     std::vector<double> kre, kim;
     std::vector<float2*> PV, PK, PT, PD;
+    const OpLayouts TL = op_layouts_tiled();
     for (int i = 0; i < count; ++i) {
-        const int64_t Ne = inst[i].ext->nv, Ni = inst[i].intr->nv;
-        for (int m = 0; m < 8; ++m) {
-            const size_t bytes = (size_t)(m < 4 ? Ne * Ne : Ni * Ni) * 8;
-            BEM_TRY(data[i].M[m].alloc(bytes, s));
-            BEM_CUDA_TRY(cudaMemsetAsync(data[i].M[m].p, 0, bytes, s));
-        }
         for (int side = 0; side < 2; ++side) {
-            grids.push_back(side == 0 ? inst[i].ext : inst[i].intr);
+            const bem_grid* g = side == 0 ? inst[i].ext : inst[i].intr;
+            GridOps& go = data[i].ops[side];
+            BEM_TRY(go.alloc(g->nv, 8, s));
+            grids.push_back(g);
             const bem_c128 k = side == 0 ? inst[i].k_ext : inst[i].k_int;
             kre.push_back(k.re);
             kim.push_back(k.im);
-            PV.push_back(data[i].M[4 * side + 0].as<float2>());
-            PK.push_back(data[i].M[4 * side + 1].as<float2>());
-            PT.push_back(data[i].M[4 * side + 2].as<float2>());
-            PD.push_back(data[i].M[4 * side + 3].as<float2>());
+            PV.push_back(go.V.as<float2>());
+            PK.push_back(go.K.as<float2>());
+            PT.push_back(nullptr);
+            PD.push_back(go.D.as<float2>());
         }
     }
     BEM_TRY(assemble_regular_fp32_many((int)grids.size(), grids.data(), kre.data(), kim.data(), PV.data(), PK.data(),
-                                       PT.data(), PD.data(), s));
+                                       PT.data(), PD.data(), TL, s));
     for (size_t g = 0; g < grids.size(); ++g)
-        BEM_TRY(assemble_singular_into_c64(grids[g], kre[g], kim[g], o->n_singular, PV[g], PK[g], PT[g], PD[g], s));
+        BEM_TRY(assemble_singular_into_c64(grids[g], kre[g], kim[g], o->n_singular, PV[g], PK[g], PT[g], PD[g], TL,
+                                           s));
     cudaEventRecord(t_asm.b, s);
     // ---- masses and mortar, instance by instance
     cudaEventRecord(t_mor.a, s);
@@ -3040,6 +2628,7 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     // ---- concatenated layout and instance descriptors
     ManyLayout L;
     L.count = count;
+    TileProd PM;  // the dense products of all instances, one tile-product launch
     std::vector<InstDesc> desc(count);
     std::vector<int32_t> rinst;
     std::vector<int64_t> cs, ce;
@@ -3052,9 +2641,11 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
         InstDesc& D = desc[i];
         D.off = L.total;
         D.n = n;
-        const float2* m1[4] = {d.M[1].as<float2>(), d.M[3].as<float2>(), d.M[5].as<float2>(), d.M[7].as<float2>()};
-        const float2* m2[4] = {d.M[0].as<float2>(), d.M[2].as<float2>(), d.M[4].as<float2>(), d.M[6].as<float2>()};
-        fill_blocks(D.B, m1, m2, Ne, Ni);
+        // the instance's multiple-traces blocks, at its offset in the concatenation
+        const int64_t o0 = D.off;
+        d.ops[0].add(PM, -1.0, 1.0, 1.0, 1.0, o0, o0 + Ne, o0, o0 + Ne, o0, o0 + Ne);
+        d.ops[1].add(PM, -1.0, 1.0, 1.0, 1.0, o0 + 2 * Ne, o0 + 2 * Ne + Ni, o0 + 2 * Ne, o0 + 2 * Ne + Ni,
+                     o0 + 2 * Ne, o0 + 2 * Ne + Ni);
         BEM_TRY(d.ell_e.build(inst[i].ext, d.mve.as<double>(), s));
         BEM_TRY(d.ell_i.build(inst[i].intr, d.mvi.as<double>(), s));
         D.M.ci[0] = d.ell_e.ci.as<int32_t>(); D.M.v[0] = d.ell_e.v.as<double>(); D.M.W[0] = d.ell_e.W;
@@ -3095,10 +2686,14 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     const InstDesc* Dd = L.desc.as<InstDesc>();
     const int32_t* RI = L.row_inst.as<int32_t>();
     // ---- workspaces
-    DevBuf z, wr, wa, wb, x32, bvec, sb, xsol, dvec, rvec, tmp, fg;
+    DevBuf z, wr, wa, wb, x32, bvec, sb, xsol, dvec, rvec, tmp, fg, xsplit, part, tperr;
     for (DevBuf* b : {&z, &wr, &wa, &wb, &bvec, &sb, &xsol, &dvec, &rvec, &tmp}) BEM_TRY(b->alloc((size_t)T * 16, s));
     BEM_TRY(x32.alloc((size_t)T * 8, s));
-    const unsigned rows_blocks = blocks_for(T * 32, 256);
+    BEM_TRY(xsplit.alloc((size_t)T * 16, s));
+    BEM_TRY(tile_prod_finish(PM, T, 8, s));
+    BEM_TRY(part.alloc(tile_part_bytes(PM, TP_DD, 1), s));
+    BEM_TRY(tperr.alloc(sizeof(int), s));
+    BEM_CUDA_TRY(cudaMemsetAsync(tperr.p, 0, sizeof(int), s));
     const double theta = 0.5 * (CHEB_BETA + CHEB_ALPHA), delta = 0.5 * (CHEB_BETA - CHEB_ALPHA);
     const double sigma = theta / delta;
     GraphCache graphs(o->cuda_graphs != 0);
@@ -3123,12 +2718,13 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     };
     ApplyMany apply_work = [&](const double2* xin, double2* yout) -> bem_status {
         BEM_LAUNCH(k_to_c64, blocks_for(T, 256), 256, 0, s, xin, T, x32.as<float2>());
-        BEM_LAUNCH(k_gemm32_many, rows_blocks, 256, 0, s, Dd, RI, T, x32.as<float2>(), z.as<double2>());
+        BEM_TRY(tile_product(PM, TP_F32, 1, x32.p, z.as<double2>(), part.p, tperr.as<int>(), s));
         BEM_LAUNCH(k_transfer_many, blocks_for(T, 64), 64, 0, s, Dd, RI, T, xin, z.as<double2>());
         return mass_many(z.as<double2>(), yout, CHEB_STEPS_INNER);
     };
     ApplyMany apply_fp64 = [&](const double2* xin, double2* yout) -> bem_status {
-        BEM_LAUNCH(k_gemm_c64_f64_many, rows_blocks, 256, 0, s, Dd, RI, T, xin, z.as<double2>());
+        BEM_LAUNCH(k_split_x, blocks_for(T, 256), 256, 0, s, xin, T, xsplit.as<float4>());
+        BEM_TRY(tile_product(PM, TP_DD, 1, xsplit.p, z.as<double2>(), part.p, tperr.as<int>(), s));
         BEM_LAUNCH(k_transfer_many, blocks_for(T, 64), 64, 0, s, Dd, RI, T, xin, z.as<double2>());
         return mass_many(z.as<double2>(), yout, CHEB_STEPS);
     };
@@ -3207,6 +2803,7 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     }
     cudaEventRecord(t_sol.b, s);
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    BEM_TRY(check_tile_flag(tperr));
     bem_status result = BEM_OK;
     const float ms_asm = t_asm.ms(), ms_mor = t_mor.ms(), ms_sol = t_sol.ms();
     for (int r = 0; r < count; ++r) {
@@ -3278,34 +2875,15 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
     BEM_TRY(dkeep.alloc((size_t)N, s));
     BEM_CUDA_TRY(cudaMemcpyAsync(dkeep.p, keep.data(), (size_t)N, cudaMemcpyHostToDevice, s));
     const uint8_t* K8 = dkeep.as<uint8_t>();
-    // ---- operators: D on the screen, V on the coarse grid
+    // ---- operators: D on the screen, V on the coarse grid (tiled storage)
     const size_t esz = mixed ? 8 : 16;
-    DevBuf Dm, Vc;
-    BEM_TRY(Dm.alloc((size_t)N * N * esz, s));
-    if (oo) BEM_TRY(Vc.alloc((size_t)Nc * Nc * esz, s));
+    const bool same = oo && gc == gf;  // conforming: V of the screen itself, from the same assembly pass
+    GridOps opF, opC;
     cudaEventRecord(t_asm.a, s);
-    if (mixed) {
-        // the conforming preconditioner's V comes out of the same assembly pass as D
-        float2* Vsame = oo && gc == gf ? Vc.as<float2>() : nullptr;
-        BEM_CUDA_TRY(cudaMemsetAsync(Dm.p, 0, Dm.bytes, s));
-        if (Vsame) BEM_CUDA_TRY(cudaMemsetAsync(Vc.p, 0, Vc.bytes, s));
-        BEM_TRY(assemble_regular_fp32(gf, k.re, k.im, Vsame, nullptr, nullptr, Dm.as<float2>(), s));
-        BEM_TRY(assemble_singular_into_c64(gf, k.re, k.im, o->n_singular, Vsame, nullptr, nullptr, Dm.as<float2>(),
-                                           s));
-        if (oo && gc != gf) {
-            BEM_CUDA_TRY(cudaMemsetAsync(Vc.p, 0, Vc.bytes, s));
-            BEM_TRY(assemble_regular_fp32(gc, k.re, k.im, Vc.as<float2>(), nullptr, nullptr, nullptr, s));
-            BEM_TRY(assemble_singular_into_c64(gc, k.re, k.im, o->n_singular, Vc.as<float2>(), nullptr, nullptr,
-                                               nullptr, s));
-        }
-    } else {
-        BEM_TRY(assemble_operators_fp64(gf, k.re, k.im, o->n_singular, oo && gc == gf ? Vc.as<double2>() : nullptr,
-                                        nullptr, nullptr, Dm.as<double2>(), s));
-        if (oo && gc != gf)
-            BEM_TRY(assemble_operators_fp64(gc, k.re, k.im, o->n_singular, Vc.as<double2>(), nullptr, nullptr, nullptr,
-                                            s));
-    }
+    BEM_TRY(opF.assemble(gf, k, mixed, o->n_singular, s, same, false, true));
+    if (oo && !same) BEM_TRY(opC.assemble(gc, k, mixed, o->n_singular, s, true, false, false));
     cudaEventRecord(t_asm.b, s);
+    const GridOps& opV = same ? opF : opC;
     // ---- mass matrices (the screen's restricted to its interior nodes) and mortar
     cudaEventRecord(t_mor.a, s);
     DevBuf mvf, dvf, mvc, dvc, prow, pcol, pval;
@@ -3362,7 +2940,21 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
     const bool dd_single = mixed && RB == 1;
     double inner_progress = 1.0;
     auto dd_now = [&]() { return dd_single && inner_progress > o->dd_switch; };
-    if (dd_single) BEM_TRY(xsplit.alloc((size_t)std::max(N, Nc) * 16, s));
+    DevBuf part, tperr;
+    BEM_TRY(xsplit.alloc((size_t)8 * std::max(N, Nc) * 16, s));
+    // one-matrix products: D phi on the screen (y2 = D x) and V c on the coarse grid (y1 = V x)
+    TileProd PD, PV;
+    opF.add(PD, 0.0, 0.0, 1.0, 0.0, 0, 0, 0, 0, -1, 0);
+    BEM_TRY(tile_prod_finish(PD, N, (int)esz, s));
+    size_t pbytes = tile_part_bytes(PD, TP_DD, std::min(RB, 8));
+    if (oo) {
+        opV.add(PV, 0.0, 1.0, 0.0, 0.0, 0, 0, 0, 0, 0, -1);
+        BEM_TRY(tile_prod_finish(PV, Nc, (int)esz, s));
+        pbytes = std::max(pbytes, tile_part_bytes(PV, TP_DD, std::min(RB, 8)));
+    }
+    BEM_TRY(part.alloc(pbytes, s));
+    BEM_TRY(tperr.alloc(sizeof(int), s));
+    BEM_CUDA_TRY(cudaMemsetAsync(tperr.p, 0, sizeof(int), s));
     MassOp mf;
     mf.M.ci[0] = ell_f.ci.as<int32_t>(); mf.M.v[0] = ell_f.v.as<double>(); mf.M.W[0] = ell_f.W;
     mf.M.dinv[0] = dvf.as<double>();
@@ -3390,53 +2982,22 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
         mc.graphs = &graphs;
         if (ctx->exclusive) csync.attach(mc);
     }
-    Blocks<float2> BD32{}, BV32{};
-    Blocks<double2> BD64{}, BV64{};
-    if (mixed) {
-        fill_blocks_row(BD32, Dm.as<float2>(), 0, 1.0, (float2*)nullptr, 0, 0.0, N);
-        if (oo) fill_blocks_row(BV32, Vc.as<float2>(), 0, 1.0, (float2*)nullptr, 0, 0.0, Nc);
-    } else {
-        fill_blocks_row(BD64, Dm.as<double2>(), 0, 1.0, (double2*)nullptr, 0, 0.0, N);
-        if (oo) fill_blocks_row(BV64, Vc.as<double2>(), 0, 1.0, (double2*)nullptr, 0, 0.0, Nc);
-    }
-    // zo = one-matrix product on nn rows in the working arithmetic or in FP64 arithmetic
-    auto product = [&](bool fp64, const Blocks<float2>& b32, const Blocks<double2>& b64, int64_t nn, float2* xw,
-                       const double2* xin, double2* zo, int R) -> bem_status {
-        const unsigned rows_blocks = blocks_for(nn * 32, 256);
-        if (!mixed) {
-            const Blocks<double2> d64 = both_matrices(b64);
-            for (int c0 = 0; c0 < R; c0 += 8) {
-                const int Wd = gemm_width(std::min(8, R - c0));
-                const double2* xc = xin + (int64_t)c0 * nn;
-                double2* zc = zo + (int64_t)c0 * nn;
-                if (Wd == 1) BEM_LAUNCH(k_gemm64<1>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
-                else if (Wd == 2) BEM_LAUNCH(k_gemm64<2>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
-                else if (Wd == 4) BEM_LAUNCH(k_gemm64<4>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
-                else BEM_LAUNCH(k_gemm64<8>, rows_blocks, 256, 0, s, d64, nn, xc, zc);
-            }
-            return BEM_OK;
-        }
-        if (fp64) {
-            const Blocks<float2> d32 = both_matrices(b32);
-            for (int c0 = 0; c0 < R; c0 += 8) {
-                const int Wd = gemm_width(std::min(8, R - c0));
-                const double2* xc = xin + (int64_t)c0 * nn;
-                double2* zc = zo + (int64_t)c0 * nn;
-                if (Wd == 1) BEM_LAUNCH(k_gemm_c64_f64<1>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
-                else if (Wd == 2) BEM_LAUNCH(k_gemm_c64_f64<2>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
-                else if (Wd == 4) BEM_LAUNCH(k_gemm_c64_f64<4>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
-                else BEM_LAUNCH(k_gemm_c64_f64<8>, rows_blocks, 256, 0, s, d32, nn, xc, zc);
-            }
-            return BEM_OK;
-        }
-        if (R == 1 && dd_now()) {
-            BEM_LAUNCH(k_split_x, blocks_for(nn, 256), 256, 0, s, xin, nn, xsplit.as<float4>());
-            return launch_gemv_dd(b32, nn, xsplit.as<float4>(), zo, s);
-        }
-        BEM_LAUNCH(k_to_c64, blocks_for((int64_t)R * nn, 256), 256, 0, s, xin, (int64_t)R * nn, xw);
+    // zo = one-matrix product P on nn rows: FP32 (mixed), double-float (FP64 mode, FP64
+    // residuals of the refinement, single-column products above the dd_switch)
+    auto product = [&](bool fp64, const TileProd& P, int64_t nn, float2* xw, const double2* xin, double2* zo,
+                       int R) -> bem_status {
+        const bool dd = !mixed || fp64 || (R == 1 && dd_now());
+        if (!dd) BEM_LAUNCH(k_to_c64, blocks_for((int64_t)R * nn, 256), 256, 0, s, xin, (int64_t)R * nn, xw);
         for (int c0 = 0; c0 < R; c0 += 8) {
-            const int Wd = gemm_width(std::min(8, R - c0));
-            BEM_TRY(launch_gemm32(Wd, b32, nn, xw + (int64_t)c0 * nn, zo + (int64_t)c0 * nn, s));
+            const int w = std::min(8, R - c0);
+            double2* zc = zo + (int64_t)c0 * nn;
+            if (dd) {
+                BEM_LAUNCH(k_split_x, blocks_for((int64_t)w * nn, 256), 256, 0, s, xin + (int64_t)c0 * nn,
+                           (int64_t)w * nn, xsplit.as<float4>());
+                BEM_TRY(tile_product(P, TP_DD, w, xsplit.p, zc, part.p, tperr.as<int>(), s));
+            } else {
+                BEM_TRY(tile_product(P, TP_F32, w, xw + (int64_t)c0 * nn, zc, part.p, tperr.as<int>(), s));
+            }
         }
         return BEM_OK;
     };
@@ -3448,7 +3009,7 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
         BEM_LAUNCH(k_csr_apply, dim3(blocks_for(Nc, 128), R), 128, 0, s, csr_cf.rp.as<int32_t>(),
                    csr_cf.ci.as<int32_t>(), csr_cf.v.as<double>(), Nc, u.as<double2>(), N, c1.as<double2>(), Nc, 1.0);
         BEM_TRY(mass_solve(mc, c1.as<double2>(), c2.as<double2>(), R, s, steps));
-        BEM_TRY(product(fp64, BV32, BV64, Nc, x32c.as<float2>(), c2.as<double2>(), c3.as<double2>(), R));
+        BEM_TRY(product(fp64, PV, Nc, x32c.as<float2>(), c2.as<double2>(), c3.as<double2>(), R));
         BEM_TRY(mass_solve(mc, c3.as<double2>(), c1.as<double2>(), R, s, steps));
         BEM_LAUNCH(k_csr_apply, dim3(blocks_for(N, 128), R), 128, 0, s, csr_fc.rp.as<int32_t>(),
                    csr_fc.ci.as<int32_t>(), csr_fc.v.as<double>(), N, c1.as<double2>(), Nc, u.as<double2>(), N, 1.0);
@@ -3456,7 +3017,7 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
         return mass_solve(mf, u.as<double2>(), y, R, s, steps);
     };
     auto apply_on = [&](bool fp64, const double2* xin, double2* yout, int R, int steps) -> bem_status {
-        BEM_TRY(product(fp64, BD32, BD64, N, x32.as<float2>(), xin, z.as<double2>(), R));
+        BEM_TRY(product(fp64, PD, N, x32.as<float2>(), xin, z.as<double2>(), R));
         return precondition(fp64, z.as<double2>(), yout, R, steps);
     };
     Apply apply_work = [&](const double2* xin, double2* yout, int R) -> bem_status {
@@ -3547,6 +3108,7 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
     }
     cudaEventRecord(t_sol.b, s);
     BEM_CUDA_TRY(cudaStreamSynchronize(s));
+    BEM_TRY(check_tile_flag(tperr));
     BEM_TRY(csync.check());
     if (result == BEM_E_NOT_CONVERGED)
         set_error("GMRES did not reach the tolerance within gmres_maxiter iterations; outputs hold the last iterate");

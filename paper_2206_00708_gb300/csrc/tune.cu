@@ -27,7 +27,7 @@ struct TuneEntry {
 std::mutex g_tune_mu;
 std::vector<TuneEntry> g_tune;
 
-const char* const kNames[TUNE_KERNELS] = {"gemm32", "gemv_dd", "gemm_tc", "cheb"};
+const char* const kNames[TUNE_KERNELS] = {"gemm_tc", "cheb"};
 
 int kernel_id(const std::string& name) {
     for (int k = 0; k < TUNE_KERNELS; ++k)

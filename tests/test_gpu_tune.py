@@ -38,11 +38,7 @@ def test_autotune_fills_the_table_and_keeps_results(env, tmp_path):
         ref64 = bem.bem_solve_transmission(ctx, ge, gi, 3.0, 2.0, 1.5, dirs[:3])[0]
         refmx = bem.bem_solve_transmission(ctx, ge, gi, 3.0, 2.0, 1.5, dirs, opts={"precision": 1})[0]
         bem.bem_autotune(ctx, ge, gi, 12)
-        assert bem.bem_tune_count() == 4 + 1 + 2 + 1
-        for w in (1, 2, 4, 8):
-            b, v, ms = bem.bem_tune_get("gemm32", w, n)
-            assert b in (128, 256, 512) and v in (2, 4) and ms > 0.0
-        assert bem.bem_tune_get("gemv_dd", 1, n)[0] in (128, 256, 512)
+        assert bem.bem_tune_count() == 2 + 1
         for w in (1, 8):
             assert bem.bem_tune_get("cheb", w, n)[0] in (64, 128, 256)
         b, v, ms = bem.bem_tune_get("gemm_tc", 16, n)
@@ -56,7 +52,7 @@ def test_autotune_fills_the_table_and_keeps_results(env, tmp_path):
         bem.bem_tune_save(str(p))
         bem.bem_tune_clear()
         bem.bem_tune_load(str(p))
-        assert bem.bem_tune_count() == 8
+        assert bem.bem_tune_count() == 3
     finally:
         bem.bem_tune_clear()
         bem.bem_grid_destroy(ge)
