@@ -101,12 +101,13 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     const float bb = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
-// (h, l) += (bh, bl)
+// (h, l) += (bh, bl); symmetric in its two operands (the same bits for a + b and b + a),
+// so that a butterfly gives the same sums whichever lane keeps which half
 __device__ __forceinline__ void dd_add(float& h, float& l, float bh, float bl) {
     float s, e;
     two_sum(h, bh, s, e);
     h = s;
-    l = __fadd_rn(l, __fadd_rn(e, bl));
+    l = __fadd_rn(__fadd_rn(l, bl), e);
 }
 // (h, l) += a (ah + al) times x (xh + xl): the main product exactly (two-product by FMA),
 // the cross terms rounded (2^-24 of the main term), al xl dropped (2^-48)
@@ -620,14 +621,20 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tile(TileLaunch L) {
 }
 
 // z rows of every active output: the sum over the partial-sum slots of the row's tile
-// row, in slot order, in double-float; one CTA per (set, output, tile row).
+// row in double-float, one CTA per (set, output, tile row) and column; the 64 rows x 4
+// groups of slots (slot J to group J mod 4, the groups then added in order) give the
+// same summation order for any number of columns, so a batched column equals the same
+// column computed alone.
+constexpr int RED_GROUPS = 4;
 template <int MODE, int R>
-__global__ void __launch_bounds__(512) k_tile_reduce(const TileSet* __restrict__ sets, int nsets, int64_t rtiles,
-                                                     int64_t n, int rc, const void* __restrict__ part,
-                                                     double2* __restrict__ z) {
+__global__ void __launch_bounds__(64 * RED_GROUPS) k_tile_reduce(const TileSet* __restrict__ sets, int nsets,
+                                                                 int64_t rtiles, int64_t n,
+                                                                 const void* __restrict__ part,
+                                                                 double2* __restrict__ z) {
     using A = typename Arith<MODE>::A;
-    __shared__ float4 sh[512];
+    __shared__ float4 sh[64 * RED_GROUPS];
     const int64_t b = blockIdx.x;
+    const int r = blockIdx.y;
     int lo = 0, hi = nsets - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -640,28 +647,25 @@ __global__ void __launch_bounds__(512) k_tile_reduce(const TileSet* __restrict__
     const int64_t I = (b - St.rtile0) % nt;
     const int64_t yoff = out == 0 ? St.y1 : St.y2;
     if (yoff < 0) return;
-    const int groups = blockDim.x / (64 * R);
     const int t = threadIdx.x;
-    const int row = t & 63, r = (t >> 6) % R, jg = t / (64 * R);
+    const int row = t & 63, jg = t >> 6;
     float sr = 0.f, srl = 0.f, si = 0.f, sil = 0.f;
     const A* __restrict__ p = static_cast<const A*>(part) + St.part * R + (((out * nt + I) * nt) * R << 6);
-    if (r < rc) {
-        for (int64_t J = jg; J < nt; J += groups) {
-            const A a = p[((J * R + r) << 6) + row];
-            if constexpr (MODE == TP_F32) {
-                dd_add(sr, srl, a.x, 0.0f);
-                dd_add(si, sil, a.y, 0.0f);
-            } else {
-                dd_add(sr, srl, a.x, a.z);
-                dd_add(si, sil, a.y, a.w);
-            }
+    for (int64_t J = jg; J < nt; J += RED_GROUPS) {
+        const A a = p[((J * R + r) << 6) + row];
+        if constexpr (MODE == TP_F32) {
+            dd_add(sr, srl, a.x, 0.0f);
+            dd_add(si, sil, a.y, 0.0f);
+        } else {
+            dd_add(sr, srl, a.x, a.z);
+            dd_add(si, sil, a.y, a.w);
         }
     }
     sh[t] = make_float4(sr, si, srl, sil);
     __syncthreads();
-    if (jg != 0 || r >= rc) return;
-    for (int g = 1; g < groups; ++g) {
-        const float4 o = sh[t + g * 64 * R];
+    if (jg != 0) return;
+    for (int g = 1; g < RED_GROUPS; ++g) {
+        const float4 o = sh[t + g * 64];
         dd_add(sr, srl, o.x, o.z);
         dd_add(si, sil, o.y, o.w);
     }
@@ -709,12 +713,11 @@ bem_status launch_tile(const TileProd& P, int rc, const void* x, double2* z, voi
          {"k_tile<c128,dd,1>", "k_tile<c128,dd,2>", "k_tile<c128,dd,4>", "k_tile<c128,dd,8>"}}};
     const int ri = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : 3;
     BEM_LAUNCH_PTR(names[sizeof(ST) == 16][MODE][ri], (k_tile<ST, MODE, R>), grid, TP_THREADS, LT::BYTES, s, L);
-    const int threads = std::max(256, 64 * R);
     static const char* rnames[2][4] = {
         {"k_tile_reduce<f32,1>", "k_tile_reduce<f32,2>", "k_tile_reduce<f32,4>", "k_tile_reduce<f32,8>"},
         {"k_tile_reduce<dd,1>", "k_tile_reduce<dd,2>", "k_tile_reduce<dd,4>", "k_tile_reduce<dd,8>"}};
-    BEM_LAUNCH_PTR(rnames[MODE][ri], (k_tile_reduce<MODE, R>), (unsigned)P.rtiles, threads, 0, s, L.sets, L.nsets,
-                   P.rtiles, P.n, rc, part, z);
+    BEM_LAUNCH_PTR(rnames[MODE][ri], (k_tile_reduce<MODE, R>), dim3((unsigned)P.rtiles, (unsigned)rc),
+                   64 * RED_GROUPS, 0, s, L.sets, L.nsets, P.rtiles, P.n, part, z);
     return BEM_OK;
 }
 
