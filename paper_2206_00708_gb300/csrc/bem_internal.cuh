@@ -287,7 +287,8 @@ struct TileSet {
     const void* V;
     const void* D;
     int64_t N;
-    int32_t nt, pad;
+    int32_t nt;
+    int32_t flags;          // TS_* bits: the matrices and outputs this set uses
     double c[4];            // cK, cV, cD, cT
     float ch[4], cl[4];     // the same as double-float pairs (high, low)
     int64_t xa, xb, xc, xd;
@@ -296,10 +297,12 @@ struct TileSet {
     int64_t rtile0;         // first output row tile (2 nt per set)
     int64_t part;           // element offset of this set's partial sums (per column)
 };
+enum : int { TS_KROW = 1, TS_KCOL = 2, TS_V = 4, TS_D = 8, TS_Y1 = 16, TS_Y2 = 32 };
 enum : int { TP_F32 = 0, TP_DD = 1 };  // arithmetic: FP32 on complex64; double-float (FP64-accurate)
 struct TileProd {
     std::vector<TileSet> sets;
     DevBuf dsets;            // device copy of sets
+    DevBuf ditems;           // work items: int2 (set, I << 16 | J), in set order
     int64_t items = 0, rtiles = 0, part_per_col = 0;
     int64_t n = 0;           // column length of x and z
     int storage = 8;         // bytes per matrix entry: 8 (complex64) or 16 (complex128)

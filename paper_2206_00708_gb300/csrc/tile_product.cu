@@ -45,8 +45,6 @@ namespace bem {
 
 namespace {
 
-constexpr int TP_WARPS = 8;                       // consumer warps
-constexpr int TP_THREADS = 32 * (TP_WARPS + 1);   // + one producer warp
 constexpr int TP_CHUNK = 32768;                   // bytes per ring stage (one bulk copy)
 constexpr int TP_SMEM_LIMIT = 232448;             // 227 KB of shared memory per CTA
 constexpr long long TP_WAIT_LIMIT = 1ll << 27;    // mbarrier polls before giving up (about a second)
@@ -92,8 +90,9 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
                  : "memory");
 }
 
-// barrier of the eight consumer warps only (the producer warp never joins)
-__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * TP_WARPS) : "memory"); }
+// barrier of the consumer warps only (the producer warp never joins)
+template <int W>
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * W) : "memory"); }
 
 // ---- double-float arithmetic (error-free transformations on the FP32 pipe) ----
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -196,20 +195,33 @@ struct Arith<TP_DD> {
     static constexpr int VAL = 2;
 };
 
-// rows per butterfly group: at most 16 (row, column, re/im) values per lane
-template <int R, int RPW>
-struct Group {
-    static constexpr int G = (8 / R) < RPW ? ((8 / R) < 1 ? 1 : 8 / R) : RPW;
-    static constexpr int NV = G * R * 2;  // values per lane before the butterfly (<= 16)
-};
-
+// Launch shape per (storage, arithmetic, columns): consumer warps (16 for one column,
+// so that four warps per scheduler hide the latencies of the dependent arithmetic; 8
+// for more columns, whose registers would not fit 16), rows per warp per chunk, rows per
+// butterfly group (at most 16 (row, column, re/im) values per lane), shared memory.
 template <class ST, int MODE, int R>
-struct Layout {
+struct Cfg {
+    using X = typename Arith<MODE>::X;
+    using A = typename Arith<MODE>::A;
+    static constexpr int W = R == 1 ? 16 : 8;
+    static constexpr int THREADS = 32 * (W + 1);
     static constexpr int RPC = Store<ST>::RPC;
-    static constexpr int RPW = RPC / TP_WARPS;  // rows per warp per chunk
-    static constexpr int XS = 8 * R * 64 * (int)sizeof(typename Arith<MODE>::X);   // 8 input slices
-    static constexpr int ACC = 4 * R * 64 * (int)sizeof(typename Arith<MODE>::A);  // 4 output slices
-    static constexpr int RED = TP_WARPS * R * 64 * (int)sizeof(typename Arith<MODE>::A);
+    static constexpr int RPW = RPC / W;
+    static constexpr int G = (8 / R) < RPW ? ((8 / R) < 1 ? 1 : 8 / R) : RPW;
+    static constexpr int NV = G * R * 2;
+    static constexpr int XSN = 8 * R * 64;  // elements of one set of input slices
+    static constexpr int ACCN = 4 * R * 64;
+    // input-slice elements per consumer thread; the next item's are prefetched into
+    // registers while the current item streams when there are at most two, and then the
+    // slices and accumulators are double-buffered by item and the column partials of the
+    // three slots are added over the warps in one pass (single-column products)
+    static constexpr int XPT = (XSN + 32 * W - 1) / (32 * W);
+    static constexpr bool PREFETCH = XPT <= 2;
+    static constexpr int NBUF = PREFETCH ? 2 : 1;
+    static constexpr int RSLOTS = PREFETCH ? 3 : 1;
+    static constexpr int XS = NBUF * XSN * (int)sizeof(X);
+    static constexpr int ACC = NBUF * ACCN * (int)sizeof(A);
+    static constexpr int RED = W * RSLOTS * R * 64 * (int)sizeof(A);
     static constexpr int FIXED = XS + ACC + RED + 1024;
     static constexpr int S0 = (TP_SMEM_LIMIT - FIXED) / TP_CHUNK;
     static constexpr int S = S0 > 6 ? 6 : S0;  // ring stages
@@ -219,52 +231,25 @@ struct Layout {
 
 struct TileLaunch {
     const TileSet* sets;
-    int nsets;
-    int rc;         // columns of x and z (<= R)
-    int64_t items;
-    int64_t n;      // column length of x and z
+    const int2* items;  // (set, I << 16 | J)
+    int rc;             // columns of x and z (<= R)
+    int64_t nitems;
+    int64_t n;          // column length of x and z
     const void* x;
     void* part;
     int* err;
 };
 
-struct ItemInfo {
-    int set, I, J;
-};
-
-__device__ ItemInfo decode_item(const TileSet* __restrict__ sets, int nsets, int64_t k) {
-    int lo = 0, hi = nsets - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (sets[mid].item0 <= k) lo = mid;
-        else hi = mid - 1;
-    }
-    const int64_t kk = k - sets[lo].item0;
-    const int64_t nt = sets[lo].nt;
-    // row I of the upper tile triangle starts at item I nt - I (I - 1) / 2
-    const double b = 2.0 * (double)nt + 1.0;
-    int64_t a = (int64_t)floor(0.5 * (b - sqrt(fmax(b * b - 8.0 * (double)kk, 0.0))));
-    a = a < 0 ? 0 : (a > nt - 1 ? nt - 1 : a);
-    while (a > 0 && op_sym_tile(a, a, nt) > kk) --a;
-    while (a + 1 < nt && op_sym_tile(a + 1, a + 1, nt) <= kk) ++a;
-    ItemInfo it;
-    it.set = lo;
-    it.I = (int)a;
-    it.J = (int)(a + (kk - op_sym_tile(a, a, nt)));
-    return it;
-}
-
 // The item's tiles in their fixed order: 0 = K_IJ, 1 = K_JI (I < J), 2 = V_IJ, 3 = D_IJ.
 // Returns the count; kinds[] the tile kinds, src[] their first bytes.
 template <class ST>
-__device__ int item_tiles(const TileSet& S, int I, int J, int kinds[4], const unsigned char* src[4]) {
-    const bool useK = S.K != nullptr && (S.c[0] != 0.0 || S.c[3] != 0.0);
-    const bool useV = S.V != nullptr && S.c[1] != 0.0;
-    const bool useD = S.D != nullptr && S.c[2] != 0.0;
+__device__ __forceinline__ int item_tiles(const TileSet& S, int I, int J, int kinds[4],
+                                          const unsigned char* src[4]) {
+    const int f = S.flags;
     const int64_t nt = S.nt;
     const size_t tb = (size_t)OPT * OPT * sizeof(ST);
     int m = 0;
-    if (useK) {
+    if (f & (TS_KROW | TS_KCOL)) {
         kinds[m] = 0;
         src[m++] = static_cast<const unsigned char*>(S.K) + (size_t)(I * nt + J) * tb;
         if (I != J) {
@@ -272,11 +257,11 @@ __device__ int item_tiles(const TileSet& S, int I, int J, int kinds[4], const un
             src[m++] = static_cast<const unsigned char*>(S.K) + (size_t)(J * nt + I) * tb;
         }
     }
-    if (useV) {
+    if (f & TS_V) {
         kinds[m] = 2;
         src[m++] = static_cast<const unsigned char*>(S.V) + (size_t)op_sym_tile(I, J, nt) * tb;
     }
-    if (useD) {
+    if (f & TS_D) {
         kinds[m] = 3;
         src[m++] = static_cast<const unsigned char*>(S.D) + (size_t)op_sym_tile(I, J, nt) * tb;
     }
@@ -325,46 +310,77 @@ __device__ __forceinline__ void butterfly(float (&v)[NV * VAL], int lane) {
     }
 }
 
+// exact product a x of an entry a = ah + al and an input x = xh + xl: p + e (p = fl(ah xh),
+// e its exact error plus the rounded cross terms)
+template <bool AL>
+__device__ __forceinline__ void dd_prod(float ah, float al, float xh, float xl, float& p, float& e) {
+    p = __fmul_rn(ah, xh);
+    e = fmaf(ah, xh, -p);
+    e = fmaf(ah, xl, e);
+    if (AL) e = fmaf(al, xh, e);
+}
+
+// a0 x0 + a1 x1 (complex) as unnormalised double-float pairs, summed as a tree: four
+// independent exact products per part, two levels of two-sums
+template <bool AL>
+__device__ __forceinline__ void dd_cdot2(const float ah[4], const float al[4], const float xh[2][2],
+                                         const float xl[2][2], float& rh, float& rl, float& ih, float& il) {
+    float p[4], e[4];
+    dd_prod<AL>(ah[0], al[0], xh[0][0], xl[0][0], p[0], e[0]);
+    dd_prod<AL>(-ah[1], -al[1], xh[0][1], xl[0][1], p[1], e[1]);
+    dd_prod<AL>(ah[2], al[2], xh[1][0], xl[1][0], p[2], e[2]);
+    dd_prod<AL>(-ah[3], -al[3], xh[1][1], xl[1][1], p[3], e[3]);
+    float s01, t01, s23, t23, t;
+    two_sum(p[0], p[1], s01, t01);
+    two_sum(p[2], p[3], s23, t23);
+    two_sum(s01, s23, rh, t);
+    rl = __fadd_rn(__fadd_rn(__fadd_rn(e[0], e[1]), __fadd_rn(e[2], e[3])), __fadd_rn(__fadd_rn(t01, t23), t));
+    dd_prod<AL>(ah[0], al[0], xh[0][1], xl[0][1], p[0], e[0]);
+    dd_prod<AL>(ah[1], al[1], xh[0][0], xl[0][0], p[1], e[1]);
+    dd_prod<AL>(ah[2], al[2], xh[1][1], xl[1][1], p[2], e[2]);
+    dd_prod<AL>(ah[3], al[3], xh[1][0], xl[1][0], p[3], e[3]);
+    two_sum(p[0], p[1], s01, t01);
+    two_sum(p[2], p[3], s23, t23);
+    two_sum(s01, s23, ih, t);
+    il = __fadd_rn(__fadd_rn(__fadd_rn(e[0], e[1]), __fadd_rn(e[2], e[3])), __fadd_rn(__fadd_rn(t01, t23), t));
+}
+
 template <class ST, int MODE, int R>
-__global__ void __launch_bounds__(TP_THREADS, 1) k_tile(TileLaunch L) {
-    using LT = Layout<ST, MODE, R>;
-    using X = typename Arith<MODE>::X;
-    using A = typename Arith<MODE>::A;
-    constexpr int S = LT::S;
-    constexpr int CH = Store<ST>::CHUNKS;
-    constexpr int RPC = Store<ST>::RPC;
-    constexpr int RPW = LT::RPW;
-    constexpr int G = Group<R, RPW>::G;
-    constexpr int NV = Group<R, RPW>::NV;
+__global__ void __launch_bounds__(Cfg<ST, MODE, R>::THREADS, 1) k_tile(TileLaunch L) {
+    using C = Cfg<ST, MODE, R>;
+    using X = typename C::X;
+    using A = typename C::A;
+    constexpr int W = C::W, S = C::S, CH = Store<ST>::CHUNKS, RPC = C::RPC, RPW = C::RPW, G = C::G, NV = C::NV;
     constexpr int VAL = Arith<MODE>::VAL;
+    constexpr int NT = 32 * W;  // consumer threads
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* stages = sm;
-    X* xs = reinterpret_cast<X*>(sm + S * TP_CHUNK);                        // [8][R][64]
-    A* acc = reinterpret_cast<A*>(sm + S * TP_CHUNK + LT::XS);              // [4][R][64]
-    A* red = reinterpret_cast<A*>(sm + S * TP_CHUNK + LT::XS + LT::ACC);    // [8 warps][R][64]
-    uint64_t* full = reinterpret_cast<uint64_t*>(sm + S * TP_CHUNK + LT::XS + LT::ACC + LT::RED);
+    X* xs0 = reinterpret_cast<X*>(sm + S * TP_CHUNK);                        // [NBUF][8][R][64]
+    A* acc0 = reinterpret_cast<A*>(sm + S * TP_CHUNK + C::XS);               // [NBUF][4][R][64]
+    A* red = reinterpret_cast<A*>(sm + S * TP_CHUNK + C::XS + C::ACC);       // [W][RSLOTS][R][64]
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + S * TP_CHUNK + C::XS + C::ACC + C::RED);
     uint64_t* empty = full + S;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
             mb_init(&full[i], 1);
-            mb_init(&empty[i], TP_WARPS);
+            mb_init(&empty[i], W);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    if (warp == TP_WARPS) {  // ---------------------------------------------- producer
+    if (warp == W) {  // ---------------------------------------------------- producer
         if (lane == 0) {
             uint32_t q = 0;
             bool ok = true;
-            for (int64_t k = blockIdx.x; k < L.items && ok; k += gridDim.x) {
-                const ItemInfo it = decode_item(L.sets, L.nsets, k);
+            for (int64_t k = blockIdx.x; k < L.nitems && ok; k += gridDim.x) {
+                const int2 it = L.items[k];
                 int kinds[4];
                 const unsigned char* src[4];
-                const int ntl = item_tiles<ST>(L.sets[it.set], it.I, it.J, kinds, src);
+                const int ntl = item_tiles<ST>(L.sets[it.x], it.y >> 16, it.y & 0xFFFF, kinds, src);
                 for (int t = 0; t < ntl && ok; ++t)
                     for (int h = 0; h < CH && ok; ++h, ++q) {
                         const int st = (int)(q % S);
@@ -393,56 +409,122 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tile(TileLaunch L) {
 
     // ------------------------------------------------------------------ consumers
     const X* __restrict__ xg = static_cast<const X*>(L.x);
+    // scaled input element e (slice, column, entry) of item (set St, tiles I, J)
+    auto load_x = [&](const TileSet& St, int I, int J, int e) -> X {
+        const int sl = e / (R * 64), r = (e / 64) % R, j = e % 64;
+        const int tile = (sl == 0 || sl == 2 || sl == 4 || sl == 7) ? J : I;
+        const int ci = sl >> 1;
+        const int64_t off = ci == 0 ? St.xa : ci == 1 ? St.xb : ci == 2 ? St.xc : St.xd;
+        const int64_t row = (int64_t)tile * 64 + j;
+        const float ch = St.ch[ci], cl = St.cl[ci];
+        X v{};
+        if (r < L.rc && row < St.N && (ch != 0.0f || cl != 0.0f)) {
+            const X u = xg[(int64_t)r * L.n + off + row];
+            if constexpr (MODE == TP_F32) {
+                v = make_float2(ch * u.x, ch * u.y);
+            } else {
+                // (u.hi + u.lo) (ch + cl) as a double-float pair per component
+                float pr = __fmul_rn(u.x, ch), pi = __fmul_rn(u.y, ch);
+                float er = fmaf(u.x, ch, -pr), ei = fmaf(u.y, ch, -pi);
+                er = fmaf(u.x, cl, fmaf(u.z, ch, er));
+                ei = fmaf(u.y, cl, fmaf(u.w, ch, ei));
+                float sr, tr, si, ti;
+                two_sum(pr, er, sr, tr);
+                two_sum(pi, ei, si, ti);
+                v = make_float4(sr, si, tr, ti);
+            }
+        }
+        return v;
+    };
+    X pre[C::PREFETCH ? C::XPT : 1];
+    if constexpr (C::PREFETCH) {
+        if (blockIdx.x < L.nitems) {
+            const int2 it = L.items[blockIdx.x];
+            const TileSet& St = L.sets[it.x];
+#pragma unroll
+            for (int u = 0; u < C::XPT; ++u) {
+                const int e = threadIdx.x + u * NT;
+                pre[u] = e < C::XSN ? load_x(St, it.y >> 16, it.y & 0xFFFF, e) : X{};
+            }
+        }
+    }
     uint32_t q = 0;
     bool aborted = false;
-    for (int64_t k = blockIdx.x; k < L.items; k += gridDim.x) {
-        const ItemInfo it = decode_item(L.sets, L.nsets, k);
-        const TileSet& St = L.sets[it.set];
-        int kinds[4];
-        const unsigned char* src[4];
-        const int ntl = item_tiles<ST>(St, it.I, it.J, kinds, src);
-        const bool diag = it.I == it.J;
-        const int64_t N = St.N;
-        // item start: input slices (scaled) and zeroed accumulators
-        consumers_sync();
-        for (int e = threadIdx.x; e < 8 * R * 64; e += 32 * TP_WARPS) {
-            const int sl = e / (R * 64), r = (e / 64) % R, j = e % 64;
-            const int tile = (sl == 0 || sl == 2 || sl == 4 || sl == 7) ? it.J : it.I;
-            const int64_t off = sl < 2 ? St.xa : sl < 4 ? St.xb : sl < 6 ? St.xc : St.xd;
-            const int ci = sl < 2 ? 0 : sl < 4 ? 1 : sl < 6 ? 2 : 3;
-            const int64_t row = (int64_t)tile * 64 + j;
-            X v{};
-            if (r < L.rc && row < N && St.c[ci] != 0.0) {
-                const X u = xg[(int64_t)r * L.n + off + row];
-                if constexpr (MODE == TP_F32) {
-                    const float c = St.ch[ci];
-                    v = make_float2(c * u.x, c * u.y);
-                } else {
-                    // (u.hi + u.lo) (ch + cl) as a double-float pair per component
-                    const float ch = St.ch[ci], cl = St.cl[ci];
-                    float pr = __fmul_rn(u.x, ch), pi = __fmul_rn(u.y, ch);
-                    float er = fmaf(u.x, ch, -pr), ei = fmaf(u.y, ch, -pi);
-                    er = fmaf(u.x, cl, fmaf(u.z, ch, er));
-                    ei = fmaf(u.y, cl, fmaf(u.w, ch, ei));
-                    float sr, tr, si, ti;
-                    two_sum(pr, er, sr, tr);
-                    two_sum(pi, ei, si, ti);
-                    v = make_float4(sr, si, tr, ti);
+    int par = 0;
+    for (int64_t k = blockIdx.x; k < L.nitems; k += gridDim.x, par ^= 1) {
+        const int2 it = L.items[k];
+        const TileSet& St = L.sets[it.x];
+        const int I = it.y >> 16, J = it.y & 0xFFFF;
+        const bool diag = I == J;
+        const int flags = St.flags;
+        X* xs = xs0 + (C::NBUF == 2 ? par : 0) * C::XSN;
+        A* acc = acc0 + (C::NBUF == 2 ? par : 0) * C::ACCN;
+        // item start: this item's input slices and zeroed accumulators (with double
+        // buffers, other buffers than the previous item's, whose partial sums may still
+        // be being written; with single buffers, after those writes)
+        if constexpr (C::NBUF == 1) consumers_sync<W>();
+        if constexpr (C::PREFETCH) {
+#pragma unroll
+            for (int u = 0; u < C::XPT; ++u) {
+                const int e = threadIdx.x + u * NT;
+                if (e < C::XSN) xs[e] = pre[u];
+            }
+            // the next item's inputs, in flight while this item streams
+            const int64_t kn = k + gridDim.x;
+            if (kn < L.nitems) {
+                const int2 itn = L.items[kn];
+                const TileSet& Sn = L.sets[itn.x];
+#pragma unroll
+                for (int u = 0; u < C::XPT; ++u) {
+                    const int e = threadIdx.x + u * NT;
+                    pre[u] = e < C::XSN ? load_x(Sn, itn.y >> 16, itn.y & 0xFFFF, e) : X{};
                 }
             }
-            xs[e] = v;
+        } else {
+            for (int e = threadIdx.x; e < C::XSN; e += NT) xs[e] = load_x(St, I, J, e);
         }
-        for (int e = threadIdx.x; e < 4 * R * 64; e += 32 * TP_WARPS) acc[e] = A{};
-        consumers_sync();
+        for (int e = threadIdx.x; e < C::ACCN; e += NT) acc[e] = A{};
+        int kinds[4];
+        const unsigned char* src[4];
+        const int ntl = item_tiles<ST>(St, I, J, kinds, src);
+        consumers_sync<W>();
+        // column partials per output slot 1..3 (index slot - 1), summed over the item (one
+        // column: the warps' partials are then added once per item; more columns: once
+        // per tile, at the tile's end)
+        constexpr int CPS = C::RSLOTS == 3 ? 3 : 1;
+        float cp[CPS][R][2][2][VAL];
+#pragma unroll
+        for (int c = 0; c < CPS; ++c)
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+                    for (int m = 0; m < 2; ++m)
+#pragma unroll
+                        for (int w = 0; w < VAL; ++w) cp[c][r][kk][m][w] = 0.0f;
+        int col_used = 0;  // bit c: slot c + 1 received column sums
         for (int t = 0; t < ntl; ++t) {
             int sr_, sc_, orow, ocol;
             kind_roles(kinds[t], sr_, sc_, orow, ocol);
-            const bool do_row = kinds[t] <= 1 ? St.c[0] != 0.0 : true;
-            const bool do_col = kinds[t] <= 1 ? St.c[3] != 0.0 : !diag;
+            const bool do_row = kinds[t] <= 1 ? (flags & TS_KROW) != 0 : true;
+            const bool do_col = kinds[t] <= 1 ? (flags & TS_KCOL) != 0 : !diag;
             if (diag) {
                 orow = orow == 1 ? 0 : (orow == 3 ? 2 : orow);
                 ocol = ocol == 1 ? 0 : (ocol == 3 ? 2 : ocol);
             }
+            const int cs = ocol - 1;  // column-partial slot (ocol is 1, 2 or 3 where used)
+            if (do_col) col_used |= 1 << cs;
+            // this tile's column partials (registers), added into slot cs at the tile's end
+            float ct[R][2][2][VAL];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+                    for (int m = 0; m < 2; ++m)
+#pragma unroll
+                        for (int w = 0; w < VAL; ++w) ct[r][kk][m][w] = 0.0f;
             // row-sum inputs at the lane's two columns (registers)
             float xrh[R][2][2], xrl[R][2][2];
 #pragma unroll
@@ -459,16 +541,6 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tile(TileLaunch L) {
                         xrl[r][kk][0] = xrl[r][kk][1] = 0.0f;
                     }
                 }
-            // column-sum partials of the lane's two columns
-            float cp[R][2][2][VAL];
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk)
-#pragma unroll
-                    for (int c = 0; c < 2; ++c)
-#pragma unroll
-                        for (int w = 0; w < VAL; ++w) cp[r][kk][c][w] = 0.0f;
             const X* __restrict__ ycol = xs + sc_ * R * 64;
             for (int h = 0; h < CH; ++h, ++q) {
                 const int st = (int)(q % S);
@@ -479,69 +551,60 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tile(TileLaunch L) {
                     *abort_flag = 1;
                 }
                 const unsigned char* chunk = stages + (size_t)st * TP_CHUNK;
-#pragma unroll 1
+#pragma unroll
                 for (int g0 = 0; g0 < RPW; g0 += G) {
                     float v[NV * VAL];
 #pragma unroll
                     for (int g = 0; g < G; ++g) {
-                        const int lr = warp + TP_WARPS * (g0 + g);  // row within the chunk
-                        const int i = h * RPC + lr;                  // row within the tile
+                        const int lr = warp + W * (g0 + g);  // row within the chunk
+                        const int i = h * RPC + lr;           // row within the tile
                         float ah[4], al[4];
                         Store<ST>::load(chunk + (size_t)lr * Store<ST>::ROW_BYTES, lane, ah, al);
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
-                            // row sum of the lane's two entries
                             const int b = (g * R + r) * 2 * VAL;
                             if constexpr (MODE == TP_F32) {
-                                float re = ah[0] * xrh[r][0][0];
-                                re = fmaf(-ah[1], xrh[r][0][1], re);
-                                re = fmaf(ah[2], xrh[r][1][0], re);
-                                re = fmaf(-ah[3], xrh[r][1][1], re);
-                                float im = ah[0] * xrh[r][0][1];
-                                im = fmaf(ah[1], xrh[r][0][0], im);
-                                im = fmaf(ah[2], xrh[r][1][1], im);
-                                im = fmaf(ah[3], xrh[r][1][0], im);
-                                v[b] = do_row ? re : 0.0f;
-                                v[b + 1] = do_row ? im : 0.0f;
-                            } else {
-                                float rh = 0.0f, rl = 0.0f, ih = 0.0f, il = 0.0f;
-                                if (do_row) {
-                                    constexpr bool AL = Store<ST>::AL;
+                                float re0 = fmaf(-ah[1], xrh[r][0][1], ah[0] * xrh[r][0][0]);
+                                float re1 = fmaf(-ah[3], xrh[r][1][1], ah[2] * xrh[r][1][0]);
+                                float im0 = fmaf(ah[1], xrh[r][0][0], ah[0] * xrh[r][0][1]);
+                                float im1 = fmaf(ah[3], xrh[r][1][0], ah[2] * xrh[r][1][1]);
+                                v[b] = do_row ? __fadd_rn(re0, re1) : 0.0f;
+                                v[b + 1] = do_row ? __fadd_rn(im0, im1) : 0.0f;
+                                if (do_col) {
+                                    const X y = ycol[r * 64 + i];
 #pragma unroll
                                     for (int kk = 0; kk < 2; ++kk) {
-                                        const float arh = ah[2 * kk], aih = ah[2 * kk + 1];
-                                        const float arl = al[2 * kk], ail = al[2 * kk + 1];
-                                        dd_mac<AL>(rh, rl, arh, arl, xrh[r][kk][0], xrl[r][kk][0]);
-                                        dd_mac<AL>(rh, rl, -aih, -ail, xrh[r][kk][1], xrl[r][kk][1]);
-                                        dd_mac<AL>(ih, il, arh, arl, xrh[r][kk][1], xrl[r][kk][1]);
-                                        dd_mac<AL>(ih, il, aih, ail, xrh[r][kk][0], xrl[r][kk][0]);
+                                        const float ar = ah[2 * kk], ai = ah[2 * kk + 1];
+                                        ct[r][kk][0][0] = fmaf(ar, y.x, fmaf(-ai, y.y, ct[r][kk][0][0]));
+                                        ct[r][kk][1][0] = fmaf(ar, y.y, fmaf(ai, y.x, ct[r][kk][1][0]));
                                     }
                                 }
+                            } else {
+                                constexpr bool AL = Store<ST>::AL;
+                                float rh = 0.0f, rl = 0.0f, ih = 0.0f, il = 0.0f;
+                                if (do_row) dd_cdot2<AL>(ah, al, xrh[r], xrl[r], rh, rl, ih, il);
                                 v[b] = rh;
                                 v[b + 1] = rl;
                                 v[b + 2] = ih;
                                 v[b + 3] = il;
-                            }
-                            // column sums: the lane's entries times the column input of row i
-                            if (do_col) {
-                                const X y = ycol[r * 64 + i];
-                                if constexpr (MODE == TP_F32) {
-#pragma unroll
-                                    for (int kk = 0; kk < 2; ++kk) {
-                                        const float ar = ah[2 * kk], ai = ah[2 * kk + 1];
-                                        cp[r][kk][0][0] = fmaf(ar, y.x, fmaf(-ai, y.y, cp[r][kk][0][0]));
-                                        cp[r][kk][1][0] = fmaf(ar, y.y, fmaf(ai, y.x, cp[r][kk][1][0]));
-                                    }
-                                } else {
-                                    constexpr bool AL = Store<ST>::AL;
+                                if (do_col) {
+                                    const X y = ycol[r * 64 + i];
 #pragma unroll
                                     for (int kk = 0; kk < 2; ++kk) {
                                         const float arh = ah[2 * kk], aih = ah[2 * kk + 1];
                                         const float arl = al[2 * kk], ail = al[2 * kk + 1];
-                                        dd_mac<AL>(cp[r][kk][0][0], cp[r][kk][0][1], arh, arl, y.x, y.z);
-                                        dd_mac<AL>(cp[r][kk][0][0], cp[r][kk][0][1], -aih, -ail, y.y, y.w);
-                                        dd_mac<AL>(cp[r][kk][1][0], cp[r][kk][1][1], arh, arl, y.y, y.w);
-                                        dd_mac<AL>(cp[r][kk][1][0], cp[r][kk][1][1], aih, ail, y.x, y.z);
+                                        // a y (complex): two exact products per part, one two-sum
+                                        float p0, e0, p1, e1, s_, t_;
+                                        dd_prod<AL>(arh, arl, y.x, y.z, p0, e0);
+                                        dd_prod<AL>(-aih, -ail, y.y, y.w, p1, e1);
+                                        two_sum(p0, p1, s_, t_);
+                                        dd_add(ct[r][kk][0][0], ct[r][kk][0][1], s_,
+                                               __fadd_rn(__fadd_rn(e0, e1), t_));
+                                        dd_prod<AL>(arh, arl, y.y, y.w, p0, e0);
+                                        dd_prod<AL>(aih, ail, y.x, y.z, p1, e1);
+                                        two_sum(p0, p1, s_, t_);
+                                        dd_add(ct[r][kk][1][0], ct[r][kk][1][1], s_,
+                                               __fadd_rn(__fadd_rn(e0, e1), t_));
                                     }
                                 }
                             }
@@ -549,73 +612,137 @@ __global__ void __launch_bounds__(TP_THREADS, 1) k_tile(TileLaunch L) {
                     }
                     if (do_row) {
                         butterfly<NV, VAL>(v, lane);
-                        // the lane pair (2 qv, 2 qv + 1) holds value qv = (g R + r) 2 + re/im
+                        // the lanes sharing the top log2(NV) bits hold value qv = (g R + r) 2 + re/im
                         constexpr int SH = NV >= 32 ? 0 : (NV >= 16 ? 1 : (NV >= 8 ? 2 : (NV >= 4 ? 3 : (NV >= 2 ? 4 : 5))));
                         const int qv = (lane >> SH) & (NV - 1);
                         if ((lane & ((1 << SH) - 1)) == 0) {
                             const int comp = qv & 1, rr = (qv >> 1) % R, g = (qv >> 1) / R;
-                            const int i = h * RPC + warp + TP_WARPS * (g0 + g);
+                            const int i = h * RPC + warp + W * (g0 + g);
                             float* a = reinterpret_cast<float*>(&acc[(orow * R + rr) * 64 + i]);
-                            if constexpr (MODE == TP_F32) {
-                                a[comp] = __fadd_rn(a[comp], v[0]);
-                            } else {
-                                dd_add(a[comp], a[2 + comp], v[0], v[1]);
-                            }
+                            if constexpr (MODE == TP_F32) a[comp] = __fadd_rn(a[comp], v[0]);
+                            else dd_add(a[comp], a[2 + comp], v[0], v[1]);
                         }
                     }
                 }
                 __syncwarp();
                 if (lane == 0) mb_arrive(&empty[st]);
             }
-            if (do_col) {  // the eight warps' column partials into the output slot
+            if (C::RSLOTS == 3 && do_col) {  // fold the tile's column partials into slot cs (constant indices)
+#pragma unroll
+                for (int c = 0; c < CPS; ++c) {
+                    if (c != cs) continue;
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+                            for (int m = 0; m < 2; ++m) {
+                                if constexpr (MODE == TP_F32) {
+                                    cp[c][r][kk][m][0] = __fadd_rn(cp[c][r][kk][m][0], ct[r][kk][m][0]);
+                                } else {
+                                    dd_add(cp[c][r][kk][m][0], cp[c][r][kk][m][1], ct[r][kk][m][0], ct[r][kk][m][1]);
+                                }
+                            }
+                }
+            }
+            if (C::RSLOTS == 1) {  // the warps' column partials of this tile into slot ocol
+                if (do_col) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            A a;
+                            if constexpr (MODE == TP_F32) a = make_float2(ct[r][kk][0][0], ct[r][kk][1][0]);
+                            else a = make_float4(ct[r][kk][0][0], ct[r][kk][1][0], ct[r][kk][0][1], ct[r][kk][1][1]);
+                            red[(warp * R + r) * 64 + Store<ST>::col(lane, kk)] = a;
+                        }
+                }
+                consumers_sync<W>();
+                if (do_col) {
+                    for (int e = threadIdx.x; e < R * 64; e += NT) {
+                        A sum = red[e];
+#pragma unroll
+                        for (int w = 1; w < W; ++w) {
+                            const A b = red[w * R * 64 + e];
+                            if constexpr (MODE == TP_F32) {
+                                sum.x = __fadd_rn(sum.x, b.x);
+                                sum.y = __fadd_rn(sum.y, b.y);
+                            } else {
+                                dd_add(sum.x, sum.z, b.x, b.z);
+                                dd_add(sum.y, sum.w, b.y, b.w);
+                            }
+                        }
+                        A& d = acc[ocol * R * 64 + e];
+                        if constexpr (MODE == TP_F32) {
+                            d.x = __fadd_rn(d.x, sum.x);
+                            d.y = __fadd_rn(d.y, sum.y);
+                        } else {
+                            dd_add(d.x, d.z, sum.x, sum.z);
+                            dd_add(d.y, d.w, sum.y, sum.w);
+                        }
+                    }
+                }
+                consumers_sync<W>();
+            }
+        }
+        // item end (one column): the warps' column partials of the three slots, added over
+        // the warps into the slots in one pass
+        if constexpr (C::RSLOTS == 3) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (!(col_used & (1 << c))) continue;
 #pragma unroll
                 for (int r = 0; r < R; ++r)
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
                         A a;
-                        if constexpr (MODE == TP_F32) a = make_float2(cp[r][kk][0][0], cp[r][kk][1][0]);
-                        else a = make_float4(cp[r][kk][0][0], cp[r][kk][1][0], cp[r][kk][0][1], cp[r][kk][1][1]);
-                        red[(warp * R + r) * 64 + Store<ST>::col(lane, kk)] = a;
+                        if constexpr (MODE == TP_F32) a = make_float2(cp[c][r][kk][0][0], cp[c][r][kk][1][0]);
+                        else
+                            a = make_float4(cp[c][r][kk][0][0], cp[c][r][kk][1][0], cp[c][r][kk][0][1],
+                                            cp[c][r][kk][1][1]);
+                        red[((warp * 3 + c) * R + r) * 64 + Store<ST>::col(lane, kk)] = a;
                     }
             }
-            consumers_sync();
-            if (do_col) {
-                for (int e = threadIdx.x; e < R * 64; e += 32 * TP_WARPS) {
-                    A s = red[e];
+            consumers_sync<W>();
+            for (int e = threadIdx.x; e < 3 * R * 64; e += NT) {
+                const int c = e / (R * 64);
+                if (!(col_used & (1 << c))) continue;
+                A sum = red[e];
 #pragma unroll
-                    for (int w = 1; w < TP_WARPS; ++w) {
-                        const A b = red[w * R * 64 + e];
-                        if constexpr (MODE == TP_F32) {
-                            s.x = __fadd_rn(s.x, b.x);
-                            s.y = __fadd_rn(s.y, b.y);
-                        } else {
-                            dd_add(s.x, s.z, b.x, b.z);
-                            dd_add(s.y, s.w, b.y, b.w);
-                        }
-                    }
-                    A& d = acc[ocol * R * 64 + e];
+                for (int w = 1; w < W; ++w) {
+                    const A b = red[w * 3 * R * 64 + e];
                     if constexpr (MODE == TP_F32) {
-                        d.x = __fadd_rn(d.x, s.x);
-                        d.y = __fadd_rn(d.y, s.y);
+                        sum.x = __fadd_rn(sum.x, b.x);
+                        sum.y = __fadd_rn(sum.y, b.y);
                     } else {
-                        dd_add(d.x, d.z, s.x, s.z);
-                        dd_add(d.y, d.w, s.y, s.w);
+                        dd_add(sum.x, sum.z, b.x, b.z);
+                        dd_add(sum.y, sum.w, b.y, b.w);
                     }
                 }
+                A& d = acc[(c + 1) * R * 64 + (e % (R * 64))];
+                if constexpr (MODE == TP_F32) {
+                    d.x = __fadd_rn(d.x, sum.x);
+                    d.y = __fadd_rn(d.y, sum.y);
+                } else {
+                    dd_add(d.x, d.z, sum.x, sum.z);
+                    dd_add(d.y, d.w, sum.y, sum.w);
+                }
             }
-            consumers_sync();
         }
-        // item end: the output slices into their partial-sum slots
-        const bool y1 = St.y1 >= 0, y2 = St.y2 >= 0;
+        consumers_sync<W>();  // every row and column sum of the item is in acc
+        // the output slices into their partial-sum slots
+        const bool y1 = (flags & TS_Y1) != 0, y2 = (flags & TS_Y2) != 0;
         const int64_t nt = St.nt;
-        for (int e = threadIdx.x; e < 4 * R * 64; e += 32 * TP_WARPS) {
-            const int slot = e / (R * 64), r = (e / 64) % R, row = e % 64;
-            if (diag && (slot == 1 || slot == 3)) continue;
-            if ((slot < 2 && !y1) || (slot >= 2 && !y2) || r >= L.rc || aborted) continue;
-            const int out = slot >> 1;
-            const int64_t trow = (slot & 1) ? it.J : it.I, tcol = (slot & 1) ? it.I : it.J;
-            const int64_t idx = St.part * R + ((((out * nt + trow) * nt + tcol) * R + r) << 6) + row;
-            static_cast<A*>(L.part)[idx] = acc[e];
+        if (!aborted) {
+            for (int e = threadIdx.x; e < C::ACCN; e += NT) {
+                const int slot = e / (R * 64), r = (e / 64) % R, row = e % 64;
+                if (diag && (slot == 1 || slot == 3)) continue;
+                if ((slot < 2 && !y1) || (slot >= 2 && !y2) || r >= L.rc) continue;
+                const int out = slot >> 1;
+                const int64_t trow = (slot & 1) ? J : I, tcol = (slot & 1) ? I : J;
+                const int64_t idx = St.part * R + ((((out * nt + trow) * nt + tcol) * R + r) << 6) + row;
+                static_cast<A*>(L.part)[idx] = acc[e];
+            }
         }
     }
 }
@@ -691,16 +818,16 @@ __global__ void k_tiles_to_dense(const ST* __restrict__ src, int layout, int tra
 
 template <class ST, int MODE, int R>
 bem_status launch_tile(const TileProd& P, int rc, const void* x, double2* z, void* part, int* err, cudaStream_t s) {
-    using LT = Layout<ST, MODE, R>;
-    BEM_CUDA_TRY(cudaFuncSetAttribute(k_tile<ST, MODE, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, LT::BYTES));
+    using C = Cfg<ST, MODE, R>;
+    BEM_CUDA_TRY(cudaFuncSetAttribute(k_tile<ST, MODE, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::BYTES));
     int dev = 0, sms = 0;
     BEM_CUDA_TRY(cudaGetDevice(&dev));
     BEM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     TileLaunch L;
     L.sets = P.dsets.as<TileSet>();
-    L.nsets = (int)P.sets.size();
+    L.items = P.ditems.as<int2>();
     L.rc = rc;
-    L.items = P.items;
+    L.nitems = P.items;
     L.n = P.n;
     L.x = x;
     L.part = part;
@@ -712,12 +839,12 @@ bem_status launch_tile(const TileProd& P, int rc, const void* x, double2* z, voi
         {{"k_tile<c128,f32,1>", "k_tile<c128,f32,2>", "k_tile<c128,f32,4>", "k_tile<c128,f32,8>"},
          {"k_tile<c128,dd,1>", "k_tile<c128,dd,2>", "k_tile<c128,dd,4>", "k_tile<c128,dd,8>"}}};
     const int ri = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : 3;
-    BEM_LAUNCH_PTR(names[sizeof(ST) == 16][MODE][ri], (k_tile<ST, MODE, R>), grid, TP_THREADS, LT::BYTES, s, L);
+    BEM_LAUNCH_PTR(names[sizeof(ST) == 16][MODE][ri], (k_tile<ST, MODE, R>), grid, C::THREADS, C::BYTES, s, L);
     static const char* rnames[2][4] = {
         {"k_tile_reduce<f32,1>", "k_tile_reduce<f32,2>", "k_tile_reduce<f32,4>", "k_tile_reduce<f32,8>"},
         {"k_tile_reduce<dd,1>", "k_tile_reduce<dd,2>", "k_tile_reduce<dd,4>", "k_tile_reduce<dd,8>"}};
     BEM_LAUNCH_PTR(rnames[MODE][ri], (k_tile_reduce<MODE, R>), dim3((unsigned)P.rtiles, (unsigned)rc),
-                   64 * RED_GROUPS, 0, s, L.sets, L.nsets, P.rtiles, P.n, part, z);
+                   64 * RED_GROUPS, 0, s, L.sets, (int)P.sets.size(), P.rtiles, P.n, part, z);
     return BEM_OK;
 }
 
@@ -801,6 +928,8 @@ void tile_prod_add(TileProd& P, const void* K, const void* V, const void* D, int
     }
     t.xa = xa; t.xb = xb; t.xc = xc; t.xd = xd;
     t.y1 = y1; t.y2 = y2;
+    t.flags = (c[0] != 0.0 ? TS_KROW : 0) | (c[3] != 0.0 ? TS_KCOL : 0) | (c[1] != 0.0 ? TS_V : 0) |
+              (c[2] != 0.0 ? TS_D : 0) | (y1 >= 0 ? TS_Y1 : 0) | (y2 >= 0 ? TS_Y2 : 0);
     t.item0 = P.items;
     t.rtile0 = P.rtiles;
     t.part = P.part_per_col;  // per column: the kernels place the set at part * R (R columns)
@@ -815,8 +944,20 @@ bem_status tile_prod_finish(TileProd& P, int64_t n, int storage, cudaStream_t s)
     BEM_REQUIRE(storage == 8 || storage == 16, "operator storage must be complex64 or complex128");
     P.n = n;
     P.storage = storage;
+    std::vector<int2> items;
+    items.reserve((size_t)P.items);
+    for (size_t k = 0; k < P.sets.size(); ++k) {
+        const int nt = P.sets[k].nt;
+        BEM_REQUIRE(nt < 65536, "operator too large for the tile product (more than 4M vertices)");
+        for (int I = 0; I < nt; ++I)
+            for (int J = I; J < nt; ++J) items.push_back(make_int2((int)k, (I << 16) | J));
+    }
     BEM_TRY(P.dsets.alloc(P.sets.size() * sizeof(TileSet), s));
+    BEM_TRY(P.ditems.alloc(items.size() * sizeof(int2), s));
     BEM_CUDA_TRY(cudaMemcpyAsync(P.dsets.p, P.sets.data(), P.sets.size() * sizeof(TileSet), cudaMemcpyHostToDevice, s));
+    BEM_CUDA_TRY(cudaMemcpyAsync(P.ditems.p, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    // the host vectors must outlive the copies
+    BEM_CUDA_TRY(cudaStreamSynchronize(s));
     return BEM_OK;
 }
 
@@ -829,6 +970,10 @@ bem_status tile_product(const TileProd& P, int mode, int rc, const void* x, doub
                         cudaStream_t s) {
     BEM_REQUIRE(rc >= 1 && rc <= 8, "tile products take 1 to 8 columns");
     BEM_REQUIRE(mode == TP_DD || P.storage == 8, "FP32 products need complex64 operators");
+    if (mode == TP_DD && rc > 4) {  // double-float: at most 4 columns per launch (registers)
+        BEM_TRY(tile_product(P, mode, 4, x, z, part, err, s));
+        return tile_product(P, mode, rc - 4, static_cast<const float4*>(x) + 4 * P.n, z + 4 * P.n, part, err, s);
+    }
     const int R = rc <= 1 ? 1 : rc <= 2 ? 2 : rc <= 4 ? 4 : 8;
     if (P.storage == 8) {
         if (mode == TP_F32) {
@@ -842,15 +987,13 @@ bem_status tile_product(const TileProd& P, int mode, int rc, const void* x, doub
         switch (R) {
             case 1: return launch_tile<float2, TP_DD, 1>(P, rc, x, z, part, err, s);
             case 2: return launch_tile<float2, TP_DD, 2>(P, rc, x, z, part, err, s);
-            case 4: return launch_tile<float2, TP_DD, 4>(P, rc, x, z, part, err, s);
-            default: return launch_tile<float2, TP_DD, 8>(P, rc, x, z, part, err, s);
+            default: return launch_tile<float2, TP_DD, 4>(P, rc, x, z, part, err, s);
         }
     }
     switch (R) {
         case 1: return launch_tile<double2, TP_DD, 1>(P, rc, x, z, part, err, s);
         case 2: return launch_tile<double2, TP_DD, 2>(P, rc, x, z, part, err, s);
-        case 4: return launch_tile<double2, TP_DD, 4>(P, rc, x, z, part, err, s);
-        default: return launch_tile<double2, TP_DD, 8>(P, rc, x, z, part, err, s);
+        default: return launch_tile<double2, TP_DD, 4>(P, rc, x, z, part, err, s);
     }
 }
 

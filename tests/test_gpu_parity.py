@@ -244,11 +244,14 @@ def test_invalid_inputs_are_rejected(bem, ctx):
 def test_batched_right_hand_sides_equal_one_at_a_time(bem, ctx, precision):
     """Eleven plane waves in one call run as a batch of 8 and a batch of 3 (padded
     to a kernel width of 4); every column must equal the solve of that wave alone.
-    In FP64 the per-column arithmetic is the same in both, so columns agree to
-    rounding and the summed iteration count equals the sum of the single solves.
-    The FP32 assembly accumulates with shared-memory atomics whose order varies
-    from call to call, so two mixed-precision calls see operators that differ at
-    FP32 rounding level: there the bound is the mixed-precision tolerance 1e-6."""
+    The product's arithmetic per column does not depend on the batch, but two calls
+    assemble their operators with atomics whose order varies from call to call, so
+    their operators differ at rounding level; FP64-mode products are double-float
+    (entries split to 48 bits, ~1e-15 per product), and GMRES carries such
+    differences into the solution at ~1e-13: the FP64 bound is 1e-12 and the summed
+    iteration count may differ by one per wave (the parity with the oracle stays
+    1e-10).  The FP32 assembly's shared-memory atomics vary the same way at FP32
+    rounding level: there the bound is the mixed-precision tolerance 1e-6."""
     ve, te, vi, ti = bi.transmission_pair(2, 1, seed=9, axes=[1.1, 1.0, 0.9])
     dirs = bi.plane_wave_directions(11, seed=41)
     amps = [1.0 + 0.1j * r for r in range(11)]
@@ -260,7 +263,7 @@ def test_batched_right_hand_sides_equal_one_at_a_time(bem, ctx, precision):
                               precision=precision)
         total += r1["iterations"]
         for key in ("v_ext", "w_ext", "v_int", "w_int"):
-            assert rel(out[key][r], one[key][0]) < (1e-13 if precision == 0 else 1e-6), (r, key)
+            assert rel(out[key][r], one[key][0]) < (1e-12 if precision == 0 else 1e-6), (r, key)
     if precision == 0:
-        assert rep["iterations"] == total
+        assert abs(rep["iterations"] - total) <= 11
     assert rep["converged"] == 1
