@@ -793,8 +793,10 @@ def run_case(args):
             print("iterations", rep["iterations"])
         else:
             dirs = np.array([[0.0, 0.0, 1.0]]) if args.rhs == 1 else bi.plane_wave_directions(args.rhs, seed=40)
-            _, rep = bem.bem_solve_transmission(ctx, ge, gi, 1.5 * args.k, args.k, 2.0, dirs,
-                                                opts={"precision": prec, "formulation": args.formulation})
+            opts = {"precision": prec, "formulation": args.formulation}
+            if args.dd_switch is not None:
+                opts["dd_switch"] = args.dd_switch
+            _, rep = bem.bem_solve_transmission(ctx, ge, gi, 1.5 * args.k, args.k, 2.0, dirs, opts=opts)
             print("iterations", rep["iterations"])
     bem.bem_grid_destroy(ge)
     bem.bem_grid_destroy(gi)
@@ -835,6 +837,9 @@ def main():
     ap.add_argument("--mixed", action="store_true", help="--case: mixed precision instead of FP64")
     ap.add_argument("--rhs", type=int, default=1, help="--case solve: plane waves (batched)")
     ap.add_argument("--formulation", type=int, default=0, help="--case solve: BEM_FORM_* formulation")
+    ap.add_argument("--dd-switch", dest="dd_switch", type=float, default=None,
+                    help="--case solve: bem_solve_opts.dd_switch (0: double-float inner products throughout, "
+                         "1: FP32 throughout)")
     ap.add_argument("--screen-cells", dest="screen_cells", type=int, default=60,
                     help="--case screen: cells per side of the fine grid")
     args = ap.parse_args()
