@@ -60,33 +60,32 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
 // pi/2 with a three-part constant (the first part has 8 significant bits, so n * P1 is
 // exact), then the Taylor series of sin and cos on |r| <= pi/4 (truncation below
 // 2e-9), evaluated by Horner's rule in r^2; the quadrant selects signs and swaps.
-__device__ __forceinline__ void sincos_moderate(float x, float* s, float* c) {
+// Returned as a (cos, sin) pair; the two Horner recurrences run together as packed
+// FP32x2 FMAs.
+__device__ __forceinline__ float2 sincos_moderate2(float x) {
     const float n = rintf(x * 0.636619772367581343f);  // 2 / pi
     float r = fmaf(-n, 1.5703125f, x);                  // pi/2 = P1 + P2 + P3
     r = fmaf(-n, 4.838267923332751e-4f, r);
     r = fmaf(-n, 2.5632829192545614e-12f, r);
     const float r2 = r * r;
-    // sin r = r (1 - r^2/3! + r^4/5! - r^6/7! + r^8/9!)
-    float ps = fmaf(r2, 2.75573192239858907e-6f, -1.98412698412698413e-4f);
-    ps = fmaf(r2, ps, 8.33333333333333333e-3f);
-    ps = fmaf(r2, ps, -1.66666666666666667e-1f);
-    const float sr = fmaf(r * r2, ps, r);
-    // cos r = 1 - r^2/2! + r^4/4! - r^6/6! + r^8/8! - r^10/10!
-    float pc = fmaf(r2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);
-    pc = fmaf(r2, pc, -1.38888888888888889e-3f);
-    pc = fmaf(r2, pc, 4.16666666666666667e-2f);
-    pc = fmaf(r2, pc, -0.5f);
+    const float2 R2 = make_float2(r2, r2);
+    // (sin, cos) series in r^2: (1/9!, -1/10!) ... as in sincos_moderate
+    float2 P = __ffma2_rn(R2, make_float2(2.75573192239858907e-6f, -2.75573192239858907e-7f),
+                          make_float2(-1.98412698412698413e-4f, 2.48015873015873016e-5f));
+    P = __ffma2_rn(R2, P, make_float2(8.33333333333333333e-3f, -1.38888888888888889e-3f));
+    P = __ffma2_rn(R2, P, make_float2(-1.66666666666666667e-1f, 4.16666666666666667e-2f));
+    const float sr = fmaf(r * r2, P.x, r);
+    const float pc = fmaf(r2, P.y, -0.5f);
     const float cr = fmaf(r2, pc, 1.0f);
     const int q = ((int)n) & 3;
     const float ss = (q & 1) ? cr : sr, cc = (q & 1) ? sr : cr;
-    *s = (q & 2) ? -ss : ss;
-    *c = ((q + 1) & 2) ? -cc : cc;
+    return make_float2(((q + 1) & 2) ? -cc : cc, (q & 2) ? -ss : ss);
 }
 
 struct TrialTile32 {
     float ch[3][TILE_TRI], cl[3][TILE_TRI];
     float u[6][3][TILE_TRI];
-    float wl[6][3][TILE_TRI];
+    float2 wl2[6][3][TILE_TRI];  // w_q J lambda_b(q), duplicated (an FP32x2 operand)
     float n[3][TILE_TRI];
     float curl[3][3][TILE_TRI];
     int32_t v[3][TILE_TRI];
@@ -197,7 +196,7 @@ __device__ __forceinline__ void regular32_tile(const Grid32& G, const int it, co
             if (f < 3) trial->ch[f][s] = val;
             else if (f < 6) trial->cl[f - 3][s] = val;
             else if (f < 24) trial->u[(f - 6) / 3][(f - 6) % 3][s] = val;
-            else if (f < 42) trial->wl[(f - 24) / 3][(f - 24) % 3][s] = val;
+            else if (f < 42) trial->wl2[(f - 24) / 3][(f - 24) % 3][s] = make_float2(val, val);
             else if (f < 45) trial->n[f - 42][s] = val;
             else trial->curl[(f - 45) / 3][(f - 45) % 3][s] = val;
         }
@@ -227,7 +226,7 @@ __device__ __forceinline__ void regular32_tile(const Grid32& G, const int it, co
             }
             for (int a = 0; a < 3; ++a) {
                 float w = 0.f, c2 = 0.f;
-                for (int p = 0; p < 6; ++p) w += fabsf(tside ? test[t].wl[p][a] : trial->wl[p][a][t]);
+                for (int p = 0; p < 6; ++p) w += fabsf(tside ? test[t].wl[p][a] : trial->wl2[p][a][t].x);
                 for (int d = 0; d < 3; ++d) {
                     const float c = tside ? test[t].curl[a][d] : trial->curl[a][d][t];
                     c2 = fmaf(c, c, c2);
@@ -340,15 +339,25 @@ __device__ __forceinline__ void regular32_tile(const Grid32& G, const int it, co
         // exp(i k R), times exp(-k_i R) for a complex wavenumber
         const float amp0 = CK ? expf(-P.k_i * Rh) : 1.0f;
         {
+            // complex values as (re, im) pairs, products with real scalars as packed
+            // FP32x2 FMAs: E0 = exp(i k R) as (E0r, E0r) and (-E0i, E0i) for E0 (c, s)
             const float E0r = amp0 * cs0, E0i = amp0 * sn0;
+            const float2 E0rr = make_float2(E0r, E0r), E0im = make_float2(-E0i, E0i);
             const float R2f = R2h + R2l;
             const float Dns = Dh[0] * trial->n[0][sl] + Dh[1] * trial->n[1][sl] + Dh[2] * trial->n[2][sl];
             const float Dnt = Dh[0] * tr.n[0] + Dh[1] * tr.n[1] + Dh[2] * tr.n[2];
-            float Vr[3][3] = {}, Vi[3][3] = {}, Kr[3][3] = {}, Ki[3][3] = {}, Tr[3][3] = {}, Ti[3][3] = {};
+            const float nsx = trial->n[0][sl], nsy = trial->n[1][sl], nsz = trial->n[2][sl];
+            float2 V[3][3], K[3][3], T[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) V[a][b] = K[a][b] = T[a][b] = make_float2(0.f, 0.f);
 #pragma unroll 1
             for (int p = 0; p < 6; ++p) {
                 const float ux = tr.u[p][0], uy = tr.u[p][1], uz = tr.u[p][2];
-                float SVr[3] = {}, SVi[3] = {}, SKr[3] = {}, SKi[3] = {}, STr[3] = {}, STi[3] = {};
+                float2 SV[3], SK[3], ST[3];
+#pragma unroll
+                for (int b = 0; b < 3; ++b) SV[b] = SK[b] = ST[b] = make_float2(0.f, 0.f);
 #pragma unroll 2
                 for (int q = 0; q < 6; ++q) {
                     const float wx = ux - trial->u[q][0][sl], wy = uy - trial->u[q][1][sl],
@@ -360,44 +369,37 @@ __device__ __forceinline__ void regular32_tile(const Grid32& G, const int it, co
                     const float rinv = rsqrtf(r2);
                     const float r = r2 * rinv;
                     const float delta = __fdividef(num, r + Rh);
-                    float sd, cd;
-                    sincos_moderate(P.k_h * delta, &sd, &cd);
+                    const float2 cs = sincos_moderate2(P.k_h * delta);  // (cos, sin) of k delta
                     float g = rinv * INV_4PI_F;
                     if (CK) g *= __expf(-P.k_i * delta);
                     // G = g exp(i k R) exp(i k delta)
-                    const float Er = E0r * cd - E0i * sd, Ei = E0r * sd + E0i * cd;
-                    const float Gr = g * Er, Gi = g * Ei;
+                    const float2 E = __ffma2_rn(E0rr, cs, __fmul2_rn(E0im, make_float2(cs.y, cs.x)));
+                    const float2 G = __fmul2_rn(make_float2(g, g), E);
                     // F = G (1 - i k r) / r^2, k = k_h + i k_i: (1 + k_i r) - i k_h r
                     const float ar = CK ? 1.0f + P.k_i * r : 1.0f;
                     const float ai = -P.k_h * r;
                     const float ri2 = rinv * rinv;
-                    const float Fr = (Gr * ar - Gi * ai) * ri2, Fi = (Gr * ai + Gi * ar) * ri2;
+                    const float Fr = (G.x * ar - G.y * ai) * ri2, Fi = (G.x * ai + G.y * ar) * ri2;
                     // (x - y).n = (D + w).n
-                    const float dns = Dns + wx * trial->n[0][sl] + wy * trial->n[1][sl] + wz * trial->n[2][sl];
+                    const float dns = Dns + wx * nsx + wy * nsy + wz * nsz;
                     const float dnt = -(Dnt + wx * tr.n[0] + wy * tr.n[1] + wz * tr.n[2]);
+                    const float2 KF = make_float2(dns * Fr, dns * Fi), TF = make_float2(dnt * Fr, dnt * Fi);
 #pragma unroll
                     for (int b = 0; b < 3; ++b) {
-                        const float wl = trial->wl[q][b][sl];
-                        SVr[b] = fmaf(wl, Gr, SVr[b]);
-                        SVi[b] = fmaf(wl, Gi, SVi[b]);
-                        const float cs = wl * dns, ct = wl * dnt;
-                        SKr[b] = fmaf(cs, Fr, SKr[b]);
-                        SKi[b] = fmaf(cs, Fi, SKi[b]);
-                        STr[b] = fmaf(ct, Fr, STr[b]);
-                        STi[b] = fmaf(ct, Fi, STi[b]);
+                        const float2 wl = trial->wl2[q][b][sl];
+                        SV[b] = __ffma2_rn(wl, G, SV[b]);
+                        SK[b] = __ffma2_rn(wl, KF, SK[b]);
+                        ST[b] = __ffma2_rn(wl, TF, ST[b]);
                     }
                 }
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const float wl = tr.wl[p][a];
+                    const float2 wl = make_float2(tr.wl[p][a], tr.wl[p][a]);
 #pragma unroll
                     for (int b = 0; b < 3; ++b) {
-                        Vr[a][b] = fmaf(wl, SVr[b], Vr[a][b]);
-                        Vi[a][b] = fmaf(wl, SVi[b], Vi[a][b]);
-                        Kr[a][b] = fmaf(wl, SKr[b], Kr[a][b]);
-                        Ki[a][b] = fmaf(wl, SKi[b], Ki[a][b]);
-                        Tr[a][b] = fmaf(wl, STr[b], Tr[a][b]);
-                        Ti[a][b] = fmaf(wl, STi[b], Ti[a][b]);
+                        V[a][b] = __ffma2_rn(wl, SV[b], V[a][b]);
+                        K[a][b] = __ffma2_rn(wl, SK[b], K[a][b]);
+                        T[a][b] = __ffma2_rn(wl, ST[b], T[a][b]);
                     }
                 }
             }
@@ -406,8 +408,8 @@ __device__ __forceinline__ void regular32_tile(const Grid32& G, const int it, co
             for (int a = 0; a < 3; ++a)
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
-                    I0r += Vr[a][b];
-                    I0i += Vi[a][b];
+                    I0r += V[a][b].x;
+                    I0i += V[a][b].y;
                 }
             const float nn2 = tr.n[0] * trial->n[0][sl] + tr.n[1] * trial->n[1][sl] + tr.n[2] * trial->n[2][sl];
             const uint32_t ts = testslot[tl], ss = trial->slot[sl];
@@ -420,19 +422,19 @@ __device__ __forceinline__ void regular32_tile(const Grid32& G, const int it, co
                     const int idx = li * TILE_NV + lj;
                     const float cc = tr.curl[a][0] * trial->curl[b][0][sl] + tr.curl[a][1] * trial->curl[b][1][sl] +
                                      tr.curl[a][2] * trial->curl[b][2][sl];
-                    const float dr = cc * I0r - nn2 * (P.k2r * Vr[a][b] - P.k2i * Vi[a][b]);
-                    const float di = cc * I0i - nn2 * (P.k2r * Vi[a][b] + P.k2i * Vr[a][b]);
+                    const float dr = cc * I0r - nn2 * (P.k2r * V[a][b].x - P.k2i * V[a][b].y);
+                    const float di = cc * I0i - nn2 * (P.k2r * V[a][b].y + P.k2i * V[a][b].x);
                     // slab of value o: high words at acc + 2 o SLAB, low words SLAB further
                     auto put = [&](int o, float v) {
                         int32_t* H = acc + (2 * o) * SLAB;
                         fx_add(H, H + SLAB, idx, v, scale, &s_overflow);
                     };
-                    put(0, Vr[a][b]);
-                    put(1, Vi[a][b]);
-                    put(2, Kr[a][b]);
-                    put(3, Ki[a][b]);
-                    put(4, Tr[a][b]);
-                    put(5, Ti[a][b]);
+                    put(0, V[a][b].x);
+                    put(1, V[a][b].y);
+                    put(2, K[a][b].x);
+                    put(3, K[a][b].y);
+                    put(4, T[a][b].x);
+                    put(5, T[a][b].y);
                     put(6, dr);
                     put(7, di);
                 }
@@ -503,10 +505,10 @@ __global__ void k_sincos_check(int n, float xmax, float* __restrict__ err) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float x = -xmax + 2.0f * xmax * ((float)i + 0.5f) / (float)n;
-    float s0, c0, s1, c1;
+    float s0, c0;
     sincosf(x, &s0, &c0);
-    sincos_moderate(x, &s1, &c1);
-    err[i] = fmaxf(fabsf(s1 - s0), fabsf(c1 - c0));
+    const float2 cs = sincos_moderate2(x);
+    err[i] = fmaxf(fabsf(cs.y - s0), fabsf(cs.x - c0));
 }
 
 }  // namespace
