@@ -195,37 +195,34 @@ struct Arith<TP_DD> {
     static constexpr int VAL = 2;
 };
 
-// Launch shape per (storage, arithmetic, columns): consumer warps (16 for one column,
-// so that four warps per scheduler hide the latencies of the dependent arithmetic; 8
-// for more columns, whose registers would not fit 16), rows per warp per chunk, rows per
-// butterfly group (at most 16 (row, column, re/im) values per lane), shared memory.
+// Launch shape per (storage, arithmetic, columns).  Consumer warps W: 16 for one
+// column, 8 for more (registers).  Half of them are row warps: one lane per tile row,
+// the 64 columns split into W/4 blocks; the other half column warps: one lane per tile
+// column, the 64 rows split into W/4 blocks.  Neither needs a cross-lane reduction; the
+// W/4 block partials of each output are added once per item.
 template <class ST, int MODE, int R>
 struct Cfg {
     using X = typename Arith<MODE>::X;
     using A = typename Arith<MODE>::A;
     static constexpr int W = R == 1 ? 16 : 8;
     static constexpr int THREADS = 32 * (W + 1);
-    static constexpr int RPC = Store<ST>::RPC;
-    static constexpr int RPW = RPC / W;
-    static constexpr int G = (8 / R) < RPW ? ((8 / R) < 1 ? 1 : 8 / R) : RPW;
-    static constexpr int NV = G * R * 2;
+    static constexpr int NB = W / 4;      // blocks per half (column blocks of row warps, row blocks of column warps)
+    static constexpr int BW = 64 / NB;    // block width (columns) or height (rows)
+    static constexpr int CH = Store<ST>::CHUNKS;
     static constexpr int XSN = 8 * R * 64;  // elements of one set of input slices
-    static constexpr int ACCN = 4 * R * 64;
     // input-slice elements per consumer thread; the next item's are prefetched into
-    // registers while the current item streams when there are at most two, and then the
-    // slices and accumulators are double-buffered by item and the column partials of the
-    // three slots are added over the warps in one pass (single-column products)
+    // registers while the current item streams when there are at most two (then the
+    // slices are double-buffered by item)
     static constexpr int XPT = (XSN + 32 * W - 1) / (32 * W);
     static constexpr bool PREFETCH = XPT <= 2;
     static constexpr int NBUF = PREFETCH ? 2 : 1;
-    static constexpr int RSLOTS = PREFETCH ? 3 : 1;
     static constexpr int XS = NBUF * XSN * (int)sizeof(X);
-    static constexpr int ACC = NBUF * ACCN * (int)sizeof(A);
-    static constexpr int RED = W * RSLOTS * R * 64 * (int)sizeof(A);
-    static constexpr int FIXED = XS + ACC + RED + 1024;
+    static constexpr int RED = W * 3 * R * 32 * (int)sizeof(A);  // per-warp partials of three slots
+    static constexpr int FIXED = XS + RED + 1024;
     static constexpr int S0 = (TP_SMEM_LIMIT - FIXED) / TP_CHUNK;
     static constexpr int S = S0 > 6 ? 6 : S0;  // ring stages
     static constexpr int BYTES = S * TP_CHUNK + FIXED;
+    static constexpr int EMPTY = W / CH;  // warps reading each chunk
     static_assert(S >= 2, "shared-memory budget");
 };
 
@@ -241,73 +238,20 @@ struct TileLaunch {
 };
 
 // The item's tiles in their fixed order: 0 = K_IJ, 1 = K_JI (I < J), 2 = V_IJ, 3 = D_IJ.
-// Returns the count; kinds[] the tile kinds, src[] their first bytes.
+// Returns the count; src[] their first bytes.
 template <class ST>
-__device__ __forceinline__ int item_tiles(const TileSet& S, int I, int J, int kinds[4],
-                                          const unsigned char* src[4]) {
+__device__ __forceinline__ int item_tiles(const TileSet& S, int I, int J, const unsigned char* src[4]) {
     const int f = S.flags;
     const int64_t nt = S.nt;
     const size_t tb = (size_t)OPT * OPT * sizeof(ST);
     int m = 0;
     if (f & (TS_KROW | TS_KCOL)) {
-        kinds[m] = 0;
         src[m++] = static_cast<const unsigned char*>(S.K) + (size_t)(I * nt + J) * tb;
-        if (I != J) {
-            kinds[m] = 1;
-            src[m++] = static_cast<const unsigned char*>(S.K) + (size_t)(J * nt + I) * tb;
-        }
+        if (I != J) src[m++] = static_cast<const unsigned char*>(S.K) + (size_t)(J * nt + I) * tb;
     }
-    if (f & TS_V) {
-        kinds[m] = 2;
-        src[m++] = static_cast<const unsigned char*>(S.V) + (size_t)op_sym_tile(I, J, nt) * tb;
-    }
-    if (f & TS_D) {
-        kinds[m] = 3;
-        src[m++] = static_cast<const unsigned char*>(S.D) + (size_t)op_sym_tile(I, J, nt) * tb;
-    }
+    if (f & TS_V) src[m++] = static_cast<const unsigned char*>(S.V) + (size_t)op_sym_tile(I, J, nt) * tb;
+    if (f & TS_D) src[m++] = static_cast<const unsigned char*>(S.D) + (size_t)op_sym_tile(I, J, nt) * tb;
     return m;
-}
-
-// Input slices of an item: 0 xa_J, 1 xa_I, 2 xb_J, 3 xb_I, 4 xc_J, 5 xc_I, 6 xd_I, 7 xd_J,
-// each pre-scaled by its coefficient.  Per tile kind: (row-sum slice, column-sum slice,
-// row output slot, column output slot) with slots 0 y1_I, 1 y1_J, 2 y2_I, 3 y2_J.
-__device__ __forceinline__ void kind_roles(int kind, int& xr, int& xcs, int& orow, int& ocol) {
-    switch (kind) {
-        case 0: xr = 0; xcs = 6; orow = 0; ocol = 3; break;   // K_IJ: cK K x_a(J) -> y1_I; cT K^T x_d(I) -> y2_J
-        case 1: xr = 1; xcs = 7; orow = 1; ocol = 2; break;   // K_JI: -> y1_J; -> y2_I
-        case 2: xr = 2; xcs = 3; orow = 0; ocol = 1; break;   // V_IJ: cV V x_b(J) -> y1_I; cV V^T x_b(I) -> y1_J
-        default: xr = 4; xcs = 5; orow = 2; ocol = 3; break;  // D_IJ: -> y2_I; -> y2_J
-    }
-}
-
-template <int NV, int VAL>
-__device__ __forceinline__ void butterfly(float (&v)[NV * VAL], int lane) {
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const int off = 16 >> k;
-        const int nv = (NV >> k) > 1 ? (NV >> k) : 1;
-        if (nv > 1) {
-            const bool up = (lane & off) != 0;
-#pragma unroll
-            for (int j = 0; j < nv / 2; ++j) {
-#pragma unroll
-                for (int q = 0; q < VAL; ++q) {
-                    const float send = up ? v[j * VAL + q] : v[(j + nv / 2) * VAL + q];
-                    const float keep = up ? v[(j + nv / 2) * VAL + q] : v[j * VAL + q];
-                    v[j * VAL + q] = keep;
-                    v[(j + nv / 2) * VAL + q] = __shfl_xor_sync(0xffffffffu, send, off);
-                }
-                if (VAL == 1) v[j] = __fadd_rn(v[j], v[j + nv / 2]);
-                else dd_add(v[2 * j], v[2 * j + 1], v[2 * (j + nv / 2)], v[2 * (j + nv / 2) + 1]);
-            }
-        } else {
-            float h[VAL];
-#pragma unroll
-            for (int q = 0; q < VAL; ++q) h[q] = __shfl_xor_sync(0xffffffffu, v[q], off);
-            if (VAL == 1) v[0] = __fadd_rn(v[0], h[0]);
-            else dd_add(v[0], v[1], h[0], h[1]);
-        }
-    }
 }
 
 // exact product a x of an entry a = ah + al and an input x = xh + xl: p + e (p = fl(ah xh),
@@ -320,29 +264,90 @@ __device__ __forceinline__ void dd_prod(float ah, float al, float xh, float xl, 
     if (AL) e = fmaf(al, xh, e);
 }
 
-// a0 x0 + a1 x1 (complex) as unnormalised double-float pairs, summed as a tree: four
-// independent exact products per part, two levels of two-sums
-template <bool AL>
-__device__ __forceinline__ void dd_cdot2(const float ah[4], const float al[4], const float xh[2][2],
-                                         const float xl[2][2], float& rh, float& rl, float& ih, float& il) {
-    float p[4], e[4];
-    dd_prod<AL>(ah[0], al[0], xh[0][0], xl[0][0], p[0], e[0]);
-    dd_prod<AL>(-ah[1], -al[1], xh[0][1], xl[0][1], p[1], e[1]);
-    dd_prod<AL>(ah[2], al[2], xh[1][0], xl[1][0], p[2], e[2]);
-    dd_prod<AL>(-ah[3], -al[3], xh[1][1], xl[1][1], p[3], e[3]);
-    float s01, t01, s23, t23, t;
-    two_sum(p[0], p[1], s01, t01);
-    two_sum(p[2], p[3], s23, t23);
-    two_sum(s01, s23, rh, t);
-    rl = __fadd_rn(__fadd_rn(__fadd_rn(e[0], e[1]), __fadd_rn(e[2], e[3])), __fadd_rn(__fadd_rn(t01, t23), t));
-    dd_prod<AL>(ah[0], al[0], xh[0][1], xl[0][1], p[0], e[0]);
-    dd_prod<AL>(ah[1], al[1], xh[0][0], xl[0][0], p[1], e[1]);
-    dd_prod<AL>(ah[2], al[2], xh[1][1], xl[1][1], p[2], e[2]);
-    dd_prod<AL>(ah[3], al[3], xh[1][0], xl[1][0], p[3], e[3]);
-    two_sum(p[0], p[1], s01, t01);
-    two_sum(p[2], p[3], s23, t23);
-    two_sum(s01, s23, ih, t);
-    il = __fadd_rn(__fadd_rn(__fadd_rn(e[0], e[1]), __fadd_rn(e[2], e[3])), __fadd_rn(__fadd_rn(t01, t23), t));
+// accumulators (re, im) += a (ar, ai) times x, in the product's arithmetic: FP32, or
+// double-float (two exact products per part, one two-sum, one double-float add)
+template <int MODE, bool AL>
+__device__ __forceinline__ void cmac(float (&acc)[2][MODE == TP_DD ? 2 : 1], float arh, float aih, float arl,
+                                     float ail, const typename Arith<MODE>::X& x) {
+    if constexpr (MODE == TP_F32) {
+        acc[0][0] = fmaf(arh, x.x, fmaf(-aih, x.y, acc[0][0]));
+        acc[1][0] = fmaf(arh, x.y, fmaf(aih, x.x, acc[1][0]));
+    } else {
+        float p0, e0, p1, e1, s_, t_;
+        dd_prod<AL>(arh, arl, x.x, x.z, p0, e0);
+        dd_prod<AL>(-aih, -ail, x.y, x.w, p1, e1);
+        two_sum(p0, p1, s_, t_);
+        dd_add(acc[0][0], acc[0][1], s_, __fadd_rn(__fadd_rn(e0, e1), t_));
+        dd_prod<AL>(arh, arl, x.y, x.w, p0, e0);
+        dd_prod<AL>(aih, ail, x.x, x.z, p1, e1);
+        two_sum(p0, p1, s_, t_);
+        dd_add(acc[1][0], acc[1][1], s_, __fadd_rn(__fadd_rn(e0, e1), t_));
+    }
+}
+
+// one stored entry (complex64 exact, or complex128 split into high + low parts)
+template <class ST>
+__device__ __forceinline__ void entry_at(const unsigned char* p, float& arh, float& aih, float& arl, float& ail) {
+    if constexpr (sizeof(ST) == 8) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        arh = v.x; aih = v.y; arl = 0.f; ail = 0.f;
+    } else {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        split_double(v.x, arh, arl);
+        split_double(v.y, aih, ail);
+    }
+}
+
+// Per-warp role in a tile (see Cfg): row warp (rows 32 half + lane, columns of block
+// blk) or column warp (column 32 half + lane, rows of block blk)
+template <class ST, int MODE, int R>
+struct Role {
+    bool row;
+    int half, blk, chunk;  // chunk: which 32 KB chunk of a complex128 tile the warp reads
+};
+
+// the tile's work of one warp: ROW: row sums of its lane's row over its column block into
+// register slot RS; else column sums of its lane's column over its row block into slot CS
+template <class ST, int MODE, int R, bool ROW>
+__device__ __forceinline__ void tile_warp(const unsigned char* chunk, int half, int blk, int lane,
+                                          const typename Arith<MODE>::X* __restrict__ xsl,
+                                          float (&acc)[R][2][MODE == TP_DD ? 2 : 1]) {
+    using C = Cfg<ST, MODE, R>;
+    using X = typename Arith<MODE>::X;
+    constexpr int RB = Store<ST>::ROW_BYTES;
+    constexpr int RPC = Store<ST>::RPC;
+    constexpr bool AL = Store<ST>::AL;
+    if constexpr (ROW) {
+        // lane's row in the chunk; its column block in 16-byte pieces visited from a
+        // lane-dependent start, so that the 32 lanes' loads fall in distinct bank groups
+        const int lrow = C::CH == 1 ? 32 * half + lane : lane;
+        constexpr int EP = 16 / (int)sizeof(ST);  // entries per 16-byte piece
+        constexpr int NP = C::BW / EP;            // pieces per block row
+        const unsigned char* rp = chunk + (size_t)lrow * RB + (size_t)blk * C::BW * sizeof(ST);
+#pragma unroll 4
+        for (int c = 0; c < NP; ++c) {
+            const int k = (c + lane) & (NP - 1);
+            const int col = blk * C::BW + k * EP;
+#pragma unroll
+            for (int e = 0; e < EP; ++e) {
+                float arh, aih, arl, ail;
+                entry_at<ST>(rp + (k * EP + e) * sizeof(ST), arh, aih, arl, ail);
+#pragma unroll
+                for (int r = 0; r < R; ++r) cmac<MODE, AL>(acc[r], arh, aih, arl, ail, xsl[r * 64 + col + e]);
+            }
+        }
+    } else {
+        const int col = 32 * half + lane;
+        const int row0 = blk * C::BW;
+        const int lrow0 = C::CH == 1 ? row0 : row0 - RPC * (row0 / RPC);
+#pragma unroll 4
+        for (int t = 0; t < C::BW; ++t) {
+            float arh, aih, arl, ail;
+            entry_at<ST>(chunk + (size_t)(lrow0 + t) * RB + (size_t)col * sizeof(ST), arh, aih, arl, ail);
+#pragma unroll
+            for (int r = 0; r < R; ++r) cmac<MODE, AL>(acc[r], arh, aih, arl, ail, xsl[r * 64 + row0 + t]);
+        }
+    }
 }
 
 template <class ST, int MODE, int R>
@@ -350,22 +355,21 @@ __global__ void __launch_bounds__(Cfg<ST, MODE, R>::THREADS, 1) k_tile(TileLaunc
     using C = Cfg<ST, MODE, R>;
     using X = typename C::X;
     using A = typename C::A;
-    constexpr int W = C::W, S = C::S, CH = Store<ST>::CHUNKS, RPC = C::RPC, RPW = C::RPW, G = C::G, NV = C::NV;
+    constexpr int W = C::W, S = C::S, CH = C::CH;
     constexpr int VAL = Arith<MODE>::VAL;
     constexpr int NT = 32 * W;  // consumer threads
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* stages = sm;
-    X* xs0 = reinterpret_cast<X*>(sm + S * TP_CHUNK);                        // [NBUF][8][R][64]
-    A* acc0 = reinterpret_cast<A*>(sm + S * TP_CHUNK + C::XS);               // [NBUF][4][R][64]
-    A* red = reinterpret_cast<A*>(sm + S * TP_CHUNK + C::XS + C::ACC);       // [W][RSLOTS][R][64]
-    uint64_t* full = reinterpret_cast<uint64_t*>(sm + S * TP_CHUNK + C::XS + C::ACC + C::RED);
+    X* xs0 = reinterpret_cast<X*>(sm + S * TP_CHUNK);                 // [NBUF][8][R][64]
+    A* red = reinterpret_cast<A*>(sm + S * TP_CHUNK + C::XS);         // [W][3][R][32]
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + S * TP_CHUNK + C::XS + C::RED);
     uint64_t* empty = full + S;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int i = 0; i < S; ++i) {
             mb_init(&full[i], 1);
-            mb_init(&empty[i], W);
+            mb_init(&empty[i], C::EMPTY);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -378,9 +382,8 @@ __global__ void __launch_bounds__(Cfg<ST, MODE, R>::THREADS, 1) k_tile(TileLaunc
             bool ok = true;
             for (int64_t k = blockIdx.x; k < L.nitems && ok; k += gridDim.x) {
                 const int2 it = L.items[k];
-                int kinds[4];
                 const unsigned char* src[4];
-                const int ntl = item_tiles<ST>(L.sets[it.x], it.y >> 16, it.y & 0xFFFF, kinds, src);
+                const int ntl = item_tiles<ST>(L.sets[it.x], it.y >> 16, it.y & 0xFFFF, src);
                 for (int t = 0; t < ntl && ok; ++t)
                     for (int h = 0; h < CH && ok; ++h, ++q) {
                         const int st = (int)(q % S);
@@ -408,6 +411,12 @@ __global__ void __launch_bounds__(Cfg<ST, MODE, R>::THREADS, 1) k_tile(TileLaunc
     }
 
     // ------------------------------------------------------------------ consumers
+    const bool roww = warp < W / 2;
+    const int ww = roww ? warp : warp - W / 2;
+    const int half = ww & 1, blk = ww >> 1;
+    // the chunk of a two-chunk (complex128) tile this warp reads: rows 32 half.. (row
+    // warps) or the rows of its block (column warps)
+    const int mychunk = CH == 1 ? 0 : (roww ? half : (blk * C::BW) / Store<ST>::RPC);
     const X* __restrict__ xg = static_cast<const X*>(L.x);
     // scaled input element e (slice, column, entry) of item (set St, tiles I, J)
     auto load_x = [&](const TileSet& St, int I, int J, int e) -> X {
@@ -458,19 +467,15 @@ __global__ void __launch_bounds__(Cfg<ST, MODE, R>::THREADS, 1) k_tile(TileLaunc
         const bool diag = I == J;
         const int flags = St.flags;
         X* xs = xs0 + (C::NBUF == 2 ? par : 0) * C::XSN;
-        A* acc = acc0 + (C::NBUF == 2 ? par : 0) * C::ACCN;
-        // item start: this item's input slices and zeroed accumulators (with double
-        // buffers, other buffers than the previous item's, whose partial sums may still
-        // be being written; with single buffers, after those writes)
-        if constexpr (C::NBUF == 1) consumers_sync<W>();
+        // item start: this item's scaled input slices (the previous item's readers of this
+        // buffer passed the end-of-item barrier before any thread got here)
         if constexpr (C::PREFETCH) {
 #pragma unroll
             for (int u = 0; u < C::XPT; ++u) {
                 const int e = threadIdx.x + u * NT;
                 if (e < C::XSN) xs[e] = pre[u];
             }
-            // the next item's inputs, in flight while this item streams
-            const int64_t kn = k + gridDim.x;
+            const int64_t kn = k + gridDim.x;  // the next item's inputs, in flight meanwhile
             if (kn < L.nitems) {
                 const int2 itn = L.items[kn];
                 const TileSet& Sn = L.sets[itn.x];
@@ -483,265 +488,98 @@ __global__ void __launch_bounds__(Cfg<ST, MODE, R>::THREADS, 1) k_tile(TileLaunc
         } else {
             for (int e = threadIdx.x; e < C::XSN; e += NT) xs[e] = load_x(St, I, J, e);
         }
-        for (int e = threadIdx.x; e < C::ACCN; e += NT) acc[e] = A{};
-        int kinds[4];
-        const unsigned char* src[4];
-        const int ntl = item_tiles<ST>(St, I, J, kinds, src);
         consumers_sync<W>();
-        // column partials per output slot 1..3 (index slot - 1), summed over the item (one
-        // column: the warps' partials are then added once per item; more columns: once
-        // per tile, at the tile's end)
-        constexpr int CPS = C::RSLOTS == 3 ? 3 : 1;
-        float cp[CPS][R][2][2][VAL];
+        // per-lane partials: row warps slots 0, 1, 2 (y1_I, y1_J, y2_I), column warps
+        // slots 1, 2, 3 (y1_J, y2_I, y2_J), R columns, (re, im), double-float pairs in TP_DD
+        float acc[3][R][2][VAL];
 #pragma unroll
-        for (int c = 0; c < CPS; ++c)
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int r = 0; r < R; ++r)
 #pragma unroll
-                for (int kk = 0; kk < 2; ++kk)
+                for (int m = 0; m < 2; ++m)
 #pragma unroll
-                    for (int m = 0; m < 2; ++m)
-#pragma unroll
-                        for (int w = 0; w < VAL; ++w) cp[c][r][kk][m][w] = 0.0f;
-        int col_used = 0;  // bit c: slot c + 1 received column sums
-        for (int t = 0; t < ntl; ++t) {
-            int sr_, sc_, orow, ocol;
-            kind_roles(kinds[t], sr_, sc_, orow, ocol);
-            const bool do_row = kinds[t] <= 1 ? (flags & TS_KROW) != 0 : true;
-            const bool do_col = kinds[t] <= 1 ? (flags & TS_KCOL) != 0 : !diag;
-            if (diag) {
-                orow = orow == 1 ? 0 : (orow == 3 ? 2 : orow);
-                ocol = ocol == 1 ? 0 : (ocol == 3 ? 2 : ocol);
+                    for (int v = 0; v < VAL; ++v) acc[a][r][m][v] = 0.0f;
+        // one tile: wait for the warp's chunk, compute, release it.  Kinds: K_IJ (row slot 0
+        // from x_a(J); column slot y2_J = 3, or y2_I = 2 on the diagonal, from x_d(I)),
+        // K_JI (row slot 1 from x_a(I); column slot 2 from x_d(J)), V_IJ (row 0 from x_b(J);
+        // column 1 from x_b(I), off the diagonal), D_IJ (row 2 from x_c(J); column 3 from
+        // x_c(I), off the diagonal).  Input slices: 0 xa_J, 1 xa_I, 2 xb_J, 3 xb_I, 4 xc_J,
+        // 5 xc_I, 6 xd_I, 7 xd_J.
+        auto tile = [&](int xr, int xc, int rs, int cs, bool do_row, bool do_col) {
+            const uint32_t qq = q + mychunk;
+            const int st = (int)(qq % S);
+            if (!aborted && *abort_flag) aborted = true;
+            if (!aborted && !mb_wait(&full[st], (qq / S) & 1)) {
+                aborted = true;
+                if (lane == 0) atomicOr(L.err, 8);
+                *abort_flag = 1;
             }
-            const int cs = ocol - 1;  // column-partial slot (ocol is 1, 2 or 3 where used)
-            if (do_col) col_used |= 1 << cs;
-            // this tile's column partials (registers), added into slot cs at the tile's end
-            float ct[R][2][2][VAL];
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk)
-#pragma unroll
-                    for (int m = 0; m < 2; ++m)
-#pragma unroll
-                        for (int w = 0; w < VAL; ++w) ct[r][kk][m][w] = 0.0f;
-            // row-sum inputs at the lane's two columns (registers)
-            float xrh[R][2][2], xrl[R][2][2];
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-#pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                    const X u = xs[(sr_ * R + r) * 64 + Store<ST>::col(lane, kk)];
-                    xrh[r][kk][0] = u.x;
-                    xrh[r][kk][1] = u.y;
-                    if constexpr (MODE == TP_DD) {
-                        xrl[r][kk][0] = u.z;
-                        xrl[r][kk][1] = u.w;
-                    } else {
-                        xrl[r][kk][0] = xrl[r][kk][1] = 0.0f;
-                    }
-                }
-            const X* __restrict__ ycol = xs + sc_ * R * 64;
-            for (int h = 0; h < CH; ++h, ++q) {
-                const int st = (int)(q % S);
-                if (!aborted && *abort_flag) aborted = true;
-                if (!aborted && !mb_wait(&full[st], (q / S) & 1)) {
-                    aborted = true;
-                    if (lane == 0) atomicOr(L.err, 8);
-                    *abort_flag = 1;
-                }
-                const unsigned char* chunk = stages + (size_t)st * TP_CHUNK;
-#pragma unroll
-                for (int g0 = 0; g0 < RPW; g0 += G) {
-                    float v[NV * VAL];
-#pragma unroll
-                    for (int g = 0; g < G; ++g) {
-                        const int lr = warp + W * (g0 + g);  // row within the chunk
-                        const int i = h * RPC + lr;           // row within the tile
-                        float ah[4], al[4];
-                        Store<ST>::load(chunk + (size_t)lr * Store<ST>::ROW_BYTES, lane, ah, al);
-#pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            const int b = (g * R + r) * 2 * VAL;
-                            if constexpr (MODE == TP_F32) {
-                                float re0 = fmaf(-ah[1], xrh[r][0][1], ah[0] * xrh[r][0][0]);
-                                float re1 = fmaf(-ah[3], xrh[r][1][1], ah[2] * xrh[r][1][0]);
-                                float im0 = fmaf(ah[1], xrh[r][0][0], ah[0] * xrh[r][0][1]);
-                                float im1 = fmaf(ah[3], xrh[r][1][0], ah[2] * xrh[r][1][1]);
-                                v[b] = do_row ? __fadd_rn(re0, re1) : 0.0f;
-                                v[b + 1] = do_row ? __fadd_rn(im0, im1) : 0.0f;
-                                if (do_col) {
-                                    const X y = ycol[r * 64 + i];
-#pragma unroll
-                                    for (int kk = 0; kk < 2; ++kk) {
-                                        const float ar = ah[2 * kk], ai = ah[2 * kk + 1];
-                                        ct[r][kk][0][0] = fmaf(ar, y.x, fmaf(-ai, y.y, ct[r][kk][0][0]));
-                                        ct[r][kk][1][0] = fmaf(ar, y.y, fmaf(ai, y.x, ct[r][kk][1][0]));
-                                    }
-                                }
-                            } else {
-                                constexpr bool AL = Store<ST>::AL;
-                                float rh = 0.0f, rl = 0.0f, ih = 0.0f, il = 0.0f;
-                                if (do_row) dd_cdot2<AL>(ah, al, xrh[r], xrl[r], rh, rl, ih, il);
-                                v[b] = rh;
-                                v[b + 1] = rl;
-                                v[b + 2] = ih;
-                                v[b + 3] = il;
-                                if (do_col) {
-                                    const X y = ycol[r * 64 + i];
-#pragma unroll
-                                    for (int kk = 0; kk < 2; ++kk) {
-                                        const float arh = ah[2 * kk], aih = ah[2 * kk + 1];
-                                        const float arl = al[2 * kk], ail = al[2 * kk + 1];
-                                        // a y (complex): two exact products per part, one two-sum
-                                        float p0, e0, p1, e1, s_, t_;
-                                        dd_prod<AL>(arh, arl, y.x, y.z, p0, e0);
-                                        dd_prod<AL>(-aih, -ail, y.y, y.w, p1, e1);
-                                        two_sum(p0, p1, s_, t_);
-                                        dd_add(ct[r][kk][0][0], ct[r][kk][0][1], s_,
-                                               __fadd_rn(__fadd_rn(e0, e1), t_));
-                                        dd_prod<AL>(arh, arl, y.y, y.w, p0, e0);
-                                        dd_prod<AL>(aih, ail, y.x, y.z, p1, e1);
-                                        two_sum(p0, p1, s_, t_);
-                                        dd_add(ct[r][kk][1][0], ct[r][kk][1][1], s_,
-                                               __fadd_rn(__fadd_rn(e0, e1), t_));
-                                    }
-                                }
-                            }
-                        }
-                    }
-                    if (do_row) {
-                        butterfly<NV, VAL>(v, lane);
-                        // the lanes sharing the top log2(NV) bits hold value qv = (g R + r) 2 + re/im
-                        constexpr int SH = NV >= 32 ? 0 : (NV >= 16 ? 1 : (NV >= 8 ? 2 : (NV >= 4 ? 3 : (NV >= 2 ? 4 : 5))));
-                        const int qv = (lane >> SH) & (NV - 1);
-                        if ((lane & ((1 << SH) - 1)) == 0) {
-                            const int comp = qv & 1, rr = (qv >> 1) % R, g = (qv >> 1) / R;
-                            const int i = h * RPC + warp + W * (g0 + g);
-                            float* a = reinterpret_cast<float*>(&acc[(orow * R + rr) * 64 + i]);
-                            if constexpr (MODE == TP_F32) a[comp] = __fadd_rn(a[comp], v[0]);
-                            else dd_add(a[comp], a[2 + comp], v[0], v[1]);
-                        }
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mb_arrive(&empty[st]);
+            const unsigned char* chunk = stages + (size_t)st * TP_CHUNK;
+            if (roww && do_row) {
+                const X* xsl = xs + xr * R * 64;
+                if (rs == 0) tile_warp<ST, MODE, R, true>(chunk, half, blk, lane, xsl, acc[0]);
+                else if (rs == 1) tile_warp<ST, MODE, R, true>(chunk, half, blk, lane, xsl, acc[1]);
+                else tile_warp<ST, MODE, R, true>(chunk, half, blk, lane, xsl, acc[2]);
             }
-            if (C::RSLOTS == 3 && do_col) {  // fold the tile's column partials into slot cs (constant indices)
-#pragma unroll
-                for (int c = 0; c < CPS; ++c) {
-                    if (c != cs) continue;
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-#pragma unroll
-                        for (int kk = 0; kk < 2; ++kk)
-#pragma unroll
-                            for (int m = 0; m < 2; ++m) {
-                                if constexpr (MODE == TP_F32) {
-                                    cp[c][r][kk][m][0] = __fadd_rn(cp[c][r][kk][m][0], ct[r][kk][m][0]);
-                                } else {
-                                    dd_add(cp[c][r][kk][m][0], cp[c][r][kk][m][1], ct[r][kk][m][0], ct[r][kk][m][1]);
-                                }
-                            }
-                }
+            if (!roww && do_col) {
+                const X* xsl = xs + xc * R * 64;
+                if (cs == 1) tile_warp<ST, MODE, R, false>(chunk, half, blk, lane, xsl, acc[0]);
+                else if (cs == 2) tile_warp<ST, MODE, R, false>(chunk, half, blk, lane, xsl, acc[1]);
+                else tile_warp<ST, MODE, R, false>(chunk, half, blk, lane, xsl, acc[2]);
             }
-            if (C::RSLOTS == 1) {  // the warps' column partials of this tile into slot ocol
-                if (do_col) {
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-#pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {
-                            A a;
-                            if constexpr (MODE == TP_F32) a = make_float2(ct[r][kk][0][0], ct[r][kk][1][0]);
-                            else a = make_float4(ct[r][kk][0][0], ct[r][kk][1][0], ct[r][kk][0][1], ct[r][kk][1][1]);
-                            red[(warp * R + r) * 64 + Store<ST>::col(lane, kk)] = a;
-                        }
-                }
-                consumers_sync<W>();
-                if (do_col) {
-                    for (int e = threadIdx.x; e < R * 64; e += NT) {
-                        A sum = red[e];
-#pragma unroll
-                        for (int w = 1; w < W; ++w) {
-                            const A b = red[w * R * 64 + e];
-                            if constexpr (MODE == TP_F32) {
-                                sum.x = __fadd_rn(sum.x, b.x);
-                                sum.y = __fadd_rn(sum.y, b.y);
-                            } else {
-                                dd_add(sum.x, sum.z, b.x, b.z);
-                                dd_add(sum.y, sum.w, b.y, b.w);
-                            }
-                        }
-                        A& d = acc[ocol * R * 64 + e];
-                        if constexpr (MODE == TP_F32) {
-                            d.x = __fadd_rn(d.x, sum.x);
-                            d.y = __fadd_rn(d.y, sum.y);
-                        } else {
-                            dd_add(d.x, d.z, sum.x, sum.z);
-                            dd_add(d.y, d.w, sum.y, sum.w);
-                        }
-                    }
-                }
-                consumers_sync<W>();
-            }
+            __syncwarp();
+            if (lane == 0) mb_arrive(&empty[st]);
+            q += CH;
+        };
+        if (flags & (TS_KROW | TS_KCOL)) {
+            tile(0, 6, 0, diag ? 2 : 3, (flags & TS_KROW) != 0, (flags & TS_KCOL) != 0);
+            if (!diag) tile(1, 7, 1, 2, (flags & TS_KROW) != 0, (flags & TS_KCOL) != 0);
         }
-        // item end (one column): the warps' column partials of the three slots, added over
-        // the warps into the slots in one pass
-        if constexpr (C::RSLOTS == 3) {
+        if (flags & TS_V) tile(2, 3, 0, 1, true, !diag);
+        if (flags & TS_D) tile(4, 5, 2, 3, true, !diag);
+        // item end: the warps' partials, then per output the block partials of the row
+        // warps and the column warps added in a fixed order, into the partial-sum slots
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                if (!(col_used & (1 << c))) continue;
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-                for (int r = 0; r < R; ++r)
-#pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        A a;
-                        if constexpr (MODE == TP_F32) a = make_float2(cp[c][r][kk][0][0], cp[c][r][kk][1][0]);
-                        else
-                            a = make_float4(cp[c][r][kk][0][0], cp[c][r][kk][1][0], cp[c][r][kk][0][1],
-                                            cp[c][r][kk][1][1]);
-                        red[((warp * 3 + c) * R + r) * 64 + Store<ST>::col(lane, kk)] = a;
-                    }
+            for (int r = 0; r < R; ++r) {
+                A v;
+                if constexpr (MODE == TP_F32) v = make_float2(acc[a][r][0][0], acc[a][r][1][0]);
+                else v = make_float4(acc[a][r][0][0], acc[a][r][1][0], acc[a][r][0][1], acc[a][r][1][1]);
+                red[((warp * 3 + a) * R + r) * 32 + lane] = v;
             }
-            consumers_sync<W>();
-            for (int e = threadIdx.x; e < 3 * R * 64; e += NT) {
-                const int c = e / (R * 64);
-                if (!(col_used & (1 << c))) continue;
-                A sum = red[e];
-#pragma unroll
-                for (int w = 1; w < W; ++w) {
-                    const A b = red[w * 3 * R * 64 + e];
-                    if constexpr (MODE == TP_F32) {
-                        sum.x = __fadd_rn(sum.x, b.x);
-                        sum.y = __fadd_rn(sum.y, b.y);
-                    } else {
-                        dd_add(sum.x, sum.z, b.x, b.z);
-                        dd_add(sum.y, sum.w, b.y, b.w);
-                    }
-                }
-                A& d = acc[(c + 1) * R * 64 + (e % (R * 64))];
-                if constexpr (MODE == TP_F32) {
-                    d.x = __fadd_rn(d.x, sum.x);
-                    d.y = __fadd_rn(d.y, sum.y);
-                } else {
-                    dd_add(d.x, d.z, sum.x, sum.z);
-                    dd_add(d.y, d.w, sum.y, sum.w);
-                }
-            }
-        }
-        consumers_sync<W>();  // every row and column sum of the item is in acc
-        // the output slices into their partial-sum slots
+        consumers_sync<W>();
         const bool y1 = (flags & TS_Y1) != 0, y2 = (flags & TS_Y2) != 0;
         const int64_t nt = St.nt;
         if (!aborted) {
-            for (int e = threadIdx.x; e < C::ACCN; e += NT) {
-                const int slot = e / (R * 64), r = (e / 64) % R, row = e % 64;
+            for (int e = threadIdx.x; e < 4 * R * 64; e += NT) {
+                const int slot = e / (R * 64), r = (e / 64) % R, o = e % 64;
                 if (diag && (slot == 1 || slot == 3)) continue;
                 if ((slot < 2 && !y1) || (slot >= 2 && !y2) || r >= L.rc) continue;
+                const int h = o >> 5, l = o & 31;
+                A sum{};
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {  // row warps (slots 0..2), column warps (slots 1..3)
+                    const int a = side == 0 ? slot : slot - 1;
+                    if (a < 0 || a > 2) continue;
+#pragma unroll
+                    for (int b = 0; b < C::NB; ++b) {
+                        const int w = side * (W / 2) + h + 2 * b;
+                        const A v = red[((w * 3 + a) * R + r) * 32 + l];
+                        if constexpr (MODE == TP_F32) {
+                            sum.x = __fadd_rn(sum.x, v.x);
+                            sum.y = __fadd_rn(sum.y, v.y);
+                        } else {
+                            dd_add(sum.x, sum.z, v.x, v.z);
+                            dd_add(sum.y, sum.w, v.y, v.w);
+                        }
+                    }
+                }
                 const int out = slot >> 1;
                 const int64_t trow = (slot & 1) ? J : I, tcol = (slot & 1) ? I : J;
-                const int64_t idx = St.part * R + ((((out * nt + trow) * nt + tcol) * R + r) << 6) + row;
-                static_cast<A*>(L.part)[idx] = acc[e];
+                const int64_t idx = St.part * R + ((((out * nt + trow) * nt + tcol) * R + r) << 6) + o;
+                static_cast<A*>(L.part)[idx] = sum;
             }
         }
     }
