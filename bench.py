@@ -894,7 +894,8 @@ def main():
         """Warm-up, then the timed steps (CUDA events around each solve on the launching
         stream, no profiler events inside), then untimed profiled steps: one with every
         launch bracketed (the kernel table) and `roof_steps` with only the two longest
-        kernels bracketed (their average launch durations for the rooflines)."""
+        kernels bracketed (their average launch durations for the rooflines; the four
+        longest, the first two in the contract line)."""
         out = new_out()
         for _ in range(args.warmup):
             step(precision, out, w["tol"])
@@ -921,7 +922,8 @@ def main():
             tt = torch.tensor([total], dtype=torch.float64, device=dev)
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             total = float(tt.item())
-        # profiled steps (not part of the timed region)
+        # profiled steps (not part of the timed region): the kernel table, then the four
+        # longest kernels bracketed by events
         bem.bem_profile_select(None)
         bem.bem_profile_reset()
         bem.bem_profile_enable(True)
@@ -930,7 +932,7 @@ def main():
         torch.cuda.synchronize()
         bem.bem_profile_enable(False)
         table = bem.bem_profile_table()
-        top = [p[0] for p in table[:2]]
+        top = [p[0] for p in table[:4]]
         bem.bem_profile_reset()
         bem.bem_profile_select(top)
         for _ in range(roof_steps):
@@ -972,8 +974,9 @@ def main():
                  if fp64 else None)
 
     pp_cache = {}
-    roof = kernel_roofline(*mixed["prof"][0], te, ti, Ne, Ni, pp_cache) if mixed["prof"] else None
-    roof2 = kernel_roofline(*mixed["prof"][1], te, ti, Ne, Ni, pp_cache) if len(mixed["prof"]) > 1 else None
+    roofs = [kernel_roofline(*p, te, ti, Ne, Ni, pp_cache) for p in mixed["prof"]]
+    roof = roofs[0] if roofs else None
+    roof2 = roofs[1] if len(roofs) > 1 else None
     roof64 = [kernel_roofline(*p, te, ti, Ne, Ni, pp_cache) for p in fp64["prof"]] if fp64 else None
 
     def solve_info(rep):
@@ -990,7 +993,7 @@ def main():
                                "accuracy": {"rel_l2_vs_fp64_converged": err, "target": 1e-6,
                                             "reference": "FP64 GPU solve of the same system at GMRES tol 1e-12 "
                                                          "(the FP64 path matches the CPU oracle to 1e-10)"},
-                               "roofline": roof, "roofline_second": roof2,
+                               "rooflines": roofs,
                                "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in mixed["table"][:12]]})
         if fp64:
             emit_section("fp64", {"value": fp64["value"], "unit": UNIT, "times_ms": fp64["times"],
