@@ -75,6 +75,36 @@ FLOP_COUNT_PER_POINT_PAIR = (
 )
 FLOP_PER_POINT_PAIR = sum(f for _, f in FLOP_COUNT_PER_POINT_PAIR)  # 91, FP64 and FP32 kernels alike
 
+# Flops per point of the Sauter-Schwab singular-pair quadrature, counted from the oracle's
+# formula the same way (each point carries its own x, y and all nine shape-value products):
+FLOP_COUNT_PER_SINGULAR_POINT = (
+    ("x = sum_m B_m(x^) X_m, y likewise (3 components each)", 30),
+    ("kernel values G, dG/dn(y), dG/dn(x) as for a regular point pair", 37),
+    ("per (a, b): w L_a L_b, then V, K, T accumulations (complex)", 126),
+)
+FLOP_PER_SINGULAR_POINT = sum(f for _, f in FLOP_COUNT_PER_SINGULAR_POINT)  # 193
+SINGULAR_N = 4  # Gauss-Legendre points per axis (bem_solve_opts.n_singular default)
+
+
+def singular_points(t, n=SINGULAR_N):
+    """Quadrature points of the singular pairs of one grid: each unordered pair once
+    (coincident: 6 regions, edge-adjacent: 4, vertex-adjacent: 2; n^4 points each)."""
+    t = np.asarray(t)
+    nv = int(t.max()) + 1
+    vt = [[] for _ in range(nv)]
+    for i, tri in enumerate(t):
+        for v in tri:
+            vt[v].append(i)
+    shared = {}
+    for i, tri in enumerate(t):
+        for v in tri:
+            for j in vt[v]:
+                if j > i:
+                    shared[(i, j)] = shared.get((i, j), 0) + 1
+    edge = sum(1 for c in shared.values() if c == 2)
+    vert = sum(1 for c in shared.values() if c == 1)
+    return (6 * len(t) + 4 * edge + 2 * vert) * n ** 4
+
 
 # Unit-cube efficiency benchmarks (Sec. 5.5): the physics of the paper's table of physical
 # parameters (wavenumber 2 pi f / c of each medium; density ratio rho_int / rho_ext) and
@@ -647,9 +677,11 @@ def tiled_operator_bytes(N, entry_bytes):
     return (nt * (nt + 1) + nt * nt) * 64 * 64 * entry_bytes
 
 
-# DRAM bytes (read + write) per launch of the single-column tile product over the bytes it
-# streams, from an ncu capture of the current kernel (None until captured)
-TILE_TRAFFIC_RATIO = None
+# DRAM bytes (read + write) per launch of the single-column FP32 tile product over the bytes
+# it streams: ncu capture of the L4/L4 sphere solve (dram__bytes_read.sum 223,205,888 B +
+# dram__bytes_write.sum 5,181,696 B over 223,019,008 B of tiles); the traffic grows with the
+# tiles streamed, so the L5 launch's traffic is this ratio times its bytes
+TILE_TRAFFIC_RATIO = 1.024
 
 
 def kernel_roofline(name, ms, n, te, ti, Ne, Ni, pp_cache):
@@ -666,6 +698,15 @@ def kernel_roofline(name, ms, n, te, ti, Ne, Ni, pp_cache):
                 "traffic": traffic, "peak_kind": kind, "algorithmic_bytes_per_launch": bytes_,
                 "bytes_note": "V, D upper tile triangles + K, 64 x 64 tiles, both grids (T = K^T not stored)",
                 "avg_launch_ms": ms / n}
+    if "k_singular" in name:
+        if "sp" not in pp_cache:
+            pp_cache["sp"] = (singular_points(te) + singular_points(ti)) / 2
+        units = pp_cache["sp"]
+        ach = FLOP_PER_SINGULAR_POINT * units / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_kind": "derived FP64 FMA peak: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
+                "flop_per_point": FLOP_PER_SINGULAR_POINT, "points_per_launch": units, "avg_launch_ms": ms / n}
     if name.startswith("k_regular"):
         if "pp" not in pp_cache:
             pp_cache["pp"] = (regular_point_pairs(te) + regular_point_pairs(ti)) / 2
@@ -893,7 +934,7 @@ def main():
     def timed(precision, roof_steps):
         """Warm-up, then the timed steps (CUDA events around each solve on the launching
         stream, no profiler events inside), then untimed profiled steps: one with every
-        launch bracketed (the kernel table) and `roof_steps` with only the two longest
+        launch bracketed (the kernel table) and `roof_steps` with only the four longest
         kernels bracketed (their average launch durations for the rooflines; the four
         longest, the first two in the contract line)."""
         out = new_out()
