@@ -330,9 +330,12 @@ def serving_requests(n: int, seed: int, rate: float):
     """Poisson-arrival stream of transmission requests (the serving workload):
     ellipsoid semi-axes ~ U[0.5,1.5]^3, independent ext/int icosphere levels in
     {2,3,4}, k_ext ~ U[1,8], k_int/k_ext ~ U[1.2,2], rho_int/rho_ext log-uniform on
-    [0.1,10], 1-16 plane waves.  `rate` is arrivals per second."""
-    rng = np.random.Generator(np.random.PCG64(seed))
-    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    [0.1,10], 1-16 plane waves.  `rate` is arrivals per second.  Arrival gaps and
+    request parameters come from two generators drawn in request order, so the
+    first n requests of a longer stream are the same requests."""
+    rng_t = np.random.Generator(np.random.PCG64([seed, 0]))
+    rng = np.random.Generator(np.random.PCG64([seed, 1]))
+    t = np.cumsum(rng_t.exponential(1.0 / rate, size=n))
     reqs = []
     for i in range(n):
         axes = rng.uniform(0.5, 1.5, size=3)

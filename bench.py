@@ -376,10 +376,15 @@ def serving_stream(n, seed=50):
     return out
 
 
-def run_serving(bem, reqs, precision, rate=None, max_inflight=4):
+SERVE_STREAM_LENGTH = 2000  # requests of the whole seeded serving stream
+
+
+def run_serving(bem, reqs, precision, rate=None, max_inflight=4, group_max=0):
     """Submit the requests (all at once when rate is None, else at Poisson arrival
-    times scaled to `rate` per second); returns latencies (ms) and solves/s."""
-    srv = bem.bem_serve_create(max_inflight=max_inflight, precision=precision)
+    times scaled to `rate` per second); returns latencies (ms) and solves/s.
+    group_max: the server's lockstep-group limit (0: its default; 1: every request
+    alone)."""
+    srv = bem.bem_serve_create(max_inflight=max_inflight, precision=precision, group_max=group_max)
     try:
         t0 = time.perf_counter()
         tickets = []
@@ -405,7 +410,8 @@ def run_serving(bem, reqs, precision, rate=None, max_inflight=4):
     return {"requests": len(reqs), "ok": ok, "solves_per_s": len(reqs) / wall,
             "rhs_per_s": sum(len(r["dirs"]) for r in reqs) / wall,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-            "wall_s": wall, "hbm_high_water_bytes": stats["hbm_high_water_bytes"]}
+            "wall_s": wall, "hbm_high_water_bytes": stats["hbm_high_water_bytes"],
+            "lockstep_groups": stats["groups"], "requests_in_groups": stats["grouped"]}
 
 
 BATCH_WORKLOAD = dict(level=4, seed=4, k_ext=5.0, k_int=7.5, rho=1.0, n_dirs=64, n_single=8)
@@ -473,6 +479,45 @@ def run_batching(bem, ctx, precision, tensor_cores=1, batch_columns=0):
                                   "bytes_per_launch": 8 * 4 * (N * N + len(vi) * len(vi)),
                                   "hbm_frac": 8 * 4 * (N * N + len(vi) * len(vi)) / (ms / nl / 1e3) / 1e9 / hbm_peak()[0]}
     return out
+
+
+BATCH_FULL_WORKLOAD = dict(level=4, seed=4, n_dirs=256, n_freq=8, k_lo=2.0, k_hi=8.0, ratio=1.5, rho=1.0)
+
+
+def run_batching_full(bem, ctx):
+    """The whole many-waves workload: 256 plane-wave directions uniform on S^2 at each
+    of 8 frequencies (k_ext U[2, 8], k_int = 1.5 k_ext) on the icosphere L4 pair, one
+    bem_solve_transmission call per frequency (operators assembled once per call, the
+    256 waves in tensor-core batches of 64), mixed precision, host buffers; wall clock
+    of the 8 calls."""
+    import torch
+    import bem_inputs as bi
+    b = BATCH_FULL_WORKLOAD
+    ve, te, vi, ti = bi.transmission_pair(b["level"], b["level"], b["seed"])
+    dirs = bi.plane_wave_directions(b["n_dirs"], seed=b["seed"] + 200)
+    ks = np.random.default_rng(b["seed"] + 300).uniform(b["k_lo"], b["k_hi"], b["n_freq"])
+    ge = bem.bem_grid_create(ctx, ve, te)
+    gi = bem.bem_grid_create(ctx, vi, ti)
+    opts = {"precision": bem.BEM_PREC_MIXED}
+    bem.bem_solve_transmission(ctx, ge, gi, b["ratio"] * ks[0], ks[0], b["rho"], dirs[:16], opts=opts)  # warm-up
+    torch.cuda.synchronize()
+    per, t_all = [], time.perf_counter()
+    for k in ks:
+        t0 = time.perf_counter()
+        _, rep = bem.bem_solve_transmission(ctx, ge, gi, b["ratio"] * k, k, b["rho"], dirs, opts=opts)
+        per.append({"k_ext": float(k), "seconds": time.perf_counter() - t0,
+                    "iterations_per_rhs": rep["iterations"] / b["n_dirs"], "converged": bool(rep["converged"]),
+                    "t_assembly_ms": rep["t_assembly_ms"]})
+    wall = time.perf_counter() - t_all
+    bem.bem_grid_destroy(ge)
+    bem.bem_grid_destroy(gi)
+    n = b["n_dirs"] * b["n_freq"]
+    return {"workload": f"icosphere L{b['level']} pair (seed {b['seed']}), {b['n_dirs']} directions uniform on "
+                        f"S^2 x {b['n_freq']} frequencies k_ext U[{b['k_lo']}, {b['k_hi']}], "
+                        f"k_int = {b['ratio']} k_ext, rho {b['rho']}, mixed precision, tensor-core batches "
+                        "of 64, one call per frequency, host buffers",
+            "rhs": n, "seconds": wall, "rhs_per_s": n / wall, "all_converged": all(q["converged"] for q in per),
+            "per_frequency": per}
 
 
 def run_field(bem, ctx, w, ve, te, vi, ti, out):
@@ -867,7 +912,7 @@ def main():
                     help="skip the section timing the other formulations (single-trace, high-contrast)")
     ap.add_argument("--no-batching", dest="batching", action="store_false",
                     help="skip the many-directions section")
-    ap.add_argument("--serve-requests", type=int, default=24,
+    ap.add_argument("--serve-requests", type=int, default=96,
                     help="requests of the seeded serving stream to replay (0: skip serving)")
     ap.add_argument("--case", choices=["assemble", "solve", "mortar", "screen"], default=None,
                     help="run one small profiling case instead of the benchmark (for ncu)")
@@ -1075,14 +1120,18 @@ def main():
     if args.serve_requests > 0:
         reqs = serving_stream(args.serve_requests)
         sat = {p: run_serving(bem, reqs, p) for p in (bem.BEM_PREC_FP64, bem.BEM_PREC_MIXED)}
+        sat_alone = run_serving(bem, reqs, bem.BEM_PREC_MIXED, group_max=1)
         rate = 0.7 * sat[bem.BEM_PREC_FP64]["solves_per_s"]
         rep = {p: run_serving(bem, reqs, p, rate=rate) for p in (bem.BEM_PREC_FP64, bem.BEM_PREC_MIXED)}
         if rank == 0:
             emit_section("serving", {
-                "workload": f"first {len(reqs)} requests of the seeded serving stream (seed 50): ellipsoids "
-                            "with semi-axes U[0.5,1.5], icosphere levels 2-4 per grid, k_ext U[1,8], "
-                            "k_int/k_ext U[1.2,2], rho log-U[0.1,10], 1-16 plane waves; 4 requests in flight",
-                "saturated": {"fp64": sat[bem.BEM_PREC_FP64], "mixed": sat[bem.BEM_PREC_MIXED]},
+                "workload": f"first {len(reqs)} of the {SERVE_STREAM_LENGTH} requests of the seeded serving "
+                            "stream (seed 50): ellipsoids with semi-axes U[0.5,1.5], icosphere levels 2-4 per "
+                            "grid, k_ext U[1,8], k_int/k_ext U[1.2,2], rho log-U[0.1,10], 1-16 plane waves; "
+                            "4 requests in flight; small mixed-precision requests in lockstep groups of up to 8",
+                "fraction_of_stream": len(reqs) / SERVE_STREAM_LENGTH,
+                "saturated": {"fp64": sat[bem.BEM_PREC_FP64], "mixed": sat[bem.BEM_PREC_MIXED],
+                              "mixed_every_request_alone": sat_alone},
                 "poisson": {"rate_per_s": rate, "fp64": rep[bem.BEM_PREC_FP64], "mixed": rep[bem.BEM_PREC_MIXED]}})
 
     if args.field and rank == 0:
@@ -1148,6 +1197,7 @@ def main():
             "mixed_tensor_cores": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 1, 0),
             "mixed_cuda_cores_8": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 0, 8),
             "fp64": run_batching(bem, ctx, bem.BEM_PREC_FP64)})
+        emit_section("batching_full", run_batching_full(bem, ctx))
         emit_section("uneven_instances", run_uneven(bem, ctx))
 
     cpu = None

@@ -309,7 +309,9 @@ typedef struct {
     double  dd_switch;        /* BEM_PREC_MIXED, one right-hand side: the inner GMRES products run
                                  in double-float arithmetic while the inner residual is above
                                  dd_switch of its right-hand side, in FP32 below (default 1e-3;
-                                 0: double-float throughout, 1: FP32 throughout)                  */
+                                 0: double-float throughout, 1: FP32 throughout).  bem_solve_many:
+                                 a lockstep step runs in double-float while some running
+                                 instance's residual estimate is above it                         */
     int32_t cuda_graphs;      /* 1 (default): the fixed launch sequences of each iteration (the
                                  Chebyshev mass inverses) are captured once per solve and replayed
                                  as CUDA graphs; 0: every kernel is launched on its own.  Results
@@ -456,9 +458,23 @@ BEM_API bem_status bem_solve_many(bem_context* ctx, int32_t count, const bem_ins
  * Krylov basis, workspaces; an upper estimate) fits in what is left of the HBM
  * budget; requests that could never fit are refused at submission.  The head of
  * the queue is never overtaken, so no request starves.  The server is thread-safe.
+ * Lockstep groups: when a slot takes a mixed-precision request with one or two plane
+ * waves whose operators are small (complex64 tiles of both grids at most 64 MiB, so
+ * that a group's operators stay in L2), it also takes requests of the same kind from
+ * the first 4 * group_max
+ * places of the queue, up to group_max requests, 64 plane waves, 64 MiB of operators
+ * and the memory budget; the requests it passes over keep their order and their room
+ * in the budget, so the next free slot takes them.  The group's waves are solved
+ * together through bem_solve_many's lockstep path: every GMRES step is one launch
+ * for the whole group, each wave keeping its own Krylov process and stopping test;
+ * cancellation and deadlines stop a member alone.  Members finish together, when
+ * the group's last wave converges.  Larger, FP64 and many-wave requests run alone,
+ * their waves batched as columns of one product (faster than one lockstep instance
+ * per wave, which reads the operators once per wave).
  * dry_run = 1 runs the scheduler without any GPU work (each request "runs" for
- * dry_run_us_per_unknown microseconds per unknown and returns zeros): this is the
- * host-side mode used to test admission, ordering, timeouts and cancellation.   */
+ * dry_run_us_per_unknown microseconds per unknown and wave, a group for the longest
+ * of its members, and returns zeros): this is the host-side mode used to test
+ * admission, ordering, grouping, timeouts and cancellation.                      */
 typedef struct bem_server bem_server;
 
 typedef struct {
@@ -469,7 +485,8 @@ typedef struct {
     int32_t gmres_maxiter;          /* default 2000                                          */
     double  gmres_tol;              /* default 1e-8                                          */
     int32_t dry_run;                /* 1: no GPU work (scheduler tests)                      */
-    int32_t reserved;
+    int32_t group_max;              /* requests solved together in one lockstep group
+                                       (0: default 8; 1: every request alone), see below     */
     double  dry_run_us_per_unknown; /* dry-run service time per unknown (default 1 us)       */
 } bem_server_opts;
 
@@ -494,12 +511,15 @@ typedef struct {
     int64_t nv_ext, nv_int;
     int32_t n_rhs, precision;
     int64_t bytes_reserved;         /* admission estimate charged to the budget              */
+    int32_t group_size;             /* requests of the lockstep group it ran in (1: alone)   */
+    int32_t group_waves;            /* plane waves of that group                             */
 } bem_result;
 
 typedef struct {
     int64_t submitted, completed, refused, cancelled, timed_out, failed;
     int64_t queued, running;
     int64_t hbm_budget_bytes, hbm_reserved_bytes, hbm_high_water_bytes;
+    int64_t groups, grouped;        /* lockstep groups of two or more requests; their requests */
 } bem_serve_stats;
 
 BEM_API void       bem_serve_opts_default(bem_server_opts* opts);

@@ -158,7 +158,7 @@ class bem_server_opts(C.Structure):
         ("gmres_maxiter", C.c_int32),
         ("gmres_tol", C.c_double),
         ("dry_run", C.c_int32),
-        ("reserved", C.c_int32),
+        ("group_max", C.c_int32),
         ("dry_run_us_per_unknown", C.c_double),
     ]
 
@@ -183,13 +183,14 @@ class bem_result(C.Structure):
         ("queue_ms", C.c_double), ("run_ms", C.c_double), ("total_ms", C.c_double),
         ("nv_ext", C.c_int64), ("nv_int", C.c_int64), ("n_rhs", C.c_int32), ("precision", C.c_int32),
         ("bytes_reserved", C.c_int64),
+        ("group_size", C.c_int32), ("group_waves", C.c_int32),
     ]
 
 
 class bem_serve_stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("submitted", "completed", "refused", "cancelled", "timed_out", "failed",
                                          "queued", "running", "hbm_budget_bytes", "hbm_reserved_bytes",
-                                         "hbm_high_water_bytes")]
+                                         "hbm_high_water_bytes", "groups", "grouped")]
 
 
 _VP = C.c_void_p

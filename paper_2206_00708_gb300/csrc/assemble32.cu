@@ -82,6 +82,20 @@ __device__ __forceinline__ float2 sincos_moderate2(float x) {
     return make_float2(((q + 1) & 2) ? -cc : cc, (q & 2) ? -ss : ss);
 }
 
+// sin and cos of a small FP32 argument (|x| <= pi/4, no reduction): the same Taylor
+// series as sincos_moderate2 on r = x, returned as (cos, sin).
+__device__ __forceinline__ float2 sincos_small2(float r) {
+    const float r2 = r * r;
+    const float2 R2 = make_float2(r2, r2);
+    float2 P = __ffma2_rn(R2, make_float2(2.75573192239858907e-6f, -2.75573192239858907e-7f),
+                          make_float2(-1.98412698412698413e-4f, 2.48015873015873016e-5f));
+    P = __ffma2_rn(R2, P, make_float2(8.33333333333333333e-3f, -1.38888888888888889e-3f));
+    P = __ffma2_rn(R2, P, make_float2(-1.66666666666666667e-1f, 4.16666666666666667e-2f));
+    const float sr = fmaf(r * r2, P.x, r);
+    const float pc = fmaf(r2, P.y, -0.5f);
+    return make_float2(fmaf(r2, pc, 1.0f), sr);
+}
+
 struct TrialTile32 {
     float ch[3][TILE_TRI], cl[3][TILE_TRI];
     float u[6][3][TILE_TRI];
@@ -148,148 +162,16 @@ struct Grid32 {
     int lay[4];  // storage layouts of V, K, T, D
 };
 
-// One CTA's work: the regular pairs of test tile it and trial tile is (it <= is).
-template <bool CK>
-__device__ __forceinline__ void regular32_tile(const Grid32& G, const int it, const int is) {
-    const TriRec32* __restrict__ rec = G.rec;
-    const int32_t* __restrict__ tverts = G.tverts;
-    const uint32_t* __restrict__ tslots = G.tslots;
-    const int32_t* __restrict__ tstart = G.tstart;
-    const int32_t* __restrict__ vstart = G.vstart;
-    const int32_t* __restrict__ tvert = G.tvert;
+// The regular pairs of test tile it and trial tile is: kernel values at the 6 x 6 point
+// pairs of each triangle pair, their 3x3 blocks summed in fixed point into acc.  SMALL:
+// every phase offset k delta of the tile pair is below pi/4 (no argument reduction).
+template <bool CK, bool SMALL>
+__device__ __forceinline__ void regular32_pairs(const Grid32& G, const int it, const int is, const int nI,
+                                                const int nJ, const TriRec32* test, const TrialTile32* trial,
+                                                const int32_t (*testv)[3], const uint32_t* testslot, int32_t* acc,
+                                                const float scale, int* overflow) {
     const KP32 P = G.P;
-    float2* __restrict__ Vm = G.Vm;
-    float2* __restrict__ Km = G.Km;
-    float2* __restrict__ Tm = G.Tm;
-    float2* __restrict__ Dm = G.Dm;
-    int* __restrict__ err = G.err;
-    extern __shared__ float smem[];
-    // accumulation slabs: [op V,K,T,D][re,im][high | low int32][TILE_NV * TILE_NV]
     constexpr int SLAB = TILE_NV * TILE_NV;
-    int32_t* acc = reinterpret_cast<int32_t*>(smem);
-    TriRec32* test = reinterpret_cast<TriRec32*>(smem + 16 * SLAB);
-    TrialTile32* trial = reinterpret_cast<TrialTile32*>(test + TILE_TRI);
-    __shared__ int32_t testv[TILE_TRI][3];
-    __shared__ uint32_t testslot[TILE_TRI];
-    __shared__ int32_t vI[TILE_NV], vJ[TILE_NV];
-    __shared__ float rho_t[TILE_TRI], rho_s[TILE_TRI];
-    // bound factors: [0] min r, [1] max r, [2..3] max weight sum, [4..5] max area, [6..7] max |curl|
-    __shared__ float bnd[8];
-    __shared__ float s_scale, s_inv_scale;
-    __shared__ int s_overflow;
-
-    const int t0 = tstart[it], nI = tstart[it + 1] - t0;
-    const int s0 = tstart[is], nJ = tstart[is + 1] - s0;
-    const int nvI = vstart[it + 1] - vstart[it], nvJ = vstart[is + 1] - vstart[is];
-    for (int e = threadIdx.x; e < 16 * SLAB; e += NT32) acc[e] = 0;
-    if (threadIdx.x < 8) bnd[threadIdx.x] = threadIdx.x == 0 ? 3.0e38f : 0.0f;
-    if (threadIdx.x == 0) s_overflow = 0;
-    {
-        const float* src = reinterpret_cast<const float*>(rec + t0);
-        float* dst = reinterpret_cast<float*>(test);
-        for (int e = threadIdx.x; e < nI * TRIREC32_FLOATS; e += NT32) dst[e] = src[e];
-        for (int e = threadIdx.x; e < nI * 3; e += NT32) testv[e / 3][e % 3] = tverts[3 * t0 + e];
-        for (int e = threadIdx.x; e < nI; e += NT32) testslot[e] = tslots[t0 + e];
-        for (int e = threadIdx.x; e < 54 * TILE_TRI; e += NT32) {
-            const int s = e % TILE_TRI, f = e / TILE_TRI;
-            const float val = s < nJ ? reinterpret_cast<const float*>(rec + s0 + s)[f] : 0.0f;
-            if (f < 3) trial->ch[f][s] = val;
-            else if (f < 6) trial->cl[f - 3][s] = val;
-            else if (f < 24) trial->u[(f - 6) / 3][(f - 6) % 3][s] = val;
-            else if (f < 42) trial->wl2[(f - 24) / 3][(f - 24) % 3][s] = make_float2(val, val);
-            else if (f < 45) trial->n[f - 42][s] = val;
-            else trial->curl[(f - 45) / 3][(f - 45) % 3][s] = val;
-        }
-        for (int e = threadIdx.x; e < 3 * TILE_TRI; e += NT32) {
-            const int s = e % TILE_TRI, a = e / TILE_TRI;
-            trial->v[a][s] = s < nJ ? tverts[3 * (s0 + s) + a] : -1;
-        }
-        for (int e = threadIdx.x; e < TILE_TRI; e += NT32) trial->slot[e] = e < nJ ? tslots[s0 + e] : 0u;
-        for (int e = threadIdx.x; e < nvI; e += NT32) vI[e] = tvert[vstart[it] + e];
-        for (int e = threadIdx.x; e < nvJ; e += NT32) vJ[e] = tvert[vstart[is] + e];
-    }
-    __syncthreads();
-
-    // ---- bound of every value this CTA produces, and the fixed-point scale
-    if (threadIdx.x < 2 * TILE_TRI) {  // per-triangle radius, weight sums, area, curls
-        const bool tside = threadIdx.x < TILE_TRI;
-        const int t = tside ? threadIdx.x : threadIdx.x - TILE_TRI;
-        if (t < (tside ? nI : nJ)) {
-            float rho = 0.f, area = 0.f, wmax = 0.f, cmax = 0.f;
-            for (int p = 0; p < 6; ++p) {
-                float u2 = 0.f;
-                for (int d = 0; d < 3; ++d) {
-                    const float u = tside ? test[t].u[p][d] : trial->u[p][d][t];
-                    u2 = fmaf(u, u, u2);
-                }
-                rho = fmaxf(rho, sqrtf(u2));
-            }
-            for (int a = 0; a < 3; ++a) {
-                float w = 0.f, c2 = 0.f;
-                for (int p = 0; p < 6; ++p) w += fabsf(tside ? test[t].wl[p][a] : trial->wl2[p][a][t].x);
-                for (int d = 0; d < 3; ++d) {
-                    const float c = tside ? test[t].curl[a][d] : trial->curl[a][d][t];
-                    c2 = fmaf(c, c, c2);
-                }
-                area += w;
-                wmax = fmaxf(wmax, w);
-                cmax = fmaxf(cmax, sqrtf(c2));
-            }
-            rho *= 1.0001f;
-            (tside ? rho_t : rho_s)[t] = rho;
-            smax(&bnd[tside ? 2 : 3], wmax);
-            smax(&bnd[tside ? 4 : 5], area);
-            smax(&bnd[tside ? 6 : 7], cmax);
-        }
-    }
-    __syncthreads();
-    for (int pidx = threadIdx.x; pidx < TILE_TRI * TILE_TRI; pidx += NT32) {  // point distances
-        const int tl = pidx / TILE_TRI, sl = pidx % TILE_TRI;
-        if (tl >= nI || sl >= nJ || !regular_pair(it, is, tl, sl, testv, trial)) continue;
-        const TriRec32& tr = test[tl];
-        float D[3], R2 = 0.f;
-        for (int d = 0; d < 3; ++d) {
-            D[d] = (tr.ch[d] - trial->ch[d][sl]) + (tr.cl[d] - trial->cl[d][sl]);
-            R2 = fmaf(D[d], D[d], R2);
-        }
-        const float R = sqrtf(R2), ro = rho_t[tl] + rho_s[sl];
-        float rmin = R - ro;
-        if (rmin < 0.5f * R) {  // near pair: the smallest of its 36 point distances
-            float m2 = 3.0e38f;
-            for (int p = 0; p < 6; ++p)
-                for (int q = 0; q < 6; ++q) {
-                    float r2 = 0.f;
-                    for (int d = 0; d < 3; ++d) {
-                        const float x = D[d] + tr.u[p][d] - trial->u[q][d][sl];
-                        r2 = fmaf(x, x, r2);
-                    }
-                    m2 = fminf(m2, r2);
-                }
-            rmin = 0.999f * sqrtf(m2);
-        }
-        smin(&bnd[0], fmaxf(rmin, 1e-30f));
-        smax(&bnd[1], R + ro);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const float rmin = bnd[0], rmax = bnd[1];
-        const float kabs = sqrtf(P.k_h * P.k_h + P.k_i * P.k_i);
-        const float amp = CK ? expf(fmaxf(0.0f, -P.k_i) * rmax) : 1.0f;
-        const float g = INV_4PI_F / rmin;
-        const float ww = bnd[2] * bnd[3];
-        const float bV = ww * g;
-        const float bK = ww * g * (1.0f + kabs * rmin) / rmin;
-        const float bD = (bnd[6] * bnd[7] * bnd[4] * bnd[5] + kabs * kabs * ww) * g;
-        float B = 2.0f * amp * fmaxf(bV, fmaxf(bK, bD));  // factor 2: FP32 rounding of the values
-        B = fminf(fmaxf(B, 1e-30f), 1e30f);                // also maps NaN (no regular pair) to 1e-30
-        int e = 40 - ilogbf(B) - 1;                        // B < 2^(ilogb B + 1), so |v| 2^e < 2^40
-        e = max(-120, min(120, e));
-        s_scale = ldexpf(1.0f, e);
-        s_inv_scale = ldexpf(1.0f, -e);
-    }
-    __syncthreads();
-    const float scale = s_scale;
-
     const float tp_h = 6.28318548202514648f, tp_l = -1.7484555314695172e-7f;  // 2 pi as hi + lo
     const float inv_tp = 0.159154943091895336f;
     for (int pidx = threadIdx.x; pidx < TILE_TRI * TILE_TRI; pidx += NT32) {
@@ -369,7 +251,7 @@ __device__ __forceinline__ void regular32_tile(const Grid32& G, const int it, co
                     const float rinv = rsqrtf(r2);
                     const float r = r2 * rinv;
                     const float delta = __fdividef(num, r + Rh);
-                    const float2 cs = sincos_moderate2(P.k_h * delta);  // (cos, sin) of k delta
+                    const float2 cs = SMALL ? sincos_small2(P.k_h * delta) : sincos_moderate2(P.k_h * delta);  // (cos, sin)
                     float g = rinv * INV_4PI_F;
                     if (CK) g *= __expf(-P.k_i * delta);
                     // G = g exp(i k R) exp(i k delta)
@@ -427,7 +309,7 @@ __device__ __forceinline__ void regular32_tile(const Grid32& G, const int it, co
                     // slab of value o: high words at acc + 2 o SLAB, low words SLAB further
                     auto put = [&](int o, float v) {
                         int32_t* H = acc + (2 * o) * SLAB;
-                        fx_add(H, H + SLAB, idx, v, scale, &s_overflow);
+                        fx_add(H, H + SLAB, idx, v, scale, overflow);
                     };
                     put(0, V[a][b].x);
                     put(1, V[a][b].y);
@@ -441,14 +323,19 @@ __device__ __forceinline__ void regular32_tile(const Grid32& G, const int it, co
             }
         }
     }
-    __syncthreads();
-    if (s_overflow) {  // cannot happen for finite inputs if the bound holds; reported, tile not written
-        if (threadIdx.x == 0) atomicOr(err, 1);
-        return;
-    }
-    // flush: high * 2^21 + low, unscaled, of every touched (i, j) to the global matrices, both orientations
-    const float inv_scale = s_inv_scale;
-    const int64_t N = P.n;
+}
+
+// Adds the tile sums (high * 2^21 + low, unscaled) of every touched (i, j) to the global
+// matrices, both orientations.
+__device__ __forceinline__ void regular32_flush(const Grid32& G, const int32_t* acc, const int32_t* vI,
+                                                const int32_t* vJ, const int nvI, const int nvJ,
+                                                const float inv_scale) {
+    const int64_t N = G.P.n;
+    float2* __restrict__ Vm = G.Vm;
+    float2* __restrict__ Km = G.Km;
+    float2* __restrict__ Tm = G.Tm;
+    float2* __restrict__ Dm = G.Dm;
+    constexpr int SLAB = TILE_NV * TILE_NV;
     for (int e = threadIdx.x; e < nvI * nvJ; e += NT32) {
         const int li = e / nvJ, lj = e % nvJ;
         const int idx = li * TILE_NV + lj;
@@ -473,6 +360,158 @@ __device__ __forceinline__ void regular32_tile(const Grid32& G, const int it, co
         if (Tm) { put(Tm, 2, i, j, v[4], v[5]); put(Tm, 2, j, i, v[2], v[3]); }
         if (Dm) { put(Dm, 3, i, j, v[6], v[7]); put(Dm, 3, j, i, v[6], v[7]); }
     }
+}
+
+
+// One CTA's work: the regular pairs of test tile it and trial tile is (it <= is).
+template <bool CK>
+__device__ __forceinline__ void regular32_tile(const Grid32& G, const int it, const int is) {
+    const TriRec32* __restrict__ rec = G.rec;
+    const int32_t* __restrict__ tverts = G.tverts;
+    const uint32_t* __restrict__ tslots = G.tslots;
+    const int32_t* __restrict__ tstart = G.tstart;
+    const int32_t* __restrict__ vstart = G.vstart;
+    const int32_t* __restrict__ tvert = G.tvert;
+    const KP32 P = G.P;
+    extern __shared__ float smem[];
+    // accumulation slabs: [op V,K,T,D][re,im][high | low int32][TILE_NV * TILE_NV]
+    constexpr int SLAB = TILE_NV * TILE_NV;
+    int32_t* acc = reinterpret_cast<int32_t*>(smem);
+    TriRec32* test = reinterpret_cast<TriRec32*>(smem + 16 * SLAB);
+    TrialTile32* trial = reinterpret_cast<TrialTile32*>(test + TILE_TRI);
+    __shared__ int32_t testv[TILE_TRI][3];
+    __shared__ uint32_t testslot[TILE_TRI];
+    __shared__ int32_t vI[TILE_NV], vJ[TILE_NV];
+    __shared__ float rho_t[TILE_TRI], rho_s[TILE_TRI];
+    // bound factors: [0] min r, [1] max r, [2..3] max weight sum, [4..5] max area, [6..7] max |curl|,
+    // [8..9] largest quadrature-point radius of a test / trial triangle
+    __shared__ float bnd[10];
+    __shared__ float s_scale, s_inv_scale;
+    __shared__ int s_overflow, s_small;
+
+    const int t0 = tstart[it], nI = tstart[it + 1] - t0;
+    const int s0 = tstart[is], nJ = tstart[is + 1] - s0;
+    const int nvI = vstart[it + 1] - vstart[it], nvJ = vstart[is + 1] - vstart[is];
+    for (int e = threadIdx.x; e < 16 * SLAB; e += NT32) acc[e] = 0;
+    if (threadIdx.x < 10) bnd[threadIdx.x] = threadIdx.x == 0 ? 3.0e38f : 0.0f;
+    if (threadIdx.x == 0) s_overflow = 0;
+    {
+        const float* src = reinterpret_cast<const float*>(rec + t0);
+        float* dst = reinterpret_cast<float*>(test);
+        for (int e = threadIdx.x; e < nI * TRIREC32_FLOATS; e += NT32) dst[e] = src[e];
+        for (int e = threadIdx.x; e < nI * 3; e += NT32) testv[e / 3][e % 3] = tverts[3 * t0 + e];
+        for (int e = threadIdx.x; e < nI; e += NT32) testslot[e] = tslots[t0 + e];
+        for (int e = threadIdx.x; e < 54 * TILE_TRI; e += NT32) {
+            const int s = e % TILE_TRI, f = e / TILE_TRI;
+            const float val = s < nJ ? reinterpret_cast<const float*>(rec + s0 + s)[f] : 0.0f;
+            if (f < 3) trial->ch[f][s] = val;
+            else if (f < 6) trial->cl[f - 3][s] = val;
+            else if (f < 24) trial->u[(f - 6) / 3][(f - 6) % 3][s] = val;
+            else if (f < 42) trial->wl2[(f - 24) / 3][(f - 24) % 3][s] = make_float2(val, val);
+            else if (f < 45) trial->n[f - 42][s] = val;
+            else trial->curl[(f - 45) / 3][(f - 45) % 3][s] = val;
+        }
+        for (int e = threadIdx.x; e < 3 * TILE_TRI; e += NT32) {
+            const int s = e % TILE_TRI, a = e / TILE_TRI;
+            trial->v[a][s] = s < nJ ? tverts[3 * (s0 + s) + a] : -1;
+        }
+        for (int e = threadIdx.x; e < TILE_TRI; e += NT32) trial->slot[e] = e < nJ ? tslots[s0 + e] : 0u;
+        for (int e = threadIdx.x; e < nvI; e += NT32) vI[e] = tvert[vstart[it] + e];
+        for (int e = threadIdx.x; e < nvJ; e += NT32) vJ[e] = tvert[vstart[is] + e];
+    }
+    __syncthreads();
+
+    // ---- bound of every value this CTA produces, and the fixed-point scale
+    if (threadIdx.x < 2 * TILE_TRI) {  // per-triangle radius, weight sums, area, curls
+        const bool tside = threadIdx.x < TILE_TRI;
+        const int t = tside ? threadIdx.x : threadIdx.x - TILE_TRI;
+        if (t < (tside ? nI : nJ)) {
+            float rho = 0.f, area = 0.f, wmax = 0.f, cmax = 0.f;
+            for (int p = 0; p < 6; ++p) {
+                float u2 = 0.f;
+                for (int d = 0; d < 3; ++d) {
+                    const float u = tside ? test[t].u[p][d] : trial->u[p][d][t];
+                    u2 = fmaf(u, u, u2);
+                }
+                rho = fmaxf(rho, sqrtf(u2));
+            }
+            for (int a = 0; a < 3; ++a) {
+                float w = 0.f, c2 = 0.f;
+                for (int p = 0; p < 6; ++p) w += fabsf(tside ? test[t].wl[p][a] : trial->wl2[p][a][t].x);
+                for (int d = 0; d < 3; ++d) {
+                    const float c = tside ? test[t].curl[a][d] : trial->curl[a][d][t];
+                    c2 = fmaf(c, c, c2);
+                }
+                area += w;
+                wmax = fmaxf(wmax, w);
+                cmax = fmaxf(cmax, sqrtf(c2));
+            }
+            rho *= 1.0001f;
+            (tside ? rho_t : rho_s)[t] = rho;
+            smax(&bnd[tside ? 8 : 9], rho);
+            smax(&bnd[tside ? 2 : 3], wmax);
+            smax(&bnd[tside ? 4 : 5], area);
+            smax(&bnd[tside ? 6 : 7], cmax);
+        }
+    }
+    __syncthreads();
+    for (int pidx = threadIdx.x; pidx < TILE_TRI * TILE_TRI; pidx += NT32) {  // point distances
+        const int tl = pidx / TILE_TRI, sl = pidx % TILE_TRI;
+        if (tl >= nI || sl >= nJ || !regular_pair(it, is, tl, sl, testv, trial)) continue;
+        const TriRec32& tr = test[tl];
+        float D[3], R2 = 0.f;
+        for (int d = 0; d < 3; ++d) {
+            D[d] = (tr.ch[d] - trial->ch[d][sl]) + (tr.cl[d] - trial->cl[d][sl]);
+            R2 = fmaf(D[d], D[d], R2);
+        }
+        const float R = sqrtf(R2), ro = rho_t[tl] + rho_s[sl];
+        float rmin = R - ro;
+        if (rmin < 0.5f * R) {  // near pair: the smallest of its 36 point distances
+            float m2 = 3.0e38f;
+            for (int p = 0; p < 6; ++p)
+                for (int q = 0; q < 6; ++q) {
+                    float r2 = 0.f;
+                    for (int d = 0; d < 3; ++d) {
+                        const float x = D[d] + tr.u[p][d] - trial->u[q][d][sl];
+                        r2 = fmaf(x, x, r2);
+                    }
+                    m2 = fminf(m2, r2);
+                }
+            rmin = 0.999f * sqrtf(m2);
+        }
+        smin(&bnd[0], fmaxf(rmin, 1e-30f));
+        smax(&bnd[1], R + ro);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const float rmin = bnd[0], rmax = bnd[1];
+        const float kabs = sqrtf(P.k_h * P.k_h + P.k_i * P.k_i);
+        const float amp = CK ? expf(fmaxf(0.0f, -P.k_i) * rmax) : 1.0f;
+        const float g = INV_4PI_F / rmin;
+        const float ww = bnd[2] * bnd[3];
+        const float bV = ww * g;
+        const float bK = ww * g * (1.0f + kabs * rmin) / rmin;
+        const float bD = (bnd[6] * bnd[7] * bnd[4] * bnd[5] + kabs * kabs * ww) * g;
+        float B = 2.0f * amp * fmaxf(bV, fmaxf(bK, bD));  // factor 2: FP32 rounding of the values
+        B = fminf(fmaxf(B, 1e-30f), 1e30f);                // also maps NaN (no regular pair) to 1e-30
+        int e = 40 - ilogbf(B) - 1;                        // B < 2^(ilogb B + 1), so |v| 2^e < 2^40
+        e = max(-120, min(120, e));
+        s_scale = ldexpf(1.0f, e);
+        s_inv_scale = ldexpf(1.0f, -e);
+        // |k delta| <= |k| (rho_t + rho_s) for every point pair (delta = r - R, |delta| <= |w|):
+        // below pi/4 the phase offsets need no reduction
+        s_small = fabsf(P.k_h) * (bnd[8] + bnd[9]) <= 0.78f;
+    }
+    __syncthreads();
+    const float scale = s_scale;
+    if (s_small) regular32_pairs<CK, true>(G, it, is, nI, nJ, test, trial, testv, testslot, acc, scale, &s_overflow);
+    else regular32_pairs<CK, false>(G, it, is, nI, nJ, test, trial, testv, testslot, acc, scale, &s_overflow);
+    __syncthreads();
+    if (s_overflow) {  // cannot happen for finite inputs if the bound holds; reported, tile not written
+        if (threadIdx.x == 0) atomicOr(G.err, 1);
+        return;
+    }
+    regular32_flush(G, acc, vI, vJ, nvI, nvJ, s_inv_scale);
 }
 
 template <bool CK>

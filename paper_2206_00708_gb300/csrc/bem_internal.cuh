@@ -6,6 +6,7 @@
 #include <atomic>
 #include <chrono>
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -368,5 +369,15 @@ bem_status selftest_barrier(double* result, cudaStream_t s);
 
 bem_status mortar_coo(const bem_grid* a, const bem_grid* b, const double center[3],
                       DevBuf& row, DevBuf& col, DevBuf& val, int64_t* nnz, cudaStream_t s);
+
+// Many transmission instances in lockstep (solver.cu).  Instances with the same grids
+// and wavenumbers share one copy of their operators, masses and mortar.  halt (may be
+// null) is asked, for each running instance, between GMRES iterations: a status other
+// than BEM_OK stops that instance alone (cancellation, deadlines); status_out[count]
+// (may be null) receives each instance's outcome.
+using HaltCheck = std::function<bem_status(int)>;
+bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst, const bem_solve_opts* o,
+                           int on_device, bem_solve_report* reps, const HaltCheck* halt = nullptr,
+                           int32_t* status_out = nullptr);
 
 }  // namespace bem

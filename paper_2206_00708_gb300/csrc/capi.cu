@@ -50,8 +50,6 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                                    bem_c128 k_ext, double rho_ratio, const bem_incident* inc,
                                    const bem_solve_opts* o, bem_c128* v_ext, bem_c128* w_ext, bem_c128* v_int,
                                    bem_c128* w_int, int on_device, bem_solve_report* rep);
-bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst, const bem_solve_opts* o,
-                           int on_device, bem_solve_report* reps);
 bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_grid* gc, bem_c128 k,
                              const bem_incident* inc, const bem_solve_opts* o, int precond, bem_c128* phi,
                              int on_device, bem_solve_report* rep);

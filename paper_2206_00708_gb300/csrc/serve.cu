@@ -1,12 +1,15 @@
-// Request server for streams of transmission solves (the serving pattern of the
-// build: continuous batching with admission by HBM budget).  Host-side C++: worker
-// threads, each with its own context and CUDA stream, take requests from a FIFO
-// queue when a slot is free and the request's device working set fits in what is
-// left of the budget; the GPU work of different requests overlaps on the streams.
+// Request server for streams of transmission solves (continuous batching with
+// admission by HBM budget).  Host-side C++: worker threads, each with its own context
+// and CUDA stream, take requests from a FIFO queue when a slot is free and the
+// request's device working set fits in what is left of the budget; the GPU work of
+// different requests overlaps on the streams.  Small mixed-precision requests that
+// wait together at the head of the queue are taken as one lockstep group and solved
+// through the many-instance path (one launch per GMRES step for all their waves).
 #include "bem_internal.cuh"
 
 #include <condition_variable>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <deque>
 #include <memory>
@@ -16,6 +19,16 @@
 #include <unordered_map>
 
 namespace bem {
+
+// lockstep groups: at most this many bytes of complex64 operator tiles in one group
+// (the operators of a group are read once per wave and product, so they should stay
+// in L2), at most this many plane waves, and only requests of at most GROUP_RHS waves
+// (a request with more waves runs faster alone, its waves as columns of one product)
+constexpr int64_t GROUP_OP_BYTES = 64ll << 20;
+constexpr int GROUP_MAX_WAVES = 64;
+constexpr int GROUP_RHS = 2;
+constexpr int GROUP_MAX_DEFAULT = 8;
+constexpr int GROUP_SCAN = 4;  // a group looks at the first GROUP_SCAN * group_max queued requests
 
 bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const bem_grid* gi, bem_c128 k_int,
                                    bem_c128 k_ext, double rho_ratio, const bem_incident* inc,
@@ -34,8 +47,10 @@ struct Request {
     bem_c128 k_ext{}, k_int{};
     double rho = 1.0;
     int32_t n_rhs = 1, precision = BEM_PREC_MIXED;
+    double tol = 1e-8;
+    int32_t maxiter = 2000;
     double t_submit = 0, t_start = 0, t_end = 0, deadline = 0;
-    int64_t bytes = 0;
+    int64_t bytes = 0, op_bytes = 0;
     std::atomic<int> cancel{0};
     RState state = RState::Queued;
     bem_result result{};
@@ -56,6 +71,7 @@ struct bem_server {
     bool stopping = false;
     uint64_t next_ticket = 1;
     int64_t reserved = 0, high_water = 0;
+    int group_max = 1;
     bem_serve_stats stats{};
 };
 
@@ -87,6 +103,16 @@ int64_t working_set_bytes(int64_t ne, int64_t ni, int precision, int maxiter, in
     return ops + krylov + vectors + partial + tc + grids + mortar + (int64_t)(16 << 20);
 }
 
+// complex64 tile bytes of a request's operators (V, D upper tile triangles, K)
+int64_t operator_bytes_c64(int64_t ne, int64_t ni) {
+    const int64_t te = op_tiles(ne), ti = op_tiles(ni);
+    return (te * (te + 1) + te * te + ti * (ti + 1) + ti * ti) * OPT * OPT * 8;
+}
+
+bool groupable(const Request& r) {
+    return r.precision == BEM_PREC_MIXED && r.op_bytes <= GROUP_OP_BYTES && r.n_rhs <= GROUP_RHS;
+}
+
 void finish_locked(bem_server* srv, const std::shared_ptr<Request>& r, int32_t status) {
     r->t_end = now_seconds();
     r->state = RState::Done;
@@ -102,38 +128,31 @@ void finish_locked(bem_server* srv, const std::shared_ptr<Request>& r, int32_t s
     }
 }
 
-int32_t run_request(bem_server* srv, bem_context* ctx, Request& r) {
+// a member's stop condition (cancellation, its deadline)
+bem_status member_halt(const Request& r) {
+    if (r.cancel.load()) return BEM_E_CANCELLED;
+    if (r.deadline > 0 && now_seconds() > r.deadline) return BEM_E_TIMEOUT;
+    return BEM_OK;
+}
+
+// one request alone, through the single-problem solver (its waves batched as columns)
+int32_t run_alone(bem_context* ctx, Request& r) {
     const int64_t ne = (int64_t)r.xe.size() / 3, ni = (int64_t)r.xi.size() / 3;
-    const size_t oe = (size_t)r.n_rhs * ne, oi = (size_t)r.n_rhs * ni;
-    r.v_ext.assign(oe, bem_c128{0, 0});
-    r.w_ext.assign(oe, bem_c128{0, 0});
-    r.v_int.assign(oi, bem_c128{0, 0});
-    r.w_int.assign(oi, bem_c128{0, 0});
-    if (srv->opts.dry_run) {
-        // simulated service time, with the same stop checks as a real solve
-        const double us = srv->opts.dry_run_us_per_unknown * (double)(2 * ne + 2 * ni) * r.n_rhs;
-        const double t_end = now_seconds() + us * 1e-6;
-        while (now_seconds() < t_end) {
-            if (r.cancel.load()) return BEM_E_CANCELLED;
-            if (r.deadline > 0 && now_seconds() > r.deadline) return BEM_E_TIMEOUT;
-            std::this_thread::sleep_for(std::chrono::microseconds(200));
-        }
-        r.result.iterations = 0;
-        r.result.residual = 0.0;
-        return BEM_OK;
-    }
     ctx->cancel = &r.cancel;
     ctx->deadline = r.deadline;
     bem_grid *ge = nullptr, *gi = nullptr;
     bem_status st = bem_grid_create(ctx, r.xe.data(), ne, r.te.data(), (int64_t)r.te.size() / 3, 0, &ge);
     if (st == BEM_OK) st = bem_grid_create(ctx, r.xi.data(), ni, r.ti.data(), (int64_t)r.ti.size() / 3, 0, &gi);
     if (st == BEM_OK) {
-        bem_incident inc{r.n_rhs, r.dirs.data(), r.amps.empty() ? nullptr : r.amps.data()};
+        bem_incident inc{};
+        inc.n_rhs = r.n_rhs;
+        inc.dirs = r.dirs.data();
+        inc.amps = r.amps.empty() ? nullptr : r.amps.data();
         bem_solve_opts o;
         bem_solve_opts_default(&o);
         o.precision = r.precision;
-        o.gmres_tol = srv->opts.gmres_tol;
-        o.gmres_maxiter = srv->opts.gmres_maxiter;
+        o.gmres_tol = r.tol;
+        o.gmres_maxiter = r.maxiter;
         bem_solve_report rep{};
         st = solve_transmission_impl(ctx, ge, gi, r.k_int, r.k_ext, r.rho, &inc, &o, r.v_ext.data(), r.w_ext.data(),
                                      r.v_int.data(), r.w_int.data(), 0, &rep);
@@ -148,11 +167,114 @@ int32_t run_request(bem_server* srv, bem_context* ctx, Request& r) {
     return st;
 }
 
+// the waves of all members as instances of one lockstep solve; statuses per member
+void run_lockstep(bem_context* ctx, std::vector<std::shared_ptr<Request>>& g, std::vector<int32_t>& status) {
+    const int m = (int)g.size();
+    std::vector<bem_grid*> grids(2 * m, nullptr);
+    bem_status st = BEM_OK;
+    for (int i = 0; i < m && st == BEM_OK; ++i) {
+        Request& r = *g[i];
+        st = bem_grid_create(ctx, r.xe.data(), (int64_t)r.xe.size() / 3, r.te.data(), (int64_t)r.te.size() / 3, 0,
+                             &grids[2 * i]);
+        if (st == BEM_OK)
+            st = bem_grid_create(ctx, r.xi.data(), (int64_t)r.xi.size() / 3, r.ti.data(), (int64_t)r.ti.size() / 3,
+                                 0, &grids[2 * i + 1]);
+    }
+    std::vector<bem_instance> inst;
+    std::vector<int> owner;
+    if (st == BEM_OK) {
+        for (int i = 0; i < m; ++i) {
+            Request& r = *g[i];
+            const int64_t ne = (int64_t)r.xe.size() / 3, ni = (int64_t)r.xi.size() / 3;
+            for (int w = 0; w < r.n_rhs; ++w) {
+                bem_instance q{};
+                q.ext = grids[2 * i];
+                q.intr = grids[2 * i + 1];
+                q.k_ext = r.k_ext;
+                q.k_int = r.k_int;
+                q.rho_int_over_rho_ext = r.rho;
+                for (int d = 0; d < 3; ++d) q.dir[d] = r.dirs[3 * w + d];
+                q.amp = r.amps.empty() ? bem_c128{1.0, 0.0} : r.amps[w];
+                q.v_ext = r.v_ext.data() + w * ne;
+                q.w_ext = r.w_ext.data() + w * ne;
+                q.v_int = r.v_int.data() + w * ni;
+                q.w_int = r.w_int.data() + w * ni;
+                inst.push_back(q);
+                owner.push_back(i);
+            }
+        }
+        bem_solve_opts o;
+        bem_solve_opts_default(&o);
+        o.precision = BEM_PREC_MIXED;
+        o.gmres_tol = g[0]->tol;
+        o.gmres_maxiter = g[0]->maxiter;
+        const HaltCheck halt = [&](int k) { return member_halt(*g[owner[k]]); };
+        const int n = (int)inst.size();
+        std::vector<int32_t> ist(n, BEM_OK);
+        std::vector<bem_solve_report> reps(n);
+        st = solve_many_impl(ctx, n, inst.data(), &o, 0, reps.data(), &halt, ist.data());
+        for (int i = 0; i < m; ++i) {
+            g[i]->result.iterations = 0;
+            g[i]->result.residual = 0.0;
+        }
+        for (int k = 0; k < n; ++k) {
+            Request& r = *g[owner[k]];
+            r.result.iterations = std::max(r.result.iterations, reps[k].iterations);
+            r.result.residual = std::max(r.result.residual, reps[k].residual);
+            if (status[owner[k]] == BEM_OK) status[owner[k]] = ist[k];
+        }
+    }
+    if (st != BEM_OK && st != BEM_E_NOT_CONVERGED)
+        for (int i = 0; i < m; ++i) status[i] = st;
+    for (bem_grid* gr : grids)
+        if (gr) bem_grid_destroy(gr);
+    cudaStreamSynchronize(ctx->stream);
+}
+
+// runs a group (one request or a lockstep group) and sets each member's status
+void run_group(bem_server* srv, bem_context* ctx, std::vector<std::shared_ptr<Request>>& g,
+               std::vector<int32_t>& status) {
+    const int m = (int)g.size();
+    status.assign(m, BEM_OK);
+    for (auto& r : g) {
+        const int64_t ne = (int64_t)r->xe.size() / 3, ni = (int64_t)r->xi.size() / 3;
+        r->v_ext.assign((size_t)r->n_rhs * ne, bem_c128{0, 0});
+        r->w_ext.assign((size_t)r->n_rhs * ne, bem_c128{0, 0});
+        r->v_int.assign((size_t)r->n_rhs * ni, bem_c128{0, 0});
+        r->w_int.assign((size_t)r->n_rhs * ni, bem_c128{0, 0});
+    }
+    if (srv->opts.dry_run) {
+        // simulated service time (the longest member's), with the members' stop checks
+        double us = 0.0;
+        for (auto& r : g)
+            us = std::max(us, srv->opts.dry_run_us_per_unknown * (double)(r->xe.size() / 3 * 2 + r->xi.size() / 3 * 2) *
+                                  r->n_rhs);
+        const double t_end = now_seconds() + us * 1e-6;
+        for (;;) {
+            bool live = false;
+            for (int i = 0; i < m; ++i) {
+                if (status[i] == BEM_OK) status[i] = member_halt(*g[i]);
+                live = live || status[i] == BEM_OK;
+            }
+            if (!live || now_seconds() >= t_end) break;
+            std::this_thread::sleep_for(std::chrono::microseconds(200));
+        }
+        for (auto& r : g) {
+            r->result.iterations = 0;
+            r->result.residual = 0.0;
+        }
+        return;
+    }
+    if (m == 1) status[0] = run_alone(ctx, *g[0]);
+    else run_lockstep(ctx, g, status);
+}
+
 void worker_main(bem_server* srv, int idx) {
     bem_context* ctx = srv->opts.dry_run ? nullptr : srv->contexts[idx];
     if (ctx) cudaSetDevice(ctx->device);
     for (;;) {
-        std::shared_ptr<Request> r;
+        std::vector<std::shared_ptr<Request>> g;
+        int64_t gbytes = 0;
         {
             std::unique_lock<std::mutex> lk(srv->mu);
             srv->cv_work.wait(lk, [&] {
@@ -162,30 +284,71 @@ void worker_main(bem_server* srv, int idx) {
                 return h->cancel.load() || srv->reserved + h->bytes <= srv->opts.hbm_budget_bytes;
             });
             if (srv->stopping) return;
-            r = srv->queue.front();
+            std::shared_ptr<Request> r = srv->queue.front();
             srv->queue.pop_front();
-            srv->stats.queued = (int64_t)srv->queue.size();
             if (r->cancel.load()) {
+                srv->stats.queued = (int64_t)srv->queue.size();
                 finish_locked(srv, r, BEM_E_CANCELLED);
                 srv->cv_done.notify_all();
                 srv->cv_work.notify_all();
                 continue;
             }
-            r->state = RState::Running;
-            r->t_start = now_seconds();
-            srv->reserved += r->bytes;
+            g.push_back(r);
+            gbytes = r->bytes;
+            // requests of the same kind from the first places of the queue join its
+            // lockstep group while they fit; those passed over keep their order and
+            // their room in the budget (they are next for the following free slot)
+            if (srv->group_max > 1 && groupable(*r)) {
+                int64_t ops = r->op_bytes, passed = 0;
+                int waves = r->n_rhs;
+                size_t pos = 0;
+                const size_t window = (size_t)GROUP_SCAN * (size_t)srv->group_max;
+                while (pos < srv->queue.size() && pos < window && (int)g.size() < srv->group_max) {
+                    std::shared_ptr<Request> q = srv->queue[pos];
+                    if (q->cancel.load()) {
+                        srv->queue.erase(srv->queue.begin() + (std::ptrdiff_t)pos);
+                        finish_locked(srv, q, BEM_E_CANCELLED);
+                        continue;
+                    }
+                    if (groupable(*q) && q->tol == r->tol && q->maxiter == r->maxiter &&
+                        waves + q->n_rhs <= GROUP_MAX_WAVES && ops + q->op_bytes <= GROUP_OP_BYTES &&
+                        srv->reserved + gbytes + passed + q->bytes <= srv->opts.hbm_budget_bytes) {
+                        srv->queue.erase(srv->queue.begin() + (std::ptrdiff_t)pos);
+                        g.push_back(q);
+                        gbytes += q->bytes;
+                        ops += q->op_bytes;
+                        waves += q->n_rhs;
+                    } else {
+                        passed += q->bytes;
+                        ++pos;
+                    }
+                }
+            }
+            srv->stats.queued = (int64_t)srv->queue.size();
+            const double t0 = now_seconds();
+            int waves = 0;
+            for (auto& q : g) waves += q->n_rhs;
+            for (auto& q : g) {
+                q->state = RState::Running;
+                q->t_start = t0;
+                q->result.group_size = (int32_t)g.size();
+                q->result.group_waves = waves;
+            }
+            if (g.size() > 1) {
+                srv->stats.groups++;
+                srv->stats.grouped += (int64_t)g.size();
+            }
+            srv->reserved += gbytes;
             srv->high_water = std::max(srv->high_water, srv->reserved);
-            srv->stats.running++;
+            srv->stats.running += (int64_t)g.size();
         }
-        int32_t st;
-        if (r->deadline > 0 && now_seconds() > r->deadline) st = BEM_E_TIMEOUT;
-        else if (r->cancel.load()) st = BEM_E_CANCELLED;
-        else st = run_request(srv, ctx, *r);
+        std::vector<int32_t> status;
+        run_group(srv, ctx, g, status);
         {
             std::lock_guard<std::mutex> lk(srv->mu);
-            srv->reserved -= r->bytes;
-            srv->stats.running--;
-            finish_locked(srv, r, st);
+            srv->reserved -= gbytes;
+            srv->stats.running -= (int64_t)g.size();
+            for (size_t i = 0; i < g.size(); ++i) finish_locked(srv, g[i], status[i]);
         }
         srv->cv_done.notify_all();
         srv->cv_work.notify_all();
@@ -209,6 +372,7 @@ void bem_serve_opts_default(bem_server_opts* o) {
     o->gmres_maxiter = 2000;
     o->gmres_tol = 1e-8;
     o->dry_run = 0;
+    o->group_max = 0;
     o->dry_run_us_per_unknown = 1.0;
 }
 
@@ -221,6 +385,7 @@ bem_status bem_serve_create(const bem_server_opts* opts, bem_server** out) {
     BEM_REQUIRE(o.max_inflight >= 1 && o.max_inflight <= 64, "max_inflight must be in [1, 64]");
     BEM_REQUIRE(o.precision == BEM_PREC_FP64 || o.precision == BEM_PREC_MIXED, "unknown precision");
     BEM_REQUIRE(o.gmres_maxiter >= 1 && o.gmres_tol >= 0.0, "bad GMRES options");
+    BEM_REQUIRE(o.group_max >= 0 && o.group_max <= 64, "group_max must be in [0, 64]");
     std::unique_ptr<bem_server> srv(new (std::nothrow) bem_server());
     if (!srv) {
         set_error("host allocation failed");
@@ -252,6 +417,7 @@ bem_status bem_serve_create(const bem_server_opts* opts, bem_server** out) {
         BEM_REQUIRE(o.dry_run_us_per_unknown >= 0.0, "dry_run_us_per_unknown must be >= 0");
     }
     srv->opts = o;
+    srv->group_max = o.group_max == 0 ? GROUP_MAX_DEFAULT : o.group_max;
     srv->stats.hbm_budget_bytes = o.hbm_budget_bytes;
     bem_server* p = srv.release();
     for (int i = 0; i < o.max_inflight; ++i) p->workers.emplace_back(worker_main, p, i);
@@ -294,7 +460,12 @@ bem_status bem_serve_submit(bem_server* srv, const bem_request* q, uint64_t* tic
     r->rho = q->rho_int_over_rho_ext;
     r->n_rhs = q->n_rhs;
     r->precision = q->precision < 0 ? srv->opts.precision : q->precision;
+    r->tol = srv->opts.gmres_tol;
+    r->maxiter = srv->opts.gmres_maxiter;
     r->bytes = working_set_bytes(q->nv_ext, q->nv_int, r->precision, srv->opts.gmres_maxiter, q->n_rhs);
+    r->op_bytes = operator_bytes_c64(q->nv_ext, q->nv_int);
+    r->result.group_size = 1;
+    r->result.group_waves = q->n_rhs;
     r->result.nv_ext = q->nv_ext;
     r->result.nv_int = q->nv_int;
     r->result.n_rhs = q->n_rhs;

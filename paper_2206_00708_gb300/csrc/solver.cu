@@ -2484,7 +2484,7 @@ using ApplyMany = std::function<bem_status(const double2* in, double2* out)>;
 // the lockstep GMRES of gmres_run, one Krylov process per instance
 bem_status gmres_run_many(const ManyLayout& L, ManyGmres& W, const ApplyMany& apply, const double2* rhs,
                           const double* beta, const double* tol_abs, double2* x, int* iters_out, double* res_out,
-                          cudaStream_t s) {
+                          const HaltCheck& halted, cudaStream_t s) {
     const int C = L.count;
     const int64_t T = L.total, ldh = W.ldh, gs = W.gstride;
     double2* Vp = W.Vb.as<double2>();
@@ -2497,7 +2497,7 @@ bem_status gmres_run_many(const ManyLayout& L, ManyGmres& W, const ApplyMany& ap
     for (int r = 0; r < C; ++r) {
         qr[r].reset(beta[r]);
         res_out[r] = beta[r];
-        if (!(beta[r] > tol_abs[r])) {
+        if (!(beta[r] > tol_abs[r]) || halted(r) != BEM_OK) {
             done[r] = 1;
             ++ndone;
         }
@@ -2511,7 +2511,7 @@ bem_status gmres_run_many(const ManyLayout& L, ManyGmres& W, const ApplyMany& ap
             const double est = qr[r].add_column(W.h_col + ((size_t)slot * C + r) * gs, checked);
             it[r] = checked + 1;
             res_out[r] = est;
-            if (!(est > tol_abs[r])) {
+            if (!(est > tol_abs[r]) || halted(r) != BEM_OK) {
                 done[r] = 1;
                 ++ndone;
             }
@@ -2563,8 +2563,9 @@ bem_status gmres_run_many(const ManyLayout& L, ManyGmres& W, const ApplyMany& ap
     return BEM_OK;
 }
 
-// operators, masses and mortar of one instance (owned buffers)
-struct InstanceData {
+// operators, masses and mortar of one distinct problem (grids and wavenumbers), shared by
+// the instances that differ only in their wave or density ratio (owned buffers)
+struct ProblemData {
     GridOps ops[2];  // exterior, interior
     DevBuf mve, mvi, dve, dvi, prow, pcol, pval;
     CsrBuf csr_p, csr_t;
@@ -2574,9 +2575,30 @@ struct InstanceData {
 }  // namespace
 
 bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst, const bem_solve_opts* o,
-                           int on_device, bem_solve_report* reps) {
+                           int on_device, bem_solve_report* reps, const HaltCheck* halt, int32_t* status_out) {
     cudaStream_t s = ctx->stream;
-    std::vector<InstanceData> data(count);
+    // distinct problems: instances with the same grids and wavenumbers share one
+    std::vector<int> prob(count);
+    std::vector<int> first;  // an instance of each problem
+    for (int i = 0; i < count; ++i) {
+        int p = 0;
+        for (; p < (int)first.size(); ++p) {
+            const bem_instance& q = inst[first[p]];
+            if (q.ext == inst[i].ext && q.intr == inst[i].intr && q.k_ext.re == inst[i].k_ext.re &&
+                q.k_ext.im == inst[i].k_ext.im && q.k_int.re == inst[i].k_int.re && q.k_int.im == inst[i].k_int.im)
+                break;
+        }
+        if (p == (int)first.size()) first.push_back(i);
+        prob[i] = p;
+    }
+    const int nprob = (int)first.size();
+    std::vector<ProblemData> data(nprob);
+    // per-instance halting (cancellation, deadlines), remembered once it happens
+    std::vector<bem_status> halted(count, BEM_OK);
+    const HaltCheck halted_check = [&](int r) -> bem_status {
+        if (halted[r] == BEM_OK && halt) halted[r] = (*halt)(r);
+        return halted[r];
+    };
     EventTimer t_asm, t_mor, t_sol;
     // ---- operators: one persistent launch for the regular pairs of all grids, then the
     // singular pairs grid by grid
@@ -2585,13 +2607,14 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     std::vector<double> kre, kim;
     std::vector<float2*> PV, PK, PT, PD;
     const OpLayouts TL = op_layouts_tiled();
-    for (int i = 0; i < count; ++i) {
+    for (int p = 0; p < nprob; ++p) {
+        const bem_instance& q = inst[first[p]];
         for (int side = 0; side < 2; ++side) {
-            const bem_grid* g = side == 0 ? inst[i].ext : inst[i].intr;
-            GridOps& go = data[i].ops[side];
+            const bem_grid* g = side == 0 ? q.ext : q.intr;
+            GridOps& go = data[p].ops[side];
             BEM_TRY(go.alloc(g->nv, 8, s));
             grids.push_back(g);
-            const bem_c128 k = side == 0 ? inst[i].k_ext : inst[i].k_int;
+            const bem_c128 k = side == 0 ? q.k_ext : q.k_int;
             kre.push_back(k.re);
             kim.push_back(k.im);
             PV.push_back(go.V.as<float2>());
@@ -2606,11 +2629,11 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
         BEM_TRY(assemble_singular_into_c64(grids[g], kre[g], kim[g], o->n_singular, PV[g], PK[g], PT[g], PD[g], TL,
                                            s));
     cudaEventRecord(t_asm.b, s);
-    // ---- masses and mortar, instance by instance
+    // ---- masses and mortar, problem by problem
     cudaEventRecord(t_mor.a, s);
-    for (int i = 0; i < count; ++i) {
-        const bem_grid *ge = inst[i].ext, *gi = inst[i].intr;
-        InstanceData& d = data[i];
+    for (int p = 0; p < nprob; ++p) {
+        const bem_grid *ge = inst[first[p]].ext, *gi = inst[first[p]].intr;
+        ProblemData& d = data[p];
         BEM_TRY(d.mve.alloc(ge->m_nnz * 8, s));
         BEM_TRY(d.mvi.alloc(gi->m_nnz * 8, s));
         BEM_TRY(d.dve.alloc(ge->nv * 8, s));
@@ -2637,7 +2660,7 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     for (int i = 0; i < count; ++i) {
         const int64_t Ne = inst[i].ext->nv, Ni = inst[i].intr->nv, n = 2 * Ne + 2 * Ni;
         const double rho = inst[i].rho_int_over_rho_ext;
-        InstanceData& d = data[i];
+        ProblemData& d = data[prob[i]];
         InstDesc& D = desc[i];
         D.off = L.total;
         D.n = n;
@@ -2646,8 +2669,10 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
         d.ops[0].add(PM, -1.0, 1.0, 1.0, 1.0, o0, o0 + Ne, o0, o0 + Ne, o0, o0 + Ne);
         d.ops[1].add(PM, -1.0, 1.0, 1.0, 1.0, o0 + 2 * Ne, o0 + 2 * Ne + Ni, o0 + 2 * Ne, o0 + 2 * Ne + Ni,
                      o0 + 2 * Ne, o0 + 2 * Ne + Ni);
-        BEM_TRY(d.ell_e.build(inst[i].ext, d.mve.as<double>(), s));
-        BEM_TRY(d.ell_i.build(inst[i].intr, d.mvi.as<double>(), s));
+        if (first[prob[i]] == i) {
+            BEM_TRY(d.ell_e.build(inst[i].ext, d.mve.as<double>(), s));
+            BEM_TRY(d.ell_i.build(inst[i].intr, d.mvi.as<double>(), s));
+        }
         D.M.ci[0] = d.ell_e.ci.as<int32_t>(); D.M.v[0] = d.ell_e.v.as<double>(); D.M.W[0] = d.ell_e.W;
         D.M.dinv[0] = d.dve.as<double>();
         D.M.ci[1] = d.ell_i.ci.as<int32_t>(); D.M.v[1] = d.ell_i.v.as<double>(); D.M.W[1] = d.ell_i.W;
@@ -2716,7 +2741,7 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
         }
         return BEM_OK;
     };
-    ApplyMany apply_work = [&](const double2* xin, double2* yout) -> bem_status {
+    ApplyMany apply_f32 = [&](const double2* xin, double2* yout) -> bem_status {
         BEM_LAUNCH(k_to_c64, blocks_for(T, 256), 256, 0, s, xin, T, x32.as<float2>());
         BEM_TRY(tile_product(PM, TP_F32, 1, x32.p, z.as<double2>(), part.p, tperr.as<int>(), s));
         BEM_LAUNCH(k_transfer_many, blocks_for(T, 64), 64, 0, s, Dd, RI, T, xin, z.as<double2>());
@@ -2766,7 +2791,18 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     BEM_CUDA_TRY(cudaMemsetAsync(xsol.p, 0, (size_t)T * 16, s));
     BEM_CUDA_TRY(cudaMemcpyAsync(rvec.p, sb.p, (size_t)T * 16, cudaMemcpyDeviceToDevice, s));
     rn = beta;
-    auto pending = [&](int r) { return beta[r] > 0.0 && rn[r] > tol_abs[r] && total[r] < o->gmres_maxiter; };
+    auto pending = [&](int r) {
+        return beta[r] > 0.0 && rn[r] > tol_abs[r] && total[r] < o->gmres_maxiter && halted_check(r) == BEM_OK;
+    };
+    // inner products: double-float while the residual estimate of some running instance
+    // is above dd_switch of its inner right-hand side (the estimates trail the launches by
+    // a few iterations), FP32 after, as in the single-problem solver
+    ApplyMany apply_work = [&](const double2* xin, double2* yout) -> bem_status {
+        bool dd = false;
+        for (int r = 0; r < count && !dd; ++r)
+            dd = halted[r] == BEM_OK && est[r] > inner_tol[r] && est[r] > o->dd_switch * rn[r];
+        return dd ? apply_fp64(xin, yout) : apply_f32(xin, yout);
+    };
     int outer = 0;
     for (; outer < 12; ++outer) {
         bool any = false;
@@ -2776,7 +2812,7 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
         }
         if (!any) break;
         BEM_TRY(gmres_run_many(L, W, apply_work, rvec.as<double2>(), rn.data(), inner_tol.data(), dvec.as<double2>(),
-                               its.data(), est.data(), s));
+                               its.data(), est.data(), halted_check, s));
         int moved = 0;
         for (int r = 0; r < count; ++r) {
             total[r] += its[r];
@@ -2809,7 +2845,8 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     for (int r = 0; r < count; ++r) {
         const double rel = beta[r] > 0.0 ? rn[r] / beta[r] : 0.0;
         const bool conv = beta[r] == 0.0 || rel <= o->gmres_tol;
-        if (!conv) result = BEM_E_NOT_CONVERGED;
+        if (status_out) status_out[r] = halted[r] != BEM_OK ? halted[r] : conv ? BEM_OK : BEM_E_NOT_CONVERGED;
+        if (!conv && halted[r] == BEM_OK) result = BEM_E_NOT_CONVERGED;
         if (reps) {
             reps[r].iterations = total[r];
             reps[r].converged = conv ? 1 : 0;
@@ -3067,7 +3104,9 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
             BEM_CUDA_TRY(cudaMemcpyAsync(rvec.p, sb.p, (size_t)R * colf, cudaMemcpyDeviceToDevice, s));
             rn = beta;
             int outer = 0;
-            auto pending = [&](int r) { return beta[r] > 0.0 && rn[r] > tol_abs[r] && total[r] < o->gmres_maxiter; };
+            auto pending = [&](int r) {
+                return beta[r] > 0.0 && rn[r] > tol_abs[r] && total[r] < o->gmres_maxiter;
+            };
             auto any_pending = [&] {
                 for (int r = 0; r < R; ++r)
                     if (pending(r)) return true;

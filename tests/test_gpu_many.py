@@ -95,3 +95,29 @@ def test_many_rejects_fp64_and_bad_input(env):
         assert e.value.status == bem.BEM_E_INVALID_ARG
     finally:
         bem.bem_grid_destroy(g)
+
+
+def test_instances_of_one_problem_share_operators_and_equal_solo_solves(env):
+    """Instances with the same grids and wavenumbers (several waves, amplitudes and
+    density ratios of one problem) share one copy of the operators; each still equals
+    its solo solve, with the default switch from double-float to FP32 products, with
+    double-float products throughout (dd_switch 0) and with FP32 throughout (1)."""
+    bem, ctx = env
+    ve, te, vi, ti = bi.transmission_pair(2, 3, seed=31, axes=(1.2, 0.8, 1.0))
+    ge, gi = bem.bem_grid_create(ctx, ve, te), bem.bem_grid_create(ctx, vi, ti)
+    try:
+        dirs = bi.plane_wave_directions(4, seed=32)
+        probs = [dict(ext=ge, intr=gi, k_ext=3.0, k_int=4.5, rho=[0.5, 1.0, 2.0, 7.0][i], dir=dirs[i],
+                      amp=complex(1.0 + 0.2 * i, -0.1 * i)) for i in range(4)]
+        for sw in (1e-3, 0.0, 1.0):
+            outs, reps = bem.bem_solve_many(ctx, probs, opts={"dd_switch": sw})
+            for p, out, rep in zip(probs, outs, reps):
+                assert rep["converged"] == 1
+                solo, _ = bem.bem_solve_transmission(ctx, ge, gi, p["k_int"], p["k_ext"], p["rho"],
+                                                     np.array([p["dir"]]), amps=[p["amp"]],
+                                                     opts={"precision": bem.BEM_PREC_MIXED})
+                for key in ("v_ext", "w_ext", "v_int", "w_int"):
+                    assert rel(out[key], solo[key][0]) < TOL, (sw, key)
+    finally:
+        bem.bem_grid_destroy(ge)
+        bem.bem_grid_destroy(gi)

@@ -53,13 +53,23 @@ def mixed_ops(bem, ctx, v, t, k):
     return out
 
 
-@pytest.mark.parametrize("case", ["sphere-L1", "ellipsoid-L2-complex-k", "sphere-L3-k8"])
+# The kernel takes a shorter sin/cos (no argument reduction) on tile pairs where every
+# phase offset |k delta| <= |k| (rho_test + rho_trial) is below pi/4: the L2 cases with
+# k near 1 and the full-size rows below run that form, the others the reduced one.
+@pytest.mark.parametrize("case", ["sphere-L1", "ellipsoid-L2-complex-k", "sphere-L3-k8", "sphere-L2-k1-small-phase",
+                                  "ellipsoid-L2-complex-k-small-phase"])
 def test_mixed_operators_match_oracle(env, case):
     from oracle.helmholtz import assemble
     bem, ctx = env
     if case == "sphere-L1":
         v, t = bi.icosphere(1)
         k = 1.0
+    elif case == "sphere-L2-k1-small-phase":
+        v, t = bi.icosphere(2)
+        k = 1.0
+    elif case == "ellipsoid-L2-complex-k-small-phase":
+        _, _, v, t = bi.transmission_pair(2, 2, seed=5, axes=[1.1, 0.9, 1.0])
+        k = 1.2 + 0.3j
     elif case == "ellipsoid-L2-complex-k":
         _, _, v, t = bi.transmission_pair(2, 2, seed=3, axes=[1.3, 0.8, 1.1])
         k = 3.0 + 0.5j
