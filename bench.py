@@ -427,7 +427,17 @@ def tf32_peak():
         return 1900.0 * TF32_PER_BF16, "fallback 1.9 PFLOP/s bf16 x nominal TF32/BF16 ratio"
 
 
-def run_batching(bem, ctx, precision, tensor_cores=1, batch_columns=0):
+def fp16_peak():
+    """Dense FP16 tensor rate: the measured BF16 burst (FP16 and BF16 run at the same
+    nominal rate on GB300)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured bf16 burst (MEASURED_PEAKS.json), = fp16 rate"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback 1.9 PFLOP/s bf16 (= fp16 rate)"
+
+
+def run_batching(bem, ctx, precision, tensor_cores=2, batch_columns=0):
     """Many plane waves at one frequency: one call with all directions (solved in
     lockstep batches) against the same directions one call each; the batched call
     is profiled per kernel."""
@@ -465,19 +475,24 @@ def run_batching(bem, ctx, precision, tensor_cores=1, batch_columns=0):
            "iterations_per_rhs_batched": rep["iterations"] / b["n_dirs"],
            "assembly_ms": rep["t_assembly_ms"],
            "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in prof[:8]]}
-    tc = [p for p in prof if p[0] == "k_gemm_tc"]
+    tc = [p for p in prof if p[0] in ("k_gemm_tc", "k_gemm_tc16")]
     if tc:
         name, ms, nl = tc[0]
         N = len(ve)  # both grids have the same level here
         rp = (b["n_dirs"] + 7) // 8 * 8 if batch_columns == 0 else (batch_columns + 7) // 8 * 8
         flops = 96.0 * rp * (N * N + len(vi) * len(vi))  # 3 split terms x 2 flops x K 4N x N_b x 2 RP, 4 block rows
-        peak, kind = tf32_peak()
+        if name == "k_gemm_tc16":
+            peak, kind = fp16_peak()
+            kp = lambda n: (4 * n + 63) // 64 * 64
+            nbytes = 2 * (N * kp(N) + len(vi) * kp(len(vi))) * 4  # hi + lo halves, padded rows, 4 block rows
+        else:
+            peak, kind = tf32_peak()
+            nbytes = 8 * 4 * (N * N + len(vi) * len(vi))
         ach = flops / (ms / nl / 1e3) / 1e12
         out["tensor_roofline"] = {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak,
                                   "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "peak_kind": kind,
-                                  "flops_per_launch": flops, "avg_launch_ms": ms / nl,
-                                  "bytes_per_launch": 8 * 4 * (N * N + len(vi) * len(vi)),
-                                  "hbm_frac": 8 * 4 * (N * N + len(vi) * len(vi)) / (ms / nl / 1e3) / 1e9 / hbm_peak()[0]}
+                                  "flops_per_launch": flops, "avg_launch_ms": ms / nl, "bytes_per_launch": nbytes,
+                                  "hbm_frac": nbytes / (ms / nl / 1e3) / 1e9 / hbm_peak()[0]}
     return out
 
 
@@ -882,6 +897,8 @@ def run_case(args):
             opts = {"precision": prec, "formulation": args.formulation}
             if args.dd_switch is not None:
                 opts["dd_switch"] = args.dd_switch
+            if args.tensor_cores is not None:
+                opts["tensor_cores"] = args.tensor_cores
             _, rep = bem.bem_solve_transmission(ctx, ge, gi, 1.5 * args.k, args.k, 2.0, dirs, opts=opts)
             print("iterations", rep["iterations"])
     bem.bem_grid_destroy(ge)
@@ -923,6 +940,8 @@ def main():
     ap.add_argument("--mixed", action="store_true", help="--case: mixed precision instead of FP64")
     ap.add_argument("--rhs", type=int, default=1, help="--case solve: plane waves (batched)")
     ap.add_argument("--formulation", type=int, default=0, help="--case solve: BEM_FORM_* formulation")
+    ap.add_argument("--tensor-cores", dest="tensor_cores", type=int, default=None,
+                    help="--case solve: bem_solve_opts.tensor_cores (0 CUDA cores, 1 TF32 split, 2 FP16 split)")
     ap.add_argument("--dd-switch", dest="dd_switch", type=float, default=None,
                     help="--case solve: bem_solve_opts.dd_switch (0: double-float inner products throughout, "
                          "1: FP32 throughout)")
@@ -1192,9 +1211,11 @@ def main():
             "workload": f"unit sphere, icosphere L{bw['level']} on both grids (seed {bw['seed']}), "
                         f"k_ext={bw['k_ext']}, k_int={bw['k_int']}, rho={bw['rho']}, {bw['n_dirs']} plane "
                         f"waves in one call vs {bw['n_single']} of them one call each; mixed precision "
-                        "with tensor-core products (one batch of 64) and with CUDA-core products "
-                        "(batches of 8), FP64 (batches of 8)",
-            "mixed_tensor_cores": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 1, 0),
+                        "with tensor-core products (one batch of 64; FP16 two-term split fed by TMA "
+                        "bulk copies, the default, and TF32 three-term split) and with CUDA-core "
+                        "products (batches of 8), FP64 (batches of 8)",
+            "mixed_tensor_cores_fp16_split": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 2, 0),
+            "mixed_tensor_cores_tf32_split": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 1, 0),
             "mixed_cuda_cores_8": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 0, 8),
             "fp64": run_batching(bem, ctx, bem.BEM_PREC_FP64)})
         emit_section("batching_full", run_batching_full(bem, ctx))

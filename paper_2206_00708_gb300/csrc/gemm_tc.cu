@@ -21,7 +21,7 @@
 // threads stage A (split into Ah, Al) and copy Bh, Bl into shared memory in the
 // canonical no-swizzle K-major layout (core matrices of 8 rows x 16 bytes); one
 // thread issues 4 x 3 MMAs (M = 128, N = 2R, K = 8) into one of 2-8 TMEM accumulators
-// (chosen by stage, summed in FP64 at the end) and commits them to the stage's
+// (chosen by stage, summed in FP32 at the end) and commits them to the stage's
 // mbarrier; two shared-memory stages alternate and the global loads of A for stages
 // s + 1 and s + 2 are in flight (two register buffers) while stage s is staged and
 // issued.  With fewer row tiles than SMs (or as the autotuner chose for the shape)
@@ -97,6 +97,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// the double of a float built from its bits with integer operations (zero and FP32
+// subnormals give 0, infinities and NaNs stay so)
+__device__ __forceinline__ double widen_f32(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    if (e == 0) return 0.0;
+    const uint64_t de = e == 0xFFu ? 0x7FFull : (uint64_t)(e + 896u);
+    return __longlong_as_double((long long)(((uint64_t)(u >> 31) << 63) | (de << 52) |
+                                            ((uint64_t)(u & 0x7FFFFFu) << 29)));
+}
 
 // round to the nearest TF32 value (10 explicit mantissa bits); finite inputs
 __device__ __forceinline__ float tf32_rn(float a) {
@@ -193,7 +204,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs P, double* __r
     const int stage_bytes = 2 * TC_A_STAGE + 2 * b_stage;
     // stage s accumulates into accumulator s % nacc (columns [acc nb, acc nb + nb)):
     // the tensor cores' FP32 accumulation is biased, and nacc shorter chains, summed
-    // in FP64 at the end, keep its error near 1e-6 over K = 4 N
+    // at the end, keep its error near 1e-6 over K = 4 N
     const int nacc = nb <= 64 ? 8 : nb <= 128 ? 4 : 2;
     const int used = nacc * nb;
     const int ncols = used <= 32 ? 32 : used <= 64 ? 64 : used <= 128 ? 128 : used <= 256 ? 256 : 512;
@@ -303,11 +314,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs P, double* __r
     tc_fence_after();
     __syncthreads();
     if (!s_fail) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns [h RP, h RP + RP), h = w / 4
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns [h RP, h RP + RP), h = w / 4;
+        // the accumulators are summed in FP32 and widened to FP64 with integer operations
+        // (GB300's FP64 pipe runs at 1/64 of the FP32 rate: FP64 sums here cost as much as the MMAs)
         const int q = warp & 3, h = warp >> 2;
         const int64_t row = (int64_t)tile * TC_M + 32 * q + lane;
         for (int c0 = 0; c0 < P.RP; c0 += 8) {
-            double sum[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            float sum[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             for (int acc = 0; acc < nacc && acc < S; ++acc) {  // accumulators this CTA wrote
                 uint32_t v[8];
                 const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * nb + h * P.RP + c0);
@@ -318,7 +331,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs P, double* __r
                     : "r"(taddr)
                     : "memory");
 #pragma unroll
-                for (int j = 0; j < 8; ++j) sum[j] += (double)__uint_as_float(v[j]);
+                for (int j = 0; j < 8; ++j) sum[j] += __uint_as_float(v[j]);
             }
             if (row < N) {
 #pragma unroll
@@ -326,8 +339,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc(TcArgs P, double* __r
                     const int r = c0 + j;
                     if (r >= P.R) continue;
                     double* zz = z + 2 * ((int64_t)r * P.n + br.base + row) + h;
-                    if (gridDim.y == 1) *zz = sum[j];
-                    else atomicAdd(zz, sum[j]);  // two K halves into a zeroed z: order-free
+                    if (gridDim.y == 1) *zz = widen_f32(sum[j]);
+                    else atomicAdd(zz, widen_f32(sum[j]));  // two K halves into a zeroed z: order-free
                 }
             }
         }

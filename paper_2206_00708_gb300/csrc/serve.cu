@@ -95,8 +95,9 @@ int64_t working_set_bytes(int64_t ne, int64_t ni, int precision, int maxiter, in
     const int64_t vectors = 16 * (R + 8) * n * 16;
     // partial sums of the tile products (8 columns, double-float) and the input splits
     const int64_t partial = 2 * (te * te + ti * ti) * OPT * 8 * 16 + 8 * n * 16;
-    // tensor-core batches (mixed, more than 8 waves) also keep dense copies of the blocks
-    const int64_t dense = precision == BEM_PREC_MIXED && R > 8 ? 4 * (ne * ne + ni * ni) * 8 : 0;
+    // tensor-core batches (mixed, more than 8 waves) also keep a copy of the blocks (dense
+    // complex64, from which the FP16 split copy is made: both exist for a moment)
+    const int64_t dense = precision == BEM_PREC_MIXED && R > 8 ? 2 * 4 * (ne * ne + ni * ni) * 8 : 0;
     const int64_t tc = precision == BEM_PREC_MIXED ? 128 * ((R + 7) / 8 * 8) * (ne + ni + 16) + dense : 0;
     const int64_t grids = 600 * (ne + ni) * 2;
     const int64_t mortar = 2 * 9 * 40 * (ne + ni) * 16;

@@ -1417,7 +1417,7 @@ bem_status selftest_barrier(double* result, cudaStream_t s) {
     return BEM_OK;
 }
 
-bem_status selftest_tc(int R, double* rel_err, cudaStream_t s) {
+bem_status selftest_tc(int R, double* rel_err, cudaStream_t s, bool fp16) {
     const int64_t Ne = 300, Ni = 170, n = 2 * Ne + 2 * Ni;
     const int RW = R + 7;
     DevBuf tl[2][3], dn[2][4], xf, x, z1, z2, work, err, part, tperr;
@@ -1434,11 +1434,19 @@ bem_status selftest_tc(int R, double* rel_err, cudaStream_t s) {
     const float2* m1[4] = {dn[0][1].as<float2>(), dn[0][3].as<float2>(), dn[1][1].as<float2>(), dn[1][3].as<float2>()};
     const float2* m2[4] = {dn[0][0].as<float2>(), dn[0][2].as<float2>(), dn[1][0].as<float2>(), dn[1][2].as<float2>()};
     fill_blocks(B, m1, m2, Ne, Ni);
-    BEM_TRY(work.alloc(tc_workspace_bytes(B.rows, tc_padded_columns(R)), s));
     BEM_TRY(err.alloc(sizeof(int), s));
     BEM_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    BEM_TRY(mtf_product_tc(B.A1, B.A2, B.c1, B.c2, B.rows, B.base, B.x1, B.x2, n, R, x.as<double2>(),
-                           z1.as<double2>(), work.p, work.bytes, err.as<int>(), s));
+    Tc16Ops t16;
+    if (fp16) {
+        BEM_TRY(tc16_build(B.A1, B.A2, B.rows, t16, s));
+        BEM_TRY(work.alloc(tc16_workspace_bytes(B.rows, tc_padded_columns(R)), s));
+        BEM_TRY(mtf_product_tc16(t16, B.c1, B.c2, B.base, B.x1, B.x2, n, R, x.as<double2>(), z1.as<double2>(),
+                                 work.p, work.bytes, err.as<int>(), s));
+    } else {
+        BEM_TRY(work.alloc(tc_workspace_bytes(B.rows, tc_padded_columns(R)), s));
+        BEM_TRY(mtf_product_tc(B.A1, B.A2, B.c1, B.c2, B.rows, B.base, B.x1, B.x2, n, R, x.as<double2>(),
+                               z1.as<double2>(), work.p, work.bytes, err.as<int>(), s));
+    }
     // the FP32 tile product of the same operators
     TileProd P;
     tile_prod_add(P, tl[0][1].p, tl[0][0].p, tl[0][2].p, Ne, -1.0, 1.0, 1.0, 1.0, 0, Ne, 0, Ne, 0, Ne);
@@ -1866,6 +1874,8 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     // tensor-core batches read dense row-major blocks: dense copies of the operators
     DevBuf dense[8];  // Ve, Ke, Te, De, Vi, Ki, Ti, Di
     Blocks<float2> B32{}, Bh32{};
+    const bool tc16 = o->tensor_cores == 2;  // FP16 two-term split, TMA-fed
+    Tc16Ops t16, t16h;                       // its operator copies of B32 and Bh32
     if (mixed) {
         BEM_TRY(x32.alloc((size_t)RW * n * 8, s));
         BEM_CUDA_TRY(cudaMemsetAsync(x32.p, 0, x32.bytes, s));
@@ -1882,8 +1892,18 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
             if (st) fill_blocks_single(B32, Bh32, m1, m2, oA, oB, NA, NB, sA, sB, cv, cd);
             else fill_blocks(B32, m1, m2, Ne, Ni);
             const int RP = tc_padded_columns(RB);
-            BEM_TRY(tcw.alloc(std::max(tc_workspace_bytes(B32.rows, RP), st ? tc_workspace_bytes(Bh32.rows, RP) : 0),
-                              s));
+            if (tc16) {
+                // the split copies replace the dense complex64 copies
+                BEM_TRY(tc16_build(B32.A1, B32.A2, B32.rows, t16, s));
+                if (st) BEM_TRY(tc16_build(Bh32.A1, Bh32.A2, Bh32.rows, t16h, s));
+                for (DevBuf& d : dense) d.release();  // stream-ordered: after the split kernels
+                BEM_TRY(tcw.alloc(std::max(tc16_workspace_bytes(B32.rows, RP),
+                                           st ? tc16_workspace_bytes(Bh32.rows, RP) : 0),
+                                  s));
+            } else {
+                BEM_TRY(tcw.alloc(
+                    std::max(tc_workspace_bytes(B32.rows, RP), st ? tc_workspace_bytes(Bh32.rows, RP) : 0), s));
+            }
             BEM_TRY(tcerr.alloc(sizeof(int), s));
             BEM_CUDA_TRY(cudaMemsetAsync(tcerr.p, 0, sizeof(int), s));
         }
@@ -1895,9 +1915,13 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     // the dense view of the same blocks)
     auto gemm_work_on = [&](const TileProd& P, const Blocks<float2>* tcb, int64_t nn, float2* xw, const double2* xin,
                             double2* zo, int R) -> bem_status {
-        if (mixed && tc_batches && R > 8)
+        if (mixed && tc_batches && R > 8) {
+            if (tc16)
+                return mtf_product_tc16(tcb == &Bh32 ? t16h : t16, tcb->c1, tcb->c2, tcb->base, tcb->x1, tcb->x2, nn,
+                                        R, xin, zo, tcw.p, tcw.bytes, tcerr.as<int>(), s);
             return mtf_product_tc(tcb->A1, tcb->A2, tcb->c1, tcb->c2, tcb->rows, tcb->base, tcb->x1, tcb->x2, nn, R,
                                   xin, zo, tcw.p, tcw.bytes, tcerr.as<int>(), s);
+        }
         const bool dd = !mixed || (R == 1 && dd_now());
         if (mixed && !dd)
             BEM_LAUNCH(k_to_c64, blocks_for((int64_t)R * nn, 256), 256, 0, s, xin, (int64_t)R * nn, xw);

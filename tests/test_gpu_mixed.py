@@ -145,7 +145,7 @@ def test_mixed_solve_matches_fp64_gpu_at_level4(env):
 
 def test_tensor_core_product_matches_cuda_core_product(env):
     """The tcgen05 product (TF32, three-term split, FP32 accumulation in 8 TMEM
-    accumulators summed in FP64) against the compensated FP32 CUDA-core product on
+    accumulators, summed at the end) against the compensated FP32 CUDA-core product on
     seeded random blocks, 24 columns (three groups of 8 on the CUDA cores) and 8
     columns.  The split drops terms below 2^-22 of each product; the tensor cores'
     FP32 accumulation is biased (one accumulator over K = 1200 gave 1.04e-5 here),
@@ -157,10 +157,26 @@ def test_tensor_core_product_matches_cuda_core_product(env):
         assert err < 1e-5
 
 
-def test_tensor_core_batches_equal_cuda_core_batches(env):
+def test_fp16_split_tensor_core_product_matches_cuda_core_product(env):
+    """The TMA-fed tcgen05 product with the FP16 two-term split of both operands
+    (powers of two per block row and per column keep the parts in FP16's range;
+    Ah Bh + Ah Bl + Al Bh, FP32 accumulation in 2-8 TMEM accumulators, summed at the end)
+    against the FP32 CUDA-core product on the same seeded blocks: 24 columns (four
+    ring stages) and 128 columns (MMA N = 256, two stages).  The split keeps 22
+    significant bits of each operand, as the TF32 three-term split does."""
+    bem, ctx = env
+    for which in (10, 11):
+        err = bem.bem_selftest(ctx, which)
+        print("FP16-split tensor-core vs CUDA-core product, rel. L2", which, err)
+        assert err < 1e-5
+
+
+@pytest.mark.parametrize("tc", [1, 2])
+def test_tensor_core_batches_equal_cuda_core_batches(env, tc):
     """Twenty plane waves in one mixed-precision call, products on the tensor cores
-    (one batch of 20) or on the CUDA cores (groups of 8): both refine to the same
-    complex64 system, so the traces agree within the mode's tolerance."""
+    (one batch of 20; TF32 three-term split or FP16 two-term split) or on the CUDA
+    cores (groups of 8): all refine to the same complex64 system, so the traces agree
+    within the mode's tolerance."""
     bem, ctx = env
     ve, te, vi, ti = bi.transmission_pair(2, 2, seed=12)
     dirs = bi.plane_wave_directions(20, seed=44)
@@ -168,7 +184,7 @@ def test_tensor_core_batches_equal_cuda_core_batches(env):
     gi = bem.bem_grid_create(ctx, vi, ti)
     try:
         a, ra = bem.bem_solve_transmission(ctx, ge, gi, 4.5, 3.0, 1.3, dirs,
-                                           opts={"precision": bem.BEM_PREC_MIXED, "tensor_cores": 1})
+                                           opts={"precision": bem.BEM_PREC_MIXED, "tensor_cores": tc})
         b, rb = bem.bem_solve_transmission(ctx, ge, gi, 4.5, 3.0, 1.3, dirs,
                                            opts={"precision": bem.BEM_PREC_MIXED, "tensor_cores": 0})
     finally:

@@ -126,11 +126,14 @@ def test_single_trace_transmission_conditions_hold_on_the_gpu_solution(env):
 
 @pytest.mark.parametrize("form,tensor_cores,n_rhs", [("pmchwt_ext", 0, 1), ("pmchwt_ext", 0, 5),
                                                      ("pmchwt_ext", 1, 12), ("muller_ext", 0, 1),
-                                                     ("pmchwt_int", 1, 12), ("muller_int", 0, 3)])
+                                                     ("pmchwt_int", 1, 12), ("muller_int", 0, 3),
+                                                     ("muller_ext", 2, 10)])
 def test_single_trace_mixed_matches_oracle(env, form, tensor_cores, n_rhs):
     """Mixed precision (complex64 operators, refinement with FP64 residuals): one
     column (double-float then FP32 products), three or five columns on the CUDA cores,
-    twelve on the tensor cores; every column within 1e-6 of the FP64 oracle."""
+    twelve on the tensor cores (TF32 split), ten on the tensor cores with the FP16
+    split (two operator copies: the own grid's and the other grid's blocks, two of the
+    four block rows empty); every column within 1e-6 of the FP64 oracle."""
     from oracle.mtf import mtf_blocks
     from oracle.pmchwt import solve_single_trace
     bem, ctx = env
