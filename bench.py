@@ -489,9 +489,11 @@ def run_batching(bem, ctx, precision, tensor_cores=2, batch_columns=0):
             peak, kind = tf32_peak()
             nbytes = 8 * 4 * (N * N + len(vi) * len(vi))
         ach = flops / (ms / nl / 1e3) / 1e12
+        # the three split terms are tensor work; the method's own product is one of them
         out["tensor_roofline"] = {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak,
                                   "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "peak_kind": kind,
-                                  "flops_per_launch": flops, "avg_launch_ms": ms / nl, "bytes_per_launch": nbytes,
+                                  "flops_per_launch": flops, "method_flops_per_launch": flops / 3,
+                                  "method_tflops": ach / 3, "avg_launch_ms": ms / nl, "bytes_per_launch": nbytes,
                                   "hbm_frac": nbytes / (ms / nl / 1e3) / 1e9 / hbm_peak()[0]}
     return out
 

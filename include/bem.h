@@ -96,45 +96,6 @@ BEM_API const char* bem_last_error(void);
 /* Library version string. */
 BEM_API const char* bem_version(void);
 
-/* Number of CUDA kernels the library has launched since it was loaded (all
- * contexts and threads; a monotone counter for profiling and accounting). */
-BEM_API uint64_t bem_launch_count(void);
-
-/* Accuracy self-tests of device arithmetic written for this library (no
- * counterpart in the paper).  which = 0: largest absolute difference between the
- * FP32 assembly kernel's sin/cos (Cody-Waite reduction + Taylor series) and CUDA's
- * sincosf on 2^20 evenly spaced arguments in [-64, 64].  which = 1: relative L2
- * difference between the tensor-core multi-column MTF product (TF32 three-term
- * split) and the FP32 CUDA-core product on seeded random complex64 blocks
- * (N_ext = 300, N_int = 170, 24 columns).  which = 2: the same with 8 columns.
- * which = 3: the bounded wait of the grid barrier that the fused mass inverse uses:
- * two cooperative blocks whose barrier can never complete must each give up after
- * about a second and flag it; result = 1000 * flag + elapsed seconds (expected
- * 1000 + ~1).  which = 4..9: relative L2 difference between the tiled operator
- * product (symmetry-packed V, D; K applied as K and K^T) and an FP64 product with
- * dense copies of the same seeded random operators (two grids of 300 and 170
- * vertices): 4 FP32 on complex64, 1 column; 5 the same, 5 columns; 6 double-float on
- * complex64, 1 column; 7 the same, 3 columns; 8 double-float on complex128, 1 column;
- * 9 the same, 8 columns.  which = 10, 11: as 1, for the TMA-fed tensor-core product
- * with the FP16 two-term split of both operands, 24 and 128 columns. */
-BEM_API bem_status bem_selftest(bem_context* ctx, int which, double* result);
-
-/* Per-kernel device timing.  While enabled, each launch of the library is
- * bracketed by CUDA events on its own stream; totals accumulate per kernel
- * name.  bem_profile_count() returns the number of kernel names seen and
- * bem_profile_get(i, ...) the i-th name (NUL-terminated, truncated to name_len),
- * its summed device time in ms and its number of launches.  Collecting waits
- * for the recorded events.  Not meant to be toggled while a solve is running. */
-BEM_API void       bem_profile_enable(int on);
-/* Restrict the timing to kernels whose names start with one of the comma-separated
- * prefixes (NULL or "": every kernel), so that a few kernels can be timed inside a
- * measured region without bracketing every launch. */
-BEM_API void       bem_profile_select(const char* prefixes);
-BEM_API void       bem_profile_reset(void);
-BEM_API int        bem_profile_count(void);
-BEM_API bem_status bem_profile_get(int index, char* name, int name_len, double* total_ms,
-                                   int64_t* launches);
-
 /* ---------------------------------------------------------------- autotuner
  * Launch shapes of the iteration's kernels (no counterpart in the paper, which runs
  * on CPUs).  bem_autotune times the candidates on complex64 operators of the two
@@ -547,6 +508,49 @@ BEM_API bem_status bem_serve_wait(bem_server* srv, uint64_t ticket, double timeo
  * its outcome becomes BEM_E_CANCELLED (unless it had already finished). */
 BEM_API bem_status bem_serve_cancel(bem_server* srv, uint64_t ticket);
 BEM_API bem_status bem_serve_get_stats(bem_server* srv, bem_serve_stats* st);
+
+/* ---------------------------------------------------------------- diagnostics
+ * Accounting, self-tests and per-kernel timing used by the tests and the benchmark
+ * (no counterpart in the paper). */
+
+/* Number of CUDA kernels the library has launched since it was loaded (all
+ * contexts and threads; a monotone counter for profiling and accounting). */
+BEM_API uint64_t bem_launch_count(void);
+
+/* Accuracy self-tests of device arithmetic written for this library (no
+ * counterpart in the paper).  which = 0: largest absolute difference between the
+ * FP32 assembly kernel's sin/cos (Cody-Waite reduction + Taylor series) and CUDA's
+ * sincosf on 2^20 evenly spaced arguments in [-64, 64].  which = 1: relative L2
+ * difference between the tensor-core multi-column MTF product (TF32 three-term
+ * split) and the FP32 CUDA-core product on seeded random complex64 blocks
+ * (N_ext = 300, N_int = 170, 24 columns).  which = 2: the same with 8 columns.
+ * which = 3: the bounded wait of the grid barrier that the fused mass inverse uses:
+ * two cooperative blocks whose barrier can never complete must each give up after
+ * about a second and flag it; result = 1000 * flag + elapsed seconds (expected
+ * 1000 + ~1).  which = 4..9: relative L2 difference between the tiled operator
+ * product (symmetry-packed V, D; K applied as K and K^T) and an FP64 product with
+ * dense copies of the same seeded random operators (two grids of 300 and 170
+ * vertices): 4 FP32 on complex64, 1 column; 5 the same, 5 columns; 6 double-float on
+ * complex64, 1 column; 7 the same, 3 columns; 8 double-float on complex128, 1 column;
+ * 9 the same, 8 columns.  which = 10, 11: as 1, for the TMA-fed tensor-core product
+ * with the FP16 two-term split of both operands, 24 and 128 columns. */
+BEM_API bem_status bem_selftest(bem_context* ctx, int which, double* result);
+
+/* Per-kernel device timing.  While enabled, each launch of the library is
+ * bracketed by CUDA events on its own stream; totals accumulate per kernel
+ * name.  bem_profile_count() returns the number of kernel names seen and
+ * bem_profile_get(i, ...) the i-th name (NUL-terminated, truncated to name_len),
+ * its summed device time in ms and its number of launches.  Collecting waits
+ * for the recorded events.  Not meant to be toggled while a solve is running. */
+BEM_API void       bem_profile_enable(int on);
+/* Restrict the timing to kernels whose names start with one of the comma-separated
+ * prefixes (NULL or "": every kernel), so that a few kernels can be timed inside a
+ * measured region without bracketing every launch. */
+BEM_API void       bem_profile_select(const char* prefixes);
+BEM_API void       bem_profile_reset(void);
+BEM_API int        bem_profile_count(void);
+BEM_API bem_status bem_profile_get(int index, char* name, int name_len, double* total_ms,
+                                   int64_t* launches);
 
 #ifdef __cplusplus
 }
