@@ -15,8 +15,10 @@ pytestmark = pytest.mark.gpu
 
 KEYS = ("v_ext", "w_ext", "v_int", "w_int")
 # formulation -> bound on the largest relative L2 error of the four traces
-BOUNDS = {"mtf": 1e-6, "pmchwt_ext": 1e-6, "pmchwt_int": 1e-6, "muller_ext": 3e-6, "muller_int": 3e-6,
-          "hc_ext_neu": 1e-6, "hc_ext_dir": 4e-5, "hc_int_neu": 1e-5, "hc_int_dir": 1e-6}
+# (measured at L4: MTF 6.0e-7, PMCHWT 4.4e-7 / 4.3e-7, Mueller 1.01e-6 / 8.3e-7, high-contrast
+# 4.5e-7 / 6.2e-6 / 2.3e-6 / 4.8e-7; at L5 the bench reports 9.6e-7 for the MTF)
+BOUNDS = {"mtf": 1e-6, "pmchwt_ext": 1e-6, "pmchwt_int": 1e-6, "muller_ext": 2e-6, "muller_int": 2e-6,
+          "hc_ext_neu": 1e-6, "hc_ext_dir": 1.5e-5, "hc_int_neu": 5e-6, "hc_int_dir": 1e-6}
 
 
 @pytest.fixture(scope="module")
