@@ -128,8 +128,9 @@ __device__ __forceinline__ void fx_add(int32_t* H, int32_t* L, int idx, float v,
     const float l = fmaf(-h, 2097152.0f, c);                    // c - h 2^21, exact
     const int32_t hi = __float_as_int(th) - FX_MAGIC_BITS;
     const int32_t lo = __float_as_int(l + FX_MAGIC) - FX_MAGIC_BITS;
-    if (lo != 0) atomicAdd(&L[idx], lo);
-    if (hi != 0) atomicAdd(&H[idx], hi);
+    // unconditional: skipping zero words costs more (tests, divergence) than it saves
+    atomicAdd(&L[idx], lo);
+    atomicAdd(&H[idx], hi);
 }
 
 // largest |v| of a positive float kept as its bit pattern (monotone for x >= 0)
@@ -240,7 +241,7 @@ __device__ __forceinline__ void regular32_pairs(const Grid32& G, const int it, c
                 float2 SV[3], SK[3], ST[3];
 #pragma unroll
                 for (int b = 0; b < 3; ++b) SV[b] = SK[b] = ST[b] = make_float2(0.f, 0.f);
-#pragma unroll 2
+#pragma unroll 3
                 for (int q = 0; q < 6; ++q) {
                     const float wx = ux - trial->u[q][0][sl], wy = uy - trial->u[q][1][sl],
                                 wz = uz - trial->u[q][2][sl];
