@@ -27,6 +27,7 @@
 // rotations and the residual estimates kept on the device; the host reads R scalars
 // per iteration to stop.  x0 = 0, stop when |g_{j+1}| <= tol * ||S b||.
 #include "bem_internal.cuh"
+#include "ddf.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -630,12 +631,17 @@ __global__ void __launch_bounds__(256) k_cheb_fused(MassPair M, const double2* _
 // ---------------------------------------------------------------- GMRES kernels
 // Krylov basis: vector i of right-hand side r at V + (i * R + r) * n.
 // Hessenberg of r: column-major, H + r * ldh * ldh, column j at + j * ldh.
+// The vectors are FP64; the inner products and basis updates run in double-float
+// arithmetic on the FP32 pipe (ddf.cuh: 2^-48 relative per product, errors collected
+// in a second word), which is several times faster than GB300's FP64 pipe.
 // Inner products conj(V_{i,r}) . w_r for i < m: the rows are cut into `nblk`
-// contiguous chunks; warp (chunk, i) of grid (nblk, ceil(m / 8), R) sums its chunk
-// with eight independent accumulators per lane (eight loads in flight), reduces
-// within the warp and writes partial[((r * m) + i) * nblk + chunk].
+// contiguous chunks; warp w of block (chunk, y, r) takes the DOT_VPW basis vectors
+// i = (8 y + w) DOT_VPW + u over its chunk (w split once per row for all of them),
+// reduces within the warp and writes partial[((r * m) + i) * nblk + chunk].
 constexpr int DOT_ROWS = 256;         // target rows per chunk
 constexpr int DOT_MAX_BLOCKS = 1216;  // 8 per SM
+constexpr int DOT_VPW = 4;            // basis vectors per warp
+constexpr int DOT_VPB = 8 * DOT_VPW;  // basis vectors per block
 
 int dot_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(DOT_MAX_BLOCKS, (n + DOT_ROWS - 1) / DOT_ROWS)); }
 
@@ -644,36 +650,37 @@ __global__ void __launch_bounds__(256) k_dots_partial(const double2* __restrict_
                                                       double2* __restrict__ partial) {
     const int r = blockIdx.z, b = blockIdx.x;
     const int lane = threadIdx.x & 31;
-    const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (i >= m) return;
+    const int i0 = (blockIdx.y * 8 + (threadIdx.x >> 5)) * DOT_VPW;
+    if (i0 >= m) return;
+    const int nv = min(DOT_VPW, m - i0);
     const int64_t chunk = (n + nblk - 1) / nblk;
     const int64_t e0 = b * chunk, e1 = min(n, e0 + chunk);
     const double2* __restrict__ wr = w + (int64_t)r * n;
-    const double2* __restrict__ v = Vb + ((int64_t)i * R + r) * n;
-    double2 s[8];
+    float4 S[DOT_VPW];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) s[u] = make_double2(0, 0);
-    int64_t e = e0 + lane;
-    for (; e + 224 < e1; e += 256) {
+    for (int u = 0; u < DOT_VPW; ++u) S[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+        const float4 c = ddf::split2(wr[e]);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const double2 a = v[e + 32 * u], c = wr[e + 32 * u];
-            s[u].x = fma(a.x, c.x, fma(a.y, c.y, s[u].x));
-            s[u].y = fma(a.x, c.y, fma(-a.y, c.x, s[u].y));
+        for (int u = 0; u < DOT_VPW; ++u)
+            if (u < nv) ddf::cmac<true>(S[u], ddf::split2(Vb[((int64_t)(i0 + u) * R + r) * n + e]), c);
+    }
+#pragma unroll
+    for (int u = 0; u < DOT_VPW; ++u) {
+        if (u >= nv) break;
+        float4 t = S[u];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float4 q;
+            q.x = __shfl_xor_sync(0xffffffffu, t.x, o);
+            q.y = __shfl_xor_sync(0xffffffffu, t.y, o);
+            q.z = __shfl_xor_sync(0xffffffffu, t.z, o);
+            q.w = __shfl_xor_sync(0xffffffffu, t.w, o);
+            ddf::add(t, q);
         }
+        if (lane == 0) partial[((int64_t)r * m + i0 + u) * nblk + b] = ddf::value(t);
     }
-    for (; e < e1; e += 32) {
-        const double2 a = v[e], c = wr[e];
-        s[0].x = fma(a.x, c.x, fma(a.y, c.y, s[0].x));
-        s[0].y = fma(a.x, c.y, fma(-a.y, c.x, s[0].y));
-    }
-#pragma unroll
-    for (int u = 1; u < 8; ++u) {
-        s[0].x += s[u].x;
-        s[0].y += s[u].y;
-    }
-    const double2 t = warp_sum2(s[0]);
-    if (lane == 0) partial[((int64_t)r * m + i) * nblk + b] = t;
 }
 
 // out[r * ostride + i] = sum_b partial[r][i][b]  (+= when accumulate)
@@ -695,45 +702,60 @@ __global__ void k_dots_final(const double2* __restrict__ partial, int m, int nbl
 }
 
 // w_r -= sum_{i<m} h_r[i] V_{i,r}   or (overwrite) x_r = sum_{i<m_r} y_r[i] V_{i,r}.
-// A block takes 32 rows; its 8 warps take the basis vectors i = warp (mod 8), four
-// loads in flight per thread, and the 8 partial sums of a row are added in a fixed
-// order: many more threads than rows for the latency-bound late iterations.
+// A block takes 32 rows; its 8 warps take the basis vectors i = warp (mod 8), and the 8
+// partial sums of a row are added in a fixed order: many more threads than rows for the
+// latency-bound late iterations.  HS: the coefficients are split once per block into
+// shared memory (m of them), else per use.
+constexpr int COMBINE_HS_MAX = 2048;
+
+template <bool HS>
 __global__ void __launch_bounds__(256) k_combine(const double2* __restrict__ Vb, int64_t n, int R, int m,
                                                  const int* __restrict__ mr, const double2* __restrict__ h,
                                                  int64_t hstride, double2* __restrict__ w, int overwrite) {
+    extern __shared__ float4 hs[];
     const int r = blockIdx.y;
     const int lr = threadIdx.x & 31, sl = threadIdx.x >> 5;
     const int64_t e = blockIdx.x * 32ll + lr;
     const int mm = mr ? mr[r] : m;
     const double2* __restrict__ hr = h + r * hstride;
-    double2 s[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) s[u] = make_double2(0, 0);
-    if (e < n) {
-        int i = sl;
-        for (; i + 24 < mm; i += 32) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) s[u] = cfma(hr[i + 8 * u], Vb[((int64_t)(i + 8 * u) * R + r) * n + e], s[u]);
-        }
-        for (; i < mm; i += 8) s[0] = cfma(hr[i], Vb[((int64_t)i * R + r) * n + e], s[0]);
+    if (HS) {
+        for (int i = threadIdx.x; i < mm; i += blockDim.x) hs[i] = ddf::split2(hr[i]);
+        __syncthreads();
     }
-    __shared__ double2 part[8][32];
-    part[sl][lr] = make_double2((s[0].x + s[1].x) + (s[2].x + s[3].x), (s[0].y + s[1].y) + (s[2].y + s[3].y));
+    float4 S = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e < n) {
+#pragma unroll 4
+        for (int i = sl; i < mm; i += 8) {
+            const float4 hv = HS ? hs[i] : ddf::split2(hr[i]);
+            ddf::cmac<false>(S, hv, ddf::split2(Vb[((int64_t)i * R + r) * n + e]));
+        }
+    }
+    __shared__ float4 part[8][32];
+    part[sl][lr] = S;
     __syncthreads();
     if (sl == 0 && e < n) {
-        double2 t = part[0][lr];
+        float4 t = part[0][lr];
 #pragma unroll
-        for (int k = 1; k < 8; ++k) {
-            t.x += part[k][lr].x;
-            t.y += part[k][lr].y;
-        }
+        for (int k = 1; k < 8; ++k) ddf::add(t, part[k][lr]);
+        const double2 tv = ddf::value(t);
         double2* wr = w + (int64_t)r * n;
-        if (overwrite) wr[e] = t;
+        if (overwrite) wr[e] = tv;
         else {
             const double2 q = wr[e];
-            wr[e] = make_double2(q.x - t.x, q.y - t.y);
+            wr[e] = make_double2(q.x - tv.x, q.y - tv.y);
         }
     }
+}
+
+// the basis update / combination above, with the coefficients in shared memory when
+// their count is known on the host and small enough
+bem_status launch_combine(dim3 grid, const double2* Vb, int64_t n, int R, int m, const int* mr, const double2* h,
+                          int64_t hstride, double2* w, int overwrite, cudaStream_t s) {
+    if (!mr && m <= COMBINE_HS_MAX)
+        BEM_LAUNCH(k_combine<true>, grid, 256, (size_t)m * sizeof(float4), s, Vb, n, R, m, mr, h, hstride, w,
+                   overwrite);
+    else BEM_LAUNCH(k_combine<false>, grid, 256, 0, s, Vb, n, R, m, mr, h, hstride, w, overwrite);
+    return BEM_OK;
 }
 
 __global__ void k_add_cols(double2* __restrict__ a, int64_t astride, const double2* __restrict__ b,
@@ -1213,14 +1235,14 @@ bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs
             double2* vj = Vp + (int64_t)j * R * n;
             BEM_TRY(apply(vj, W.w.as<double2>(), R));
             double2* Hj = W.H.as<double2>() + (int64_t)j * ldh;  // + r * ldh * ldh per column
-            const unsigned gy = (unsigned)((j + 1 + 7) / 8);
+            const unsigned gy = (unsigned)((j + 1 + DOT_VPB - 1) / DOT_VPB);
             for (int pass = 0; pass < 2; ++pass) {  // CGS2
                 double2* h = pass == 0 ? Hj : W.hbuf.as<double2>();
                 const int64_t hst = pass == 0 ? ldh * ldh : gs;
                 BEM_LAUNCH(k_dots_partial, dim3(W.nblk, gy, R), 256, 0, s, Vp, n, R, j + 1, W.w.as<double2>(),
                            W.nblk, W.partial.as<double2>());
                 BEM_LAUNCH(k_dots_final, dim3(j + 1, R), 32, 0, s, W.partial.as<double2>(), j + 1, W.nblk, h, hst, 0);
-                BEM_LAUNCH(k_combine, ecb, 256, 0, s, Vp, n, R, j + 1, nullptr, h, hst, W.w.as<double2>(), 0);
+                BEM_TRY(launch_combine(ecb, Vp, n, R, j + 1, nullptr, h, hst, W.w.as<double2>(), 0, s));
             }
             BEM_LAUNCH(k_add_cols, dim3(1, R), 256, 0, s, Hj, ldh * ldh, W.hbuf.as<double2>(), gs, j + 1);
             BEM_TRY(W.sq_norms(W.w.as<double2>(), s));
@@ -1242,7 +1264,7 @@ bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs
     }
     BEM_CUDA_TRY(cudaMemcpyAsync(W.mr.p, W.h_mr, R * 4, cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(cudaMemcpyAsync(W.y.p, W.h_y, (size_t)R * gs * 16, cudaMemcpyHostToDevice, s));
-    BEM_LAUNCH(k_combine, ecb, 256, 0, s, Vp, n, R, 0, W.mr.as<int>(), W.y.as<double2>(), gs, x, 1);
+    BEM_TRY(launch_combine(ecb, Vp, n, R, 0, W.mr.as<int>(), W.y.as<double2>(), gs, x, 1, s));
     BEM_CUDA_TRY(cudaStreamSynchronize(s));  // pinned h_y / h_mr are reused by the next run
     for (int r = 0; r < R; ++r) iters_out[r] = it[r];
     return BEM_OK;
