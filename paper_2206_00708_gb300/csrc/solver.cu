@@ -48,9 +48,6 @@ constexpr double CHEB_ALPHA = 0.5, CHEB_BETA = 2.0;
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // a*b + c
-    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
-}
 
 __device__ __forceinline__ double2 warp_sum2(double2 v) {
 #pragma unroll
@@ -2357,32 +2354,38 @@ __global__ void __launch_bounds__(256) k_dots_partial_many(const double2* __rest
                                                            const int64_t* __restrict__ cs,
                                                            const int64_t* __restrict__ ce, int nchunks,
                                                            double2* __restrict__ partial) {
+    // double-float, DOT_VPW basis vectors per warp, as k_dots_partial
     const int c = blockIdx.x;
     const int lane = threadIdx.x & 31;
-    const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (i >= m) return;
-    const double2* __restrict__ v = Vb + (int64_t)i * total;
+    const int i0 = (blockIdx.y * 8 + (threadIdx.x >> 5)) * DOT_VPW;
+    if (i0 >= m) return;
+    const int nv = min(DOT_VPW, m - i0);
     const int64_t e1 = ce[c];
-    double2 s[4];
+    float4 S[DOT_VPW];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) s[u] = make_double2(0, 0);
-    int64_t e = cs[c] + lane;
-    for (; e + 96 < e1; e += 128) {
+    for (int u = 0; u < DOT_VPW; ++u) S[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
+    for (int64_t e = cs[c] + lane; e < e1; e += 32) {
+        const float4 b = ddf::split2(w[e]);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const double2 a = v[e + 32 * u], b = w[e + 32 * u];
-            s[u].x = fma(a.x, b.x, fma(a.y, b.y, s[u].x));
-            s[u].y = fma(a.x, b.y, fma(-a.y, b.x, s[u].y));
+        for (int u = 0; u < DOT_VPW; ++u)
+            if (u < nv) ddf::cmac<true>(S[u], ddf::split2(Vb[(int64_t)(i0 + u) * total + e]), b);
+    }
+#pragma unroll
+    for (int u = 0; u < DOT_VPW; ++u) {
+        if (u >= nv) break;
+        float4 t = S[u];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float4 q;
+            q.x = __shfl_xor_sync(0xffffffffu, t.x, o);
+            q.y = __shfl_xor_sync(0xffffffffu, t.y, o);
+            q.z = __shfl_xor_sync(0xffffffffu, t.z, o);
+            q.w = __shfl_xor_sync(0xffffffffu, t.w, o);
+            ddf::add(t, q);
         }
+        if (lane == 0) partial[(int64_t)(i0 + u) * nchunks + c] = ddf::value(t);
     }
-    for (; e < e1; e += 32) {
-        const double2 a = v[e], b = w[e];
-        s[0].x = fma(a.x, b.x, fma(a.y, b.y, s[0].x));
-        s[0].y = fma(a.x, b.y, fma(-a.y, b.x, s[0].y));
-    }
-    const double2 t = warp_sum2(make_double2((s[0].x + s[1].x) + (s[2].x + s[3].x),
-                                             (s[0].y + s[1].y) + (s[2].y + s[3].y)));
-    if (lane == 0) partial[(int64_t)i * nchunks + c] = t;
 }
 
 // out[r * ostride + i] = sum of the chunks of instance r (grid (m, instances))
@@ -2403,34 +2406,28 @@ __global__ void __launch_bounds__(256) k_combine_many(const double2* __restrict_
                                                       const int* __restrict__ mr, const int32_t* __restrict__ row_inst,
                                                       const double2* __restrict__ h, int64_t hstride,
                                                       double2* __restrict__ w, int overwrite) {
+    // double-float, as k_combine (each row's instance picks its coefficients)
     const int lr = threadIdx.x & 31, sl = threadIdx.x >> 5;
     const int64_t e = blockIdx.x * 32ll + lr;
-    double2 s[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) s[u] = make_double2(0, 0);
+    float4 S = make_float4(0.f, 0.f, 0.f, 0.f);
     if (e < total) {
         const int r = row_inst[e];
         const int mm = mr ? mr[r] : m;
         const double2* __restrict__ hr = h + r * hstride;
-        int i = sl;
-        for (; i + 24 < mm; i += 32) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) s[u] = cfma(hr[i + 8 * u], Vb[(int64_t)(i + 8 * u) * total + e], s[u]);
-        }
-        for (; i < mm; i += 8) s[0] = cfma(hr[i], Vb[(int64_t)i * total + e], s[0]);
+#pragma unroll 4
+        for (int i = sl; i < mm; i += 8)
+            ddf::cmac<false>(S, ddf::split2(hr[i]), ddf::split2(Vb[(int64_t)i * total + e]));
     }
-    __shared__ double2 part[8][32];
-    part[sl][lr] = make_double2((s[0].x + s[1].x) + (s[2].x + s[3].x), (s[0].y + s[1].y) + (s[2].y + s[3].y));
+    __shared__ float4 part[8][32];
+    part[sl][lr] = S;
     __syncthreads();
     if (sl == 0 && e < total) {
-        double2 t = part[0][lr];
+        float4 t = part[0][lr];
 #pragma unroll
-        for (int k = 1; k < 8; ++k) {
-            t.x += part[k][lr].x;
-            t.y += part[k][lr].y;
-        }
-        if (overwrite) w[e] = t;
-        else w[e] = make_double2(w[e].x - t.x, w[e].y - t.y);
+        for (int k = 1; k < 8; ++k) ddf::add(t, part[k][lr]);
+        const double2 tv = ddf::value(t);
+        if (overwrite) w[e] = tv;
+        else w[e] = make_double2(w[e].x - tv.x, w[e].y - tv.y);
     }
 }
 
@@ -2574,7 +2571,7 @@ bem_status gmres_run_many(const ManyLayout& L, ManyGmres& W, const ApplyMany& ap
             const double2* vj = Vp + (int64_t)j * T;
             BEM_TRY(apply(vj, W.w.as<double2>()));
             double2* Hj = W.H.as<double2>() + (int64_t)j * ldh;
-            const unsigned gy = (unsigned)((j + 1 + 7) / 8);
+            const unsigned gy = (unsigned)((j + 1 + DOT_VPB - 1) / DOT_VPB);
             for (int pass = 0; pass < 2; ++pass) {
                 double2* h = pass == 0 ? Hj : W.hbuf.as<double2>();
                 const int64_t hst = pass == 0 ? ldh * ldh : gs;
