@@ -767,7 +767,8 @@ def kernel_roofline(name, ms, n, te, ti, Ne, Ni, pp_cache):
         ach = FLOP_PER_SINGULAR_POINT * units / avg_s / 1e12
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_kind": "derived FP64 FMA peak: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
+                "peak_kind": "derived FP64 FMA peak: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (geometry and kernel "
+                             "values on the FP64 pipe; the 54 sums run in double-float on the FP32 pipe)",
                 "flop_per_point": FLOP_PER_SINGULAR_POINT, "points_per_launch": units, "avg_launch_ms": ms / n}
     if name.startswith("k_regular"):
         if "pp" not in pp_cache:

@@ -21,6 +21,7 @@
 // Singular pairs (coincident / edge / vertex): one warp per pair, lanes stride the
 // Sauter-Schwab points, a butterfly reduction sums the 3x3 blocks.
 #include "bem_internal.cuh"
+#include "ddf.cuh"
 
 namespace bem {
 
@@ -236,9 +237,14 @@ k_singular(const double* __restrict__ xyz, const int32_t* __restrict__ tri, cons
     const double JJ = rt.J * rs.J;
     const int cnt = kind == 0 ? count.x : (kind == 1 ? count.y : count.z);
     const int off = kind == 0 ? offset.x : (kind == 1 ? offset.y : offset.z);
-    double acc[54];
+    // the 54 sums (3 x 3 blocks of V, K, T as re, im) in double-float on the FP32 pipe:
+    // the kernel values are formed in FP64, each sum term (w_q L_a L_b times a kernel
+    // value) is added as an exact FP32 product plus its rounded cross terms, every
+    // rounding error collected in a second word (ddf.cuh); GB300's FP64 pipe (1/64 of
+    // the FP32 rate) is left with the geometry and the kernel values
+    float ah[54], ac[54];
 #pragma unroll
-    for (int e = 0; e < 54; ++e) acc[e] = 0.0;
+    for (int e = 0; e < 54; ++e) ah[e] = ac[e] = 0.0f;
     for (int e = lane; e < cnt; e += 32) {
         const double* pnt = ss + 5 * (int64_t)(off + e);
         const double x1 = pnt[0], x2 = pnt[1], y1 = pnt[2], y2 = pnt[3], wq = pnt[4] * JJ;
@@ -260,32 +266,48 @@ k_singular(const double* __restrict__ xyz, const int32_t* __restrict__ tri, cons
         kernel_values(CK, P, dx, dy, dz, Gr, Gi, Fr, Fi);
         const double dns = dx * ns0 + dy * ns1 + dz * ns2;
         const double dnt = -(dx * nt0 + dy * nt1 + dz * nt2);
+        float ch[9], cl[9];
+        {
+            float xh[3], xl[3], yh[3], yl[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                const double c = wq * Lx[a] * Ly[b];
-                const int e9 = 3 * a + b;
-                acc[e9] += c * Gr;
-                acc[9 + e9] += c * Gi;
-                acc[18 + e9] += c * dns * Fr;
-                acc[27 + e9] += c * dns * Fi;
-                acc[36 + e9] += c * dnt * Fr;
-                acc[45 + e9] += c * dnt * Fi;
+            for (int a = 0; a < 3; ++a) {
+                ddf::split(wq * Lx[a], xh[a], xl[a]);
+                ddf::split(Ly[a], yh[a], yl[a]);
             }
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {  // w_q L_a L_b as a double-float pair
+                    ch[3 * a + b] = __fmul_rn(xh[a], yh[b]);
+                    cl[3 * a + b] =
+                        fmaf(xl[a], yh[b], fmaf(xh[a], yl[b], fmaf(xh[a], yh[b], -ch[3 * a + b])));
+                }
+        }
+        const double kv[6] = {Gr, Gi, dns * Fr, dns * Fi, dnt * Fr, dnt * Fi};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            float kh, kl;
+            ddf::split(kv[k], kh, kl);
+#pragma unroll
+            for (int e9 = 0; e9 < 9; ++e9) ddf::mac(ah[9 * k + e9], ac[9 * k + e9], ch[e9], cl[e9], kh, kl);
         }
     }
 #pragma unroll
     for (int e = 0; e < 54; ++e)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+        for (int o = 16; o > 0; o >>= 1) {
+            const float qh = __shfl_xor_sync(0xffffffffu, ah[e], o), qc = __shfl_xor_sync(0xffffffffu, ac[e], o);
+            float t;
+            ddf::two_sum(ah[e], qh, ah[e], t);
+            ac[e] = __fadd_rn(ac[e], __fadd_rn(qc, t));
+        }
     // lanes 0..8 each write one (a, b) entry: stage the sums in shared memory so that
     // no register array is indexed by the lane number
     __shared__ double red[4][54];
     double* rw = red[(threadIdx.x >> 5) & 3];
     if (lane == 0) {
 #pragma unroll
-        for (int e = 0; e < 54; ++e) rw[e] = acc[e];
+        for (int e = 0; e < 54; ++e) rw[e] = ddf::widen(ah[e]) + ddf::widen(ac[e]);
     }
     __syncwarp();
     if (lane >= 9) return;
