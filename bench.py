@@ -822,7 +822,7 @@ def contract_line(*, value, steps, warmup, world, times, clocks, launches, err=N
         "ms_per_step": _r(sum(times) / len(times)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_SHORT, "parallelism": "replicas" if world > 1 else "single",
-                   "precision": "mixed: FP32 assembly/matvec (c64), FP64 singular/mass/mortar/refinement",
+                   "precision": "mixed: FP32 assembly/matvec (c64); FP64 or double-float singular/mass/mortar/refinement",
                    "l2": "inputs > L2 + 256 MB flush"},
         "latency_ms": {"p50": _r(float(np.percentile(times, 50))), "p99": _r(float(np.percentile(times, 99)))},
         "accuracy": (None if err is None else {"max": _r(max(err.values()), 3), "target": 1e-6,
