@@ -444,6 +444,7 @@ __global__ void k_mask_mass_ell(int32_t* __restrict__ ci, double* __restrict__ v
 struct MassPair {
     const int32_t* ci[2];
     const double *v[2], *dinv[2];
+    const float *vf[2] = {nullptr, nullptr}, *dinvf[2] = {nullptr, nullptr};  // FP32 copies (optional)
     int W[2];
     int64_t Ne, Ni, n;
 };
@@ -482,6 +483,12 @@ __device__ __forceinline__ double2 mass_apply_row(const MassRow& m, const double
     return md;
 }
 
+// FP32 copy of FP64 values
+__global__ void k_narrow(const double* __restrict__ a, int64_t n, float* __restrict__ b) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
 // ELL copy of one grid's mass CSR (one thread per row)
 __global__ void k_mass_ell(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                            const double* __restrict__ val, int64_t N, int W, int32_t* __restrict__ ci,
@@ -507,6 +514,56 @@ __global__ void k_cheb_init(MassPair M, const double2* __restrict__ z, double2* 
     y[off + g] = make_double2(0, 0);
     r[off + g] = zz;
     d[off + g] = make_double2(s * zz.x, s * zz.y);
+}
+
+// The same iteration in FP32 (the 17-step inverse of the inner solves that use FP32
+// products: its rounding, ~2e-7, matches theirs): r, d and the running sum y as float2
+// (y in the second half of the dA workspace), the result widened to FP64 by the last step.
+__global__ void k_cheb_init32(MassPair M, const double2* __restrict__ z, float2* __restrict__ r,
+                              float2* __restrict__ d, float inv_theta) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= M.n) return;
+    const int64_t off = blockIdx.y * M.n;
+    const MassRow m = mass_row(M, g);
+    const double2 zz = z[off + g];
+    const float2 rz = make_float2((float)zz.x, (float)zz.y);
+    const float sc = (m.base < 2 * M.Ne ? M.dinvf[0] : M.dinvf[1])[m.i] * inv_theta;
+    r[off + g] = rz;
+    d[off + g] = make_float2(sc * rz.x, sc * rz.y);
+}
+
+__global__ void k_cheb_step32(MassPair M, const float2* __restrict__ dk, float2* __restrict__ dn,
+                              float2* __restrict__ y, float2* __restrict__ r, float c1, float c2, int first,
+                              double2* __restrict__ yout) {
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= M.n) return;
+    const int64_t off = blockIdx.y * M.n;
+    const MassRow m = mass_row(M, g);
+    const bool ext = m.base < 2 * M.Ne;
+    const float* __restrict__ vf = ext ? M.vf[0] : M.vf[1];
+    const float2* __restrict__ d = dk + off + m.base;
+    float2 md = make_float2(0.f, 0.f);
+    for (int k = 0; k < m.W; ++k) {
+        const float v = vf[(int64_t)k * m.N + m.i];
+        const float2 dd = d[m.ci[(int64_t)k * m.N + m.i]];
+        md.x = fmaf(v, dd.x, md.x);
+        md.y = fmaf(v, dd.y, md.y);
+    }
+    const float2 d0 = dk[off + g];
+    float2 yy = d0;
+    if (!first) {
+        const float2 yp = y[off + g];
+        yy.x += yp.x;
+        yy.y += yp.y;
+    }
+    float2 rr = r[off + g];
+    rr.x -= md.x;
+    rr.y -= md.y;
+    if (yout) yout[off + g] = make_double2((double)yy.x, (double)yy.y);
+    else y[off + g] = yy;
+    r[off + g] = rr;
+    const float sc = c2 * (ext ? M.dinvf[0] : M.dinvf[1])[m.i];
+    dn[off + g] = make_float2(fmaf(c1, d0.x, sc * rr.x), fmaf(c1, d0.y, sc * rr.y));
 }
 
 // y += d_k; r -= M d_k; d_{k+1} = c1 d_k + c2 D^-1 r
@@ -794,7 +851,7 @@ __global__ void k_acc(double2* __restrict__ x, const double2* __restrict__ d, in
 // ------------------------------------------------------------------ host side
 // ELL form of one grid's mass matrix (values of this solve)
 struct MassEll {
-    DevBuf ci, v;
+    DevBuf ci, v, vf;  // vf: FP32 copy of the values (FP32 Chebyshev iterations)
     int W = 0;
     bem_status build(const bem_grid* g, const double* val, cudaStream_t s) {
         W = std::max(1, (int)g->m_maxrow);
@@ -802,6 +859,9 @@ struct MassEll {
         BEM_TRY(v.alloc((size_t)W * g->nv * 8, s));
         BEM_LAUNCH(k_mass_ell, blocks_for(g->nv, 128), 128, 0, s, g->m_rowptr.as<int32_t>(), g->m_col.as<int32_t>(),
                    val, g->nv, W, ci.as<int32_t>(), v.as<double>());
+        BEM_TRY(vf.alloc((size_t)W * g->nv * 4, s));
+        BEM_LAUNCH(k_narrow, blocks_for((int64_t)W * g->nv, 256), 256, 0, s, v.as<double>(), (int64_t)W * g->nv,
+                   vf.as<float>());
         return BEM_OK;
     }
 };
@@ -981,6 +1041,24 @@ bem_status mass_solve(const MassOp& op, const double2* z, double2* y, int R, cud
     // every SM
     const int nb = tune_get(TUNE_CHEB, R, n, TuneChoice{64, 0, 0.0}).block;
     const dim3 grid(blocks_for(n, nb), R);
+    if (steps == CHEB_STEPS_INNER && op.M.vf[0] && op.M.vf[1] && steps >= 1) {
+        // FP32 iteration: r in op.r, d in the first halves of dA / dB, y in the second half of dA
+        float2* r32 = reinterpret_cast<float2*>(op.r);
+        float2* da = reinterpret_cast<float2*>(op.dA);
+        float2* db = reinterpret_cast<float2*>(op.dB);
+        float2* y32 = da + (int64_t)R * n;
+        BEM_LAUNCH(k_cheb_init32, grid, nb, 0, s, op.M, z, r32, da, (float)(1.0 / theta));
+        double rho = 1.0 / sigma;
+        float2 *dk = da, *dn = db;
+        for (int k = 0; k < steps; ++k) {
+            const double rho_n = 1.0 / (2.0 * sigma - rho);
+            BEM_LAUNCH(k_cheb_step32, grid, nb, 0, s, op.M, dk, dn, y32, r32, (float)(rho_n * rho),
+                       (float)(2.0 * rho_n / delta), k == 0 ? 1 : 0, k == steps - 1 ? y : nullptr);
+            rho = rho_n;
+            std::swap(dk, dn);
+        }
+        return BEM_OK;
+    }
     BEM_LAUNCH(k_cheb_init, grid, nb, 0, s, op.M, z, y, op.r, op.dA, 1.0 / theta);
     double rho = 1.0 / sigma;
     double2 *dk = op.dA, *dn = op.dB;
@@ -1777,6 +1855,15 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     mop.M.dinv[0] = dve.as<double>();
     mop.M.ci[1] = ell_i.ci.as<int32_t>(); mop.M.v[1] = ell_i.v.as<double>(); mop.M.W[1] = ell_i.W;
     mop.M.dinv[1] = dvi.as<double>();
+    DevBuf dvef, dvif;  // FP32 copies for the FP32 inner mass inverses
+    if (mixed) {
+        BEM_TRY(dvef.alloc((size_t)Ne * 4, s));
+        BEM_TRY(dvif.alloc((size_t)Ni * 4, s));
+        BEM_LAUNCH(k_narrow, blocks_for(Ne, 256), 256, 0, s, dve.as<double>(), Ne, dvef.as<float>());
+        BEM_LAUNCH(k_narrow, blocks_for(Ni, 256), 256, 0, s, dvi.as<double>(), Ni, dvif.as<float>());
+        mop.M.vf[0] = ell_e.vf.as<float>(); mop.M.vf[1] = ell_i.vf.as<float>();
+        mop.M.dinvf[0] = dvef.as<float>(); mop.M.dinvf[1] = dvif.as<float>();
+    }
     // a MassPair with no rows on one grid is the mass inverse of the other grid alone
     // (vectors of its two potentials): single-trace systems use M_A^-1 (mop) and M_B^-1 (mopB)
     mop.M.Ne = st_int ? 0 : Ne; mop.M.Ni = st && !st_int ? 0 : Ni; mop.M.n = n;
