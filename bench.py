@@ -475,13 +475,13 @@ def run_batching(bem, ctx, precision, tensor_cores=2, batch_columns=0):
            "iterations_per_rhs_batched": rep["iterations"] / b["n_dirs"],
            "assembly_ms": rep["t_assembly_ms"],
            "kernels": [{"name": p[0], "ms": p[1], "launches": p[2]} for p in prof[:8]]}
-    tc = [p for p in prof if p[0] in ("k_gemm_tc", "k_gemm_tc16")]
+    tc = [p for p in prof if p[0] == "k_gemm_tc" or p[0].startswith("k_gemm_tc16")]
     if tc:
         name, ms, nl = tc[0]
         N = len(ve)  # both grids have the same level here
         rp = (b["n_dirs"] + 7) // 8 * 8 if batch_columns == 0 else (batch_columns + 7) // 8 * 8
         flops = 96.0 * rp * (N * N + len(vi) * len(vi))  # 3 split terms x 2 flops x K 4N x N_b x 2 RP, 4 block rows
-        if name == "k_gemm_tc16":
+        if name.startswith("k_gemm_tc16"):
             peak, kind = fp16_peak()
             kp = lambda n: (4 * n + 63) // 64 * 64
             nbytes = 2 * (N * kp(N) + len(vi) * kp(len(vi))) * 4  # hi + lo halves, padded rows, 4 block rows
@@ -1215,10 +1215,11 @@ def main():
                         f"k_ext={bw['k_ext']}, k_int={bw['k_int']}, rho={bw['rho']}, {bw['n_dirs']} plane "
                         f"waves in one call vs {bw['n_single']} of them one call each; mixed precision "
                         "with tensor-core products (one batch of 64; FP16 two-term split fed by TMA "
-                        "bulk copies, the default, and TF32 three-term split) and with CUDA-core "
-                        "products (batches of 8), FP64 (batches of 8)",
+                        "bulk copies, the default; TF32 three-term split; BF16 two-term split) and with "
+                        "CUDA-core products (batches of 8), FP64 (batches of 8)",
             "mixed_tensor_cores_fp16_split": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 2, 0),
             "mixed_tensor_cores_tf32_split": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 1, 0),
+            "mixed_tensor_cores_bf16_split": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 3, 0),
             "mixed_cuda_cores_8": run_batching(bem, ctx, bem.BEM_PREC_MIXED, 0, 8),
             "fp64": run_batching(bem, ctx, bem.BEM_PREC_FP64)})
         emit_section("batching_full", run_batching_full(bem, ctx))

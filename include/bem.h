@@ -269,8 +269,10 @@ typedef struct {
     int32_t tensor_cores;     /* BEM_PREC_MIXED batches of more than 8 right-hand sides: 2 (default)
                                  = products on the tcgen05 tensor cores with an FP16 two-term
                                  split of both operands (pre-tiled operator copy read by TMA bulk
-                                 copies, FP32 accumulation), 1 = tensor cores with a TF32
-                                 three-term split, 0 = FP32 CUDA cores in groups of 8 columns      */
+                                 copies, FP32 accumulation), 3 = the same with a BF16 two-term
+                                 split (8 + 8 bits: products to ~2e-5, more refinement), 1 =
+                                 tensor cores with a TF32 three-term split, 0 = FP32 CUDA cores in
+                                 groups of 8 columns                                               */
     int32_t formulation;      /* BEM_FORM_* (default BEM_FORM_MTF); the single-trace and
                                  high-contrast systems are available in bem_solve_transmission
                                  only (bem_solve_many and the server solve the multiple-traces
@@ -538,7 +540,8 @@ BEM_API uint64_t bem_launch_count(void);
  * vertices): 4 FP32 on complex64, 1 column; 5 the same, 5 columns; 6 double-float on
  * complex64, 1 column; 7 the same, 3 columns; 8 double-float on complex128, 1 column;
  * 9 the same, 8 columns.  which = 10, 11: as 1, for the TMA-fed tensor-core product
- * with the FP16 two-term split of both operands, 24 and 128 columns. */
+ * with the FP16 two-term split of both operands, 24 and 128 columns; 12: the same
+ * with the BF16 two-term split, 24 columns. */
 BEM_API bem_status bem_selftest(bem_context* ctx, int which, double* result);
 
 /* Per-kernel device timing.  While enabled, each launch of the library is

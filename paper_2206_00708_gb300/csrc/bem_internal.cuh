@@ -364,7 +364,7 @@ bem_status mtf_product_tc(const float2* const a1[4], const float2* const a2[4], 
                           const double c2[4], const int64_t N[4], const int64_t base[4], const int64_t x1[4],
                           const int64_t x2[4], int64_t n, int R, const double2* x, double2* z, void* work,
                           size_t work_bytes, int* err, cudaStream_t s);
-bem_status selftest_tc(int R, double* rel_err, cudaStream_t s, bool fp16 = false);
+bem_status selftest_tc(int R, double* rel_err, cudaStream_t s, int kind = 1);  // 1 TF32, 2 FP16, 3 BF16
 
 // FP16-split tensor-core product fed by TMA (gemm_tc16.cu): the operator copy of the
 // four block rows ([A1 | A2] rows as FP16 hi / lo parts, scaled by 2^eA, padded to Kp)
@@ -372,9 +372,10 @@ struct Tc16Ops {
     DevBuf hi[4], lo[4];
     int64_t N[4] = {0, 0, 0, 0}, Kp[4] = {0, 0, 0, 0};
     int eA[4] = {0, 0, 0, 0};
+    bool bf16 = false;  // BF16 parts instead of FP16
 };
 bem_status tc16_build(const float2* const a1[4], const float2* const a2[4], const int64_t N[4], Tc16Ops& out,
-                      cudaStream_t s);
+                      cudaStream_t s, bool bf16 = false);
 size_t tc16_workspace_bytes(const int64_t N[4], int RP);
 bem_status mtf_product_tc16(const Tc16Ops& ops, const double c1[4], const double c2[4], const int64_t base[4],
                             const int64_t x1[4], const int64_t x2[4], int64_t n, int R, const double2* x,

@@ -108,10 +108,11 @@ uint64_t bem_launch_count(void) { return g_launches.load(std::memory_order_relax
 bem_status bem_selftest(bem_context* ctx, int which, double* result) {
     CTX_GUARD(ctx);
     BEM_REQUIRE(result != nullptr, "null result");
-    BEM_REQUIRE(which >= 0 && which <= 11, "unknown self-test");
+    BEM_REQUIRE(which >= 0 && which <= 12, "unknown self-test");
     if (which == 0) return selftest_sincos(1 << 20, 64.0f, result, ctx->stream);
     if (which == 3) return selftest_barrier(result, ctx->stream);
-    if (which >= 10) return selftest_tc(which == 10 ? 24 : 128, result, ctx->stream, true);
+    if (which == 12) return selftest_tc(24, result, ctx->stream, 3);
+    if (which >= 10) return selftest_tc(which == 10 ? 24 : 128, result, ctx->stream, 2);
     if (which >= 4) {
         // tile products: (arithmetic, storage bytes, columns)
         const int cfg[6][3] = {{TP_F32, 8, 1}, {TP_F32, 8, 5}, {TP_DD, 8, 1}, {TP_DD, 8, 3}, {TP_DD, 16, 1},
@@ -119,7 +120,7 @@ bem_status bem_selftest(bem_context* ctx, int which, double* result) {
         const int* c = cfg[which - 4];
         return selftest_tile(c[0], c[1], c[2], result, ctx->stream);
     }
-    return selftest_tc(which == 1 ? 24 : 8, result, ctx->stream);
+    return selftest_tc(which == 1 ? 24 : 8, result, ctx->stream, 1);
 }
 
 bem_status bem_context_create(int device, void* stream, bem_context** out) {
@@ -420,7 +421,7 @@ bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const b
     BEM_REQUIRE(o.precision == BEM_PREC_FP64 || o.precision == BEM_PREC_MIXED, "unsupported precision");
     BEM_REQUIRE(o.ir_inner_tol > 0.0 && o.ir_inner_tol < 1.0, "ir_inner_tol must be in (0, 1)");
     BEM_REQUIRE(o.batch_columns >= 0 && o.batch_columns <= 128, "batch_columns must be in [0, 128]");
-    BEM_REQUIRE(o.tensor_cores >= 0 && o.tensor_cores <= 2, "tensor_cores must be 0, 1 or 2");
+    BEM_REQUIRE(o.tensor_cores >= 0 && o.tensor_cores <= 3, "tensor_cores must be 0, 1, 2 or 3");
     BEM_REQUIRE(o.formulation >= BEM_FORM_MTF && o.formulation <= BEM_FORM_HC_INT_DIR, "unknown formulation");
     BEM_REQUIRE(o.cuda_graphs == 0 || o.cuda_graphs == 1, "cuda_graphs must be 0 or 1");
     BEM_REQUIRE(o.dd_switch >= 0.0 && o.dd_switch <= 1.0, "dd_switch must be in [0, 1]");

@@ -1,7 +1,8 @@
-// Multi-column MTF products on the tcgen05 tensor cores with an FP16 two-term split of
-// both operands, fed by TMA: the split-complex tensor-core variant of the
+// Multi-column MTF products on the tcgen05 tensor cores with an FP16 (or BF16) two-term
+// split of both operands, fed by TMA: the split-complex tensor-core variants of the
 // mixed-precision mode (paper eq. mtf:discrete; the dense products are the a9 step of
-// the solve, Sec. 3.3 / Sec. 5.1).
+// the solve, Sec. 3.3 / Sec. 5.1).  BF16 keeps 8 + 8 significant bits per operand
+// (products to ~2^-16) against FP16's 11 + 11 (~2^-22), in the same kernel.
 //
 // A block row b of the MTF is z_b = c1 A1 x1 + c2 A2 x2 with complex64 N_b x N_b
 // matrices A.  As in the TF32 product, one row of [A1 | A2] read as interleaved
@@ -38,6 +39,7 @@
 // and the CTA still drains its copies and frees its TMEM.
 #include "bem_internal.cuh"
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -48,6 +50,21 @@
 namespace bem {
 
 namespace {
+
+// the 16-bit operand type: FP16 (11 significant bits, range handled by the scaling) or
+// BF16 (8 significant bits, FP32's range); its tcgen05 instruction-descriptor format code
+struct F16 {
+    __device__ static uint16_t from(float x) { return __half_as_ushort(__float2half_rn(x)); }
+    __device__ static float to(uint16_t b) { return __half2float(__ushort_as_half(b)); }
+    static constexpr uint32_t FMT = 0;
+};
+struct BF16 {
+    __device__ static uint16_t from(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+    __device__ static float to(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+    static constexpr uint32_t FMT = 1;
+};
+// a 16-bit pair (low half first in memory)
+__device__ __forceinline__ uint32_t pack16(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
 
 constexpr int T16_THREADS = 192;
 constexpr int T16_M = 128;                    // rows per CTA (MMA M)
@@ -68,9 +85,10 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
     return start | (lbo << 16) | (sbo << 32) | (1ull << 46) | (2ull << 61);
 }
 
-// instruction descriptor: D = F32, A = B = F16, both K-major, N = n, M = 128
-__device__ __forceinline__ uint32_t f16_idesc(int n) {
-    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(T16_M >> 4) << 24);
+// instruction descriptor: D = F32, A = B = F16 (fmt 0) or BF16 (fmt 1), both K-major,
+// N = n, M = 128
+__device__ __forceinline__ uint32_t f16_idesc(int n, uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(T16_M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, int accumulate) {
@@ -176,6 +194,7 @@ __global__ void k_t16_absmax(const float* __restrict__ a, int64_t count, int* __
     if ((threadIdx.x & 31) == 0) max_bits(out, m);
 }
 
+template <class TR>
 __global__ void k_t16_split_ops(const float* __restrict__ a1, const float* __restrict__ a2, int64_t N, int64_t Kp,
                                 float scale, __half* __restrict__ hi, __half* __restrict__ lo) {
     const int64_t total = N * (2 * N);  // complex entries of the row [A1 | A2]
@@ -186,12 +205,12 @@ __global__ void k_t16_split_ops(const float* __restrict__ a1, const float* __res
                          : *reinterpret_cast<const float2*>(a2 + row * 2 * N + 2 * (j - N));
         v.x *= scale;
         v.y *= scale;
-        const __half hx = __float2half_rn(v.x), hy = __float2half_rn(v.y);
-        const __half lx = __float2half_rn(v.x - __half2float(hx)), ly = __float2half_rn(v.y - __half2float(hy));
+        const uint16_t hx = TR::from(v.x), hy = TR::from(v.y);
+        const uint16_t lx = TR::from(v.x - TR::to(hx)), ly = TR::from(v.y - TR::to(hy));
         const int64_t k = 2 * j, tile = row / T16_M, st = k / T16_KS;
         const int64_t off = (tile * stages + st) * (T16_M * T16_KS) + swz((int)(row % T16_M), (int)(k % T16_KS));
-        *reinterpret_cast<__half2*>(hi + off) = __halves2half2(hx, hy);
-        *reinterpret_cast<__half2*>(lo + off) = __halves2half2(lx, ly);
+        *reinterpret_cast<uint32_t*>(hi + off) = pack16(hx, hy);
+        *reinterpret_cast<uint32_t*>(lo + off) = pack16(lx, ly);
     }
 }
 
@@ -228,6 +247,7 @@ __global__ void k_t16_scales(T16Prep P, const int* __restrict__ xmax, int* __res
     eB[b * P.RP + r] = e;
 }
 
+template <class TR>
 __global__ void k_t16_prep(T16Prep P, const double2* __restrict__ x, const int* __restrict__ eB) {
     const int b = blockIdx.z, r = blockIdx.y;
     if (r >= P.R) return;
@@ -242,19 +262,21 @@ __global__ void k_t16_prep(T16Prep P, const double2* __restrict__ x, const int* 
         const double2 xv = x[(int64_t)r * P.n + (second ? P.x2[b] + (j - N) : P.x1[b] + j)];
         const float re = (float)(c * xv.x) * s, im = (float)(c * xv.y) * s;
         // real row: (re, -im); imaginary row: (im, re)
-        const __half h_re = __float2half_rn(re), h_im = __float2half_rn(im);
-        const __half l_re = __float2half_rn(re - __half2float(h_re)), l_im = __float2half_rn(im - __half2float(h_im));
+        const uint16_t h_re = TR::from(re), h_im = TR::from(im);
+        const uint16_t l_re = TR::from(re - TR::to(h_re)), l_im = TR::from(im - TR::to(h_im));
+        const uint16_t nh_im = h_im ^ 0x8000u, nl_im = l_im ^ 0x8000u;  // sign flips (both formats)
         const int64_t k = 2 * j, st = k / T16_KS;
         const int kk = (int)(k % T16_KS);
         const int64_t tbase = st * (int64_t)nb * T16_KS;
         const int64_t ore = tbase + swz(r, kk), oim = tbase + swz(P.RP + r, kk);
-        *reinterpret_cast<__half2*>(bh + ore) = __halves2half2(h_re, __hneg(h_im));
-        *reinterpret_cast<__half2*>(bl + ore) = __halves2half2(l_re, __hneg(l_im));
-        *reinterpret_cast<__half2*>(bh + oim) = __halves2half2(h_im, h_re);
-        *reinterpret_cast<__half2*>(bl + oim) = __halves2half2(l_im, l_re);
+        *reinterpret_cast<uint32_t*>(bh + ore) = pack16(h_re, nh_im);
+        *reinterpret_cast<uint32_t*>(bl + ore) = pack16(l_re, nl_im);
+        *reinterpret_cast<uint32_t*>(bh + oim) = pack16(h_im, h_re);
+        *reinterpret_cast<uint32_t*>(bl + oim) = pack16(l_im, l_re);
     }
 }
 
+template <class TR>
 __global__ void __launch_bounds__(T16_THREADS, 1) k_gemm_tc16(const T16Args P,
                                                                double* __restrict__ z, int* __restrict__ err) {
     extern __shared__ unsigned char t16_raw[];
@@ -329,7 +351,7 @@ __global__ void __launch_bounds__(T16_THREADS, 1) k_gemm_tc16(const T16Args P,
             if (!bar_wait(smem_addr(&full[t % NS]), (uint32_t)((t / NS) & 1))) s_fail = 1;
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issue
-        const uint32_t idesc = f16_idesc(nb);
+        const uint32_t idesc = f16_idesc(nb, TR::FMT);
         for (int ls = 0; ls < S; ++ls) {
             const int buf = ls % NS;
             if (!bar_wait(smem_addr(&full[buf]), (uint32_t)((ls / NS) & 1))) {
@@ -413,7 +435,8 @@ int64_t padded_k(int64_t N) { return (4 * N + T16_KS - 1) / T16_KS * T16_KS; }
 }  // namespace
 
 bem_status tc16_build(const float2* const a1[4], const float2* const a2[4], const int64_t N[4], Tc16Ops& out,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool bf16) {
+    out.bf16 = bf16;
     DevBuf mx;
     BEM_TRY(mx.alloc(4 * sizeof(int), s));
     BEM_CUDA_TRY(cudaMemsetAsync(mx.p, 0, 4 * sizeof(int), s));
@@ -439,9 +462,14 @@ bem_status tc16_build(const float2* const a1[4], const float2* const a2[4], cons
         BEM_TRY(out.lo[b].alloc(bytes, s));
         BEM_CUDA_TRY(cudaMemsetAsync(out.hi[b].p, 0, bytes, s));
         BEM_CUDA_TRY(cudaMemsetAsync(out.lo[b].p, 0, bytes, s));
-        BEM_LAUNCH(k_t16_split_ops, 152 * 8, 256, 0, s, reinterpret_cast<const float*>(a1[b]),
-                   reinterpret_cast<const float*>(a2[b]), N[b], out.Kp[b], ldexpf(1.0f, out.eA[b]),
-                   out.hi[b].as<__half>(), out.lo[b].as<__half>());
+        if (out.bf16)
+            BEM_LAUNCH(k_t16_split_ops<BF16>, 152 * 8, 256, 0, s, reinterpret_cast<const float*>(a1[b]),
+                       reinterpret_cast<const float*>(a2[b]), N[b], out.Kp[b], ldexpf(1.0f, out.eA[b]),
+                       out.hi[b].as<__half>(), out.lo[b].as<__half>());
+        else
+            BEM_LAUNCH(k_t16_split_ops<F16>, 152 * 8, 256, 0, s, reinterpret_cast<const float*>(a1[b]),
+                       reinterpret_cast<const float*>(a2[b]), N[b], out.Kp[b], ldexpf(1.0f, out.eA[b]),
+                       out.hi[b].as<__half>(), out.lo[b].as<__half>());
     }
     return BEM_OK;
 }
@@ -513,8 +541,9 @@ bem_status mtf_product_tc16(const Tc16Ops& ops, const double c1[4], const double
     BEM_LAUNCH(k_t16_scales, 4, 128, 0, s, pp, xmax, eB);
     int64_t nmax = 0;
     for (int b = 0; b < 4; ++b) nmax = std::max(nmax, ops.N[b]);
-    BEM_LAUNCH(k_t16_prep, dim3((unsigned)std::min<int64_t>(64, (2 * nmax + 255) / 256), R, 4), 256, 0, s, pp, x,
-               eB);
+    const dim3 pgrid((unsigned)std::min<int64_t>(64, (2 * nmax + 255) / 256), R, 4);
+    if (ops.bf16) BEM_LAUNCH(k_t16_prep<BF16>, pgrid, 256, 0, s, pp, x, eB);
+    else BEM_LAUNCH(k_t16_prep<F16>, pgrid, 256, 0, s, pp, x, eB);
     // K split: the wave efficiency of tiles * ksplit CTAs (one per SM) over 1..8
     int sms = 0, dev = 0;
     BEM_CUDA_TRY(cudaGetDevice(&dev));
@@ -534,9 +563,16 @@ bem_status mtf_product_tc16(const Tc16Ops& ops, const double c1[4], const double
     const int stage_bytes = 2 * T16_A_PART + 2 * nb * T16_KS * 2;
     const int NS = stage_bytes <= 48 * 1024 ? 4 : stage_bytes <= 64 * 1024 ? 3 : 2;
     const int smem = NS * stage_bytes + 1024;
-    BEM_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc16, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     if (ksplit > 1) BEM_CUDA_TRY(cudaMemsetAsync(z, 0, (size_t)R * n * sizeof(double2), s));
-    BEM_LAUNCH(k_gemm_tc16, dim3(tiles, ksplit), T16_THREADS, smem, s, A, reinterpret_cast<double*>(z), err);
+    if (ops.bf16) {
+        BEM_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc16<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        BEM_LAUNCH(k_gemm_tc16<BF16>, dim3(tiles, ksplit), T16_THREADS, smem, s, A, reinterpret_cast<double*>(z),
+                   err);
+    } else {
+        BEM_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc16<F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        BEM_LAUNCH(k_gemm_tc16<F16>, dim3(tiles, ksplit), T16_THREADS, smem, s, A, reinterpret_cast<double*>(z),
+                   err);
+    }
     return BEM_OK;
 }
 

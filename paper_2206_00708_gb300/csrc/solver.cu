@@ -1514,7 +1514,8 @@ bem_status selftest_barrier(double* result, cudaStream_t s) {
     return BEM_OK;
 }
 
-bem_status selftest_tc(int R, double* rel_err, cudaStream_t s, bool fp16) {
+bem_status selftest_tc(int R, double* rel_err, cudaStream_t s, int kind) {
+    const bool fp16 = kind >= 2;
     const int64_t Ne = 300, Ni = 170, n = 2 * Ne + 2 * Ni;
     const int RW = R + 7;
     DevBuf tl[2][3], dn[2][4], xf, x, z1, z2, work, err, part, tperr;
@@ -1535,7 +1536,7 @@ bem_status selftest_tc(int R, double* rel_err, cudaStream_t s, bool fp16) {
     BEM_CUDA_TRY(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     Tc16Ops t16;
     if (fp16) {
-        BEM_TRY(tc16_build(B.A1, B.A2, B.rows, t16, s));
+        BEM_TRY(tc16_build(B.A1, B.A2, B.rows, t16, s, kind == 3));
         BEM_TRY(work.alloc(tc16_workspace_bytes(B.rows, tc_padded_columns(R)), s));
         BEM_TRY(mtf_product_tc16(t16, B.c1, B.c2, B.base, B.x1, B.x2, n, R, x.as<double2>(), z1.as<double2>(),
                                  work.p, work.bytes, err.as<int>(), s));
@@ -1980,7 +1981,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     // tensor-core batches read dense row-major blocks: dense copies of the operators
     DevBuf dense[8];  // Ve, Ke, Te, De, Vi, Ki, Ti, Di
     Blocks<float2> B32{}, Bh32{};
-    const bool tc16 = o->tensor_cores == 2;  // FP16 two-term split, TMA-fed
+    const bool tc16 = o->tensor_cores >= 2;  // FP16 (2) or BF16 (3) two-term split, TMA-fed
     Tc16Ops t16, t16h;                       // its operator copies of B32 and Bh32
     if (mixed) {
         BEM_TRY(x32.alloc((size_t)RW * n * 8, s));
@@ -2000,8 +2001,8 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
             const int RP = tc_padded_columns(RB);
             if (tc16) {
                 // the split copies replace the dense complex64 copies
-                BEM_TRY(tc16_build(B32.A1, B32.A2, B32.rows, t16, s));
-                if (st) BEM_TRY(tc16_build(Bh32.A1, Bh32.A2, Bh32.rows, t16h, s));
+                BEM_TRY(tc16_build(B32.A1, B32.A2, B32.rows, t16, s, o->tensor_cores == 3));
+                if (st) BEM_TRY(tc16_build(Bh32.A1, Bh32.A2, Bh32.rows, t16h, s, o->tensor_cores == 3));
                 for (DevBuf& d : dense) d.release();  // stream-ordered: after the split kernels
                 BEM_TRY(tcw.alloc(std::max(tc16_workspace_bytes(B32.rows, RP),
                                            st ? tc16_workspace_bytes(Bh32.rows, RP) : 0),
