@@ -67,11 +67,11 @@ typedef struct bem_sparse  bem_sparse;
 #define BEM_OP_D 3   /* hypersingular (with the paper's minus sign), Maue's weak form     */
 
 /* Arithmetic of assembly and matvec. */
-#define BEM_PREC_FP64   0   /* FP64 operators and vectors; the kernel values of the assembly
-                               in FP64; the products, the Arnoldi inner products and basis
-                               updates and the singular-pair sums in double-float arithmetic
-                               (pairs of FP32 values, 48 significant bits) on the FP32 pipe,
-                               which on GB300 is 64 times the FP64 rate                       */
+#define BEM_PREC_FP64   0   /* FP64 operators and vectors; the geometry and kernel values of
+                               the assembly in FP64; the quadrature sums of the assembly, the
+                               products and the Arnoldi inner products and basis updates in
+                               double-float arithmetic (pairs of FP32 values, 48 significant
+                               bits) on the FP32 pipe, which on GB300 is 64 times the FP64 rate */
 #define BEM_PREC_MIXED  1   /* regular pairs assembled in FP32 into complex64 operators;
                                singular pairs (as in FP64 mode), mass and mortar in FP64;
                                solve: GMRES with an FP32 matvec inside iterative refinement

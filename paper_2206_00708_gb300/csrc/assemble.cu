@@ -42,9 +42,15 @@ struct KParams {
 struct TrialTile {
     double q[6][3][TB];
     double wl[6][3][TB];
+    float wlh[6][3][TB], wll[6][3][TB];  // the weights split into FP32 pairs (double-float sums)
     double n[3][TB];
     double curl[3][3][TB];
     int32_t v[3][TB];
+};
+
+// double-float accumulator: value h plus collected error c
+struct DDAcc {
+    float h, c;
 };
 
 __device__ __forceinline__ void kernel_values(bool complex_k, const KParams& P, double dx, double dy, double dz,
@@ -116,6 +122,11 @@ k_regular(const TriRec* __restrict__ rec, const int32_t* __restrict__ tri, int64
         }
     }
     __syncthreads();
+    for (int e = threadIdx.x; e < TB * 18; e += NTHREADS) {
+        const int s = e % TB, f = e / TB;
+        ddf::split(trial.wl[f / 3][f % 3][s], trial.wlh[f / 3][f % 3][s], trial.wll[f / 3][f % 3][s]);
+    }
+    __syncthreads();
     for (int pidx = threadIdx.x; pidx < TB * TB; pidx += NTHREADS) {
         const int tl = pidx / TB, sl = pidx % TB;
         if (t0 + tl >= nt || s0 + sl >= nt) continue;
@@ -128,11 +139,24 @@ k_regular(const TriRec* __restrict__ rec, const int32_t* __restrict__ tri, int64
         const TriRec& tr = test[tl];
         const double nsx = trial.n[0][sl], nsy = trial.n[1][sl], nsz = trial.n[2][sl];
         const double ntx = tr.n[0], nty = tr.n[1], ntz = tr.n[2];
-        double Vr[3][3] = {}, Vi[3][3] = {}, Kr[3][3] = {}, Ki[3][3] = {}, Tr[3][3] = {}, Ti[3][3] = {};
+        // sums over the 36 point pairs in double-float on the FP32 pipe (the kernel values are
+        // FP64): GB300's FP64 pipe, 1/64 of the FP32 rate, keeps only the geometry and the
+        // kernel evaluation.  A[0..5][a][b] = V re, V im, K re, K im, T re, T im
+        DDAcc A[6][3][3];
+#pragma unroll
+        for (int o = 0; o < 6; ++o)
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) A[o][a][b] = DDAcc{0.f, 0.f};
 #pragma unroll 1
         for (int p = 0; p < 6; ++p) {
             const double xx = tr.q[p][0], xy = tr.q[p][1], xz = tr.q[p][2];
-            double SVr[3] = {}, SVi[3] = {}, SKr[3] = {}, SKi[3] = {}, STr[3] = {}, STi[3] = {};
+            DDAcc S[6][3];
+#pragma unroll
+            for (int o = 0; o < 6; ++o)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) S[o][b] = DDAcc{0.f, 0.f};
 #pragma unroll 2
             for (int q = 0; q < 6; ++q) {
                 const double dx = xx - trial.q[q][0][sl], dy = xy - trial.q[q][1][sl], dz = xz - trial.q[q][2][sl];
@@ -140,32 +164,51 @@ k_regular(const TriRec* __restrict__ rec, const int32_t* __restrict__ tri, int64
                 kernel_values(CK, P, dx, dy, dz, Gr, Gi, Fr, Fi);
                 const double dns = dx * nsx + dy * nsy + dz * nsz;
                 const double dnt = -(dx * ntx + dy * nty + dz * ntz);
+                float grh, grl, gih, gil, frh, frl, fih, fil, nsh, nsl, nth, ntl;
+                ddf::split(Gr, grh, grl);
+                ddf::split(Gi, gih, gil);
+                ddf::split(Fr, frh, frl);
+                ddf::split(Fi, fih, fil);
+                ddf::split(dns, nsh, nsl);
+                ddf::split(dnt, nth, ntl);
 #pragma unroll
                 for (int b = 0; b < 3; ++b) {
-                    const double wl = trial.wl[q][b][sl];
-                    SVr[b] += wl * Gr;
-                    SVi[b] += wl * Gi;
-                    const double cs = wl * dns, ct = wl * dnt;
-                    SKr[b] += cs * Fr;
-                    SKi[b] += cs * Fi;
-                    STr[b] += ct * Fr;
-                    STi[b] += ct * Fi;
+                    const float wh = trial.wlh[q][b][sl], wlo = trial.wll[q][b][sl];
+                    ddf::mac(S[0][b].h, S[0][b].c, wh, wlo, grh, grl);
+                    ddf::mac(S[1][b].h, S[1][b].c, wh, wlo, gih, gil);
+                    // w (x - y).n as a double-float pair, times F
+                    const float csh = __fmul_rn(wh, nsh);
+                    const float csl = fmaf(wlo, nsh, fmaf(wh, nsl, fmaf(wh, nsh, -csh)));
+                    const float cth = __fmul_rn(wh, nth);
+                    const float ctl = fmaf(wlo, nth, fmaf(wh, ntl, fmaf(wh, nth, -cth)));
+                    ddf::mac(S[2][b].h, S[2][b].c, csh, csl, frh, frl);
+                    ddf::mac(S[3][b].h, S[3][b].c, csh, csl, fih, fil);
+                    ddf::mac(S[4][b].h, S[4][b].c, cth, ctl, frh, frl);
+                    ddf::mac(S[5][b].h, S[5][b].c, cth, ctl, fih, fil);
                 }
             }
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const double wl = tr.wl[p][a];
+                float wh, wlo;
+                ddf::split(tr.wl[p][a], wh, wlo);
 #pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    Vr[a][b] += wl * SVr[b];
-                    Vi[a][b] += wl * SVi[b];
-                    Kr[a][b] += wl * SKr[b];
-                    Ki[a][b] += wl * SKi[b];
-                    Tr[a][b] += wl * STr[b];
-                    Ti[a][b] += wl * STi[b];
-                }
+                for (int o = 0; o < 6; ++o)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) ddf::mac(A[o][a][b].h, A[o][a][b].c, wh, wlo, S[o][b].h, S[o][b].c);
             }
         }
+        double Vr[3][3], Vi[3][3], Kr[3][3], Ki[3][3], Tr[3][3], Ti[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                Vr[a][b] = ddf::widen(A[0][a][b].h) + ddf::widen(A[0][a][b].c);
+                Vi[a][b] = ddf::widen(A[1][a][b].h) + ddf::widen(A[1][a][b].c);
+                Kr[a][b] = ddf::widen(A[2][a][b].h) + ddf::widen(A[2][a][b].c);
+                Ki[a][b] = ddf::widen(A[3][a][b].h) + ddf::widen(A[3][a][b].c);
+                Tr[a][b] = ddf::widen(A[4][a][b].h) + ddf::widen(A[4][a][b].c);
+                Ti[a][b] = ddf::widen(A[5][a][b].h) + ddf::widen(A[5][a][b].c);
+            }
         double I0r = 0, I0i = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
