@@ -2435,6 +2435,56 @@ __global__ void k_cheb_step_many(const InstDesc* __restrict__ D, const int32_t* 
     dn[gw] = make_double2(c1 * d0.x + sc * rr.x, c1 * d0.y + sc * rr.y);
 }
 
+// the FP32 iteration of k_cheb_init32 / k_cheb_step32 over the concatenation
+__global__ void k_cheb_init32_many(const InstDesc* __restrict__ D, const int32_t* __restrict__ row_inst,
+                                   int64_t total, const double2* __restrict__ z, float2* __restrict__ r,
+                                   float2* __restrict__ d0, float inv_theta) {
+    const int64_t gw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gw >= total) return;
+    const InstDesc& d = D[row_inst[gw]];
+    const MassRow m = mass_row(d.M, gw - d.off);
+    const double2 zz = z[gw];
+    const float2 rz = make_float2((float)zz.x, (float)zz.y);
+    const float sc = (m.base < 2 * d.M.Ne ? d.M.dinvf[0] : d.M.dinvf[1])[m.i] * inv_theta;
+    r[gw] = rz;
+    d0[gw] = make_float2(sc * rz.x, sc * rz.y);
+}
+
+__global__ void k_cheb_step32_many(const InstDesc* __restrict__ D, const int32_t* __restrict__ row_inst,
+                                   int64_t total, const float2* __restrict__ dk, float2* __restrict__ dn,
+                                   float2* __restrict__ y, float2* __restrict__ r, float c1, float c2, int first,
+                                   double2* __restrict__ yout) {
+    const int64_t gw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gw >= total) return;
+    const InstDesc& d = D[row_inst[gw]];
+    const MassRow m = mass_row(d.M, gw - d.off);
+    const bool ext = m.base < 2 * d.M.Ne;
+    const float* __restrict__ vf = ext ? d.M.vf[0] : d.M.vf[1];
+    const float2* __restrict__ dd = dk + d.off + m.base;
+    float2 md = make_float2(0.f, 0.f);
+    for (int k = 0; k < m.W; ++k) {
+        const float v = vf[(int64_t)k * m.N + m.i];
+        const float2 x = dd[m.ci[(int64_t)k * m.N + m.i]];
+        md.x = fmaf(v, x.x, md.x);
+        md.y = fmaf(v, x.y, md.y);
+    }
+    const float2 d0 = dk[gw];
+    float2 yy = d0;
+    if (!first) {
+        const float2 yp = y[gw];
+        yy.x += yp.x;
+        yy.y += yp.y;
+    }
+    float2 rr = r[gw];
+    rr.x -= md.x;
+    rr.y -= md.y;
+    if (yout) yout[gw] = make_double2((double)yy.x, (double)yy.y);
+    else y[gw] = yy;
+    r[gw] = rr;
+    const float sc = c2 * (ext ? d.M.dinvf[0] : d.M.dinvf[1])[m.i];
+    dn[gw] = make_float2(fmaf(c1, d0.x, sc * rr.x), fmaf(c1, d0.y, sc * rr.y));
+}
+
 // inner products over chunks that never straddle two instances: chunk c covers
 // rows [cs[c], ce[c]) of instance ci[c]; partial[i * nchunks + c]
 __global__ void __launch_bounds__(256) k_dots_partial_many(const double2* __restrict__ Vb, int64_t total, int m,
@@ -2698,7 +2748,7 @@ bem_status gmres_run_many(const ManyLayout& L, ManyGmres& W, const ApplyMany& ap
 // the instances that differ only in their wave or density ratio (owned buffers)
 struct ProblemData {
     GridOps ops[2];  // exterior, interior
-    DevBuf mve, mvi, dve, dvi, prow, pcol, pval;
+    DevBuf mve, mvi, dve, dvi, dvef, dvif, prow, pcol, pval;
     CsrBuf csr_p, csr_t;
     MassEll ell_e, ell_i;
 };
@@ -2803,11 +2853,17 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
         if (first[prob[i]] == i) {
             BEM_TRY(d.ell_e.build(inst[i].ext, d.mve.as<double>(), s));
             BEM_TRY(d.ell_i.build(inst[i].intr, d.mvi.as<double>(), s));
+            BEM_TRY(d.dvef.alloc((size_t)Ne * 4, s));
+            BEM_TRY(d.dvif.alloc((size_t)Ni * 4, s));
+            BEM_LAUNCH(k_narrow, blocks_for(Ne, 256), 256, 0, s, d.dve.as<double>(), Ne, d.dvef.as<float>());
+            BEM_LAUNCH(k_narrow, blocks_for(Ni, 256), 256, 0, s, d.dvi.as<double>(), Ni, d.dvif.as<float>());
         }
         D.M.ci[0] = d.ell_e.ci.as<int32_t>(); D.M.v[0] = d.ell_e.v.as<double>(); D.M.W[0] = d.ell_e.W;
         D.M.dinv[0] = d.dve.as<double>();
         D.M.ci[1] = d.ell_i.ci.as<int32_t>(); D.M.v[1] = d.ell_i.v.as<double>(); D.M.W[1] = d.ell_i.W;
         D.M.dinv[1] = d.dvi.as<double>();
+        D.M.vf[0] = d.ell_e.vf.as<float>(); D.M.vf[1] = d.ell_i.vf.as<float>();
+        D.M.dinvf[0] = d.dvef.as<float>(); D.M.dinvf[1] = d.dvif.as<float>();
         D.M.Ne = Ne; D.M.Ni = Ni; D.M.n = n;
         D.T.prp = d.csr_p.rp.as<int32_t>(); D.T.pci = d.csr_p.ci.as<int32_t>(); D.T.pv = d.csr_p.v.as<double>();
         D.T.trp = d.csr_t.rp.as<int32_t>(); D.T.tci = d.csr_t.ci.as<int32_t>(); D.T.tv = d.csr_t.v.as<double>();
@@ -2859,6 +2915,23 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     };
     mass_many_eager = [&](const double2* zin, double2* yout, int steps) -> bem_status {
         const unsigned g64 = blocks_for(T, 64);
+        if (steps == CHEB_STEPS_INNER) {  // FP32 iteration (inner solves with FP32 products)
+            float2* r32 = reinterpret_cast<float2*>(wr.p);
+            float2* da = reinterpret_cast<float2*>(wa.p);
+            float2* db = reinterpret_cast<float2*>(wb.p);
+            float2* y32 = da + T;
+            BEM_LAUNCH(k_cheb_init32_many, g64, 64, 0, s, Dd, RI, T, zin, r32, da, (float)(1.0 / theta));
+            double rho = 1.0 / sigma;
+            float2 *dk = da, *dn = db;
+            for (int k = 0; k < steps; ++k) {
+                const double rho_n = 1.0 / (2.0 * sigma - rho);
+                BEM_LAUNCH(k_cheb_step32_many, g64, 64, 0, s, Dd, RI, T, dk, dn, y32, r32, (float)(rho_n * rho),
+                           (float)(2.0 * rho_n / delta), k == 0 ? 1 : 0, k == steps - 1 ? yout : nullptr);
+                rho = rho_n;
+                std::swap(dk, dn);
+            }
+            return BEM_OK;
+        }
         BEM_LAUNCH(k_cheb_init_many, g64, 64, 0, s, Dd, RI, T, zin, yout, wr.as<double2>(), wa.as<double2>(),
                    1.0 / theta);
         double rho = 1.0 / sigma;
