@@ -260,9 +260,13 @@ typedef struct {
     int32_t mtf_variant;      /* BEM_MTF_DERIVED (default) or BEM_MTF_PRINTED                     */
     double  center[3];        /* projection centre for the mortar (default origin)               */
     double  ir_inner_tol;     /* BEM_PREC_MIXED: relative residual reduction asked of each inner
-                                 GMRES solve (default 1e-8: the first inner solve runs to the
-                                 target tolerance, the FP64 residual then needs one short
-                                 correction); never below gmres_tol * ||S b|| overall              */
+                                 GMRES solve, never below gmres_tol * ||S b|| overall.  0 (default)
+                                 chooses: 1e-8 for one right-hand side (its double-float phase
+                                 reaches the target in one inner solve) and bem_solve_many, 1e-5
+                                 for batches (FP32 or tensor-core inner products: the true inner
+                                 residual stalls near their 1e-7 accuracy, so a second short inner
+                                 solve on the FP64 residual is cheaper than running the first one
+                                 on); any value in (0, 1) is used as given                         */
     int32_t batch_columns;    /* right-hand sides solved together (one Krylov process each, the
                                  operator read once per iteration for all): 0 = default (64 with
                                  BEM_PREC_MIXED and tensor cores, else 8); 1..128                   */

@@ -392,7 +392,7 @@ void bem_solve_opts_default(bem_solve_opts* o) {
     o->n_singular = 4;
     o->mtf_variant = BEM_MTF_DERIVED;
     o->center[0] = o->center[1] = o->center[2] = 0.0;
-    o->ir_inner_tol = 1e-8;
+    o->ir_inner_tol = 0.0;  // chosen per solve (one right-hand side or a batch)
     o->batch_columns = 0;
     o->tensor_cores = 2;
     o->formulation = BEM_FORM_MTF;
@@ -419,7 +419,7 @@ bem_status bem_solve_transmission(bem_context* ctx, const bem_grid* ext, const b
     BEM_REQUIRE(o.n_singular >= 1 && o.n_singular <= 16, "n_singular must be in [1, 16]");
     BEM_REQUIRE(o.mtf_variant == BEM_MTF_DERIVED || o.mtf_variant == BEM_MTF_PRINTED, "unknown MTF variant");
     BEM_REQUIRE(o.precision == BEM_PREC_FP64 || o.precision == BEM_PREC_MIXED, "unsupported precision");
-    BEM_REQUIRE(o.ir_inner_tol > 0.0 && o.ir_inner_tol < 1.0, "ir_inner_tol must be in (0, 1)");
+    BEM_REQUIRE(o.ir_inner_tol >= 0.0 && o.ir_inner_tol < 1.0, "ir_inner_tol must be 0 or in (0, 1)");
     BEM_REQUIRE(o.batch_columns >= 0 && o.batch_columns <= 128, "batch_columns must be in [0, 128]");
     BEM_REQUIRE(o.tensor_cores >= 0 && o.tensor_cores <= 3, "tensor_cores must be 0, 1, 2 or 3");
     BEM_REQUIRE(o.formulation >= BEM_FORM_MTF && o.formulation <= BEM_FORM_HC_INT_DIR, "unknown formulation");
@@ -452,7 +452,7 @@ bem_status bem_solve_screen(bem_context* ctx, const bem_grid* screen, const bem_
     BEM_REQUIRE(o.gmres_tol >= 0.0 && o.gmres_maxiter >= 1, "bad GMRES options");
     BEM_REQUIRE(o.n_singular >= 1 && o.n_singular <= 16, "n_singular must be in [1, 16]");
     BEM_REQUIRE(o.precision == BEM_PREC_FP64 || o.precision == BEM_PREC_MIXED, "unsupported precision");
-    BEM_REQUIRE(o.ir_inner_tol > 0.0 && o.ir_inner_tol < 1.0, "ir_inner_tol must be in (0, 1)");
+    BEM_REQUIRE(o.ir_inner_tol >= 0.0 && o.ir_inner_tol < 1.0, "ir_inner_tol must be 0 or in (0, 1)");
     BEM_REQUIRE(o.batch_columns >= 0 && o.batch_columns <= 128, "batch_columns must be in [0, 128]");
     BEM_REQUIRE(o.cuda_graphs == 0 || o.cuda_graphs == 1, "cuda_graphs must be 0 or 1");
     BEM_REQUIRE(o.dd_switch >= 0.0 && o.dd_switch <= 1.0, "dd_switch must be in [0, 1]");
@@ -496,7 +496,7 @@ bem_status bem_solve_many(bem_context* ctx, int32_t count, const bem_instance* i
     BEM_REQUIRE(o.gmres_tol >= 0.0 && o.gmres_maxiter >= 1, "bad GMRES options");
     BEM_REQUIRE(o.n_singular >= 1 && o.n_singular <= 16, "n_singular must be in [1, 16]");
     BEM_REQUIRE(o.mtf_variant == BEM_MTF_DERIVED || o.mtf_variant == BEM_MTF_PRINTED, "unknown MTF variant");
-    BEM_REQUIRE(o.ir_inner_tol > 0.0 && o.ir_inner_tol < 1.0, "ir_inner_tol must be in (0, 1)");
+    BEM_REQUIRE(o.ir_inner_tol >= 0.0 && o.ir_inner_tol < 1.0, "ir_inner_tol must be 0 or in (0, 1)");
     for (int i = 0; i < count; ++i) {
         const bem_instance& q = instances[i];
         BEM_REQUIRE(q.ext != nullptr && q.intr != nullptr, "null grid");

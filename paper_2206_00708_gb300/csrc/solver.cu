@@ -519,51 +519,56 @@ __global__ void k_cheb_init(MassPair M, const double2* __restrict__ z, double2* 
 // The same iteration in FP32 (the 17-step inverse of the inner solves that use FP32
 // products: its rounding, ~2e-7, matches theirs): r, d and the running sum y as float2
 // (y in the second half of the dA workspace), the result widened to FP64 by the last step.
-__global__ void k_cheb_init32(MassPair M, const double2* __restrict__ z, float2* __restrict__ r,
+// The FP32 vectors are interleaved by column (entry (g, c) of R columns at g R + c): the
+// threads of a warp take consecutive columns of a row, so that the row's mass entries
+// are loaded once per warp and the gathers of its neighbours are contiguous.  z and the
+// result keep the column-major layout of the other kernels.  Thread t = g R + c; n R
+// stays below 2^31 (checked by the caller).
+__global__ void k_cheb_init32(MassPair M, int R, const double2* __restrict__ z, float2* __restrict__ r,
                               float2* __restrict__ d, float inv_theta) {
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= M.n) return;
-    const int64_t off = blockIdx.y * M.n;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((int64_t)t >= M.n * R) return;
+    const uint32_t g = t / (uint32_t)R, c = t - g * (uint32_t)R;
     const MassRow m = mass_row(M, g);
-    const double2 zz = z[off + g];
+    const double2 zz = z[(int64_t)c * M.n + g];
     const float2 rz = make_float2((float)zz.x, (float)zz.y);
     const float sc = (m.base < 2 * M.Ne ? M.dinvf[0] : M.dinvf[1])[m.i] * inv_theta;
-    r[off + g] = rz;
-    d[off + g] = make_float2(sc * rz.x, sc * rz.y);
+    r[t] = rz;
+    d[t] = make_float2(sc * rz.x, sc * rz.y);
 }
 
-__global__ void k_cheb_step32(MassPair M, const float2* __restrict__ dk, float2* __restrict__ dn,
+__global__ void k_cheb_step32(MassPair M, int R, const float2* __restrict__ dk, float2* __restrict__ dn,
                               float2* __restrict__ y, float2* __restrict__ r, float c1, float c2, int first,
                               double2* __restrict__ yout) {
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= M.n) return;
-    const int64_t off = blockIdx.y * M.n;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((int64_t)t >= M.n * R) return;
+    const uint32_t g = t / (uint32_t)R, c = t - g * (uint32_t)R;
     const MassRow m = mass_row(M, g);
     const bool ext = m.base < 2 * M.Ne;
     const float* __restrict__ vf = ext ? M.vf[0] : M.vf[1];
-    const float2* __restrict__ d = dk + off + m.base;
+    const float2* __restrict__ d = dk + m.base * R + c;
     float2 md = make_float2(0.f, 0.f);
     for (int k = 0; k < m.W; ++k) {
         const float v = vf[(int64_t)k * m.N + m.i];
-        const float2 dd = d[m.ci[(int64_t)k * m.N + m.i]];
+        const float2 dd = d[(int64_t)m.ci[(int64_t)k * m.N + m.i] * R];
         md.x = fmaf(v, dd.x, md.x);
         md.y = fmaf(v, dd.y, md.y);
     }
-    const float2 d0 = dk[off + g];
+    const float2 d0 = dk[t];
     float2 yy = d0;
     if (!first) {
-        const float2 yp = y[off + g];
+        const float2 yp = y[t];
         yy.x += yp.x;
         yy.y += yp.y;
     }
-    float2 rr = r[off + g];
+    float2 rr = r[t];
     rr.x -= md.x;
     rr.y -= md.y;
-    if (yout) yout[off + g] = make_double2((double)yy.x, (double)yy.y);
-    else y[off + g] = yy;
-    r[off + g] = rr;
+    if (yout) yout[(int64_t)c * M.n + g] = make_double2((double)yy.x, (double)yy.y);
+    else y[t] = yy;
+    r[t] = rr;
     const float sc = c2 * (ext ? M.dinvf[0] : M.dinvf[1])[m.i];
-    dn[off + g] = make_float2(fmaf(c1, d0.x, sc * rr.x), fmaf(c1, d0.y, sc * rr.y));
+    dn[t] = make_float2(fmaf(c1, d0.x, sc * rr.x), fmaf(c1, d0.y, sc * rr.y));
 }
 
 // y += d_k; r -= M d_k; d_{k+1} = c1 d_k + c2 D^-1 r
@@ -821,16 +826,150 @@ __global__ void k_add_cols(double2* __restrict__ a, int64_t astride, const doubl
     }
 }
 
+// the norm and its reciprocal once per block (FP64 square roots and divisions run on
+// GB300's narrow FP64 pipe: one per thread cost more than the whole copy)
+__device__ __forceinline__ double2 block_norm_inv(const double2* __restrict__ nrm2, int r) {
+    __shared__ double2 ni;
+    if (threadIdx.x == 0) {
+        const double nr = sqrt(fmax(nrm2[r].x, 0.0));
+        ni = make_double2(nr, nr > 0.0 ? 1.0 / nr : 0.0);
+    }
+    __syncthreads();
+    return ni;
+}
+
 // v_r = w_r / |w_r| (|w_r|^2 = real part of nrm2[r]); writes |w_r| to dst[r * dstride]
 __global__ void k_normalize(const double2* __restrict__ w, int64_t n, const double2* __restrict__ nrm2,
                             double2* __restrict__ v, int64_t vstride, double2* __restrict__ dst, int64_t dstride) {
     const int r = blockIdx.y;
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const double nr = sqrt(fmax(nrm2[r].x, 0.0));
-    if (e == 0 && dst) dst[r * dstride] = make_double2(nr, 0.0);
+    const double2 ni = block_norm_inv(nrm2, r);
+    if (e == 0 && dst) dst[r * dstride] = make_double2(ni.x, 0.0);
     if (e >= n) return;
-    const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+    const double inv = ni.y;
     v[r * vstride + e] = make_double2(w[(int64_t)r * n + e].x * inv, w[(int64_t)r * n + e].y * inv);
+}
+
+// ---- complex64 Krylov basis (mixed precision, several right-hand sides)
+// The inner solves of a batch run on FP32 or tensor-core products (~1e-7) and are
+// refined against the FP64 residual, so their basis is stored in complex64 and
+// orthogonalised in FP32 arithmetic: half the bytes of the basis passes, which for a
+// batch are most of an iteration's memory traffic.  CGS2 keeps the FP32 basis
+// orthogonal to O(2^-24).  The working vector w stays FP64; the current basis vector
+// is also kept widened to FP64 (exactly the stored value) as the operator's input.
+constexpr int DOT32_VPW = 8;              // basis vectors per warp
+constexpr int DOT32_VPB = 8 * DOT32_VPW;  // basis vectors per block
+
+// conj(V_{i,r}) . w_r partial sums over row chunks, as k_dots_partial: FP32 products
+// and sums within a chunk, partial[((r * m) + i) * nblk + chunk] in FP64
+__global__ void __launch_bounds__(256) k_dots_partial32(const float2* __restrict__ Vb, int64_t n, int R, int m,
+                                                        const double2* __restrict__ w, int nblk,
+                                                        double2* __restrict__ partial) {
+    const int r = blockIdx.z, b = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int i0 = (blockIdx.y * 8 + (threadIdx.x >> 5)) * DOT32_VPW;
+    if (i0 >= m) return;
+    const int nv = min(DOT32_VPW, m - i0);
+    const int64_t chunk = (n + nblk - 1) / nblk;
+    const int64_t e0 = b * chunk, e1 = min(n, e0 + chunk);
+    const double2* __restrict__ wr = w + (int64_t)r * n;
+    float2 S[DOT32_VPW];
+#pragma unroll
+    for (int u = 0; u < DOT32_VPW; ++u) S[u] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+        const double2 wd = wr[e];
+        const float wx = (float)wd.x, wy = (float)wd.y;
+#pragma unroll
+        for (int u = 0; u < DOT32_VPW; ++u)
+            if (u < nv) {
+                const float2 v = Vb[((int64_t)(i0 + u) * R + r) * n + e];
+                S[u].x = fmaf(v.x, wx, fmaf(v.y, wy, S[u].x));
+                S[u].y = fmaf(v.x, wy, fmaf(-v.y, wx, S[u].y));
+            }
+    }
+#pragma unroll
+    for (int u = 0; u < DOT32_VPW; ++u) {
+        if (u >= nv) break;
+        float2 t = S[u];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+            t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+        }
+        if (lane == 0) partial[((int64_t)r * m + i0 + u) * nblk + b] = make_double2(t.x, t.y);
+    }
+}
+
+// w_r -= sum_{i<m} h_r[i] V_{i,r}  or (overwrite) x_r = sum_{i<m_r} y_r[i] V_{i,r}, as
+// k_combine with the sums in FP32 (fixed order) and the update of w in FP64
+template <bool HS>
+__global__ void __launch_bounds__(256) k_combine32(const float2* __restrict__ Vb, int64_t n, int R, int m,
+                                                   const int* __restrict__ mr, const double2* __restrict__ h,
+                                                   int64_t hstride, double2* __restrict__ w, int overwrite) {
+    extern __shared__ float2 hs2[];
+    const int r = blockIdx.y;
+    const int lr = threadIdx.x & 31, sl = threadIdx.x >> 5;
+    const int64_t e = blockIdx.x * 32ll + lr;
+    const int mm = mr ? mr[r] : m;
+    const double2* __restrict__ hr = h + r * hstride;
+    if (HS) {
+        for (int i = threadIdx.x; i < mm; i += blockDim.x) hs2[i] = make_float2((float)hr[i].x, (float)hr[i].y);
+        __syncthreads();
+    }
+    float2 S = make_float2(0.f, 0.f);
+    if (e < n) {
+#pragma unroll 4
+        for (int i = sl; i < mm; i += 8) {
+            const float2 hv = HS ? hs2[i] : make_float2((float)hr[i].x, (float)hr[i].y);
+            const float2 v = Vb[((int64_t)i * R + r) * n + e];
+            S.x = fmaf(hv.x, v.x, fmaf(-hv.y, v.y, S.x));
+            S.y = fmaf(hv.x, v.y, fmaf(hv.y, v.x, S.y));
+        }
+    }
+    __shared__ float2 part[8][32];
+    part[sl][lr] = S;
+    __syncthreads();
+    if (sl == 0 && e < n) {
+        float2 t = part[0][lr];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) {
+            t.x += part[k][lr].x;
+            t.y += part[k][lr].y;
+        }
+        double2* wr = w + (int64_t)r * n;
+        if (overwrite) wr[e] = make_double2(t.x, t.y);
+        else {
+            const double2 q = wr[e];
+            wr[e] = make_double2(q.x - (double)t.x, q.y - (double)t.y);
+        }
+    }
+}
+
+bem_status launch_combine32(dim3 grid, const float2* Vb, int64_t n, int R, int m, const int* mr, const double2* h,
+                            int64_t hstride, double2* w, int overwrite, cudaStream_t s) {
+    if (!mr && m <= COMBINE_HS_MAX)
+        BEM_LAUNCH(k_combine32<true>, grid, 256, (size_t)m * sizeof(float2), s, Vb, n, R, m, mr, h, hstride, w,
+                   overwrite);
+    else BEM_LAUNCH(k_combine32<false>, grid, 256, 0, s, Vb, n, R, m, mr, h, hstride, w, overwrite);
+    return BEM_OK;
+}
+
+// v_r = w_r / |w_r| into the complex64 basis, and the stored value widened into
+// vcur (columns of length n, stride n); |w_r| to dst[r * dstride]
+__global__ void k_normalize32(const double2* __restrict__ w, int64_t n, const double2* __restrict__ nrm2,
+                              float2* __restrict__ v, double2* __restrict__ vcur, double2* __restrict__ dst,
+                              int64_t dstride) {
+    const int r = blockIdx.y;
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const double2 ni = block_norm_inv(nrm2, r);
+    if (e == 0 && dst) dst[r * dstride] = make_double2(ni.x, 0.0);
+    if (e >= n) return;
+    const double inv = ni.y;
+    const double2 q = w[(int64_t)r * n + e];
+    const float2 f = make_float2((float)(q.x * inv), (float)(q.y * inv));
+    v[(int64_t)r * n + e] = f;
+    vcur[(int64_t)r * n + e] = make_double2(f.x, f.y);
 }
 
 // y = a - b;  x += d (whole blocks)
@@ -1041,18 +1180,20 @@ bem_status mass_solve(const MassOp& op, const double2* z, double2* y, int R, cud
     // every SM
     const int nb = tune_get(TUNE_CHEB, R, n, TuneChoice{64, 0, 0.0}).block;
     const dim3 grid(blocks_for(n, nb), R);
-    if (steps == CHEB_STEPS_INNER && op.M.vf[0] && op.M.vf[1] && steps >= 1) {
-        // FP32 iteration: r in op.r, d in the first halves of dA / dB, y in the second half of dA
+    if (steps == CHEB_STEPS_INNER && op.M.vf[0] && op.M.vf[1] && steps >= 1 && (int64_t)R * n < (1ll << 31)) {
+        // FP32 iteration, vectors interleaved by column: r in op.r, d in the first halves
+        // of dA / dB, y in the second half of dA
         float2* r32 = reinterpret_cast<float2*>(op.r);
         float2* da = reinterpret_cast<float2*>(op.dA);
         float2* db = reinterpret_cast<float2*>(op.dB);
         float2* y32 = da + (int64_t)R * n;
-        BEM_LAUNCH(k_cheb_init32, grid, nb, 0, s, op.M, z, r32, da, (float)(1.0 / theta));
+        const dim3 g1(blocks_for((int64_t)R * n, nb));
+        BEM_LAUNCH(k_cheb_init32, g1, nb, 0, s, op.M, R, z, r32, da, (float)(1.0 / theta));
         double rho = 1.0 / sigma;
         float2 *dk = da, *dn = db;
         for (int k = 0; k < steps; ++k) {
             const double rho_n = 1.0 / (2.0 * sigma - rho);
-            BEM_LAUNCH(k_cheb_step32, grid, nb, 0, s, op.M, dk, dn, y32, r32, (float)(rho_n * rho),
+            BEM_LAUNCH(k_cheb_step32, g1, nb, 0, s, op.M, R, dk, dn, y32, r32, (float)(rho_n * rho),
                        (float)(2.0 * rho_n / delta), k == 0 ? 1 : 0, k == steps - 1 ? y : nullptr);
             rho = rho_n;
             std::swap(dk, dn);
@@ -1118,6 +1259,15 @@ using StopCheck = std::function<bem_status()>;
 // iterations a host check of the residual trails the launches by (the GPU keeps
 // this many iterations queued; at most this many are computed past convergence)
 constexpr int GMRES_LAG = 2;
+
+// relative inner tolerances of the mixed mode's refinement when
+// bem_solve_opts.ir_inner_tol is 0: one right-hand side (double-float products above
+// the switch point: one inner solve reaches the target) and batches (FP32 or
+// tensor-core products throughout: the true inner residual stalls near their
+// accuracy while the recurrence estimate runs on, so the first inner solve stops
+// early and a second one starts from the FP64 residual)
+constexpr double IR_INNER_TOL_SINGLE = 1e-8;
+constexpr double IR_INNER_TOL_BATCH = 1e-5;
 constexpr int GMRES_SLOTS = GMRES_LAG + 2;
 
 using cplx = std::complex<double>;
@@ -1130,7 +1280,8 @@ using cplx = std::complex<double>;
 struct GmresWork {
     int maxit = 0, R = 0, RW = 0, nblk = 0;
     int64_t n = 0, ldh = 0, gstride = 0;
-    DevBuf Vb, H, partial, hbuf, y, w, nrm, mr;
+    bool f32 = false;  // complex64 basis + FP32 orthogonalisation (vcur: the current vector in FP64)
+    DevBuf Vb, H, partial, hbuf, y, w, nrm, mr, vcur;
     double2* h_nrm = nullptr;  // pinned, [R]
     double2* h_col = nullptr;  // pinned, [GMRES_SLOTS][R][maxit + 2]: copied Hessenberg columns
     double2* h_y = nullptr;    // pinned, [R][gstride]: least-squares solutions
@@ -1149,20 +1300,31 @@ struct GmresWork {
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
     }
-    bem_status init(int maxit_, int64_t n_, int R_, int spare, cudaStream_t s) {
+    bem_status init(int maxit_, int64_t n_, int R_, int spare, cudaStream_t s, bool f32_ = false) {
         maxit = maxit_;
         n = n_;
         R = R_;
         stream = s;
         RW = R_ + spare;
+        f32 = f32_;
         nblk = dot_blocks(n_);
         ldh = maxit + 1;
         gstride = maxit + 2;
-        // (maxit + 1) basis blocks of R columns, plus RW - R spare columns read by the
-        // width-padded operator kernels past the last block
-        const size_t vb = ((size_t)(maxit + 1) * R + (RW - R)) * n * 16;
-        BEM_TRY(Vb.alloc(vb, s));
-        BEM_CUDA_TRY(cudaMemsetAsync(Vb.p, 0, vb, s));
+        if (f32) {
+            // (maxit + 1) complex64 basis blocks of R columns; the operator reads vcur,
+            // whose RW - R spare columns stay zero for the width-padded kernels
+            const size_t vb = (size_t)(maxit + 1) * R * n * 8;
+            BEM_TRY(Vb.alloc(vb, s));
+            BEM_CUDA_TRY(cudaMemsetAsync(Vb.p, 0, vb, s));
+            BEM_TRY(vcur.alloc((size_t)RW * n * 16, s));
+            BEM_CUDA_TRY(cudaMemsetAsync(vcur.p, 0, vcur.bytes, s));
+        } else {
+            // (maxit + 1) basis blocks of R columns, plus RW - R spare columns read by the
+            // width-padded operator kernels past the last block
+            const size_t vb = ((size_t)(maxit + 1) * R + (RW - R)) * n * 16;
+            BEM_TRY(Vb.alloc(vb, s));
+            BEM_CUDA_TRY(cudaMemsetAsync(Vb.p, 0, vb, s));
+        }
         BEM_TRY(H.alloc((size_t)R * ldh * ldh * 16, s));
         BEM_TRY(partial.alloc((size_t)R * (maxit + 1) * nblk * 16, s));
         BEM_TRY(hbuf.alloc((size_t)R * gstride * 16, s));
@@ -1303,26 +1465,43 @@ bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs
         ++checked;
         return BEM_OK;
     };
+    float2* Vp32 = W.Vb.as<float2>();  // the complex64 basis (W.f32)
+    // v_{j} = w / |w| into basis block j (and vcur), |w| to dst
+    auto normalize_into = [&](const double2* wv, int j, double2* dst, int64_t dstride) -> bem_status {
+        if (W.f32)
+            BEM_LAUNCH(k_normalize32, eb, 256, 0, s, wv, n, W.nrm.as<double2>(), Vp32 + (int64_t)j * R * n,
+                       W.vcur.as<double2>(), dst, dstride);
+        else
+            BEM_LAUNCH(k_normalize, eb, 256, 0, s, wv, n, W.nrm.as<double2>(), Vp + (int64_t)j * R * n, n, dst,
+                       dstride);
+        return BEM_OK;
+    };
     if (ndone < R) {
         BEM_TRY(W.sq_norms(rhs, s));  // V_0 = rhs / beta
-        BEM_LAUNCH(k_normalize, eb, 256, 0, s, rhs, n, W.nrm.as<double2>(), Vp, n, nullptr, 0);
+        BEM_TRY(normalize_into(rhs, 0, nullptr, 0));
         for (int j = 0; j < W.maxit && ndone < R; ++j) {
-            double2* vj = Vp + (int64_t)j * R * n;
+            const double2* vj = W.f32 ? W.vcur.as<double2>() : Vp + (int64_t)j * R * n;
             BEM_TRY(apply(vj, W.w.as<double2>(), R));
             double2* Hj = W.H.as<double2>() + (int64_t)j * ldh;  // + r * ldh * ldh per column
-            const unsigned gy = (unsigned)((j + 1 + DOT_VPB - 1) / DOT_VPB);
             for (int pass = 0; pass < 2; ++pass) {  // CGS2
                 double2* h = pass == 0 ? Hj : W.hbuf.as<double2>();
                 const int64_t hst = pass == 0 ? ldh * ldh : gs;
-                BEM_LAUNCH(k_dots_partial, dim3(W.nblk, gy, R), 256, 0, s, Vp, n, R, j + 1, W.w.as<double2>(),
-                           W.nblk, W.partial.as<double2>());
+                if (W.f32) {
+                    const unsigned gy = (unsigned)((j + 1 + DOT32_VPB - 1) / DOT32_VPB);
+                    BEM_LAUNCH(k_dots_partial32, dim3(W.nblk, gy, R), 256, 0, s, Vp32, n, R, j + 1,
+                               W.w.as<double2>(), W.nblk, W.partial.as<double2>());
+                } else {
+                    const unsigned gy = (unsigned)((j + 1 + DOT_VPB - 1) / DOT_VPB);
+                    BEM_LAUNCH(k_dots_partial, dim3(W.nblk, gy, R), 256, 0, s, Vp, n, R, j + 1, W.w.as<double2>(),
+                               W.nblk, W.partial.as<double2>());
+                }
                 BEM_LAUNCH(k_dots_final, dim3(j + 1, R), 32, 0, s, W.partial.as<double2>(), j + 1, W.nblk, h, hst, 0);
-                BEM_TRY(launch_combine(ecb, Vp, n, R, j + 1, nullptr, h, hst, W.w.as<double2>(), 0, s));
+                if (W.f32) BEM_TRY(launch_combine32(ecb, Vp32, n, R, j + 1, nullptr, h, hst, W.w.as<double2>(), 0, s));
+                else BEM_TRY(launch_combine(ecb, Vp, n, R, j + 1, nullptr, h, hst, W.w.as<double2>(), 0, s));
             }
             BEM_LAUNCH(k_add_cols, dim3(1, R), 256, 0, s, Hj, ldh * ldh, W.hbuf.as<double2>(), gs, j + 1);
             BEM_TRY(W.sq_norms(W.w.as<double2>(), s));
-            BEM_LAUNCH(k_normalize, eb, 256, 0, s, W.w.as<double2>(), n, W.nrm.as<double2>(),
-                       Vp + (int64_t)(j + 1) * R * n, n, Hj + j + 1, ldh * ldh);
+            BEM_TRY(normalize_into(W.w.as<double2>(), j + 1, Hj + j + 1, ldh * ldh));
             const int slot = j % GMRES_SLOTS;
             BEM_CUDA_TRY(cudaMemcpy2DAsync(W.h_col + (size_t)slot * R * gs, gs * 16, Hj, ldh * ldh * 16,
                                            (size_t)(j + 2) * 16, R, cudaMemcpyDeviceToHost, s));
@@ -1339,7 +1518,8 @@ bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs
     }
     BEM_CUDA_TRY(cudaMemcpyAsync(W.mr.p, W.h_mr, R * 4, cudaMemcpyHostToDevice, s));
     BEM_CUDA_TRY(cudaMemcpyAsync(W.y.p, W.h_y, (size_t)R * gs * 16, cudaMemcpyHostToDevice, s));
-    BEM_TRY(launch_combine(ecb, Vp, n, R, 0, W.mr.as<int>(), W.y.as<double2>(), gs, x, 1, s));
+    if (W.f32) BEM_TRY(launch_combine32(ecb, Vp32, n, R, 0, W.mr.as<int>(), W.y.as<double2>(), gs, x, 1, s));
+    else BEM_TRY(launch_combine(ecb, Vp, n, R, 0, W.mr.as<int>(), W.y.as<double2>(), gs, x, 1, s));
     BEM_CUDA_TRY(cudaStreamSynchronize(s));  // pinned h_y / h_mr are reused by the next run
     for (int r = 0; r < R; ++r) iters_out[r] = it[r];
     return BEM_OK;
@@ -2152,7 +2332,10 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     // ---- GMRES ------------------------------------------------------------------------
     const int maxit = (int)std::min<int64_t>(o->gmres_maxiter, n);
     GmresWork W;
-    BEM_TRY(W.init(maxit, n, RB, RW - RB, s));
+    // batches of the mixed mode (FP32 or tensor-core inner products throughout) keep a
+    // complex64 basis; single right-hand sides keep the FP64 basis of their
+    // double-float phase
+    BEM_TRY(W.init(maxit, n, RB, RW - RB, s, mixed && !dd_single));
     DevBuf fvec, gvec, bvec, sb, xsol, dvec, rvec, tmp, wave;
     BEM_TRY(wave.alloc((size_t)5 * RB * 8, s));
     BEM_TRY(fvec.alloc((size_t)RB * Ne * 16, s));
@@ -2248,11 +2431,13 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                     if (pending(r)) return true;
                 return false;
             };
+            const double inner_rel =
+                o->ir_inner_tol > 0.0 ? o->ir_inner_tol : dd_single ? IR_INNER_TOL_SINGLE : IR_INNER_TOL_BATCH;
             while (any_pending() && outer < max_outer) {
                 // a column that is finished (or out of iterations) gets tolerance |r|,
                 // so that its inner GMRES takes no step and its correction is zero
                 for (int r = 0; r < R; ++r)
-                    inner_tol[r] = pending(r) ? std::max(tol_abs[r], o->ir_inner_tol * rn[r]) : rn[r];
+                    inner_tol[r] = pending(r) ? std::max(tol_abs[r], inner_rel * rn[r]) : rn[r];
                 BEM_TRY(gmres_run(W, R, apply_work, rvec.as<double2>(), rn.data(), inner_tol.data(),
                                   dvec.as<double2>(), its.data(), est.data(), s, stop, &inner_progress));
                 int moved = 0;
@@ -2992,6 +3177,7 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     BEM_TRY(many_norms(L, W, sb.as<double2>(), beta.data(), s));
     for (int r = 0; r < count; ++r) tol_abs[r] = o->gmres_tol * beta[r];
     // ---- iterative refinement, all instances in lockstep
+    const double inner_rel = o->ir_inner_tol > 0.0 ? o->ir_inner_tol : IR_INNER_TOL_SINGLE;
     BEM_CUDA_TRY(cudaMemsetAsync(xsol.p, 0, (size_t)T * 16, s));
     BEM_CUDA_TRY(cudaMemcpyAsync(rvec.p, sb.p, (size_t)T * 16, cudaMemcpyDeviceToDevice, s));
     rn = beta;
@@ -3011,7 +3197,7 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     for (; outer < 12; ++outer) {
         bool any = false;
         for (int r = 0; r < count; ++r) {
-            inner_tol[r] = pending(r) ? std::max(tol_abs[r], o->ir_inner_tol * rn[r]) : rn[r];
+            inner_tol[r] = pending(r) ? std::max(tol_abs[r], inner_rel * rn[r]) : rn[r];
             any = any || pending(r);
         }
         if (!any) break;
@@ -3316,9 +3502,11 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
                     if (pending(r)) return true;
                 return false;
             };
+            const double inner_rel =
+                o->ir_inner_tol > 0.0 ? o->ir_inner_tol : dd_single ? IR_INNER_TOL_SINGLE : IR_INNER_TOL_BATCH;
             while (any_pending() && outer < 12) {
                 for (int r = 0; r < R; ++r)
-                    inner_tol[r] = pending(r) ? std::max(tol_abs[r], o->ir_inner_tol * rn[r]) : rn[r];
+                    inner_tol[r] = pending(r) ? std::max(tol_abs[r], inner_rel * rn[r]) : rn[r];
                 BEM_TRY(gmres_run(W, R, apply_work, rvec.as<double2>(), rn.data(), inner_tol.data(), dvec.as<double2>(),
                                   its.data(), est.data(), s, stop, &inner_progress));
                 int moved = 0;

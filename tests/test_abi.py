@@ -66,3 +66,14 @@ def test_noalloc_wrapper_rejects_unsuitable_outputs_before_calling(bem):
         bem.bem_projection_noalloc(fake_ctx, None, None, i32, i32, f64)
     with pytest.raises(ValueError, match="CUDA tensor"):
         bem.bem_projection_noalloc(fake_ctx, None, None, i32.numpy(), i32, f64)
+
+
+def test_solve_option_defaults(bem):
+    """Defaults of bem_solve_opts that the solver's refinement depends on: the inner
+    tolerance 0 selects its per-solve rule (1e-8 for one right-hand side, 1e-5 for
+    batches), tensor cores default to the FP16 split."""
+    o = bem.bem_solve_opts_default()
+    assert o.ir_inner_tol == 0.0
+    assert o.tensor_cores == 2
+    assert o.dd_switch == pytest.approx(1e-3)
+    assert o.gmres_tol == pytest.approx(1e-8)
