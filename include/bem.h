@@ -261,12 +261,12 @@ typedef struct {
     double  center[3];        /* projection centre for the mortar (default origin)               */
     double  ir_inner_tol;     /* BEM_PREC_MIXED: relative residual reduction asked of each inner
                                  GMRES solve, never below gmres_tol * ||S b|| overall.  0 (default)
-                                 chooses: 1e-8 for one right-hand side (its double-float phase
-                                 reaches the target in one inner solve) and bem_solve_many, 1e-5
-                                 for batches (FP32 or tensor-core inner products: the true inner
+                                 chooses: 1e-5 where the inner products are FP32 or tensor-core
+                                 products throughout (batches, dd_switch = 1: the true inner
                                  residual stalls near their 1e-7 accuracy, so a second short inner
                                  solve on the FP64 residual is cheaper than running the first one
-                                 on); any value in (0, 1) is used as given                         */
+                                 on), 1e-8 where a double-float phase reaches the target in one
+                                 inner solve (dd_switch < 1); any value in (0, 1) is used as given */
     int32_t batch_columns;    /* right-hand sides solved together (one Krylov process each, the
                                  operator read once per iteration for all): 0 = default (64 with
                                  BEM_PREC_MIXED and tensor cores, else 8); 1..128                   */
@@ -283,10 +283,12 @@ typedef struct {
                                  system); high-contrast products always use the CUDA cores         */
     double  dd_switch;        /* BEM_PREC_MIXED, one right-hand side: the inner GMRES products run
                                  in double-float arithmetic while the inner residual is above
-                                 dd_switch of its right-hand side, in FP32 below (default 1e-3;
-                                 0: double-float throughout, 1: FP32 throughout).  bem_solve_many:
-                                 a lockstep step runs in double-float while some running
-                                 instance's residual estimate is above it                         */
+                                 dd_switch of its right-hand side, in FP32 below (default 1: FP32
+                                 throughout, with a complex64 Krylov basis and two inner solves;
+                                 0: double-float throughout; e.g. 1e-3: double-float to 1e-3, one
+                                 inner solve).  bem_solve_many: a lockstep step runs in
+                                 double-float while some running instance's residual estimate is
+                                 above it.  Every setting refines to the same FP64 residual        */
     int32_t cuda_graphs;      /* 1 (default): the fixed launch sequences of each iteration (the
                                  Chebyshev mass inverses) are captured once per solve and replayed
                                  as CUDA graphs; 0: every kernel is launched on its own.  Results

@@ -396,7 +396,7 @@ void bem_solve_opts_default(bem_solve_opts* o) {
     o->batch_columns = 0;
     o->tensor_cores = 2;
     o->formulation = BEM_FORM_MTF;
-    o->dd_switch = 1e-3;
+    o->dd_switch = 1.0;
     o->cuda_graphs = 1;
 }
 

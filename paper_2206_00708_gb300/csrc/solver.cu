@@ -2012,16 +2012,22 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     // reading and writing up to 7 spare (in-bounds) columns past the batch
     const int RW = RB + 7;
     const bool tc_batches = use_tc && RB > 8 && !hc;  // high-contrast products: CUDA cores
-    // Single-column inner solves of the refinement: the products run in double-float
-    // arithmetic while the inner residual is above dd_switch of its right-hand side and
-    // in FP32 after it.  GMRES tolerates product errors that grow as the residual falls
-    // (the residual gap is a sum of each product's error times its coefficient in the
-    // solution, and those coefficients shrink with the residual), so a 1e-7 FP32
-    // product after the switch leaves the inner solve accurate to ~1e-9 and the
-    // refinement converges in one pass, without paying double-float on every product.
+    // Single-column inner solves of the refinement with dd_switch < 1: the products run
+    // in double-float arithmetic while the inner residual is above dd_switch of its
+    // right-hand side and in FP32 after it.  GMRES tolerates product errors that grow as
+    // the residual falls (the residual gap is a sum of each product's error times its
+    // coefficient in the solution, and those coefficients shrink with the residual), so
+    // a 1e-7 FP32 product after the switch leaves the inner solve accurate to ~1e-9 and
+    // the refinement converges in one pass.  The default (dd_switch = 1) runs FP32
+    // products throughout and refines in two passes instead, which costs fewer
+    // double-float products than the one pass saves.
     const bool dd_single = mixed && RB == 1;
     double inner_progress = 1.0;
     auto dd_now = [&]() { return dd_single && inner_progress > o->dd_switch; };
+    // inner solves on FP32 (or tensor-core) products throughout: batches, and single
+    // columns with dd_switch >= 1.  They keep a complex64 basis and stop the first inner
+    // solve early (IR_INNER_TOL_BATCH) unless ir_inner_tol is given.
+    const bool fp32_inner = mixed && (!dd_single || o->dd_switch >= 1.0);
     const size_t colb = (size_t)n * 16;
     DevBuf wz, wr, wa, wb, x32, tcw, tcerr, xsplit;
     BEM_TRY(wz.alloc(RW * colb, s));
@@ -2332,10 +2338,9 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     // ---- GMRES ------------------------------------------------------------------------
     const int maxit = (int)std::min<int64_t>(o->gmres_maxiter, n);
     GmresWork W;
-    // batches of the mixed mode (FP32 or tensor-core inner products throughout) keep a
-    // complex64 basis; single right-hand sides keep the FP64 basis of their
-    // double-float phase
-    BEM_TRY(W.init(maxit, n, RB, RW - RB, s, mixed && !dd_single));
+    // inner solves on FP32 or tensor-core products throughout keep a complex64 basis;
+    // single right-hand sides with a double-float phase keep the FP64 basis
+    BEM_TRY(W.init(maxit, n, RB, RW - RB, s, fp32_inner));
     DevBuf fvec, gvec, bvec, sb, xsol, dvec, rvec, tmp, wave;
     BEM_TRY(wave.alloc((size_t)5 * RB * 8, s));
     BEM_TRY(fvec.alloc((size_t)RB * Ne * 16, s));
@@ -2432,7 +2437,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                 return false;
             };
             const double inner_rel =
-                o->ir_inner_tol > 0.0 ? o->ir_inner_tol : dd_single ? IR_INNER_TOL_SINGLE : IR_INNER_TOL_BATCH;
+                o->ir_inner_tol > 0.0 ? o->ir_inner_tol : fp32_inner ? IR_INNER_TOL_BATCH : IR_INNER_TOL_SINGLE;
             while (any_pending() && outer < max_outer) {
                 // a column that is finished (or out of iterations) gets tolerance |r|,
                 // so that its inner GMRES takes no step and its correction is zero
@@ -3177,7 +3182,8 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     BEM_TRY(many_norms(L, W, sb.as<double2>(), beta.data(), s));
     for (int r = 0; r < count; ++r) tol_abs[r] = o->gmres_tol * beta[r];
     // ---- iterative refinement, all instances in lockstep
-    const double inner_rel = o->ir_inner_tol > 0.0 ? o->ir_inner_tol : IR_INNER_TOL_SINGLE;
+    const double inner_rel =
+        o->ir_inner_tol > 0.0 ? o->ir_inner_tol : o->dd_switch >= 1.0 ? IR_INNER_TOL_BATCH : IR_INNER_TOL_SINGLE;
     BEM_CUDA_TRY(cudaMemsetAsync(xsol.p, 0, (size_t)T * 16, s));
     BEM_CUDA_TRY(cudaMemcpyAsync(rvec.p, sb.p, (size_t)T * 16, cudaMemcpyDeviceToDevice, s));
     rn = beta;
@@ -3503,7 +3509,9 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
                 return false;
             };
             const double inner_rel =
-                o->ir_inner_tol > 0.0 ? o->ir_inner_tol : dd_single ? IR_INNER_TOL_SINGLE : IR_INNER_TOL_BATCH;
+                o->ir_inner_tol > 0.0                          ? o->ir_inner_tol
+                : (!dd_single || o->dd_switch >= 1.0) ? IR_INNER_TOL_BATCH
+                                                      : IR_INNER_TOL_SINGLE;
             while (any_pending() && outer < 12) {
                 for (int r = 0; r < R; ++r)
                     inner_tol[r] = pending(r) ? std::max(tol_abs[r], inner_rel * rn[r]) : rn[r];

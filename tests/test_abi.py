@@ -69,11 +69,11 @@ def test_noalloc_wrapper_rejects_unsuitable_outputs_before_calling(bem):
 
 
 def test_solve_option_defaults(bem):
-    """Defaults of bem_solve_opts that the solver's refinement depends on: the inner
-    tolerance 0 selects its per-solve rule (1e-8 for one right-hand side, 1e-5 for
-    batches), tensor cores default to the FP16 split."""
+    """Defaults of bem_solve_opts that the solver's refinement depends on: FP32 inner
+    products throughout (dd_switch 1), the inner tolerance 0 selecting its per-solve
+    rule (1e-5 there, 1e-8 with a double-float phase), tensor cores on the FP16 split."""
     o = bem.bem_solve_opts_default()
     assert o.ir_inner_tol == 0.0
     assert o.tensor_cores == 2
-    assert o.dd_switch == pytest.approx(1e-3)
+    assert o.dd_switch == 1.0
     assert o.gmres_tol == pytest.approx(1e-8)
