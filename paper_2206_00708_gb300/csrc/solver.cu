@@ -43,6 +43,14 @@ namespace {
 constexpr int CHEB_STEPS = 34;        // error <= 2 * 3^-34 ~ 1e-16: FP64 applications
 constexpr int CHEB_STEPS_INNER = 17;  // error <= 2 * 3^-17 ~ 1.6e-8: inner solves with FP32 products
 constexpr int CHEB_STEPS_DD = 24;     // error <= 2 * 3^-24 ~ 7e-12: inner solves with double-float products
+// The mass inverse of the multiple-traces system is a left preconditioner only (S A x =
+// S b, with no inverse inside A), so any fixed approximation S' of it gives the same
+// solution when both sides use it.  The FP32 inner solves of the refinement take
+// S' = 6 Chebyshev steps (error <= 2 * 3^-6 ~ 3e-3: the preconditioned spectrum moves
+// by that much, ~1 % more iterations at the sphere pairs of levels 2-3 than with the
+// exact inverse) on both their operator and their right-hand side S'(b - A x); the
+// refinement's convergence test keeps the FP64 inverse.
+constexpr int CHEB_STEPS_PRE = 6;
 constexpr double CHEB_ALPHA = 0.5, CHEB_BETA = 2.0;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -1180,7 +1188,7 @@ bem_status mass_solve(const MassOp& op, const double2* z, double2* y, int R, cud
     // every SM
     const int nb = tune_get(TUNE_CHEB, R, n, TuneChoice{64, 0, 0.0}).block;
     const dim3 grid(blocks_for(n, nb), R);
-    if (steps == CHEB_STEPS_INNER && op.M.vf[0] && op.M.vf[1] && steps >= 1 && (int64_t)R * n < (1ll << 31)) {
+    if (steps <= CHEB_STEPS_INNER && op.M.vf[0] && op.M.vf[1] && steps >= 1 && (int64_t)R * n < (1ll << 31)) {
         // FP32 iteration, vectors interleaved by column: r in op.r, d in the first halves
         // of dA / dB, y in the second half of dA
         float2* r32 = reinterpret_cast<float2*>(op.r);
@@ -2320,19 +2328,28 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
         return pair_lin(yout, xin, hu.as<double2>(), w, NA, R, hc_y);
     };
     // S A x in the working precision, and with FP64 arithmetic on the stored matrices
+    // the multiple-traces system's FP32 inner solves precondition with S' (CHEB_STEPS_PRE)
+    const bool pre_inner = fp32_inner && !hc && !st;
     Apply apply_work = [&](const double2* xin, double2* yout, int R) -> bem_status {
-        const int steps = !mixed ? CHEB_STEPS : (R == 1 && dd_now()) ? CHEB_STEPS_DD : CHEB_STEPS_INNER;
+        const int steps = !mixed                 ? CHEB_STEPS
+                          : (R == 1 && dd_now()) ? CHEB_STEPS_DD
+                          : pre_inner            ? CHEB_STEPS_PRE
+                                                 : CHEB_STEPS_INNER;
         if (hc) return apply_hc(false, xin, yout, R, steps);
         if (st) return apply_single(false, xin, yout, R, steps);
         BEM_TRY(gemm_work_on(P0, &B32, n, x32.as<float2>(), xin, z, R));
         BEM_TRY(transfer_add(top, R, xin, z, s));
         return mass_solve(mop, z, yout, R, s, steps);
     };
+    // A x of the multiple-traces system with FP64 arithmetic, before the mass inverse
+    auto raw_fp64 = [&](const double2* xin, double2* zout, int R) -> bem_status {
+        BEM_TRY(gemm_fp64_on(P0, n, xin, zout, R));
+        return transfer_add(top, R, xin, zout, s);
+    };
     Apply apply_fp64 = [&](const double2* xin, double2* yout, int R) -> bem_status {
         if (hc) return apply_hc(true, xin, yout, R, CHEB_STEPS);
         if (st) return apply_single(true, xin, yout, R, CHEB_STEPS);
-        BEM_TRY(gemm_fp64_on(P0, n, xin, z, R));
-        BEM_TRY(transfer_add(top, R, xin, z, s));
+        BEM_TRY(raw_fp64(xin, z, R));
         return mass_solve(mop, z, yout, R, s, CHEB_STEPS);
     };
     // ---- GMRES ------------------------------------------------------------------------
@@ -2352,6 +2369,8 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
     BEM_TRY(dvec.alloc(RB * colb, s));
     BEM_TRY(rvec.alloc(RB * colb, s));
     BEM_TRY(tmp.alloc(RB * colb, s));
+    DevBuf rin;  // S'(b - A x): the inner right-hand side when pre_inner
+    if (pre_inner) BEM_TRY(rin.alloc(RB * colb, s));
     bem_status result = BEM_OK;
     int total_inner = 0, outer_used = 0;
     double worst_res = 0.0;
@@ -2426,6 +2445,17 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
             BEM_CUDA_TRY(cudaMemsetAsync(xsol.p, 0, (size_t)R * colb, s));
             BEM_CUDA_TRY(cudaMemcpyAsync(rvec.p, sb.p, (size_t)R * colb, cudaMemcpyDeviceToDevice, s));
             rn = beta;
+            // inner right-hand side and its norms: S r itself, or S' r with the inner
+            // solves' own preconditioner (the raw residual r = b at x = 0)
+            std::vector<double> rinn(R);
+            double2* inner_rhs = rvec.as<double2>();
+            if (pre_inner) {
+                BEM_TRY(mass_solve(mop, bvec.as<double2>(), rin.as<double2>(), R, s, CHEB_STEPS_PRE));
+                BEM_TRY(norms(W, rin.as<double2>(), R, rinn.data(), s));
+                inner_rhs = rin.as<double2>();
+            } else {
+                rinn = rn;
+            }
             int outer = 0;
             const int max_outer = 12;
             auto pending = [&](int r) {
@@ -2442,9 +2472,9 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                 // a column that is finished (or out of iterations) gets tolerance |r|,
                 // so that its inner GMRES takes no step and its correction is zero
                 for (int r = 0; r < R; ++r)
-                    inner_tol[r] = pending(r) ? std::max(tol_abs[r], inner_rel * rn[r]) : rn[r];
-                BEM_TRY(gmres_run(W, R, apply_work, rvec.as<double2>(), rn.data(), inner_tol.data(),
-                                  dvec.as<double2>(), its.data(), est.data(), s, stop, &inner_progress));
+                    inner_tol[r] = pending(r) ? std::max(tol_abs[r], inner_rel * rinn[r]) : rinn[r];
+                BEM_TRY(gmres_run(W, R, apply_work, inner_rhs, rinn.data(), inner_tol.data(), dvec.as<double2>(),
+                                  its.data(), est.data(), s, stop, &inner_progress));
                 int moved = 0;
                 for (int r = 0; r < R; ++r) {
                     total[r] += its[r];
@@ -2452,10 +2482,23 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                 }
                 BEM_LAUNCH(k_acc, blocks_for((int64_t)R * n, 256), 256, 0, s, xsol.as<double2>(), dvec.as<double2>(),
                            (int64_t)R * n);
-                BEM_TRY(apply_fp64(xsol.as<double2>(), tmp.as<double2>(), R));
-                BEM_LAUNCH(k_sub, blocks_for((int64_t)R * n, 256), 256, 0, s, sb.as<double2>(), tmp.as<double2>(),
-                           (int64_t)R * n, rvec.as<double2>());
-                BEM_TRY(norms(W, rvec.as<double2>(), R, rn.data(), s));
+                if (pre_inner) {
+                    // r = b - A x in FP64 (into dvec, free until the next inner solve); S r for
+                    // the convergence test, S' r for the next inner solve
+                    BEM_TRY(raw_fp64(xsol.as<double2>(), z, R));
+                    BEM_LAUNCH(k_sub, blocks_for((int64_t)R * n, 256), 256, 0, s, bvec.as<double2>(), z,
+                               (int64_t)R * n, dvec.as<double2>());
+                    BEM_TRY(mass_solve(mop, dvec.as<double2>(), rvec.as<double2>(), R, s, CHEB_STEPS));
+                    BEM_TRY(mass_solve(mop, dvec.as<double2>(), rin.as<double2>(), R, s, CHEB_STEPS_PRE));
+                    BEM_TRY(norms(W, rvec.as<double2>(), R, rn.data(), s));
+                    BEM_TRY(norms(W, rin.as<double2>(), R, rinn.data(), s));
+                } else {
+                    BEM_TRY(apply_fp64(xsol.as<double2>(), tmp.as<double2>(), R));
+                    BEM_LAUNCH(k_sub, blocks_for((int64_t)R * n, 256), 256, 0, s, sb.as<double2>(), tmp.as<double2>(),
+                               (int64_t)R * n, rvec.as<double2>());
+                    BEM_TRY(norms(W, rvec.as<double2>(), R, rn.data(), s));
+                    rinn = rn;
+                }
                 ++outer;
                 if (moved == 0) break;
             }
