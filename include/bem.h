@@ -260,7 +260,8 @@ typedef struct {
     int32_t mtf_variant;      /* BEM_MTF_DERIVED (default) or BEM_MTF_PRINTED                     */
     double  center[3];        /* projection centre for the mortar (default origin)               */
     double  ir_inner_tol;     /* BEM_PREC_MIXED: relative residual reduction asked of each inner
-                                 GMRES solve, never below gmres_tol * ||S b|| overall.  0 (default)
+                                 GMRES solve, or the reduction that brings the outer residual to
+                                 half the target where that is less.  0 (default)
                                  chooses: 1e-5 where the inner products are FP32 or tensor-core
                                  products throughout (batches, dd_switch = 1: the true inner
                                  residual stalls near their 1e-7 accuracy, so a second short inner

@@ -1276,6 +1276,16 @@ constexpr int GMRES_LAG = 2;
 // early and a second one starts from the FP64 residual)
 constexpr double IR_INNER_TOL_SINGLE = 1e-8;
 constexpr double IR_INNER_TOL_BATCH = 1e-5;
+
+// Tolerance of an inner solve whose right-hand side has norm rin (in the inner
+// preconditioner's norm) while the outer residual has norm rn against the target
+// tol_abs: a reduction by inner_rel, or by what the last pass needs with a margin of 2
+// (so that the outer residual, measured with the exact mass inverse, lands below the
+// target even where the two norms differ slightly).
+double inner_tolerance(double rin, double rn, double tol_abs, double inner_rel) {
+    const double last = rn > 0.0 ? 0.5 * tol_abs / rn : 1.0;
+    return rin * std::max(inner_rel, last);
+}
 constexpr int GMRES_SLOTS = GMRES_LAG + 2;
 
 using cplx = std::complex<double>;
@@ -2472,7 +2482,7 @@ bem_status solve_transmission_impl(bem_context* ctx, const bem_grid* ge, const b
                 // a column that is finished (or out of iterations) gets tolerance |r|,
                 // so that its inner GMRES takes no step and its correction is zero
                 for (int r = 0; r < R; ++r)
-                    inner_tol[r] = pending(r) ? std::max(tol_abs[r], inner_rel * rinn[r]) : rinn[r];
+                    inner_tol[r] = pending(r) ? inner_tolerance(rinn[r], rn[r], tol_abs[r], inner_rel) : rinn[r];
                 BEM_TRY(gmres_run(W, R, apply_work, inner_rhs, rinn.data(), inner_tol.data(), dvec.as<double2>(),
                                   its.data(), est.data(), s, stop, &inner_progress));
                 int moved = 0;
@@ -3148,7 +3158,7 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     };
     mass_many_eager = [&](const double2* zin, double2* yout, int steps) -> bem_status {
         const unsigned g64 = blocks_for(T, 64);
-        if (steps == CHEB_STEPS_INNER) {  // FP32 iteration (inner solves with FP32 products)
+        if (steps <= CHEB_STEPS_INNER) {  // FP32 iteration (inner solves with FP32 products)
             float2* r32 = reinterpret_cast<float2*>(wr.p);
             float2* da = reinterpret_cast<float2*>(wa.p);
             float2* db = reinterpret_cast<float2*>(wb.p);
@@ -3178,16 +3188,24 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
         }
         return BEM_OK;
     };
+    // FP32 products throughout (dd_switch >= 1): the inner solves precondition with
+    // S' (CHEB_STEPS_PRE) on both sides, as the single-problem solver's
+    const bool pre_inner = o->dd_switch >= 1.0;
     ApplyMany apply_f32 = [&](const double2* xin, double2* yout) -> bem_status {
         BEM_LAUNCH(k_to_c64, blocks_for(T, 256), 256, 0, s, xin, T, x32.as<float2>());
         BEM_TRY(tile_product(PM, TP_F32, 1, x32.p, z.as<double2>(), part.p, tperr.as<int>(), s));
         BEM_LAUNCH(k_transfer_many, blocks_for(T, 64), 64, 0, s, Dd, RI, T, xin, z.as<double2>());
-        return mass_many(z.as<double2>(), yout, CHEB_STEPS_INNER);
+        return mass_many(z.as<double2>(), yout, pre_inner ? CHEB_STEPS_PRE : CHEB_STEPS_INNER);
+    };
+    // A x with double-float products, before the mass inverse
+    auto raw_fp64 = [&](const double2* xin, double2* zout) -> bem_status {
+        BEM_LAUNCH(k_split_x, blocks_for(T, 256), 256, 0, s, xin, T, xsplit.as<float4>());
+        BEM_TRY(tile_product(PM, TP_DD, 1, xsplit.p, zout, part.p, tperr.as<int>(), s));
+        BEM_LAUNCH(k_transfer_many, blocks_for(T, 64), 64, 0, s, Dd, RI, T, xin, zout);
+        return BEM_OK;
     };
     ApplyMany apply_fp64 = [&](const double2* xin, double2* yout) -> bem_status {
-        BEM_LAUNCH(k_split_x, blocks_for(T, 256), 256, 0, s, xin, T, xsplit.as<float4>());
-        BEM_TRY(tile_product(PM, TP_DD, 1, xsplit.p, z.as<double2>(), part.p, tperr.as<int>(), s));
-        BEM_LAUNCH(k_transfer_many, blocks_for(T, 64), 64, 0, s, Dd, RI, T, xin, z.as<double2>());
+        BEM_TRY(raw_fp64(xin, z.as<double2>()));
         return mass_many(z.as<double2>(), yout, CHEB_STEPS);
     };
     // ---- right-hand sides
@@ -3230,6 +3248,16 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     BEM_CUDA_TRY(cudaMemsetAsync(xsol.p, 0, (size_t)T * 16, s));
     BEM_CUDA_TRY(cudaMemcpyAsync(rvec.p, sb.p, (size_t)T * 16, cudaMemcpyDeviceToDevice, s));
     rn = beta;
+    // the inner right-hand side S r, or S' r (pre_inner; r = b at x = 0), and its norms
+    std::vector<double> rinn(rn);
+    DevBuf rin;
+    double2* inner_rhs = rvec.as<double2>();
+    if (pre_inner) {
+        BEM_TRY(rin.alloc((size_t)T * 16, s));
+        BEM_TRY(mass_many(bvec.as<double2>(), rin.as<double2>(), CHEB_STEPS_PRE));
+        BEM_TRY(many_norms(L, W, rin.as<double2>(), rinn.data(), s));
+        inner_rhs = rin.as<double2>();
+    }
     auto pending = [&](int r) {
         return beta[r] > 0.0 && rn[r] > tol_abs[r] && total[r] < o->gmres_maxiter && halted_check(r) == BEM_OK;
     };
@@ -3238,7 +3266,7 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     // a few iterations), FP32 after, as in the single-problem solver
     ApplyMany apply_work = [&](const double2* xin, double2* yout) -> bem_status {
         bool dd = false;
-        for (int r = 0; r < count && !dd; ++r)
+        for (int r = 0; r < count && !dd && !pre_inner; ++r)
             dd = halted[r] == BEM_OK && est[r] > inner_tol[r] && est[r] > o->dd_switch * rn[r];
         return dd ? apply_fp64(xin, yout) : apply_f32(xin, yout);
     };
@@ -3246,11 +3274,11 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
     for (; outer < 12; ++outer) {
         bool any = false;
         for (int r = 0; r < count; ++r) {
-            inner_tol[r] = pending(r) ? std::max(tol_abs[r], inner_rel * rn[r]) : rn[r];
+            inner_tol[r] = pending(r) ? inner_tolerance(rinn[r], rn[r], tol_abs[r], inner_rel) : rinn[r];
             any = any || pending(r);
         }
         if (!any) break;
-        BEM_TRY(gmres_run_many(L, W, apply_work, rvec.as<double2>(), rn.data(), inner_tol.data(), dvec.as<double2>(),
+        BEM_TRY(gmres_run_many(L, W, apply_work, inner_rhs, rinn.data(), inner_tol.data(), dvec.as<double2>(),
                                its.data(), est.data(), halted_check, s));
         int moved = 0;
         for (int r = 0; r < count; ++r) {
@@ -3258,9 +3286,23 @@ bem_status solve_many_impl(bem_context* ctx, int count, const bem_instance* inst
             moved += its[r];
         }
         BEM_LAUNCH(k_acc, blocks_for(T, 256), 256, 0, s, xsol.as<double2>(), dvec.as<double2>(), T);
-        BEM_TRY(apply_fp64(xsol.as<double2>(), tmp.as<double2>()));
-        BEM_LAUNCH(k_sub, blocks_for(T, 256), 256, 0, s, sb.as<double2>(), tmp.as<double2>(), T, rvec.as<double2>());
-        BEM_TRY(many_norms(L, W, rvec.as<double2>(), rn.data(), s));
+        if (pre_inner) {
+            // r = b - A x (into dvec, free until the next inner solve); S r for the test,
+            // S' r for the next inner solve
+            BEM_TRY(raw_fp64(xsol.as<double2>(), tmp.as<double2>()));
+            BEM_LAUNCH(k_sub, blocks_for(T, 256), 256, 0, s, bvec.as<double2>(), tmp.as<double2>(), T,
+                       dvec.as<double2>());
+            BEM_TRY(mass_many(dvec.as<double2>(), rvec.as<double2>(), CHEB_STEPS));
+            BEM_TRY(mass_many(dvec.as<double2>(), rin.as<double2>(), CHEB_STEPS_PRE));
+            BEM_TRY(many_norms(L, W, rvec.as<double2>(), rn.data(), s));
+            BEM_TRY(many_norms(L, W, rin.as<double2>(), rinn.data(), s));
+        } else {
+            BEM_TRY(apply_fp64(xsol.as<double2>(), tmp.as<double2>()));
+            BEM_LAUNCH(k_sub, blocks_for(T, 256), 256, 0, s, sb.as<double2>(), tmp.as<double2>(), T,
+                       rvec.as<double2>());
+            BEM_TRY(many_norms(L, W, rvec.as<double2>(), rn.data(), s));
+            rinn = rn;
+        }
         if (moved == 0) {
             ++outer;
             break;
@@ -3557,7 +3599,7 @@ bem_status solve_screen_impl(bem_context* ctx, const bem_grid* gf, const bem_gri
                                                       : IR_INNER_TOL_SINGLE;
             while (any_pending() && outer < 12) {
                 for (int r = 0; r < R; ++r)
-                    inner_tol[r] = pending(r) ? std::max(tol_abs[r], inner_rel * rn[r]) : rn[r];
+                    inner_tol[r] = pending(r) ? inner_tolerance(rn[r], rn[r], tol_abs[r], inner_rel) : rn[r];
                 BEM_TRY(gmres_run(W, R, apply_work, rvec.as<double2>(), rn.data(), inner_tol.data(), dvec.as<double2>(),
                                   its.data(), est.data(), s, stop, &inner_progress));
                 int moved = 0;
