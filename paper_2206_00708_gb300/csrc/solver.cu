@@ -963,6 +963,88 @@ bem_status launch_combine32(dim3 grid, const float2* Vb, int64_t n, int R, int m
     return BEM_OK;
 }
 
+// CGS2's first update and second projection in one pass over the basis: w_r -= sum_{i<m}
+// h_r[i] V_{i,r} over the block's CD_ROWS rows (as k_combine32: FP32 sums in a fixed
+// order, the update in FP64), then the inner products of the updated rows with the same
+// m basis vectors (as k_dots_partial32), partial[((r * m) + i) * nchunk + block].  The
+// second read of the block's basis rows comes from L1/L2, so the basis crosses HBM three
+// times per iteration instead of four.  m <= COMBINE_HS_MAX (coefficients in shared memory).
+constexpr int CD_ROWS = 128;  // rows per block, 4 per lane
+
+__global__ void __launch_bounds__(256) k_combine_dots32(const float2* __restrict__ Vb, int64_t n, int R, int m,
+                                                        const double2* __restrict__ h, int64_t hstride,
+                                                        double2* __restrict__ w, int nchunk,
+                                                        double2* __restrict__ partial) {
+    extern __shared__ float2 hs2[];
+    __shared__ float2 part[8][CD_ROWS];
+    __shared__ float2 w1s[CD_ROWS];
+    const int r = blockIdx.y, b = blockIdx.x;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int64_t e0 = (int64_t)b * CD_ROWS;
+    const double2* __restrict__ hr = h + r * hstride;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) hs2[i] = make_float2((float)hr[i].x, (float)hr[i].y);
+    __syncthreads();
+    float2 S[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) S[q] = make_float2(0.f, 0.f);
+    for (int i = wp; i < m; i += 8) {
+        const float2 hv = hs2[i];
+        const float2* __restrict__ vi = Vb + ((int64_t)i * R + r) * n;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t e = e0 + lane + 32 * q;
+            if (e < n) {
+                const float2 v = vi[e];
+                S[q].x = fmaf(hv.x, v.x, fmaf(-hv.y, v.y, S[q].x));
+                S[q].y = fmaf(hv.x, v.y, fmaf(hv.y, v.x, S[q].y));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) part[wp][lane + 32 * q] = S[q];
+    __syncthreads();
+    if (threadIdx.x < CD_ROWS) {
+        const int t = threadIdx.x;
+        const int64_t e = e0 + t;
+        float2 acc = part[0][t];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) {
+            acc.x += part[k][t].x;
+            acc.y += part[k][t].y;
+        }
+        float2 wf = make_float2(0.f, 0.f);
+        if (e < n) {
+            double2* wr = w + (int64_t)r * n;
+            const double2 q = wr[e];
+            const double2 u = make_double2(q.x - (double)acc.x, q.y - (double)acc.y);
+            wr[e] = u;
+            wf = make_float2((float)u.x, (float)u.y);
+        }
+        w1s[t] = wf;
+    }
+    __syncthreads();
+    for (int i = wp; i < m; i += 8) {
+        const float2* __restrict__ vi = Vb + ((int64_t)i * R + r) * n;
+        float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t e = e0 + lane + 32 * q;
+            if (e < n) {
+                const float2 v = vi[e];
+                const float2 c = w1s[lane + 32 * q];
+                t.x = fmaf(v.x, c.x, fmaf(v.y, c.y, t.x));
+                t.y = fmaf(v.x, c.y, fmaf(-v.y, c.x, t.y));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+            t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+        }
+        if (lane == 0) partial[((int64_t)r * m + i) * nchunk + b] = make_double2(t.x, t.y);
+    }
+}
+
 // v_r = w_r / |w_r| into the complex64 basis, and the stored value widened into
 // vcur (columns of length n, stride n); |w_r| to dst[r * dstride]
 __global__ void k_normalize32(const double2* __restrict__ w, int64_t n, const double2* __restrict__ nrm2,
@@ -1344,7 +1426,9 @@ struct GmresWork {
             BEM_CUDA_TRY(cudaMemsetAsync(Vb.p, 0, vb, s));
         }
         BEM_TRY(H.alloc((size_t)R * ldh * ldh * 16, s));
-        BEM_TRY(partial.alloc((size_t)R * (maxit + 1) * nblk * 16, s));
+        // inner-product partials: nblk chunks, or the fused kernel's CD_ROWS-row chunks
+        const int64_t nchunk = std::max<int64_t>(nblk, f32 ? (n + CD_ROWS - 1) / CD_ROWS : 0);
+        BEM_TRY(partial.alloc((size_t)R * (maxit + 1) * nchunk * 16, s));
         BEM_TRY(hbuf.alloc((size_t)R * gstride * 16, s));
         BEM_TRY(y.alloc((size_t)R * gstride * 16, s));
         BEM_TRY(w.alloc((size_t)R * n * 16, s));
@@ -1501,21 +1585,39 @@ bem_status gmres_run(GmresWork& W, int R, const Apply& apply, const double2* rhs
             const double2* vj = W.f32 ? W.vcur.as<double2>() : Vp + (int64_t)j * R * n;
             BEM_TRY(apply(vj, W.w.as<double2>(), R));
             double2* Hj = W.H.as<double2>() + (int64_t)j * ldh;  // + r * ldh * ldh per column
-            for (int pass = 0; pass < 2; ++pass) {  // CGS2
-                double2* h = pass == 0 ? Hj : W.hbuf.as<double2>();
-                const int64_t hst = pass == 0 ? ldh * ldh : gs;
-                if (W.f32) {
-                    const unsigned gy = (unsigned)((j + 1 + DOT32_VPB - 1) / DOT32_VPB);
-                    BEM_LAUNCH(k_dots_partial32, dim3(W.nblk, gy, R), 256, 0, s, Vp32, n, R, j + 1,
-                               W.w.as<double2>(), W.nblk, W.partial.as<double2>());
-                } else {
-                    const unsigned gy = (unsigned)((j + 1 + DOT_VPB - 1) / DOT_VPB);
-                    BEM_LAUNCH(k_dots_partial, dim3(W.nblk, gy, R), 256, 0, s, Vp, n, R, j + 1, W.w.as<double2>(),
-                               W.nblk, W.partial.as<double2>());
+            if (W.f32 && j + 1 <= COMBINE_HS_MAX) {
+                // CGS2 with the first update and the second projection fused
+                const unsigned gy = (unsigned)((j + 1 + DOT32_VPB - 1) / DOT32_VPB);
+                const int nch = (int)((n + CD_ROWS - 1) / CD_ROWS);
+                BEM_LAUNCH(k_dots_partial32, dim3(W.nblk, gy, R), 256, 0, s, Vp32, n, R, j + 1, W.w.as<double2>(),
+                           W.nblk, W.partial.as<double2>());
+                BEM_LAUNCH(k_dots_final, dim3(j + 1, R), 32, 0, s, W.partial.as<double2>(), j + 1, W.nblk, Hj,
+                           ldh * ldh, 0);
+                BEM_LAUNCH(k_combine_dots32, dim3(nch, R), 256, (size_t)(j + 1) * sizeof(float2), s, Vp32, n, R,
+                           j + 1, Hj, ldh * ldh, W.w.as<double2>(), nch, W.partial.as<double2>());
+                BEM_LAUNCH(k_dots_final, dim3(j + 1, R), 32, 0, s, W.partial.as<double2>(), j + 1, nch,
+                           W.hbuf.as<double2>(), gs, 0);
+                BEM_TRY(launch_combine32(ecb, Vp32, n, R, j + 1, nullptr, W.hbuf.as<double2>(), gs, W.w.as<double2>(),
+                                         0, s));
+            } else {
+                for (int pass = 0; pass < 2; ++pass) {  // CGS2
+                    double2* h = pass == 0 ? Hj : W.hbuf.as<double2>();
+                    const int64_t hst = pass == 0 ? ldh * ldh : gs;
+                    if (W.f32) {
+                        const unsigned gy = (unsigned)((j + 1 + DOT32_VPB - 1) / DOT32_VPB);
+                        BEM_LAUNCH(k_dots_partial32, dim3(W.nblk, gy, R), 256, 0, s, Vp32, n, R, j + 1,
+                                   W.w.as<double2>(), W.nblk, W.partial.as<double2>());
+                    } else {
+                        const unsigned gy = (unsigned)((j + 1 + DOT_VPB - 1) / DOT_VPB);
+                        BEM_LAUNCH(k_dots_partial, dim3(W.nblk, gy, R), 256, 0, s, Vp, n, R, j + 1,
+                                   W.w.as<double2>(), W.nblk, W.partial.as<double2>());
+                    }
+                    BEM_LAUNCH(k_dots_final, dim3(j + 1, R), 32, 0, s, W.partial.as<double2>(), j + 1, W.nblk, h,
+                               hst, 0);
+                    if (W.f32)
+                        BEM_TRY(launch_combine32(ecb, Vp32, n, R, j + 1, nullptr, h, hst, W.w.as<double2>(), 0, s));
+                    else BEM_TRY(launch_combine(ecb, Vp, n, R, j + 1, nullptr, h, hst, W.w.as<double2>(), 0, s));
                 }
-                BEM_LAUNCH(k_dots_final, dim3(j + 1, R), 32, 0, s, W.partial.as<double2>(), j + 1, W.nblk, h, hst, 0);
-                if (W.f32) BEM_TRY(launch_combine32(ecb, Vp32, n, R, j + 1, nullptr, h, hst, W.w.as<double2>(), 0, s));
-                else BEM_TRY(launch_combine(ecb, Vp, n, R, j + 1, nullptr, h, hst, W.w.as<double2>(), 0, s));
             }
             BEM_LAUNCH(k_add_cols, dim3(1, R), 256, 0, s, Hj, ldh * ldh, W.hbuf.as<double2>(), gs, j + 1);
             BEM_TRY(W.sq_norms(W.w.as<double2>(), s));
