@@ -91,7 +91,10 @@ int64_t working_set_bytes(int64_t ne, int64_t ni, int precision, int maxiter, in
     // the solver advances up to 64 (mixed precision, tensor-core products) or 8
     // right-hand sides together, each with its own Krylov basis and Hessenberg matrix
     const int64_t R = std::max(1, std::min(n_rhs, precision == BEM_PREC_MIXED ? 64 : 8));
-    const int64_t krylov = R * (m * n * 16 + m * m * 16 + m * 64 * 16);
+    // basis (counted at 16 bytes per entry: complex128, or complex64 plus slack), Hessenberg,
+    // and the inner-product partials of the row chunks (256 rows, or 128 for the fused pass)
+    const int64_t chunks = std::max<int64_t>(std::min<int64_t>(1216, (n + 255) / 256), (n + 127) / 128);
+    const int64_t krylov = R * (m * n * 16 + m * m * 16 + m * chunks * 16) + (R + 8) * n * 16;
     const int64_t vectors = 16 * (R + 8) * n * 16;
     // partial sums of the tile products (8 columns, double-float) and the input splits
     const int64_t partial = 2 * (te * te + ti * ti) * OPT * 8 * 16 + 8 * n * 16;
